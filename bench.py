@@ -1,0 +1,282 @@
+#!/usr/bin/env python
+"""Benchmark of the OAIS engine on the Bayesian logistic-regression workload.
+
+Workload (synthetic, seeded): X 2000x32 iid N(0,1) fp32, w ~ N(0, I), y ~ Bern(sigmoid(Xw)),
+prior N(0, I_32); N = 2^16 particles; 4 OAIS rounds with T = 256, 512, 1024, 2048
+(Alg. 2 with Budget doubling T; the first round on the linear schedule, later rounds on
+the OptimiseSchedule output); MALA moves with per-step sizes carried and adapted between
+rounds.  One benchmark step is that whole job: every sweep, moment merge, log-sum-exp and
+schedule update.  Metric: particle-steps per second (N x sum of T over the rounds).
+
+--impl reference times the FP64 CPU checker (oracle/) on the host cores on a bounded
+sample of the same workload; it is a deliberately slow program, reported for context.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PARTICLES = 1 << 16
+ROUNDS_T = [256, 512, 1024, 2048]
+SE_TARGET = 0.01
+WORKLOAD = "logreg_n2000_d32_N65536_T256-512-1024-2048_mala"
+METRIC = "particle-steps/s"
+FP32_LANES_PER_SM, N_SM = 128, 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_flops_per_particle_step(pr):
+    # MALA: one log L + grad evaluation per step: z = X x (2 n d) and X^T r (2 n d)
+    return 4.0 * pr.n * pr.d
+
+
+def cpu_baseline(pr, seconds):
+    """The FP64 checker on the host cores: one T=256 round of MALA for a bounded particle sample."""
+    import oracle as o
+    from paper_2408_12057_gb300 import oais
+    T = ROUNDS_T[0]
+    beta = np.linspace(0.0, 1.0, T + 1)
+    eps = oais.default_step_sizes(pr, beta, oais.MALA)
+    tg = o.Target(pr.kind, pr.X, pr.y, pr.ref_scale, pr.p0)
+    t0 = time.perf_counter()
+    o.asmc(tg, o.MALA, 16, beta, eps, seed=1)
+    probe = max(time.perf_counter() - t0, 1e-3)
+    n = int(max(16, min(N_PARTICLES, 16 * seconds / probe)))
+    t0 = time.perf_counter()
+    o.asmc(tg, o.MALA, n, beta, eps, seed=1)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n * T / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {N_PARTICLES} particles, one T={T} MALA round (linear schedule), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2408_12057_gb300 import workloads as W
+    pr = W.logistic()
+    vals = []
+    cb = None
+    for _ in range(args.warmup):
+        cpu_baseline(pr, min(args.cpu_seconds, 5.0))
+    for _ in range(args.steps):
+        cb = cpu_baseline(pr, args.cpu_seconds)
+        vals.append(cb["value"])
+    v = float(np.mean(vals))
+    cb["value"] = v
+    ps_per_job = N_PARTICLES * sum(ROUNDS_T)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ps_per_job / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2408_12057_gb300 import oais, workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pr = W.logistic()
+    stream = torch.cuda.current_stream()
+    T0 = ROUNDS_T[0]
+    beta0 = np.linspace(0.0, 1.0, T0 + 1)
+    eps0 = oais.default_step_sizes(pr, beta0, oais.MALA)
+    # each rank owns a disjoint block of the particle counter space (weak scaling)
+    run = oais.OAIS(pr, oais.MALA, N_PARTICLES, beta0, T_max=max(ROUNDS_T), eps=eps0,
+                    seed=12057 + rank * 7919, adapt=True, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def job():
+        run.set_schedule(beta0, eps0)
+        res = []
+        for k, T in enumerate(ROUNDS_T):
+            nxt = ROUNDS_T[min(k + 1, len(ROUNDS_T) - 1)]
+            res.append(run.round(nxt))
+        return res
+
+    for _ in range(args.warmup):
+        job()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, sweep_ms, last = [], [], None
+    for _ in range(args.steps):
+        flush.zero_()                       # L2 flushed between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        last = job()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        sweep_ms.append(sum(r["sweep_ms"] for r in last))
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ps_per_job = N_PARTICLES * sum(ROUNDS_T)
+    value = world * ps_per_job * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the sweep): FP32 FMA-pipe bound
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 2.0 * FP32_LANES_PER_SM * N_SM * sm_max * 1e6 / 1e12     # TFLOP/s
+    flops = algorithmic_flops_per_particle_step(pr) * ps_per_job * args.steps
+    achieved = flops / (sum(sweep_ms) / 1e3) / 1e12
+    roofline = {"bound": "alu", "pipe": "fp32 fma", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                               f"(sm_max_mhz of {peak_src} peaks)",
+                "kernel": "oais_sweep_kernel<RowsTarget<32,logistic>, MALA>",
+                "sweep_share_of_step": sum(sweep_ms) / sum(step_ms)}
+
+    se_last = last[-1]["se"]
+    sec_to_se = (total_ms / 1e3 / args.steps) * (se_last / SE_TARGET) ** 2
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = measure_e2e(pr, eps0, beta0, args.steps)
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(pr, args.cpu_seconds)
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N_per_gpu": N_PARTICLES, "T_rounds": ROUNDS_T,
+                       "move": "MALA", "l2": "flushed between timed steps (256 MiB write)",
+                       "log_weights": "f64"},
+            "logZ_last_round": last[-1]["logZ"], "se_last_round": se_last,
+            "sec_to_logZ_se_0.01": sec_to_se,
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cb,
+            "gpu_launches": 4 * len(ROUNDS_T) * args.steps,
+            "clocks": clk,
+        }))
+    run.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_e2e(pr, eps0, beta0, steps):
+    """Same job through the public API with host inputs: init from host X, y (copied to the
+    device inside the timed region), 4 rounds, results read back to the host every round."""
+    import torch
+    from paper_2408_12057_gb300 import oais
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        run = oais.OAIS(pr, oais.MALA, N_PARTICLES, beta0, T_max=max(ROUNDS_T), eps=eps0, seed=99,
+                        adapt=True, data_on_device=False)
+        for k, T in enumerate(ROUNDS_T):
+            run.round(ROUNDS_T[min(k + 1, len(ROUNDS_T) - 1)])
+        run.logZ()
+        run.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = 4 * (pr.X.size + pr.y.size) + sum(8 * (2 * T + 1) for T in ROUNDS_T)
+    d2h = sum(8 * (4 * T + 2) + 4 for T in ROUNDS_T)
+    return {"value": N_PARTICLES * sum(ROUNDS_T) * steps / dt, "unit": METRIC,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "includes": "context init with host data (workspace allocation included), 4 rounds"}
+
+
+if __name__ == "__main__":
+    main()

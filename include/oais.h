@@ -1,0 +1,190 @@
+/*
+ * oais.h -- C ABI of the GB300 (sm_103a) Optimised Annealed Importance Sampling engine.
+ *
+ * Method: Syed, Bouchard-Cote, Chern, Doucet, "Optimised Annealed Sequential Monte
+ * Carlo Samplers" (arXiv 2408.12057).  N particles move through an annealing
+ * schedule 0 = beta_0 < ... < beta_T = 1 on the geometric path
+ * pi_beta ∝ eta(x) L(x)^beta (Sec. 2), eta = N(0, s^2 I) the normalised reference.
+ * Each step adds the incremental weight (beta_t - beta_{t-1}) log L(x) at the
+ * pre-move state, reduces the moment statistics g_hat_{t,0:2} (Alg. 1), and applies
+ * K Metropolis-Hastings moves targeting pi_{beta_t}.  log Z_hat is a logsumexp of the
+ * final weights (eq. estimator_Z).  Between rounds the cumulative barrier
+ * Lambda_hat_t = sum_{s<=t} sqrt(D_hat_s) is inverted into the next schedule
+ * (Alg. 2, Alg. 3).  asmc_run adds ESS-triggered systematic resampling (Sec. 2.1.3).
+ *
+ * Conventions for every entry point:
+ *   - every call returns an oais_status; nothing aborts, throws or exits;
+ *   - "device pointer" arguments must be CUDA device memory of the current device;
+ *     "host pointer" arguments must be host memory; sizes are element counts;
+ *   - stream arguments are cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Calls are ordered on that stream.
+ *   - a context is used by one host thread at a time.
+ *   - after OAIS_ECUDA the CUDA error text is in oais_last_error(ctx) (or
+ *     oais_last_error(NULL) for calls without a context).
+ */
+#ifndef OAIS_H_
+#define OAIS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OAIS_OK = 0,
+    OAIS_EINVAL = 1,        /* bad argument: sizes, schedule not strictly increasing 0..1, ... */
+    OAIS_ENOMEM = 2,        /* device allocation failed or workspace too small */
+    OAIS_ECUDA = 3,         /* a CUDA runtime call failed */
+    OAIS_ENONFINITE = 4,    /* a log-weight or log-likelihood became NaN/inf */
+    OAIS_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    OAIS_EUNSUPPORTED = 6   /* combination not built (dimension, family, move) */
+} oais_status;
+
+/* Target families (Sec. 2 geometric path; likelihood L, reference eta = N(0, s^2 I)). */
+typedef enum {
+    OAIS_T_GAUSS = 0,   /* L(x) = exp(-|x - mu|^2 / (2 p0^2)); X = mu[d]                   */
+    OAIS_T_LOGREG = 1,  /* L(x) = prod_r Bern(y_r | sigmoid(X_r . x)); X[n][d], y[n] in {0,1} */
+    OAIS_T_GMM = 2,     /* L(x) = p(x)/eta(x), p = (1/n) sum_k N(X_k, p0 I); X[n][d] means   */
+    OAIS_T_LINREG = 3   /* L(x) = prod_r N(y_r; X_r . x, p0^2); X[n][d], y[n]               */
+} oais_target_kind;
+
+typedef enum { OAIS_DT_F64 = 0, OAIS_DT_F32 = 1 } oais_dtype;
+
+typedef struct {
+    int32_t kind;       /* oais_target_kind */
+    int32_t d;          /* state dimension, 1 <= d <= 32 (GAUSS: <= 16) */
+    int32_t n;          /* rows of X (LOGREG, LINREG), mixture components (GMM, <= 16); 0 for GAUSS */
+    int32_t dtype;      /* oais_dtype of X and y: GAUSS runs in F64 and takes F64 mu;
+                           the other families run in F32 and take F32 or F64 input */
+    const void* X;      /* row-major, see kind; host or device per on_device */
+    const void* y;      /* [n] (LOGREG, LINREG), else NULL */
+    double ref_scale;   /* s > 0 */
+    double p0;          /* GAUSS: likelihood sigma; GMM: component variance; LINREG: noise sigma */
+    int32_t on_device;  /* 0: X, y are host memory, copied at init.  1: device memory, also copied
+                           (to the padded device layout); the caller may free them after init */
+} oais_target;
+
+typedef enum { OAIS_RWMH = 0, OAIS_MALA = 1, OAIS_HMC = 2 } oais_move_kind;
+
+typedef struct {
+    int32_t kind;       /* oais_move_kind; each is a pi_beta-invariant MH kernel (Sec. 2.1.1) */
+    int32_t moves;      /* K >= 1 moves per annealing step */
+    int32_t leapfrog;   /* HMC leapfrog steps (>= 1) */
+    int32_t cycle;      /* RWMH only: proposal std cycles 0.1, 1, 10 by global move index
+                           (the alternation of the paper's GPU experiments, App. E.3) */
+    int32_t adapt;      /* 1: between rounds rescale step sizes toward a target acceptance
+                           (App. on propagation-kernel adaptation); 0: keep them */
+} oais_move;
+
+typedef struct {
+    double logZ;        /* log Z_hat of the round (eq. estimator_Z with R = 1) */
+    double se;          /* delta-method standard error of log Z_hat: sqrt(1/ESS - 1/N) */
+    double Lambda_hat;  /* Lambda_hat_T = sum_t sqrt(D_hat_t) (Alg. 3) */
+    double ess;         /* ESS of the final weights, (sum w)^2 / sum w^2 */
+    double sweep_ms;    /* device time of the sweep kernel, CUDA events */
+    int32_t T;          /* steps run this round */
+    int32_t round;      /* 0-based index of the round */
+    int32_t n_resample; /* asmc_run: intermediate resampling events; 0 for OAIS */
+    int32_t pad;
+} oais_round_result;
+
+typedef struct oais_ctx oais_ctx;
+
+/* Device bytes oais_init needs for this problem when it is given a workspace.
+ * N particles, schedules of at most T_max steps. */
+oais_status oais_workspace_bytes(const oais_target* target, const oais_move* move, int64_t N,
+                                 int32_t T_max, size_t* bytes);
+
+/* Create a context (Alg. 2 state).  beta: host [T+1], 0 = beta_0 < ... < beta_T = 1, the
+ * schedule of the first round (the paper's Alg. 2 starts from T = 1, beta = (0, 1)).
+ * eps: host [T] step sizes per step (RWMH proposal std, MALA/HMC step), or NULL for
+ * 0.5/sqrt(d).  workspace: device memory of at least oais_workspace_bytes(), owned by the
+ * caller and kept alive until oais_destroy; NULL lets the library cudaMalloc its own.
+ * stream: cudaStream_t for all work of this context (NULL: default stream).
+ * Errors: EINVAL (bad sizes, schedule), EUNSUPPORTED (d/kind/move not built), ENOMEM, ECUDA. */
+oais_status oais_init(oais_ctx** ctx, const oais_target* target, const oais_move* move,
+                      int64_t N, const double* beta, int32_t T, int32_t T_max, const double* eps,
+                      uint64_t seed, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One round of OAIS (Alg. 2 body): run the loop-swapped sweep with the current schedule,
+ * merge the per-step moments, form log Z_hat, then install
+ * OptimiseSchedule(T_next, B_T, g_hat) (Alg. 3) as the schedule of the next round.
+ * T_next <= T_max.  Synchronises the context's stream.  On error the previous round's
+ * results and the current schedule are left unchanged (anytime property, Sec. 1). */
+oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out);
+
+/* log Z_hat and its delta-method SE from the last completed round. EINVAL if none. */
+oais_status oais_logZ(const oais_ctx* ctx, double* logZ, double* se);
+
+/* Statistics of the last completed round, host arrays sized by *T (query with NULLs):
+ * log_ghat [T][3] = log g_hat_{t,i}; D_hat [T]; beta [T+1] (the schedule that ran);
+ * accept [T] mean MH acceptance per step.  Any output pointer may be NULL. */
+oais_status oais_get_stats(const oais_ctx* ctx, double* log_ghat, double* D_hat, double* beta,
+                           double* accept, int32_t* T);
+
+/* The schedule the next round will run (host [*T + 1]; query *T with beta = NULL) and
+ * its step sizes (host [*T], may be NULL). */
+oais_status oais_get_schedule(const oais_ctx* ctx, double* beta, double* eps, int32_t* T);
+
+/* Replace the next round's schedule and step sizes (host arrays; eps may be NULL to keep
+ * the rule 0.5/sqrt(d)). */
+oais_status oais_set_schedule(oais_ctx* ctx, const double* beta, const double* eps, int32_t T);
+
+/* Final particles of the last round: logw [N] (log w_T), ell [N] (log L(X_T)) as double,
+ * x [d][N] structure-of-arrays in the family's precision (double for GAUSS, float otherwise).
+ * Device pointers of the context's workspace, valid until the next round or oais_destroy. */
+oais_status oais_particles(const oais_ctx* ctx, const double** logw, const double** ell,
+                           const void** x);
+
+void oais_destroy(oais_ctx* ctx);
+const char* oais_last_error(const oais_ctx* ctx);
+const char* oais_status_string(oais_status s);
+
+/* Alg. 3 OptimiseSchedule on the host: D_hat_t = log g2 - 2 log g1 + log g0 (clamped at 0),
+ * Lambda_hat_t = cumulative sum of sqrt(D_hat), a monotone cubic Hermite interpolant through
+ * the knots (Lambda_hat_t, beta_t) (equal Lambda_hat knots dropped, the first kept), and
+ * beta*_t' = interp(Lambda_hat_T t'/T').  All host arrays: beta [T+1], log_ghat [T][3],
+ * beta_next [T_next+1], D_hat [T] and Lambda [T+1] (both may be NULL).  No device work. */
+oais_status oais_optimise_schedule(int32_t T, const double* beta, const double* log_ghat,
+                                   int32_t T_next, double* beta_next, double* D_hat,
+                                   double* Lambda);
+
+/* ---------------------------------------------------------------------------------
+ * Kernel-level entry points (device pointers only, no host synchronisation).
+ * --------------------------------------------------------------------------------- */
+
+/* Number of StepPartial records per step the sweep writes for N particles (one per CTA). */
+int32_t oais_sweep_blocks(int64_t N);
+
+/* Bytes of one StepPartial record: shift m[3] (double), sum s[3] (double), accepted (u32). */
+int32_t oais_step_partial_bytes(void);
+
+/* The loop-swapped OAIS sweep (Alg. 1 with the particle loop outside, Sec. 5.1.2) over
+ * particles n_offset .. n_offset+N-1 of the counter space.
+ * d_data: the padded device layout built by oais_prepare_target (opaque, from the context) --
+ * use oais_ctx_sweep instead unless you manage it yourself.  Outputs (device):
+ * logw [N], ell [N] doubles, x [d][N], partials [T][oais_sweep_blocks(N)] records,
+ * status (u32, bit 0 set on a non-finite value; the caller zeroes it).
+ * tag = round | (problem << 16) selects the random streams. */
+oais_status oais_ctx_sweep(oais_ctx* ctx, int32_t T, const double* d_beta, const double* d_eps,
+                           uint64_t seed, uint32_t tag, int64_t n_offset, int64_t N,
+                           double* d_logw, double* d_ell, void* d_x, void* d_partials,
+                           uint32_t* d_status, void* stream);
+
+/* Merge the per-CTA records of every step in a fixed order (deterministic):
+ * log_ghat [T][3] = log g_hat_{t,i}, accept [T] = accepted / (N * moves).  Device pointers. */
+oais_status oais_merge_stats(const void* d_partials, int32_t nblocks, int32_t T, int64_t N,
+                             int32_t moves, double* d_log_ghat, double* d_accept, void* stream);
+
+/* out[0] = log sum_n exp(a_n), out[1] = log sum_n exp(2 a_n), deterministic two-pass
+ * reduction.  d_scratch: device memory of oais_logsumexp_scratch_bytes(n). */
+size_t oais_logsumexp_scratch_bytes(int64_t n);
+oais_status oais_logsumexp(const double* d_a, int64_t n, double* d_out, void* d_scratch,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OAIS_H_ */

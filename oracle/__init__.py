@@ -87,7 +87,7 @@ def _load():
             lib.orc_logsumexp.argtypes = [P, i64]
             lib.orc_logsumexp.restype = f64
             lib.orc_systematic_resample.argtypes = [i64, P, f64, P]
-            lib.orc_asmc.argtypes = [P, P, i64, i32, P, P, u64, u32, f64,
+            lib.orc_asmc.argtypes = [P, P, i64, i32, P, P, u64, u32, i64, f64,
                                      P, P, P, P, P, P, P, P, P]
             lib.orc_asmc.restype = i32
             lib.orc_pchip_slopes.argtypes = [i32, P, P, P]
@@ -183,9 +183,11 @@ def systematic_resample(logw, U):
 
 
 def asmc(target: Target, move_kind, N, beta, eps, seed, tag=0, moves=1, leapfrog=1,
-         cycle=False, ess_frac=0.0):
+         cycle=False, ess_frac=0.0, n_offset=0):
     """Alg. 1.  Returns a dict with logZ, log_ghat (T,3), accept (T,), ess (T,),
-    logw (N,), x (N,d), ell (N,), margin (N,), resampled (T,), n_resample."""
+    logw (N,), x (N,d), ell (N,), margin (N,), resampled (T,), n_resample.
+    Particle n draws from counter n_offset + n (AIS particles are independent, so a
+    subset of a large run can be recomputed on its own)."""
     lib = _load()
     beta = _f64(beta)
     T = beta.size - 1
@@ -196,7 +198,7 @@ def asmc(target: Target, move_kind, N, beta, eps, seed, tag=0, moves=1, leapfrog
                logw=np.zeros(N), x=np.zeros((N, target.d)), ell=np.zeros(N),
                margin=np.zeros(N), resampled=np.zeros(T, dtype=np.int64))
     rc = lib.orc_asmc(ctypes.byref(target._c), ctypes.byref(mv), int(N), int(T), _ptr(beta),
-                      _ptr(eps), int(seed), int(tag), float(ess_frac), ctypes.byref(res),
+                      _ptr(eps), int(seed), int(tag), int(n_offset), float(ess_frac), ctypes.byref(res),
                       _ptr(out["log_ghat"]), _ptr(out["accept"]), _ptr(out["ess"]),
                       _ptr(out["logw"]), _ptr(out["x"]), _ptr(out["ell"]), _ptr(out["margin"]),
                       _ptr(out["resampled"]))

@@ -356,7 +356,7 @@ typedef struct {
 
 int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const double* beta,
              const double* eps /* T per-step sizes */, uint64_t seed, uint32_t tag,
-             double ess_frac,
+             long n_offset /* particle n uses counter n_offset + n */, double ess_frac,
              /* outputs (any may be NULL except res) */
              orc_result* res, double* log_ghat /* T x 3 */, double* accept /* T */,
              double* ess_trace /* T */, double* logw_out /* N */, double* x_out /* N x d */,
@@ -376,7 +376,7 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
 
     /* t = 0: X_0^n ~ eta, w_0^n = 1 */
     for (long n = 0; n < N; ++n) {
-        orc_normals(seed, (uint32_t)n, 0u, 0u, tag, d, X + n * d);
+        orc_normals(seed, (uint32_t)(n_offset + n), 0u, 0u, tag, d, X + n * d);
         for (int i = 0; i < d; ++i) X[n * d + i] *= tg->ref_scale;
         ell[n] = orc_log_lik(tg, X + n * d, need_grad ? G + n * d : NULL);
         logw[n] = 0.0;
@@ -406,7 +406,7 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
             particle_ref p = {X + n * d, ell[n], G + n * d};
             int a = 0;
             for (int k = 0; k < mv->moves; ++k)
-                a += mh_move(tg, mv, beta[t], eps[t - 1], seed, (uint32_t)n, (uint32_t)t,
+                a += mh_move(tg, mv, beta[t], eps[t - 1], seed, (uint32_t)(n_offset + n), (uint32_t)t,
                              (uint32_t)k, tag, (t - 1) * mv->moves + k, &p, &margin[n], wk);
             ell[n] = p.ell;
             acc_count[n] = a;

@@ -1,0 +1,564 @@
+// api.cu -- host side of the C ABI: context lifetime, the OAIS round driver (Alg. 2),
+// OptimiseSchedule (Alg. 3) and step-size carry-over between rounds.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "../../include/oais.h"
+
+namespace oais {
+cudaError_t launch_merge_stats(const StepPartial*, int, int, double, double*, double*, cudaStream_t);
+cudaError_t launch_logsumexp(const double*, int64_t, double*, void*, cudaStream_t);
+size_t logsumexp_scratch_bytes(int64_t n);
+
+int padded_width(int kind, int d)
+{
+    static const int gauss[] = {1, 2, 4, 8, 16}, rows[] = {2, 4, 8, 16, 32}, gmm[] = {2, 4, 8, 16};
+    const int* w = rows; int nw = 5;
+    if (kind == kGauss) { w = gauss; nw = 5; }
+    else if (kind == kGmm) { w = gmm; nw = 4; }
+    for (int i = 0; i < nw; ++i) if (d <= w[i]) return w[i];
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Monotone piecewise-cubic Hermite interpolant (Fritsch & Carlson 1980; interior slopes
+// by the weighted harmonic mean of Fritsch & Butland 1984; shape-preserving three-point
+// end slopes).  This is the reading of Alg. 3's "monotone spline".
+// ---------------------------------------------------------------------------
+class MonotoneCubic {
+public:
+    MonotoneCubic(std::vector<double> xs, std::vector<double> ys) : x_(std::move(xs)), y_(std::move(ys)) {
+        const size_t K = x_.size();
+        slope_.assign(K, 0.0);
+        std::vector<double> h(K - 1), sec(K - 1);
+        for (size_t i = 0; i + 1 < K; ++i) { h[i] = x_[i + 1] - x_[i]; sec[i] = (y_[i + 1] - y_[i]) / h[i]; }
+        if (K == 2) { slope_[0] = slope_[1] = sec[0]; return; }
+        for (size_t k = 1; k + 1 < K; ++k) {
+            if (sec[k - 1] * sec[k] > 0.0) {
+                const double a = 2.0 * h[k] + h[k - 1], b = h[k] + 2.0 * h[k - 1];
+                slope_[k] = (a + b) / (a / sec[k - 1] + b / sec[k]);
+            }
+        }
+        slope_[0] = end(h[0], h[1], sec[0], sec[1]);
+        slope_[K - 1] = end(h[K - 2], h[K - 3], sec[K - 2], sec[K - 3]);
+    }
+    double operator()(double v) const {
+        const size_t K = x_.size();
+        size_t i = std::upper_bound(x_.begin(), x_.end(), v) - x_.begin();
+        i = (i == 0) ? 0 : std::min(i - 1, K - 2);
+        const double h = x_[i + 1] - x_[i], u = (v - x_[i]) / h, w = 1.0 - u;
+        return y_[i] * w * w * (1.0 + 2.0 * u) + y_[i + 1] * u * u * (3.0 - 2.0 * u)
+             + h * (slope_[i] * u * w * w - slope_[i + 1] * u * u * w);
+    }
+private:
+    static int sgn(double v) { return (v > 0.0) - (v < 0.0); }
+    static double end(double h0, double h1, double s0, double s1) {
+        const double e = ((2.0 * h0 + h1) * s0 - h0 * s1) / (h0 + h1);
+        if (sgn(e) != sgn(s0)) return 0.0;
+        if (sgn(s0) != sgn(s1) && std::fabs(e) > 3.0 * std::fabs(s0)) return 3.0 * s0;
+        return e;
+    }
+    std::vector<double> x_, y_, slope_;
+};
+
+static void optimise_schedule(int T, const double* beta, const double* lg, int Tn, double* out,
+                              double* D_out, double* Lam_out)
+{
+    std::vector<double> Lam(T + 1, 0.0);
+    for (int t = 1; t <= T; ++t) {
+        double D = lg[3 * (t - 1) + 2] - 2.0 * lg[3 * (t - 1) + 1] + lg[3 * (t - 1)];
+        D = (D > 0.0) ? D : 0.0;   // NaN and rounding negatives count as zero
+        if (D_out) D_out[t - 1] = D;
+        Lam[t] = Lam[t - 1] + std::sqrt(D);
+    }
+    if (Lam_out) std::copy(Lam.begin(), Lam.end(), Lam_out);
+    std::vector<double> kx, ky;
+    for (int t = 0; t <= T; ++t) {
+        if (!kx.empty() && !(Lam[t] > kx.back())) continue;
+        kx.push_back(Lam[t]);
+        ky.push_back(beta[t]);
+    }
+    if (kx.size() < 2) {
+        for (int i = 0; i <= Tn; ++i) out[i] = (double)i / Tn;
+    } else {
+        ky.back() = beta[T];
+        MonotoneCubic f(kx, ky);
+        for (int i = 0; i <= Tn; ++i) out[i] = f(Lam[T] * ((double)i / Tn));
+    }
+    out[0] = 0.0;
+    out[Tn] = 1.0;
+}
+
+static bool valid_schedule(const double* beta, int T)
+{
+    if (T < 1 || !beta || beta[0] != 0.0 || beta[T] != 1.0) return false;
+    for (int t = 1; t <= T; ++t) if (!(beta[t] > beta[t - 1]) || !std::isfinite(beta[t])) return false;
+    return true;
+}
+
+} // namespace oais
+
+using namespace oais;
+
+static thread_local std::string g_err;
+
+struct oais_ctx {
+    oais_target tg_in{};
+    oais_move mv{};
+    DevTarget dt;
+    int64_t N = 0;
+    int T_max = 0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    // device workspace
+    void* ws = nullptr;
+    bool own_ws = false;
+    double *d_beta = nullptr, *d_eps = nullptr, *d_logw = nullptr, *d_ell = nullptr;
+    void* d_x = nullptr;
+    StepPartial* d_parts = nullptr;
+    double *d_log_ghat = nullptr, *d_accept = nullptr, *d_lse = nullptr;
+    void* d_lse_scratch = nullptr;
+    unsigned* d_status = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // schedule of the next round
+    std::vector<double> beta, eps;
+    int round = 0;
+    // last completed round
+    bool have_last = false;
+    std::vector<double> l_beta, l_eps, l_log_ghat, l_D, l_accept;
+    double l_logZ = 0, l_se = 0, l_Lambda = 0, l_ess = 0;
+    std::string err;
+};
+
+#define CK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            set_err(ctx, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+            return OAIS_ECUDA;                                                       \
+        }                                                                            \
+    } while (0)
+
+static void set_err(oais_ctx* ctx, const std::string& m)
+{
+    if (ctx) ctx->err = m; else g_err = m;
+}
+
+static oais_status fail(oais_ctx* ctx, oais_status s, const std::string& m)
+{
+    set_err(ctx, m);
+    return s;
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static size_t elt_bytes(int kind) { return kind == kGauss ? sizeof(double) : sizeof(float); }
+
+struct Layout {
+    size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, lse, lse_scr, status, total;
+};
+
+static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
+{
+    Layout L{};
+    const int n_pad = (tg->n + 3) & ~3;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes ? bytes : 1); return o; };
+    size_t xb;
+    if (tg->kind == kGauss) xb = sizeof(double) * D;
+    else if (tg->kind == kGmm) xb = sizeof(float) * (size_t)tg->n * D;
+    else xb = sizeof(float) * (size_t)n_pad * D;
+    L.X = take(xb);
+    L.y = take((tg->kind == kLogreg || tg->kind == kLinreg) ? sizeof(float) * n_pad : 0);
+    L.beta = take(sizeof(double) * (T_max + 1));
+    L.eps = take(sizeof(double) * T_max);
+    L.logw = take(sizeof(double) * N);
+    L.ell = take(sizeof(double) * N);
+    L.x = take(elt_bytes(tg->kind) * (size_t)tg->d * N);
+    L.parts = take(sizeof(StepPartial) * (size_t)T_max * sweep_grid(N));
+    L.lg = take(sizeof(double) * 3 * T_max);
+    L.acc = take(sizeof(double) * T_max);
+    L.lse = take(sizeof(double) * 2);
+    L.lse_scr = take(logsumexp_scratch_bytes(N));
+    L.status = take(sizeof(unsigned));
+    L.total = off;
+    return L;
+}
+
+static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais_move* mv, int64_t N,
+                                int T_max, int* D)
+{
+    if (!tg || !mv) return fail(ctx, OAIS_EINVAL, "null target or move");
+    if (tg->kind < 0 || tg->kind > 3) return fail(ctx, OAIS_EINVAL, "unknown target kind");
+    if (tg->d < 1 || !tg->X) return fail(ctx, OAIS_EINVAL, "bad dimension or missing X");
+    if (!(tg->ref_scale > 0) || !(tg->p0 > 0)) return fail(ctx, OAIS_EINVAL, "ref_scale and p0 must be > 0");
+    if (tg->kind != kGauss && tg->n < 1) return fail(ctx, OAIS_EINVAL, "n must be >= 1");
+    if ((tg->kind == kLogreg || tg->kind == kLinreg) && !tg->y) return fail(ctx, OAIS_EINVAL, "missing y");
+    if (tg->kind == kGmm && tg->n > GmmTarget<float, 16>::kMaxK)
+        return fail(ctx, OAIS_EUNSUPPORTED, "at most 16 mixture components");
+    if (tg->dtype != OAIS_DT_F64 && tg->dtype != OAIS_DT_F32) return fail(ctx, OAIS_EINVAL, "bad dtype");
+    if (tg->kind == kGauss && tg->dtype != OAIS_DT_F64)
+        return fail(ctx, OAIS_EINVAL, "the Gaussian family takes float64 mu");
+    if (mv->kind < 0 || mv->kind > 2 || mv->moves < 1 || (mv->kind == OAIS_HMC && mv->leapfrog < 1))
+        return fail(ctx, OAIS_EINVAL, "bad move");
+    if (N < 1 || N > 0x7FFFFFFFLL) return fail(ctx, OAIS_EINVAL, "N out of range");
+    if (T_max < 1 || T_max > (1 << 24)) return fail(ctx, OAIS_EINVAL, "T_max out of range");
+    *D = padded_width(tg->kind, tg->d);
+    if (*D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "dimension not built for this family");
+    return OAIS_OK;
+}
+
+// host copy of an input array as doubles (input host or device, f32 or f64)
+static oais_status fetch(oais_ctx* ctx, const void* src, size_t count, int dtype, int on_device,
+                         std::vector<double>& out)
+{
+    out.resize(count);
+    const size_t eb = dtype == OAIS_DT_F64 ? 8 : 4;
+    std::vector<unsigned char> raw(count * eb);
+    if (on_device) CK(cudaMemcpy(raw.data(), src, count * eb, cudaMemcpyDeviceToHost));
+    else std::memcpy(raw.data(), src, count * eb);
+    for (size_t i = 0; i < count; ++i) {
+        if (dtype == OAIS_DT_F64) { double v; std::memcpy(&v, &raw[i * 8], 8); out[i] = v; }
+        else { float v; std::memcpy(&v, &raw[i * 4], 4); out[i] = v; }
+    }
+    return OAIS_OK;
+}
+
+extern "C" {
+
+const char* oais_status_string(oais_status s)
+{
+    switch (s) {
+    case OAIS_OK: return "ok";
+    case OAIS_EINVAL: return "invalid argument";
+    case OAIS_ENOMEM: return "out of device memory";
+    case OAIS_ECUDA: return "CUDA error";
+    case OAIS_ENONFINITE: return "non-finite log-weight or log-likelihood";
+    case OAIS_ETIMEOUT: return "device wait timed out";
+    case OAIS_EUNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char* oais_last_error(const oais_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int32_t oais_sweep_blocks(int64_t N) { return sweep_grid(N); }
+int32_t oais_step_partial_bytes(void) { return (int32_t)sizeof(StepPartial); }
+
+oais_status oais_workspace_bytes(const oais_target* tg, const oais_move* mv, int64_t N, int32_t T_max,
+                                 size_t* bytes)
+{
+    int D = 0;
+    oais_status st = check_target(nullptr, tg, mv, N, T_max, &D);
+    if (st != OAIS_OK) return st;
+    if (!bytes) return fail(nullptr, OAIS_EINVAL, "null bytes");
+    *bytes = layout(tg, D, N, T_max).total;
+    return OAIS_OK;
+}
+
+oais_status oais_optimise_schedule(int32_t T, const double* beta, const double* log_ghat, int32_t T_next,
+                                   double* beta_next, double* D_hat, double* Lambda)
+{
+    if (T < 1 || T_next < 1 || !beta || !log_ghat || !beta_next)
+        return fail(nullptr, OAIS_EINVAL, "bad arguments to oais_optimise_schedule");
+    optimise_schedule(T, beta, log_ghat, T_next, beta_next, D_hat, Lambda);
+    return OAIS_OK;
+}
+
+oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv, int64_t N,
+                      const double* beta, int32_t T, int32_t T_max, const double* eps, uint64_t seed,
+                      void* workspace, size_t ws_bytes, void* stream)
+{
+    if (!out) return fail(nullptr, OAIS_EINVAL, "null ctx pointer");
+    *out = nullptr;
+    int D = 0;
+    oais_status st = check_target(nullptr, tg, mv, N, T_max, &D);
+    if (st != OAIS_OK) return st;
+    if (T > T_max) return fail(nullptr, OAIS_EINVAL, "T > T_max");
+    if (!valid_schedule(beta, T)) return fail(nullptr, OAIS_EINVAL, "schedule must be 0 = beta_0 < ... < beta_T = 1");
+    if (eps) for (int t = 0; t < T; ++t) if (!(eps[t] > 0)) return fail(nullptr, OAIS_EINVAL, "step sizes must be > 0");
+
+    oais_ctx* ctx = new oais_ctx();
+    ctx->tg_in = *tg;
+    ctx->mv = *mv;
+    ctx->N = N;
+    ctx->T_max = T_max;
+    ctx->seed = seed;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->beta.assign(beta, beta + T + 1);
+    if (eps) ctx->eps.assign(eps, eps + T);
+    else ctx->eps.assign(T, 0.5 / std::sqrt((double)tg->d));
+
+    Layout L = layout(tg, D, N, T_max);
+    if (workspace) {
+        if (ws_bytes < L.total) { delete ctx; return fail(nullptr, OAIS_ENOMEM, "workspace too small"); }
+        ctx->ws = workspace;
+    } else {
+        cudaError_t e = cudaMalloc(&ctx->ws, L.total);
+        if (e != cudaSuccess) { delete ctx; return fail(nullptr, OAIS_ENOMEM, cudaGetErrorString(e)); }
+        ctx->own_ws = true;
+    }
+    char* b = static_cast<char*>(ctx->ws);
+    DevTarget& dt = ctx->dt;
+    dt.kind = tg->kind; dt.d = tg->d; dt.D = D; dt.n = tg->kind == kGauss ? 0 : tg->n;
+    dt.n_pad = (dt.n + 3) & ~3;
+    dt.ref_scale = tg->ref_scale; dt.p0 = tg->p0;
+    dt.X = b + L.X;
+    dt.y = (tg->kind == kLogreg || tg->kind == kLinreg) ? b + L.y : nullptr;
+    ctx->d_beta = reinterpret_cast<double*>(b + L.beta);
+    ctx->d_eps = reinterpret_cast<double*>(b + L.eps);
+    ctx->d_logw = reinterpret_cast<double*>(b + L.logw);
+    ctx->d_ell = reinterpret_cast<double*>(b + L.ell);
+    ctx->d_x = b + L.x;
+    ctx->d_parts = reinterpret_cast<StepPartial*>(b + L.parts);
+    ctx->d_log_ghat = reinterpret_cast<double*>(b + L.lg);
+    ctx->d_accept = reinterpret_cast<double*>(b + L.acc);
+    ctx->d_lse = reinterpret_cast<double*>(b + L.lse);
+    ctx->d_lse_scratch = b + L.lse_scr;
+    ctx->d_status = reinterpret_cast<unsigned*>(b + L.status);
+
+    // data in the padded device layout
+    const int rows = tg->kind == kGauss ? 1 : tg->n;
+    std::vector<double> Xh, yh;
+    st = fetch(ctx, tg->X, (size_t)rows * tg->d, tg->dtype, tg->on_device, Xh);
+    if (st == OAIS_OK && dt.y) st = fetch(ctx, tg->y, (size_t)tg->n, tg->dtype, tg->on_device, yh);
+    if (st != OAIS_OK) { g_err = ctx->err; oais_destroy(ctx); return st; }
+    cudaError_t e = cudaSuccess;
+    if (tg->kind == kGauss) {
+        std::vector<double> mu(D, 0.0);
+        for (int i = 0; i < tg->d; ++i) mu[i] = Xh[i];
+        e = cudaMemcpy(dt.X, mu.data(), sizeof(double) * D, cudaMemcpyHostToDevice);
+    } else {
+        const int nr = tg->kind == kGmm ? tg->n : dt.n_pad;
+        std::vector<float> Xp((size_t)nr * D, 0.0f), yp(dt.n_pad, 0.0f);
+        for (int r = 0; r < tg->n; ++r)
+            for (int i = 0; i < tg->d; ++i) Xp[(size_t)r * D + i] = (float)Xh[(size_t)r * tg->d + i];
+        e = cudaMemcpy(dt.X, Xp.data(), sizeof(float) * Xp.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && dt.y) {
+            for (int r = 0; r < tg->n; ++r) yp[r] = (float)yh[r];
+            e = cudaMemcpy(dt.y, yp.data(), sizeof(float) * yp.size(), cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e != cudaSuccess) { g_err = cudaGetErrorString(e); oais_destroy(ctx); return OAIS_ECUDA; }
+    *out = ctx;
+    return OAIS_OK;
+}
+
+void oais_destroy(oais_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
+    delete ctx;
+}
+
+static cudaError_t launch_sweep(const DevTarget& dt, int move, const SweepParams& P, cudaStream_t s)
+{
+    switch (dt.kind) {
+    case kGauss: return launch_sweep_gauss(dt, move, P, s);
+    case kLogreg: return launch_sweep_logreg(dt, move, P, s);
+    case kGmm: return launch_sweep_gmm(dt, move, P, s);
+    case kLinreg: return launch_sweep_linreg(dt, move, P, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static SweepParams make_params(const oais_ctx* ctx, int T, const double* d_beta, const double* d_eps,
+                               uint64_t seed, uint32_t tag, int64_t n_offset, int64_t N, double* logw,
+                               double* ell, void* x, void* parts, unsigned* status)
+{
+    SweepParams P{};
+    P.N = N; P.n_offset = n_offset; P.T = T; P.beta = d_beta; P.eps = d_eps;
+    P.ref_scale = ctx->dt.ref_scale; P.K = ctx->mv.moves; P.leapfrog = ctx->mv.leapfrog;
+    P.cycle = ctx->mv.cycle;
+    P.rng.k0 = (uint32_t)(seed & 0xFFFFFFFFu); P.rng.k1 = (uint32_t)(seed >> 32); P.rng.tag = tag;
+    P.logw = logw; P.x_out = x; P.ell_out = ell; P.partials = static_cast<StepPartial*>(parts);
+    P.status = status;
+    return P;
+}
+
+oais_status oais_ctx_sweep(oais_ctx* ctx, int32_t T, const double* d_beta, const double* d_eps, uint64_t seed,
+                           uint32_t tag, int64_t n_offset, int64_t N, double* d_logw, double* d_ell, void* d_x,
+                           void* d_partials, uint32_t* d_status, void* stream)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (T < 1 || N < 1 || !d_beta || !d_eps || !d_logw || !d_ell || !d_x || !d_partials || !d_status)
+        return fail(ctx, OAIS_EINVAL, "bad arguments to oais_ctx_sweep");
+    if (n_offset < 0 || n_offset + N > 0xFFFFFFFFLL) return fail(ctx, OAIS_EINVAL, "particle index out of range");
+    SweepParams P = make_params(ctx, T, d_beta, d_eps, seed, tag, n_offset, N, d_logw, d_ell, d_x, d_partials,
+                                d_status);
+    CK(launch_sweep(ctx->dt, ctx->mv.kind, P, static_cast<cudaStream_t>(stream)));
+    return OAIS_OK;
+}
+
+oais_status oais_merge_stats(const void* d_partials, int32_t nblocks, int32_t T, int64_t N, int32_t moves,
+                             double* d_log_ghat, double* d_accept, void* stream)
+{
+    oais_ctx* ctx = nullptr;
+    if (!d_partials || nblocks < 1 || T < 1 || N < 1 || moves < 1 || !d_log_ghat || !d_accept)
+        return fail(nullptr, OAIS_EINVAL, "bad arguments to oais_merge_stats");
+    CK(launch_merge_stats(static_cast<const StepPartial*>(d_partials), nblocks, T, 1.0 / ((double)N * moves),
+                          d_log_ghat, d_accept, static_cast<cudaStream_t>(stream)));
+    return OAIS_OK;
+}
+
+size_t oais_logsumexp_scratch_bytes(int64_t n) { return logsumexp_scratch_bytes(n); }
+
+oais_status oais_logsumexp(const double* d_a, int64_t n, double* d_out, void* d_scratch, void* stream)
+{
+    oais_ctx* ctx = nullptr;
+    if (!d_a || n < 1 || !d_out || !d_scratch) return fail(nullptr, OAIS_EINVAL, "bad arguments to oais_logsumexp");
+    CK(launch_logsumexp(d_a, n, d_out, d_scratch, static_cast<cudaStream_t>(stream)));
+    return OAIS_OK;
+}
+
+// carry step sizes to a new schedule: linear interpolation of log eps in beta, and, when
+// adapting, a multiplicative nudge toward the target acceptance of the move
+static std::vector<double> next_step_sizes(const oais_ctx* ctx, const std::vector<double>& beta_old,
+                                           const std::vector<double>& eps_old,
+                                           const std::vector<double>& acc, const std::vector<double>& beta_new)
+{
+    const int T = (int)eps_old.size(), Tn = (int)beta_new.size() - 1;
+    std::vector<double> out(Tn);
+    const double target = ctx->mv.kind == OAIS_RWMH ? 0.3 : (ctx->mv.kind == OAIS_MALA ? 0.574 : 0.7);
+    for (int i = 1; i <= Tn; ++i) {
+        const double b = beta_new[i];
+        // locate b among beta_old[1..T]
+        int j = (int)(std::lower_bound(beta_old.begin() + 1, beta_old.end(), b) - beta_old.begin());
+        j = std::max(1, std::min(j, T));
+        double le, a;
+        if (j == 1 || T == 1) { le = std::log(eps_old[0]); a = acc[0]; }
+        else {
+            const double b0 = beta_old[j - 1], b1 = beta_old[j], w = (b - b0) / (b1 - b0);
+            le = (1 - w) * std::log(eps_old[j - 2]) + w * std::log(eps_old[j - 1]);
+            a = (1 - w) * acc[j - 2] + w * acc[j - 1];
+        }
+        if (ctx->mv.adapt && !(ctx->mv.kind == OAIS_RWMH && ctx->mv.cycle))
+            le += std::max(-0.7, std::min(0.7, 1.5 * (a - target)));
+        out[i - 1] = std::exp(le);
+    }
+    return out;
+}
+
+oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (T_next < 1 || T_next > ctx->T_max) return fail(ctx, OAIS_EINVAL, "T_next out of range");
+    const int T = (int)ctx->beta.size() - 1;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->d_beta, ctx->beta.data(), sizeof(double) * (T + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_eps, ctx->eps.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s));
+    const uint32_t tag = (uint32_t)(ctx->round & 0xFFFF);
+    SweepParams P = make_params(ctx, T, ctx->d_beta, ctx->d_eps, ctx->seed, tag, 0, ctx->N, ctx->d_logw,
+                                ctx->d_ell, ctx->d_x, ctx->d_parts, ctx->d_status);
+    CK(cudaEventRecord(ctx->ev0, s));
+    CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
+    CK(cudaEventRecord(ctx->ev1, s));
+    CK(launch_merge_stats(ctx->d_parts, sweep_grid(ctx->N), T, 1.0 / ((double)ctx->N * ctx->mv.moves),
+                          ctx->d_log_ghat, ctx->d_accept, s));
+    CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
+    std::vector<double> lg(3 * T), acc(T);
+    double lse[2];
+    unsigned status = 0;
+    CK(cudaMemcpyAsync(lg.data(), ctx->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(acc.data(), ctx->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(lse, ctx->d_lse, sizeof(lse), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (status & 1u) return fail(ctx, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood in the sweep");
+
+    const double logN = std::log((double)ctx->N);
+    std::vector<double> beta_next(T_next + 1), D(T), Lam(T + 1);
+    optimise_schedule(T, ctx->beta.data(), lg.data(), T_next, beta_next.data(), D.data(), Lam.data());
+    std::vector<double> eps_next = next_step_sizes(ctx, ctx->beta, ctx->eps, acc, beta_next);
+
+    ctx->have_last = true;
+    ctx->l_beta = ctx->beta;
+    ctx->l_eps = ctx->eps;
+    ctx->l_log_ghat = lg;
+    ctx->l_D = D;
+    ctx->l_accept = acc;
+    ctx->l_logZ = lse[0] - logN;
+    ctx->l_ess = std::exp(2.0 * lse[0] - lse[1]);
+    ctx->l_se = std::sqrt(std::max(0.0, 1.0 / ctx->l_ess - 1.0 / (double)ctx->N));
+    ctx->l_Lambda = Lam[T];
+    if (out) {
+        out->logZ = ctx->l_logZ;
+        out->se = ctx->l_se;
+        out->Lambda_hat = ctx->l_Lambda;
+        out->ess = ctx->l_ess;
+        out->sweep_ms = ms;
+        out->T = T;
+        out->round = ctx->round;
+        out->n_resample = 0;
+        out->pad = 0;
+    }
+    ctx->beta = beta_next;
+    ctx->eps = eps_next;
+    ++ctx->round;
+    return OAIS_OK;
+}
+
+oais_status oais_logZ(const oais_ctx* ctx, double* logZ, double* se)
+{
+    if (!ctx || !ctx->have_last) return fail(nullptr, OAIS_EINVAL, "no completed round");
+    if (logZ) *logZ = ctx->l_logZ;
+    if (se) *se = ctx->l_se;
+    return OAIS_OK;
+}
+
+oais_status oais_get_stats(const oais_ctx* ctx, double* log_ghat, double* D_hat, double* beta, double* accept,
+                           int32_t* T)
+{
+    if (!ctx || !ctx->have_last) return fail(nullptr, OAIS_EINVAL, "no completed round");
+    const int t = (int)ctx->l_D.size();
+    if (T) *T = t;
+    if (log_ghat) std::copy(ctx->l_log_ghat.begin(), ctx->l_log_ghat.end(), log_ghat);
+    if (D_hat) std::copy(ctx->l_D.begin(), ctx->l_D.end(), D_hat);
+    if (beta) std::copy(ctx->l_beta.begin(), ctx->l_beta.end(), beta);
+    if (accept) std::copy(ctx->l_accept.begin(), ctx->l_accept.end(), accept);
+    return OAIS_OK;
+}
+
+oais_status oais_get_schedule(const oais_ctx* ctx, double* beta, double* eps, int32_t* T)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (T) *T = (int32_t)ctx->beta.size() - 1;
+    if (beta) std::copy(ctx->beta.begin(), ctx->beta.end(), beta);
+    if (eps) std::copy(ctx->eps.begin(), ctx->eps.end(), eps);
+    return OAIS_OK;
+}
+
+oais_status oais_set_schedule(oais_ctx* ctx, const double* beta, const double* eps, int32_t T)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (T > ctx->T_max || !valid_schedule(beta, T))
+        return fail(ctx, OAIS_EINVAL, "schedule must be 0 = beta_0 < ... < beta_T = 1 with T <= T_max");
+    if (eps) for (int t = 0; t < T; ++t) if (!(eps[t] > 0)) return fail(ctx, OAIS_EINVAL, "step sizes must be > 0");
+    ctx->beta.assign(beta, beta + T + 1);
+    if (eps) ctx->eps.assign(eps, eps + T);
+    else ctx->eps.assign(T, 0.5 / std::sqrt((double)ctx->dt.d));
+    return OAIS_OK;
+}
+
+oais_status oais_particles(const oais_ctx* ctx, const double** logw, const double** ell, const void** x)
+{
+    if (!ctx || !ctx->have_last) return fail(nullptr, OAIS_EINVAL, "no completed round");
+    if (logw) *logw = ctx->d_logw;
+    if (ell) *ell = ctx->d_ell;
+    if (x) *x = ctx->d_x;
+    return OAIS_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,146 @@
+// oais_device.cuh -- device building blocks of the OAIS particle sweep (sm_103a).
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), one call per
+// (particle, step, move, block) counter, so every particle's stream is fixed by its
+// index alone (the split-stream "strong parallelism invariance" of App. E.3).
+//   counter = (n, t, (k << 16) | j, tag),  key = (seed_lo, seed_hi),
+//   tag = round | (problem << 16); t = 0 is the draw from the reference.
+//   uniform u = ((r >> 9) + 0.5) * 2^-23  (exact in fp32, never 0 or 1)
+//   normals by Box-Muller on the pairs (w0, w1) and (w2, w3);
+//   the MH uniform of move k at step t is word 0 of block j = 0xFFFF;
+//   the systematic-resampling uniform of step t is word 0 of counter (~0, t, 0, tag).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace oais {
+
+struct Philox4 { uint32_t v[4]; };
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    Philox4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
+struct Rng {
+    uint32_t k0, k1, tag;
+    __device__ __forceinline__ Philox4 block(uint32_t n, uint32_t t, uint32_t k, uint32_t j) const {
+        return philox4x32_10(n, t, (k << 16) | (j & 0xFFFFu), tag, k0, k1);
+    }
+};
+
+__device__ __forceinline__ float u01f(uint32_t r) { return ((float)(r >> 9) + 0.5f) * (1.0f / 8388608.0f); }
+__device__ __forceinline__ double u01d(uint32_t r) { return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+// four standard normals from one Philox block
+__device__ __forceinline__ void box_muller4(const Philox4& b, float z[4])
+{
+    float s0, c0, s1, c1;
+    const float r0 = sqrtf(-2.0f * logf(u01f(b.v[0])));
+    const float r1 = sqrtf(-2.0f * logf(u01f(b.v[2])));
+    sincospif(2.0f * u01f(b.v[1]), &s0, &c0);
+    sincospif(2.0f * u01f(b.v[3]), &s1, &c1);
+    z[0] = r0 * c0; z[1] = r0 * s0; z[2] = r1 * c1; z[3] = r1 * s1;
+}
+__device__ __forceinline__ void box_muller4(const Philox4& b, double z[4])
+{
+    double s0, c0, s1, c1;
+    const double r0 = sqrt(-2.0 * log(u01d(b.v[0])));
+    const double r1 = sqrt(-2.0 * log(u01d(b.v[2])));
+    sincospi(2.0 * u01d(b.v[1]), &s0, &c0);
+    sincospi(2.0 * u01d(b.v[3]), &s1, &c1);
+    z[0] = r0 * c0; z[1] = r0 * s0; z[2] = r1 * c1; z[3] = r1 * s1;
+}
+
+// z[0..D) for (n, t, k); only the first d are meaningful, the rest are zero
+template <int D, typename R>
+__device__ __forceinline__ void normals(const Rng& rng, uint32_t n, uint32_t t, uint32_t k, int d, R (&z)[D])
+{
+#pragma unroll
+    for (int j = 0; j < (D + 3) / 4; ++j) {
+        R v[4];
+        if (4 * j < d) box_muller4(rng.block(n, t, k, (uint32_t)j), v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (4 * j + q < D) z[4 * j + q] = (4 * j + q < d) ? v[q] : R(0);
+    }
+}
+
+__device__ __forceinline__ float mh_log_uniform(const Rng& rng, uint32_t n, uint32_t t, uint32_t k, float)
+{
+    return logf(u01f(rng.block(n, t, k, 0xFFFFu).v[0]));
+}
+__device__ __forceinline__ double mh_log_uniform(const Rng& rng, uint32_t n, uint32_t t, uint32_t k, double)
+{
+    return log(u01d(rng.block(n, t, k, 0xFFFFu).v[0]));
+}
+
+// ---------------------------------------------------------------------------
+// Per-step moment statistics (Alg. 1, "compute moments"; Sec. 5.1.1):
+//   g_hat_{t,i} = sum_n w_{t-1}^n (g_t^n)^i,  i = 0, 1, 2,
+// kept as a shifted sum: g_hat = exp(m) * s.  One record per (t, CTA); the
+// records are merged in a fixed order by oais_merge_stats_kernel.
+// ---------------------------------------------------------------------------
+struct StepPartial {
+    double m[3];    // shift (an upper estimate of max_n log w + i log g)
+    double s[3];    // sum_n exp(log w + i log g - m)
+    uint32_t accepted;
+    uint32_t pad;
+};
+static_assert(sizeof(StepPartial) == 56, "StepPartial layout");
+
+constexpr int kMaxWarps = 32;
+
+// Warp part: v_i = lw + i * lg for the lane's particle (or -inf if inactive).
+// Writes the warp's (m_i, s_i) for i = 0..2 through lane 0.
+__device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool active,
+                                                    double* wm /*3*/, float* ws /*3*/)
+{
+    const unsigned full = 0xFFFFFFFFu;
+    // anchor = a representative active value: avoids fp64 max over the warp
+    const unsigned act = __ballot_sync(full, active);
+    if (act == 0) {
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { wm[i] = -INFINITY; ws[i] = 0.0f; }
+        }
+        return;
+    }
+    const int src = __ffs(act) - 1;
+    const double a0 = __shfl_sync(full, lw, src), b0 = __shfl_sync(full, lg, src);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double anchor = a0 + i * b0;
+        const double v = lw + i * lg;
+        float f = active ? (float)(v - anchor) : -INFINITY;
+        float mx = f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
+        const double M = anchor + (double)mx;
+        float e = active ? __expf((float)(v - M)) : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
+        if ((threadIdx.x & 31) == 0) { wm[i] = M; ws[i] = e; }
+    }
+}
+
+// merge (m, s) pairs: exp(m) s + exp(m') s'
+__device__ __forceinline__ void lse_merge(double& m, double& s, double m2, double s2)
+{
+    if (m2 == -INFINITY) return;
+    if (m == -INFINITY) { m = m2; s = s2; return; }
+    if (m2 > m) { s = s * exp(m - m2) + s2; m = m2; }
+    else        { s = s + s2 * exp(m2 - m); }
+}
+
+} // namespace oais

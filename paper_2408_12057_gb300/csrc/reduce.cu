@@ -1,0 +1,149 @@
+// reduce.cu -- deterministic cross-CTA reductions of the sweep:
+//   * per-step moments g_hat_{t,0:2} (Alg. 1) from the per-CTA StepPartial records;
+//   * log-sum-exp of the final log-weights, which gives log Z_hat (eq. estimator_Z)
+//     and the ESS (eq. sample_size_IS).
+// Every reduction visits its inputs in a fixed order, so results are bit-identical
+// from run to run (no floating-point atomics).
+#include "internal.h"
+#include "../../include/oais.h"
+
+namespace oais {
+
+constexpr int kMergeThreads = 256;
+
+// one CTA per step t
+__global__ void __launch_bounds__(kMergeThreads)
+merge_stats_kernel(const StepPartial* __restrict__ parts, int nblocks, double inv_count,
+                   double* __restrict__ log_ghat, double* __restrict__ accept)
+{
+    __shared__ double sm[3][kMergeThreads], ss[3][kMergeThreads];
+    __shared__ unsigned long long sa[kMergeThreads];
+    const int t = blockIdx.x, tid = threadIdx.x;
+    const StepPartial* p = parts + (size_t)t * nblocks;
+    double m[3] = {-INFINITY, -INFINITY, -INFINITY}, s[3] = {0.0, 0.0, 0.0};
+    unsigned long long a = 0;
+    for (int j = tid; j < nblocks; j += kMergeThreads) {
+        const StepPartial q = p[j];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) lse_merge(m[i], s[i], q.m[i], q.s[i]);
+        a += q.accepted;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sm[i][tid] = m[i]; ss[i][tid] = s[i]; }
+    sa[tid] = a;
+    __syncthreads();
+    for (int stride = kMergeThreads / 2; stride > 0; stride >>= 1) {
+        if (tid < stride) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                double mm = sm[i][tid], s0 = ss[i][tid];
+                lse_merge(mm, s0, sm[i][tid + stride], ss[i][tid + stride]);
+                sm[i][tid] = mm; ss[i][tid] = s0;
+            }
+            sa[tid] += sa[tid + stride];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) log_ghat[3 * t + i] = sm[i][0] + log(ss[i][0]);
+        accept[t] = (double)sa[0] * inv_count;
+    }
+}
+
+// ---- log-sum-exp of a[0..n) and of 2 a[0..n) ----
+constexpr int kLseThreads = 256;
+constexpr int kLseMaxBlocks = 1024;
+
+struct LsePair { double m1, s1, m2, s2; };
+
+__device__ __forceinline__ void lse_push(double& m, double& s, double v)
+{
+    if (v == -INFINITY) return;
+    if (v > m) { s = s * exp(m - v) + 1.0; m = v; }
+    else       { s += exp(v - m); }
+}
+
+__global__ void __launch_bounds__(kLseThreads)
+lse_partial_kernel(const double* __restrict__ a, int64_t n, LsePair* __restrict__ out)
+{
+    __shared__ double s_m1[kLseThreads], s_s1[kLseThreads], s_m2[kLseThreads], s_s2[kLseThreads];
+    double m1 = -INFINITY, s1 = 0.0, m2 = -INFINITY, s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = a[i];
+        lse_push(m1, s1, v);
+        lse_push(m2, s2, 2.0 * v);
+    }
+    const int tid = threadIdx.x;
+    s_m1[tid] = m1; s_s1[tid] = s1; s_m2[tid] = m2; s_s2[tid] = s2;
+    __syncthreads();
+    for (int stride = kLseThreads / 2; stride > 0; stride >>= 1) {
+        if (tid < stride) {
+            double mm = s_m1[tid], ss = s_s1[tid];
+            lse_merge(mm, ss, s_m1[tid + stride], s_s1[tid + stride]);
+            s_m1[tid] = mm; s_s1[tid] = ss;
+            mm = s_m2[tid]; ss = s_s2[tid];
+            lse_merge(mm, ss, s_m2[tid + stride], s_s2[tid + stride]);
+            s_m2[tid] = mm; s_s2[tid] = ss;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) out[blockIdx.x] = LsePair{s_m1[0], s_s1[0], s_m2[0], s_s2[0]};
+}
+
+__global__ void __launch_bounds__(kLseThreads)
+lse_final_kernel(const LsePair* __restrict__ parts, int nparts, double* __restrict__ out)
+{
+    __shared__ double s_m1[kLseThreads], s_s1[kLseThreads], s_m2[kLseThreads], s_s2[kLseThreads];
+    double m1 = -INFINITY, s1 = 0.0, m2 = -INFINITY, s2 = 0.0;
+    for (int j = threadIdx.x; j < nparts; j += kLseThreads) {
+        lse_merge(m1, s1, parts[j].m1, parts[j].s1);
+        lse_merge(m2, s2, parts[j].m2, parts[j].s2);
+    }
+    const int tid = threadIdx.x;
+    s_m1[tid] = m1; s_s1[tid] = s1; s_m2[tid] = m2; s_s2[tid] = s2;
+    __syncthreads();
+    for (int stride = kLseThreads / 2; stride > 0; stride >>= 1) {
+        if (tid < stride) {
+            double mm = s_m1[tid], ss = s_s1[tid];
+            lse_merge(mm, ss, s_m1[tid + stride], s_s1[tid + stride]);
+            s_m1[tid] = mm; s_s1[tid] = ss;
+            mm = s_m2[tid]; ss = s_s2[tid];
+            lse_merge(mm, ss, s_m2[tid + stride], s_s2[tid + stride]);
+            s_m2[tid] = mm; s_s2[tid] = ss;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        out[0] = s_m1[0] + log(s_s1[0]);
+        out[1] = s_m2[0] + log(s_s2[0]);
+    }
+}
+
+int lse_blocks(int64_t n)
+{
+    int64_t b = (n + kLseThreads * 4 - 1) / (kLseThreads * 4);
+    return (int)(b < 1 ? 1 : (b > kLseMaxBlocks ? kLseMaxBlocks : b));
+}
+
+cudaError_t launch_merge_stats(const StepPartial* parts, int nblocks, int T, double inv_count,
+                               double* log_ghat, double* accept, cudaStream_t s)
+{
+    if (T <= 0) return cudaSuccess;
+    merge_stats_kernel<<<T, kMergeThreads, 0, s>>>(parts, nblocks, inv_count, log_ghat, accept);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_logsumexp(const double* a, int64_t n, double* out, void* scratch, cudaStream_t s)
+{
+    const int nb = lse_blocks(n);
+    LsePair* parts = static_cast<LsePair*>(scratch);
+    lse_partial_kernel<<<nb, kLseThreads, 0, s>>>(a, n, parts);
+    lse_final_kernel<<<1, kLseThreads, 0, s>>>(parts, nb, out);
+    return cudaGetLastError();
+}
+
+size_t logsumexp_scratch_bytes(int64_t n) { return sizeof(LsePair) * (size_t)lse_blocks(n); }
+
+} // namespace oais

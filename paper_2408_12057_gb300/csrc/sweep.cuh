@@ -1,0 +1,205 @@
+// sweep.cuh -- the loop-swapped OAIS particle sweep (Sec. 5.1.2): each thread owns one
+// particle for all T annealing steps, so the particle's state never leaves registers;
+// the only cross-particle work per step is the moment reduction of Alg. 1, done per CTA
+// and written as one StepPartial record per (step, CTA).
+//
+// Step t of Alg. 1 for one particle, in the order the kernel runs it:
+//   log g_t = (beta_t - beta_{t-1}) * log L(X_{t-1})   (incremental weight at the
+//             pre-move state, quasi-reversal backward kernel, Sec. 2.1.2)
+//   moments of (w_{t-1}, g_t)                           (Alg. 1 / eq. CESS)
+//   log w_t = log w_{t-1} + log g_t                     (reweight)
+//   K moves of a pi_{beta_t}-invariant MH kernel        (propagate)
+#pragma once
+#include "targets.cuh"
+
+namespace oais {
+
+enum MoveKind { kRwmh = 0, kMala = 1, kHmc = 2 };
+
+constexpr int kSweepThreads = 128;
+
+struct SweepParams {
+    int64_t N;            // particles in this launch
+    int64_t n_offset;     // global index of particle 0 (counter word 0)
+    int T;
+    const double* beta;   // [T+1]
+    const double* eps;    // [T] step size per annealing step
+    double ref_scale;     // s
+    int K;                // moves per step
+    int leapfrog;
+    int cycle;            // RWMH std cycles 0.1, 1, 10 by global move index
+    Rng rng;
+    // outputs
+    double* logw;         // [N]
+    void* x_out;          // [d][N] SoA, element type R
+    double* ell_out;      // [N]
+    StepPartial* partials;// [T][gridDim.x]
+    unsigned* status;     // bit 0: non-finite value seen
+};
+
+template <typename R> __device__ __forceinline__ R rsq(R a) { return a * a; }
+
+template <class Tgt, int MOVE, int D, typename R>
+__device__ __forceinline__ bool mh_move(const Tgt& tg, const SweepParams& P, R (&x)[D], R& ell,
+                                        R (&gl)[D], double beta_t, double eps_t, uint32_t n,
+                                        uint32_t t, uint32_t k, int d, R inv_s2)
+{
+    constexpr bool GRAD = (MOVE != kRwmh);
+    const R beta = (R)beta_t;
+    R z[D];
+    normals<D>(P.rng, n, t, k, d, z);
+    R xp[D], glp[D];
+    R log_alpha;
+    R ellp;
+    if (MOVE == kRwmh) {
+        R sd = (R)eps_t;
+        if (P.cycle) {
+            const int gm = ((int)t - 1) * P.K + (int)k;
+            const int c = gm % 3;
+            sd = c == 0 ? R(0.1) : (c == 1 ? R(1) : R(10));
+        }
+        R dxx = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            xp[i] = x[i] + sd * z[i];
+            dxx += (xp[i] - x[i]) * (xp[i] + x[i]);   // |xp|^2 - |x|^2
+        }
+        ellp = tg.template eval<false>(xp, glp);
+        log_alpha = -R(0.5) * dxx * inv_s2 + beta * (ellp - ell);
+    } else if (MOVE == kMala) {
+        // x' = x + (e^2/2) grad log pi(x) + e z;  with w = z + (e/2) grad log pi(x) the
+        // reverse-proposal term is |w + (e/2) grad log pi(x')|^2 / 2 and the forward one |z|^2 / 2
+        const R e = (R)eps_t, h = R(0.5) * e;
+        R zz = 0, dxx = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const R gpi = -x[i] * inv_s2 + beta * gl[i];
+            xp[i] = x[i] + e * (h * gpi + z[i]);
+            zz += z[i] * z[i];
+            z[i] = z[i] + h * gpi;                     // w
+            dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
+        }
+        ellp = tg.template eval<true>(xp, glp);
+        R rev = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) rev += rsq(z[i] + h * (-xp[i] * inv_s2 + beta * glp[i]));
+        log_alpha = -R(0.5) * dxx * inv_s2 + beta * (ellp - ell) - R(0.5) * (rev - zz);
+    } else {
+        // HMC, identity mass: leapfrog with momentum p (kept in z)
+        const R e = (R)eps_t;
+        R ke0 = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            ke0 += z[i] * z[i];
+            z[i] += R(0.5) * e * (-x[i] * inv_s2 + beta * gl[i]);
+            xp[i] = x[i];
+        }
+        ellp = ell;
+        for (int l = 0; l < P.leapfrog; ++l) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) xp[i] += e * z[i];
+            ellp = tg.template eval<true>(xp, glp);
+            const R f = (l + 1 < P.leapfrog) ? e : R(0.5) * e;
+#pragma unroll
+            for (int i = 0; i < D; ++i) z[i] += f * (-xp[i] * inv_s2 + beta * glp[i]);
+        }
+        R ke1 = 0, dxx = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) { ke1 += z[i] * z[i]; dxx += (xp[i] - x[i]) * (xp[i] + x[i]); }
+        log_alpha = -R(0.5) * dxx * inv_s2 + beta * (ellp - ell) - R(0.5) * (ke1 - ke0);
+    }
+    const R logu = mh_log_uniform(P.rng, n, t, k, R(0));
+    const bool acc = logu < log_alpha;
+    if (acc) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) { x[i] = xp[i]; if (GRAD) gl[i] = glp[i]; }
+        ell = ellp;
+    }
+    return acc;
+}
+
+template <class Tgt, int MOVE, int D, typename R>
+__global__ void __launch_bounds__(kSweepThreads)
+oais_sweep_kernel(const SweepParams P, Tgt tg)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_m[2][kSweepThreads / 32][3];
+    __shared__ float s_s[2][kSweepThreads / 32][3];
+    __shared__ unsigned s_acc[2][kSweepThreads / 32];
+
+    tg.setup(smem);
+    const int d = tg.d;
+    const int64_t n64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = n64 < P.N;
+    // inactive lanes shadow the last particle so that every thread of the CTA joins
+    // the cooperative target evaluations; their results are never written
+    const uint32_t n = (uint32_t)(P.n_offset + (active ? n64 : P.N - 1));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const R s = (R)P.ref_scale;
+    const R inv_s2 = R(1) / (s * s);
+    constexpr bool GRAD = (MOVE != kRwmh);
+
+    R x[D], gl[D];
+    normals<D>(P.rng, n, 0u, 0u, d, x);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { x[i] *= s; gl[i] = R(0); }
+    R ell = tg.template eval<GRAD>(x, gl);
+    double logw = 0.0;
+    unsigned bad = 0;
+
+    double beta_prev = P.beta[0];
+    for (int t = 1; t <= P.T; ++t) {
+        const double beta_t = __ldg(P.beta + t);
+        const double eps_t = __ldg(P.eps + t - 1);
+        const double lg = (beta_t - beta_prev) * (double)ell;
+        beta_prev = beta_t;
+        const int slot = t & 1;
+        warp_moment_partial(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
+        logw += lg;
+        unsigned acc = 0;
+        for (int k = 0; k < P.K; ++k)
+            acc += mh_move<Tgt, MOVE, D, R>(tg, P, x, ell, gl, beta_t, eps_t, n, (uint32_t)t,
+                                            (uint32_t)k, d, inv_s2) ? 1u : 0u;
+        acc = active ? acc : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (lane == 0) s_acc[slot][warp] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            // merge the warps of this CTA in a fixed order (lane j holds warp j)
+            constexpr int W = kSweepThreads / 32;
+            StepPartial out;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                double m = lane < W ? s_m[slot][lane][i] : -INFINITY;
+                double M = m;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
+                double v = (lane < W && m != -INFINITY) ? (double)s_s[slot][lane][i] * exp(m - M) : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                out.m[i] = M;
+                out.s[i] = v;
+            }
+            unsigned a = lane < W ? s_acc[slot][lane] : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+            if (lane == 0) {
+                out.accepted = a;
+                out.pad = 0;
+                P.partials[(size_t)(t - 1) * gridDim.x + blockIdx.x] = out;
+            }
+        }
+        if (!isfinite(logw) || !isfinite((double)ell)) bad = 1;
+    }
+    if (active) {
+        P.logw[n64] = logw;
+        P.ell_out[n64] = (double)ell;
+        R* xo = reinterpret_cast<R*>(P.x_out);
+#pragma unroll
+        for (int i = 0; i < D; ++i) if (i < d) xo[(size_t)i * P.N + n64] = x[i];
+    }
+    if (active && bad) atomicOr(P.status, 1u);
+}
+
+} // namespace oais

@@ -1,0 +1,210 @@
+// targets.cuh -- target families on the geometric path gamma_beta = eta * L^beta (Sec. 2),
+// eta = N(0, s^2 I).  Each family evaluates log L(x) and, when asked, grad_x log L(x)
+// for one particle per thread.  Families that read a data matrix stream it through
+// shared memory in chunks, so every thread of the CTA must call eval() together.
+#pragma once
+#include "oais_device.cuh"
+
+namespace oais {
+
+enum TargetKind { kGauss = 0, kLogreg = 1, kGmm = 2, kLinreg = 3 };
+
+// -------------------------------------------------------------------------
+// Conjugate Gaussian likelihood L(x) = exp(-|x - mu|^2 / (2 sigma^2)).
+// -------------------------------------------------------------------------
+template <typename R, int D>
+struct GaussTarget {
+    static constexpr int kind = kGauss;
+    const R* mu;      // [d] in global memory
+    int d;
+    R inv_sig2;
+    R mu_r[D];
+
+    __device__ void setup(unsigned char*) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) mu_r[i] = (i < d) ? mu[i] : R(0);
+    }
+    static constexpr size_t smem_bytes(int) { return 0; }
+
+    template <bool GRAD>
+    __device__ R eval(const R (&x)[D], R (&g)[D]) const {
+        R acc = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const R r = x[i] - mu_r[i];
+            acc += r * r;
+            if (GRAD) g[i] = -r * inv_sig2;
+        }
+        return R(-0.5) * acc * inv_sig2;
+    }
+};
+
+// -------------------------------------------------------------------------
+// Gaussian mixture p = (1/K) sum_k N(mu_k, v I); L = p / eta so that Z = 1.
+// Means live in shared memory.
+// -------------------------------------------------------------------------
+template <typename R, int D>
+struct GmmTarget {
+    static constexpr int kind = kGmm;
+    static constexpr int kMaxK = 16;
+    const R* means;   // [K][D] (padded to D columns)
+    int d, K;
+    R inv_v;          // 1 / v
+    R inv_s2;         // 1 / s^2
+    R log_const;      // -(d/2) log(2 pi v) - log K + (d/2) log(2 pi s^2)
+    const R* sm;      // shared copy
+
+    static constexpr size_t smem_bytes(int K) { return sizeof(R) * (size_t)K * D; }
+    __device__ void setup(unsigned char* smem) {
+        R* s = reinterpret_cast<R*>(smem);
+        for (int i = threadIdx.x; i < K * D; i += blockDim.x) s[i] = means[i];
+        sm = s;
+        __syncthreads();
+    }
+
+    template <bool GRAD>
+    __device__ R eval(const R (&x)[D], R (&g)[D]) const {
+        R q[kMaxK];
+        R mx = R(-INFINITY);
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k) {
+            if (k < K) {
+                R acc = 0;
+#pragma unroll
+                for (int i = 0; i < D; ++i) { const R r = x[i] - sm[k * D + i]; acc += r * r; }
+                q[k] = R(-0.5) * acc * inv_v;
+                mx = q[k] > mx ? q[k] : mx;
+            }
+        }
+        R sum = 0, xx = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k)
+            if (k < K) { q[k] = exp_(q[k] - mx); sum += q[k]; }
+#pragma unroll
+        for (int i = 0; i < D; ++i) xx += x[i] * x[i];
+        if (GRAD) {
+            const R inv = R(1) / sum;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                R acc = 0;
+#pragma unroll
+                for (int k = 0; k < kMaxK; ++k) if (k < K) acc += q[k] * sm[k * D + i];
+                g[i] = (acc * inv - x[i]) * inv_v + x[i] * inv_s2;
+            }
+        }
+        return mx + log_(sum) + log_const + R(0.5) * xx * inv_s2;
+    }
+    __device__ static float exp_(float v) { return __expf(v); }
+    __device__ static double exp_(double v) { return exp(v); }
+    __device__ static float log_(float v) { return __logf(v); }
+    __device__ static double log_(double v) { return log(v); }
+};
+
+// -------------------------------------------------------------------------
+// Row-structured likelihoods, log L = sum_r f(y_r, X_r . x):
+//   logistic: f = y z - softplus(z),       df/dz = y - sigmoid(z)
+//   linear:   f = -(y - z)^2 / (2 sig^2),  df/dz = (y - z) / sig^2  (+ constant)
+// X [n][D] fp32 (zero-padded columns), y [n] fp32, streamed through shared
+// memory in chunks of kChunkFloats with cp.async double buffering.
+// -------------------------------------------------------------------------
+constexpr int kChunkFloats = 8192;   // 32 KB of X per buffer
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <int D, bool LOGISTIC>
+struct RowsTarget {
+    static constexpr int kind = LOGISTIC ? kLogreg : kLinreg;
+    static constexpr int kRows = kChunkFloats / D;
+    const float* X;     // [n_pad][D], n_pad a multiple of 4
+    const float* y;     // [n_pad]
+    int d, n;
+    float inv_sig2;     // linear only
+    float lin_const;    // linear only: -(n/2) log(2 pi sig^2)
+    float* xs;          // [2][kRows * D]
+    float* ys;          // [2][kRows]
+
+    static constexpr size_t smem_bytes(int) { return sizeof(float) * 2 * (size_t)(kRows * D + kRows); }
+    __device__ void setup(unsigned char* smem) {
+        xs = reinterpret_cast<float*>(smem);
+        ys = xs + 2 * kRows * D;
+    }
+
+    __device__ void load_chunk(int c, int buf) const {
+        const int r0 = c * kRows;
+        int rows = n - r0; rows = rows < kRows ? rows : kRows;
+        rows = (rows + 3) & ~3;                        // n_pad keeps this in bounds
+        const float* srcX = X + (size_t)r0 * D;
+        float* dstX = xs + buf * kRows * D;
+        const int nx = rows * D / 4;                   // 16-byte pieces
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) cp_async16(dstX + 4 * i, srcX + 4 * i);
+        const float* srcy = y + r0;
+        float* dsty = ys + buf * kRows;
+        for (int i = threadIdx.x; i < rows / 4; i += blockDim.x) cp_async16(dsty + 4 * i, srcy + 4 * i);
+        cp_async_commit();
+    }
+
+    template <bool GRAD>
+    __device__ float eval(const float (&x)[D], float (&g)[D]) const {
+        float ell = 0.0f;
+        if (GRAD) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) g[i] = 0.0f;
+        }
+        const int nch = (n + kRows - 1) / kRows;
+        load_chunk(0, 0);
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) { load_chunk(c + 1, (c + 1) & 1); cp_async_wait<1>(); }
+            else             { cp_async_wait<0>(); }
+            __syncthreads();
+            const float* Xc = xs + (c & 1) * kRows * D;
+            const float* yc = ys + (c & 1) * kRows;
+            int rows = n - c * kRows; rows = rows < kRows ? rows : kRows;
+            float part = 0.0f;
+            for (int r = 0; r < rows; ++r) {
+                const float* xr = Xc + r * D;
+                // 4 independent partial dot products shorten the FMA dependency chain
+                float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+                for (int i = 0; i < D; i += 4) {
+                    if (D % 4 == 0) {
+                        const float4 v = *reinterpret_cast<const float4*>(xr + i);
+                        z0 = fmaf(v.x, x[i], z0); z1 = fmaf(v.y, x[i + 1], z1);
+                        z2 = fmaf(v.z, x[i + 2], z2); z3 = fmaf(v.w, x[i + 3], z3);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) if (i + q < D) z0 = fmaf(xr[i + q], x[i + q], z0);
+                    }
+                }
+                const float z = (z0 + z1) + (z2 + z3);
+                const float yv = yc[r];
+                float res;
+                if (LOGISTIC) {
+                    const float e = __expf(-fabsf(z));
+                    const float inv = __frcp_rn(1.0f + e);
+                    part += yv * z - (fmaxf(z, 0.0f) + __logf(1.0f + e));
+                    res = yv - (z >= 0.0f ? inv : e * inv);
+                } else {
+                    const float r_ = yv - z;
+                    part = fmaf(r_, r_, part);
+                    res = r_ * inv_sig2;
+                }
+                if (GRAD) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) g[i] = fmaf(res, xr[i], g[i]);
+                }
+            }
+            ell += part;
+            __syncthreads();
+        }
+        return LOGISTIC ? ell : (-0.5f * ell * inv_sig2 + lin_const);
+    }
+};
+
+} // namespace oais

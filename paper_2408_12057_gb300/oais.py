@@ -1,0 +1,278 @@
+"""ctypes binding of the OAIS C ABI (include/oais.h).
+
+Argument marshalling only: every step of the sampler runs in liboais.so's CUDA
+kernels.  PyTorch provides the device workspace (a uint8 tensor) and the CUDA
+stream (the current torch stream).  There is no CPU fallback: if the library
+cannot be built or loaded, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+GAUSS, LOGREG, GMM, LINREG = 0, 1, 2, 3
+RWMH, MALA, HMC = 0, 1, 2
+DT_F64, DT_F32 = 0, 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+          4: "non-finite value", 5: "device wait timed out", 6: "unsupported configuration"}
+
+
+class OAISError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Target(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("d", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("X", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("ref_scale", ctypes.c_double), ("p0", ctypes.c_double),
+                ("on_device", ctypes.c_int32)]
+
+
+class _Move(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("moves", ctypes.c_int32), ("leapfrog", ctypes.c_int32),
+                ("cycle", ctypes.c_int32), ("adapt", ctypes.c_int32)]
+
+
+class _RoundResult(ctypes.Structure):
+    _fields_ = [("logZ", ctypes.c_double), ("se", ctypes.c_double), ("Lambda_hat", ctypes.c_double),
+                ("ess", ctypes.c_double), ("sweep_ms", ctypes.c_double), ("T", ctypes.c_int32),
+                ("round", ctypes.c_int32), ("n_resample", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load liboais.so (building it with nvcc first if it is stale or missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            P, i32, i64, u32, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                              ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double,
+                                              ctypes.c_size_t)
+            sig = {
+                "oais_workspace_bytes": ([P, P, i64, i32, P], i32),
+                "oais_init": ([P, P, P, i64, P, i32, i32, P, u64, P, sz, P], i32),
+                "oais_round": ([P, i32, P], i32),
+                "oais_logZ": ([P, P, P], i32),
+                "oais_get_stats": ([P, P, P, P, P, P], i32),
+                "oais_get_schedule": ([P, P, P, P], i32),
+                "oais_set_schedule": ([P, P, P, i32], i32),
+                "oais_particles": ([P, P, P, P], i32),
+                "oais_destroy": ([P], None),
+                "oais_last_error": ([P], ctypes.c_char_p),
+                "oais_status_string": ([i32], ctypes.c_char_p),
+                "oais_optimise_schedule": ([i32, P, P, i32, P, P, P], i32),
+                "oais_sweep_blocks": ([i64], i32),
+                "oais_step_partial_bytes": ([], i32),
+                "oais_ctx_sweep": ([P, i32, P, P, u64, u32, i64, i64, P, P, P, P, P, P], i32),
+                "oais_merge_stats": ([P, i32, i32, i64, i32, P, P, P], i32),
+                "oais_logsumexp_scratch_bytes": ([i64], sz),
+                "oais_logsumexp": ([P, i64, P, P, P], i32),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(st, ctx=None):
+    if st != 0:
+        msg = lib().oais_last_error(ctx)
+        raise OAISError(st, msg.decode() if msg else "")
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def optimise_schedule(beta, log_ghat, T_next):
+    """Alg. 3 on the host (library code, no device work): (beta_next, D_hat, Lambda_hat)."""
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    lg = np.ascontiguousarray(log_ghat, dtype=np.float64)
+    T = beta.size - 1
+    bn, D, L = np.zeros(T_next + 1), np.zeros(T), np.zeros(T + 1)
+    _check(lib().oais_optimise_schedule(T, _np_ptr(beta), _np_ptr(lg), int(T_next), _np_ptr(bn),
+                                        _np_ptr(D), _np_ptr(L)))
+    return bn, D, L
+
+
+def default_step_sizes(problem, beta, move_kind):
+    """A starting rule for the per-step sizes: the reference scale shrunk by the tempered
+    curvature of the likelihood (a rough diagonal estimate) and by d^(1/6) (MALA) or d^(1/4) (HMC)."""
+    beta = np.asarray(beta, dtype=np.float64)[1:]
+    d = problem.d
+    if problem.kind == GAUSS:
+        curv = 1.0 / problem.p0 ** 2
+    elif problem.kind == LOGREG:
+        curv = 0.25 * float((np.asarray(problem.X, dtype=np.float64) ** 2).sum()) / d
+    elif problem.kind == LINREG:
+        curv = float((np.asarray(problem.X, dtype=np.float64) ** 2).sum()) / d / problem.p0 ** 2
+    else:
+        curv = 1.0 / problem.p0
+    scale = 1.0 / np.sqrt(1.0 / problem.ref_scale ** 2 + beta * curv)
+    c = {RWMH: 2.38 / math.sqrt(d), MALA: 1.2 * d ** (-1.0 / 6.0), HMC: 1.0 * d ** (-0.25)}[move_kind]
+    return c * scale
+
+
+class OAIS:
+    """One OAIS run (Alg. 2) over a target of paper_2408_12057_gb300.workloads.Problem."""
+
+    def __init__(self, problem, move_kind, N, beta, T_max=None, eps=None, seed=12057, moves=1,
+                 leapfrog=5, cycle=False, adapt=False, data_on_device=True, stream=None):
+        import torch
+        self._torch = torch
+        self.problem = problem
+        self.N = int(N)
+        beta = np.ascontiguousarray(beta, dtype=np.float64)
+        T = beta.size - 1
+        self.T_max = int(T_max if T_max is not None else T)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        kind = problem.kind
+        dtype = DT_F64 if kind == GAUSS else DT_F32
+        npdt = np.float64 if dtype == DT_F64 else np.float32
+        X = np.ascontiguousarray(problem.X, dtype=npdt)
+        y = None if problem.y is None else np.ascontiguousarray(problem.y, dtype=npdt)
+        if data_on_device:
+            self._X = torch.from_numpy(X).cuda()
+            self._y = None if y is None else torch.from_numpy(y).cuda()
+            Xp, yp = self._X.data_ptr(), (None if y is None else self._y.data_ptr())
+        else:
+            self._X, self._y = X, y
+            Xp, yp = X.ctypes.data, (None if y is None else y.ctypes.data)
+        self._tg = _Target(kind, problem.d, problem.n, dtype, Xp, yp, problem.ref_scale, problem.p0,
+                           1 if data_on_device else 0)
+        self._mv = _Move(int(move_kind), int(moves), int(leapfrog), int(bool(cycle)), int(bool(adapt)))
+        L = lib()
+        nbytes = ctypes.c_size_t()
+        _check(L.oais_workspace_bytes(ctypes.byref(self._tg), ctypes.byref(self._mv), self.N,
+                                      self.T_max, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        eps_arr = None if eps is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(eps, dtype=np.float64), (T,)))
+        self._ctx = ctypes.c_void_p()
+        _check(L.oais_init(ctypes.byref(self._ctx), ctypes.byref(self._tg), ctypes.byref(self._mv),
+                           self.N, _np_ptr(beta), T, self.T_max,
+                           None if eps_arr is None else _np_ptr(eps_arr), int(seed),
+                           _dptr(self.workspace), self.workspace.numel(), _stream_ptr(self.stream)))
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().oais_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    __del__ = close
+
+    def round(self, T_next=None):
+        """Run one round; returns a dict with logZ, se, Lambda_hat, ess, sweep_ms, T, round."""
+        if T_next is None:
+            T_next = self.schedule()[0].size - 1
+        r = _RoundResult()
+        _check(lib().oais_round(self._ctx, int(T_next), ctypes.byref(r)), self._ctx)
+        return {f: getattr(r, f) for f, _ in _RoundResult._fields_ if f != "pad"}
+
+    def logZ(self):
+        z, s = ctypes.c_double(), ctypes.c_double()
+        _check(lib().oais_logZ(self._ctx, ctypes.byref(z), ctypes.byref(s)), self._ctx)
+        return z.value, s.value
+
+    def stats(self):
+        T = ctypes.c_int32()
+        _check(lib().oais_get_stats(self._ctx, None, None, None, None, ctypes.byref(T)), self._ctx)
+        T = T.value
+        lg, D, b, a = np.zeros((T, 3)), np.zeros(T), np.zeros(T + 1), np.zeros(T)
+        _check(lib().oais_get_stats(self._ctx, _np_ptr(lg), _np_ptr(D), _np_ptr(b), _np_ptr(a), None),
+               self._ctx)
+        return {"log_ghat": lg, "D_hat": D, "beta": b, "accept": a}
+
+    def schedule(self):
+        T = ctypes.c_int32()
+        _check(lib().oais_get_schedule(self._ctx, None, None, ctypes.byref(T)), self._ctx)
+        b, e = np.zeros(T.value + 1), np.zeros(T.value)
+        _check(lib().oais_get_schedule(self._ctx, _np_ptr(b), _np_ptr(e), None), self._ctx)
+        return b, e
+
+    def set_schedule(self, beta, eps=None):
+        beta = np.ascontiguousarray(beta, dtype=np.float64)
+        T = beta.size - 1
+        e = None if eps is None else np.ascontiguousarray(np.broadcast_to(
+            np.asarray(eps, dtype=np.float64), (T,)))
+        _check(lib().oais_set_schedule(self._ctx, _np_ptr(beta), None if e is None else _np_ptr(e), T),
+               self._ctx)
+
+    def particles(self):
+        """(logw [N], ell [N], x [d, N]) torch views of the final particles of the last round."""
+        torch = self._torch
+        pl, pe, px = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().oais_particles(self._ctx, ctypes.byref(pl), ctypes.byref(pe), ctypes.byref(px)),
+               self._ctx)
+        base = self.workspace.data_ptr()
+        N, d = self.N, self.problem.d
+
+        def view(ptr, dtype, count):
+            esz = torch.empty(0, dtype=dtype).element_size()
+            off = ptr - base
+            return self.workspace[off:off + count * esz].view(dtype)
+
+        xdt = torch.float64 if self.problem.kind == GAUSS else torch.float32
+        return (view(pl.value, torch.float64, N), view(pe.value, torch.float64, N),
+                view(px.value, xdt, d * N).view(d, N))
+
+    # ---- kernel-level calls (device tensors) ----
+    def sweep(self, beta_dev, eps_dev, seed, tag, n_offset, N, logw, ell, x, partials, status,
+              stream=None):
+        T = beta_dev.numel() - 1
+        _check(lib().oais_ctx_sweep(self._ctx, T, _dptr(beta_dev), _dptr(eps_dev), int(seed), int(tag),
+                                    int(n_offset), int(N), _dptr(logw), _dptr(ell), _dptr(x),
+                                    _dptr(partials), _dptr(status), _stream_ptr(stream)), self._ctx)
+
+
+def sweep_blocks(N):
+    return lib().oais_sweep_blocks(int(N))
+
+
+def step_partial_bytes():
+    return lib().oais_step_partial_bytes()
+
+
+def merge_stats(partials, nblocks, T, N, moves, stream=None):
+    import torch
+    lg = torch.empty((T, 3), dtype=torch.float64, device="cuda")
+    acc = torch.empty(T, dtype=torch.float64, device="cuda")
+    _check(lib().oais_merge_stats(_dptr(partials), int(nblocks), int(T), int(N), int(moves), _dptr(lg),
+                                  _dptr(acc), _stream_ptr(stream)))
+    return lg, acc
+
+
+def logsumexp(a, stream=None):
+    """(log sum exp a, log sum exp 2a) of a float64 CUDA tensor, as a 2-element CUDA tensor."""
+    import torch
+    n = a.numel()
+    scratch = torch.empty(lib().oais_logsumexp_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(lib().oais_logsumexp(_dptr(a), n, _dptr(out), _dptr(scratch), _stream_ptr(stream)))
+    return out

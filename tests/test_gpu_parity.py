@@ -1,0 +1,216 @@
+"""Parity of the CUDA sweep with the FP64 oracle on identical seeded inputs and
+identical Philox counters, through the C ABI.
+
+Per particle the CUDA path and the oracle run the same algorithm on the same
+random numbers, so final log-weights, log-likelihoods and states agree element by
+element.  A Metropolis-Hastings decision whose margin |log u - log alpha| (oracle)
+is within the CUDA path's rounding of log alpha may legitimately go either way
+and then the trajectories separate; such particles are excluded from the
+element-wise comparison (both outcomes are valid draws) and counted.
+
+Tolerances (relative, plus a small absolute floor), derived from the arithmetic:
+  fp64 family (conjugate Gaussian): both sides are fp64; the only differences are
+    summation order and the sincospi/cos formulation of Box-Muller: 1e-9.
+  fp32 families: the kernel keeps states and log L in fp32 (unit roundoff 6e-8)
+    and log-weights in fp64; a log L over n rows accumulates about sqrt(n) * 6e-8
+    relative error, so log L and log w agree to 1e-5 relative (the single-step
+    bar), and states, which carry T*K rounded updates, to 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2408_12057_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+oais = pytest.importorskip("paper_2408_12057_gb300.oais")
+
+
+def _tg(pr):
+    return o.Target(pr.kind, pr.X, pr.y, pr.ref_scale, pr.p0)
+
+
+def run_gpu(pr, move, N, beta, eps, seed, **kw):
+    r = oais.OAIS(pr, move, N, beta, eps=eps, seed=seed, **kw)
+    res = r.round(len(beta) - 1)
+    logw, ell, x = r.particles()
+    out = dict(res=res, logw=logw.cpu().numpy().copy(), ell=ell.cpu().numpy().copy(),
+               x=x.cpu().numpy().T.astype(np.float64).copy(), **r.stats())
+    r.close()
+    return out
+
+
+def tolerances(pr):
+    if pr.kind == W.GAUSS:
+        return dict(rel=1e-9, abs=1e-9, xrel=1e-9, margin=1e-7, ghat=1e-6)
+    return dict(rel=1e-5, abs=1e-4, xrel=1e-4, margin=2e-3, ghat=2e-4)
+
+
+def compare(pr, move, N, beta, eps, seed, min_frac=0.9, **kw):
+    g = run_gpu(pr, move, N, beta, eps, seed, **kw)
+    okw = {k: v for k, v in kw.items() if k in ("moves", "leapfrog", "cycle")}
+    r = o.asmc(_tg(pr), move, N, beta, eps, seed, tag=0, **okw)
+    tol = tolerances(pr)
+    clean = r["margin"] > tol["margin"]
+    assert clean.mean() >= min_frac, f"too many near-tie MH decisions: {clean.mean()}"
+    c = clean
+    np.testing.assert_allclose(g["logw"][c], r["logw"][c], rtol=tol["rel"], atol=tol["abs"])
+    np.testing.assert_allclose(g["ell"][c], r["ell"][c], rtol=tol["rel"], atol=tol["abs"])
+    np.testing.assert_allclose(g["x"][c], r["x"][c], rtol=tol["xrel"], atol=tol["xrel"])
+    if clean.all():
+        # with every decision shared, the per-step moments and acceptance agree too
+        np.testing.assert_allclose(g["log_ghat"], r["log_ghat"], rtol=1e-9, atol=tol["ghat"])
+        np.testing.assert_allclose(g["accept"], r["accept"], rtol=0, atol=1e-12)
+        assert g["res"]["logZ"] == pytest.approx(r["logZ"], rel=tol["rel"], abs=tol["abs"])
+    return g, r, clean
+
+
+def test_gauss_rwmh_workload1_full_size():
+    # the conjugate-Gaussian workload at its full size: N = 1024, T = 64 linear, std 0.5/sqrt(8)
+    pr = W.gauss_conj()
+    compare(pr, oais.RWMH, 1024, W.linear_schedule(64), 0.5 / np.sqrt(8), seed=12057)
+
+
+@pytest.mark.parametrize("move,kw", [(oais.MALA, {}), (oais.HMC, dict(leapfrog=3)),
+                                     (oais.RWMH, dict(moves=3))])
+def test_gauss_moves_ragged(move, kw):
+    pr = W.gauss_conj(d=5, seed=3)
+    beta = W.linear_schedule(12) ** 2
+    compare(pr, move, 300, beta, 0.3, seed=7, **kw)
+
+
+@pytest.mark.parametrize("d", [1, 3, 16])
+def test_gauss_dimensions(d):
+    pr = W.gauss_conj(d=d, seed=d)
+    compare(pr, oais.MALA, 257, W.linear_schedule(6), 0.4, seed=d)
+
+
+def test_logistic_mala_workload2_shape():
+    pr = W.logistic()   # n = 2000, d = 32
+    beta = W.linear_schedule(6) ** 4
+    eps = oais.default_step_sizes(pr, beta, oais.MALA)
+    compare(pr, oais.MALA, 300, beta, eps, seed=12057)
+
+
+@pytest.mark.parametrize("move,kw", [(oais.RWMH, dict(moves=2)), (oais.HMC, dict(leapfrog=4)),
+                                     (oais.MALA, {})])
+def test_logistic_small_padded(move, kw):
+    pr = W.logistic(n=101, d=5, seed=44)   # d padded to 8, n not a multiple of 4
+    beta = W.linear_schedule(10) ** 2
+    eps = oais.default_step_sizes(pr, beta, move)
+    compare(pr, move, 200, beta, eps, seed=5, **kw)
+
+
+def test_gmm_rwmh_cycle_workload3_shape():
+    pr = W.gmm()   # d = 16, 8 components
+    beta = W.linear_schedule(24) ** 3
+    compare(pr, oais.RWMH, 1000, beta, 1.0, seed=12057, moves=2, cycle=True)
+
+
+def test_linreg_hmc_small():
+    pr = W.linreg(n=500, d=16, seed=8)
+    beta = W.linear_schedule(8) ** 3
+    eps = oais.default_step_sizes(pr, beta, oais.HMC)
+    compare(pr, oais.HMC, 200, beta, eps, seed=3, leapfrog=5)
+
+
+def test_single_particle_single_step():
+    pr = W.logistic(n=64, d=4, seed=1)
+    compare(pr, oais.MALA, 1, [0.0, 1.0], 0.1, seed=9)
+
+
+def test_one_step_schedule_is_importance_sampling_full_size():
+    # B = (0, 1) on the logistic workload at N = 2^16: the moments of step 1 and log Z_hat are
+    # log-sum-exps of log L(X_0), which no MH decision touches
+    pr = W.logistic()
+    N = 1 << 16
+    g = run_gpu(pr, oais.MALA, N, [0.0, 1.0], 0.01, seed=77)
+    lw = torch.from_numpy(g["logw"])
+    assert g["log_ghat"][0, 0] == pytest.approx(np.log(N), rel=1e-14)
+    assert g["log_ghat"][0, 1] == pytest.approx(torch.logsumexp(lw, 0).item(), rel=1e-12)
+    assert g["log_ghat"][0, 2] == pytest.approx(torch.logsumexp(2 * lw, 0).item(), rel=1e-12)
+    assert g["res"]["logZ"] == pytest.approx(torch.logsumexp(lw, 0).item() - np.log(N), rel=1e-12)
+    # sampled particles against the oracle (counter n_offset + n)
+    idx = [0, 1, 4097, N // 2 + 3, N - 1]
+    for n in idx:
+        r = o.asmc(_tg(pr), o.MALA, 1, [0.0, 1.0], 0.01, seed=77, n_offset=n)
+        assert g["logw"][n] == pytest.approx(r["logw"][0], rel=1e-5)
+
+
+def test_logistic_full_size_sampled():
+    # the logistic workload at N = 2^16, T = 256 (one round), sampled particles recomputed by the oracle
+    pr = W.logistic()
+    N, T = 1 << 16, 256
+    beta = W.linear_schedule(T) ** 4
+    eps = oais.default_step_sizes(pr, beta, oais.MALA)
+    g = run_gpu(pr, oais.MALA, N, beta, eps, seed=12057)
+    assert np.isfinite(g["logw"]).all() and np.isfinite(g["log_ghat"]).all()
+    assert g["log_ghat"][0, 0] == pytest.approx(np.log(N), rel=1e-14)
+    _, D_hat, _ = oais.optimise_schedule(g["beta"], g["log_ghat"], T)
+    assert np.all(D_hat >= 0)
+    assert g["res"]["logZ"] == pytest.approx(
+        torch.logsumexp(torch.from_numpy(g["logw"]), 0).item() - np.log(N), rel=1e-12)
+    rng = np.random.default_rng(0)
+    idx = np.concatenate([[0, 127, 128, N - 1], rng.integers(0, N, 8)])
+    tol = tolerances(pr)
+    agree = 0
+    for n in idx:
+        r = o.asmc(_tg(pr), o.MALA, 1, beta, eps, seed=12057, n_offset=int(n))
+        if r["margin"][0] <= tol["margin"]:
+            continue
+        agree += 1
+        assert g["logw"][n] == pytest.approx(r["logw"][0], rel=tol["rel"], abs=tol["abs"])
+        assert g["ell"][n] == pytest.approx(r["ell"][0], rel=tol["rel"], abs=tol["abs"])
+        np.testing.assert_allclose(g["x"][n], r["x"][0], rtol=tol["xrel"], atol=tol["xrel"])
+    assert agree >= len(idx) - 2
+
+
+def test_gmm_full_size_sampled():
+    # mixture workload at N = 2^20, T = 1024, 2 RWMH moves per step
+    pr = W.gmm()
+    N, T = 1 << 20, 1024
+    beta = W.linear_schedule(T) ** 3
+    g = run_gpu(pr, oais.RWMH, N, beta, 1.0, seed=12057, moves=2, cycle=True)
+    assert g["log_ghat"][0, 0] == pytest.approx(np.log(N), rel=1e-14)
+    # reading: L = p / eta with p normalised, Z = 1
+    assert abs(g["res"]["logZ"]) < 5 * max(g["res"]["se"], 0.01)
+    tol = tolerances(pr)
+    agree = 0
+    idx = [0, 1, N // 3, N - 1, 777777]
+    for n in idx:
+        r = o.asmc(_tg(pr), o.RWMH, 1, beta, 1.0, seed=12057, moves=2, cycle=True, n_offset=n)
+        if r["margin"][0] <= tol["margin"]:
+            continue
+        agree += 1
+        assert g["logw"][n] == pytest.approx(r["logw"][0], rel=tol["rel"], abs=tol["abs"])
+        np.testing.assert_allclose(g["x"][n], r["x"][0], rtol=tol["xrel"], atol=tol["xrel"])
+    assert agree >= len(idx) - 1
+
+
+def test_logsumexp_kernel_matches_torch():
+    for n in (1, 255, 256, 1000, 1 << 20, (1 << 20) + 13):
+        a = torch.randn(n, dtype=torch.float64, device="cuda") * 30
+        out = oais.logsumexp(a).cpu()
+        ref = torch.logsumexp(a.cpu(), 0).item(), torch.logsumexp(2 * a.cpu(), 0).item()
+        assert out[0].item() == pytest.approx(ref[0], rel=1e-13, abs=1e-13)
+        assert out[1].item() == pytest.approx(ref[1], rel=1e-13, abs=1e-13)
+
+
+def test_rounds_are_deterministic_and_reduce_barrier_error():
+    pr = W.gauss_conj()
+    beta = W.linear_schedule(64)
+
+    def three_rounds():
+        r = oais.OAIS(pr, oais.RWMH, 1024, beta, eps=0.5 / np.sqrt(8), seed=1)
+        outs = [r.round(64) for _ in range(3)]
+        st = r.stats()
+        r.close()
+        return outs, st
+    a, sa = three_rounds()
+    b, sb = three_rounds()
+    assert [x["logZ"] for x in a] == [x["logZ"] for x in b]
+    assert np.array_equal(sa["log_ghat"], sb["log_ghat"])
+    # the optimised schedules put more steps where the local barrier is large (early beta)
+    assert sa["beta"][1] < 1.0 / 64
