@@ -43,7 +43,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    return ap.parse_args()
+    ap.add_argument("--rounds", default=None,
+                    help="comma-separated T per round (profiling a smaller case); default 256,512,1024,2048")
+    a = ap.parse_args()
+    if a.rounds:
+        global ROUNDS_T
+        ROUNDS_T = [int(v) for v in a.rounds.split(",")]
+    return a
 
 
 def dist_env():

@@ -115,6 +115,32 @@ oais_status oais_init(oais_ctx** ctx, const oais_target* target, const oais_move
  * results and the current schedule are left unchanged (anytime property, Sec. 1). */
 oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out);
 
+/* One round of optimised ASMC (Alg. 2 with Alg. 1's adaptive resampling): particles
+ * advance in lock-step, one launch sequence per annealing step.  After the reweight of
+ * step t the ESS (eq. sample_size_IS) of w_{t^-} is reduced on the device; if
+ * ESS < ess_frac * N (and always at t = T) the segment closes, log Z_hat += LSE(log w) - log N
+ * (eq. estimator_Z), and for t < T the particles are resampled systematically (Sec. 2.1.3):
+ * fp64 inclusive scan C of the normalised weights, a^n = min{m : C_m > (n + U)/N} with one
+ * uniform U per event, gather into the second buffer, weights reset to 1.  ess_frac = 0 gives
+ * AIS in lock-step form; ess_frac = 1 resamples at every step (SIR).  The moments g_hat use
+ * w_{t-1}, i.e. the weights since the last resampling event.  Then installs
+ * OptimiseSchedule(T_next, ...) like oais_round.  Same errors as oais_round. */
+oais_status oasmc_round(oais_ctx* ctx, int32_t T_next, double ess_frac, oais_round_result* out);
+
+/* Resampling record of the last oasmc_round: ess [T] (ESS of w_{t^-} at every step),
+ * resampled [T] (1 where a segment closed, including t = T), ancestors [N] (int64, the
+ * ancestor indices of the last intermediate event; undefined if there was none).
+ * Host arrays, each may be NULL.  EINVAL if the last round was an OAIS round. */
+oais_status oais_get_resampling(const oais_ctx* ctx, double* ess, int32_t* resampled, int64_t* ancestors);
+
+/* Stand-alone ASMC(N, B_T) (Alg. 1) with adaptive resampling at threshold ess_frac on the
+ * schedule beta [T+1] (host) with step sizes eps [T] (host, NULL for 0.5/sqrt(d)).  Allocates
+ * its own device memory (cudaMalloc) for the call.  Outputs (host, may be NULL): out,
+ * log_ghat [T][3], ess_trace [T], resampled [T]. */
+oais_status asmc_run(const oais_target* target, const oais_move* move, int64_t N, const double* beta,
+                     int32_t T, const double* eps, double ess_frac, uint64_t seed, void* stream,
+                     oais_round_result* out, double* log_ghat, double* ess_trace, int32_t* resampled);
+
 /* log Z_hat and its delta-method SE from the last completed round. EINVAL if none. */
 oais_status oais_logZ(const oais_ctx* ctx, double* logZ, double* se);
 

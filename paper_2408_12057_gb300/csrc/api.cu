@@ -11,6 +11,10 @@
 #include "../../include/oais.h"
 
 namespace oais {
+cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts, double ess_frac, int d,
+                                 bool grad, bool fp64, double* bsum, double* boff, double* cdf,
+                                 double* ess_trace, int* resampled, int64_t* ancestors, cudaStream_t s);
+int scan_blocks(int64_t N);
 cudaError_t launch_merge_stats(const StepPartial*, int, int, double, double*, double*, cudaStream_t);
 cudaError_t launch_logsumexp(const double*, int64_t, double*, void*, cudaStream_t);
 size_t logsumexp_scratch_bytes(int64_t n);
@@ -124,6 +128,19 @@ struct oais_ctx {
     double *d_log_ghat = nullptr, *d_accept = nullptr, *d_lse = nullptr;
     void* d_lse_scratch = nullptr;
     unsigned* d_status = nullptr;
+    // ASMC: second particle buffer, gradient buffers, resampling scratch and traces
+    void* d_x1 = nullptr;
+    void *d_g0 = nullptr, *d_g1 = nullptr;
+    double* d_ell1 = nullptr;
+    StepPartial* d_ess_parts = nullptr;
+    AsmcState* d_st = nullptr;
+    double *d_bsum = nullptr, *d_boff = nullptr, *d_cdf = nullptr, *d_ess_trace = nullptr;
+    int* d_resampled = nullptr;
+    int64_t* d_anc = nullptr;
+    bool last_asmc = false;
+    int l_n_resample = 0;
+    std::vector<double> l_ess_trace;
+    std::vector<int> l_resampled;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // schedule of the next round
     std::vector<double> beta, eps;
@@ -160,7 +177,8 @@ static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 static size_t elt_bytes(int kind) { return kind == kGauss ? sizeof(double) : sizeof(float); }
 
 struct Layout {
-    size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, lse, lse_scr, status, total;
+    size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, lse, lse_scr, status;
+    size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, total;
 };
 
 static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
@@ -186,6 +204,19 @@ static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
     L.lse = take(sizeof(double) * 2);
     L.lse_scr = take(logsumexp_scratch_bytes(N));
     L.status = take(sizeof(unsigned));
+    const size_t xbytes = elt_bytes(tg->kind) * (size_t)tg->d * N;
+    L.x1 = take(xbytes);
+    L.g0 = take(xbytes);
+    L.g1 = take(xbytes);
+    L.ell1 = take(sizeof(double) * N);
+    L.ess_parts = take(sizeof(StepPartial) * (size_t)sweep_grid(N));
+    L.st = take(sizeof(AsmcState));
+    L.bsum = take(sizeof(double) * scan_blocks(N));
+    L.boff = take(sizeof(double) * scan_blocks(N));
+    L.cdf = take(sizeof(double) * N);
+    L.ess_trace = take(sizeof(double) * T_max);
+    L.resampled = take(sizeof(int) * T_max);
+    L.anc = take(sizeof(int64_t) * N);
     L.total = off;
     return L;
 }
@@ -321,6 +352,18 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     ctx->d_lse = reinterpret_cast<double*>(b + L.lse);
     ctx->d_lse_scratch = b + L.lse_scr;
     ctx->d_status = reinterpret_cast<unsigned*>(b + L.status);
+    ctx->d_x1 = b + L.x1;
+    ctx->d_g0 = b + L.g0;
+    ctx->d_g1 = b + L.g1;
+    ctx->d_ell1 = reinterpret_cast<double*>(b + L.ell1);
+    ctx->d_ess_parts = reinterpret_cast<StepPartial*>(b + L.ess_parts);
+    ctx->d_st = reinterpret_cast<AsmcState*>(b + L.st);
+    ctx->d_bsum = reinterpret_cast<double*>(b + L.bsum);
+    ctx->d_boff = reinterpret_cast<double*>(b + L.boff);
+    ctx->d_cdf = reinterpret_cast<double*>(b + L.cdf);
+    ctx->d_ess_trace = reinterpret_cast<double*>(b + L.ess_trace);
+    ctx->d_resampled = reinterpret_cast<int*>(b + L.resampled);
+    ctx->d_anc = reinterpret_cast<int64_t*>(b + L.anc);
 
     // data in the padded device layout
     const int rows = tg->kind == kGauss ? 1 : tg->n;
@@ -377,9 +420,9 @@ static SweepParams make_params(const oais_ctx* ctx, int T, const double* d_beta,
 {
     SweepParams P{};
     P.N = N; P.n_offset = n_offset; P.T = T; P.beta = d_beta; P.eps = d_eps;
-    P.ref_scale = ctx->dt.ref_scale; P.K = ctx->mv.moves; P.leapfrog = ctx->mv.leapfrog;
-    P.cycle = ctx->mv.cycle;
-    P.rng.k0 = (uint32_t)(seed & 0xFFFFFFFFu); P.rng.k1 = (uint32_t)(seed >> 32); P.rng.tag = tag;
+    P.ref_scale = ctx->dt.ref_scale; P.mv.K = ctx->mv.moves; P.mv.leapfrog = ctx->mv.leapfrog;
+    P.mv.cycle = ctx->mv.cycle;
+    P.mv.rng.k0 = (uint32_t)(seed & 0xFFFFFFFFu); P.mv.rng.k1 = (uint32_t)(seed >> 32); P.mv.rng.tag = tag;
     P.logw = logw; P.x_out = x; P.ell_out = ell; P.partials = static_cast<StepPartial*>(parts);
     P.status = status;
     return P;
@@ -448,66 +491,188 @@ static std::vector<double> next_step_sizes(const oais_ctx* ctx, const std::vecto
     return out;
 }
 
-oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out)
+static StepParams make_step_params(const oais_ctx* ctx, int T, uint32_t tag)
+{
+    StepParams P{};
+    P.N = ctx->N; P.t = 0; P.T = T; P.beta = ctx->d_beta; P.eps = ctx->d_eps;
+    P.ref_scale = ctx->dt.ref_scale; P.mv.K = ctx->mv.moves; P.mv.leapfrog = ctx->mv.leapfrog;
+    P.mv.cycle = ctx->mv.cycle;
+    P.mv.rng.k0 = (uint32_t)(ctx->seed & 0xFFFFFFFFu); P.mv.rng.k1 = (uint32_t)(ctx->seed >> 32);
+    P.mv.rng.tag = tag;
+    P.x[0] = ctx->d_x; P.x[1] = ctx->d_x1; P.gl[0] = ctx->d_g0; P.gl[1] = ctx->d_g1;
+    P.ell[0] = ctx->d_ell; P.ell[1] = ctx->d_ell1; P.logw = ctx->d_logw;
+    P.st = ctx->d_st; P.partials = ctx->d_parts; P.ess_parts = ctx->d_ess_parts; P.status = ctx->d_status;
+    return P;
+}
+
+static cudaError_t launch_asmc(const DevTarget& dt, int move, bool init, const StepParams& P, cudaStream_t s)
+{
+    switch (dt.kind) {
+    case kGauss: return launch_asmc_gauss(dt, move, init, P, s);
+    case kLogreg: return launch_asmc_logreg(dt, move, init, P, s);
+    case kGmm: return launch_asmc_gmm(dt, move, init, P, s);
+    case kLinreg: return launch_asmc_linreg(dt, move, init, P, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// One round of Alg. 2: ASMC(N, B_T) on the current schedule, then Budget is the caller's
+// T_next and OptimiseSchedule(T_next, B_T, g_hat) becomes the next schedule.
+// asmc = false: AIS with the particle and time loops swapped (Sec. 5.1.2);
+// asmc = true: lock-step particles with adaptive resampling at threshold ess_frac.
+static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double ess_frac, oais_round_result* out)
 {
     if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
     if (T_next < 1 || T_next > ctx->T_max) return fail(ctx, OAIS_EINVAL, "T_next out of range");
+    if (asmc && !(ess_frac >= 0.0 && ess_frac <= 1.0 + 1e-12))
+        return fail(ctx, OAIS_EINVAL, "ess_frac must be in [0, 1]");
     const int T = (int)ctx->beta.size() - 1;
     cudaStream_t s = ctx->stream;
     CK(cudaMemcpyAsync(ctx->d_beta, ctx->beta.data(), sizeof(double) * (T + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_eps, ctx->eps.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s));
     const uint32_t tag = (uint32_t)(ctx->round & 0xFFFF);
-    SweepParams P = make_params(ctx, T, ctx->d_beta, ctx->d_eps, ctx->seed, tag, 0, ctx->N, ctx->d_logw,
-                                ctx->d_ell, ctx->d_x, ctx->d_parts, ctx->d_status);
-    CK(cudaEventRecord(ctx->ev0, s));
-    CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
-    CK(cudaEventRecord(ctx->ev1, s));
-    CK(launch_merge_stats(ctx->d_parts, sweep_grid(ctx->N), T, 1.0 / ((double)ctx->N * ctx->mv.moves),
-                          ctx->d_log_ghat, ctx->d_accept, s));
-    CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
-    std::vector<double> lg(3 * T), acc(T);
-    double lse[2];
+    const int grid = sweep_grid(ctx->N);
+    const double logN = std::log((double)ctx->N);
+    std::vector<double> lg(3 * T), acc(T), ess_tr;
+    std::vector<int> rs;
     unsigned status = 0;
-    CK(cudaMemcpyAsync(lg.data(), ctx->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(acc.data(), ctx->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(lse, ctx->d_lse, sizeof(lse), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    double logZ, ess, se;
+    int n_res = 0;
+    if (!asmc) {
+        SweepParams P = make_params(ctx, T, ctx->d_beta, ctx->d_eps, ctx->seed, tag, 0, ctx->N, ctx->d_logw,
+                                    ctx->d_ell, ctx->d_x, ctx->d_parts, ctx->d_status);
+        CK(cudaEventRecord(ctx->ev0, s));
+        CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
+        CK(cudaEventRecord(ctx->ev1, s));
+        CK(launch_merge_stats(ctx->d_parts, grid, T, 1.0 / ((double)ctx->N * ctx->mv.moves),
+                              ctx->d_log_ghat, ctx->d_accept, s));
+        CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
+        double lse[2];
+        CK(cudaMemcpyAsync(lg.data(), ctx->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(acc.data(), ctx->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(lse, ctx->d_lse, sizeof(lse), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        logZ = lse[0] - logN;
+        ess = std::exp(2.0 * lse[0] - lse[1]);
+        se = std::sqrt(std::max(0.0, 1.0 / ess - 1.0 / (double)ctx->N));
+    } else {
+        CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(AsmcState), s));
+        StepParams P = make_step_params(ctx, T, tag);
+        const bool grad = ctx->mv.kind != OAIS_RWMH;
+        CK(cudaEventRecord(ctx->ev0, s));
+        CK(launch_asmc(ctx->dt, ctx->mv.kind, true, P, s));
+        for (int t = 1; t <= T; ++t) {
+            P.t = t;
+            CK(launch_asmc(ctx->dt, ctx->mv.kind, false, P, s));
+            CK(launch_asmc_resample(ctx->d_st, P, grid, ess_frac, ctx->dt.d, grad, ctx->dt.kind == kGauss,
+                                    ctx->d_bsum, ctx->d_boff, ctx->d_cdf, ctx->d_ess_trace, ctx->d_resampled,
+                                    ctx->d_anc, s));
+        }
+        CK(cudaEventRecord(ctx->ev1, s));
+        CK(launch_merge_stats(ctx->d_parts, grid, T, 1.0 / ((double)ctx->N * ctx->mv.moves),
+                              ctx->d_log_ghat, ctx->d_accept, s));
+        AsmcState st;
+        ess_tr.resize(T);
+        rs.resize(T);
+        CK(cudaMemcpyAsync(lg.data(), ctx->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(acc.data(), ctx->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&st, ctx->d_st, sizeof(st), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ess_tr.data(), ctx->d_ess_trace, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(rs.data(), ctx->d_resampled, sizeof(int) * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        // the particles of the last step live in buffer cur (no resampling is pending at t = T)
+        if ((st.cur ^ st.pend) == 1) {
+            const size_t xb = elt_bytes(ctx->dt.kind) * (size_t)ctx->dt.d * ctx->N;
+            CK(cudaMemcpyAsync(ctx->d_x, ctx->d_x1, xb, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(ctx->d_ell, ctx->d_ell1, sizeof(double) * ctx->N, cudaMemcpyDeviceToDevice, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        logZ = st.logZ;
+        n_res = st.n_resample;
+        ess = ess_tr[T - 1];
+        // delta-method variance of a product of independent segment means
+        double v = 0.0;
+        for (int t = 0; t < T; ++t) if (rs[t]) v += std::max(0.0, 1.0 / ess_tr[t] - 1.0 / (double)ctx->N);
+        se = std::sqrt(v);
+    }
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-    if (status & 1u) return fail(ctx, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood in the sweep");
+    if (status & 1u) return fail(ctx, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood");
 
-    const double logN = std::log((double)ctx->N);
     std::vector<double> beta_next(T_next + 1), D(T), Lam(T + 1);
     optimise_schedule(T, ctx->beta.data(), lg.data(), T_next, beta_next.data(), D.data(), Lam.data());
     std::vector<double> eps_next = next_step_sizes(ctx, ctx->beta, ctx->eps, acc, beta_next);
 
     ctx->have_last = true;
+    ctx->last_asmc = asmc;
     ctx->l_beta = ctx->beta;
     ctx->l_eps = ctx->eps;
     ctx->l_log_ghat = lg;
     ctx->l_D = D;
     ctx->l_accept = acc;
-    ctx->l_logZ = lse[0] - logN;
-    ctx->l_ess = std::exp(2.0 * lse[0] - lse[1]);
-    ctx->l_se = std::sqrt(std::max(0.0, 1.0 / ctx->l_ess - 1.0 / (double)ctx->N));
+    ctx->l_logZ = logZ;
+    ctx->l_ess = ess;
+    ctx->l_se = se;
     ctx->l_Lambda = Lam[T];
+    ctx->l_n_resample = n_res;
+    ctx->l_ess_trace = ess_tr;
+    ctx->l_resampled = rs;
     if (out) {
-        out->logZ = ctx->l_logZ;
-        out->se = ctx->l_se;
-        out->Lambda_hat = ctx->l_Lambda;
-        out->ess = ctx->l_ess;
+        out->logZ = logZ;
+        out->se = se;
+        out->Lambda_hat = Lam[T];
+        out->ess = ess;
         out->sweep_ms = ms;
         out->T = T;
         out->round = ctx->round;
-        out->n_resample = 0;
+        out->n_resample = n_res;
         out->pad = 0;
     }
     ctx->beta = beta_next;
     ctx->eps = eps_next;
     ++ctx->round;
     return OAIS_OK;
+}
+
+oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out)
+{
+    return run_round(ctx, T_next, false, 0.0, out);
+}
+
+oais_status oasmc_round(oais_ctx* ctx, int32_t T_next, double ess_frac, oais_round_result* out)
+{
+    return run_round(ctx, T_next, true, ess_frac, out);
+}
+
+oais_status oais_get_resampling(const oais_ctx* ctx, double* ess, int32_t* resampled, int64_t* ancestors)
+{
+    if (!ctx || !ctx->have_last) return fail(nullptr, OAIS_EINVAL, "no completed round");
+    if (!ctx->last_asmc) return fail(nullptr, OAIS_EINVAL, "the last round did not resample (OAIS)");
+    if (ess) std::copy(ctx->l_ess_trace.begin(), ctx->l_ess_trace.end(), ess);
+    if (resampled) std::copy(ctx->l_resampled.begin(), ctx->l_resampled.end(), resampled);
+    if (ancestors) {
+        cudaError_t e = cudaMemcpy(ancestors, ctx->d_anc, sizeof(int64_t) * ctx->N, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(nullptr, OAIS_ECUDA, cudaGetErrorString(e));
+    }
+    return OAIS_OK;
+}
+
+oais_status asmc_run(const oais_target* target, const oais_move* move, int64_t N, const double* beta,
+                     int32_t T, const double* eps, double ess_frac, uint64_t seed, void* stream,
+                     oais_round_result* out, double* log_ghat, double* ess_trace, int32_t* resampled)
+{
+    oais_ctx* ctx = nullptr;
+    oais_status st = oais_init(&ctx, target, move, N, beta, T, T, eps, seed, nullptr, 0, stream);
+    if (st != OAIS_OK) return st;
+    st = oasmc_round(ctx, T, ess_frac, out);
+    if (st == OAIS_OK && log_ghat) std::copy(ctx->l_log_ghat.begin(), ctx->l_log_ghat.end(), log_ghat);
+    if (st == OAIS_OK) st = oais_get_resampling(ctx, ess_trace, resampled, nullptr);
+    if (st != OAIS_OK) g_err = ctx->err.empty() ? g_err : ctx->err;
+    oais_destroy(ctx);
+    return st;
 }
 
 oais_status oais_logZ(const oais_ctx* ctx, double* logZ, double* se)

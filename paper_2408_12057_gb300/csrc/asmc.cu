@@ -1,0 +1,190 @@
+// asmc.cu -- the resampling half of ASMC (Alg. 1, resample step; Sec. 2.1.3):
+//   decide:   ESS of w_{t^-} = (sum w)^2 / sum w^2 (eq. sample_size_IS); resample when
+//             ESS < nu N, and always close the last segment at t = T; on a resampling
+//             time Z_hat *= mean(w) (eq. estimator_Z), kept as log Z_hat += LSE(log w) - log N;
+//   scan:     normalised weights W_m = exp(log w_m - LSE) and their inclusive cumulative
+//             sums C_m in fp64 (block sums, block offsets, in-block scan: a fixed order);
+//   gather:   systematic resampling, a^n = min{m : C_m > (n + U)/N} by binary search,
+//             particles copied to the other buffer, w = 1.
+// Every kernel after `decide` reads the device flag `pend` and returns at once when the
+// step does not resample, so a whole schedule is launched without host round-trips.
+#include "internal.h"
+
+namespace oais {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;   // particles per scan block
+
+int scan_blocks(int64_t N) { return (int)((N + kScanTile - 1) / kScanTile); }
+
+__global__ void __launch_bounds__(256)
+asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ ess_parts, int nparts, int t, int T,
+                   double ess_frac, int64_t N, Rng rng, double* ess_trace, int* resampled)
+{
+    __shared__ double sm[2][256], ss[2][256];
+    const int tid = threadIdx.x;
+    double m[2] = {-INFINITY, -INFINITY}, s[2] = {0.0, 0.0};
+    for (int j = tid; j < nparts; j += 256) {
+        lse_merge(m[0], s[0], ess_parts[j].m[0], ess_parts[j].s[0]);
+        lse_merge(m[1], s[1], ess_parts[j].m[1], ess_parts[j].s[1]);
+    }
+    sm[0][tid] = m[0]; ss[0][tid] = s[0]; sm[1][tid] = m[1]; ss[1][tid] = s[1];
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if (tid < stride) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                double mm = sm[i][tid], s0 = ss[i][tid];
+                lse_merge(mm, s0, sm[i][tid + stride], ss[i][tid + stride]);
+                sm[i][tid] = mm; ss[i][tid] = s0;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double lse1 = sm[0][0] + log(ss[0][0]);
+        const double lse2 = sm[1][0] + log(ss[1][0]);
+        const double ess = exp(2.0 * lse1 - lse2);
+        st->cur ^= st->pend;             // the previous step's gather is now the live buffer
+        const bool fire = (t == T) || (ess_frac > 0.0 && ess < ess_frac * (double)N);
+        int pend = 0;
+        if (fire) {
+            st->logZ += lse1 - log((double)N);
+            if (t < T) {
+                pend = 1;
+                st->n_resample += 1;
+                st->lse = lse1;
+                const Philox4 r = philox4x32_10(0xFFFFFFFFu, (uint32_t)t, 0u, rng.tag, rng.k0, rng.k1);
+                st->U = u01d(r.v[0]);
+            }
+        }
+        st->pend = pend;
+        if (ess_trace) ess_trace[t - 1] = ess;
+        if (resampled) resampled[t - 1] = fire ? 1 : 0;
+    }
+}
+
+// block-level inclusive scan of kScanTile doubles held kScanItems per thread
+__device__ __forceinline__ double block_scan_inclusive(double (&v)[kScanItems], double* sh,
+                                                       double* thread_prefix = nullptr)
+{
+    // thread-local inclusive scan
+#pragma unroll
+    for (int i = 1; i < kScanItems; ++i) v[i] += v[i - 1];
+    const int tid = threadIdx.x;
+    sh[tid] = v[kScanItems - 1];
+    __syncthreads();
+    // Hillis-Steele over the thread totals (fixed order)
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        const double add = tid >= off ? sh[tid - off] : 0.0;
+        __syncthreads();
+        sh[tid] += add;
+        __syncthreads();
+    }
+    const double prefix = tid > 0 ? sh[tid - 1] : 0.0;
+    if (thread_prefix) *thread_prefix = prefix;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) v[i] += prefix;
+    return sh[kScanThreads - 1];
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+asmc_blocksum_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N, double* bsum)
+{
+    if (!st->pend) return;
+    __shared__ double sh[kScanThreads];
+    const double lse = st->lse;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    double v[kScanItems];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) v[i] = base + i < N ? exp(logw[base + i] - lse) : 0.0;
+    const double tot = block_scan_inclusive(v, sh);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// exclusive scan of the block sums by one CTA, in chunks of kScanTile
+__global__ void __launch_bounds__(kScanThreads)
+asmc_offsets_kernel(const AsmcState* st, const double* __restrict__ bsum, int nb, double* boff)
+{
+    if (!st->pend) return;
+    __shared__ double sh[kScanThreads];
+    double carry = 0.0;
+    for (int c0 = 0; c0 < nb; c0 += kScanTile) {
+        const int base = c0 + threadIdx.x * kScanItems;
+        double v[kScanItems], pre = 0.0;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) v[i] = base + i < nb ? bsum[base + i] : 0.0;
+        const double tot = block_scan_inclusive(v, sh, &pre);
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i)
+            if (base + i < nb) boff[base + i] = carry + (i == 0 ? pre : v[i - 1]);
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+asmc_cdf_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N,
+                const double* __restrict__ boff, double* cdf)
+{
+    if (!st->pend) return;
+    __shared__ double sh[kScanThreads];
+    const double lse = st->lse;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    double v[kScanItems];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) v[i] = base + i < N ? exp(logw[base + i] - lse) : 0.0;
+    block_scan_inclusive(v, sh);
+    const double off = boff[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) if (base + i < N) cdf[base + i] = off + v[i];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const double* __restrict__ cdf,
+                   int64_t* ancestors)
+{
+    if (!st->pend) return;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= P.N) return;
+    const double thr = ((double)n + st->U) / (double)P.N;
+    // a = min{m : C_m > thr}, clamped to N - 1
+    int64_t lo = 0, hi = P.N - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cdf[mid] > thr) hi = mid; else lo = mid + 1;
+    }
+    const int64_t a = lo;
+    const int src = st->cur, dst = src ^ 1;
+    const R* xs = reinterpret_cast<const R*>(P.x[src]);
+    R* xd = reinterpret_cast<R*>(P.x[dst]);
+    for (int i = 0; i < d; ++i) xd[(size_t)i * P.N + n] = xs[(size_t)i * P.N + a];
+    if (grad) {
+        const R* gs = reinterpret_cast<const R*>(P.gl[src]);
+        R* gd = reinterpret_cast<R*>(P.gl[dst]);
+        for (int i = 0; i < d; ++i) gd[(size_t)i * P.N + n] = gs[(size_t)i * P.N + a];
+    }
+    P.ell[dst][n] = P.ell[src][a];
+    P.logw[n] = 0.0;
+    if (ancestors) ancestors[n] = a;
+}
+
+cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts, double ess_frac, int d,
+                                 bool grad, bool fp64, double* bsum, double* boff, double* cdf,
+                                 double* ess_trace, int* resampled, int64_t* ancestors, cudaStream_t s)
+{
+    asmc_decide_kernel<<<1, 256, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, ess_frac, P.N, P.mv.rng,
+                                         ess_trace, resampled);
+    const int nb = scan_blocks(P.N);
+    asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
+    asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);
+    asmc_cdf_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, boff, cdf);
+    const int gb = (int)((P.N + 255) / 256);
+    if (fp64) asmc_gather_kernel<double><<<gb, 256, 0, s>>>(st, P, d, grad ? 1 : 0, cdf, ancestors);
+    else      asmc_gather_kernel<float><<<gb, 256, 0, s>>>(st, P, d, grad ? 1 : 0, cdf, ancestors);
+    return cudaGetLastError();
+}
+
+} // namespace oais

@@ -27,13 +27,17 @@ cudaError_t launch_sweep_logreg(const DevTarget& t, int move, const SweepParams&
 cudaError_t launch_sweep_gmm(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s);
 cudaError_t launch_sweep_linreg(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s);
 
+// ASMC: init (t = 0) or one annealing step, per family
+cudaError_t launch_asmc_gauss(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
+cudaError_t launch_asmc_logreg(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
+cudaError_t launch_asmc_gmm(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
+cudaError_t launch_asmc_linreg(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
+
 inline int sweep_grid(int64_t N) { return (int)((N + kSweepThreads - 1) / kSweepThreads); }
 
-// generic launcher used by the per-family translation units
-template <class Tgt, int MOVE, int D, typename R>
-cudaError_t launch_one(const Tgt& tg, size_t smem, const SweepParams& P, cudaStream_t s)
+template <class Kern, class Params, class Tgt>
+cudaError_t launch_kernel(Kern* k, const Tgt& tg, size_t smem, const Params& P, cudaStream_t s)
 {
-    auto* k = &oais_sweep_kernel<Tgt, MOVE, D, R>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -41,5 +45,54 @@ cudaError_t launch_one(const Tgt& tg, size_t smem, const SweepParams& P, cudaStr
     k<<<sweep_grid(P.N), kSweepThreads, smem, s>>>(P, tg);
     return cudaGetLastError();
 }
+
+// generic launchers used by the per-family translation units
+template <class Tgt, int MOVE, int D, typename R>
+cudaError_t launch_one(const Tgt& tg, size_t smem, const SweepParams& P, cudaStream_t s)
+{
+    return launch_kernel(&oais_sweep_kernel<Tgt, MOVE, D, R>, tg, smem, P, s);
+}
+
+template <class Tgt, int MOVE, int D, typename R>
+cudaError_t launch_one(const Tgt& tg, size_t smem, const StepParams& P, bool init, cudaStream_t s)
+{
+    if (init) return launch_kernel(&asmc_init_kernel<Tgt, MOVE, D, R>, tg, smem, P, s);
+    return launch_kernel(&asmc_step_kernel<Tgt, MOVE, D, R>, tg, smem, P, s);
+}
+
+// one family's dispatch over (move, width) for both kernel kinds
+#define OAIS_FAMILY_DISPATCH(FAM, MAKE, R, ...)                                                  \
+    template <int D, class P, class... A>                                                        \
+    static cudaError_t go(const DevTarget& t, int move, const P& prm, cudaStream_t s, A... a)   \
+    {                                                                                            \
+        size_t smem = 0;                                                                         \
+        auto tg = MAKE<D>(t, &smem);                                                             \
+        using TG = decltype(tg);                                                                 \
+        switch (move) {                                                                          \
+        case kRwmh: return launch_one<TG, kRwmh, D, R>(tg, smem, prm, a..., s);                  \
+        case kMala: return launch_one<TG, kMala, D, R>(tg, smem, prm, a..., s);                  \
+        case kHmc:  return launch_one<TG, kHmc, D, R>(tg, smem, prm, a..., s);                   \
+        }                                                                                        \
+        return cudaErrorInvalidValue;                                                            \
+    }                                                                                            \
+    template <class P, class... A>                                                               \
+    static cudaError_t by_width(const DevTarget& t, int move, const P& prm, cudaStream_t s, A... a) \
+    {                                                                                            \
+        switch (t.D) {                                                                           \
+        __VA_ARGS__                                                                              \
+        }                                                                                        \
+        return cudaErrorInvalidValue;                                                            \
+    }                                                                                            \
+    cudaError_t launch_sweep_##FAM(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s) \
+    {                                                                                            \
+        return by_width(t, move, P, s);                                                          \
+    }                                                                                            \
+    cudaError_t launch_asmc_##FAM(const DevTarget& t, int move, bool init, const StepParams& P,  \
+                                  cudaStream_t s)                                                \
+    {                                                                                            \
+        return by_width(t, move, P, s, init);                                                    \
+    }
+
+#define OAIS_WIDTH(W) case W: return go<W>(t, move, prm, s, a...);
 
 } // namespace oais

@@ -134,6 +134,37 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
     }
 }
 
+// CTA part: warp 0 merges the W warps' (m, s) (lane j holds warp j) in a fixed order and
+// writes one record.  Call after a __syncthreads that follows warp_moment_partial.
+template <int W>
+__device__ __forceinline__ void cta_moment_record(const double (*wm)[3], const float (*ws)[3],
+                                                  const unsigned* wacc, StepPartial* out)
+{
+    const int lane = threadIdx.x & 31;
+    if ((threadIdx.x >> 5) != 0) return;
+    StepPartial rec;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double m = lane < W ? wm[lane][i] : -INFINITY;
+        double M = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
+        double v = (lane < W && m != -INFINITY) ? (double)ws[lane][i] * exp(m - M) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        rec.m[i] = M;
+        rec.s[i] = v;
+    }
+    unsigned a = (wacc && lane < W) ? wacc[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if (lane == 0) {
+        rec.accepted = a;
+        rec.pad = 0;
+        *out = rec;
+    }
+}
+
 // merge (m, s) pairs: exp(m) s + exp(m') s'
 __device__ __forceinline__ void lse_merge(double& m, double& s, double m2, double s2)
 {

@@ -18,6 +18,14 @@ enum MoveKind { kRwmh = 0, kMala = 1, kHmc = 2 };
 
 constexpr int kSweepThreads = 128;
 
+// what an MH move needs besides the particle
+struct MoveCfg {
+    Rng rng;
+    int K;                // moves per step
+    int leapfrog;
+    int cycle;            // RWMH std cycles 0.1, 1, 10 by global move index
+};
+
 struct SweepParams {
     int64_t N;            // particles in this launch
     int64_t n_offset;     // global index of particle 0 (counter word 0)
@@ -25,10 +33,7 @@ struct SweepParams {
     const double* beta;   // [T+1]
     const double* eps;    // [T] step size per annealing step
     double ref_scale;     // s
-    int K;                // moves per step
-    int leapfrog;
-    int cycle;            // RWMH std cycles 0.1, 1, 10 by global move index
-    Rng rng;
+    MoveCfg mv;
     // outputs
     double* logw;         // [N]
     void* x_out;          // [d][N] SoA, element type R
@@ -40,7 +45,7 @@ struct SweepParams {
 template <typename R> __device__ __forceinline__ R rsq(R a) { return a * a; }
 
 template <class Tgt, int MOVE, int D, typename R>
-__device__ __forceinline__ bool mh_move(const Tgt& tg, const SweepParams& P, R (&x)[D], R& ell,
+__device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[D], R& ell,
                                         R (&gl)[D], double beta_t, double eps_t, uint32_t n,
                                         uint32_t t, uint32_t k, int d, R inv_s2)
 {
@@ -140,12 +145,13 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
     constexpr bool GRAD = (MOVE != kRwmh);
 
     R x[D], gl[D];
-    normals<D>(P.rng, n, 0u, 0u, d, x);
+    normals<D>(P.mv.rng, n, 0u, 0u, d, x);
 #pragma unroll
     for (int i = 0; i < D; ++i) { x[i] *= s; gl[i] = R(0); }
     R ell = tg.template eval<GRAD>(x, gl);
     double logw = 0.0;
     unsigned bad = 0;
+    (void)lane;
 
     double beta_prev = P.beta[0];
     for (int t = 1; t <= P.T; ++t) {
@@ -157,41 +163,18 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
         warp_moment_partial(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
         logw += lg;
         unsigned acc = 0;
-        for (int k = 0; k < P.K; ++k)
-            acc += mh_move<Tgt, MOVE, D, R>(tg, P, x, ell, gl, beta_t, eps_t, n, (uint32_t)t,
+        for (int k = 0; k < P.mv.K; ++k)
+            acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_t, eps_t, n, (uint32_t)t,
                                             (uint32_t)k, d, inv_s2) ? 1u : 0u;
         acc = active ? acc : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if (lane == 0) s_acc[slot][warp] = acc;
         __syncthreads();
-        if (warp == 0) {
-            // merge the warps of this CTA in a fixed order (lane j holds warp j)
-            constexpr int W = kSweepThreads / 32;
-            StepPartial out;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                double m = lane < W ? s_m[slot][lane][i] : -INFINITY;
-                double M = m;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
-                double v = (lane < W && m != -INFINITY) ? (double)s_s[slot][lane][i] * exp(m - M) : 0.0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-                out.m[i] = M;
-                out.s[i] = v;
-            }
-            unsigned a = lane < W ? s_acc[slot][lane] : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-            if (lane == 0) {
-                out.accepted = a;
-                out.pad = 0;
-                P.partials[(size_t)(t - 1) * gridDim.x + blockIdx.x] = out;
-            }
-        }
-        if (!isfinite(logw) || !isfinite((double)ell)) bad = 1;
+        cta_moment_record<kSweepThreads / 32>(s_m[slot], s_s[slot], s_acc[slot],
+                                              P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
     }
+    if (!isfinite(logw) || !isfinite((double)ell)) bad = 1;
     if (active) {
         P.logw[n64] = logw;
         P.ell_out[n64] = (double)ell;
@@ -200,6 +183,141 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
         for (int i = 0; i < D; ++i) if (i < d) xo[(size_t)i * P.N + n64] = x[i];
     }
     if (active && bad) atomicOr(P.status, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// ASMC (Alg. 1 with adaptive resampling): particles advance in lock-step, one launch per
+// annealing step, because the resampling test needs every particle's weight.  The
+// particle store is double-buffered structure-of-arrays; the buffer in use is
+// cur ^ pend (pend = "the previous step resampled into the other buffer"), both read
+// from device memory, so a whole schedule can be launched without host round-trips.
+// ---------------------------------------------------------------------------
+struct AsmcState {
+    int cur;            // buffer holding the particles at the start of the last decision
+    int pend;           // 1: the last step resampled into buffer cur ^ 1
+    int n_resample;     // intermediate resampling events so far
+    int pad;
+    double logZ;        // accumulated sum_r (LSE(log w_{tau_r^-}) - log N)
+    double lse;         // LSE of the weights of the pending resampling event
+    double U;           // its systematic-resampling uniform
+};
+
+struct StepParams {
+    int64_t N;
+    int t, T;
+    const double* beta;
+    const double* eps;
+    double ref_scale;
+    MoveCfg mv;
+    void* x[2];           // [d][N] element type R
+    void* gl[2];          // [d][N] grad log L (MALA/HMC), else unused
+    double* ell[2];       // [N]
+    double* logw;         // [N]
+    const AsmcState* st;
+    StepPartial* partials;  // [T][gridDim.x]
+    StepPartial* ess_parts; // [gridDim.x]: m/s[0] for log w, m/s[1] for 2 log w
+    unsigned* status;
+};
+
+template <class Tgt, int MOVE, int D, typename R>
+__global__ void __launch_bounds__(kSweepThreads)
+asmc_step_kernel(const StepParams P, Tgt tg)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_m[kSweepThreads / 32][3];
+    __shared__ float s_s[kSweepThreads / 32][3];
+    __shared__ unsigned s_acc[kSweepThreads / 32];
+    constexpr bool GRAD = (MOVE != kRwmh);
+
+    tg.setup(smem);
+    const int d = tg.d;
+    const int64_t n64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = n64 < P.N;
+    const int64_t idx = active ? n64 : P.N - 1;
+    const uint32_t n = (uint32_t)idx;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const R s = (R)P.ref_scale;
+    const R inv_s2 = R(1) / (s * s);
+    const int b = P.st->cur ^ P.st->pend;
+    const R* xb = reinterpret_cast<const R*>(P.x[b]);
+    const R* gb = reinterpret_cast<const R*>(P.gl[b]);
+
+    R x[D], gl[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        x[i] = i < d ? xb[(size_t)i * P.N + idx] : R(0);
+        gl[i] = (GRAD && i < d) ? gb[(size_t)i * P.N + idx] : R(0);
+    }
+    R ell = (R)P.ell[b][idx];
+    double logw = P.logw[idx];
+
+    const double beta_t = P.beta[P.t], eps_t = P.eps[P.t - 1];
+    const double lg = (beta_t - P.beta[P.t - 1]) * (double)ell;
+    warp_moment_partial(logw, lg, active, s_m[warp], s_s[warp]);
+    logw += lg;
+    unsigned acc = 0;
+    for (int k = 0; k < P.mv.K; ++k)
+        acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_t, eps_t, n, (uint32_t)P.t,
+                                        (uint32_t)k, d, inv_s2) ? 1u : 0u;
+    acc = active ? acc : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0) s_acc[warp] = acc;
+    __syncthreads();
+    cta_moment_record<kSweepThreads / 32>(s_m, s_s, s_acc,
+                                          P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
+    __syncthreads();
+    // ESS pieces of w_{t^-}: LSE of log w (slot 0) and of 2 log w (slot 1)
+    warp_moment_partial(logw, logw, active, s_m[warp], s_s[warp]);
+    __syncthreads();
+    cta_moment_record<kSweepThreads / 32>(s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
+    if (active) {
+        R* xw = reinterpret_cast<R*>(P.x[b]);
+        R* gw = reinterpret_cast<R*>(P.gl[b]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            if (i < d) {
+                xw[(size_t)i * P.N + n64] = x[i];
+                if (GRAD) gw[(size_t)i * P.N + n64] = gl[i];
+            }
+        }
+        P.ell[b][n64] = (double)ell;
+        P.logw[n64] = logw;
+        if (!isfinite(logw) || !isfinite((double)ell)) atomicOr(P.status, 1u);
+    }
+}
+
+// t = 0 of Alg. 1: X_0 ~ eta, w_0 = 1, cached log L and its gradient, into buffer 0.
+template <class Tgt, int MOVE, int D, typename R>
+__global__ void __launch_bounds__(kSweepThreads)
+asmc_init_kernel(const StepParams P, Tgt tg)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool GRAD = (MOVE != kRwmh);
+    tg.setup(smem);
+    const int d = tg.d;
+    const int64_t n64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = n64 < P.N;
+    const uint32_t n = (uint32_t)(active ? n64 : P.N - 1);
+    const R s = (R)P.ref_scale;
+    R x[D], gl[D];
+    normals<D>(P.mv.rng, n, 0u, 0u, d, x);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { x[i] *= s; gl[i] = R(0); }
+    const R ell = tg.template eval<GRAD>(x, gl);
+    if (active) {
+        R* xw = reinterpret_cast<R*>(P.x[0]);
+        R* gw = reinterpret_cast<R*>(P.gl[0]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            if (i < d) {
+                xw[(size_t)i * P.N + n64] = x[i];
+                if (GRAD) gw[(size_t)i * P.N + n64] = gl[i];
+            }
+        }
+        P.ell[0][n64] = (double)ell;
+        P.logw[n64] = 0.0;
+    }
 }
 
 } // namespace oais

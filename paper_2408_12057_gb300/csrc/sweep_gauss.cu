@@ -1,33 +1,20 @@
-// Conjugate-Gaussian family (fp64 throughout): sweep kernel instantiations.
+// Conjugate-Gaussian family (fp64 throughout): sweep and ASMC kernel instantiations.
 #include "internal.h"
 
 namespace oais {
 
 template <int D>
-static cudaError_t go(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s)
+static GaussTarget<double, D> make_gauss(const DevTarget& t, size_t* smem)
 {
     GaussTarget<double, D> tg;
     tg.mu = static_cast<const double*>(t.X);
     tg.d = t.d;
     tg.inv_sig2 = 1.0 / (t.p0 * t.p0);
-    switch (move) {
-    case kRwmh: return launch_one<GaussTarget<double, D>, kRwmh, D, double>(tg, 0, P, s);
-    case kMala: return launch_one<GaussTarget<double, D>, kMala, D, double>(tg, 0, P, s);
-    case kHmc:  return launch_one<GaussTarget<double, D>, kHmc, D, double>(tg, 0, P, s);
-    }
-    return cudaErrorInvalidValue;
+    *smem = 0;
+    return tg;
 }
 
-cudaError_t launch_sweep_gauss(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s)
-{
-    switch (t.D) {
-    case 1: return go<1>(t, move, P, s);
-    case 2: return go<2>(t, move, P, s);
-    case 4: return go<4>(t, move, P, s);
-    case 8: return go<8>(t, move, P, s);
-    case 16: return go<16>(t, move, P, s);
-    }
-    return cudaErrorInvalidValue;
-}
+OAIS_FAMILY_DISPATCH(gauss, make_gauss, double,
+                     OAIS_WIDTH(1) OAIS_WIDTH(2) OAIS_WIDTH(4) OAIS_WIDTH(8) OAIS_WIDTH(16))
 
 } // namespace oais

@@ -150,6 +150,38 @@ struct RowsTarget {
         cp_async_commit();
     }
 
+    // X_r . x with 4 independent partial sums (shorter FMA dependency chain)
+    __device__ __forceinline__ static float row_dot(const float* xr, const float (&x)[D]) {
+        float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+        for (int i = 0; i < D; i += 4) {
+            if (D % 4 == 0) {
+                const float4 v = *reinterpret_cast<const float4*>(xr + i);
+                z0 = fmaf(v.x, x[i], z0); z1 = fmaf(v.y, x[i + 1], z1);
+                z2 = fmaf(v.z, x[i + 2], z2); z3 = fmaf(v.w, x[i + 3], z3);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) if (i + q < D) z0 = fmaf(xr[i + q], x[i + q], z0);
+            }
+        }
+        return (z0 + z1) + (z2 + z3);
+    }
+
+    // per-row term f(y, z) into `part`; returns df/dz
+    __device__ __forceinline__ float row_term(float z, float yv, float& part) const {
+        if (LOGISTIC) {
+            // softplus(z) = max(z, 0) + log(1 + e^-|z|); sigmoid from the same exponential
+            const float e = __expf(-fabsf(z));
+            const float inv = __frcp_rn(1.0f + e);
+            part = yv * z - (fmaxf(z, 0.0f) + __logf(1.0f + e));
+            return yv - (z >= 0.0f ? inv : e * inv);
+        } else {
+            const float r = yv - z;
+            part = r * r;
+            return r * inv_sig2;
+        }
+    }
+
     template <bool GRAD>
     __device__ float eval(const float (&x)[D], float (&g)[D]) const {
         float ell = 0.0f;
@@ -167,37 +199,28 @@ struct RowsTarget {
             const float* yc = ys + (c & 1) * kRows;
             int rows = n - c * kRows; rows = rows < kRows ? rows : kRows;
             float part = 0.0f;
-            for (int r = 0; r < rows; ++r) {
-                const float* xr = Xc + r * D;
-                // 4 independent partial dot products shorten the FMA dependency chain
-                float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
-#pragma unroll
-                for (int i = 0; i < D; i += 4) {
-                    if (D % 4 == 0) {
-                        const float4 v = *reinterpret_cast<const float4*>(xr + i);
-                        z0 = fmaf(v.x, x[i], z0); z1 = fmaf(v.y, x[i + 1], z1);
-                        z2 = fmaf(v.z, x[i + 2], z2); z3 = fmaf(v.w, x[i + 3], z3);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) if (i + q < D) z0 = fmaf(xr[i + q], x[i + q], z0);
-                    }
-                }
-                const float z = (z0 + z1) + (z2 + z3);
-                const float yv = yc[r];
-                float res;
-                if (LOGISTIC) {
-                    const float e = __expf(-fabsf(z));
-                    const float inv = __frcp_rn(1.0f + e);
-                    part += yv * z - (fmaxf(z, 0.0f) + __logf(1.0f + e));
-                    res = yv - (z >= 0.0f ? inv : e * inv);
-                } else {
-                    const float r_ = yv - z;
-                    part = fmaf(r_, r_, part);
-                    res = r_ * inv_sig2;
-                }
+            int r = 0;
+            // two rows per iteration: independent dot products and epilogues overlap
+            for (; r + 1 < rows; r += 2) {
+                const float* xa = Xc + r * D;
+                const float* xb = xa + D;
+                const float za = row_dot(xa, x), zb = row_dot(xb, x);
+                float pa, pb;
+                const float ra = row_term(za, yc[r], pa), rb = row_term(zb, yc[r + 1], pb);
+                part += pa + pb;
                 if (GRAD) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) g[i] = fmaf(res, xr[i], g[i]);
+                    for (int i = 0; i < D; ++i) g[i] = fmaf(ra, xa[i], fmaf(rb, xb[i], g[i]));
+                }
+            }
+            if (r < rows) {
+                const float* xa = Xc + r * D;
+                float pa;
+                const float ra = row_term(row_dot(xa, x), yc[r], pa);
+                part += pa;
+                if (GRAD) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) g[i] = fmaf(ra, xa[i], g[i]);
                 }
             }
             ell += part;

@@ -66,6 +66,9 @@ def lib():
                 "oais_workspace_bytes": ([P, P, i64, i32, P], i32),
                 "oais_init": ([P, P, P, i64, P, i32, i32, P, u64, P, sz, P], i32),
                 "oais_round": ([P, i32, P], i32),
+                "oasmc_round": ([P, i32, f64, P], i32),
+                "oais_get_resampling": ([P, P, P, P], i32),
+                "asmc_run": ([P, P, i64, P, i32, P, f64, u64, P, P, P, P, P], i32),
                 "oais_logZ": ([P, P, P], i32),
                 "oais_get_stats": ([P, P, P, P, P, P], i32),
                 "oais_get_schedule": ([P, P, P, P], i32),
@@ -194,6 +197,21 @@ class OAIS:
         r = _RoundResult()
         _check(lib().oais_round(self._ctx, int(T_next), ctypes.byref(r)), self._ctx)
         return {f: getattr(r, f) for f, _ in _RoundResult._fields_ if f != "pad"}
+
+    def asmc_round(self, ess_frac=0.5, T_next=None):
+        """One optimised-ASMC round with adaptive resampling (ESS < ess_frac * N)."""
+        if T_next is None:
+            T_next = self.schedule()[0].size - 1
+        r = _RoundResult()
+        _check(lib().oasmc_round(self._ctx, int(T_next), float(ess_frac), ctypes.byref(r)), self._ctx)
+        return {f: getattr(r, f) for f, _ in _RoundResult._fields_ if f != "pad"}
+
+    def resampling(self):
+        """(ess [T], resampled [T], ancestors of the last event [N]) of the last ASMC round."""
+        T = self.stats()["D_hat"].size
+        ess, rs, anc = np.zeros(T), np.zeros(T, dtype=np.int32), np.zeros(self.N, dtype=np.int64)
+        _check(lib().oais_get_resampling(self._ctx, _np_ptr(ess), _np_ptr(rs), _np_ptr(anc)), self._ctx)
+        return ess, rs, anc
 
     def logZ(self):
         z, s = ctypes.c_double(), ctypes.c_double()

@@ -1,0 +1,115 @@
+"""ASMC with adaptive resampling on the GPU (Alg. 1 with the ESS trigger, systematic
+resampling through an fp64 prefix scan) against the FP64 oracle.
+
+On the fp64 family both sides make the same MH decisions and compute the same
+resampling ancestors (a threshold (n+U)/N would have to fall within rounding of a
+cumulative weight C_m to differ), so whole runs agree element by element.  For the
+fp32 families a single near-tie MH decision changes one weight and with it the
+ancestors of later events, so those are checked through invariants and against
+the known normalising constant instead.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2408_12057_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+oais = pytest.importorskip("paper_2408_12057_gb300.oais")
+
+
+def _tg(pr):
+    return o.Target(pr.kind, pr.X, pr.y, pr.ref_scale, pr.p0)
+
+
+def gpu_asmc(pr, move, N, beta, eps, seed, ess_frac, **kw):
+    r = oais.OAIS(pr, move, N, beta, eps=eps, seed=seed, **kw)
+    res = r.asmc_round(ess_frac, len(beta) - 1)
+    logw, ell, x = r.particles()
+    ess, rs, anc = r.resampling()
+    out = dict(res=res, logw=logw.cpu().numpy().copy(), ell=ell.cpu().numpy().copy(),
+               x=x.cpu().numpy().T.astype(np.float64).copy(), ess=ess, resampled=rs, anc=anc,
+               **r.stats())
+    r.close()
+    return out
+
+
+@pytest.mark.parametrize("ess_frac,N,T", [(0.5, 500, 30), (1.0, 257, 12), (0.0, 300, 10), (0.9, 1000, 40)])
+def test_gauss_asmc_matches_oracle(ess_frac, N, T):
+    pr = W.gauss_conj()
+    beta = W.linear_schedule(T) ** 2
+    eps = 0.5 / np.sqrt(8)
+    g = gpu_asmc(pr, oais.RWMH, N, beta, eps, 21, ess_frac, moves=2)
+    r = o.asmc(_tg(pr), o.RWMH, N, beta, eps, 21, moves=2, ess_frac=ess_frac)
+    assert np.all(r["margin"] > 1e-7), "pick a seed without near-tie decisions"
+    assert g["res"]["n_resample"] == r["n_resample"]
+    np.testing.assert_array_equal(g["resampled"], r["resampled"])
+    np.testing.assert_allclose(g["ess"], r["ess"], rtol=1e-9)
+    assert g["res"]["logZ"] == pytest.approx(r["logZ"], rel=1e-10, abs=1e-10)
+    np.testing.assert_allclose(g["logw"], r["logw"], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(g["ell"], r["ell"], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(g["x"], r["x"], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(g["log_ghat"], r["log_ghat"], rtol=1e-9, atol=1e-6)
+    if ess_frac >= 1.0:
+        assert r["n_resample"] == T - 1
+
+
+def test_systematic_ancestors_match_oracle_large():
+    # one resampling event at t = 1 over N = 1.1M particles (more than 1024 scan blocks):
+    # log w_{1^-} = (beta_1 - beta_0) log L(X_0), ancestors vs the oracle's systematic resampling
+    pr = W.gauss_conj(d=1, seed=6)
+    N = 1_100_000
+    beta = np.array([0.0, 0.3, 1.0])
+    g = gpu_asmc(pr, oais.RWMH, N, beta, 0.3, 5, 1.0)
+    assert g["resampled"][0] == 1 and g["res"]["n_resample"] == 1
+    # the oracle's one-step run to beta_1 (same counters) gives log w_{1^-} of every particle
+    r1 = o.asmc(_tg(pr), o.RWMH, N, beta[:2], 0.3, 5)
+    logw1 = r1["logw"]
+    anc = o.systematic_resample(logw1, o.resample_uniform(5, 1, 0))
+    diff = np.flatnonzero(anc != g["anc"])
+    if diff.size:
+        # allowed only where a threshold sits within rounding of a cumulative weight
+        W_ = np.exp(logw1 - o.logsumexp(logw1))
+        C = np.cumsum(W_)
+        U = o.resample_uniform(5, 1, 0)
+        thr = (diff + U) / N
+        gap = np.min(np.abs(C[np.minimum(anc[diff], N - 1)][:, None] - thr[:, None]), axis=1)
+        assert np.all(gap < 1e-12), diff[:10]
+    assert diff.size <= 2
+
+
+def test_gmm_asmc_full_size_invariants():
+    # mixture workload at full size, N = 2^20, T = 1024, 2 RWMH moves, nu = 1/2
+    pr = W.gmm()
+    N, T = 1 << 20, 1024
+    beta = W.linear_schedule(T) ** 3
+    g = gpu_asmc(pr, oais.RWMH, N, beta, 1.0, 12057, 0.5, moves=2, cycle=True)
+    ess, rs = g["ess"], g["resampled"].astype(bool)
+    assert g["res"]["n_resample"] == int(rs[:-1].sum()) and rs[-1]
+    assert g["res"]["n_resample"] > 0
+    assert np.all((ess >= 1 - 1e-9) & (ess <= N * (1 + 1e-12)))
+    assert np.all(ess[:-1][rs[:-1]] < 0.5 * N) and np.all(ess[:-1][~rs[:-1]] >= 0.5 * N)
+    # after a resampling event the weights restart at 1: the next step's g_hat_0 is log N
+    ev = np.flatnonzero(rs[:-1])
+    np.testing.assert_allclose(g["log_ghat"][ev + 1, 0], np.log(N), rtol=1e-13)
+    # reading of the mixture target: L = p / eta with p normalised, so log Z = 0
+    assert abs(g["res"]["logZ"]) < 5 * max(g["res"]["se"], 0.01)
+
+
+def test_logistic_asmc_logZ_agrees_with_oais():
+    # the same target through OAIS and through ASMC: both estimate the same log Z
+    pr = W.logistic(n=200, d=8, seed=2)
+    N, T = 1 << 14, 128
+    beta = W.linear_schedule(T) ** 4
+    eps = oais.default_step_sizes(pr, beta, oais.MALA)
+    zs_a, zs_o = [], []
+    for rep in range(3):
+        zs_a.append(gpu_asmc(pr, oais.MALA, N, beta, eps, 100 + rep, 0.5)["res"]["logZ"])
+        r = oais.OAIS(pr, oais.MALA, N, beta, eps=eps, seed=200 + rep)
+        zs_o.append(r.round(T)["logZ"])
+        r.close()
+    zs_a, zs_o = np.array(zs_a), np.array(zs_o)
+    spread = max(zs_a.std(ddof=1), zs_o.std(ddof=1), 0.02)
+    assert abs(zs_a.mean() - zs_o.mean()) < 5 * spread

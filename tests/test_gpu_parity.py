@@ -5,8 +5,9 @@ Per particle the CUDA path and the oracle run the same algorithm on the same
 random numbers, so final log-weights, log-likelihoods and states agree element by
 element.  A Metropolis-Hastings decision whose margin |log u - log alpha| (oracle)
 is within the CUDA path's rounding of log alpha may legitimately go either way
-and then the trajectories separate; such particles are excluded from the
-element-wise comparison (both outcomes are valid draws) and counted.
+and then the trajectories separate.  So: every particle that disagrees must have
+such a near-tie decision in its history (both outcomes are valid draws), and
+nearly all particles must agree.
 
 Tolerances (relative, plus a small absolute floor), derived from the arithmetic:
   fp64 family (conjugate Gaussian): both sides are fp64; the only differences are
@@ -14,7 +15,10 @@ Tolerances (relative, plus a small absolute floor), derived from the arithmetic:
   fp32 families: the kernel keeps states and log L in fp32 (unit roundoff 6e-8)
     and log-weights in fp64; a log L over n rows accumulates about sqrt(n) * 6e-8
     relative error, so log L and log w agree to 1e-5 relative (the single-step
-    bar), and states, which carry T*K rounded updates, to 1e-4.
+    bar), and states, which carry T*K rounded updates, to 1e-4.  The moments
+    log g_hat_{t,i} = LSE_n(log w + i log g) inherit the log-weight tolerance.
+  near tie: |log u - log alpha| below 1e-3 (fp32; log alpha carries the fp32
+    error of log L differences) or 1e-7 (fp64).
 """
 import numpy as np
 import pytest
@@ -44,8 +48,25 @@ def run_gpu(pr, move, N, beta, eps, seed, **kw):
 
 def tolerances(pr):
     if pr.kind == W.GAUSS:
-        return dict(rel=1e-9, abs=1e-9, xrel=1e-9, margin=1e-7, ghat=1e-6)
-    return dict(rel=1e-5, abs=1e-4, xrel=1e-4, margin=2e-3, ghat=2e-4)
+        return dict(rel=1e-9, abs=1e-9, xrel=1e-9, tie=1e-7, ghat_rel=1e-9, ghat_abs=1e-6)
+    return dict(rel=1e-5, abs=1e-4, xrel=1e-4, tie=1e-3, ghat_rel=1e-5, ghat_abs=1e-4)
+
+
+def close(a, b, rtol, atol):
+    return np.abs(a - b) <= atol + rtol * np.abs(b)
+
+
+def particle_agreement(pr, g_logw, g_ell, g_x, r_logw, r_ell, r_x, r_margin):
+    """Per particle: True if the CUDA path and the oracle agree on (log w, log L, x)."""
+    tol = tolerances(pr)
+    ok = (close(g_logw, r_logw, tol["rel"], tol["abs"]) & close(g_ell, r_ell, tol["rel"], tol["abs"])
+          & np.all(close(g_x, r_x, tol["xrel"], tol["xrel"]), axis=-1))
+    # a disagreement must come from a near-tie Metropolis-Hastings decision
+    unexplained = ~ok & (r_margin > tol["tie"])
+    assert not unexplained.any(), (
+        f"{int(unexplained.sum())} particles disagree without a near-tie decision; first at "
+        f"{np.flatnonzero(unexplained)[:5]}: logw {g_logw[unexplained][:3]} vs {r_logw[unexplained][:3]}")
+    return ok
 
 
 def compare(pr, move, N, beta, eps, seed, min_frac=0.9, **kw):
@@ -53,18 +74,18 @@ def compare(pr, move, N, beta, eps, seed, min_frac=0.9, **kw):
     okw = {k: v for k, v in kw.items() if k in ("moves", "leapfrog", "cycle")}
     r = o.asmc(_tg(pr), move, N, beta, eps, seed, tag=0, **okw)
     tol = tolerances(pr)
-    clean = r["margin"] > tol["margin"]
-    assert clean.mean() >= min_frac, f"too many near-tie MH decisions: {clean.mean()}"
-    c = clean
-    np.testing.assert_allclose(g["logw"][c], r["logw"][c], rtol=tol["rel"], atol=tol["abs"])
-    np.testing.assert_allclose(g["ell"][c], r["ell"][c], rtol=tol["rel"], atol=tol["abs"])
-    np.testing.assert_allclose(g["x"][c], r["x"][c], rtol=tol["xrel"], atol=tol["xrel"])
-    if clean.all():
+    ok = particle_agreement(pr, g["logw"], g["ell"], g["x"], r["logw"], r["ell"], r["x"], r["margin"])
+    assert ok.mean() >= min_frac, f"only {ok.mean():.3f} of particles agree"
+    if ok.all():
         # with every decision shared, the per-step moments and acceptance agree too
-        np.testing.assert_allclose(g["log_ghat"], r["log_ghat"], rtol=1e-9, atol=tol["ghat"])
+        np.testing.assert_allclose(g["log_ghat"], r["log_ghat"], rtol=tol["ghat_rel"], atol=tol["ghat_abs"])
         np.testing.assert_allclose(g["accept"], r["accept"], rtol=0, atol=1e-12)
         assert g["res"]["logZ"] == pytest.approx(r["logZ"], rel=tol["rel"], abs=tol["abs"])
-    return g, r, clean
+        # the barrier estimate, a difference of the three moments
+        _, Dg, Lg = oais.optimise_schedule(g["beta"], g["log_ghat"], 4)
+        _, Do, Lo = o.optimise_schedule(np.asarray(beta, dtype=float), r["log_ghat"], 4)
+        assert Lg[-1] == pytest.approx(Lo[-1], rel=1e-3 if pr.kind != W.GAUSS else 1e-6)
+    return g, r, ok
 
 
 def test_gauss_rwmh_workload1_full_size():
@@ -133,8 +154,7 @@ def test_one_step_schedule_is_importance_sampling_full_size():
     assert g["log_ghat"][0, 2] == pytest.approx(torch.logsumexp(2 * lw, 0).item(), rel=1e-12)
     assert g["res"]["logZ"] == pytest.approx(torch.logsumexp(lw, 0).item() - np.log(N), rel=1e-12)
     # sampled particles against the oracle (counter n_offset + n)
-    idx = [0, 1, 4097, N // 2 + 3, N - 1]
-    for n in idx:
+    for n in [0, 1, 4097, N // 2 + 3, N - 1]:
         r = o.asmc(_tg(pr), o.MALA, 1, [0.0, 1.0], 0.01, seed=77, n_offset=n)
         assert g["logw"][n] == pytest.approx(r["logw"][0], rel=1e-5)
 
@@ -153,18 +173,12 @@ def test_logistic_full_size_sampled():
     assert g["res"]["logZ"] == pytest.approx(
         torch.logsumexp(torch.from_numpy(g["logw"]), 0).item() - np.log(N), rel=1e-12)
     rng = np.random.default_rng(0)
-    idx = np.concatenate([[0, 127, 128, N - 1], rng.integers(0, N, 8)])
-    tol = tolerances(pr)
-    agree = 0
-    for n in idx:
-        r = o.asmc(_tg(pr), o.MALA, 1, beta, eps, seed=12057, n_offset=int(n))
-        if r["margin"][0] <= tol["margin"]:
-            continue
-        agree += 1
-        assert g["logw"][n] == pytest.approx(r["logw"][0], rel=tol["rel"], abs=tol["abs"])
-        assert g["ell"][n] == pytest.approx(r["ell"][0], rel=tol["rel"], abs=tol["abs"])
-        np.testing.assert_allclose(g["x"][n], r["x"][0], rtol=tol["xrel"], atol=tol["xrel"])
-    assert agree >= len(idx) - 2
+    idx = np.concatenate([[0, 127, 128, N - 1], rng.integers(0, N, 12)])
+    rs = [o.asmc(_tg(pr), o.MALA, 1, beta, eps, seed=12057, n_offset=int(n)) for n in idx]
+    ok = particle_agreement(pr, g["logw"][idx], g["ell"][idx], g["x"][idx],
+                            np.array([r["logw"][0] for r in rs]), np.array([r["ell"][0] for r in rs]),
+                            np.stack([r["x"][0] for r in rs]), np.array([r["margin"][0] for r in rs]))
+    assert ok.mean() >= 0.75
 
 
 def test_gmm_full_size_sampled():
@@ -176,17 +190,13 @@ def test_gmm_full_size_sampled():
     assert g["log_ghat"][0, 0] == pytest.approx(np.log(N), rel=1e-14)
     # reading: L = p / eta with p normalised, Z = 1
     assert abs(g["res"]["logZ"]) < 5 * max(g["res"]["se"], 0.01)
-    tol = tolerances(pr)
-    agree = 0
-    idx = [0, 1, N // 3, N - 1, 777777]
-    for n in idx:
-        r = o.asmc(_tg(pr), o.RWMH, 1, beta, 1.0, seed=12057, moves=2, cycle=True, n_offset=n)
-        if r["margin"][0] <= tol["margin"]:
-            continue
-        agree += 1
-        assert g["logw"][n] == pytest.approx(r["logw"][0], rel=tol["rel"], abs=tol["abs"])
-        np.testing.assert_allclose(g["x"][n], r["x"][0], rtol=tol["xrel"], atol=tol["xrel"])
-    assert agree >= len(idx) - 1
+    idx = np.array([0, 1, 127, 128, N // 3, N - 1, 777777, 5, 999, 65536])
+    rs = [o.asmc(_tg(pr), o.RWMH, 1, beta, 1.0, seed=12057, moves=2, cycle=True, n_offset=int(n))
+          for n in idx]
+    ok = particle_agreement(pr, g["logw"][idx], g["ell"][idx], g["x"][idx],
+                            np.array([r["logw"][0] for r in rs]), np.array([r["ell"][0] for r in rs]),
+                            np.stack([r["x"][0] for r in rs]), np.array([r["margin"][0] for r in rs]))
+    assert ok.mean() >= 0.7
 
 
 def test_logsumexp_kernel_matches_torch():
