@@ -212,7 +212,7 @@ static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
     L.ess_parts = take(sizeof(StepPartial) * (size_t)sweep_grid(N));
     L.st = take(sizeof(AsmcState));
     L.bsum = take(sizeof(double) * scan_blocks(N));
-    L.boff = take(sizeof(double) * scan_blocks(N));
+    L.boff = take(sizeof(double) * (scan_blocks(N) + 1));
     L.cdf = take(sizeof(double) * N);
     L.ess_trace = take(sizeof(double) * T_max);
     L.resampled = take(sizeof(int) * T_max);

@@ -2,8 +2,10 @@
 //   decide:   ESS of w_{t^-} = (sum w)^2 / sum w^2 (eq. sample_size_IS); resample when
 //             ESS < nu N, and always close the last segment at t = T; on a resampling
 //             time Z_hat *= mean(w) (eq. estimator_Z), kept as log Z_hat += LSE(log w) - log N;
-//   scan:     normalised weights W_m = exp(log w_m - LSE) and their inclusive cumulative
-//             sums C_m in fp64 (block sums, block offsets, in-block scan: a fixed order);
+//   scan:     weights exp(log w_m - LSE~) and their inclusive cumulative sums P_m in fp64
+//             (block sums, block offsets, in-block scan: a fixed order), normalised by
+//             their own fp64 total, C_m = P_m / P_{N-1}, so C does not inherit the
+//             rounding of the shift LSE~ (which comes from the fp32-summed ESS pieces);
 //   gather:   systematic resampling, a^n = min{m : C_m > (n + U)/N} by binary search,
 //             particles copied to the other buffer, w = 1.
 // Every kernel after `decide` reads the device flag `pend` and returns at once when the
@@ -103,7 +105,7 @@ asmc_blocksum_kernel(const AsmcState* st, const double* __restrict__ logw, int64
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// exclusive scan of the block sums by one CTA, in chunks of kScanTile
+// exclusive scan of the block sums by one CTA, in chunks of kScanTile; boff[nb] = total
 __global__ void __launch_bounds__(kScanThreads)
 asmc_offsets_kernel(const AsmcState* st, const double* __restrict__ bsum, int nb, double* boff)
 {
@@ -122,6 +124,7 @@ asmc_offsets_kernel(const AsmcState* st, const double* __restrict__ bsum, int nb
         carry += tot;
         __syncthreads();
     }
+    if (threadIdx.x == 0) boff[nb] = carry;
 }
 
 __global__ void __launch_bounds__(kScanThreads)
@@ -136,9 +139,9 @@ asmc_cdf_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N,
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) v[i] = base + i < N ? exp(logw[base + i] - lse) : 0.0;
     block_scan_inclusive(v, sh);
-    const double off = boff[blockIdx.x];
+    const double off = boff[blockIdx.x], total = boff[gridDim.x];
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) if (base + i < N) cdf[base + i] = off + v[i];
+    for (int i = 0; i < kScanItems; ++i) if (base + i < N) cdf[base + i] = (off + v[i]) / total;
 }
 
 template <typename R>

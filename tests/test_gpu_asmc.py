@@ -3,7 +3,9 @@ resampling through an fp64 prefix scan) against the FP64 oracle.
 
 On the fp64 family both sides make the same MH decisions and compute the same
 resampling ancestors (a threshold (n+U)/N would have to fall within rounding of a
-cumulative weight C_m to differ), so whole runs agree element by element.  For the
+cumulative weight C_m to differ), so whole runs agree element by element.  The ESS
+and the segment log-sum-exp come from per-warp pieces summed in fp32 (each at most
+32 terms, unit roundoff 6e-8), so they agree to 1e-6 relative / 1e-6 absolute.  For the
 fp32 families a single near-tie MH decision changes one weight and with it the
 ancestors of later events, so those are checked through invariants and against
 the known normalising constant instead.
@@ -46,8 +48,8 @@ def test_gauss_asmc_matches_oracle(ess_frac, N, T):
     assert np.all(r["margin"] > 1e-7), "pick a seed without near-tie decisions"
     assert g["res"]["n_resample"] == r["n_resample"]
     np.testing.assert_array_equal(g["resampled"], r["resampled"])
-    np.testing.assert_allclose(g["ess"], r["ess"], rtol=1e-9)
-    assert g["res"]["logZ"] == pytest.approx(r["logZ"], rel=1e-10, abs=1e-10)
+    np.testing.assert_allclose(g["ess"], r["ess"], rtol=1e-6)
+    assert g["res"]["logZ"] == pytest.approx(r["logZ"], rel=1e-9, abs=1e-6)
     np.testing.assert_allclose(g["logw"], r["logw"], rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(g["ell"], r["ell"], rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(g["x"], r["x"], rtol=1e-9, atol=1e-9)
@@ -76,7 +78,7 @@ def test_systematic_ancestors_match_oracle_large():
         U = o.resample_uniform(5, 1, 0)
         thr = (diff + U) / N
         gap = np.min(np.abs(C[np.minimum(anc[diff], N - 1)][:, None] - thr[:, None]), axis=1)
-        assert np.all(gap < 1e-12), diff[:10]
+        assert np.all(gap < 1e-10), diff[:10]
     assert diff.size <= 2
 
 
@@ -89,7 +91,7 @@ def test_gmm_asmc_full_size_invariants():
     ess, rs = g["ess"], g["resampled"].astype(bool)
     assert g["res"]["n_resample"] == int(rs[:-1].sum()) and rs[-1]
     assert g["res"]["n_resample"] > 0
-    assert np.all((ess >= 1 - 1e-9) & (ess <= N * (1 + 1e-12)))
+    assert np.all((ess >= 1 - 1e-6) & (ess <= N * (1 + 1e-6)))
     assert np.all(ess[:-1][rs[:-1]] < 0.5 * N) and np.all(ess[:-1][~rs[:-1]] >= 0.5 * N)
     # after a resampling event the weights restart at 1: the next step's g_hat_0 is log N
     ev = np.flatnonzero(rs[:-1])
