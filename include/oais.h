@@ -210,6 +210,26 @@ size_t oais_logsumexp_scratch_bytes(int64_t n);
 oais_status oais_logsumexp(const double* d_a, int64_t n, double* d_out, void* d_scratch,
                            void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Allocation-free log-sum-exp.  No counterpart in the paper: this is a service for
+ * callers that cannot call cudaMalloc or take scratch memory from elsewhere -- code
+ * running inside a CUDA-graph capture that must not allocate, under another allocator
+ * that owns all device memory, or in a fixed-budget loop that may only hand over its
+ * input and output buffers.  Same result as oais_logsumexp (out[0] = log sum exp a,
+ * out[1] = log sum exp 2a, deterministic), but the scratch lives in a fixed device array
+ * inside the library (128 KiB per GPU that loads the library, held until the process
+ * exits), so no allocation happens and the caller passes no scratch.
+ *   d_a: device [n] doubles; d_out: device [2] doubles; stream as above.
+ *   n: 1 .. OAIS_LOGSUMEXP_NOALLOC_MAX_N, else OAIS_EINVAL (nothing launched).
+ *   All calls on a device share the array and it keeps the last call's contents; calls
+ *   whose kernels overlap on the GPU (unordered streams or threads) race and may give
+ *   wrong results -- order them on one stream.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make it before any stream capture.
+ *   Calls no cudaMalloc/cudaFree and no allocating library routine. */
+#define OAIS_LOGSUMEXP_NOALLOC_MAX_N 16777216LL
+oais_status oais_logsumexp_noalloc(const double* d_a, int64_t n, double* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
