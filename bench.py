@@ -32,6 +32,8 @@ SE_TARGET = 0.01
 WORKLOAD = "logreg_n2000_d32_N65536_T256-512-1024-2048_mala"
 METRIC = "particle-steps/s"
 FP32_LANES_PER_SM, N_SM = 128, 152
+MUFU_PER_SM_CLK = 16            # special-function results per SM per clock
+MUFU_OPS_PER_ELEMENT = 3        # softplus and sigmoid of z need exp, log and a reciprocal
 
 
 def parse():
@@ -45,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--rounds", default=None,
                     help="comma-separated T per round (profiling a smaller case); default 256,512,1024,2048")
+    ap.add_argument("--contraction", default="fp32", choices=["fp32", "bf16_tc"],
+                    help="X x on CUDA cores in fp32, or on the tcgen05 tensor cores with X rounded to bf16")
     a = ap.parse_args()
     if a.rounds:
         global ROUNDS_T
@@ -177,9 +181,13 @@ def main():
     T0 = ROUNDS_T[0]
     beta0 = np.linspace(0.0, 1.0, T0 + 1)
     eps0 = oais.default_step_sizes(pr, beta0, oais.MALA)
-    # each rank owns a disjoint block of the particle counter space (weak scaling)
+    contraction = oais.CONTRACT_BF16_TC if args.contraction == "bf16_tc" else oais.CONTRACT_FP32
+    # one sharded run: each rank owns a disjoint block of the particle counter space (weak
+    # scaling, N_PARTICLES per GPU); the round statistics are exchanged once per round
     run = oais.OAIS(pr, oais.MALA, N_PARTICLES, beta0, T_max=max(ROUNDS_T), eps=eps0,
-                    seed=12057 + rank * 7919, adapt=True, stream=stream)
+                    seed=12057, adapt=True, stream=stream, contraction=contraction)
+    if world > 1:
+        run.set_shard(rank * N_PARTICLES, world * N_PARTICLES)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def job():
@@ -187,7 +195,10 @@ def main():
         res = []
         for k, T in enumerate(ROUNDS_T):
             nxt = ROUNDS_T[min(k + 1, len(ROUNDS_T) - 1)]
-            res.append(run.round(nxt))
+            if world > 1:
+                res.append(oais.distributed_round(run, nxt, device=torch.device("cuda", local)))
+            else:
+                res.append(run.round(nxt))
         return res
 
     for _ in range(args.warmup):
@@ -218,25 +229,39 @@ def main():
     ps_per_job = N_PARTICLES * sum(ROUNDS_T)
     value = world * ps_per_job * args.steps / (total_ms / 1e3)
 
-    # roofline of the dominant kernel (the sweep): FP32 FMA-pipe bound
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 2.0 * FP32_LANES_PER_SM * N_SM * sm_max * 1e6 / 1e12     # TFLOP/s
-    flops = algorithmic_flops_per_particle_step(pr) * ps_per_job * args.steps
-    achieved = flops / (sum(sweep_ms) / 1e3) / 1e12
-    roofline = {"bound": "alu", "pipe": "fp32 fma", "achieved": achieved, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                               f"(sm_max_mhz of {peak_src} peaks)",
-                "kernel": "oais_sweep_kernel<RowsTarget<32,logistic>, MALA>",
-                "sweep_share_of_step": sum(sweep_ms) / sum(step_ms)}
+    sweep_s = sum(sweep_ms) / 1e3
+    if args.contraction == "fp32":
+        # FP32 form: the FMA pipe bounds it (4 n d FLOP per particle-step)
+        fp32_peak = 2.0 * FP32_LANES_PER_SM * N_SM * sm_max * 1e6 / 1e12     # TFLOP/s
+        achieved = algorithmic_flops_per_particle_step(pr) * ps_per_job * args.steps / sweep_s / 1e12
+        roofline = {"bound": "alu", "pipe": "fp32 fma", "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                   f"(sm_max_mhz of {peak_src} peaks)",
+                    "kernel": "oais_sweep_kernel<RowsTarget<32,logistic>, MALA>"}
+    else:
+        # tensor-core form: the contraction is on tcgen05; the per-element epilogue
+        # (exp, reciprocal per element; one log per 16) runs on the MUFU (XU) pipe
+        mufu_peak = MUFU_PER_SM_CLK * N_SM * sm_max * 1e6 / 1e12             # Tops/s
+        ops = MUFU_OPS_PER_ELEMENT * pr.n * ps_per_job * args.steps
+        achieved = ops / sweep_s / 1e12
+        roofline = {"bound": "alu", "pipe": "mufu (xu)", "achieved": achieved, "peak": mufu_peak,
+                    "unit": "Tops/s", "frac": achieved / mufu_peak, "traffic": None,
+                    "peak_source": f"152 SMs x 16 MUFU results/clk x {sm_max:.0f} MHz "
+                                   f"(sm_max_mhz of {peak_src} peaks)",
+                    "kernel": "oais_sweep_tc_kernel (tcgen05 bf16, MALA)",
+                    "tensor_tflops_issued": 2 * algorithmic_flops_per_particle_step(pr) * 2048 / pr.n
+                                            * ps_per_job * args.steps / sweep_s / 1e12}
+    roofline["sweep_share_of_step"] = sum(sweep_ms) / sum(step_ms)
 
     se_last = last[-1]["se"]
     sec_to_se = (total_ms / 1e3 / args.steps) * (se_last / SE_TARGET) ** 2
 
     e2e = None
     if not args.no_e2e and rank == 0:
-        e2e = measure_e2e(pr, eps0, beta0, args.steps)
+        e2e = measure_e2e(pr, eps0, beta0, args.steps, contraction)
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -246,10 +271,11 @@ def main():
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if args.contraction == "bf16_tc" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N_per_gpu": N_PARTICLES, "T_rounds": ROUNDS_T,
                        "move": "MALA", "l2": "flushed between timed steps (256 MiB write)",
-                       "log_weights": "f64"},
+                       "log_weights": "f64", "contraction": args.contraction},
             "logZ_last_round": last[-1]["logZ"], "se_last_round": se_last,
             "sec_to_logZ_se_0.01": sec_to_se,
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cb,
@@ -261,7 +287,7 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def measure_e2e(pr, eps0, beta0, steps):
+def measure_e2e(pr, eps0, beta0, steps, contraction):
     """Same job through the public API with host inputs: init from host X, y (copied to the
     device inside the timed region), 4 rounds, results read back to the host every round."""
     import torch
@@ -270,7 +296,7 @@ def measure_e2e(pr, eps0, beta0, steps):
     t0 = time.perf_counter()
     for _ in range(steps):
         run = oais.OAIS(pr, oais.MALA, N_PARTICLES, beta0, T_max=max(ROUNDS_T), eps=eps0, seed=99,
-                        adapt=True, data_on_device=False)
+                        adapt=True, data_on_device=False, contraction=contraction)
         for k, T in enumerate(ROUNDS_T):
             run.round(ROUNDS_T[min(k + 1, len(ROUNDS_T) - 1)])
         run.logZ()

@@ -64,7 +64,15 @@ typedef struct {
     double p0;          /* GAUSS: likelihood sigma; GMM: component variance; LINREG: noise sigma */
     int32_t on_device;  /* 0: X, y are host memory, copied at init.  1: device memory, also copied
                            (to the padded device layout); the caller may free them after init */
+    int32_t contraction;/* how X x is computed: OAIS_CONTRACT_FP32 (CUDA cores, fp32 data) or
+                           OAIS_CONTRACT_BF16_TC (tcgen05 tensor cores; X is rounded once to
+                           bf16 and the sampler targets that X~; states and residuals are split
+                           into two bf16 terms so products keep fp32 accuracy).  The tensor-core
+                           form is built for LOGREG with d <= 32, n <= 2048 and MALA moves in
+                           oais_round; other combinations return OAIS_EUNSUPPORTED at init. */
 } oais_target;
+
+typedef enum { OAIS_CONTRACT_FP32 = 0, OAIS_CONTRACT_BF16_TC = 1 } oais_contraction;
 
 typedef enum { OAIS_RWMH = 0, OAIS_MALA = 1, OAIS_HMC = 2 } oais_move_kind;
 
@@ -141,6 +149,34 @@ oais_status asmc_run(const oais_target* target, const oais_move* move, int64_t N
                      int32_t T, const double* eps, double ess_frac, uint64_t seed, void* stream,
                      oais_round_result* out, double* log_ghat, double* ess_trace, int32_t* resampled);
 
+/* Sharding across processes (OAIS particles are independent within a round, Sec. 5.1.2):
+ * this context's N particles are [n_offset, n_offset + N) of a run of N_total; particle n
+ * draws from counter n, so the union of the shards is the same sample as one context with
+ * N_total particles.  A round is then split in two:
+ *   oais_round_local:  the sweep of this shard and its reductions; returns host arrays
+ *     log_ghat [T][3] (log g_hat_{t,i} over this shard), accepted [T] (accepted-move counts)
+ *     and lse [2] (log sum w_T, log sum w_T^2 over this shard), T in *T.
+ *   oais_round_commit: takes the statistics merged over all shards -- log_ghat and lse by
+ *     log-sum-exp over shards, accepted by summing -- forms log Z_hat = lse[0] - log N_total,
+ *     ESS and SE, and installs OptimiseSchedule(T_next, ...) exactly as oais_round does.
+ * The exchange itself (an all-gather of 4T + 2 doubles per shard) is the caller's.
+ * ASMC resamples across all particles and is not sharded (oasmc_round returns
+ * EUNSUPPORTED on a shard); oais_round returns EINVAL on a shard. */
+oais_status oais_set_shard(oais_ctx* ctx, int64_t n_offset, int64_t N_total);
+oais_status oais_round_local(oais_ctx* ctx, double* log_ghat, double* accepted, double* lse, int32_t* T);
+oais_status oais_round_commit(oais_ctx* ctx, int32_t T_next, const double* log_ghat, const double* accepted,
+                              const double* lse, oais_round_result* out);
+
+/* Checkpoint / resume between rounds.  The state of Alg. 2 between rounds is the round
+ * counter, the next schedule and its step sizes, the seed and the shard; the particles are
+ * redrawn every round, and the counter-based random numbers make a resumed round
+ * bit-identical to an uninterrupted one.  oais_state_bytes gives the size of the blob;
+ * oais_save_state writes it into host memory; oais_load_state restores it into a context
+ * created for the same target, move and N (EINVAL otherwise, the context unchanged). */
+oais_status oais_state_bytes(const oais_ctx* ctx, size_t* bytes);
+oais_status oais_save_state(const oais_ctx* ctx, void* buf, size_t bytes);
+oais_status oais_load_state(oais_ctx* ctx, const void* buf, size_t bytes);
+
 /* log Z_hat and its delta-method SE from the last completed round. EINVAL if none. */
 oais_status oais_logZ(const oais_ctx* ctx, double* logZ, double* se);
 
@@ -163,6 +199,23 @@ oais_status oais_set_schedule(oais_ctx* ctx, const double* beta, const double* e
  * Device pointers of the context's workspace, valid until the next round or oais_destroy. */
 oais_status oais_particles(const oais_ctx* ctx, const double** logw, const double** ell,
                            const void** x);
+
+/* Fisher-identity gradient of log Z with respect to theta = (log s, log p0):
+ * grad_theta log Z = E_pi[grad_theta log gamma(x; theta)] (not in the paper; the weighted
+ * expectation estimator of eq. estimator_pi_t with the final weights and states of the last
+ * round).  grad[0] = sum_n W_n (|x_n|^2 / s^2 - d)  (reference scale s),
+ * grad[1] = sum_n W_n d log L(x_n)/d log p0 for the Gaussian (-2 log L) and linear-regression
+ * (-n - 2 log L - n log(2 pi p0^2)) families, NaN for the others.  grad: host [2].
+ * A ratio estimator: consistent, biased at finite N.  Synchronises the context's stream. */
+oais_status oais_grad_logZ(oais_ctx* ctx, double* grad);
+
+/* The target's potential for a batch of states (the forward and backward of the likelihood
+ * used inside MALA and HMC): ell[n] = log L(x_n) and, if d_grad != NULL,
+ * grad[i][n] = d log L / d x_i at x_n.  d_x, d_grad: device [d][N] in the family's precision
+ * (double for GAUSS, float otherwise); d_ell: device [N] doubles.  Ordered on `stream`.
+ * For the tensor-core contraction this uses the fp32 CUDA-core evaluation of X. */
+oais_status oais_potential(oais_ctx* ctx, const void* d_x, int64_t N, double* d_ell, void* d_grad,
+                           void* stream);
 
 void oais_destroy(oais_ctx* ctx);
 const char* oais_last_error(const oais_ctx* ctx);

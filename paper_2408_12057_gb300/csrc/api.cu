@@ -15,7 +15,14 @@ cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts,
                                  bool grad, bool fp64, double* bsum, double* boff, double* cdf,
                                  double* ess_trace, int* resampled, int64_t* ancestors, cudaStream_t s);
 int scan_blocks(int64_t N);
+int tc_image_bytes();
+int tc_max_rows();
+void tc_prepare_logreg(const float* X, const float* y, int n, int d, std::vector<uint16_t>& img,
+                       std::vector<uint32_t>& ybits);
 cudaError_t launch_merge_stats(const StepPartial*, int, int, double, double*, double*, cudaStream_t);
+cudaError_t launch_fisher(const double* logw, const double* ell, const void* x, bool fp64, int64_t N, int d,
+                          const double* lse, double ref_scale, int kind, int nrows, double p0, void* scratch,
+                          double* out, cudaStream_t s);
 cudaError_t launch_logsumexp(const double*, int64_t, double*, void*, cudaStream_t);
 size_t logsumexp_scratch_bytes(int64_t n);
 
@@ -139,6 +146,12 @@ struct oais_ctx {
     int64_t* d_anc = nullptr;
     bool last_asmc = false;
     int l_n_resample = 0;
+    // sharding: this context's particles are [n_offset, n_offset + N) of N_total
+    int64_t n_offset = 0, N_total = 0;
+    int pend_T = 0;                      // > 0 after oais_round_local, until the commit
+    float pend_ms = 0.0f;
+    std::vector<double> pend_lg, pend_acc;
+    double pend_lse[2] = {0.0, 0.0};
     std::vector<double> l_ess_trace;
     std::vector<int> l_resampled;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -178,8 +191,10 @@ static size_t elt_bytes(int kind) { return kind == kGauss ? sizeof(double) : siz
 
 struct Layout {
     size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, lse, lse_scr, status;
-    size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, total;
+    size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, tc_img, tc_y, total;
 };
+
+static int records_per_step(int64_t N) { return std::max(sweep_grid(N), tc_records(N)); }
 
 static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
 {
@@ -198,7 +213,7 @@ static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
     L.logw = take(sizeof(double) * N);
     L.ell = take(sizeof(double) * N);
     L.x = take(elt_bytes(tg->kind) * (size_t)tg->d * N);
-    L.parts = take(sizeof(StepPartial) * (size_t)T_max * sweep_grid(N));
+    L.parts = take(sizeof(StepPartial) * (size_t)T_max * records_per_step(N));
     L.lg = take(sizeof(double) * 3 * T_max);
     L.acc = take(sizeof(double) * T_max);
     L.lse = take(sizeof(double) * 2);
@@ -217,6 +232,9 @@ static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
     L.ess_trace = take(sizeof(double) * T_max);
     L.resampled = take(sizeof(int) * T_max);
     L.anc = take(sizeof(int64_t) * N);
+    const bool tc = tg->contraction == OAIS_CONTRACT_BF16_TC;
+    L.tc_img = take(tc ? (size_t)tc_image_bytes() : 0);
+    L.tc_y = take(tc ? (size_t)tc_max_rows() / 8 : 0);
     L.total = off;
     return L;
 }
@@ -233,6 +251,12 @@ static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais
     if (tg->kind == kGmm && tg->n > GmmTarget<float, 16>::kMaxK)
         return fail(ctx, OAIS_EUNSUPPORTED, "at most 16 mixture components");
     if (tg->dtype != OAIS_DT_F64 && tg->dtype != OAIS_DT_F32) return fail(ctx, OAIS_EINVAL, "bad dtype");
+    if (tg->contraction != OAIS_CONTRACT_FP32 && tg->contraction != OAIS_CONTRACT_BF16_TC)
+        return fail(ctx, OAIS_EINVAL, "bad contraction");
+    if (tg->contraction == OAIS_CONTRACT_BF16_TC &&
+        (tg->kind != kLogreg || tg->d > 32 || tg->n > tc_max_rows() || mv->kind != OAIS_MALA))
+        return fail(ctx, OAIS_EUNSUPPORTED,
+                    "the tensor-core contraction is built for LOGREG, d <= 32, n <= 2048, MALA");
     if (tg->kind == kGauss && tg->dtype != OAIS_DT_F64)
         return fail(ctx, OAIS_EINVAL, "the Gaussian family takes float64 mu");
     if (mv->kind < 0 || mv->kind > 2 || mv->moves < 1 || (mv->kind == OAIS_HMC && mv->leapfrog < 1))
@@ -318,6 +342,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     ctx->tg_in = *tg;
     ctx->mv = *mv;
     ctx->N = N;
+    ctx->N_total = N;
     ctx->T_max = T_max;
     ctx->seed = seed;
     ctx->stream = static_cast<cudaStream_t>(stream);
@@ -385,6 +410,20 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
         if (e == cudaSuccess && dt.y) {
             for (int r = 0; r < tg->n; ++r) yp[r] = (float)yh[r];
             e = cudaMemcpy(dt.y, yp.data(), sizeof(float) * yp.size(), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess && tg->contraction == OAIS_CONTRACT_BF16_TC) {
+            std::vector<float> Xf((size_t)tg->n * tg->d), yf(tg->n);
+            for (size_t i = 0; i < Xf.size(); ++i) Xf[i] = (float)Xh[i];
+            for (int r = 0; r < tg->n; ++r) yf[r] = (float)yh[r];
+            std::vector<uint16_t> img;
+            std::vector<uint32_t> yb;
+            tc_prepare_logreg(Xf.data(), yf.data(), tg->n, tg->d, img, yb);
+            dt.tc = true;
+            dt.tc_img = b + L.tc_img;
+            dt.tc_ybits = reinterpret_cast<uint32_t*>(b + L.tc_y);
+            e = cudaMemcpy(dt.tc_img, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(dt.tc_ybits, yb.data(), yb.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         }
     }
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
@@ -520,12 +559,20 @@ static cudaError_t launch_asmc(const DevTarget& dt, int move, bool init, const S
 // T_next and OptimiseSchedule(T_next, B_T, g_hat) becomes the next schedule.
 // asmc = false: AIS with the particle and time loops swapped (Sec. 5.1.2);
 // asmc = true: lock-step particles with adaptive resampling at threshold ess_frac.
-static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double ess_frac, oais_round_result* out)
+static oais_status commit_round(oais_ctx* ctx, int T, int32_t T_next, const std::vector<double>& lg,
+                                const std::vector<double>& acc, double logZ, double ess, double se, float ms,
+                                bool asmc, int n_res, const std::vector<double>& ess_tr,
+                                const std::vector<int>& rs, oais_round_result* out);
+
+static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double ess_frac, oais_round_result* out,
+                             bool local_only = false)
 {
     if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
     if (T_next < 1 || T_next > ctx->T_max) return fail(ctx, OAIS_EINVAL, "T_next out of range");
     if (asmc && !(ess_frac >= 0.0 && ess_frac <= 1.0 + 1e-12))
         return fail(ctx, OAIS_EINVAL, "ess_frac must be in [0, 1]");
+    if (ctx->N_total != ctx->N && !local_only)
+        return fail(ctx, OAIS_EINVAL, "a shard's round needs the global statistics: use oais_round_local/commit");
     const int T = (int)ctx->beta.size() - 1;
     cudaStream_t s = ctx->stream;
     CK(cudaMemcpyAsync(ctx->d_beta, ctx->beta.data(), sizeof(double) * (T + 1), cudaMemcpyHostToDevice, s));
@@ -540,13 +587,14 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
     double logZ, ess, se;
     int n_res = 0;
     if (!asmc) {
-        SweepParams P = make_params(ctx, T, ctx->d_beta, ctx->d_eps, ctx->seed, tag, 0, ctx->N, ctx->d_logw,
-                                    ctx->d_ell, ctx->d_x, ctx->d_parts, ctx->d_status);
+        SweepParams P = make_params(ctx, T, ctx->d_beta, ctx->d_eps, ctx->seed, tag, ctx->n_offset, ctx->N,
+                                    ctx->d_logw, ctx->d_ell, ctx->d_x, ctx->d_parts, ctx->d_status);
         CK(cudaEventRecord(ctx->ev0, s));
-        CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
+        if (ctx->dt.tc) CK(launch_sweep_tc(P, ctx->dt.tc_img, ctx->dt.tc_ybits, ctx->dt.n, ctx->dt.d, s));
+        else CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
         CK(cudaEventRecord(ctx->ev1, s));
-        CK(launch_merge_stats(ctx->d_parts, grid, T, 1.0 / ((double)ctx->N * ctx->mv.moves),
-                              ctx->d_log_ghat, ctx->d_accept, s));
+        CK(launch_merge_stats(ctx->d_parts, ctx->dt.tc ? tc_records(ctx->N) : grid, T,
+                              1.0 / ((double)ctx->N * ctx->mv.moves), ctx->d_log_ghat, ctx->d_accept, s));
         CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
         double lse[2];
         CK(cudaMemcpyAsync(lg.data(), ctx->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
@@ -554,10 +602,26 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         CK(cudaMemcpyAsync(lse, ctx->d_lse, sizeof(lse), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        if (local_only) {
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+            if (status & 2u) return fail(ctx, OAIS_ETIMEOUT, "a tensor-core completion wait gave up");
+            if (status & 4u) return fail(ctx, OAIS_ECUDA, "shared memory base not 1024-byte aligned");
+            if (status & 1u) return fail(ctx, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood");
+            ctx->pend_T = T;
+            ctx->pend_ms = ms;
+            ctx->pend_lg = lg;
+            ctx->pend_acc.resize(T);
+            for (int t = 0; t < T; ++t) ctx->pend_acc[t] = std::round(acc[t] * (double)ctx->N * ctx->mv.moves);
+            ctx->pend_lse[0] = lse[0];
+            ctx->pend_lse[1] = lse[1];
+            return OAIS_OK;
+        }
         logZ = lse[0] - logN;
         ess = std::exp(2.0 * lse[0] - lse[1]);
         se = std::sqrt(std::max(0.0, 1.0 / ess - 1.0 / (double)ctx->N));
     } else {
+        if (ctx->N_total != ctx->N) return fail(ctx, OAIS_EUNSUPPORTED, "ASMC resamples globally: no shards");
         CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(AsmcState), s));
         StepParams P = make_step_params(ctx, T, tag);
         const bool grad = ctx->mv.kind != OAIS_RWMH;
@@ -600,8 +664,18 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
     }
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (status & 2u) return fail(ctx, OAIS_ETIMEOUT, "a tensor-core completion wait gave up");
+    if (status & 4u) return fail(ctx, OAIS_ECUDA, "shared memory base not 1024-byte aligned");
     if (status & 1u) return fail(ctx, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood");
+    return commit_round(ctx, T, T_next, lg, acc, logZ, ess, se, ms, asmc, n_res, ess_tr, rs, out);
+}
 
+// Alg. 3 and the carry-over of step sizes from the round's (global) statistics
+static oais_status commit_round(oais_ctx* ctx, int T, int32_t T_next, const std::vector<double>& lg,
+                                const std::vector<double>& acc, double logZ, double ess, double se, float ms,
+                                bool asmc, int n_res, const std::vector<double>& ess_tr,
+                                const std::vector<int>& rs, oais_round_result* out)
+{
     std::vector<double> beta_next(T_next + 1), D(T), Lam(T + 1);
     optimise_schedule(T, ctx->beta.data(), lg.data(), T_next, beta_next.data(), D.data(), Lam.data());
     std::vector<double> eps_next = next_step_sizes(ctx, ctx->beta, ctx->eps, acc, beta_next);
@@ -645,6 +719,106 @@ oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out)
 oais_status oasmc_round(oais_ctx* ctx, int32_t T_next, double ess_frac, oais_round_result* out)
 {
     return run_round(ctx, T_next, true, ess_frac, out);
+}
+
+// ---- checkpoint / resume of the round state (Alg. 2 between rounds) ----
+static const uint64_t kStateMagic = 0x4F41495353543031ull;   // "OAISST01"
+
+struct StateHeader {
+    uint64_t magic;
+    int64_t N, N_total, n_offset;
+    uint64_t seed;
+    int32_t round, T, kind, d, move, moves;
+};
+
+size_t state_bytes_for(const oais_ctx* ctx)
+{
+    return sizeof(StateHeader) + sizeof(double) * (2 * ctx->beta.size() - 1);
+}
+
+oais_status oais_state_bytes(const oais_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return fail(nullptr, OAIS_EINVAL, "null argument");
+    *bytes = state_bytes_for(ctx);
+    return OAIS_OK;
+}
+
+oais_status oais_save_state(const oais_ctx* ctx, void* buf, size_t bytes)
+{
+    if (!ctx || !buf) return fail(nullptr, OAIS_EINVAL, "null argument");
+    if (bytes < state_bytes_for(ctx)) return fail(nullptr, OAIS_EINVAL, "state buffer too small");
+    StateHeader h{kStateMagic, ctx->N, ctx->N_total, ctx->n_offset, ctx->seed, ctx->round,
+                  (int32_t)ctx->beta.size() - 1, ctx->dt.kind, ctx->dt.d, ctx->mv.kind, ctx->mv.moves};
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    std::memcpy(p + sizeof(h), ctx->beta.data(), sizeof(double) * ctx->beta.size());
+    std::memcpy(p + sizeof(h) + sizeof(double) * ctx->beta.size(), ctx->eps.data(), sizeof(double) * ctx->eps.size());
+    return OAIS_OK;
+}
+
+oais_status oais_load_state(oais_ctx* ctx, const void* buf, size_t bytes)
+{
+    if (!ctx || !buf) return fail(nullptr, OAIS_EINVAL, "null argument");
+    if (bytes < sizeof(StateHeader)) return fail(ctx, OAIS_EINVAL, "state buffer too small");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kStateMagic) return fail(ctx, OAIS_EINVAL, "not an OAIS state");
+    if (h.N != ctx->N || h.kind != ctx->dt.kind || h.d != ctx->dt.d || h.move != ctx->mv.kind ||
+        h.moves != ctx->mv.moves)
+        return fail(ctx, OAIS_EINVAL, "state belongs to a different problem or move");
+    if (h.T < 1 || h.T > ctx->T_max || bytes < sizeof(h) + sizeof(double) * (2 * (size_t)h.T + 1))
+        return fail(ctx, OAIS_EINVAL, "bad schedule size in state");
+    const double* b = reinterpret_cast<const double*>(static_cast<const char*>(buf) + sizeof(h));
+    if (!valid_schedule(b, h.T)) return fail(ctx, OAIS_EINVAL, "bad schedule in state");
+    ctx->beta.assign(b, b + h.T + 1);
+    ctx->eps.assign(b + h.T + 1, b + 2 * h.T + 1);
+    ctx->seed = h.seed;
+    ctx->round = h.round;
+    ctx->n_offset = h.n_offset;
+    ctx->N_total = h.N_total;
+    ctx->pend_T = 0;
+    return OAIS_OK;
+}
+
+oais_status oais_set_shard(oais_ctx* ctx, int64_t n_offset, int64_t N_total)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (n_offset < 0 || N_total < ctx->N || n_offset + ctx->N > N_total || N_total > 0xFFFFFFFFLL)
+        return fail(ctx, OAIS_EINVAL, "shard [n_offset, n_offset + N) must lie in [0, N_total)");
+    ctx->n_offset = n_offset;
+    ctx->N_total = N_total;
+    return OAIS_OK;
+}
+
+oais_status oais_round_local(oais_ctx* ctx, double* log_ghat, double* accepted, double* lse, int32_t* T)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    oais_status st = run_round(ctx, ctx->T_max, false, 0.0, nullptr, true);
+    if (st != OAIS_OK) return st;
+    const int t = ctx->pend_T;
+    if (T) *T = t;
+    if (log_ghat) std::copy(ctx->pend_lg.begin(), ctx->pend_lg.end(), log_ghat);
+    if (accepted) std::copy(ctx->pend_acc.begin(), ctx->pend_acc.end(), accepted);
+    if (lse) { lse[0] = ctx->pend_lse[0]; lse[1] = ctx->pend_lse[1]; }
+    return OAIS_OK;
+}
+
+oais_status oais_round_commit(oais_ctx* ctx, int32_t T_next, const double* log_ghat, const double* accepted,
+                              const double* lse, oais_round_result* out)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (ctx->pend_T <= 0) return fail(ctx, OAIS_EINVAL, "no local round to commit");
+    if (T_next < 1 || T_next > ctx->T_max) return fail(ctx, OAIS_EINVAL, "T_next out of range");
+    if (!log_ghat || !accepted || !lse) return fail(ctx, OAIS_EINVAL, "null global statistics");
+    const int T = ctx->pend_T;
+    const double Nt = (double)ctx->N_total;
+    std::vector<double> lg(log_ghat, log_ghat + 3 * T), acc(T);
+    for (int t = 0; t < T; ++t) acc[t] = accepted[t] / (Nt * ctx->mv.moves);
+    const double logZ = lse[0] - std::log(Nt);
+    const double ess = std::exp(2.0 * lse[0] - lse[1]);
+    const double se = std::sqrt(std::max(0.0, 1.0 / ess - 1.0 / Nt));
+    ctx->pend_T = 0;
+    return commit_round(ctx, T, T_next, lg, acc, logZ, ess, se, ctx->pend_ms, false, 0, {}, {}, out);
 }
 
 oais_status oais_get_resampling(const oais_ctx* ctx, double* ess, int32_t* resampled, int64_t* ancestors)
@@ -723,6 +897,39 @@ oais_status oais_particles(const oais_ctx* ctx, const double** logw, const doubl
     if (logw) *logw = ctx->d_logw;
     if (ell) *ell = ctx->d_ell;
     if (x) *x = ctx->d_x;
+    return OAIS_OK;
+}
+
+oais_status oais_grad_logZ(oais_ctx* ctx, double* grad)
+{
+    if (!ctx || !ctx->have_last) return fail(nullptr, OAIS_EINVAL, "no completed round");
+    if (!grad) return fail(ctx, OAIS_EINVAL, "null grad");
+    cudaStream_t s = ctx->stream;
+    // log-sum-exp of the final weights, then the weighted sums of grad_theta log gamma
+    CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
+    CK(launch_fisher(ctx->d_logw, ctx->d_ell, ctx->d_x, ctx->dt.kind == kGauss, ctx->N, ctx->dt.d, ctx->d_lse,
+                     ctx->dt.ref_scale, ctx->dt.kind, ctx->dt.n, ctx->dt.p0, ctx->d_lse_scratch,
+                     ctx->d_lse, s));
+    double g[2];
+    CK(cudaMemcpyAsync(g, ctx->d_lse, sizeof(g), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    grad[0] = g[0];
+    grad[1] = (ctx->dt.kind == kGauss || ctx->dt.kind == kLinreg) ? g[1] : NAN;
+    return OAIS_OK;
+}
+
+oais_status oais_potential(oais_ctx* ctx, const void* d_x, int64_t N, double* d_ell, void* d_grad, void* stream)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (!d_x || !d_ell || N < 1) return fail(ctx, OAIS_EINVAL, "bad arguments to oais_potential");
+    PotentialParams P{N, d_x, d_ell, d_grad};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (ctx->dt.kind) {
+    case kGauss: CK(launch_potential_gauss(ctx->dt, P, s)); break;
+    case kLogreg: CK(launch_potential_logreg(ctx->dt, P, s)); break;
+    case kGmm: CK(launch_potential_gmm(ctx->dt, P, s)); break;
+    case kLinreg: CK(launch_potential_linreg(ctx->dt, P, s)); break;
+    }
     return OAIS_OK;
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include "sweep.cuh"
 
 namespace oais {
@@ -16,7 +17,16 @@ struct DevTarget {
     double ref_scale = 1.0, p0 = 1.0;
     void* X = nullptr;   // GAUSS: double[D]; GMM: float[n][D]; rows: float[n_pad][D]
     void* y = nullptr;   // rows: float[n_pad]
+    bool tc = false;     // tensor-core form: BF16 image of X and label bits below
+    void* tc_img = nullptr;
+    uint32_t* tc_ybits = nullptr;
 };
+
+// tensor-core logistic sweep (sweep_tc.cu)
+int tc_grid(int64_t N);
+int tc_records(int64_t N);
+cudaError_t launch_sweep_tc(const SweepParams& sp, const void* Ximg, const uint32_t* ybits, int n, int d,
+                            cudaStream_t s);
 
 // smallest compiled width >= d for the family, 0 if none
 int padded_width(int kind, int d);
@@ -32,6 +42,12 @@ cudaError_t launch_asmc_gauss(const DevTarget& t, int move, bool init, const Ste
 cudaError_t launch_asmc_logreg(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
 cudaError_t launch_asmc_gmm(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
 cudaError_t launch_asmc_linreg(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
+
+// log L and grad log L for a batch of states, per family
+cudaError_t launch_potential_gauss(const DevTarget& t, const PotentialParams& P, cudaStream_t s);
+cudaError_t launch_potential_logreg(const DevTarget& t, const PotentialParams& P, cudaStream_t s);
+cudaError_t launch_potential_gmm(const DevTarget& t, const PotentialParams& P, cudaStream_t s);
+cudaError_t launch_potential_linreg(const DevTarget& t, const PotentialParams& P, cudaStream_t s);
 
 inline int sweep_grid(int64_t N) { return (int)((N + kSweepThreads - 1) / kSweepThreads); }
 
@@ -58,6 +74,13 @@ cudaError_t launch_one(const Tgt& tg, size_t smem, const StepParams& P, bool ini
 {
     if (init) return launch_kernel(&asmc_init_kernel<Tgt, MOVE, D, R>, tg, smem, P, s);
     return launch_kernel(&asmc_step_kernel<Tgt, MOVE, D, R>, tg, smem, P, s);
+}
+
+// the potential kernel does not depend on the move: every MOVE maps to one instantiation
+template <class Tgt, int MOVE, int D, typename R>
+cudaError_t launch_one(const Tgt& tg, size_t smem, const PotentialParams& P, cudaStream_t s)
+{
+    return launch_kernel(&potential_kernel<Tgt, D, R>, tg, smem, P, s);
 }
 
 // one family's dispatch over (move, width) for both kernel kinds
@@ -91,6 +114,10 @@ cudaError_t launch_one(const Tgt& tg, size_t smem, const StepParams& P, bool ini
                                   cudaStream_t s)                                                \
     {                                                                                            \
         return by_width(t, move, P, s, init);                                                    \
+    }                                                                                            \
+    cudaError_t launch_potential_##FAM(const DevTarget& t, const PotentialParams& P, cudaStream_t s) \
+    {                                                                                            \
+        return by_width(t, (int)kRwmh, P, s);                                                    \
     }
 
 #define OAIS_WIDTH(W) case W: return go<W>(t, move, prm, s, a...);

@@ -146,4 +146,69 @@ cudaError_t launch_logsumexp(const double* a, int64_t n, double* out, void* scra
 
 size_t logsumexp_scratch_bytes(int64_t n) { return sizeof(LsePair) * (size_t)lse_blocks(n); }
 
+// ---- Fisher identity: grad_theta log Z = E_pi[grad_theta log gamma(x; theta)] ----
+// estimated with the normalised final weights W_n = exp(log w_n - LSE) (eq. estimator_pi_t)
+// for theta = (log s, log p0): d/dlog s log N(x; 0, s^2 I) = |x|^2 / s^2 - d, and
+// d/dlog p0 log L from the cached log L: Gaussian -2 log L; linear regression
+// -n - 2 log L - n log(2 pi p0^2); other families: not defined (0).
+struct FisherPair { double a, b; };
+
+template <typename R>
+__global__ void __launch_bounds__(kLseThreads)
+fisher_partial_kernel(const double* __restrict__ logw, const double* __restrict__ ell,
+                      const R* __restrict__ x, int64_t N, int d, const double* __restrict__ lse,
+                      double inv_s2, int kind, double nrows, double lin_c, FisherPair* __restrict__ out)
+{
+    __shared__ double sa[kLseThreads], sb[kLseThreads];
+    const double L = lse[0];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double W = exp(logw[i] - L);
+        double xx = 0.0;
+        for (int j = 0; j < d; ++j) { const double v = (double)x[(size_t)j * N + i]; xx += v * v; }
+        a += W * (xx * inv_s2 - d);
+        double db = 0.0;
+        if (kind == kGauss) db = -2.0 * ell[i];
+        else if (kind == kLinreg) db = -nrows - 2.0 * ell[i] - nrows * lin_c;
+        b += W * db;
+    }
+    const int tid = threadIdx.x;
+    sa[tid] = a; sb[tid] = b;
+    __syncthreads();
+    for (int stride = kLseThreads / 2; stride > 0; stride >>= 1) {
+        if (tid < stride) { sa[tid] += sa[tid + stride]; sb[tid] += sb[tid + stride]; }
+        __syncthreads();
+    }
+    if (tid == 0) out[blockIdx.x] = FisherPair{sa[0], sb[0]};
+}
+
+__global__ void fisher_final_kernel(const FisherPair* __restrict__ parts, int nparts, double* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < nparts; ++j) { a += parts[j].a; b += parts[j].b; }
+    out[0] = a;
+    out[1] = b;
+}
+
+size_t fisher_scratch_bytes(int64_t n) { return sizeof(FisherPair) * (size_t)lse_blocks(n); }
+
+cudaError_t launch_fisher(const double* logw, const double* ell, const void* x, bool fp64, int64_t N, int d,
+                          const double* lse, double ref_scale, int kind, int nrows, double p0, void* scratch,
+                          double* out, cudaStream_t s)
+{
+    const int nb = lse_blocks(N);
+    FisherPair* parts = static_cast<FisherPair*>(scratch);
+    const double inv_s2 = 1.0 / (ref_scale * ref_scale);
+    const double lin_c = log(6.283185307179586 * p0 * p0);
+    if (fp64)
+        fisher_partial_kernel<double><<<nb, kLseThreads, 0, s>>>(logw, ell, static_cast<const double*>(x), N, d,
+                                                                 lse, inv_s2, kind, (double)nrows, lin_c, parts);
+    else
+        fisher_partial_kernel<float><<<nb, kLseThreads, 0, s>>>(logw, ell, static_cast<const float*>(x), N, d,
+                                                                lse, inv_s2, kind, (double)nrows, lin_c, parts);
+    fisher_final_kernel<<<1, 32, 0, s>>>(parts, nb, out);
+    return cudaGetLastError();
+}
+
 } // namespace oais

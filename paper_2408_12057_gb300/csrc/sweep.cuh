@@ -287,6 +287,41 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     }
 }
 
+// The potential on its own: log L(x_n) and, if asked, grad_x log L(x_n) for a batch of
+// states x [d][N] (the forward and backward of the likelihood used by MALA and HMC).
+struct PotentialParams {
+    int64_t N;
+    const void* x;        // [d][N] element type R
+    double* ell;          // [N]
+    void* grad;           // [d][N] element type R, or nullptr
+};
+
+template <class Tgt, int D, typename R>
+__global__ void __launch_bounds__(kSweepThreads)
+potential_kernel(const PotentialParams P, Tgt tg)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    tg.setup(smem);
+    const int d = tg.d;
+    const int64_t n64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = n64 < P.N;
+    const int64_t idx = active ? n64 : P.N - 1;
+    const R* xs = reinterpret_cast<const R*>(P.x);
+    R x[D], g[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) { x[i] = i < d ? xs[(size_t)i * P.N + idx] : R(0); g[i] = R(0); }
+    // all threads take the same branch (cooperative evaluation)
+    const R ell = P.grad ? tg.template eval<true>(x, g) : tg.template eval<false>(x, g);
+    if (active) {
+        P.ell[n64] = (double)ell;
+        if (P.grad) {
+            R* gw = reinterpret_cast<R*>(P.grad);
+#pragma unroll
+            for (int i = 0; i < D; ++i) if (i < d) gw[(size_t)i * P.N + n64] = g[i];
+        }
+    }
+}
+
 // t = 0 of Alg. 1: X_0 ~ eta, w_0 = 1, cached log L and its gradient, into buffer 0.
 template <class Tgt, int MOVE, int D, typename R>
 __global__ void __launch_bounds__(kSweepThreads)

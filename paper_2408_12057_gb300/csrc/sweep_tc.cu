@@ -1,0 +1,567 @@
+// sweep_tc.cu -- the loop-swapped OAIS sweep (Sec. 5.1.2) for the logistic-regression
+// family with the likelihood contraction on the tensor cores (tcgen05, BF16 operands,
+// FP32 accumulation in tensor memory).
+//
+// For a tile of 128 particles P (rows) and a chunk of 64 data rows X_c:
+//   forward   Z   = P X_c^T          (M = 128 particles, N = 64 rows,  K = d = 32)
+//   epilogue  f   = y z - softplus(z),  r = y - sigmoid(z)      (CUDA cores, per element)
+//   backward  G  += R X_c            (M = 128 particles, N = d = 32, K = 64 rows)
+// so log L(x) = sum f (kept in fp32 registers) and grad log L(x) = G (kept in TMEM)
+// for every particle of the tile in one pass over X.  To keep the products at fp32
+// accuracy the particle states and the residuals are split into two BF16 terms,
+// v = hi + lo with hi a bf16 and lo = bf16(v - hi) (relative error below 2^-15), and each
+// contraction is issued once per term.  The data X is rounded to BF16 once (X~); the
+// sampler targets the posterior of X~.
+//
+// CTA = 2 independent groups of 4 warps; group g owns 128 particles, its own TMEM
+// columns, operand tiles and MMA barrier, and shares the BF16 image of X (resident in
+// shared memory for the whole sweep).  One thread per group issues the MMAs.
+//
+// Shared memory (dynamic, 1024-byte aligned base):
+//   R tiles  [group][hi|lo]  128 x 64 bf16, K-major, 128B swizzle    4 x 16 KB
+//   A tiles  [group][hi|lo]  128 x 32 bf16, K-major, 64B swizzle     4 x  8 KB
+//   X image  2048 x 32 bf16, rows of 64 B, 64B swizzle              128 KB
+//            (read as the K-major B of the forward and the MN-major B of the backward)
+//   y bits   2048 labels as a bitmask                                256 B
+//   2 mbarriers, the TMEM base address, per-group moment scratch
+#include <cuda_bf16.h>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "../../include/oais.h"
+
+namespace oais {
+namespace tc {
+
+constexpr int kGroups = 2;
+constexpr int kGroupThreads = 128;
+constexpr int kThreads = kGroups * kGroupThreads;
+constexpr int kD = 32;                       // padded state dimension
+constexpr int kChunk = 64;                   // data rows per contraction chunk
+constexpr int kMaxRows = 2048;
+constexpr int kRTile = 128 * kChunk * 2;     // 16 KB
+constexpr int kATile = 128 * kD * 2;         // 8 KB
+constexpr int kOffR = 0;
+constexpr int kOffA = kOffR + kGroups * 2 * kRTile;          // 64 KB
+constexpr int kOffX = kOffA + kGroups * 2 * kATile;          // 96 KB
+constexpr int kOffY = kOffX + kMaxRows * kD * 2;             // 224 KB
+constexpr int kOffBar = kOffY + kMaxRows / 8;                // + 256 B; 3 barriers per group
+constexpr int kOffTmem = kOffBar + 8 * 3 * kGroups;
+constexpr int kOffStat = kOffTmem + 16;
+constexpr int kStatBytes = 2 * 4 * 3 * 8 + 2 * 4 * 3 * 4 + 2 * 4 * 4;   // [slot][warp] m, s, acc
+constexpr int kSmemBytes = kOffStat + kGroups * kStatBytes;
+constexpr int kTmemCols = 512;               // group g: D1[0], D1[1] at 256 g + {0, 64}, D2 at 256 g + 128
+static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok;
+}
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait on an MMA-completion barrier: false after ~2 s without completion
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer() - t0 > 2000000000ull) return false;
+    return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void group_sync(int g)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                   "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                   "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                   "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4, leading / stride byte offsets >> 4,
+// descriptor version 1, swizzle layout in the top 3 bits (2 = 128B, 4 = 64B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint64_t layout)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16)
+         | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (layout << 61);
+}
+constexpr uint64_t kSW128 = 2, kSW64 = 4;
+
+// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
+// A/B major-ness (bit 15 / 16: 1 = MN-major), N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn_major ? 1u : 0u) << 16)
+         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+constexpr uint32_t kIdescFwd = idesc_bf16(128, kChunk, false);
+constexpr uint32_t kIdescBwd = idesc_bf16(128, kD, true);
+
+// Two-term bf16 split of a pair of floats, v = hi + lo: hi = v with the low 16 bits of its
+// fp32 word cleared (a bf16 value), lo = v - hi (exact in fp32, |lo| < 2^-7 |v|); lo is
+// rounded to the nearest bf16 by adding half a bf16 ulp to its fp32 word before taking the
+// top half (error at most 2^-8 |lo|, no sign bias), so hi + bf16(lo) is within 2^-15 |v|.
+// The bf16 bit patterns are the top halves of the fp32 words, packed pairwise with one byte
+// permute each.
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo)
+{
+    const float ha = __uint_as_float(__float_as_uint(a) & 0xFFFF0000u);
+    const float hb = __uint_as_float(__float_as_uint(b) & 0xFFFF0000u);
+    const float la = __fsub_rn(a, ha), lb = __fsub_rn(b, hb);
+    hi = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+    lo = __byte_perm(__float_as_uint(la) + 0x8000u, __float_as_uint(lb) + 0x8000u, 0x7632);
+}
+
+// special-function unit, flush-to-zero forms (documented PTX approximations)
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct TcParams {
+    SweepParams sp;
+    const uint4* Ximg;       // [kMaxRows * 64 B / 16] BF16 image of X in the smem layout
+    const uint32_t* ybits;   // [kMaxRows / 32]
+    int n;                   // data rows
+    int d;                   // true dimension (<= 32; padded columns of X are zero)
+};
+
+struct Group {
+    int g, tid, warp;
+    uint32_t barF[2], barB;  // mbarriers (smem addresses): forward into D1[i], backward
+    uint32_t d1[2], d2;      // TMEM addresses
+    uint32_t phF, phB;       // expected phase of barF[i] (bit i) and of barB
+    bool dead;               // an MMA barrier wait timed out
+    unsigned char* smem;
+};
+
+// write a 128-particle row of 32 values (split hi/lo) into the group's A tiles
+__device__ __forceinline__ void write_state_tile(const Group& G, const float (&v)[kD])
+{
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) split_pair(v[2 * j], v[2 * j + 1], hi[j], lo[j]);
+    unsigned char* ah = G.smem + kOffA + (G.g * 2 + 0) * kATile;
+    unsigned char* al = G.smem + kOffA + (G.g * 2 + 1) * kATile;
+    const int p = G.tid;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int off = p * 64 + ((c ^ ((p >> 1) & 3)) << 4);
+        *reinterpret_cast<uint4*>(ah + off) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
+        *reinterpret_cast<uint4*>(al + off) = make_uint4(lo[4 * c], lo[4 * c + 1], lo[4 * c + 2], lo[4 * c + 3]);
+    }
+}
+
+// forward contraction of chunk c into D1[buf]: Z = (P_hi + P_lo) X'_c^T
+__device__ __forceinline__ void issue_fwd(const Group& G, int c, int buf)
+{
+    const uint32_t base = saddr(G.smem);
+    const uint32_t xb = base + kOffX;
+#pragma unroll
+    for (int hl = 0; hl < 2; ++hl) {
+        const uint32_t aa = base + kOffA + (G.g * 2 + hl) * kATile;
+#pragma unroll
+        for (int kk = 0; kk < kD / 16; ++kk) {
+            const uint64_t a = sdesc(aa + kk * 32, 16, 512, kSW64);
+            const uint64_t b = sdesc(xb + c * kChunk * 64 + kk * 32, 16, 512, kSW64);
+            mma_bf16(G.d1[buf], a, b, kIdescFwd, (hl == 0 && kk == 0) ? 0u : 1u);
+        }
+    }
+    mma_commit(G.barF[buf]);
+}
+
+// backward contraction of chunk c into D2: G += (R_hi + R_lo) X'_c (first starts the sum)
+__device__ __forceinline__ void issue_bwd(const Group& G, int c, bool first)
+{
+    const uint32_t base = saddr(G.smem);
+    const uint32_t xb = base + kOffX;
+#pragma unroll
+    for (int hl = 0; hl < 2; ++hl) {
+        const uint32_t ra = base + kOffR + (G.g * 2 + hl) * kRTile;
+#pragma unroll
+        for (int kk = 0; kk < kChunk / 16; ++kk) {
+            const uint64_t a = sdesc(ra + kk * 32, 16, 1024, kSW128);
+            const uint64_t b = sdesc(xb + (c * kChunk + kk * 16) * 64, 8192, 512, kSW64);
+            mma_bf16(G.d2, a, b, kIdescBwd, (first && hl == 0 && kk == 0) ? 0u : 1u);
+        }
+    }
+    mma_commit(G.barB);
+}
+
+__device__ __forceinline__ void wait_fwd(Group& G, int buf)
+{
+    if (!G.dead && !mbar_wait(G.barF[buf], (G.phF >> buf) & 1u)) G.dead = true;
+    G.phF ^= 1u << buf;
+}
+__device__ __forceinline__ void wait_bwd(Group& G)
+{
+    if (!G.dead && !mbar_wait(G.barB, G.phB)) G.dead = true;
+    G.phB ^= 1u;
+}
+
+// log L(x) and grad log L(x) for the group's 128 particles; every thread of the group calls it.
+// Pipeline per chunk c: the forward of chunk c+1 runs into the other D1 buffer while the
+// epilogue of chunk c reads D1[c%2]; the backward of chunk c is issued after the epilogue and
+// runs while the next chunk's first slice is computed (its R tile is waited for before the
+// next write).
+__device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], float (&grad)[kD])
+{
+    write_state_tile(G, x);
+    fence_proxy_async();
+    tc_before_sync();
+    group_sync(G.g);
+    const int nch = (P.n + kChunk - 1) / kChunk;
+    const int p = G.tid;
+    const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
+    unsigned char* rh = G.smem + kOffR + (G.g * 2 + 0) * kRTile;
+    unsigned char* rl = G.smem + kOffR + (G.g * 2 + 1) * kRTile;
+    // The image holds X'_r = s_r X~_r with s_r = 2 y_r - 1, so the forward contraction gives
+    // u = s z directly.  Per row: log-likelihood term log sigmoid(u) = min(u, 0) + log(q),
+    // q = 1 / (1 + e^-|u|), and d/dz = s sigmoid(-u), so grad = sum_r sigmoid(-u_r) X'_r.
+    // sum min(u, 0) is accumulated as sum (u - |u|) / 2; the logs (base 2) as one log per 16
+    // rows of the product of q (each q in [1/2, 1], no underflow).  Padded rows (X' = 0) give
+    // u = 0: -log 2 each, corrected below, and nothing to the gradient.
+    float twice_min = 0.0f, logs2 = 0.0f;
+    if (G.tid == 0 && !G.dead) {
+        tc_after_sync();
+        issue_fwd(G, 0, 0);
+    }
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
+        if (G.tid == 0 && !G.dead && c + 1 < nch) issue_fwd(G, c + 1, b ^ 1);
+        wait_fwd(G, b);
+        tc_after_sync();
+#pragma unroll
+        for (int s = 0; s < kChunk / 32; ++s) {
+            uint32_t v[32];
+            tmem_ld32(G.d1[b] + lane_off + s * 32, v);
+            tmem_wait_ld();
+            float prod = 1.0f, tm = 0.0f;
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                float r2[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float u = __uint_as_float(v[j + q]);
+                    const float e = ex2_approx(fabsf(u) * -1.4426950408889634f);   // e^-|u|
+                    const float qinv = rcp_approx(1.0f + e);
+                    r2[q] = u >= 0.0f ? e * qinv : qinv;                          // sigmoid(-u)
+                    tm += u - fabsf(u);
+                    prod *= qinv;
+                }
+                if ((j & 15) == 14) { logs2 += lg2_approx(prod); prod = 1.0f; }
+                split_pair(r2[0], r2[1], hi[j / 2], lo[j / 2]);
+            }
+            twice_min += tm;
+            if (s == 0 && c > 0) wait_bwd(G);     // the backward of chunk c-1 has read R
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int chunk = s * 4 + cc;
+                const int off = p * 128 + ((chunk ^ (p & 7)) << 4);
+                *reinterpret_cast<uint4*>(rh + off) =
+                    make_uint4(hi[4 * cc], hi[4 * cc + 1], hi[4 * cc + 2], hi[4 * cc + 3]);
+                *reinterpret_cast<uint4*>(rl + off) =
+                    make_uint4(lo[4 * cc], lo[4 * cc + 1], lo[4 * cc + 2], lo[4 * cc + 3]);
+            }
+        }
+        fence_proxy_async();
+        tc_before_sync();
+        group_sync(G.g);
+        if (G.tid == 0 && !G.dead) {
+            tc_after_sync();
+            issue_bwd(G, c, c == 0);
+        }
+    }
+    wait_bwd(G);                                  // the backward of the last chunk
+    tc_after_sync();
+    uint32_t v[32];
+    tmem_ld32(G.d2 + lane_off, v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < kD; ++i) grad[i] = __uint_as_float(v[i]);
+    tc_before_sync();
+    const float ln2 = 0.69314718055994531f;
+    return 0.5f * twice_min + ln2 * logs2 + (float)(nch * kChunk - P.n) * ln2;
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// the group's 4 warps merge their (m, s) moment pieces and acceptance counts (fixed order)
+__device__ __forceinline__ void group_record(const Group& G, const double (*wm)[3], const float (*ws)[3],
+                                             const unsigned* wacc, StepPartial* out)
+{
+    if (G.warp != 0) return;
+    const int lane = G.tid & 31;
+    StepPartial rec;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double m = lane < 4 ? wm[lane][i] : -INFINITY;
+        double M = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
+        double v = (lane < 4 && m != -INFINITY) ? (double)ws[lane][i] * exp(m - M) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        rec.m[i] = M;
+        rec.s[i] = v;
+    }
+    unsigned a = lane < 4 ? wacc[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if (lane == 0) {
+        rec.accepted = a;
+        rec.pad = 0;
+        *out = rec;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+oais_sweep_tc_kernel(const TcParams P)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const SweepParams& S = P.sp;
+    // the 128B-swizzled tiles need a 1024-byte aligned base
+    if (saddr(smem) & 1023u) {
+        if (threadIdx.x == 0) atomicOr(S.status, 4u);
+        return;
+    }
+    // stage the BF16 image of the label-signed data X' (kept for the whole sweep)
+    {
+        const uint4* src = P.Ximg;
+        for (int i = threadIdx.x; i < kMaxRows * kD * 2 / 16; i += kThreads) cp_async16(smem + kOffX + 16 * i, src + i);
+        cp_async_commit();
+        cp_async_wait<0>();
+    }
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 3 * kGroups; ++i) mbar_init(saddr(&bars[i]), 1);
+        fence_mbar_init();
+    }
+    if (threadIdx.x < 32) {
+        tmem_alloc(saddr(smem + kOffTmem), kTmemCols);
+        tmem_relinquish();
+    }
+    fence_proxy_async();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + kOffTmem);
+
+    Group G;
+    G.g = threadIdx.x / kGroupThreads;
+    G.tid = threadIdx.x % kGroupThreads;
+    G.warp = G.tid / 32;
+    G.barF[0] = saddr(&bars[3 * G.g + 0]);
+    G.barF[1] = saddr(&bars[3 * G.g + 1]);
+    G.barB = saddr(&bars[3 * G.g + 2]);
+    G.d1[0] = tmem + (uint32_t)(G.g * 256);
+    G.d1[1] = tmem + (uint32_t)(G.g * 256 + 64);
+    G.d2 = tmem + (uint32_t)(G.g * 256 + 128);
+    G.phF = 0;
+    G.phB = 0;
+    G.dead = false;
+    G.smem = smem;
+    unsigned char* st = smem + kOffStat + G.g * kStatBytes;
+    double (*s_m)[4][3] = reinterpret_cast<double (*)[4][3]>(st);
+    float (*s_s)[4][3] = reinterpret_cast<float (*)[4][3]>(st + 2 * 4 * 3 * 8);
+    unsigned (*s_acc)[4] = reinterpret_cast<unsigned (*)[4]>(st + 2 * 4 * 3 * 8 + 2 * 4 * 3 * 4);
+
+    const int64_t tile = (int64_t)blockIdx.x * kGroups + G.g;
+    const int64_t n64 = tile * kGroupThreads + G.tid;
+    const bool active = n64 < S.N;
+    const uint32_t n = (uint32_t)(S.n_offset + (active ? n64 : S.N - 1));
+    const int d = P.d;
+    const float sref = (float)S.ref_scale;
+    const float inv_s2 = 1.0f / (sref * sref);
+    const int lane = G.tid & 31;
+
+    float x[kD], gl[kD];
+    normals<kD>(S.mv.rng, n, 0u, 0u, d, x);
+#pragma unroll
+    for (int i = 0; i < kD; ++i) x[i] *= sref;
+    float ell = tc_eval(G, P, x, gl);
+    double logw = 0.0;
+    double beta_prev = S.beta[0];
+    for (int t = 1; t <= S.T; ++t) {
+        const double beta_t = __ldg(S.beta + t);
+        const double eps_t = __ldg(S.eps + t - 1);
+        const double lg = (beta_t - beta_prev) * (double)ell;
+        beta_prev = beta_t;
+        const int slot = t & 1;
+        warp_moment_partial(logw, lg, active, s_m[slot][G.warp], s_s[slot][G.warp]);
+        logw += lg;
+        unsigned acc = 0;
+        const float beta = (float)beta_t, e = (float)eps_t, h = 0.5f * e;
+        for (int k = 0; k < S.mv.K; ++k) {
+            // MALA (Sec. 2.1.1 kernel family): x' = x + (e^2/2) grad log pi(x) + e z
+            float z[kD], xp[kD];
+            normals<kD>(S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, z);
+            float zz = 0.0f, dxx = 0.0f;
+#pragma unroll
+            for (int i = 0; i < kD; ++i) {
+                const float gpi = -x[i] * inv_s2 + beta * gl[i];
+                xp[i] = x[i] + e * (h * gpi + z[i]);
+                zz += z[i] * z[i];
+                z[i] = z[i] + h * gpi;
+                dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
+            }
+            float glp[kD];
+            const float ellp = tc_eval(G, P, xp, glp);
+            float rev = 0.0f;
+#pragma unroll
+            for (int i = 0; i < kD; ++i) {
+                const float q = z[i] + h * (-xp[i] * inv_s2 + beta * glp[i]);
+                rev += q * q;
+            }
+            const float log_alpha = -0.5f * dxx * inv_s2 + beta * (ellp - ell) - 0.5f * (rev - zz);
+            const float logu = mh_log_uniform(S.mv.rng, n, (uint32_t)t, (uint32_t)k, 0.0f);
+            if (logu < log_alpha) {
+#pragma unroll
+                for (int i = 0; i < kD; ++i) { x[i] = xp[i]; gl[i] = glp[i]; }
+                ell = ellp;
+                ++acc;
+            }
+        }
+        acc = active ? acc : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (lane == 0) s_acc[slot][G.warp] = acc;
+        group_sync(G.g);
+        group_record(G, s_m[slot], s_s[slot], s_acc[slot],
+                     S.partials + (size_t)(t - 1) * (gridDim.x * kGroups) + tile);
+    }
+    if (active) {
+        S.logw[n64] = logw;
+        S.ell_out[n64] = (double)ell;
+        float* xo = reinterpret_cast<float*>(S.x_out);
+#pragma unroll
+        for (int i = 0; i < kD; ++i) if (i < d) xo[(size_t)i * S.N + n64] = x[i];
+        if (!isfinite(logw) || !isfinite(ell)) atomicOr(S.status, 1u);
+    }
+    if (G.dead && G.tid == 0) atomicOr(S.status, 2u);
+    tc_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(tmem, kTmemCols);
+}
+
+} // namespace tc
+
+int tc_grid(int64_t N) { return (int)((N + tc::kThreads - 1) / tc::kThreads); }
+int tc_records(int64_t N) { return tc_grid(N) * tc::kGroups; }
+
+// BF16 image of X in the kernel's shared-memory layout (rows of 64 B, 64B swizzle) and the
+// label bitmask; X is [n][d] row-major fp32 on the host.
+int tc_image_bytes() { return tc::kMaxRows * tc::kD * 2; }
+int tc_max_rows() { return tc::kMaxRows; }
+void tc_prepare_logreg(const float* X, const float* y, int n, int d, std::vector<uint16_t>& img,
+                       std::vector<uint32_t>& ybits)
+{
+    img.assign((size_t)tc::kMaxRows * tc::kD, 0);
+    ybits.assign(tc::kMaxRows / 32, 0u);
+    auto bf16 = [](float v) -> uint16_t {
+        uint32_t u;
+        std::memcpy(&u, &v, 4);
+        u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even (finite inputs)
+        return (uint16_t)(u >> 16);
+    };
+    for (int r = 0; r < n; ++r) {
+        // label sign folded into the row: X'_r = (2 y_r - 1) X_r (exact in bf16)
+        const bool pos = y[r] > 0.5f;
+        for (int i = 0; i < d; ++i) {
+            const int c = i / 8, q = i % 8;
+            const int phys = (c ^ ((r >> 1) & 3));
+            const uint16_t b = bf16(X[(size_t)r * d + i]);
+            img[(size_t)r * tc::kD + phys * 8 + q] = pos ? b : (uint16_t)(b ^ 0x8000u);
+        }
+        if (pos) ybits[r / 32] |= 1u << (r % 32);
+    }
+}
+
+cudaError_t launch_sweep_tc(const SweepParams& sp, const void* Ximg, const uint32_t* ybits, int n, int d,
+                            cudaStream_t s)
+{
+    tc::TcParams P;
+    P.sp = sp;
+    P.Ximg = static_cast<const uint4*>(Ximg);
+    P.ybits = ybits;
+    P.n = n;
+    P.d = d;
+    cudaError_t e = cudaFuncSetAttribute(tc::oais_sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    tc::oais_sweep_tc_kernel<<<tc_grid(sp.N), tc::kThreads, tc::kSmemBytes, s>>>(P);
+    return cudaGetLastError();
+}
+
+} // namespace oais

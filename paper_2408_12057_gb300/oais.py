@@ -19,6 +19,7 @@ from . import _build
 GAUSS, LOGREG, GMM, LINREG = 0, 1, 2, 3
 RWMH, MALA, HMC = 0, 1, 2
 DT_F64, DT_F32 = 0, 1
+CONTRACT_FP32, CONTRACT_BF16_TC = 0, 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "non-finite value", 5: "device wait timed out", 6: "unsupported configuration"}
@@ -34,7 +35,7 @@ class _Target(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("d", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("X", ctypes.c_void_p), ("y", ctypes.c_void_p),
                 ("ref_scale", ctypes.c_double), ("p0", ctypes.c_double),
-                ("on_device", ctypes.c_int32)]
+                ("on_device", ctypes.c_int32), ("contraction", ctypes.c_int32)]
 
 
 class _Move(ctypes.Structure):
@@ -74,6 +75,14 @@ def lib():
                 "oais_get_schedule": ([P, P, P, P], i32),
                 "oais_set_schedule": ([P, P, P, i32], i32),
                 "oais_particles": ([P, P, P, P], i32),
+                "oais_grad_logZ": ([P, P], i32),
+                "oais_set_shard": ([P, i64, i64], i32),
+                "oais_state_bytes": ([P, P], i32),
+                "oais_save_state": ([P, P, sz], i32),
+                "oais_load_state": ([P, P, sz], i32),
+                "oais_round_local": ([P, P, P, P, P], i32),
+                "oais_round_commit": ([P, i32, P, P, P, P], i32),
+                "oais_potential": ([P, P, i64, P, P, P], i32),
                 "oais_destroy": ([P], None),
                 "oais_last_error": ([P], ctypes.c_char_p),
                 "oais_status_string": ([i32], ctypes.c_char_p),
@@ -146,7 +155,8 @@ class OAIS:
     """One OAIS run (Alg. 2) over a target of paper_2408_12057_gb300.workloads.Problem."""
 
     def __init__(self, problem, move_kind, N, beta, T_max=None, eps=None, seed=12057, moves=1,
-                 leapfrog=5, cycle=False, adapt=False, data_on_device=True, stream=None):
+                 leapfrog=5, cycle=False, adapt=False, data_on_device=True, stream=None,
+                 contraction=CONTRACT_FP32):
         import torch
         self._torch = torch
         self.problem = problem
@@ -168,7 +178,7 @@ class OAIS:
             self._X, self._y = X, y
             Xp, yp = X.ctypes.data, (None if y is None else y.ctypes.data)
         self._tg = _Target(kind, problem.d, problem.n, dtype, Xp, yp, problem.ref_scale, problem.p0,
-                           1 if data_on_device else 0)
+                           1 if data_on_device else 0, int(contraction))
         self._mv = _Move(int(move_kind), int(moves), int(leapfrog), int(bool(cycle)), int(bool(adapt)))
         L = lib()
         nbytes = ctypes.c_size_t()
@@ -242,6 +252,58 @@ class OAIS:
         _check(lib().oais_set_schedule(self._ctx, _np_ptr(beta), None if e is None else _np_ptr(e), T),
                self._ctx)
 
+    # ---- checkpoint / resume between rounds ----
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        _check(lib().oais_state_bytes(self._ctx, ctypes.byref(n)), self._ctx)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().oais_save_state(self._ctx, buf, n.value), self._ctx)
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().oais_load_state(self._ctx, buf, len(blob)), self._ctx)
+
+    # ---- sharding across processes (one exchange of 4T + 2 doubles per round) ----
+    def set_shard(self, n_offset, N_total):
+        """This run's particles are [n_offset, n_offset + N) of a run of N_total."""
+        _check(lib().oais_set_shard(self._ctx, int(n_offset), int(N_total)), self._ctx)
+
+    def round_local(self):
+        """Sweep this shard: dict(log_ghat [T,3], accepted [T], lse [2]) for the exchange."""
+        T = self.schedule()[0].size - 1
+        lg, acc, lse, Tc = np.zeros((T, 3)), np.zeros(T), np.zeros(2), ctypes.c_int32()
+        _check(lib().oais_round_local(self._ctx, _np_ptr(lg), _np_ptr(acc), _np_ptr(lse), ctypes.byref(Tc)),
+               self._ctx)
+        return {"log_ghat": lg, "accepted": acc, "lse": lse}
+
+    def round_commit(self, T_next, merged):
+        """Install the statistics merged over all shards; returns the round result."""
+        r = _RoundResult()
+        lg = np.ascontiguousarray(merged["log_ghat"], dtype=np.float64)
+        acc = np.ascontiguousarray(merged["accepted"], dtype=np.float64)
+        lse = np.ascontiguousarray(merged["lse"], dtype=np.float64)
+        _check(lib().oais_round_commit(self._ctx, int(T_next), _np_ptr(lg), _np_ptr(acc), _np_ptr(lse),
+                                       ctypes.byref(r)), self._ctx)
+        return {f: getattr(r, f) for f, _ in _RoundResult._fields_ if f != "pad"}
+
+    def grad_logZ(self):
+        """Fisher-identity estimate of d log Z / d(log ref_scale, log p0) from the last round."""
+        g = np.zeros(2)
+        _check(lib().oais_grad_logZ(self._ctx, _np_ptr(g)), self._ctx)
+        return g
+
+    def potential(self, x, grad=True, stream=None):
+        """log L and grad log L at states x [d, N] (CUDA tensor of the family's dtype)."""
+        torch = self._torch
+        x = x.contiguous()
+        N = x.shape[1]
+        ell = torch.empty(N, dtype=torch.float64, device=x.device)
+        g = torch.empty_like(x) if grad else None
+        _check(lib().oais_potential(self._ctx, _dptr(x), N, _dptr(ell), None if g is None else _dptr(g),
+                                    _stream_ptr(stream)), self._ctx)
+        return (ell, g) if grad else ell
+
     def particles(self):
         """(logw [N], ell [N], x [d, N]) torch views of the final particles of the last round."""
         torch = self._torch
@@ -269,6 +331,41 @@ class OAIS:
                                     _dptr(partials), _dptr(status), _stream_ptr(stream)), self._ctx)
 
 
+def merge_shard_stats(parts):
+    """Merge per-shard round statistics: the moments and the final weight sums are sums over
+    particles, so their logarithms combine by log-sum-exp; acceptance counts add."""
+    lg = np.logaddexp.reduce(np.stack([p["log_ghat"] for p in parts]), axis=0)
+    lse = np.logaddexp.reduce(np.stack([p["lse"] for p in parts]), axis=0)
+    acc = np.sum(np.stack([p["accepted"] for p in parts]), axis=0)
+    return {"log_ghat": lg, "accepted": acc, "lse": lse}
+
+
+def exchange_stats(local, group=None, device=None):
+    """All-gather one shard's statistics (4T + 2 doubles) over a torch.distributed group and
+    merge them.  Works with gloo (CPU tensors) and NCCL (pass device=cuda)."""
+    import torch
+    import torch.distributed as dist
+    T = local["log_ghat"].shape[0]
+    flat = np.concatenate([local["log_ghat"].ravel(), local["accepted"], local["lse"]])
+    t = torch.from_numpy(flat)
+    if device is not None:
+        t = t.to(device)
+    world = dist.get_world_size(group)
+    bufs = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(bufs, t, group=group)
+    parts = []
+    for b in bufs:
+        v = b.cpu().numpy()
+        parts.append({"log_ghat": v[:3 * T].reshape(T, 3), "accepted": v[3 * T:4 * T], "lse": v[4 * T:]})
+    return merge_shard_stats(parts)
+
+
+def distributed_round(run, T_next, group=None, device=None):
+    """One OAIS round of a run sharded over the ranks of `group` (each rank one OAIS shard)."""
+    merged = exchange_stats(run.round_local(), group=group, device=device)
+    return run.round_commit(T_next, merged)
+
+
 def sweep_blocks(N):
     return lib().oais_sweep_blocks(int(N))
 
@@ -294,3 +391,25 @@ def logsumexp(a, stream=None):
     out = torch.empty(2, dtype=torch.float64, device="cuda")
     _check(lib().oais_logsumexp(_dptr(a), n, _dptr(out), _dptr(scratch), _stream_ptr(stream)))
     return out
+
+
+def log_likelihood_function():
+    """torch.autograd.Function whose forward is log L(x) for a batch of states and whose
+    backward applies the hand-written gradient kernel (both from one oais_potential call).
+
+    Usage: LogLik = log_likelihood_function(); ell = LogLik.apply(x, run) with x [N, d]."""
+    import torch
+
+    class LogLikelihood(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, x, run):
+            ell, g = run.potential(x.detach().t().contiguous(), grad=True)
+            fctx.save_for_backward(g)
+            return ell.to(x.dtype)
+
+        @staticmethod
+        def backward(fctx, grad_out):
+            (g,) = fctx.saved_tensors
+            return (grad_out.to(g.dtype)[:, None] * g.t()), None
+
+    return LogLikelihood
