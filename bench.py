@@ -31,9 +31,7 @@ ROUNDS_T = [256, 512, 1024, 2048]
 SE_TARGET = 0.01
 WORKLOAD = "logreg_n2000_d32_N65536_T256-512-1024-2048_mala"
 METRIC = "particle-steps/s"
-FP32_LANES_PER_SM, N_SM = 128, 152
-MUFU_PER_SM_CLK = 16            # special-function results per SM per clock
-MUFU_OPS_PER_ELEMENT = 3        # softplus and sigmoid of z need exp, log and a reciprocal
+N_SM = 152
 
 
 def parse():
@@ -47,8 +45,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--rounds", default=None,
                     help="comma-separated T per round (profiling a smaller case); default 256,512,1024,2048")
-    ap.add_argument("--contraction", default="fp32", choices=["fp32", "bf16_tc"],
-                    help="X x on CUDA cores in fp32, or on the tcgen05 tensor cores with X rounded to bf16")
+    ap.add_argument("--contraction", default="bf16_tc", choices=["fp32", "bf16_tc"],
+                    help="X x on the tcgen05 tensor cores with X rounded to bf16 (default), or on "
+                         "CUDA cores in fp32")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the other form of the contraction")
     a = ap.parse_args()
     if a.rounds:
         global ROUNDS_T
@@ -181,79 +182,109 @@ def main():
     T0 = ROUNDS_T[0]
     beta0 = np.linspace(0.0, 1.0, T0 + 1)
     eps0 = oais.default_step_sizes(pr, beta0, oais.MALA)
-    contraction = oais.CONTRACT_BF16_TC if args.contraction == "bf16_tc" else oais.CONTRACT_FP32
-    # one sharded run: each rank owns a disjoint block of the particle counter space (weak
-    # scaling, N_PARTICLES per GPU); the round statistics are exchanged once per round
-    run = oais.OAIS(pr, oais.MALA, N_PARTICLES, beta0, T_max=max(ROUNDS_T), eps=eps0,
-                    seed=12057, adapt=True, stream=stream, contraction=contraction)
-    if world > 1:
-        run.set_shard(rank * N_PARTICLES, world * N_PARTICLES)
+    code = {"bf16_tc": oais.CONTRACT_BF16_TC, "fp32": oais.CONTRACT_FP32}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def job():
-        run.set_schedule(beta0, eps0)
+    def make_run(contraction):
+        # one sharded run: each rank owns a disjoint block of the particle counter space (weak
+        # scaling, N_PARTICLES per GPU); the round statistics are exchanged once per round
+        r = oais.OAIS(pr, oais.MALA, N_PARTICLES, beta0, T_max=max(ROUNDS_T), eps=eps0,
+                      seed=12057, adapt=True, stream=stream, contraction=code[contraction])
+        if world > 1:
+            r.set_shard(rank * N_PARTICLES, world * N_PARTICLES)
+        return r
+
+    def job(r):
+        r.set_schedule(beta0, eps0)
         res = []
         for k, T in enumerate(ROUNDS_T):
             nxt = ROUNDS_T[min(k + 1, len(ROUNDS_T) - 1)]
             if world > 1:
-                res.append(oais.distributed_round(run, nxt, device=torch.device("cuda", local)))
+                res.append(oais.distributed_round(r, nxt, device=torch.device("cuda", local)))
             else:
-                res.append(run.round(nxt))
+                res.append(r.round(nxt))
         return res
 
-    for _ in range(args.warmup):
-        job()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    step_ms, sweep_ms, last = [], [], None
-    for _ in range(args.steps):
-        flush.zero_()                       # L2 flushed between timed steps
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def timed(r, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            job(r)
         torch.cuda.synchronize()
-        e0.record(stream)
-        last = job()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        sweep_ms.append(sum(r["sweep_ms"] for r in last))
-    clk = clocks.stop()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
+        if world > 1:
+            torch.distributed.barrier()
+        if clocks:
+            clocks.start()
+        step_ms, sweep_ms, last = [], [], None
+        for _ in range(steps):
+            flush.zero_()                       # L2 flushed between timed steps
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            last = job(r)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            sweep_ms.append(sum(x["sweep_ms"] for x in last))
+        clk = clocks.stop() if clocks else None
+        total = float(sum(step_ms))
+        if world > 1:
+            t = torch.tensor([total], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+            torch.distributed.barrier()
+        return total, sweep_ms, step_ms, last, clk
+
+    run = make_run(args.contraction)
+    total_ms, sweep_ms, step_ms, last, clk = timed(run, args.steps, args.warmup, ClockSampler(local))
     ps_per_job = N_PARTICLES * sum(ROUNDS_T)
     value = world * ps_per_job * args.steps / (total_ms / 1e3)
+
+    # the other form of the contraction, timed the same way (one step after one warm-up)
+    compare = None
+    if not args.no_compare:
+        other = "fp32" if args.contraction == "bf16_tc" else "bf16_tc"
+        r2 = make_run(other)
+        t2, _, _, last2, _ = timed(r2, 1, 1)
+        compare = {"contraction": other, "value": world * ps_per_job / (t2 / 1e3), "unit": METRIC,
+                   "ms_per_step": t2, "steps": 1, "warmup": 1,
+                   "logZ_last_round": last2[-1]["logZ"], "se_last_round": last2[-1]["se"],
+                   "sec_to_logZ_se_0.01": (t2 / 1e3) * (last2[-1]["se"] / SE_TARGET) ** 2}
+        r2.close()
 
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sweep_s = sum(sweep_ms) / 1e3
+    # rates (lane-operations per second per SM) of the units that bound the two forms,
+    # measured on this GPU right after the timed region
+    rates = {name: oais.measure_unit_rate(u) for name, u in
+             [("ex2", oais.UNIT_EX2), ("rcp", oais.UNIT_RCP), ("lg2", oais.UNIT_LG2),
+              ("ffma", oais.UNIT_FFMA)]}
     if args.contraction == "fp32":
         # FP32 form: the FMA pipe bounds it (4 n d FLOP per particle-step)
-        fp32_peak = 2.0 * FP32_LANES_PER_SM * N_SM * sm_max * 1e6 / 1e12     # TFLOP/s
+        fp32_peak = 2.0 * rates["ffma"] * N_SM / 1e12                          # TFLOP/s
         achieved = algorithmic_flops_per_particle_step(pr) * ps_per_job * args.steps / sweep_s / 1e12
         roofline = {"bound": "alu", "pipe": "fp32 fma", "achieved": achieved, "peak": fp32_peak,
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                   f"(sm_max_mhz of {peak_src} peaks)",
+                    "peak_source": f"measured FFMA rate {rates['ffma'] / 1e9:.1f} G lane-ops/s/SM x 2 x "
+                                   f"152 SMs (oais_measure_unit_rate)",
                     "kernel": "oais_sweep_kernel<RowsTarget<32,logistic>, MALA>"}
     else:
-        # tensor-core form: the contraction is on tcgen05; the per-element epilogue
-        # (exp, reciprocal per element; one log per 16) runs on the MUFU (XU) pipe
-        mufu_peak = MUFU_PER_SM_CLK * N_SM * sm_max * 1e6 / 1e12             # Tops/s
-        ops = MUFU_OPS_PER_ELEMENT * pr.n * ps_per_job * args.steps
-        achieved = ops / sweep_s / 1e12
-        roofline = {"bound": "alu", "pipe": "mufu (xu)", "achieved": achieved, "peak": mufu_peak,
-                    "unit": "Tops/s", "frac": achieved / mufu_peak, "traffic": None,
-                    "peak_source": f"152 SMs x 16 MUFU results/clk x {sm_max:.0f} MHz "
-                                   f"(sm_max_mhz of {peak_src} peaks)",
+        # tensor-core form: the contractions run on tcgen05 (a small share of their peak); the
+        # per-row epilogue needs one exp and one reciprocal per row and one log per 16 rows on
+        # the special-function unit, whose measured rates bound the row throughput
+        sec_per_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (16.0 * rates["lg2"])
+        sfu_per_row = 2.0 + 1.0 / 16.0
+        rows = pr.n * ps_per_job * args.steps
+        achieved = sfu_per_row * rows / sweep_s / 1e12
+        peak = sfu_per_row * N_SM / sec_per_row_sm / 1e12
+        roofline = {"bound": "alu", "pipe": "sfu (xu)", "achieved": achieved, "peak": peak,
+                    "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"measured ex2/rcp/lg2 rates {rates['ex2'] / 1e9:.1f}/"
+                                   f"{rates['rcp'] / 1e9:.1f}/{rates['lg2'] / 1e9:.1f} G lane-ops/s/SM x "
+                                   f"152 SMs (oais_measure_unit_rate)",
                     "kernel": "oais_sweep_tc_kernel (tcgen05 bf16, MALA)",
                     "tensor_tflops_issued": 2 * algorithmic_flops_per_particle_step(pr) * 2048 / pr.n
                                             * ps_per_job * args.steps / sweep_s / 1e12}
+    roofline["measured_rates_lane_ops_per_s_per_sm"] = rates
     roofline["sweep_share_of_step"] = sum(sweep_ms) / sum(step_ms)
 
     se_last = last[-1]["se"]
@@ -261,7 +292,7 @@ def main():
 
     e2e = None
     if not args.no_e2e and rank == 0:
-        e2e = measure_e2e(pr, eps0, beta0, args.steps, contraction)
+        e2e = measure_e2e(pr, eps0, beta0, args.steps, code[args.contraction])
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -278,7 +309,7 @@ def main():
                        "log_weights": "f64", "contraction": args.contraction},
             "logZ_last_round": last[-1]["logZ"], "se_last_round": se_last,
             "sec_to_logZ_se_0.01": sec_to_se,
-            "roofline": roofline, "e2e": e2e, "cpu_baseline": cb,
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cb, "other_form": compare,
             "gpu_launches": 4 * len(ROUNDS_T) * args.steps,
             "clocks": clk,
         }))

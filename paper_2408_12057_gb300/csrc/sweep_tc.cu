@@ -47,7 +47,7 @@ constexpr int kOffA = kOffR + kGroups * 2 * kRTile;          // 64 KB
 constexpr int kOffX = kOffA + kGroups * 2 * kATile;          // 96 KB
 constexpr int kOffY = kOffX + kMaxRows * kD * 2;             // 224 KB
 constexpr int kOffBar = kOffY + kMaxRows / 8;                // + 256 B; 3 barriers per group
-constexpr int kOffTmem = kOffBar + 8 * 3 * kGroups;
+constexpr int kOffTmem = kOffBar + 8 * 4 * kGroups;       // 4 barriers per group
 constexpr int kOffStat = kOffTmem + 16;
 constexpr int kStatBytes = 2 * 4 * 3 * 8 + 2 * 4 * 3 * 4 + 2 * 4 * 4;   // [slot][warp] m, s, acc
 constexpr int kSmemBytes = kOffStat + kGroups * kStatBytes;
@@ -121,6 +121,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
                  : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&f)[32])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+                 "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+                 "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+                 ::"r"(taddr), "f"(f[0]), "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]), "f"(f[6]),
+                   "f"(f[7]), "f"(f[8]), "f"(f[9]), "f"(f[10]), "f"(f[11]), "f"(f[12]), "f"(f[13]), "f"(f[14]),
+                   "f"(f[15]), "f"(f[16]), "f"(f[17]), "f"(f[18]), "f"(f[19]), "f"(f[20]), "f"(f[21]),
+                   "f"(f[22]), "f"(f[23]), "f"(f[24]), "f"(f[25]), "f"(f[26]), "f"(f[27]), "f"(f[28]),
+                   "f"(f[29]), "f"(f[30]), "f"(f[31])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld32f(uint32_t taddr, float (&f)[32])
+{
+    uint32_t v[32];
+    tmem_ld32(taddr, v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(v[i]);
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
 // Shared-memory matrix descriptor (tcgen05): start >> 4, leading / stride byte offsets >> 4,
 // descriptor version 1, swizzle layout in the top 3 bits (2 = 128B, 4 = 64B).
@@ -187,8 +212,10 @@ struct TcParams {
 struct Group {
     int g, tid, warp;
     uint32_t barF[2], barB;  // mbarriers (smem addresses): forward into D1[i], backward
+    uint32_t barR;           // mbarrier: the group's 4 warps have written their R rows
     uint32_t d1[2], d2;      // TMEM addresses
-    uint32_t phF, phB;       // expected phase of barF[i] (bit i) and of barB
+    uint32_t stash;          // TMEM columns parking the particle state during an evaluation
+    uint32_t phF, phB, phR;  // expected phase of barF[i] (bit i), barB, barR
     bool dead;               // an MMA barrier wait timed out
     unsigned char* smem;
 };
@@ -259,9 +286,10 @@ __device__ __forceinline__ void wait_bwd(Group& G)
 
 // log L(x) and grad log L(x) for the group's 128 particles; every thread of the group calls it.
 // Pipeline per chunk c: the forward of chunk c+1 runs into the other D1 buffer while the
-// epilogue of chunk c reads D1[c%2]; the backward of chunk c is issued after the epilogue and
-// runs while the next chunk's first slice is computed (its R tile is waited for before the
-// next write).
+// epilogue of chunk c reads D1[c%2].  Each warp, once its rows of the R tile are written,
+// arrives on barR; only the issuing thread waits for all four, then issues the backward of
+// chunk c (it runs while the next chunk's first slice is computed; the R tile is waited for
+// before the next write) and the forward of chunk c+2 into the D1 buffer just read.
 __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], float (&grad)[kD])
 {
     write_state_tile(G, x);
@@ -283,17 +311,21 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
     if (G.tid == 0 && !G.dead) {
         tc_after_sync();
         issue_fwd(G, 0, 0);
+        if (nch > 1) issue_fwd(G, 1, 1);
     }
     for (int c = 0; c < nch; ++c) {
         const int b = c & 1;
-        if (G.tid == 0 && !G.dead && c + 1 < nch) issue_fwd(G, c + 1, b ^ 1);
         wait_fwd(G, b);
+        __syncwarp();                             // tcgen05.ld below is warp-aligned
         tc_after_sync();
+        // both 32-column slices of the chunk are requested before one wait
+        uint32_t vs[kChunk / 32][32];
+#pragma unroll
+        for (int s = 0; s < kChunk / 32; ++s) tmem_ld32(G.d1[b] + lane_off + s * 32, vs[s]);
+        tmem_wait_ld();
 #pragma unroll
         for (int s = 0; s < kChunk / 32; ++s) {
-            uint32_t v[32];
-            tmem_ld32(G.d1[b] + lane_off + s * 32, v);
-            tmem_wait_ld();
+            const uint32_t (&v)[32] = vs[s];
             float prod = 1.0f, tm = 0.0f;
             uint32_t hi[16], lo[16];
 #pragma unroll
@@ -323,15 +355,22 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
                     make_uint4(lo[4 * cc], lo[4 * cc + 1], lo[4 * cc + 2], lo[4 * cc + 3]);
             }
         }
-        fence_proxy_async();
-        tc_before_sync();
-        group_sync(G.g);
-        if (G.tid == 0 && !G.dead) {
-            tc_after_sync();
-            issue_bwd(G, c, c == 0);
+        fence_proxy_async();                      // my R rows, visible to the tensor core
+        tc_before_sync();                         // my reads of D1[b] before its next forward
+        __syncwarp();
+        if ((G.tid & 31) == 0) mbar_arrive(G.barR);
+        if (G.tid == 0) {
+            if (!G.dead && !mbar_wait(G.barR, G.phR)) G.dead = true;
+            G.phR ^= 1u;
+            if (!G.dead) {
+                tc_after_sync();
+                issue_bwd(G, c, c == 0);
+                if (c + 2 < nch) issue_fwd(G, c + 2, b);
+            }
         }
     }
     wait_bwd(G);                                  // the backward of the last chunk
+    __syncwarp();
     tc_after_sync();
     uint32_t v[32];
     tmem_ld32(G.d2 + lane_off, v);
@@ -405,7 +444,10 @@ oais_sweep_tc_kernel(const TcParams P)
     }
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 3 * kGroups; ++i) mbar_init(saddr(&bars[i]), 1);
+        for (int g = 0; g < kGroups; ++g) {
+            for (int i = 0; i < 3; ++i) mbar_init(saddr(&bars[4 * g + i]), 1);
+            mbar_init(saddr(&bars[4 * g + 3]), kGroupThreads / 32);   // one arrival per warp
+        }
         fence_mbar_init();
     }
     if (threadIdx.x < 32) {
@@ -422,14 +464,17 @@ oais_sweep_tc_kernel(const TcParams P)
     G.g = threadIdx.x / kGroupThreads;
     G.tid = threadIdx.x % kGroupThreads;
     G.warp = G.tid / 32;
-    G.barF[0] = saddr(&bars[3 * G.g + 0]);
-    G.barF[1] = saddr(&bars[3 * G.g + 1]);
-    G.barB = saddr(&bars[3 * G.g + 2]);
+    G.barF[0] = saddr(&bars[4 * G.g + 0]);
+    G.barF[1] = saddr(&bars[4 * G.g + 1]);
+    G.barB = saddr(&bars[4 * G.g + 2]);
+    G.barR = saddr(&bars[4 * G.g + 3]);
     G.d1[0] = tmem + (uint32_t)(G.g * 256);
     G.d1[1] = tmem + (uint32_t)(G.g * 256 + 64);
     G.d2 = tmem + (uint32_t)(G.g * 256 + 128);
+    G.stash = tmem + (uint32_t)(G.g * 256 + 160);   // 96 free columns: x, grad, w
     G.phF = 0;
     G.phB = 0;
+    G.phR = 0;
     G.dead = false;
     G.smem = smem;
     unsigned char* st = smem + kOffStat + G.g * kStatBytes;
@@ -476,8 +521,19 @@ oais_sweep_tc_kernel(const TcParams P)
                 z[i] = z[i] + h * gpi;
                 dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
             }
+            // park x, grad and w in the group's free TMEM columns while the evaluation
+            // runs (registers go to the epilogue), then bring them back
+            const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
+            tmem_st32(G.stash + lane_off, x);
+            tmem_st32(G.stash + lane_off + 32, gl);
+            tmem_st32(G.stash + lane_off + 64, z);
+            tmem_wait_st();
             float glp[kD];
             const float ellp = tc_eval(G, P, xp, glp);
+            __syncwarp();
+            tmem_ld32f(G.stash + lane_off, x);
+            tmem_ld32f(G.stash + lane_off + 32, gl);
+            tmem_ld32f(G.stash + lane_off + 64, z);
             float rev = 0.0f;
 #pragma unroll
             for (int i = 0; i < kD; ++i) {
