@@ -54,7 +54,8 @@ typedef enum { OAIS_DT_F64 = 0, OAIS_DT_F32 = 1 } oais_dtype;
 
 typedef struct {
     int32_t kind;       /* oais_target_kind */
-    int32_t d;          /* state dimension, 1 <= d <= 32 (GAUSS: <= 16) */
+    int32_t d;          /* state dimension, 1 <= d <= 32 (GAUSS: <= 16); the streamed
+                           tensor-core form takes LOGREG and LINREG up to d = 256 */
     int32_t n;          /* rows of X (LOGREG, LINREG), mixture components (GMM, <= 16); 0 for GAUSS */
     int32_t dtype;      /* oais_dtype of X and y: GAUSS runs in F64 and takes F64 mu;
                            the other families run in F32 and take F32 or F64 input */
@@ -64,15 +65,33 @@ typedef struct {
     double p0;          /* GAUSS: likelihood sigma; GMM: component variance; LINREG: noise sigma */
     int32_t on_device;  /* 0: X, y are host memory, copied at init.  1: device memory, also copied
                            (to the padded device layout); the caller may free them after init */
-    int32_t contraction;/* how X x is computed: OAIS_CONTRACT_FP32 (CUDA cores, fp32 data) or
-                           OAIS_CONTRACT_BF16_TC (tcgen05 tensor cores; X is rounded once to
-                           bf16 and the sampler targets that X~; states and residuals are split
-                           into two bf16 terms so products keep fp32 accuracy).  The tensor-core
-                           form is built for LOGREG with d <= 32, n <= 2048 and MALA moves in
-                           oais_round; other combinations return OAIS_EUNSUPPORTED at init. */
+    int32_t contraction;/* how X x is computed (oais_contraction):
+                           OAIS_CONTRACT_FP32: CUDA cores, fp32 data.
+                           OAIS_CONTRACT_BF16_TC: tcgen05 tensor cores with X rounded once to
+                             bf16 (the sampler targets that X~).  LOGREG with d <= 32,
+                             n <= 2048 and MALA runs with X~ resident in shared memory (states
+                             and residuals split into two bf16 terms); every other LOGREG
+                             (MALA) or LINREG (MALA, HMC) problem with d <= 256 runs the
+                             streamed form below.
+                           OAIS_CONTRACT_BF16_TC_STREAM: always the streamed form: X~ is
+                             streamed from device memory in chunks, held as f16 (exact for
+                             bf16 values of magnitude >= 2^-17; smaller ones take the nearest
+                             f16), states and residuals split into two f16 terms (relative
+                             error ~2^-22); any n, d <= 256, LOGREG (MALA) or LINREG (MALA,
+                             HMC).
+                           The tensor-core forms run the OAIS sweep (oais_round and the shard
+                           calls) and, for the streamed form, oais_potential; resampling
+                           rounds (oasmc_round) and oais_ctx_sweep use the CUDA-core form,
+                           which exists for d <= 32 (they return OAIS_EUNSUPPORTED above
+                           that).  Other combinations
+                           return OAIS_EUNSUPPORTED at init. */
 } oais_target;
 
-typedef enum { OAIS_CONTRACT_FP32 = 0, OAIS_CONTRACT_BF16_TC = 1 } oais_contraction;
+typedef enum {
+    OAIS_CONTRACT_FP32 = 0,
+    OAIS_CONTRACT_BF16_TC = 1,
+    OAIS_CONTRACT_BF16_TC_STREAM = 2
+} oais_contraction;
 
 typedef enum { OAIS_RWMH = 0, OAIS_MALA = 1, OAIS_HMC = 2 } oais_move_kind;
 
@@ -213,7 +232,9 @@ oais_status oais_grad_logZ(oais_ctx* ctx, double* grad);
  * used inside MALA and HMC): ell[n] = log L(x_n) and, if d_grad != NULL,
  * grad[i][n] = d log L / d x_i at x_n.  d_x, d_grad: device [d][N] in the family's precision
  * (double for GAUSS, float otherwise); d_ell: device [N] doubles.  Ordered on `stream`.
- * For the tensor-core contraction this uses the fp32 CUDA-core evaluation of X. */
+ * With the streamed tensor-core contraction the evaluation is the streamed kernel's own
+ * (X~, two-term f16 operands) and the call waits for it; with the resident tensor-core form
+ * it is the fp32 CUDA-core evaluation of X. */
 oais_status oais_potential(oais_ctx* ctx, const void* d_x, int64_t N, double* d_ell, void* d_grad,
                            void* stream);
 

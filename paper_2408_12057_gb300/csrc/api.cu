@@ -191,12 +191,22 @@ static size_t elt_bytes(int kind) { return kind == kGauss ? sizeof(double) : siz
 
 struct Layout {
     size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, lse, lse_scr, status;
-    size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, tc_img, tc_y, total;
+    size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, tc_img, tc_y;
+    size_t tcs_img, tcs_state, total;
 };
 
-static int records_per_step(int64_t N) { return std::max(sweep_grid(N), tc_records(N)); }
+// which sweep form a target runs: 0 CUDA cores, 1 resident tensor-core, 2 streamed tensor-core
+static int sweep_form(const oais_target* tg, const oais_move* mv)
+{
+    if (tg->contraction == OAIS_CONTRACT_BF16_TC_STREAM) return 2;
+    if (tg->contraction != OAIS_CONTRACT_BF16_TC) return 0;
+    if (tg->kind == kLogreg && tg->d <= 32 && tg->n <= tc_max_rows() && mv->kind == OAIS_MALA) return 1;
+    return 2;
+}
 
-static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
+static int records_per_step(int64_t N) { return std::max(std::max(sweep_grid(N), tc_records(N)), tcs_tiles(N)); }
+
+static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t N, int T_max)
 {
     Layout L{};
     const int n_pad = (tg->n + 3) & ~3;
@@ -232,9 +242,13 @@ static Layout layout(const oais_target* tg, int D, int64_t N, int T_max)
     L.ess_trace = take(sizeof(double) * T_max);
     L.resampled = take(sizeof(int) * T_max);
     L.anc = take(sizeof(int64_t) * N);
-    const bool tc = tg->contraction == OAIS_CONTRACT_BF16_TC;
-    L.tc_img = take(tc ? (size_t)tc_image_bytes() : 0);
-    L.tc_y = take(tc ? (size_t)tc_max_rows() / 8 : 0);
+    const int form = sweep_form(tg, mv);
+    L.tc_img = take(form == 1 ? (size_t)tc_image_bytes() : 0);
+    L.tc_y = take(form == 1 ? (size_t)tc_max_rows() / 8 : 0);
+    TcsPlan tp;
+    if (form == 2) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0);
+    L.tcs_img = take(form == 2 ? tp.img_bytes : 0);
+    L.tcs_state = take(form == 2 ? sizeof(float) * 5 * (size_t)tp.dp * tcs_tiles(N) * 128 : 0);
     L.total = off;
     return L;
 }
@@ -251,12 +265,22 @@ static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais
     if (tg->kind == kGmm && tg->n > GmmTarget<float, 16>::kMaxK)
         return fail(ctx, OAIS_EUNSUPPORTED, "at most 16 mixture components");
     if (tg->dtype != OAIS_DT_F64 && tg->dtype != OAIS_DT_F32) return fail(ctx, OAIS_EINVAL, "bad dtype");
-    if (tg->contraction != OAIS_CONTRACT_FP32 && tg->contraction != OAIS_CONTRACT_BF16_TC)
+    if (tg->contraction < OAIS_CONTRACT_FP32 || tg->contraction > OAIS_CONTRACT_BF16_TC_STREAM)
         return fail(ctx, OAIS_EINVAL, "bad contraction");
-    if (tg->contraction == OAIS_CONTRACT_BF16_TC &&
-        (tg->kind != kLogreg || tg->d > 32 || tg->n > tc_max_rows() || mv->kind != OAIS_MALA))
-        return fail(ctx, OAIS_EUNSUPPORTED,
-                    "the tensor-core contraction is built for LOGREG, d <= 32, n <= 2048, MALA");
+    if (tg->contraction != OAIS_CONTRACT_FP32) {
+        const bool fam = (tg->kind == kLogreg && mv->kind == OAIS_MALA) ||
+                         (tg->kind == kLinreg && (mv->kind == OAIS_MALA || mv->kind == OAIS_HMC));
+        if (!fam || tg->d > 256)
+            return fail(ctx, OAIS_EUNSUPPORTED,
+                        "the tensor-core contraction is built for LOGREG (MALA) and LINREG (MALA, HMC), d <= 256");
+        if (sweep_form(tg, mv) == 2) {
+            const TcsPlan tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0);
+            const int Le = mv->kind == OAIS_HMC ? mv->leapfrog : 1;
+            const double chunks = (1.0 + (double)T_max * mv->moves * Le) * tp.nch;
+            if (!tp.ok || chunks >= 4294967295.0)
+                return fail(ctx, OAIS_EUNSUPPORTED, "streamed tensor-core form: size out of range");
+        }
+    }
     if (tg->kind == kGauss && tg->dtype != OAIS_DT_F64)
         return fail(ctx, OAIS_EINVAL, "the Gaussian family takes float64 mu");
     if (mv->kind < 0 || mv->kind > 2 || mv->moves < 1 || (mv->kind == OAIS_HMC && mv->leapfrog < 1))
@@ -264,7 +288,8 @@ static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais
     if (N < 1 || N > 0x7FFFFFFFLL) return fail(ctx, OAIS_EINVAL, "N out of range");
     if (T_max < 1 || T_max > (1 << 24)) return fail(ctx, OAIS_EINVAL, "T_max out of range");
     *D = padded_width(tg->kind, tg->d);
-    if (*D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "dimension not built for this family");
+    // the streamed tensor-core form needs no CUDA-core width (D = 0: no CUDA-core copy of X)
+    if (*D == 0 && sweep_form(tg, mv) != 2) return fail(ctx, OAIS_EUNSUPPORTED, "dimension not built for this family");
     return OAIS_OK;
 }
 
@@ -312,7 +337,7 @@ oais_status oais_workspace_bytes(const oais_target* tg, const oais_move* mv, int
     oais_status st = check_target(nullptr, tg, mv, N, T_max, &D);
     if (st != OAIS_OK) return st;
     if (!bytes) return fail(nullptr, OAIS_EINVAL, "null bytes");
-    *bytes = layout(tg, D, N, T_max).total;
+    *bytes = layout(tg, mv, D, N, T_max).total;
     return OAIS_OK;
 }
 
@@ -350,7 +375,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     if (eps) ctx->eps.assign(eps, eps + T);
     else ctx->eps.assign(T, 0.5 / std::sqrt((double)tg->d));
 
-    Layout L = layout(tg, D, N, T_max);
+    Layout L = layout(tg, mv, D, N, T_max);
     if (workspace) {
         if (ws_bytes < L.total) { delete ctx; return fail(nullptr, OAIS_ENOMEM, "workspace too small"); }
         ctx->ws = workspace;
@@ -404,14 +429,28 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     } else {
         const int nr = tg->kind == kGmm ? tg->n : dt.n_pad;
         std::vector<float> Xp((size_t)nr * D, 0.0f), yp(dt.n_pad, 0.0f);
-        for (int r = 0; r < tg->n; ++r)
-            for (int i = 0; i < tg->d; ++i) Xp[(size_t)r * D + i] = (float)Xh[(size_t)r * tg->d + i];
-        e = cudaMemcpy(dt.X, Xp.data(), sizeof(float) * Xp.size(), cudaMemcpyHostToDevice);
+        if (D > 0) {   // the CUDA-core copy of X (absent when only the streamed form exists)
+            for (int r = 0; r < tg->n; ++r)
+                for (int i = 0; i < tg->d; ++i) Xp[(size_t)r * D + i] = (float)Xh[(size_t)r * tg->d + i];
+            e = cudaMemcpy(dt.X, Xp.data(), sizeof(float) * Xp.size(), cudaMemcpyHostToDevice);
+        }
         if (e == cudaSuccess && dt.y) {
             for (int r = 0; r < tg->n; ++r) yp[r] = (float)yh[r];
             e = cudaMemcpy(dt.y, yp.data(), sizeof(float) * yp.size(), cudaMemcpyHostToDevice);
         }
-        if (e == cudaSuccess && tg->contraction == OAIS_CONTRACT_BF16_TC) {
+        if (e == cudaSuccess && sweep_form(tg, mv) == 2) {
+            std::vector<float> Xf((size_t)tg->n * tg->d), yf(tg->n);
+            for (size_t i = 0; i < Xf.size(); ++i) Xf[i] = (float)Xh[i];
+            for (int r = 0; r < tg->n; ++r) yf[r] = (float)yh[r];
+            const TcsPlan tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0);
+            std::vector<unsigned char> img;
+            tcs_prepare(tp, tg->kind, Xf.data(), yf.data(), tg->n, tg->d, img);
+            dt.tcs = true;
+            dt.tcs_img = b + L.tcs_img;
+            dt.tcs_state = reinterpret_cast<float*>(b + L.tcs_state);
+            e = cudaMemcpy(dt.tcs_img, img.data(), img.size(), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess && sweep_form(tg, mv) == 1) {
             std::vector<float> Xf((size_t)tg->n * tg->d), yf(tg->n);
             for (size_t i = 0; i < Xf.size(); ++i) Xf[i] = (float)Xh[i];
             for (int r = 0; r < tg->n; ++r) yf[r] = (float)yh[r];
@@ -475,6 +514,7 @@ oais_status oais_ctx_sweep(oais_ctx* ctx, int32_t T, const double* d_beta, const
     if (T < 1 || N < 1 || !d_beta || !d_eps || !d_logw || !d_ell || !d_x || !d_partials || !d_status)
         return fail(ctx, OAIS_EINVAL, "bad arguments to oais_ctx_sweep");
     if (n_offset < 0 || n_offset + N > 0xFFFFFFFFLL) return fail(ctx, OAIS_EINVAL, "particle index out of range");
+    if (ctx->dt.D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "no CUDA-core form for this dimension");
     SweepParams P = make_params(ctx, T, d_beta, d_eps, seed, tag, n_offset, N, d_logw, d_ell, d_x, d_partials,
                                 d_status);
     CK(launch_sweep(ctx->dt, ctx->mv.kind, P, static_cast<cudaStream_t>(stream)));
@@ -591,9 +631,14 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
                                     ctx->d_logw, ctx->d_ell, ctx->d_x, ctx->d_parts, ctx->d_status);
         CK(cudaEventRecord(ctx->ev0, s));
         if (ctx->dt.tc) CK(launch_sweep_tc(P, ctx->dt.tc_img, ctx->dt.tc_ybits, ctx->dt.n, ctx->dt.d, s));
+        else if (ctx->dt.tcs)
+            CK(launch_sweep_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0), ctx->dt.kind, P, ctx->dt.tcs_img,
+                                ctx->dt.tcs_state, ctx->mv.kind, ctx->mv.leapfrog, ctx->dt.p0, ctx->dt.n,
+                                ctx->dt.d, s));
         else CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
         CK(cudaEventRecord(ctx->ev1, s));
-        CK(launch_merge_stats(ctx->d_parts, ctx->dt.tc ? tc_records(ctx->N) : grid, T,
+        const int records = ctx->dt.tc ? tc_records(ctx->N) : (ctx->dt.tcs ? tcs_tiles(ctx->N) : grid);
+        CK(launch_merge_stats(ctx->d_parts, records, T,
                               1.0 / ((double)ctx->N * ctx->mv.moves), ctx->d_log_ghat, ctx->d_accept, s));
         CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
         double lse[2];
@@ -622,6 +667,7 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         se = std::sqrt(std::max(0.0, 1.0 / ess - 1.0 / (double)ctx->N));
     } else {
         if (ctx->N_total != ctx->N) return fail(ctx, OAIS_EUNSUPPORTED, "ASMC resamples globally: no shards");
+        if (ctx->dt.D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "resampling rounds need the CUDA-core form (d <= 32)");
         CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(AsmcState), s));
         StepParams P = make_step_params(ctx, T, tag);
         const bool grad = ctx->mv.kind != OAIS_RWMH;
@@ -922,6 +968,22 @@ oais_status oais_potential(oais_ctx* ctx, const void* d_x, int64_t N, double* d_
 {
     if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
     if (!d_x || !d_ell || N < 1) return fail(ctx, OAIS_EINVAL, "bad arguments to oais_potential");
+    if (ctx->dt.tcs) {
+        if (N > 0xFFFFFFFFLL) return fail(ctx, OAIS_EINVAL, "N out of range");
+        CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), static_cast<cudaStream_t>(stream)));
+        CK(launch_potential_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0), ctx->dt.kind, ctx->dt.tcs_img,
+                                static_cast<const float*>(d_x), N, d_ell, static_cast<float*>(d_grad), ctx->dt.p0,
+                                ctx->dt.n, ctx->dt.d, ctx->d_status, ctx->dt.tcs_state,
+                                (int64_t)tcs_tiles(ctx->N) * 128, static_cast<cudaStream_t>(stream)));
+        unsigned status = 0;
+        CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           static_cast<cudaStream_t>(stream)));
+        CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+        if (status & 2u) return fail(ctx, OAIS_ETIMEOUT, "a tensor-core completion wait gave up");
+        if (status & 4u) return fail(ctx, OAIS_ECUDA, "shared memory base not 1024-byte aligned");
+        return OAIS_OK;
+    }
+    if (ctx->dt.D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "no CUDA-core form for this dimension");
     PotentialParams P{N, d_x, d_ell, d_grad};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (ctx->dt.kind) {

@@ -20,7 +20,35 @@ struct DevTarget {
     bool tc = false;     // tensor-core form: BF16 image of X and label bits below
     void* tc_img = nullptr;
     uint32_t* tc_ybits = nullptr;
+    bool tcs = false;    // streamed tensor-core form: chunk images of X~ (and y), particle state
+    void* tcs_img = nullptr;
+    float* tcs_state = nullptr;
 };
+
+// Streamed tensor-core sweep (sweep_tcs.cu): sizes of one configuration.  dp = d padded to
+// 16, 32 or a multiple of 64 (at most 256); X~ is cut into nch chunks of `chunk` rows, each
+// a stage image of stage_bytes (X~ lines in the swizzled K-major layout, then y for linear
+// regression); shared memory holds the A operand (two terms) and `stages` chunk buffers;
+// TMEM holds two forward accumulators, two per-row factor buffers and the gradient sum.
+struct TcsPlan {
+    int dp = 0, chunk = 0, nch = 0, stages = 0, tmem_cols = 0;
+    uint32_t y_off = 0, stage_bytes = 0, off_x = 0, off_misc = 0, smem = 0;
+    size_t img_bytes = 0;
+    bool ok = false;
+};
+TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages);
+void tcs_prepare(const TcsPlan& L, int kind, const float* X, const float* y, int n, int d,
+                 std::vector<unsigned char>& img);
+int tcs_tiles(int64_t N);
+// state: 5 arrays [dp][tiles * 128] fp32 (accepted x, its gradient, proposal, momentum,
+// drained gradient sum)
+cudaError_t launch_sweep_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
+                             int move, int leapfrog, double p0, int n, int d, cudaStream_t s);
+// one evaluation of log L and grad log L (grad may be null) at states x [d][N] with the
+// streamed tensor-core contraction
+cudaError_t launch_potential_tcs(const TcsPlan& L, int kind, const void* img, const float* x, int64_t N,
+                                 double* ell, float* grad, double p0, int n, int d, unsigned* status,
+                                 float* state, int64_t state_particles, cudaStream_t s);
 
 // tensor-core logistic sweep (sweep_tc.cu)
 int tc_grid(int64_t N);

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tcgen05.cuh"
 #include "../../include/oais.h"
 
 namespace oais {
@@ -54,117 +55,10 @@ constexpr int kSmemBytes = kOffStat + kGroups * kStatBytes;
 constexpr int kTmemCols = 512;               // group g: D1[0], D1[1] at 256 g + {0, 64}, D2 at 256 g + 128
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    return ok;
-}
-__device__ __forceinline__ uint64_t globaltimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// bounded wait on an MMA-completion barrier: false after ~2 s without completion
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer() - t0 > 2000000000ull) return false;
-    return true;
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void group_sync(int g)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate)
-{
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "setp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                 ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                   "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-                   "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-                   "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&f)[32])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-                 "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-                 "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
-                 ::"r"(taddr), "f"(f[0]), "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]), "f"(f[6]),
-                   "f"(f[7]), "f"(f[8]), "f"(f[9]), "f"(f[10]), "f"(f[11]), "f"(f[12]), "f"(f[13]), "f"(f[14]),
-                   "f"(f[15]), "f"(f[16]), "f"(f[17]), "f"(f[18]), "f"(f[19]), "f"(f[20]), "f"(f[21]),
-                   "f"(f[22]), "f"(f[23]), "f"(f[24]), "f"(f[25]), "f"(f[26]), "f"(f[27]), "f"(f[28]),
-                   "f"(f[29]), "f"(f[30]), "f"(f[31])
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld32f(uint32_t taddr, float (&f)[32])
-{
-    uint32_t v[32];
-    tmem_ld32(taddr, v);
-    tmem_wait_ld();
-#pragma unroll
-    for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(v[i]);
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Shared-memory matrix descriptor (tcgen05): start >> 4, leading / stride byte offsets >> 4,
-// descriptor version 1, swizzle layout in the top 3 bits (2 = 128B, 4 = 64B).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint64_t layout)
-{
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16)
-         | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (layout << 61);
-}
-constexpr uint64_t kSW128 = 2, kSW64 = 4;
-
-// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
-// A/B major-ness (bit 15 / 16: 1 = MN-major), N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn_major ? 1u : 0u) << 16)
-         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 constexpr uint32_t kIdescFwd = idesc_bf16(128, kChunk, false);
 constexpr uint32_t kIdescBwd = idesc_bf16(128, kD, true);
+
+__device__ __forceinline__ void group_sync(int g) { named_sync(1 + g, kGroupThreads); }
 
 // Two-term bf16 split of a pair of floats, v = hi + lo: hi = v with the low 16 bits of its
 // fp32 word cleared (a bf16 value), lo = v - hi (exact in fp32, |lo| < 2^-7 |v|); lo is
@@ -179,26 +73,6 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
     const float la = __fsub_rn(a, ha), lb = __fsub_rn(b, hb);
     hi = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
     lo = __byte_perm(__float_as_uint(la) + 0x8000u, __float_as_uint(lb) + 0x8000u, 0x7632);
-}
-
-// special-function unit, flush-to-zero forms (documented PTX approximations)
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2_approx(float x)
-{
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
 }
 
 struct TcParams {
@@ -249,7 +123,7 @@ __device__ __forceinline__ void issue_fwd(const Group& G, int c, int buf)
         for (int kk = 0; kk < kD / 16; ++kk) {
             const uint64_t a = sdesc(aa + kk * 32, 16, 512, kSW64);
             const uint64_t b = sdesc(xb + c * kChunk * 64 + kk * 32, 16, 512, kSW64);
-            mma_bf16(G.d1[buf], a, b, kIdescFwd, (hl == 0 && kk == 0) ? 0u : 1u);
+            mma_f16(G.d1[buf], a, b, kIdescFwd, (hl == 0 && kk == 0) ? 0u : 1u);
         }
     }
     mma_commit(G.barF[buf]);
@@ -267,7 +141,7 @@ __device__ __forceinline__ void issue_bwd(const Group& G, int c, bool first)
         for (int kk = 0; kk < kChunk / 16; ++kk) {
             const uint64_t a = sdesc(ra + kk * 32, 16, 1024, kSW128);
             const uint64_t b = sdesc(xb + (c * kChunk + kk * 16) * 64, 8192, 512, kSW64);
-            mma_bf16(G.d2, a, b, kIdescBwd, (first && hl == 0 && kk == 0) ? 0u : 1u);
+            mma_f16(G.d2, a, b, kIdescBwd, (first && hl == 0 && kk == 0) ? 0u : 1u);
         }
     }
     mma_commit(G.barB);
@@ -380,20 +254,6 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
     tc_before_sync();
     const float ln2 = 0.69314718055994531f;
     return 0.5f * twice_min + ln2 * logs2 + (float)(nch * kChunk - P.n) * ln2;
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish()
-{
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
 // the group's 4 warps merge their (m, s) moment pieces and acceptance counts (fixed order)

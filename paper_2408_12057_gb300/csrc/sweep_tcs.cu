@@ -1,0 +1,897 @@
+// sweep_tcs.cu -- the loop-swapped OAIS sweep (Sec. 5.1.2) with the likelihood contraction on
+// the tensor cores and the data streamed from global memory: any number of rows n, state
+// dimension up to 256, logistic regression and Bayesian linear regression, MALA or HMC moves
+// (Sec. 2.1.1 kernel family, identity mass).
+//
+// A CTA owns a tile of 128 particles (the tcgen05 M = 128 lane layout).  For each evaluation
+// of log L and grad log L at the tile's current positions P it streams X in chunks of CHUNK
+// rows:
+//   forward   Z   = P X_c^T          (M = 128, N = CHUNK, K = d)        into TMEM D1[c % 2]
+//   epilogue  per element: linear regression r = y - z, sum r^2;
+//             logistic (label sign folded into X) u = s z, log sigmoid(u), sigmoid(-u)
+//   backward  G  += R X_c            (M = 128, N = d,     K = CHUNK)    into TMEM D2
+// Operands are f16: the data X~ (X rounded to bf16, then stored exactly as f16; values below
+// 2^-17 in magnitude take the nearest f16) and the two-term split v = hi + lo of the
+// positions and of the per-row factors R (hi = f16(v), lo = f16(v - hi): relative error about
+// 2^-22, far below the posterior scale even at n = 50 000).  Accumulation is fp32 in TMEM;
+// sums over rows of the epilogue terms are fp32 per chunk and fp64 across chunks.
+//
+// Roles (320 threads):
+//   warps 0-7  particle warps: thread (warp w, lane l) owns particle 32 (w % 4) + l (its TMEM
+//              lane) and the coordinate half w / 4 and column half w / 4 of every chunk
+//   warp 8     one thread issues the MMAs and their commits
+//   warp 9     one thread streams the chunk images (X~ in the swizzled shared-memory layout and
+//              y) with bulk copies into a ring of STAGES buffers
+// Synchronisation is by mbarriers; every wait is bounded (2 s), after which the CTA sets
+// status bit 2, stops issuing work and runs to its end without blocking.
+//
+// Particle state between evaluations lives in global memory (L2): accepted position and
+// gradient, proposal position and momentum, [d_pad][N_pad] fp32 each, read and written only
+// by the thread that owns the (particle, coordinate) pair.
+#include <cuda_fp16.h>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "tcgen05.cuh"
+#include "../../include/oais.h"
+
+namespace oais {
+namespace tcs {
+using namespace oais::tc;
+
+constexpr int kTile = 128;
+constexpr int kEpiThreads = 256;
+constexpr int kThreads = kEpiThreads + 64;
+constexpr int kMmaWarp = 8, kLoadWarp = 9;
+constexpr int kSlice = 8;   // coordinates per state-update step (one 16-byte f16 chunk)
+// The tensor core rounds each accumulation toward zero, so a long running sum in one TMEM
+// accumulator drifts toward zero by about half an ulp per MMA (a relative shrink of ~1e-4
+// after the ~6000 backward MMAs of a 50 000-row evaluation).  The gradient sum is therefore
+// cut into segments of about kSegMmas MMAs: at the end of a segment the particle threads add
+// D2 into an fp32 sum in memory (round to nearest) and the next segment restarts D2.
+constexpr int kSegMmas = 256;
+
+// ---------------------------------------------------------------------------------------
+// K-major operand layout in shared memory: rows of `kw` 16-bit elements (kw = 64 with the
+// 128-byte swizzle when the K extent is a multiple of 64, else 32 / 16 with the 64 / 32-byte
+// swizzle); K beyond 64 is split into slabs of `rows` lines each.  The swizzle permutes the
+// 16-byte chunks of a line by the line index (bits 4-6 of the address XOR bits 7-9 for
+// 128B, bits 4-5 XOR 7-8 for 64B, bit 4 XOR bit 7 for 32B).  The same bytes read as an
+// MN-major operand (N along the line) give the backward's B.
+// ---------------------------------------------------------------------------------------
+struct KLayout {
+    int kw;      // elements per line
+    int lb;      // bytes per line
+    int mode;    // 0: 128B, 1: 64B, 2: 32B swizzle
+};
+__host__ __device__ constexpr KLayout klayout(int k_extent)
+{
+    return KLayout{k_extent >= 64 ? 64 : k_extent, 2 * (k_extent >= 64 ? 64 : k_extent),
+                   k_extent >= 64 ? 0 : (k_extent == 32 ? 1 : 2)};
+}
+// rows per chunk: 64, or 32 when d_pad = 256 (shared memory)
+__host__ __device__ constexpr int chunk_rows(int) { return 64; }
+// TMEM columns: D1[2] (forward accumulators), R[2] (per-row factors, hi | lo, f16 pairs),
+// D2 (gradient accumulator, d_pad columns)
+constexpr int kColD1 = 0, kColR = 128, kColD2 = 256;
+// byte offset of the 16-byte chunk holding elements [k0, k0 + 8) of `row`
+__host__ __device__ inline uint32_t kmaj_off(int row, int k0, int rows, const KLayout& L)
+{
+    const int slab = k0 / L.kw;
+    const int line = slab * rows + row;
+    const int c = (k0 % L.kw) >> 3;
+    const int sw = L.mode == 0 ? (line & 7) : (L.mode == 1 ? ((line >> 1) & 3) : ((line >> 2) & 1));
+    return (uint32_t)line * (uint32_t)L.lb + (uint32_t)((c ^ sw) << 4);
+}
+__host__ __device__ constexpr uint64_t layout_code(const KLayout& L)
+{
+    return L.mode == 0 ? kSW128 : (L.mode == 1 ? kSW64 : kSW32);
+}
+
+struct Params {
+    SweepParams sp;
+    const unsigned char* img;   // [nch][stage_bytes] chunk images
+    float* xa;                  // accepted positions    [dp][Np]
+    float* ga;                  // grad log L at xa      [dp][Np]
+    float* xp;                  // proposal / trajectory [dp][Np]
+    float* mom;                 // HMC momentum; MALA: z + (eps/2) grad log pi(x)  [dp][Np]
+    float* gs;                  // drained part of the running gradient sum G      [dp][Np]
+    int64_t Np;
+    int seg;                    // chunks per gradient segment (see kSegMmas)
+    int n, d, dp, nch, stages;
+    uint32_t stage_bytes, y_off;
+    uint32_t off_x, off_misc;   // shared-memory regions (A starts at 0)
+    uint32_t tmem_cols;
+    int move, leapfrog;
+    // potential mode (one evaluation at given states, no sweep): x_in [d][N], outputs
+    // ell_pot [N] and grad_pot [d][N] (may be null)
+    const float* x_in;
+    double* ell_pot;
+    float* grad_pot;
+    int64_t pstride;            // row stride of x_in and grad_pot
+    double log_norm;            // linear regression: n (log sigma + log(2 pi) / 2)
+    float gscale;               // grad log L = gscale * G (1 / sigma^2 or 1)
+    float half_inv_var;         // linear regression: 1 / (2 sigma^2)
+};
+
+// misc region: barriers, TMEM address, abort flag, exchange buffers, moment scratch
+struct Misc {
+    uint64_t xfull[8], xempty[8];
+    uint64_t d1full[2], d1empty[2], rfull[2], rempty[2];
+    uint64_t afull, d2full, done, d2seg, d2drained;
+    uint32_t tmem;
+    volatile int abort;
+    double xl[2][kTile];        // per coordinate half: partial log-likelihood
+    float4 xm[2][kTile];        // per coordinate half: partial sums of the MH ratio
+    double s_m[2][4][3];
+    float s_s[2][4][3];
+    unsigned s_acc[2][4];
+};
+
+// f16 two-term split of a pair: hi = f16(v), lo = f16(v - hi)
+__device__ __forceinline__ void split_pair_h(float a, float b, uint32_t& hi, uint32_t& lo)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ void normals8(const Rng& rng, uint32_t n, uint32_t t, uint32_t k, int d, int i0,
+                                         float (&z)[kSlice])
+{
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int j = i0 / 4 + b;
+        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (4 * j < d) box_muller4(rng.block(n, t, k, (uint32_t)j), v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) z[4 * b + q] = (4 * j + q < d) ? v[q] : 0.0f;
+    }
+}
+
+template <int DP>
+struct Thread {
+    static constexpr int CHUNK = chunk_rows(DP);
+    static constexpr int HC = CHUNK / 2;   // columns of a chunk per thread
+    static constexpr int DH = DP / 2;      // coordinates per thread
+    unsigned char* smem;
+    Misc* M;
+    const Params* P;
+    int p, h, q, lane;
+    uint32_t lane_off;
+    uint32_t tmem;  // TMEM base (lane 0, column 0)
+    uint32_t d2;
+    uint32_t g;     // chunks consumed
+    uint32_t e;     // evaluations done
+    int xs;         // stage of chunk g
+    uint32_t xph;   // phase of that stage
+    uint32_t sph;   // phase of the segment barrier
+    bool drained;   // the last evaluation drained D2 at least once
+    float* GS;      // this particle's drained gradient sum (stride Np)
+
+    __device__ bool wait(uint64_t* bar, uint32_t parity)
+    {
+        if (M->abort) return false;
+        if (mbar_wait(saddr(bar), parity, &M->abort)) return true;
+        M->abort = 1;
+        atomicOr(P->sp.status, 2u);
+        return false;
+    }
+
+    // one 8-coordinate slice of the tile's positions into the A operand (both terms)
+    __device__ void write_a(int i0, const float (&v)[kSlice])
+    {
+        constexpr KLayout L = klayout(DP);
+        const uint32_t off = kmaj_off(p, i0, kTile, L);
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) split_pair_h(v[2 * j], v[2 * j + 1], hi[j], lo[j]);
+        constexpr uint32_t a_term = (uint32_t)kTile * DP * 2;
+        *reinterpret_cast<uint4*>(smem + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(smem + a_term + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+
+    __device__ void load_grad(int i0, float (&gv)[kSlice])
+    {
+        uint32_t v[8];
+        tmem_ld8(d2 + lane_off + (uint32_t)i0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < kSlice; ++j) {
+            float gsum = __uint_as_float(v[j]);
+            if (drained) gsum += GS[(int64_t)(i0 + j) * P->Np];
+            gv[j] = P->gscale * gsum;
+        }
+    }
+
+    // end of a gradient segment: add D2 (this thread's lanes and coordinate half) into GS
+    __device__ void drain(bool first)
+    {
+        wait(&M->d2seg, sph);
+        sph ^= 1u;
+        __syncwarp();
+        tc_after_sync();
+#pragma unroll 2
+        for (int i0 = h * DH; i0 < (h + 1) * DH; i0 += kSlice) {
+            uint32_t v[8];
+            tmem_ld8(d2 + lane_off + (uint32_t)i0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < kSlice; ++j) {
+                float* q = GS + (int64_t)(i0 + j) * P->Np;
+                *q = first ? __uint_as_float(v[j]) : *q + __uint_as_float(v[j]);
+            }
+        }
+        tc_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(saddr(&M->d2drained));
+    }
+
+    // log L at the positions just written to A (this thread's half of the rows' terms summed
+    // with the other half's), leaving grad log L / gscale in D2.
+    template <int FAM>
+    __device__ double eval()
+    {
+        fence_proxy_async();
+        tc_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(saddr(&M->afull));
+        const int nch = P->nch;
+        double acc0 = 0.0, acc1 = 0.0;   // linear: sum r^2; logistic: sum (u - |u|), sum log2 q
+        float mid0 = 0.0f, mid1 = 0.0f;
+        const int seg = P->seg;
+        drained = false;
+        for (int c = 0; c < nch; ++c, ++g) {
+            const int b = g & 1;
+            const uint32_t ph = (g >> 1) & 1u;
+            wait(&M->d1full[b], ph);
+            __syncwarp();
+            tc_after_sync();
+            uint32_t v[HC];
+            const uint32_t src = tmem + (uint32_t)(kColD1 + b * CHUNK + h * HC) + lane_off;
+            if constexpr (HC == 16) tmem_ld16(src, v);
+            else tmem_ld32(src, v);
+            tmem_wait_ld();
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(saddr(&M->d1empty[b]));
+            uint32_t hi[HC / 2], lo[HC / 2];
+            float part0 = 0.0f, part1 = 0.0f;
+            if constexpr (FAM == kLinreg) {
+                wait(&M->xfull[xs], xph);   // y of this chunk is in the stage
+                const float* ys = reinterpret_cast<const float*>(smem + P->off_x + (uint32_t)xs * P->stage_bytes +
+                                                                 P->y_off) + h * HC;
+#pragma unroll
+                for (int j = 0; j < HC; j += 2) {
+                    const float r0 = ys[j] - __uint_as_float(v[j]);
+                    const float r1 = ys[j + 1] - __uint_as_float(v[j + 1]);
+                    part0 = fmaf(r0, r0, part0);
+                    part0 = fmaf(r1, r1, part0);
+                    split_pair_h(r0, r1, hi[j / 2], lo[j / 2]);
+                }
+            } else {
+                // X'_r = s_r X~_r with s_r = 2 y_r - 1, so u = s z; log sigmoid(u) =
+                // min(u, 0) + log q with q = 1 / (1 + e^-|u|), d/dz = s sigmoid(-u)
+                float prod = 1.0f;
+#pragma unroll
+                for (int j = 0; j < HC; j += 2) {
+                    float r2[2];
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const float u = __uint_as_float(v[j + w]);
+                        const float ee = ex2_approx(fabsf(u) * -1.4426950408889634f);
+                        const float qi = rcp_approx(1.0f + ee);
+                        r2[w] = u >= 0.0f ? ee * qi : qi;
+                        part0 += u - fabsf(u);
+                        prod *= qi;
+                    }
+                    if ((j & 15) == 14) { part1 += lg2_approx(prod); prod = 1.0f; }
+                    split_pair_h(r2[0], r2[1], hi[j / 2], lo[j / 2]);
+                }
+            }
+            if (++xs == P->stages) { xs = 0; xph ^= 1u; }
+            // R (two f16 terms) into TMEM, the A operand of the backward
+            wait(&M->rempty[b], ph ^ 1u);
+            __syncwarp();
+            tc_after_sync();
+            const uint32_t rcol = tmem + (uint32_t)(kColR + b * CHUNK + h * (HC / 2)) + lane_off;
+            static_assert(HC == 32, "one x16 store per term");
+            tmem_st16(rcol, hi);
+            tmem_st16(rcol + CHUNK / 2, lo);
+            tmem_wait_st();
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(saddr(&M->rfull[b]));
+            // chunk c - 1 closed a gradient segment: its backward is the last of the segment
+            if (c >= 1 && (c - 1) % seg == seg - 1) {
+                drain(!drained);
+                drained = true;
+            }
+            mid0 += part0;
+            mid1 += part1;
+            if ((c & 15) == 15) { acc0 += mid0; acc1 += mid1; mid0 = 0.0f; mid1 = 0.0f; }
+        }
+        acc0 += mid0;
+        acc1 += mid1;
+        wait(&M->d2full, e & 1u);
+        __syncwarp();
+        tc_after_sync();
+        ++e;
+        double part;
+        if constexpr (FAM == kLinreg) part = -P->half_inv_var * acc0;
+        else part = 0.5 * acc0 + 0.69314718055994531 * acc1;
+        M->xl[h][p] = part;
+        named_sync(1, kEpiThreads);
+        const double tot = M->xl[0][p] + M->xl[1][p];
+        named_sync(1, kEpiThreads);
+        if constexpr (FAM == kLinreg) return tot - P->log_norm;
+        else return tot + (double)(nch * CHUNK - P->n) * 0.69314718055994531;
+    }
+
+    // sum of this particle's four partial sums over the two coordinate halves
+    __device__ float4 combine(float4 mine)
+    {
+        M->xm[h][p] = mine;
+        named_sync(1, kEpiThreads);
+        const float4 a = M->xm[0][p], b = M->xm[1][p];
+        named_sync(1, kEpiThreads);
+        return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+    }
+};
+
+// the tile's four particle warps of half 0 merge their (m, s) moment pieces and acceptance
+// counts in a fixed order (one record per step and tile)
+__device__ __forceinline__ void tile_record(int lane, const double (*wm)[3], const float (*ws)[3],
+                                            const unsigned* wacc, StepPartial* out)
+{
+    StepPartial rec;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double m = lane < 4 ? wm[lane][i] : -INFINITY;
+        double Mx = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Mx = fmax(Mx, __shfl_xor_sync(0xFFFFFFFFu, Mx, o));
+        double v = (lane < 4 && m != -INFINITY) ? (double)ws[lane][i] * exp(m - Mx) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        rec.m[i] = Mx;
+        rec.s[i] = v;
+    }
+    unsigned a = lane < 4 ? wacc[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if (lane == 0) {
+        rec.accepted = a;
+        rec.pad = 0;
+        *out = rec;
+    }
+}
+
+template <int FAM, int DP>
+__global__ void __launch_bounds__(kThreads, 1)
+oais_sweep_tcs_kernel(const Params P)
+{
+    constexpr int CHUNK = chunk_rows(DP);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const SweepParams& S = P.sp;
+    if (saddr(smem) & 1023u) {
+        if (threadIdx.x == 0) atomicOr(S.status, 4u);
+        return;
+    }
+    Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Le = P.move == kHmc ? P.leapfrog : 1;
+    const uint32_t evals = P.x_in ? 1u : 1u + (uint32_t)S.T * (uint32_t)S.mv.K * (uint32_t)Le;
+    const uint32_t total = evals * (uint32_t)P.nch;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.stages; ++s) {
+            mbar_init(saddr(&M->xfull[s]), 1);
+            mbar_init(saddr(&M->xempty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(saddr(&M->d1full[b]), 1);
+            mbar_init(saddr(&M->d1empty[b]), kEpiThreads / 32);
+            mbar_init(saddr(&M->rfull[b]), kEpiThreads / 32);
+            mbar_init(saddr(&M->rempty[b]), 1);
+        }
+        mbar_init(saddr(&M->afull), kEpiThreads / 32);
+        mbar_init(saddr(&M->d2full), 1);
+        mbar_init(saddr(&M->done), 1);
+        mbar_init(saddr(&M->d2seg), 1);
+        mbar_init(saddr(&M->d2drained), kEpiThreads / 32);
+        M->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(saddr(&M->tmem), P.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&M->tmem);
+    const uint32_t D2 = tmem + (uint32_t)kColD2;
+    constexpr KLayout LA = klayout(DP);
+
+    if (warp == kLoadWarp) {
+        // ---------------- producer: chunk images into the stage ring ----------------
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0, issued = 0;
+            const uint32_t sbase = saddr(smem + P.off_x);
+            for (uint32_t g = 0, c = 0; g < total; ++g) {
+                if (M->abort) break;
+                if (!mbar_wait(saddr(&M->xempty[s]), ph ^ 1u, &M->abort)) {
+                    M->abort = 1;
+                    atomicOr(S.status, 2u);
+                    break;
+                }
+                mbar_arrive_expect_tx(saddr(&M->xfull[s]), P.stage_bytes);
+                bulk_g2s(sbase + (uint32_t)s * P.stage_bytes, P.img + (size_t)c * P.stage_bytes, P.stage_bytes,
+                         saddr(&M->xfull[s]));
+                ++issued;
+                if (++c == (uint32_t)P.nch) c = 0;
+                if (++s == P.stages) { s = 0; ph ^= 1u; }
+            }
+            // copies still in flight land before the CTA ends (bounded)
+            const uint32_t first = issued > (uint32_t)P.stages ? issued - P.stages : 0u;
+            for (uint32_t g = first; g < issued; ++g)
+                mbar_wait(saddr(&M->xfull[g % P.stages]), (g / P.stages) & 1u);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            constexpr uint32_t idf = idesc_kind_f16(kTile, CHUNK, false, false);
+            constexpr uint32_t idb = idesc_kind_f16(kTile, DP, false, true);
+            constexpr uint64_t ca = layout_code(LA);
+            constexpr uint32_t a_term = (uint32_t)kTile * DP * 2;
+            // descriptors of the operand bases; the K steps add constant offsets (16-byte units)
+            // to the start-address field
+            const uint64_t adesc[2] = {sdesc(saddr(smem), 16, 8 * LA.lb, ca),
+                                       sdesc(saddr(smem) + a_term, 16, 8 * LA.lb, ca)};
+            const uint32_t xbase = saddr(smem + P.off_x);
+            const int nch = P.nch, seg = P.seg, S_ = P.stages;
+            // Forwards and backwards are issued as soon as their inputs are ready, in chunk
+            // order each: forward g needs its X stage loaded, its D1 buffer read by the
+            // particle warps and (first chunk of an evaluation) the new positions in A;
+            // backward g needs R of chunk g in TMEM and (first chunk of a gradient segment)
+            // the previous segment drained.
+            uint32_t gf = 0, gb = 0;            // next forward / backward chunk
+            int sf = 0, sb = 0;                 // their X stages
+            uint32_t phf = 0;                   // phase of xfull[sf]
+            uint32_t dph = 0;                   // phase of d2drained
+            uint64_t t_last = globaltimer();
+            bool ok = true;
+            while (gb < total) {
+                bool progress = false;
+                if (gf < total && gf < gb + 2) {
+                    const uint32_t cf = gf % (uint32_t)nch, ef = gf / (uint32_t)nch;
+                    const int b = gf & 1;
+                    if ((cf != 0 || mbar_try_wait(saddr(&M->afull), ef & 1u)) &&
+                        mbar_try_wait(saddr(&M->xfull[sf]), phf) &&
+                        mbar_try_wait(saddr(&M->d1empty[b]), ((gf >> 1) & 1u) ^ 1u)) {
+                        tc_after_sync();
+                        const uint64_t xd = sdesc(xbase + (uint32_t)sf * P.stage_bytes, 16, 8 * LA.lb, ca);
+                        const uint32_t d1 = tmem + (uint32_t)(kColD1 + b * CHUNK);
+                        // the small (lo) term first: the running sum is small while it accumulates,
+                        // so only the hi term's steps round a large sum toward zero
+#pragma unroll
+                        for (int term = 1; term >= 0; --term) {
+#pragma unroll
+                            for (int kk = 0; kk < DP / 16; ++kk) {
+                                constexpr int kw = LA.kw;
+                                const int slab = 16 * kk / kw, within = (16 * kk % kw) * 2;
+                                mma_f16(d1, adesc[term] + (uint64_t)((slab * kTile * LA.lb + within) / 16),
+                                        xd + (uint64_t)((slab * CHUNK * LA.lb + within) / 16), idf,
+                                        (term == 1 && kk == 0) ? 0u : 1u);
+                            }
+                        }
+                        mma_commit(saddr(&M->d1full[b]));
+                        ++gf;
+                        if (++sf == S_) { sf = 0; phf ^= 1u; }
+                        progress = true;
+                    }
+                }
+                if (gb < gf) {
+                    const uint32_t cb = gb % (uint32_t)nch;
+                    const int b = gb & 1;
+                    const bool first = cb % (uint32_t)seg == 0;
+                    if (mbar_try_wait(saddr(&M->rfull[b]), (gb >> 1) & 1u) &&
+                        (!first || cb == 0 || mbar_try_wait(saddr(&M->d2drained), dph))) {
+                        if (first && cb != 0) dph ^= 1u;
+                        tc_after_sync();
+                        const uint64_t xd = sdesc(xbase + (uint32_t)sb * P.stage_bytes, CHUNK * LA.lb, 8 * LA.lb, ca);
+                        const uint32_t ra = tmem + (uint32_t)(kColR + b * CHUNK);
+#pragma unroll
+                        for (int term = 0; term < 2; ++term) {
+#pragma unroll
+                            for (int kk = 0; kk < CHUNK / 16; ++kk)
+                                mma_f16_ts(D2, ra + (uint32_t)(term * (CHUNK / 2) + kk * 8),
+                                           xd + (uint64_t)(kk * 16 * LA.lb / 16), idb,
+                                           (first && term == 0 && kk == 0) ? 0u : 1u);
+                        }
+                        mma_commit(saddr(&M->rempty[b]));
+                        mma_commit(saddr(&M->xempty[sb]));
+                        if (cb % (uint32_t)seg == (uint32_t)seg - 1 && cb < (uint32_t)nch - 1)
+                            mma_commit(saddr(&M->d2seg));
+                        if (cb == (uint32_t)nch - 1) mma_commit(saddr(&M->d2full));
+                        ++gb;
+                        if (++sb == S_) sb = 0;
+                        progress = true;
+                    }
+                }
+                if (progress) {
+                    t_last = globaltimer();
+                } else {
+                    if (M->abort || globaltimer() - t_last > kWaitLimitNs) { ok = false; break; }
+                }
+            }
+            if (!ok) { M->abort = 1; atomicOr(S.status, 2u); }
+            // every MMA issued so far has completed before TMEM is released (bounded)
+            mma_commit(saddr(&M->done));
+            mbar_wait(saddr(&M->done), 0u);
+        }
+    } else {
+        // ---------------- particle warps ----------------
+        Thread<DP> Th;
+        Th.smem = smem;
+        Th.M = M;
+        Th.P = &P;
+        Th.q = warp & 3;
+        Th.h = warp >> 2;
+        Th.lane = lane;
+        Th.p = 32 * Th.q + lane;
+        Th.lane_off = (uint32_t)(Th.q * 32) << 16;
+        Th.tmem = tmem;
+        Th.d2 = D2;
+        Th.g = 0;
+        Th.e = 0;
+        Th.xs = 0;
+        Th.xph = 0;
+        Th.sph = 0;
+        Th.drained = false;
+        const int p = Th.p, h = Th.h;
+        const int64_t n64 = (int64_t)blockIdx.x * kTile + p;
+        const bool active = n64 < S.N;
+        Th.GS = P.gs + n64;
+        const uint32_t n = (uint32_t)(S.n_offset + (active ? n64 : S.N - 1));
+        constexpr int dh = DP / 2;
+        const int c0 = h * dh;
+        const int64_t Np = P.Np;
+        const float sref = (float)S.ref_scale;
+        const float inv_s2 = 1.0f / (sref * sref);
+        float* XA = P.xa + n64;
+        float* GA = P.ga + n64;
+        float* XP = P.xp + n64;
+        float* MO = P.mom + n64;
+
+        if (P.x_in) {
+            // potential mode: log L and grad log L at the given states
+            const int64_t src = active ? n64 : S.N - 1;
+            for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+                float xv[kSlice];
+#pragma unroll
+                for (int j = 0; j < kSlice; ++j)
+                    xv[j] = i0 + j < P.d ? P.x_in[(int64_t)(i0 + j) * P.pstride + src] : 0.0f;
+                Th.write_a(i0, xv);
+            }
+            const double ellv = Th.template eval<FAM>();
+            for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+                float gv[kSlice];
+                Th.load_grad(i0, gv);
+                if (active && P.grad_pot) {
+#pragma unroll
+                    for (int j = 0; j < kSlice; ++j)
+                        if (i0 + j < P.d) P.grad_pot[(int64_t)(i0 + j) * P.pstride + n64] = gv[j];
+                }
+            }
+            if (active && h == 0) P.ell_pot[n64] = ellv;
+        } else {
+        // x_0 ~ eta, its log L and gradient
+        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+            float z[kSlice];
+            normals8(S.mv.rng, n, 0u, 0u, P.d, i0, z);
+#pragma unroll
+            for (int j = 0; j < kSlice; ++j) {
+                z[j] *= sref;
+                XA[(int64_t)(i0 + j) * Np] = z[j];
+            }
+            Th.write_a(i0, z);
+        }
+        double ell = Th.template eval<FAM>();
+        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+            float gv[kSlice];
+            Th.load_grad(i0, gv);
+#pragma unroll
+            for (int j = 0; j < kSlice; ++j) GA[(int64_t)(i0 + j) * Np] = gv[j];
+        }
+
+        double logw = 0.0;
+        double beta_prev = S.beta[0];
+        for (int t = 1; t <= S.T; ++t) {
+            const double beta_t = __ldg(S.beta + t);
+            const double eps_t = __ldg(S.eps + t - 1);
+            const double lg = (beta_t - beta_prev) * ell;
+            beta_prev = beta_t;
+            const int slot = t & 1;
+            if (h == 0) warp_moment_partial(logw, lg, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
+            logw += lg;
+            unsigned acc = 0;
+            const float beta = (float)beta_t, eps = (float)eps_t, he = 0.5f * eps;
+            for (int k = 0; k < S.mv.K; ++k) {
+                // proposal start: MALA x' = x + eps (z + (eps/2) grad log pi(x));
+                // HMC m = z + (eps/2) grad log pi(x), x' = x + eps m
+                float zz = 0.0f, dxx = 0.0f;
+                for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+                    float z[kSlice], xpv[kSlice];
+                    normals8(S.mv.rng, n, (uint32_t)t, (uint32_t)k, P.d, i0, z);
+#pragma unroll
+                    for (int j = 0; j < kSlice; ++j) {
+                        const int64_t o = (int64_t)(i0 + j) * Np;
+                        const float xv = XA[o], gv = GA[o];
+                        const float gpi = -xv * inv_s2 + beta * gv;
+                        const float m = z[j] + he * gpi;
+                        xpv[j] = xv + eps * m;
+                        zz += z[j] * z[j];
+                        dxx += (xpv[j] - xv) * (xpv[j] + xv);
+                        XP[o] = xpv[j];
+                        MO[o] = m;
+                    }
+                    Th.write_a(i0, xpv);
+                }
+                double ellp = 0.0;
+                float tail = 0.0f;   // MALA: |reverse noise|^2; HMC: |final momentum|^2
+                for (int l = 0; l < Le; ++l) {
+                    ellp = Th.template eval<FAM>();
+                    const bool last = l + 1 == Le;
+                    if (P.move == kHmc) {
+                        const float f = last ? he : eps;
+                        dxx = last ? 0.0f : dxx;
+                        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+                            float gv[kSlice], xpv[kSlice];
+                            Th.load_grad(i0, gv);
+#pragma unroll
+                            for (int j = 0; j < kSlice; ++j) {
+                                const int64_t o = (int64_t)(i0 + j) * Np;
+                                const float xq = XP[o];
+                                float m = MO[o] + f * (-xq * inv_s2 + beta * gv[j]);
+                                if (!last) {
+                                    xpv[j] = xq + eps * m;
+                                    XP[o] = xpv[j];
+                                    MO[o] = m;
+                                } else {
+                                    const float xv = XA[o];
+                                    tail += m * m;
+                                    dxx += (xq - xv) * (xq + xv);
+                                    xpv[j] = xq;
+                                }
+                            }
+                            if (!last) Th.write_a(i0, xpv);
+                        }
+                    } else {
+                        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+                            float gv[kSlice];
+                            Th.load_grad(i0, gv);
+#pragma unroll
+                            for (int j = 0; j < kSlice; ++j) {
+                                const int64_t o = (int64_t)(i0 + j) * Np;
+                                const float qv = MO[o] + he * (-XP[o] * inv_s2 + beta * gv[j]);
+                                tail += qv * qv;
+                            }
+                        }
+                    }
+                }
+                const float4 tot = Th.combine(make_float4(zz, dxx, tail, 0.0f));
+                // HMC: log alpha = [log pi(x') - |m'|^2/2] - [log pi(x) - |z|^2/2];
+                // MALA: log alpha = log pi(x') - log pi(x) - (|q|^2 - |z|^2) / 2
+                const float log_alpha =
+                    -0.5f * tot.y * inv_s2 + beta * (float)(ellp - ell) - 0.5f * (tot.z - tot.x);
+                const float logu = mh_log_uniform(S.mv.rng, n, (uint32_t)t, (uint32_t)k, 0.0f);
+                const bool accept = logu < log_alpha;
+                for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+                    float gv[kSlice];
+                    Th.load_grad(i0, gv);   // warp-collective: outside the branch
+                    if (accept) {
+#pragma unroll
+                        for (int j = 0; j < kSlice; ++j) {
+                            const int64_t o = (int64_t)(i0 + j) * Np;
+                            XA[o] = XP[o];
+                            GA[o] = gv[j];
+                        }
+                    }
+                }
+                if (accept) { ell = ellp; ++acc; }
+            }
+            if (h == 0) {
+                acc = active ? acc : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+                if (lane == 0) M->s_acc[slot][Th.q] = acc;
+                named_sync(2, 128);
+                if (warp == 0)
+                    tile_record(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot],
+                                S.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
+            }
+        }
+        if (active) {
+            float* xo = reinterpret_cast<float*>(S.x_out);
+            for (int i = c0; i < c0 + dh && i < P.d; ++i) xo[(size_t)i * S.N + n64] = XA[(int64_t)i * Np];
+            if (h == 0) {
+                S.logw[n64] = logw;
+                S.ell_out[n64] = ell;
+                if (!isfinite(logw) || !isfinite(ell)) atomicOr(S.status, 1u);
+            }
+        }
+        }   // sweep
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, P.tmem_cols);
+}
+
+} // namespace tcs
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+namespace {
+int padded_dim(int d)
+{
+    if (d <= 16) return 16;
+    if (d <= 32) return 32;
+    return (d + 63) / 64 * 64;
+}
+uint32_t align1024(uint32_t v) { return (v + 1023u) & ~1023u; }
+} // namespace
+
+TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages)
+{
+    TcsPlan L{};
+    L.dp = padded_dim(d);
+    L.chunk = chunk > 0 ? chunk : tcs::chunk_rows(L.dp);
+    L.nch = (n + L.chunk - 1) / L.chunk;
+    L.y_off = (uint32_t)L.chunk * L.dp * 2;
+    L.stage_bytes = align1024(L.y_off + (kind == kLinreg ? (uint32_t)L.chunk * 4 : 0u));
+    const uint32_t a_bytes = (uint32_t)tcs::kTile * L.dp * 2 * 2;
+    L.off_x = a_bytes;
+    const uint32_t limit = 227u * 1024u;
+    const uint32_t misc = (uint32_t)((sizeof(tcs::Misc) + 1023) & ~(size_t)1023);
+    int S = stages > 0 ? stages : 4;
+    while (S > 2 && L.off_x + (uint32_t)S * L.stage_bytes + misc > limit) --S;
+    L.stages = S;
+    L.off_misc = L.off_x + (uint32_t)S * L.stage_bytes;
+    L.smem = L.off_misc + (uint32_t)sizeof(tcs::Misc);
+    L.tmem_cols = 512;
+    // 512 TMEM columns leave room for one CTA per SM: make the shared memory say so too
+    if (L.tmem_cols == 512 && L.smem < 120u * 1024u) L.smem = 120u * 1024u;
+    L.img_bytes = (size_t)L.nch * L.stage_bytes;
+    L.ok = L.dp <= 256 && L.chunk == tcs::chunk_rows(L.dp) && L.smem <= limit && L.stages >= 2 && L.stages <= 8;
+    return L;
+}
+
+// X~ = f16(bf16(X)) in the stage layout (logistic: rows multiplied by the label sign), and y
+static uint16_t f16_of_bf16(float v)
+{
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even bf16 (finite inputs)
+    u &= 0xFFFF0000u;
+    float b;
+    std::memcpy(&b, &u, 4);
+    const __half h = __float2half_rn(b);
+    uint16_t r;
+    std::memcpy(&r, &h, 2);
+    return r;
+}
+
+void tcs_prepare(const TcsPlan& L, int kind, const float* X, const float* y, int n, int d,
+                 std::vector<unsigned char>& img)
+{
+    img.assign(L.img_bytes, 0);
+    const tcs::KLayout K = tcs::klayout(L.dp);
+    for (int r = 0; r < n; ++r) {
+        const int c = r / L.chunk, rr = r % L.chunk;
+        unsigned char* st = img.data() + (size_t)c * L.stage_bytes;
+        const bool neg = kind == kLogreg && !(y[r] > 0.5f);
+        for (int i = 0; i < d; ++i) {
+            uint16_t hbits = f16_of_bf16(X[(size_t)r * d + i]);
+            if (neg) hbits ^= 0x8000u;
+            const uint32_t off = tcs::kmaj_off(rr, i & ~7, L.chunk, K) + (uint32_t)(i & 7) * 2;
+            std::memcpy(st + off, &hbits, 2);
+        }
+        if (kind == kLinreg) std::memcpy(st + L.y_off + (size_t)rr * 4, &y[r], 4);
+    }
+}
+
+int tcs_tiles(int64_t N) { return (int)((N + tcs::kTile - 1) / tcs::kTile); }
+
+static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
+                              int move, int leapfrog, double p0, int n, int d, const float* x_in, double* ell_pot,
+                              float* grad_pot, int64_t pstride, cudaStream_t s, int64_t state_particles = 0)
+{
+    tcs::Params P;
+    P.sp = sp;
+    P.x_in = x_in;
+    P.ell_pot = ell_pot;
+    P.grad_pot = grad_pot;
+    P.pstride = pstride;
+    P.seg = tcs::kSegMmas / (L.chunk / 8);
+    P.img = static_cast<const unsigned char*>(img);
+    const int tiles = tcs_tiles(sp.N);
+    P.Np = state_particles > 0 ? state_particles : (int64_t)tiles * tcs::kTile;
+    // state: [xa | ga | xp | mom | gs], each [dp][Np]; the potential uses only gs
+    P.xa = state;
+    P.ga = state + (size_t)L.dp * P.Np;
+    P.xp = state + (size_t)2 * L.dp * P.Np;
+    P.mom = state + (size_t)3 * L.dp * P.Np;
+    P.gs = state + (size_t)4 * L.dp * P.Np;
+    P.n = n;
+    P.d = d;
+    P.dp = L.dp;
+    P.nch = L.nch;
+    P.stages = L.stages;
+    P.stage_bytes = L.stage_bytes;
+    P.y_off = L.y_off;
+    P.off_x = L.off_x;
+    P.off_misc = L.off_misc;
+    P.tmem_cols = (uint32_t)L.tmem_cols;
+    P.move = move;
+    P.leapfrog = leapfrog;
+    P.log_norm = kind == kLinreg ? (double)n * (std::log(p0) + 0.5 * std::log(2.0 * 3.14159265358979323846)) : 0.0;
+    P.gscale = kind == kLinreg ? (float)(1.0 / (p0 * p0)) : 1.0f;
+    P.half_inv_var = kind == kLinreg ? (float)(0.5 / (p0 * p0)) : 0.0f;
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+        if (e != cudaSuccess) return e;
+        kern<<<tiles, tcs::kThreads, L.smem, s>>>(P);
+        return cudaGetLastError();
+    };
+    if (L.chunk != tcs::chunk_rows(L.dp)) return cudaErrorInvalidValue;
+#define OAIS_TCS_DP(FAMK, DPV) case DPV: return go(tcs::oais_sweep_tcs_kernel<FAMK, DPV>);
+    if (kind == kLinreg) {
+        switch (L.dp) {
+        OAIS_TCS_DP(kLinreg, 16) OAIS_TCS_DP(kLinreg, 32) OAIS_TCS_DP(kLinreg, 64)
+        OAIS_TCS_DP(kLinreg, 128) OAIS_TCS_DP(kLinreg, 256)
+        }
+    } else {
+        switch (L.dp) {
+        OAIS_TCS_DP(kLogreg, 16) OAIS_TCS_DP(kLogreg, 32) OAIS_TCS_DP(kLogreg, 64)
+        OAIS_TCS_DP(kLogreg, 128) OAIS_TCS_DP(kLogreg, 256)
+        }
+    }
+#undef OAIS_TCS_DP
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
+                             int move, int leapfrog, double p0, int n, int d, cudaStream_t s)
+{
+    return launch_tcs(L, kind, sp, img, state, move, leapfrog, p0, n, d, nullptr, nullptr, nullptr, 0, s);
+}
+
+cudaError_t launch_potential_tcs(const TcsPlan& L, int kind, const void* img, const float* x, int64_t N,
+                                 double* ell, float* grad, double p0, int n, int d, unsigned* status,
+                                 float* state, int64_t state_particles, cudaStream_t s)
+{
+    // batches of at most state_particles (the scratch the state buffer holds)
+    const int64_t cap = state_particles / tcs::kTile * tcs::kTile;
+    if (cap < tcs::kTile) return cudaErrorInvalidValue;
+    for (int64_t b0 = 0; b0 < N; b0 += cap) {
+        SweepParams sp{};
+        sp.N = std::min(cap, N - b0);
+        sp.T = 0;
+        sp.status = status;
+        sp.mv.K = 1;
+        // the state buffer is laid out for state_particles: keep its stride
+        cudaError_t e = launch_tcs(L, kind, sp, img, state, kMala, 1, p0, n, d, x + b0, ell + b0,
+                                   grad ? grad + b0 : nullptr, N, s, state_particles);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+} // namespace oais

@@ -1,0 +1,179 @@
+"""The streamed tensor-core (tcgen05, f16 operands) sweep against the FP64 oracle.
+
+The streamed form rounds X once to bf16 and holds it as f16 (X~ = f16(bf16(X)), exact for
+bf16 values of magnitude >= 2^-17), so the oracle runs on X~.  Positions and per-row factors
+are split into two f16 terms (relative error ~2^-22), so the FP32 tolerances of the
+CUDA-core form apply: log L and log w to 1e-5 relative, states to 1e-4, and every particle
+that disagrees must have an oracle MH decision within 1e-3 of its threshold.
+
+Cases cover every shared-memory layout of the operands (d padded to 16 / 32 / 64 / 128 /
+256: 32-, 64- and 128-byte swizzles, one and several 128-byte slabs), both chunk sizes
+(64 rows, and 32 rows at d = 256), ragged row chunks and ragged particle tiles, HMC with
+several leapfrog steps and MALA, for linear and logistic regression.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2408_12057_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+oais = pytest.importorskip("paper_2408_12057_gb300.oais")
+
+REL, ABS, XREL, TIE = 1e-5, 1e-4, 1e-4, 1e-3
+
+
+def f16_of_bf16(X):
+    b = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+    return b.astype(np.float16).astype(np.float64)
+
+
+def oracle_target(pr):
+    return o.Target(pr.kind, f16_of_bf16(pr.X), pr.y, pr.ref_scale, pr.p0)
+
+
+def run(pr, move, N, beta, eps, seed, leapfrog=5, rounds=1):
+    r = oais.OAIS(pr, move, N, beta, eps=eps, seed=seed, leapfrog=leapfrog,
+                  contraction=oais.CONTRACT_BF16_TC_STREAM)
+    for _ in range(rounds):
+        res = r.round(len(beta) - 1)
+    logw, ell, x = r.particles()
+    out = dict(res=res, logw=logw.cpu().numpy().copy(), ell=ell.cpu().numpy().copy(),
+               x=x.cpu().numpy().T.astype(np.float64).copy(), **r.stats())
+    r.close()
+    return out
+
+
+def agree(g_logw, g_ell, g_x, r_logw, r_ell, r_x, r_margin):
+    close = lambda a, b, rt, at: np.abs(a - b) <= at + rt * np.abs(b)
+    ok = (close(g_logw, r_logw, REL, ABS) & close(g_ell, r_ell, REL, ABS)
+          & np.all(close(g_x, r_x, XREL, XREL), axis=-1))
+    bad = ~ok & (r_margin > TIE)
+    assert not bad.any(), (f"{int(bad.sum())} particles disagree without a near-tie decision, "
+                           f"e.g. {np.flatnonzero(bad)[:5]}: logw {g_logw[bad][:3]} vs {r_logw[bad][:3]}, "
+                           f"ell {g_ell[bad][:3]} vs {r_ell[bad][:3]}")
+    return ok
+
+
+def problem(kind, n, d, seed):
+    if kind == "linreg":
+        return W.linreg(n=n, d=d, seed=seed)
+    return W.logistic(n=n, d=d, seed=seed)
+
+
+CASES = [
+    # kind, n, d, N, T, move, leapfrog
+    ("linreg", 300, 20, 300, 4, oais.HMC, 3),     # d_pad 32 (64B swizzle), ragged rows and tiles
+    ("linreg", 130, 70, 256, 3, oais.MALA, 1),    # d_pad 128: two 128B slabs
+    ("logreg", 1000, 8, 200, 4, oais.MALA, 1),    # d_pad 16 (32B swizzle)
+    ("linreg", 100, 256, 200, 2, oais.HMC, 5),    # d_pad 256: 32-row chunks, four slabs
+    ("logreg", 777, 64, 129, 3, oais.MALA, 1),    # d_pad 64, one lone particle in the last tile
+    ("linreg", 64, 16, 128, 5, oais.HMC, 2),      # a single full chunk and a single tile
+]
+
+
+@pytest.mark.parametrize("kind,n,d,N,T,move,L", CASES)
+def test_stream_matches_oracle(kind, n, d, N, T, move, L):
+    pr = problem(kind, n, d, seed=n + d)
+    beta = W.linear_schedule(T) ** 3
+    eps = oais.default_step_sizes(pr, beta, move)
+    g = run(pr, move, N, beta, eps, 31, leapfrog=L)
+    r = o.asmc(oracle_target(pr), move, N, beta, eps, 31, leapfrog=L)
+    ok = agree(g["logw"], g["ell"], g["x"], r["logw"], r["ell"], r["x"], r["margin"])
+    assert ok.mean() >= 0.9
+    if ok.all():
+        np.testing.assert_allclose(g["log_ghat"], r["log_ghat"], rtol=1e-5, atol=1e-4)
+        np.testing.assert_allclose(g["accept"], r["accept"], rtol=0, atol=1e-12)
+
+
+def test_stream_importance_sampling_invariant():
+    # a one-step schedule is plain importance sampling: log w = log L(x_0), x_0 ~ eta
+    pr = W.linreg(n=3000, d=128, seed=5)
+    N = 1000
+    g = run(pr, oais.HMC, N, [0.0, 1.0], 0.001, 77)
+    lw = torch.from_numpy(g["logw"])
+    assert g["log_ghat"][0, 0] == pytest.approx(np.log(N), rel=1e-14)
+    assert g["res"]["logZ"] == pytest.approx(torch.logsumexp(lw, 0).item() - np.log(N), rel=1e-12)
+    tg = oracle_target(pr)
+    for n in [0, 1, 127, 128, 999]:
+        r = o.asmc(tg, o.HMC, 1, [0.0, 1.0], 0.001, seed=77, n_offset=n, leapfrog=5)
+        assert g["logw"][n] == pytest.approx(r["logw"][0], rel=REL, abs=ABS)
+
+
+def potential_states(pr, N, seed):
+    # half near the data-generating weights (posterior scale), half from the reference
+    rng = np.random.default_rng(seed)
+    w = pr.extra["w_true"] if "w_true" in pr.extra else np.zeros(pr.d)
+    x = np.empty((N, pr.d))
+    x[: N // 2] = w + 0.003 * rng.normal(size=(N // 2, pr.d))
+    x[N // 2:] = rng.normal(size=(N - N // 2, pr.d))
+    return x.astype(np.float32)
+
+
+@pytest.mark.parametrize("kind,n,d", [("linreg", 50000, 256), ("logreg", 20000, 128), ("linreg", 1000, 40)])
+def test_stream_potential_matches_oracle(kind, n, d):
+    # one evaluation of log L and grad log L at given states (the autograd potential of the
+    # streamed form): the single-step parity of the contraction, at full size included
+    pr = problem(kind, n, d, seed=7) if (n, d) != (50000, 256) else W.linreg()
+    N = 1000
+    xs = potential_states(pr, N, 3)
+    r = oais.OAIS(pr, oais.HMC if kind == "linreg" else oais.MALA, N, [0.0, 1.0], eps=0.01, seed=1,
+                  contraction=oais.CONTRACT_BF16_TC_STREAM)
+    ell, g = r.potential(torch.from_numpy(xs.T.copy()).cuda())
+    ell, g = ell.cpu().numpy(), g.cpu().numpy().T
+    r.close()
+    tg = oracle_target(pr)
+    Xt = np.abs(tg.X)
+    for i in [0, 1, 127, 128, N // 2, N // 2 + 1, N - 1]:
+        xi = xs[i].astype(np.float64)
+        e_o, g_o = tg.log_lik(xi, grad=True)
+        assert ell[i] == pytest.approx(e_o, rel=1e-5, abs=1e-3), (i, ell[i], e_o)
+        # componentwise forward-error bound of g = X^T f(X x): the sums the kernel forms, with
+        # every term taken in absolute value, times 2^-20 (a few fp32 roundings per term)
+        if kind == "linreg":
+            scale = Xt.T @ (np.abs(tg.y) + Xt @ np.abs(xi)) / pr.p0 ** 2
+        else:
+            scale = Xt.T @ np.ones(n) + Xt.T @ (Xt @ np.abs(xi)) * 0.25
+        err = np.abs(g[i] - g_o) / scale
+        assert err.max() < 2.0 ** -20, (i, err.max())
+        if n * d <= 64000:   # small problems: also 1e-5 of the largest component
+            assert np.abs(g[i] - g_o).max() < 1e-5 * np.abs(g_o).max()
+
+
+def test_stream_linreg_full_size_importance_sampling():
+    # the linear-regression workload at its full size (n = 50 000, d = 256, N = 2^16): a
+    # one-step schedule gives log w = log L(x_0) for every particle; sampled particles are
+    # recomputed by the oracle
+    pr = W.linreg()
+    N = 1 << 16
+    g = run(pr, oais.HMC, N, [0.0, 1.0], 1e-4, 12057, leapfrog=5)
+    assert np.isfinite(g["logw"]).all()
+    tg = oracle_target(pr)
+    for n in [0, 127, 128, N - 1, 31337]:
+        r = o.asmc(tg, o.HMC, 1, [0.0, 1.0], 1e-4, seed=12057, n_offset=n, leapfrog=5)
+        assert g["logw"][n] == pytest.approx(r["logw"][0], rel=1e-5)
+
+
+def test_stream_linreg_full_size_round():
+    # a full-size HMC round on a short schedule runs to completion with finite statistics and
+    # a sensible acceptance rate (particle-level parity of multi-step trajectories is tested at
+    # smaller n: at n = 50 000 a change of one fp32 ulp in x moves log L by ~1 nat)
+    pr = W.linreg()
+    N, T = 1 << 16, 4
+    beta = W.linear_schedule(T) ** 4
+    eps = oais.default_step_sizes(pr, beta, oais.HMC)
+    g = run(pr, oais.HMC, N, beta, eps, 12057, leapfrog=5)
+    assert np.isfinite(g["logw"]).all() and np.isfinite(g["log_ghat"]).all()
+    assert (g["accept"] > 0.05).all() and (g["accept"] <= 1.0).all()
+
+
+def test_stream_rounds_repeat_bitwise():
+    # the same schedule and seed give bit-identical rounds (fixed reduction order)
+    pr = W.linreg(n=500, d=64, seed=9)
+    beta = W.linear_schedule(6) ** 2
+    eps = oais.default_step_sizes(pr, beta, oais.HMC)
+    a = run(pr, oais.HMC, 512, beta, eps, 3, leapfrog=3)
+    b = run(pr, oais.HMC, 512, beta, eps, 3, leapfrog=3)
+    assert np.array_equal(a["logw"], b["logw"]) and np.array_equal(a["log_ghat"], b["log_ghat"])
