@@ -16,10 +16,10 @@
 // 2^-22, far below the posterior scale even at n = 50 000).  Accumulation is fp32 in TMEM;
 // sums over rows of the epilogue terms are fp32 per chunk and fp64 across chunks.
 //
-// Roles (320 threads):
+// Roles (352 threads):
 //   warps 0-7  particle warps: thread (warp w, lane l) owns particle 32 (w % 4) + l (its TMEM
 //              lane) and the coordinate half w / 4 and column half w / 4 of every chunk
-//   warp 8     one thread issues the MMAs and their commits
+//   warp 8     one thread issues the forward MMAs, warp 10 one thread the backward MMAs
 //   warp 9     one thread streams the chunk images (X~ in the swizzled shared-memory layout and
 //              y) with bulk copies into a ring of STAGES buffers
 // Synchronisation is by mbarriers; every wait is bounded (2 s), after which the CTA sets
@@ -43,15 +43,16 @@ using namespace oais::tc;
 
 constexpr int kTile = 128;
 constexpr int kEpiThreads = 256;
-constexpr int kThreads = kEpiThreads + 64;
-constexpr int kMmaWarp = 8, kLoadWarp = 9;
+constexpr int kThreads = kEpiThreads + 96;
+constexpr int kFwdWarp = 8, kLoadWarp = 9, kBwdWarp = 10;
 constexpr int kSlice = 8;   // coordinates per state-update step (one 16-byte f16 chunk)
 // The tensor core rounds each accumulation toward zero, so a long running sum in one TMEM
 // accumulator drifts toward zero by about half an ulp per MMA (a relative shrink of ~1e-4
 // after the ~6000 backward MMAs of a 50 000-row evaluation).  The gradient sum is therefore
-// cut into segments of about kSegMmas MMAs: at the end of a segment the particle threads add
-// D2 into an fp32 sum in memory (round to nearest) and the next segment restarts D2.
-constexpr int kSegMmas = 256;
+// cut into segments of kSegMmas MMAs (relative drift ~1e-5): at the end of a segment the
+// particle threads add D2 into an fp32 sum in memory (round to nearest) and the next
+// segment restarts D2.
+constexpr int kSegMmas = 512;
 
 // ---------------------------------------------------------------------------------------
 // K-major operand layout in shared memory: rows of `kw` 16-bit elements (kw = 64 with the
@@ -72,10 +73,15 @@ __host__ __device__ constexpr KLayout klayout(int k_extent)
                    k_extent >= 64 ? 0 : (k_extent == 32 ? 1 : 2)};
 }
 // rows per chunk: 64, or 32 when d_pad = 256 (shared memory)
-__host__ __device__ constexpr int chunk_rows(int) { return 64; }
-// TMEM columns: D1[2] (forward accumulators), R[2] (per-row factors, hi | lo, f16 pairs),
-// D2 (gradient accumulator, d_pad columns)
-constexpr int kColD1 = 0, kColR = 128, kColD2 = 256;
+#ifndef OAIS_TCS_CHUNK256
+#define OAIS_TCS_CHUNK256 64
+#endif
+__host__ __device__ constexpr int chunk_rows(int dp) { return dp >= 256 ? OAIS_TCS_CHUNK256 : 64; }
+// TMEM columns: D1 (forward accumulator, one chunk), R (per-row factors of one chunk, hi |
+// lo, f16 pairs), A_lo (the lo term of the positions, f16 pairs: the forward's A operand for
+// that term), D2 (gradient accumulator, d_pad columns).  The hi term of the positions is the
+// shared-memory A operand.
+constexpr int kColD1 = 0, kColR = 64, kColAlo = 128, kColD2 = 256;
 // byte offset of the 16-byte chunk holding elements [k0, k0 + 8) of `row`
 __host__ __device__ inline uint32_t kmaj_off(int row, int k0, int rows, const KLayout& L)
 {
@@ -119,7 +125,7 @@ struct Params {
 // misc region: barriers, TMEM address, abort flag, exchange buffers, moment scratch
 struct Misc {
     uint64_t xfull[8], xempty[8];
-    uint64_t d1full[2], d1empty[2], rfull[2], rempty[2];
+    uint64_t d1full, d1empty, rfull, rempty;
     uint64_t afull, d2full, done, d2seg, d2drained;
     uint32_t tmem;
     volatile int abort;
@@ -190,9 +196,8 @@ struct Thread {
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) split_pair_h(v[2 * j], v[2 * j + 1], hi[j], lo[j]);
-        constexpr uint32_t a_term = (uint32_t)kTile * DP * 2;
         *reinterpret_cast<uint4*>(smem + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(smem + a_term + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        tmem_st4(tmem + (uint32_t)(kColAlo + i0 / 2) + lane_off, lo);
     }
 
     __device__ void load_grad(int i0, float (&gv)[kSlice])
@@ -208,23 +213,26 @@ struct Thread {
         }
     }
 
-    // end of a gradient segment: add D2 (this thread's lanes and coordinate half) into GS
+    // end of a gradient segment: add D2 (this thread's lanes and coordinate half) into GS,
+    // W columns at a time with all W memory reads in flight together
     __device__ void drain(bool first)
     {
         wait(&M->d2seg, sph);
         sph ^= 1u;
         __syncwarp();
         tc_after_sync();
-#pragma unroll 2
-        for (int i0 = h * DH; i0 < (h + 1) * DH; i0 += kSlice) {
-            uint32_t v[8];
-            tmem_ld8(d2 + lane_off + (uint32_t)i0, v);
+        constexpr int W = DH < 32 ? DH : 32;
+        for (int i0 = h * DH; i0 < (h + 1) * DH; i0 += W) {
+            uint32_t v[W];
+            if constexpr (W == 32) tmem_ld32(d2 + lane_off + (uint32_t)i0, v);
+            else if constexpr (W == 16) tmem_ld16(d2 + lane_off + (uint32_t)i0, v);
+            else tmem_ld8(d2 + lane_off + (uint32_t)i0, v);
+            float old[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) old[j] = first ? 0.0f : GS[(int64_t)(i0 + j) * P->Np];
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < kSlice; ++j) {
-                float* q = GS + (int64_t)(i0 + j) * P->Np;
-                *q = first ? __uint_as_float(v[j]) : *q + __uint_as_float(v[j]);
-            }
+            for (int j = 0; j < W; ++j) GS[(int64_t)(i0 + j) * P->Np] = old[j] + __uint_as_float(v[j]);
         }
         tc_before_sync();
         __syncwarp();
@@ -236,7 +244,8 @@ struct Thread {
     template <int FAM>
     __device__ double eval()
     {
-        fence_proxy_async();
+        tmem_wait_st();   // A_lo in TMEM
+        fence_proxy_async();   // A_hi in shared memory, visible to the tensor core
         tc_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(saddr(&M->afull));
@@ -246,19 +255,18 @@ struct Thread {
         const int seg = P->seg;
         drained = false;
         for (int c = 0; c < nch; ++c, ++g) {
-            const int b = g & 1;
-            const uint32_t ph = (g >> 1) & 1u;
-            wait(&M->d1full[b], ph);
+            const uint32_t ph = g & 1u;
+            wait(&M->d1full, ph);
             __syncwarp();
             tc_after_sync();
             uint32_t v[HC];
-            const uint32_t src = tmem + (uint32_t)(kColD1 + b * CHUNK + h * HC) + lane_off;
+            const uint32_t src = tmem + (uint32_t)(kColD1 + h * HC) + lane_off;
             if constexpr (HC == 16) tmem_ld16(src, v);
             else tmem_ld32(src, v);
             tmem_wait_ld();
             tc_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(saddr(&M->d1empty[b]));
+            if (lane == 0) mbar_arrive(saddr(&M->d1empty));
             uint32_t hi[HC / 2], lo[HC / 2];
             float part0 = 0.0f, part1 = 0.0f;
             if constexpr (FAM == kLinreg) {
@@ -295,17 +303,21 @@ struct Thread {
             }
             if (++xs == P->stages) { xs = 0; xph ^= 1u; }
             // R (two f16 terms) into TMEM, the A operand of the backward
-            wait(&M->rempty[b], ph ^ 1u);
+            wait(&M->rempty, ph ^ 1u);
             __syncwarp();
             tc_after_sync();
-            const uint32_t rcol = tmem + (uint32_t)(kColR + b * CHUNK + h * (HC / 2)) + lane_off;
-            static_assert(HC == 32, "one x16 store per term");
-            tmem_st16(rcol, hi);
-            tmem_st16(rcol + CHUNK / 2, lo);
+            const uint32_t rcol = tmem + (uint32_t)(kColR + h * (HC / 2)) + lane_off;
+            if constexpr (HC == 32) {
+                tmem_st16(rcol, hi);
+                tmem_st16(rcol + CHUNK / 2, lo);
+            } else {
+                tmem_st8(rcol, hi);
+                tmem_st8(rcol + CHUNK / 2, lo);
+            }
             tmem_wait_st();
             tc_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(saddr(&M->rfull[b]));
+            if (lane == 0) mbar_arrive(saddr(&M->rfull));
             // chunk c - 1 closed a gradient segment: its backward is the last of the segment
             if (c >= 1 && (c - 1) % seg == seg - 1) {
                 drain(!drained);
@@ -392,15 +404,13 @@ oais_sweep_tcs_kernel(const Params P)
             mbar_init(saddr(&M->xfull[s]), 1);
             mbar_init(saddr(&M->xempty[s]), 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(saddr(&M->d1full[b]), 1);
-            mbar_init(saddr(&M->d1empty[b]), kEpiThreads / 32);
-            mbar_init(saddr(&M->rfull[b]), kEpiThreads / 32);
-            mbar_init(saddr(&M->rempty[b]), 1);
-        }
+        mbar_init(saddr(&M->d1full), 1);
+        mbar_init(saddr(&M->d1empty), kEpiThreads / 32);
+        mbar_init(saddr(&M->rfull), kEpiThreads / 32);
+        mbar_init(saddr(&M->rempty), 1);
         mbar_init(saddr(&M->afull), kEpiThreads / 32);
         mbar_init(saddr(&M->d2full), 1);
-        mbar_init(saddr(&M->done), 1);
+        mbar_init(saddr(&M->done), 2);
         mbar_init(saddr(&M->d2seg), 1);
         mbar_init(saddr(&M->d2drained), kEpiThreads / 32);
         M->abort = 0;
@@ -442,96 +452,84 @@ oais_sweep_tcs_kernel(const Params P)
             for (uint32_t g = first; g < issued; ++g)
                 mbar_wait(saddr(&M->xfull[g % P.stages]), (g / P.stages) & 1u);
         }
-    } else if (warp == kMmaWarp) {
-        // ---------------- MMA issue ----------------
+    } else if (warp == kFwdWarp || warp == kBwdWarp) {
+        // ---------------- MMA issue: forwards and backwards from two threads ----------------
+        // Each stream is issued in chunk order as soon as its inputs are ready; a commit
+        // tracks only its own thread's MMAs, and every buffer the two streams share is
+        // ordered through the particle warps' barriers (a backward of chunk g follows the
+        // particle warps' read of that chunk's forward result).
         if (lane == 0) {
             constexpr uint32_t idf = idesc_kind_f16(kTile, CHUNK, false, false);
             constexpr uint32_t idb = idesc_kind_f16(kTile, DP, false, true);
             constexpr uint64_t ca = layout_code(LA);
-            constexpr uint32_t a_term = (uint32_t)kTile * DP * 2;
-            // descriptors of the operand bases; the K steps add constant offsets (16-byte units)
-            // to the start-address field
-            const uint64_t adesc[2] = {sdesc(saddr(smem), 16, 8 * LA.lb, ca),
-                                       sdesc(saddr(smem) + a_term, 16, 8 * LA.lb, ca)};
             const uint32_t xbase = saddr(smem + P.off_x);
             const int nch = P.nch, seg = P.seg, S_ = P.stages;
-            // Forwards and backwards are issued as soon as their inputs are ready, in chunk
-            // order each: forward g needs its X stage loaded, its D1 buffer read by the
-            // particle warps and (first chunk of an evaluation) the new positions in A;
-            // backward g needs R of chunk g in TMEM and (first chunk of a gradient segment)
-            // the previous segment drained.
-            uint32_t gf = 0, gb = 0;            // next forward / backward chunk
-            int sf = 0, sb = 0;                 // their X stages
-            uint32_t phf = 0;                   // phase of xfull[sf]
-            uint32_t dph = 0;                   // phase of d2drained
-            uint64_t t_last = globaltimer();
             bool ok = true;
-            while (gb < total) {
-                bool progress = false;
-                if (gf < total && gf < gb + 2) {
-                    const uint32_t cf = gf % (uint32_t)nch, ef = gf / (uint32_t)nch;
-                    const int b = gf & 1;
-                    if ((cf != 0 || mbar_try_wait(saddr(&M->afull), ef & 1u)) &&
-                        mbar_try_wait(saddr(&M->xfull[sf]), phf) &&
-                        mbar_try_wait(saddr(&M->d1empty[b]), ((gf >> 1) & 1u) ^ 1u)) {
-                        tc_after_sync();
-                        const uint64_t xd = sdesc(xbase + (uint32_t)sf * P.stage_bytes, 16, 8 * LA.lb, ca);
-                        const uint32_t d1 = tmem + (uint32_t)(kColD1 + b * CHUNK);
-                        // the small (lo) term first: the running sum is small while it accumulates,
-                        // so only the hi term's steps round a large sum toward zero
+            int s = 0;
+            uint32_t ph = 0;
+            if (warp == kFwdWarp) {
+                // forward g: its X stage loaded, its D1 buffer read by the particle warps and,
+                // for the first chunk of an evaluation, the new positions in A.  The
+                // descriptors of the A bases take constant offsets (16-byte units) per K step.
+                const uint64_t adesc = sdesc(saddr(smem), 16, 8 * LA.lb, ca);
+                const uint32_t d1 = tmem + (uint32_t)kColD1, alo = tmem + (uint32_t)kColAlo;
+                for (uint32_t g = 0, c = 0, e = 0; g < total; ++g) {
+                    if ((c == 0 && !mbar_wait(saddr(&M->afull), e & 1u, &M->abort)) ||
+                        !mbar_wait(saddr(&M->xfull[s]), ph, &M->abort) ||
+                        !mbar_wait(saddr(&M->d1empty), (g & 1u) ^ 1u, &M->abort)) { ok = false; break; }
+                    tc_after_sync();
+                    const uint64_t xd = sdesc(xbase + (uint32_t)s * P.stage_bytes, 16, 8 * LA.lb, ca);
+                    // the small (lo) term first, from TMEM: the running sum is small while it
+                    // accumulates, so only the hi term's steps round a large sum toward zero
 #pragma unroll
-                        for (int term = 1; term >= 0; --term) {
-#pragma unroll
-                            for (int kk = 0; kk < DP / 16; ++kk) {
-                                constexpr int kw = LA.kw;
-                                const int slab = 16 * kk / kw, within = (16 * kk % kw) * 2;
-                                mma_f16(d1, adesc[term] + (uint64_t)((slab * kTile * LA.lb + within) / 16),
-                                        xd + (uint64_t)((slab * CHUNK * LA.lb + within) / 16), idf,
-                                        (term == 1 && kk == 0) ? 0u : 1u);
-                            }
-                        }
-                        mma_commit(saddr(&M->d1full[b]));
-                        ++gf;
-                        if (++sf == S_) { sf = 0; phf ^= 1u; }
-                        progress = true;
+                    for (int kk = 0; kk < DP / 16; ++kk) {
+                        constexpr int kw = LA.kw;
+                        const int slab = 16 * kk / kw, within = (16 * kk % kw) * 2;
+                        mma_f16_ts(d1, alo + (uint32_t)(kk * 8), xd + (uint64_t)((slab * CHUNK * LA.lb + within) / 16),
+                                   idf, kk == 0 ? 0u : 1u);
                     }
-                }
-                if (gb < gf) {
-                    const uint32_t cb = gb % (uint32_t)nch;
-                    const int b = gb & 1;
-                    const bool first = cb % (uint32_t)seg == 0;
-                    if (mbar_try_wait(saddr(&M->rfull[b]), (gb >> 1) & 1u) &&
-                        (!first || cb == 0 || mbar_try_wait(saddr(&M->d2drained), dph))) {
-                        if (first && cb != 0) dph ^= 1u;
-                        tc_after_sync();
-                        const uint64_t xd = sdesc(xbase + (uint32_t)sb * P.stage_bytes, CHUNK * LA.lb, 8 * LA.lb, ca);
-                        const uint32_t ra = tmem + (uint32_t)(kColR + b * CHUNK);
 #pragma unroll
-                        for (int term = 0; term < 2; ++term) {
-#pragma unroll
-                            for (int kk = 0; kk < CHUNK / 16; ++kk)
-                                mma_f16_ts(D2, ra + (uint32_t)(term * (CHUNK / 2) + kk * 8),
-                                           xd + (uint64_t)(kk * 16 * LA.lb / 16), idb,
-                                           (first && term == 0 && kk == 0) ? 0u : 1u);
-                        }
-                        mma_commit(saddr(&M->rempty[b]));
-                        mma_commit(saddr(&M->xempty[sb]));
-                        if (cb % (uint32_t)seg == (uint32_t)seg - 1 && cb < (uint32_t)nch - 1)
-                            mma_commit(saddr(&M->d2seg));
-                        if (cb == (uint32_t)nch - 1) mma_commit(saddr(&M->d2full));
-                        ++gb;
-                        if (++sb == S_) sb = 0;
-                        progress = true;
+                    for (int kk = 0; kk < DP / 16; ++kk) {
+                        constexpr int kw = LA.kw;
+                        const int slab = 16 * kk / kw, within = (16 * kk % kw) * 2;
+                        mma_f16(d1, adesc + (uint64_t)((slab * kTile * LA.lb + within) / 16),
+                                xd + (uint64_t)((slab * CHUNK * LA.lb + within) / 16), idf, 1u);
                     }
+                    mma_commit(saddr(&M->d1full));
+                    if (++s == S_) { s = 0; ph ^= 1u; }
+                    if (++c == (uint32_t)nch) { c = 0; ++e; }
                 }
-                if (progress) {
-                    t_last = globaltimer();
-                } else {
-                    if (M->abort || globaltimer() - t_last > kWaitLimitNs) { ok = false; break; }
+            } else {
+                // backward g: R of chunk g in TMEM and, for the first chunk of a gradient
+                // segment, the previous segment drained
+                uint32_t dph = 0;
+                for (uint32_t g = 0, c = 0; g < total; ++g) {
+                    const bool first = c % (uint32_t)seg == 0;
+                    if (!mbar_wait(saddr(&M->rfull), g & 1u, &M->abort) ||
+                        !mbar_wait(saddr(&M->xfull[s]), ph, &M->abort) ||
+                        (first && c != 0 && !mbar_wait(saddr(&M->d2drained), dph, &M->abort))) { ok = false; break; }
+                    if (first && c != 0) dph ^= 1u;
+                    tc_after_sync();
+                    const uint64_t xd = sdesc(xbase + (uint32_t)s * P.stage_bytes, CHUNK * LA.lb, 8 * LA.lb, ca);
+                    const uint32_t ra = tmem + (uint32_t)kColR;
+#pragma unroll
+                    for (int term = 0; term < 2; ++term) {
+#pragma unroll
+                        for (int kk = 0; kk < CHUNK / 16; ++kk)
+                            mma_f16_ts(D2, ra + (uint32_t)(term * (CHUNK / 2) + kk * 8),
+                                       xd + (uint64_t)(kk * 16 * LA.lb / 16), idb,
+                                       (first && term == 0 && kk == 0) ? 0u : 1u);
+                    }
+                    mma_commit(saddr(&M->rempty));
+                    mma_commit(saddr(&M->xempty[s]));
+                    if (c % (uint32_t)seg == (uint32_t)seg - 1 && c < (uint32_t)nch - 1) mma_commit(saddr(&M->d2seg));
+                    if (c == (uint32_t)nch - 1) mma_commit(saddr(&M->d2full));
+                    if (++s == S_) { s = 0; ph ^= 1u; }
+                    if (++c == (uint32_t)nch) c = 0;
                 }
             }
             if (!ok) { M->abort = 1; atomicOr(S.status, 2u); }
-            // every MMA issued so far has completed before TMEM is released (bounded)
+            // every MMA issued by either thread has completed before TMEM is released (bounded)
             mma_commit(saddr(&M->done));
             mbar_wait(saddr(&M->done), 0u);
         }
@@ -756,11 +754,11 @@ TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages)
     L.nch = (n + L.chunk - 1) / L.chunk;
     L.y_off = (uint32_t)L.chunk * L.dp * 2;
     L.stage_bytes = align1024(L.y_off + (kind == kLinreg ? (uint32_t)L.chunk * 4 : 0u));
-    const uint32_t a_bytes = (uint32_t)tcs::kTile * L.dp * 2 * 2;
+    const uint32_t a_bytes = (uint32_t)tcs::kTile * L.dp * 2;   // hi term of the positions
     L.off_x = a_bytes;
     const uint32_t limit = 227u * 1024u;
     const uint32_t misc = (uint32_t)((sizeof(tcs::Misc) + 1023) & ~(size_t)1023);
-    int S = stages > 0 ? stages : 4;
+    int S = stages > 0 ? stages : 8;
     while (S > 2 && L.off_x + (uint32_t)S * L.stage_bytes + misc > limit) --S;
     L.stages = S;
     L.off_misc = L.off_x + (uint32_t)S * L.stage_bytes;
