@@ -313,6 +313,53 @@ oais_status oais_measure_unit_rate(int32_t unit, double* lane_ops_per_s_per_sm);
 #define OAIS_LOGSUMEXP_NOALLOC_MAX_N 16777216LL
 oais_status oais_logsumexp_noalloc(const double* d_a, int64_t n, double* d_out, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Many independent problems in one launch.
+ *
+ * A batch holds P independent OAIS runs (Alg. 2 each, Sec. 5.1.2 sweeps) of one family
+ * (LOGREG with MALA, or LINREG with MALA or HMC), each with its own data (n and d <= 128 may
+ * differ), particles, statistics and schedule; problem p draws its random numbers with
+ * problem index p in the counter tag (round | p << 16), so its round is the same computation
+ * as a single context given oais_set_problem(ctx, p).  Every problem uses the streamed
+ * tensor-core contraction (X~ = f16(bf16(X)), see oais_target.contraction).
+ *
+ * oais_batch_round runs one round of every problem: the sweeps of all (problem, tile)
+ * items go through ONE persistent kernel (one CTA per SM taking items from a queue ordered
+ * by decreasing cost, so long problems start first and short ones fill the tail), then each
+ * problem's moment records are merged and its schedule re-optimised (Alg. 3) as in
+ * oais_round.  The device work of a round is captured once as a CUDA graph and replayed
+ * while the schedule length stays the same.  All problems must hold schedules of the same
+ * length (they do when every round is given the same T_next).
+ *
+ *   targets   [P] target descriptions (copied at init, as oais_init)
+ *   beta      [T+1] first schedule, shared; eps [P][T] step sizes or NULL (0.5 / sqrt(d))
+ *   workspaces, ws_bytes  [P] caller-owned device workspaces of problem p (size from
+ *             oais_workspace_bytes with contraction OAIS_CONTRACT_BF16_TC_STREAM), or NULL:
+ *             the batch allocates them
+ *   results   [P] per-problem round results (may be NULL)
+ * oais_batch_autotune times the ring depth of the streamed kernel (X chunk buffers in shared
+ * memory) for each width class present (d_pad 16, 32, 64, 128) on that class's largest
+ * problem over T_probe steps and keeps the fastest; chosen [4] receives the depths (0 =
+ * class absent).  oais_batch_context lends problem p's context (owned by the batch) for the
+ * per-problem queries (oais_logZ, oais_get_stats, oais_particles, ...).
+ * Errors: OAIS_EINVAL / OAIS_EUNSUPPORTED for bad lists (mixed families, d > 128), the
+ * single-context errors otherwise; oais_batch_last_error gives the detail.  No counterpart in
+ * the paper: a way of running its method on many posteriors at once.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct oais_batch oais_batch;
+oais_status oais_batch_init(oais_batch** out, int32_t P, const oais_target* targets, const oais_move* move,
+                            int64_t N, const double* beta, int32_t T, int32_t T_max, const double* eps,
+                            uint64_t seed, void* const* workspaces, const size_t* ws_bytes, void* stream);
+oais_status oais_batch_round(oais_batch* b, int32_t T_next, oais_round_result* results);
+oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen);
+oais_status oais_batch_context(oais_batch* b, int32_t p, oais_ctx** ctx);
+const char* oais_batch_last_error(const oais_batch* b);
+void oais_batch_destroy(oais_batch* b);
+
+/* Problem index p (0 <= p <= 65535) of a single context: its random numbers use the tag
+ * round | p << 16, as problem p of a batch does.  Default 0. */
+oais_status oais_set_problem(oais_ctx* ctx, int32_t p);
+
 #ifdef __cplusplus
 }
 #endif

@@ -158,6 +158,7 @@ struct oais_ctx {
     // schedule of the next round
     std::vector<double> beta, eps;
     int round = 0;
+    int problem = 0;                     // problem index in the random-number tag
     // last completed round
     bool have_last = false;
     std::vector<double> l_beta, l_eps, l_log_ghat, l_D, l_accept;
@@ -618,7 +619,7 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
     CK(cudaMemcpyAsync(ctx->d_beta, ctx->beta.data(), sizeof(double) * (T + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_eps, ctx->eps.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s));
-    const uint32_t tag = (uint32_t)(ctx->round & 0xFFFF);
+    const uint32_t tag = (uint32_t)(ctx->round & 0xFFFF) | ((uint32_t)ctx->problem << 16);
     const int grid = sweep_grid(ctx->N);
     const double logN = std::log((double)ctx->N);
     std::vector<double> lg(3 * T), acc(T), ess_tr;
@@ -992,6 +993,346 @@ oais_status oais_potential(oais_ctx* ctx, const void* d_x, int64_t N, double* d_
     case kGmm: CK(launch_potential_gmm(ctx->dt, P, s)); break;
     case kLinreg: CK(launch_potential_linreg(ctx->dt, P, s)); break;
     }
+    return OAIS_OK;
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Batched problems: P independent OAIS runs (Alg. 2 each) whose sweeps share one persistent
+// launch of the streamed tensor-core kernel.  Each problem keeps its own context (data,
+// particles, statistics, schedule; problem index p in the random-number tag), so every
+// problem's round is the same computation as a single run with that index.
+// ---------------------------------------------------------------------------------------
+struct oais_batch {
+    int P = 0, kind = 0, T_max = 0;
+    int64_t N = 0;
+    std::vector<oais_ctx*> ctx;
+    cudaStream_t stream = nullptr;        // the caller's stream
+    cudaStream_t work = nullptr;          // the batch's own stream (captured; the default stream cannot be)
+    cudaEvent_t ready = nullptr;
+    int stages_class[4] = {0, 0, 0, 0};   // ring depth per d_pad class 16/32/64/128 (0: largest that fits)
+    std::vector<TcsPlan> plan;
+    uint32_t off_misc = 0, smem = 0;
+    size_t pbytes = 0, sched_stride = 0, out_stride = 0;
+    unsigned char* d_params = nullptr;
+    uint2* d_items = nullptr;
+    uint32_t n_items = 0;
+    uint32_t* d_head = nullptr;
+    double* d_sched = nullptr;
+    unsigned* d_status = nullptr;
+    unsigned char* h_params = nullptr;
+    double* h_sched = nullptr;
+    double* h_out = nullptr;
+    unsigned* h_status = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_T = -1;
+    int grid = 0;
+    std::string err;
+};
+
+static int dp_class(int dp) { return dp <= 16 ? 0 : dp <= 32 ? 1 : dp <= 64 ? 2 : 3; }
+
+static oais_status batch_fail(oais_batch* b, oais_status s, const std::string& m)
+{
+    if (b) b->err = m; else g_err = m;
+    return s;
+}
+
+#define BK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) return batch_fail(b, OAIS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// shared-memory plans of every problem and the common Misc offset; drops the captured graph
+static void batch_plan(oais_batch* b)
+{
+    b->plan.resize(b->P);
+    uint32_t top = 0;
+    for (int p = 0; p < b->P; ++p) {
+        const DevTarget& dt = b->ctx[p]->dt;
+        TcsPlan L = tcs_plan(dt.kind, dt.n, dt.d, 0, 0);
+        const int want = b->stages_class[dp_class(L.dp)];
+        if (want > 0 && want < L.stages) L = tcs_plan(dt.kind, dt.n, dt.d, 0, want);
+        b->plan[p] = L;
+        top = std::max(top, L.off_x + (uint32_t)L.stages * L.stage_bytes);
+    }
+    b->off_misc = (top + 1023u) & ~1023u;
+    b->smem = b->off_misc + tcs_misc_bytes();
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_T = -1;
+}
+
+// (problem, tile) items, longest first: a tile of problem p costs ~ chunks x (d_pad + 64)
+static void batch_items(oais_batch* b, std::vector<uint2>& items)
+{
+    items.clear();
+    std::vector<std::pair<double, uint2>> c;
+    const uint32_t tiles = (uint32_t)tcs_tiles(b->N);
+    for (int p = 0; p < b->P; ++p) {
+        const double cost = (double)b->plan[p].nch * (b->plan[p].dp + 64);
+        for (uint32_t t = 0; t < tiles; ++t) c.push_back({cost, make_uint2((uint32_t)p, t)});
+    }
+    std::stable_sort(c.begin(), c.end(), [](const auto& a, const auto& z) { return a.first > z.first; });
+    for (auto& e : c) items.push_back(e.second);
+}
+
+// every problem's parameter block for a round at schedule length T
+static void batch_fill(oais_batch* b, int T)
+{
+    for (int p = 0; p < b->P; ++p) {
+        oais_ctx* c = b->ctx[p];
+        double* sb = b->h_sched + (size_t)p * b->sched_stride;
+        std::copy(c->beta.begin(), c->beta.end(), sb);
+        std::copy(c->eps.begin(), c->eps.end(), sb + b->T_max + 1);
+        const double* db = b->d_sched + (size_t)p * b->sched_stride;
+        const uint32_t tag = (uint32_t)(c->round & 0xFFFF) | ((uint32_t)c->problem << 16);
+        SweepParams sp = make_params(c, T, db, db + b->T_max + 1, c->seed, tag, c->n_offset, c->N, c->d_logw, c->d_ell,
+                                     c->d_x, c->d_parts, b->d_status + p);
+        tcs_batch_params(b->plan[p], c->dt.kind, sp, c->dt.tcs_img, c->dt.tcs_state, c->mv.kind, c->mv.leapfrog,
+                         c->dt.p0, c->dt.n, c->dt.d, b->off_misc, b->h_params + (size_t)p * b->pbytes);
+    }
+}
+
+// the round's device work: schedules and parameter blocks in, the persistent sweep, then per
+// problem the merge of the moment records, the log-sum-exp of the final weights and the
+// copies of the statistics out (captured once per schedule length as a CUDA graph)
+static oais_status batch_enqueue(oais_batch* b, int T)
+{
+    cudaStream_t s = b->work;
+    BK(cudaMemcpyAsync(b->d_sched, b->h_sched, sizeof(double) * b->sched_stride * b->P, cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(b->d_params, b->h_params, b->pbytes * b->P, cudaMemcpyHostToDevice, s));
+    BK(cudaMemsetAsync(b->d_status, 0, sizeof(unsigned) * b->P, s));
+    BK(cudaMemsetAsync(b->d_head, 0, sizeof(uint32_t), s));
+    // external records: inside a captured graph a plain record only orders the capture
+    BK(cudaEventRecordWithFlags(b->ev0, s, cudaEventRecordExternal));
+    BK(launch_sweep_tcs_batch(b->kind, b->d_params, b->d_items, b->n_items, b->d_head, b->off_misc, b->smem,
+                              b->grid, s));
+    BK(cudaEventRecordWithFlags(b->ev1, s, cudaEventRecordExternal));
+    for (int p = 0; p < b->P; ++p) {
+        oais_ctx* c = b->ctx[p];
+        BK(launch_merge_stats(c->d_parts, tcs_tiles(c->N), T, 1.0 / ((double)c->N * c->mv.moves), c->d_log_ghat,
+                              c->d_accept, s));
+        BK(launch_logsumexp(c->d_logw, c->N, c->d_lse, c->d_lse_scratch, s));
+        double* o = b->h_out + (size_t)p * b->out_stride;
+        BK(cudaMemcpyAsync(o, c->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
+        BK(cudaMemcpyAsync(o + 3 * b->T_max, c->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+        BK(cudaMemcpyAsync(o + 4 * b->T_max, c->d_lse, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    }
+    BK(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(unsigned) * b->P, cudaMemcpyDeviceToHost, s));
+    return OAIS_OK;
+}
+
+extern "C" {
+
+oais_status oais_batch_init(oais_batch** out, int32_t P, const oais_target* targets, const oais_move* move,
+                            int64_t N, const double* beta, int32_t T, int32_t T_max, const double* eps,
+                            uint64_t seed, void* const* workspaces, const size_t* ws_bytes, void* stream)
+{
+    oais_batch* b = nullptr;
+    if (!out) return batch_fail(nullptr, OAIS_EINVAL, "null batch pointer");
+    *out = nullptr;
+    if (P < 1 || P > 0xFFFF || !targets || !move) return batch_fail(nullptr, OAIS_EINVAL, "bad problem list");
+    for (int p = 0; p < P; ++p) {
+        if (targets[p].kind != targets[0].kind || (targets[0].kind != kLogreg && targets[0].kind != kLinreg))
+            return batch_fail(nullptr, OAIS_EUNSUPPORTED, "a batch holds LOGREG or LINREG problems of one family");
+        if (targets[p].d > 128) return batch_fail(nullptr, OAIS_EUNSUPPORTED, "batched problems take d <= 128");
+    }
+    b = new oais_batch();
+    b->P = P;
+    b->kind = targets[0].kind;
+    b->N = N;
+    b->T_max = T_max;
+    b->stream = static_cast<cudaStream_t>(stream);
+    for (int p = 0; p < P; ++p) {
+        oais_target t = targets[p];
+        t.contraction = OAIS_CONTRACT_BF16_TC_STREAM;
+        oais_ctx* c = nullptr;
+        oais_status st = oais_init(&c, &t, move, N, beta, T, T_max, eps ? eps + (size_t)p * T : nullptr, seed,
+                                   workspaces ? workspaces[p] : nullptr, ws_bytes ? ws_bytes[p] : 0, stream);
+        if (st != OAIS_OK) {
+            std::string m = "problem " + std::to_string(p) + ": " + g_err;
+            oais_batch_destroy(b);
+            return batch_fail(nullptr, st, m);
+        }
+        c->problem = p;
+        b->ctx.push_back(c);
+    }
+    batch_plan(b);
+    std::vector<uint2> items;
+    batch_items(b, items);
+    b->n_items = (uint32_t)items.size();
+    b->pbytes = (tcs_params_bytes() + 15) & ~(size_t)15;
+    b->sched_stride = 2 * (size_t)T_max + 1;
+    b->out_stride = 4 * (size_t)T_max + 2;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = std::max(1, std::min(sms, (int)b->n_items));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_params, b->pbytes * P);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(uint2) * items.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_head, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sched, sizeof(double) * b->sched_stride * P);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(unsigned) * P);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_params, b->pbytes * P);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_sched, sizeof(double) * b->sched_stride * P);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, sizeof(double) * b->out_stride * P);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(unsigned) * P);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        std::string m = cudaGetErrorString(e);
+        oais_batch_destroy(b);
+        return batch_fail(nullptr, OAIS_ENOMEM, m);
+    }
+    *out = b;
+    return OAIS_OK;
+}
+
+oais_status oais_batch_round(oais_batch* b, int32_t T_next, oais_round_result* results)
+{
+    if (!b) return batch_fail(nullptr, OAIS_EINVAL, "null batch");
+    if (T_next < 1 || T_next > b->T_max) return batch_fail(b, OAIS_EINVAL, "T_next out of range");
+    const int T = (int)b->ctx[0]->beta.size() - 1;
+    for (oais_ctx* c : b->ctx)
+        if ((int)c->beta.size() - 1 != T) return batch_fail(b, OAIS_EINVAL, "problems hold schedules of different lengths");
+    batch_fill(b, T);
+    // the round follows the caller's earlier work on its stream
+    BK(cudaEventRecord(b->ready, b->stream));
+    BK(cudaStreamWaitEvent(b->work, b->ready, 0));
+    if (!b->gexec || b->graph_T != T) {
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        BK(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
+        oais_status st = batch_enqueue(b, T);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->work, &g);
+        if (st != OAIS_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return batch_fail(b, OAIS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        b->graph = g;
+        BK(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+        b->graph_T = T;
+    }
+    BK(cudaGraphLaunch(b->gexec, b->work));
+    BK(cudaStreamSynchronize(b->work));
+    float ms = 0.0f;
+    BK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    oais_status worst = OAIS_OK;
+    for (int p = 0; p < b->P; ++p) {
+        oais_ctx* c = b->ctx[p];
+        const unsigned status = b->h_status[p];
+        oais_status st = OAIS_OK;
+        if (status & 2u) st = fail(c, OAIS_ETIMEOUT, "a tensor-core completion wait gave up");
+        else if (status & 12u) st = fail(c, OAIS_ECUDA, "batched sweep: bad shared-memory base or width");
+        else if (status & 1u) st = fail(c, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood");
+        if (st == OAIS_OK) {
+            const double* o = b->h_out + (size_t)p * b->out_stride;
+            std::vector<double> lg(o, o + 3 * T), acc(o + 3 * b->T_max, o + 3 * b->T_max + T);
+            const double lse0 = o[4 * b->T_max], lse1 = o[4 * b->T_max + 1];
+            const double logZ = lse0 - std::log((double)c->N);
+            const double ess = std::exp(2.0 * lse0 - lse1);
+            const double se = std::sqrt(std::max(0.0, 1.0 / ess - 1.0 / (double)c->N));
+            st = commit_round(c, T, T_next, lg, acc, logZ, ess, se, ms, false, 0, {}, {},
+                              results ? results + p : nullptr);
+        }
+        if (st != OAIS_OK && worst == OAIS_OK) {
+            worst = st;
+            b->err = "problem " + std::to_string(p) + ": " + c->err;
+        }
+    }
+    return worst;
+}
+
+// Ring depth per width class, chosen by timing: for each class present, the largest problem
+// of the class sweeps T_probe steps (its own data, a linear schedule, the first tiles of its
+// particles filling every SM once) at each candidate depth; the fastest depth is kept.
+oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
+{
+    if (!b) return batch_fail(nullptr, OAIS_EINVAL, "null batch");
+    if (T_probe < 1 || T_probe > b->T_max) return batch_fail(b, OAIS_EINVAL, "T_probe out of range");
+    cudaStream_t s = b->work;
+    BK(cudaEventRecord(b->ready, b->stream));
+    BK(cudaStreamWaitEvent(s, b->ready, 0));
+    std::vector<double> sched(2 * (size_t)T_probe + 1);
+    for (int t = 0; t <= T_probe; ++t) sched[t] = (double)t / T_probe;
+    for (int c = 0; c < 4; ++c) {
+        int best_p = -1;
+        for (int p = 0; p < b->P; ++p)
+            if (dp_class(b->plan[p].dp) == c && (best_p < 0 || b->ctx[p]->dt.n > b->ctx[best_p]->dt.n)) best_p = p;
+        if (chosen) chosen[c] = 0;
+        if (best_p < 0) continue;
+        oais_ctx* x = b->ctx[best_p];
+        for (int t = 0; t < T_probe; ++t) sched[T_probe + 1 + t] = x->eps.empty() ? 0.01 : x->eps[0];
+        BK(cudaMemcpyAsync(b->d_sched, sched.data(), sizeof(double) * sched.size(), cudaMemcpyHostToDevice, s));
+        const int64_t Nprobe = std::min<int64_t>(x->N, (int64_t)b->grid * 128);
+        float best_ms = 0.0f;
+        int best_S = 0;
+        const TcsPlan full = tcs_plan(x->dt.kind, x->dt.n, x->dt.d, 0, 0);
+        for (int S : {2, 3, 4, 6, 8}) {
+            if (S > full.stages) break;
+            const TcsPlan L = tcs_plan(x->dt.kind, x->dt.n, x->dt.d, 0, S);
+            SweepParams sp = make_params(x, T_probe, b->d_sched, b->d_sched + T_probe + 1, x->seed, 0xFFFFu, 0, Nprobe,
+                                         x->d_logw, x->d_ell, x->d_x, x->d_parts, b->d_status);
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
+                BK(cudaEventRecord(b->ev0, s));
+                BK(launch_sweep_tcs(L, x->dt.kind, sp, x->dt.tcs_img, x->dt.tcs_state, x->mv.kind, x->mv.leapfrog,
+                                    x->dt.p0, x->dt.n, x->dt.d, s));
+                BK(cudaEventRecord(b->ev1, s));
+                BK(cudaEventSynchronize(b->ev1));
+                BK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+            }
+            if (best_S == 0 || ms < best_ms) { best_ms = ms; best_S = S; }
+        }
+        b->stages_class[c] = best_S;
+        if (chosen) chosen[c] = best_S;
+    }
+    batch_plan(b);
+    return OAIS_OK;
+}
+
+oais_status oais_batch_context(oais_batch* b, int32_t p, oais_ctx** ctx)
+{
+    if (!b || !ctx || p < 0 || p >= b->P) return batch_fail(b, OAIS_EINVAL, "bad problem index");
+    *ctx = b->ctx[p];
+    return OAIS_OK;
+}
+
+const char* oais_batch_last_error(const oais_batch* b) { return b ? b->err.c_str() : g_err.c_str(); }
+
+void oais_batch_destroy(oais_batch* b)
+{
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->ready) cudaEventDestroy(b->ready);
+    if (b->work) cudaStreamDestroy(b->work);
+    cudaFree(b->d_params);
+    cudaFree(b->d_items);
+    cudaFree(b->d_head);
+    cudaFree(b->d_sched);
+    cudaFree(b->d_status);
+    cudaFreeHost(b->h_params);
+    cudaFreeHost(b->h_sched);
+    cudaFreeHost(b->h_out);
+    cudaFreeHost(b->h_status);
+    for (oais_ctx* c : b->ctx) oais_destroy(c);
+    delete b;
+}
+
+oais_status oais_set_problem(oais_ctx* ctx, int32_t p)
+{
+    if (!ctx || p < 0 || p > 0xFFFF) return fail(ctx, OAIS_EINVAL, "problem index out of range");
+    ctx->problem = p;
     return OAIS_OK;
 }
 

@@ -44,6 +44,15 @@ int tcs_tiles(int64_t N);
 // drained gradient sum)
 cudaError_t launch_sweep_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
                              int move, int leapfrog, double p0, int n, int d, cudaStream_t s);
+// batched persistent form: per-problem parameter blocks (opaque, tcs_params_bytes each) whose
+// Misc region sits at the common offset off_misc, a queue of (problem, tile) items, a head
+// counter (zero before the launch), one CTA per SM
+size_t tcs_params_bytes();
+uint32_t tcs_misc_bytes();
+void tcs_batch_params(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state, int move,
+                      int leapfrog, double p0, int n, int d, uint32_t off_misc, void* out);
+cudaError_t launch_sweep_tcs_batch(int kind, const void* d_params, const void* d_items, uint32_t n_items,
+                                   uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s);
 // one evaluation of log L and grad log L (grad may be null) at states x [d][N] with the
 // streamed tensor-core contraction
 cudaError_t launch_potential_tcs(const TcsPlan& L, int kind, const void* img, const float* x, int64_t N,

@@ -134,6 +134,8 @@ struct Misc {
     double s_m[2][4][3];
     float s_s[2][4][3];
     unsigned s_acc[2][4];
+    Params prm;                 // batched launch: the current item's problem
+    uint32_t item;              // batched launch: the current item
 };
 
 // f16 two-term split of a pair: hi = f16(v), lo = f16(v - hi)
@@ -383,47 +385,50 @@ __device__ __forceinline__ void tile_record(int lane, const double (*wm)[3], con
     }
 }
 
+__device__ __forceinline__ void mbar_inval(uint32_t bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+// (thread 0) fresh barriers for one tile; prev_stages > 0: the previous tile's barriers (with
+// that many stage pairs) are invalidated first
+__device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stages)
+{
+    uint64_t* all[] = {&M->d1full, &M->d1empty, &M->rfull, &M->rempty, &M->afull, &M->d2full,
+                       &M->done, &M->d2seg, &M->d2drained};
+    if (prev_stages > 0) {
+        for (int s = 0; s < prev_stages; ++s) { mbar_inval(saddr(&M->xfull[s])); mbar_inval(saddr(&M->xempty[s])); }
+        for (uint64_t* b : all) mbar_inval(saddr(b));
+    }
+    for (int s = 0; s < stages; ++s) {
+        mbar_init(saddr(&M->xfull[s]), 1);
+        mbar_init(saddr(&M->xempty[s]), 1);
+    }
+    mbar_init(saddr(&M->d1full), 1);
+    mbar_init(saddr(&M->d1empty), kEpiThreads / 32);
+    mbar_init(saddr(&M->rfull), kEpiThreads / 32);
+    mbar_init(saddr(&M->rempty), 1);
+    mbar_init(saddr(&M->afull), kEpiThreads / 32);
+    mbar_init(saddr(&M->d2full), 1);
+    mbar_init(saddr(&M->done), 2);
+    mbar_init(saddr(&M->d2seg), 1);
+    mbar_init(saddr(&M->d2drained), kEpiThreads / 32);
+    M->abort = 0;
+    fence_mbar_init();
+}
+
+// One tile (128 particles) of one problem for a whole sweep, by all 352 threads of the CTA;
+// the barriers are fresh and TMEM (512 columns at `tmem`) is held by the caller.
 template <int FAM, int DP>
-__global__ void __launch_bounds__(kThreads, 1)
-oais_sweep_tcs_kernel(const Params P)
+__device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_t tiles, unsigned char* smem,
+                                         uint32_t tmem)
 {
     constexpr int CHUNK = chunk_rows(DP);
-    extern __shared__ __align__(1024) unsigned char smem[];
     const SweepParams& S = P.sp;
-    if (saddr(smem) & 1023u) {
-        if (threadIdx.x == 0) atomicOr(S.status, 4u);
-        return;
-    }
     Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Le = P.move == kHmc ? P.leapfrog : 1;
     const uint32_t evals = P.x_in ? 1u : 1u + (uint32_t)S.T * (uint32_t)S.mv.K * (uint32_t)Le;
     const uint32_t total = evals * (uint32_t)P.nch;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < P.stages; ++s) {
-            mbar_init(saddr(&M->xfull[s]), 1);
-            mbar_init(saddr(&M->xempty[s]), 1);
-        }
-        mbar_init(saddr(&M->d1full), 1);
-        mbar_init(saddr(&M->d1empty), kEpiThreads / 32);
-        mbar_init(saddr(&M->rfull), kEpiThreads / 32);
-        mbar_init(saddr(&M->rempty), 1);
-        mbar_init(saddr(&M->afull), kEpiThreads / 32);
-        mbar_init(saddr(&M->d2full), 1);
-        mbar_init(saddr(&M->done), 2);
-        mbar_init(saddr(&M->d2seg), 1);
-        mbar_init(saddr(&M->d2drained), kEpiThreads / 32);
-        M->abort = 0;
-        fence_mbar_init();
-    }
-    if (warp == 0) {
-        tmem_alloc(saddr(&M->tmem), P.tmem_cols);
-        tmem_relinquish();
-    }
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&M->tmem);
     const uint32_t D2 = tmem + (uint32_t)kColD2;
     constexpr KLayout LA = klayout(DP);
 
@@ -553,7 +558,7 @@ oais_sweep_tcs_kernel(const Params P)
         Th.sph = 0;
         Th.drained = false;
         const int p = Th.p, h = Th.h;
-        const int64_t n64 = (int64_t)blockIdx.x * kTile + p;
+        const int64_t n64 = (int64_t)tile * kTile + p;
         const bool active = n64 < S.N;
         Th.GS = P.gs + n64;
         const uint32_t n = (uint32_t)(S.n_offset + (active ? n64 : S.N - 1));
@@ -712,7 +717,7 @@ oais_sweep_tcs_kernel(const Params P)
                 named_sync(2, 128);
                 if (warp == 0)
                     tile_record(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot],
-                                S.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
+                                S.partials + (size_t)(t - 1) * tiles + tile);
             }
         }
         if (active) {
@@ -726,9 +731,91 @@ oais_sweep_tcs_kernel(const Params P)
         }
         }   // sweep
     }
+}
+
+template <int FAM, int DP>
+__global__ void __launch_bounds__(kThreads, 1)
+oais_sweep_tcs_kernel(const Params P)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    if (saddr(smem) & 1023u) {
+        if (threadIdx.x == 0) atomicOr(P.sp.status, 4u);
+        return;
+    }
+    Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) init_barriers(M, P.stages, 0);
+    if (warp == 0) {
+        tmem_alloc(saddr(&M->tmem), P.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&M->tmem);
+    run_tile<FAM, DP>(P, blockIdx.x, gridDim.x, smem, tmem);
     tc_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, P.tmem_cols);
+}
+
+// Many independent problems in one persistent launch: each CTA takes (problem, tile) items
+// from a queue ordered by decreasing cost (longest first) until it is empty.  All problems
+// share the family; their widths may differ (the item picks the instantiation).  Every
+// problem's Misc region sits at the same offset (the launch's largest).
+template <int FAM>
+__global__ void __launch_bounds__(kThreads, 1)
+oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __restrict__ items, uint32_t n_items,
+                            uint32_t* head, uint32_t off_misc)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    if (saddr(smem) & 1023u) {
+        if (threadIdx.x == 0) atomicOr(probs[0].sp.status, 4u);
+        return;
+    }
+    Misc* M = reinterpret_cast<Misc*>(smem + off_misc);
+    Params& sP = M->prm;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        tmem_alloc(saddr(&M->tmem), 512);
+        tmem_relinquish();
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&M->tmem);
+    int prev_stages = 0;   // thread 0 only
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t it = atomicAdd(head, 1u);
+            M->item = it;
+            if (it < n_items) {
+                sP = probs[items[it].x];
+                init_barriers(M, sP.stages, prev_stages);
+                prev_stages = sP.stages;
+            }
+        }
+        __syncthreads();
+        const uint32_t it = M->item;
+        if (it >= n_items) break;
+        const uint32_t tile = items[it].y;
+        const uint32_t tiles = (uint32_t)((sP.sp.N + kTile - 1) / kTile);
+        switch (sP.dp) {
+        case 16: run_tile<FAM, 16>(sP, tile, tiles, smem, tmem); break;
+        case 32: run_tile<FAM, 32>(sP, tile, tiles, smem, tmem); break;
+        case 64: run_tile<FAM, 64>(sP, tile, tiles, smem, tmem); break;
+        case 128: run_tile<FAM, 128>(sP, tile, tiles, smem, tmem); break;
+        default: if (threadIdx.x == 0) atomicOr(sP.sp.status, 8u);
+        }
+        // every role has finished the tile (its copies and MMAs complete) before the barriers
+        // and the item slot are reused
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 } // namespace tcs
@@ -807,11 +894,10 @@ void tcs_prepare(const TcsPlan& L, int kind, const float* X, const float* y, int
 
 int tcs_tiles(int64_t N) { return (int)((N + tcs::kTile - 1) / tcs::kTile); }
 
-static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
-                              int move, int leapfrog, double p0, int n, int d, const float* x_in, double* ell_pot,
-                              float* grad_pot, int64_t pstride, cudaStream_t s, int64_t state_particles = 0)
+static void fill_params(tcs::Params& P, const TcsPlan& L, int kind, const SweepParams& sp, const void* img,
+                        float* state, int move, int leapfrog, double p0, int n, int d, const float* x_in,
+                        double* ell_pot, float* grad_pot, int64_t pstride, int64_t state_particles)
 {
-    tcs::Params P;
     P.sp = sp;
     P.x_in = x_in;
     P.ell_pot = ell_pot;
@@ -842,6 +928,16 @@ static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp,
     P.log_norm = kind == kLinreg ? (double)n * (std::log(p0) + 0.5 * std::log(2.0 * 3.14159265358979323846)) : 0.0;
     P.gscale = kind == kLinreg ? (float)(1.0 / (p0 * p0)) : 1.0f;
     P.half_inv_var = kind == kLinreg ? (float)(0.5 / (p0 * p0)) : 0.0f;
+}
+
+static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
+                              int move, int leapfrog, double p0, int n, int d, const float* x_in, double* ell_pot,
+                              float* grad_pot, int64_t pstride, cudaStream_t s, int64_t state_particles = 0)
+{
+    tcs::Params P;
+    fill_params(P, L, kind, sp, img, state, move, leapfrog, p0, n, d, x_in, ell_pot, grad_pot, pstride,
+                state_particles);
+    const int tiles = tcs_tiles(sp.N);
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
         if (e != cudaSuccess) return e;
@@ -890,6 +986,32 @@ cudaError_t launch_potential_tcs(const TcsPlan& L, int kind, const void* img, co
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+size_t tcs_params_bytes() { return sizeof(tcs::Params); }
+uint32_t tcs_misc_bytes() { return (uint32_t)sizeof(tcs::Misc); }
+
+void tcs_batch_params(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state, int move,
+                      int leapfrog, double p0, int n, int d, uint32_t off_misc, void* out)
+{
+    tcs::Params P;
+    fill_params(P, L, kind, sp, img, state, move, leapfrog, p0, n, d, nullptr, nullptr, nullptr, 0, 0);
+    P.off_misc = off_misc;
+    std::memcpy(out, &P, sizeof(P));
+}
+
+cudaError_t launch_sweep_tcs_batch(int kind, const void* d_params, const void* d_items, uint32_t n_items,
+                                   uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s)
+{
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, tcs::kThreads, smem, s>>>(static_cast<const tcs::Params*>(d_params),
+                                                 static_cast<const uint2*>(d_items), n_items, d_head, off_misc);
+        return cudaGetLastError();
+    };
+    if (kind == kLinreg) return go(tcs::oais_sweep_tcs_batch_kernel<kLinreg>);
+    return go(tcs::oais_sweep_tcs_batch_kernel<kLogreg>);
 }
 
 } // namespace oais

@@ -94,6 +94,13 @@ def lib():
                 "oais_merge_stats": ([P, i32, i32, i64, i32, P, P, P], i32),
                 "oais_logsumexp_scratch_bytes": ([i64], sz),
                 "oais_logsumexp": ([P, i64, P, P, P], i32),
+                "oais_batch_init": ([P, i32, P, P, i64, P, i32, i32, P, u64, P, P, P], i32),
+                "oais_batch_round": ([P, i32, P], i32),
+                "oais_batch_autotune": ([P, i32, P], i32),
+                "oais_batch_context": ([P, i32, P], i32),
+                "oais_batch_last_error": ([P], ctypes.c_char_p),
+                "oais_batch_destroy": ([P], None),
+                "oais_set_problem": ([P, i32], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -195,9 +202,15 @@ class OAIS:
                            _dptr(self.workspace), self.workspace.numel(), _stream_ptr(self.stream)))
 
     def close(self):
+        if getattr(self, "_borrowed", False):
+            return
         if getattr(self, "_ctx", None) and self._ctx.value:
             lib().oais_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
+
+    def set_problem(self, p):
+        """Problem index p in the random-number tag (round | p << 16), as problem p of a batch."""
+        _check(lib().oais_set_problem(self._ctx, int(p)), self._ctx)
 
     __del__ = close
 
@@ -424,3 +437,87 @@ def log_likelihood_function():
             return (grad_out.to(g.dtype)[:, None] * g.t()), None
 
     return LogLikelihood
+
+
+class OAISBatch:
+    """P independent OAIS runs of one family whose sweeps share one persistent tensor-core
+    launch per round (captured as a CUDA graph).  problems: list of workloads.Problem (LOGREG
+    with MALA, or LINREG with MALA or HMC; d <= 128).  eps: [P][T] step sizes or None (the
+    starting rule default_step_sizes per problem).  batch.problem(p) gives an OAIS view of
+    problem p (logZ, stats, schedule, particles, ...)."""
+
+    def __init__(self, problems, move_kind, N, beta, T_max=None, eps=None, seed=12057, moves=1, leapfrog=5,
+                 stream=None):
+        import torch
+        self._torch = torch
+        self.problems = list(problems)
+        P = len(self.problems)
+        self.N = int(N)
+        beta = np.ascontiguousarray(beta, dtype=np.float64)
+        T = beta.size - 1
+        self.T_max = int(T_max if T_max is not None else T)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._keep = []
+        tgs = (_Target * P)()
+        for p, pr in enumerate(self.problems):
+            X = torch.from_numpy(np.ascontiguousarray(pr.X, dtype=np.float32)).cuda()
+            y = torch.from_numpy(np.ascontiguousarray(pr.y, dtype=np.float32)).cuda()
+            self._keep += [X, y]
+            tgs[p] = _Target(pr.kind, pr.d, pr.n, DT_F32, X.data_ptr(), y.data_ptr(), pr.ref_scale, pr.p0, 1,
+                             CONTRACT_BF16_TC_STREAM)
+        self._mv = _Move(int(move_kind), int(moves), int(leapfrog), 0, 0)
+        L = lib()
+        self.workspaces = []
+        ptrs, sizes = (ctypes.c_void_p * P)(), (ctypes.c_size_t * P)()
+        for p in range(P):
+            nb = ctypes.c_size_t()
+            _check(L.oais_workspace_bytes(ctypes.byref(tgs[p]), ctypes.byref(self._mv), self.N, self.T_max,
+                                          ctypes.byref(nb)))
+            w = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+            self.workspaces.append(w)
+            ptrs[p], sizes[p] = w.data_ptr(), nb.value
+        if eps is None:
+            eps = np.stack([default_step_sizes(pr, beta, move_kind) for pr in self.problems])
+        eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (P, T)))
+        self._b = ctypes.c_void_p()
+        st = L.oais_batch_init(ctypes.byref(self._b), P, tgs, ctypes.byref(self._mv), self.N, _np_ptr(beta), T,
+                               self.T_max, _np_ptr(eps), int(seed), ptrs, sizes, _stream_ptr(self.stream))
+        if st != 0:
+            raise OAISError(st, L.oais_batch_last_error(None).decode())
+        self._views = []
+        for p, pr in enumerate(self.problems):
+            c = ctypes.c_void_p()
+            self._check(L.oais_batch_context(self._b, p, ctypes.byref(c)))
+            v = OAIS.__new__(OAIS)
+            v._torch, v.problem, v.N, v.T_max, v.stream = torch, pr, self.N, self.T_max, self.stream
+            v._ctx, v.workspace, v._borrowed = c, self.workspaces[p], True
+            self._views.append(v)
+
+    def _check(self, st):
+        if st != 0:
+            raise OAISError(st, lib().oais_batch_last_error(self._b).decode())
+
+    def round(self, T_next=None):
+        """One round of every problem; returns a list of per-problem result dicts."""
+        P = len(self.problems)
+        if T_next is None:
+            T_next = self._views[0].schedule()[0].size - 1
+        res = (_RoundResult * P)()
+        self._check(lib().oais_batch_round(self._b, int(T_next), res))
+        return [{f: getattr(r, f) for f, _ in _RoundResult._fields_ if f != "pad"} for r in res]
+
+    def autotune(self, T_probe=4):
+        """Time the X-ring depth per width class (d_pad 16/32/64/128); returns the chosen depths."""
+        chosen = (ctypes.c_int32 * 4)()
+        self._check(lib().oais_batch_autotune(self._b, int(T_probe), chosen))
+        return list(chosen)
+
+    def problem(self, p):
+        return self._views[p]
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            lib().oais_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    __del__ = close
