@@ -10,6 +10,13 @@ schedule update.  Metric: particle-steps per second (N x sum of T over the round
 
 --impl reference times the FP64 CPU checker (oracle/) on the host cores on a bounded
 sample of the same workload; it is a deliberately slow program, reported for context.
+
+--workload linreg and --workload batched time the two other tensor-core workloads (each
+prints its own JSON line; the default line above is the one the benchmark contract uses):
+  linreg   Bayesian linear regression X 50000x256 N(0,1), sigma 0.3, tau 1; N = 2^16; HMC
+           with 5 leapfrog steps; 4 rounds T = 64, 128, 256, 512; streamed tcgen05 kernel.
+  batched  64 logistic problems, n log-uniform in [500, 50000], d in {8, ..., 128}; N = 2^14
+           each; MALA; 3 rounds at T = 256; one persistent launch per round (CUDA graph).
 """
 from __future__ import annotations
 
@@ -45,11 +52,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--rounds", default=None,
                     help="comma-separated T per round (profiling a smaller case); default 256,512,1024,2048")
-    ap.add_argument("--contraction", default="bf16_tc", choices=["fp32", "bf16_tc"],
-                    help="X x on the tcgen05 tensor cores with X rounded to bf16 (default), or on "
-                         "CUDA cores in fp32")
+    ap.add_argument("--contraction", default="bf16_tc", choices=["fp32", "bf16_tc", "bf16_tc_stream"],
+                    help="X x on the tcgen05 tensor cores with X rounded to bf16 (default: X resident in "
+                         "shared memory; bf16_tc_stream: the streamed kernel), or on CUDA cores in fp32")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other form of the contraction")
+    ap.add_argument("--workload", default="logreg", choices=["logreg", "linreg", "batched"])
+    ap.add_argument("--compare-sequential", action="store_true",
+                    help="batched: also time the problems one after another (single contexts)")
     a = ap.parse_args()
     if a.rounds:
         global ROUNDS_T
@@ -169,6 +179,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "linreg":
+        return bench_linreg(args)
+    if args.workload == "batched":
+        return bench_batched(args)
     import torch
     from paper_2408_12057_gb300 import oais, workloads as W
 
@@ -182,7 +196,8 @@ def main():
     T0 = ROUNDS_T[0]
     beta0 = np.linspace(0.0, 1.0, T0 + 1)
     eps0 = oais.default_step_sizes(pr, beta0, oais.MALA)
-    code = {"bf16_tc": oais.CONTRACT_BF16_TC, "fp32": oais.CONTRACT_FP32}
+    code = {"bf16_tc": oais.CONTRACT_BF16_TC, "fp32": oais.CONTRACT_FP32,
+            "bf16_tc_stream": oais.CONTRACT_BF16_TC_STREAM}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def make_run(contraction):
@@ -241,7 +256,7 @@ def main():
     # the other form of the contraction, timed the same way (one step after one warm-up)
     compare = None
     if not args.no_compare:
-        other = "fp32" if args.contraction == "bf16_tc" else "bf16_tc"
+        other = "bf16_tc" if args.contraction == "fp32" else "fp32"
         r2 = make_run(other)
         t2, _, _, last2, _ = timed(r2, 1, 1)
         compare = {"contraction": other, "value": world * ps_per_job / (t2 / 1e3), "unit": METRIC,
@@ -281,7 +296,8 @@ def main():
                     "peak_source": f"measured ex2/rcp/lg2 rates {rates['ex2'] / 1e9:.1f}/"
                                    f"{rates['rcp'] / 1e9:.1f}/{rates['lg2'] / 1e9:.1f} G lane-ops/s/SM x "
                                    f"152 SMs (oais_measure_unit_rate)",
-                    "kernel": "oais_sweep_tc_kernel (tcgen05 bf16, MALA)",
+                    "kernel": ("oais_sweep_tc_kernel (tcgen05 bf16, X resident, MALA)" if args.contraction == "bf16_tc"
+                               else "oais_sweep_tcs_kernel<LOGREG, 32> (tcgen05 f16, X streamed, MALA)"),
                     "tensor_tflops_issued": 2 * algorithmic_flops_per_particle_step(pr) * 2048 / pr.n
                                             * ps_per_job * args.steps / sweep_s / 1e12}
     roofline["measured_rates_lane_ops_per_s_per_sm"] = rates
@@ -303,7 +319,8 @@ def main():
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if args.contraction == "bf16_tc" else "f32", "data": "synthetic",
+            "dtype": {"bf16_tc": "bf16", "bf16_tc_stream": "f16 (bf16-valued X)", "fp32": "f32"}[args.contraction],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "N_per_gpu": N_PARTICLES, "T_rounds": ROUNDS_T,
                        "move": "MALA", "l2": "flushed between timed steps (256 MiB write)",
                        "log_weights": "f64", "contraction": args.contraction},
@@ -339,6 +356,161 @@ def measure_e2e(pr, eps0, beta0, steps, contraction):
     return {"value": N_PARTICLES * sum(ROUNDS_T) * steps / dt, "unit": METRIC,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "includes": "context init with host data (workspace allocation included), 4 rounds"}
+
+
+def timed_job(job, steps, warmup, stream, clocks=None):
+    """CUDA-event time of `steps` calls of job() after `warmup`, L2 flushed before each."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        job()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    total, last = 0.0, None
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        last = job()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    return total, last, clk
+
+
+def bench_linreg(args):
+    """Linear regression d = 256 on the streamed tensor-core kernel (tensor-pipe bound)."""
+    import torch
+    from paper_2408_12057_gb300 import oais, workloads as W
+    torch.cuda.set_device(0)
+    pr = W.linreg()
+    N, rounds, L = 1 << 16, [64, 128, 256, 512], 5
+    stream = torch.cuda.current_stream()
+    beta0 = np.linspace(0.0, 1.0, rounds[0] + 1)
+    eps0 = oais.default_step_sizes(pr, beta0, oais.HMC)
+    run = oais.OAIS(pr, oais.HMC, N, beta0, T_max=max(rounds), eps=eps0, seed=12057, leapfrog=L, adapt=True,
+                    stream=stream, contraction=oais.CONTRACT_BF16_TC_STREAM)
+
+    def job():
+        run.set_schedule(beta0, eps0)
+        return [run.round(rounds[min(k + 1, len(rounds) - 1)]) for k in range(len(rounds))]
+
+    total, last, clk = timed_job(job, args.steps, args.warmup, stream, ClockSampler(0))
+    peaks, src = measured_peaks()
+    sweep_s = sum(r["sweep_ms"] for r in last) / 1e3
+    ps = N * sum(rounds)
+    evals = N * sum(1 + T * L for T in rounds)          # log L + gradient evaluations per job
+    alg = 4.0 * pr.n * pr.d * evals / sweep_s / 1e12   # z = X x and X^T r per evaluation
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+    print(json.dumps({
+        "metric": METRIC, "value": ps * args.steps / (total / 1e3), "unit": METRIC, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16 (bf16-valued X)", "data": "synthetic",
+        "config": {"workload": "linreg_n50000_d256_N65536_T64-128-256-512_hmc5", "N_per_gpu": N,
+                   "T_rounds": rounds, "move": "HMC, 5 leapfrog", "contraction": "bf16_tc_stream",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "logZ_last_round": last[-1]["logZ"], "se_last_round": last[-1]["se"],
+        "roofline": {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
+                     "traffic": None, "peak_source": f"{src} cuBLAS bf16 sustained (f16 runs at the same rate)",
+                     "issued_tflops": 2 * alg, "issued_frac": 2 * alg / peak,
+                     "note": "achieved counts 4 n d FLOP per evaluation; the two-term operand split issues 2x",
+                     "kernel": "oais_sweep_tcs_kernel<LINREG, 256>"},
+        "gpu_launches": 3 * len(rounds) * args.steps, "clocks": clk,
+    }))
+    run.close()
+
+
+def bench_batched(args):
+    """64 uneven logistic problems in one persistent launch per round."""
+    import torch
+    from paper_2408_12057_gb300 import oais, workloads as W
+    torch.cuda.set_device(0)
+    probs = W.batched_logistic()
+    N, T, R = 1 << 14, 256, 3
+    stream = torch.cuda.current_stream()
+    beta0 = np.linspace(0.0, 1.0, T + 1)
+    eps0 = np.stack([oais.default_step_sizes(pr, beta0, oais.MALA) for pr in probs])
+    b = oais.OAISBatch(probs, oais.MALA, N, beta0, eps=eps0, seed=12057, stream=stream)
+    tuned = b.autotune(T_probe=4)
+
+    def set_all():
+        for p in range(len(probs)):
+            b.problem(p).set_schedule(beta0, eps0[p])
+
+    def job():
+        set_all()
+        return [b.round(T) for _ in range(R)]
+
+    total, last, clk = timed_job(job, args.steps, args.warmup, stream, ClockSampler(0))
+    rows = sum(pr.n for pr in probs)
+    ps = len(probs) * N * T * R
+    sweep_s = sum(r[0]["sweep_ms"] for r in last) / 1e3
+    rates = {name: oais.measure_unit_rate(u) for name, u in
+             [("ex2", oais.UNIT_EX2), ("rcp", oais.UNIT_RCP), ("lg2", oais.UNIT_LG2)]}
+    peaks, src = measured_peaks()
+    tpeak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1e12
+    # per problem the binding unit: special-function work (1 ex2 + 1 rcp + 1/16 lg2 per row
+    # and evaluation) or the tensor pipe (two-term split: 8 n d FLOP per evaluation); the
+    # roofline time of the job is the sum of the per-problem maxima
+    sec_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (16.0 * rates["lg2"])
+    t_bound = 0.0
+    for pr in probs:
+        ev = N * (1 + T) * R
+        t_sfu = pr.n * ev * sec_row_sm / N_SM
+        t_tc = 8.0 * pr.n * (16 if pr.d <= 16 else 32 if pr.d <= 32 else 64 if pr.d <= 64 else 128) * ev / tpeak
+        t_bound += max(t_sfu, t_tc)
+    line = {
+        "metric": METRIC, "value": ps * args.steps / (total / 1e3), "unit": METRIC, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16 (bf16-valued X)", "data": "synthetic",
+        "config": {"workload": "batched64_logreg_n500-50000_d8-128_N16384_T256x3_mala", "problems": len(probs),
+                   "rows_total": rows, "N_per_problem": N, "T": T, "rounds": R, "ring_depths_tuned": tuned,
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "roofline": {"bound": "sfu or tensor per problem", "achieved_s": sweep_s / args.steps,
+                     "bound_s": t_bound, "frac": t_bound / (sweep_s / args.steps), "traffic": None,
+                     "peak_source": f"measured unit rates (oais_measure_unit_rate) and {src} bf16 sustained",
+                     "kernel": "oais_sweep_tcs_batch_kernel<LOGREG>"},
+        "gpu_launches": (1 + 2 * len(probs)) * R * args.steps, "clocks": clk,
+    }
+    if args.compare_sequential:
+        singles = []
+        for p, pr in enumerate(probs):
+            s = oais.OAIS(pr, oais.MALA, N, beta0, eps=eps0[p], seed=12057, stream=stream,
+                          contraction=oais.CONTRACT_BF16_TC_STREAM)
+            s.set_problem(p)
+            singles.append(s)
+
+        def seq_job():
+            out = []
+            for p, s in enumerate(singles):
+                s.set_schedule(beta0, eps0[p])
+                out.append([s.round(T) for _ in range(R)])
+            return out
+
+        t_seq, _, _ = timed_job(seq_job, 1, 1, stream)
+        line["sequential_tc"] = {"value": ps / (t_seq / 1e3), "unit": METRIC, "ms_per_step": t_seq}
+        small = [p for p, pr in enumerate(probs) if pr.d <= 32]
+        fps = [oais.OAIS(probs[p], oais.MALA, N, beta0, eps=eps0[p], seed=12057, stream=stream,
+                         contraction=oais.CONTRACT_FP32) for p in small]
+
+        def fp32_job():
+            for p, s in zip(small, fps):
+                s.set_schedule(beta0, eps0[p])
+                for _ in range(R):
+                    s.round(T)
+
+        t_fp, _, _ = timed_job(fp32_job, 1, 1, stream)
+        line["sequential_fp32_d_le_32"] = {
+            "value": len(small) * N * T * R / (t_fp / 1e3), "unit": METRIC, "ms_per_step": t_fp,
+            "problems": len(small), "note": "the CUDA-core FP32 form exists for d <= 32 only"}
+        line["batched_vs_sequential_tc"] = t_seq / (total / args.steps)
+        for s in singles + fps:
+            s.close()
+    print(json.dumps(line))
+    b.close()
 
 
 if __name__ == "__main__":
