@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other form of the contraction")
     ap.add_argument("--workload", default="logreg", choices=["logreg", "linreg", "batched"])
+    ap.add_argument("--x-storage", default="bf16", choices=["bf16", "fp8"],
+                    help="linreg: X held as bf16 values (f16 encoding) or FP8 e4m3 with per-row scales")
     ap.add_argument("--compare-sequential", action="store_true",
                     help="batched: also time the problems one after another (single contexts)")
     a = ap.parse_args()
@@ -391,8 +393,9 @@ def bench_linreg(args):
     stream = torch.cuda.current_stream()
     beta0 = np.linspace(0.0, 1.0, rounds[0] + 1)
     eps0 = oais.default_step_sizes(pr, beta0, oais.HMC)
+    contraction = oais.CONTRACT_FP8_TC_STREAM if args.x_storage == "fp8" else oais.CONTRACT_BF16_TC_STREAM
     run = oais.OAIS(pr, oais.HMC, N, beta0, T_max=max(rounds), eps=eps0, seed=12057, leapfrog=L, adapt=True,
-                    stream=stream, contraction=oais.CONTRACT_BF16_TC_STREAM)
+                    stream=stream, contraction=contraction)
 
     def job():
         run.set_schedule(beta0, eps0)
@@ -410,14 +413,15 @@ def bench_linreg(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16 (bf16-valued X)", "data": "synthetic",
         "config": {"workload": "linreg_n50000_d256_N65536_T64-128-256-512_hmc5", "N_per_gpu": N,
-                   "T_rounds": rounds, "move": "HMC, 5 leapfrog", "contraction": "bf16_tc_stream",
+                   "T_rounds": rounds, "move": "HMC, 5 leapfrog", "contraction": "tc_stream",
+                   "x_storage": args.x_storage,
                    "l2": "flushed between timed steps (256 MiB write)"},
         "logZ_last_round": last[-1]["logZ"], "se_last_round": last[-1]["se"],
         "roofline": {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
                      "traffic": None, "peak_source": f"{src} cuBLAS bf16 sustained (f16 runs at the same rate)",
                      "issued_tflops": 2 * alg, "issued_frac": 2 * alg / peak,
                      "note": "achieved counts 4 n d FLOP per evaluation; the two-term operand split issues 2x",
-                     "kernel": "oais_sweep_tcs_kernel<LINREG, 256>"},
+                     "kernel": f"oais_sweep_tcs_kernel<LINREG, 256, {1 if args.x_storage == 'fp8' else 0}>"},
         "gpu_launches": 3 * len(rounds) * args.steps, "clocks": clk,
     }))
     run.close()

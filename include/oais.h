@@ -79,6 +79,12 @@ typedef struct {
                              f16), states and residuals split into two f16 terms (relative
                              error ~2^-22); any n, d <= 256, LOGREG (MALA) or LINREG (MALA,
                              HMC).
+                           OAIS_CONTRACT_FP8_TC_STREAM: the streamed form with X stored as
+                             FP8 e4m3 with one scale per row: s_r = max_j |X_rj| / 448 (fp32;
+                             1 for a zero row), q_rj = e4m3(X_rj / s_r) rounded to nearest
+                             even, and the sampler targets X~_rj = s_r q_rj.  The chunks are
+                             expanded to f16 on chip (exact), so the contraction keeps the
+                             accuracy of the f16 form; LINREG only.
                            The tensor-core forms run the OAIS sweep (oais_round and the shard
                            calls) and, for the streamed form, oais_potential; resampling
                            rounds (oasmc_round) and oais_ctx_sweep use the CUDA-core form,
@@ -90,7 +96,8 @@ typedef struct {
 typedef enum {
     OAIS_CONTRACT_FP32 = 0,
     OAIS_CONTRACT_BF16_TC = 1,
-    OAIS_CONTRACT_BF16_TC_STREAM = 2
+    OAIS_CONTRACT_BF16_TC_STREAM = 2,
+    OAIS_CONTRACT_FP8_TC_STREAM = 3
 } oais_contraction;
 
 typedef enum { OAIS_RWMH = 0, OAIS_MALA = 1, OAIS_HMC = 2 } oais_move_kind;

@@ -199,7 +199,7 @@ struct Layout {
 // which sweep form a target runs: 0 CUDA cores, 1 resident tensor-core, 2 streamed tensor-core
 static int sweep_form(const oais_target* tg, const oais_move* mv)
 {
-    if (tg->contraction == OAIS_CONTRACT_BF16_TC_STREAM) return 2;
+    if (tg->contraction == OAIS_CONTRACT_BF16_TC_STREAM || tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM) return 2;
     if (tg->contraction != OAIS_CONTRACT_BF16_TC) return 0;
     if (tg->kind == kLogreg && tg->d <= 32 && tg->n <= tc_max_rows() && mv->kind == OAIS_MALA) return 1;
     return 2;
@@ -247,7 +247,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     L.tc_img = take(form == 1 ? (size_t)tc_image_bytes() : 0);
     L.tc_y = take(form == 1 ? (size_t)tc_max_rows() / 8 : 0);
     TcsPlan tp;
-    if (form == 2) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0);
+    if (form == 2) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
     L.tcs_img = take(form == 2 ? tp.img_bytes : 0);
     L.tcs_state = take(form == 2 ? sizeof(float) * 5 * (size_t)tp.dp * tcs_tiles(N) * 128 : 0);
     L.total = off;
@@ -266,8 +266,10 @@ static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais
     if (tg->kind == kGmm && tg->n > GmmTarget<float, 16>::kMaxK)
         return fail(ctx, OAIS_EUNSUPPORTED, "at most 16 mixture components");
     if (tg->dtype != OAIS_DT_F64 && tg->dtype != OAIS_DT_F32) return fail(ctx, OAIS_EINVAL, "bad dtype");
-    if (tg->contraction < OAIS_CONTRACT_FP32 || tg->contraction > OAIS_CONTRACT_BF16_TC_STREAM)
+    if (tg->contraction < OAIS_CONTRACT_FP32 || tg->contraction > OAIS_CONTRACT_FP8_TC_STREAM)
         return fail(ctx, OAIS_EINVAL, "bad contraction");
+    if (tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM && tg->kind != kLinreg)
+        return fail(ctx, OAIS_EUNSUPPORTED, "FP8 storage of X is built for LINREG");
     if (tg->contraction != OAIS_CONTRACT_FP32) {
         const bool fam = (tg->kind == kLogreg && mv->kind == OAIS_MALA) ||
                          (tg->kind == kLinreg && (mv->kind == OAIS_MALA || mv->kind == OAIS_HMC));
@@ -275,7 +277,7 @@ static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais
             return fail(ctx, OAIS_EUNSUPPORTED,
                         "the tensor-core contraction is built for LOGREG (MALA) and LINREG (MALA, HMC), d <= 256");
         if (sweep_form(tg, mv) == 2) {
-            const TcsPlan tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0);
+            const TcsPlan tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
             const int Le = mv->kind == OAIS_HMC ? mv->leapfrog : 1;
             const double chunks = (1.0 + (double)T_max * mv->moves * Le) * tp.nch;
             if (!tp.ok || chunks >= 4294967295.0)
@@ -443,10 +445,13 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
             std::vector<float> Xf((size_t)tg->n * tg->d), yf(tg->n);
             for (size_t i = 0; i < Xf.size(); ++i) Xf[i] = (float)Xh[i];
             for (int r = 0; r < tg->n; ++r) yf[r] = (float)yh[r];
-            const TcsPlan tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0);
+            const bool q8 = tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM;
+            const TcsPlan tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, q8);
             std::vector<unsigned char> img;
-            tcs_prepare(tp, tg->kind, Xf.data(), yf.data(), tg->n, tg->d, img);
+            if (q8) tcs_prepare_q8(tp, Xf.data(), yf.data(), tg->n, tg->d, img);
+            else tcs_prepare(tp, tg->kind, Xf.data(), yf.data(), tg->n, tg->d, img);
             dt.tcs = true;
+            dt.tcs_q8 = q8;
             dt.tcs_img = b + L.tcs_img;
             dt.tcs_state = reinterpret_cast<float*>(b + L.tcs_state);
             e = cudaMemcpy(dt.tcs_img, img.data(), img.size(), cudaMemcpyHostToDevice);
@@ -633,7 +638,7 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         CK(cudaEventRecord(ctx->ev0, s));
         if (ctx->dt.tc) CK(launch_sweep_tc(P, ctx->dt.tc_img, ctx->dt.tc_ybits, ctx->dt.n, ctx->dt.d, s));
         else if (ctx->dt.tcs)
-            CK(launch_sweep_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0), ctx->dt.kind, P, ctx->dt.tcs_img,
+            CK(launch_sweep_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0, ctx->dt.tcs_q8), ctx->dt.kind, P, ctx->dt.tcs_img,
                                 ctx->dt.tcs_state, ctx->mv.kind, ctx->mv.leapfrog, ctx->dt.p0, ctx->dt.n,
                                 ctx->dt.d, s));
         else CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
@@ -972,7 +977,7 @@ oais_status oais_potential(oais_ctx* ctx, const void* d_x, int64_t N, double* d_
     if (ctx->dt.tcs) {
         if (N > 0xFFFFFFFFLL) return fail(ctx, OAIS_EINVAL, "N out of range");
         CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), static_cast<cudaStream_t>(stream)));
-        CK(launch_potential_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0), ctx->dt.kind, ctx->dt.tcs_img,
+        CK(launch_potential_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0, ctx->dt.tcs_q8), ctx->dt.kind, ctx->dt.tcs_img,
                                 static_cast<const float*>(d_x), N, d_ell, static_cast<float*>(d_grad), ctx->dt.p0,
                                 ctx->dt.n, ctx->dt.d, ctx->d_status, ctx->dt.tcs_state,
                                 (int64_t)tcs_tiles(ctx->N) * 128, static_cast<cudaStream_t>(stream)));

@@ -23,6 +23,7 @@ struct DevTarget {
     bool tcs = false;    // streamed tensor-core form: chunk images of X~ (and y), particle state
     void* tcs_img = nullptr;
     float* tcs_state = nullptr;
+    bool tcs_q8 = false; // the streamed form's X is stored as FP8 e4m3 with per-row scales
 };
 
 // Streamed tensor-core sweep (sweep_tcs.cu): sizes of one configuration.  dp = d padded to
@@ -33,12 +34,16 @@ struct DevTarget {
 struct TcsPlan {
     int dp = 0, chunk = 0, nch = 0, stages = 0, tmem_cols = 0;
     uint32_t y_off = 0, stage_bytes = 0, off_x = 0, off_misc = 0, smem = 0;
+    bool q8 = false;                     // FP8 e4m3 storage of X with per-row scales
+    int stages8 = 0;
+    uint32_t off_x8 = 0, stage8_bytes = 0;
     size_t img_bytes = 0;
     bool ok = false;
 };
-TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages);
+TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8 = false);
 void tcs_prepare(const TcsPlan& L, int kind, const float* X, const float* y, int n, int d,
                  std::vector<unsigned char>& img);
+void tcs_prepare_q8(const TcsPlan& L, const float* X, const float* y, int n, int d, std::vector<unsigned char>& img);
 int tcs_tiles(int64_t N);
 // state: 5 arrays [dp][tiles * 128] fp32 (accepted x, its gradient, proposal, momentum,
 // drained gradient sum)

@@ -45,6 +45,12 @@ constexpr int kTile = 128;
 constexpr int kEpiThreads = 256;
 constexpr int kThreads = kEpiThreads + 96;
 constexpr int kFwdWarp = 8, kLoadWarp = 9, kBwdWarp = 10;
+// FP8 storage of X (e4m3 values q with a per-row scale s, X~ = s q): one more warp expands each
+// chunk from the FP8 ring into the f16 stage the MMAs read, two rows per thread (a 12-warp
+// block keeps the register budget of the other roles)
+constexpr int kCvtWarp0 = 11, kCvtThreads = 32;
+constexpr int kThreadsQ8 = kThreads + kCvtThreads;
+__host__ __device__ constexpr int threads_for(int q8) { return q8 ? kThreadsQ8 : kThreads; }
 constexpr int kSlice = 8;   // coordinates per state-update step (one 16-byte f16 chunk)
 // The tensor core rounds each accumulation toward zero, so a long running sum in one TMEM
 // accumulator drifts toward zero by about half an ulp per MMA (a relative shrink of ~1e-4
@@ -107,7 +113,9 @@ struct Params {
     int64_t Np;
     int seg;                    // chunks per gradient segment (see kSegMmas)
     int n, d, dp, nch, stages;
-    uint32_t stage_bytes, y_off;
+    uint32_t stage_bytes, y_off;   // f16 stage: lines, then y [64] and (FP8 storage) s [64]
+    uint32_t off_x8, stage8_bytes; // FP8 storage: ring of chunk images (q rows, y, s)
+    int stages8;
     uint32_t off_x, off_misc;   // shared-memory regions (A starts at 0)
     uint32_t tmem_cols;
     int move, leapfrog;
@@ -125,6 +133,7 @@ struct Params {
 // misc region: barriers, TMEM address, abort flag, exchange buffers, moment scratch
 struct Misc {
     uint64_t xfull[8], xempty[8];
+    uint64_t x8full[4], x8empty[4];
     uint64_t d1full, d1empty, rfull, rempty;
     uint64_t afull, d2full, done, d2seg, d2drained;
     uint32_t tmem;
@@ -243,7 +252,7 @@ struct Thread {
 
     // log L at the positions just written to A (this thread's half of the rows' terms summed
     // with the other half's), leaving grad log L / gscale in D2.
-    template <int FAM>
+    template <int FAM, int Q8>
     __device__ double eval()
     {
         tmem_wait_st();   // A_lo in TMEM
@@ -275,13 +284,26 @@ struct Thread {
                 wait(&M->xfull[xs], xph);   // y of this chunk is in the stage
                 const float* ys = reinterpret_cast<const float*>(smem + P->off_x + (uint32_t)xs * P->stage_bytes +
                                                                  P->y_off) + h * HC;
+                if constexpr (Q8) {
+                    // X~_r = s_r q_r: z = s_r (q_r . x), and the backward's factor is r s_r
+                    const float* ss = ys + CHUNK;
 #pragma unroll
-                for (int j = 0; j < HC; j += 2) {
-                    const float r0 = ys[j] - __uint_as_float(v[j]);
-                    const float r1 = ys[j + 1] - __uint_as_float(v[j + 1]);
-                    part0 = fmaf(r0, r0, part0);
-                    part0 = fmaf(r1, r1, part0);
-                    split_pair_h(r0, r1, hi[j / 2], lo[j / 2]);
+                    for (int j = 0; j < HC; j += 2) {
+                        const float r0 = fmaf(-ss[j], __uint_as_float(v[j]), ys[j]);
+                        const float r1 = fmaf(-ss[j + 1], __uint_as_float(v[j + 1]), ys[j + 1]);
+                        part0 = fmaf(r0, r0, part0);
+                        part0 = fmaf(r1, r1, part0);
+                        split_pair_h(r0 * ss[j], r1 * ss[j + 1], hi[j / 2], lo[j / 2]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < HC; j += 2) {
+                        const float r0 = ys[j] - __uint_as_float(v[j]);
+                        const float r1 = ys[j + 1] - __uint_as_float(v[j + 1]);
+                        part0 = fmaf(r0, r0, part0);
+                        part0 = fmaf(r1, r1, part0);
+                        split_pair_h(r0, r1, hi[j / 2], lo[j / 2]);
+                    }
                 }
             } else {
                 // X'_r = s_r X~_r with s_r = 2 y_r - 1, so u = s z; log sigmoid(u) =
@@ -391,7 +413,7 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar)
 }
 // (thread 0) fresh barriers for one tile; prev_stages > 0: the previous tile's barriers (with
 // that many stage pairs) are invalidated first
-__device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stages)
+__device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stages, int stages8 = 0)
 {
     uint64_t* all[] = {&M->d1full, &M->d1empty, &M->rfull, &M->rempty, &M->afull, &M->d2full,
                        &M->done, &M->d2seg, &M->d2drained};
@@ -399,9 +421,15 @@ __device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stag
         for (int s = 0; s < prev_stages; ++s) { mbar_inval(saddr(&M->xfull[s])); mbar_inval(saddr(&M->xempty[s])); }
         for (uint64_t* b : all) mbar_inval(saddr(b));
     }
+    // f16 stages are filled by the bulk copy (one arrival + bytes) or, with FP8 storage, by
+    // the two converter warps
     for (int s = 0; s < stages; ++s) {
-        mbar_init(saddr(&M->xfull[s]), 1);
+        mbar_init(saddr(&M->xfull[s]), stages8 > 0 ? kCvtThreads / 32 : 1);
         mbar_init(saddr(&M->xempty[s]), 1);
+    }
+    for (int s = 0; s < stages8; ++s) {
+        mbar_init(saddr(&M->x8full[s]), 1);
+        mbar_init(saddr(&M->x8empty[s]), kCvtThreads / 32);
     }
     mbar_init(saddr(&M->d1full), 1);
     mbar_init(saddr(&M->d1empty), kEpiThreads / 32);
@@ -418,7 +446,7 @@ __device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stag
 
 // One tile (128 particles) of one problem for a whole sweep, by all 352 threads of the CTA;
 // the barriers are fresh and TMEM (512 columns at `tmem`) is held by the caller.
-template <int FAM, int DP>
+template <int FAM, int DP, int Q8>
 __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_t tiles, unsigned char* smem,
                                          uint32_t tmem)
 {
@@ -435,27 +463,76 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
     if (warp == kLoadWarp) {
         // ---------------- producer: chunk images into the stage ring ----------------
         if (lane == 0) {
+            // with FP8 storage the copies fill the FP8 ring (freed by the converters)
+            const int ring = Q8 ? P.stages8 : P.stages;
+            const uint32_t bytes = Q8 ? P.stage8_bytes : P.stage_bytes;
+            uint64_t* full = Q8 ? M->x8full : M->xfull;
+            uint64_t* empty = Q8 ? M->x8empty : M->xempty;
             int s = 0;
             uint32_t ph = 0, issued = 0;
-            const uint32_t sbase = saddr(smem + P.off_x);
+            const uint32_t sbase = saddr(smem + (Q8 ? P.off_x8 : P.off_x));
             for (uint32_t g = 0, c = 0; g < total; ++g) {
                 if (M->abort) break;
-                if (!mbar_wait(saddr(&M->xempty[s]), ph ^ 1u, &M->abort)) {
+                if (!mbar_wait(saddr(&empty[s]), ph ^ 1u, &M->abort)) {
                     M->abort = 1;
                     atomicOr(S.status, 2u);
                     break;
                 }
-                mbar_arrive_expect_tx(saddr(&M->xfull[s]), P.stage_bytes);
-                bulk_g2s(sbase + (uint32_t)s * P.stage_bytes, P.img + (size_t)c * P.stage_bytes, P.stage_bytes,
-                         saddr(&M->xfull[s]));
+                mbar_arrive_expect_tx(saddr(&full[s]), bytes);
+                bulk_g2s(sbase + (uint32_t)s * bytes, P.img + (size_t)c * bytes, bytes, saddr(&full[s]));
                 ++issued;
                 if (++c == (uint32_t)P.nch) c = 0;
-                if (++s == P.stages) { s = 0; ph ^= 1u; }
+                if (++s == ring) { s = 0; ph ^= 1u; }
             }
             // copies still in flight land before the CTA ends (bounded)
-            const uint32_t first = issued > (uint32_t)P.stages ? issued - P.stages : 0u;
-            for (uint32_t g = first; g < issued; ++g)
-                mbar_wait(saddr(&M->xfull[g % P.stages]), (g / P.stages) & 1u);
+            const uint32_t first = issued > (uint32_t)ring ? issued - ring : 0u;
+            for (uint32_t g = first; g < issued; ++g) mbar_wait(saddr(&full[g % ring]), (g / ring) & 1u);
+        }
+    } else if (Q8 && warp >= kCvtWarp0) {
+        // ---------------- converter: FP8 chunk -> f16 stage (rows lane, lane + 32) ----------------
+        const int lane_c = threadIdx.x - kCvtWarp0 * 32;
+        int s8 = 0, s = 0;
+        uint32_t ph8 = 0, ph = 0;
+        for (uint32_t g = 0; g < total; ++g) {
+            if (!mbar_wait(saddr(&M->x8full[s8]), ph8, &M->abort) ||
+                !mbar_wait(saddr(&M->xempty[s]), ph ^ 1u, &M->abort)) {
+                M->abort = 1;
+                atomicOr(S.status, 2u);
+                break;
+            }
+            const unsigned char* src = smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes;
+            unsigned char* dst = smem + P.off_x + (uint32_t)s * P.stage_bytes;
+            for (int row = lane_c; row < CHUNK; row += 32) {
+                const unsigned char* qrow = src + (uint32_t)row * DP;
+#pragma unroll 4
+                for (int k0 = 0; k0 < DP; k0 += 16) {
+                    const uint4 raw = *reinterpret_cast<const uint4*>(qrow + k0);
+                    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+                    uint32_t hv[8];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        hv[2 * i] = cvt_f16x2_e4m3x2((uint16_t)(w[i] & 0xFFFFu));
+                        hv[2 * i + 1] = cvt_f16x2_e4m3x2((uint16_t)(w[i] >> 16));
+                    }
+                    *reinterpret_cast<uint4*>(dst + kmaj_off(row, k0, CHUNK, LA)) =
+                        make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    *reinterpret_cast<uint4*>(dst + kmaj_off(row, k0 + 8, CHUNK, LA)) =
+                        make_uint4(hv[4], hv[5], hv[6], hv[7]);
+                }
+                // y and s follow the rows in both layouts
+                const float* yq = reinterpret_cast<const float*>(src + (uint32_t)CHUNK * DP);
+                float* yd = reinterpret_cast<float*>(dst + P.y_off);
+                yd[row] = yq[row];
+                yd[CHUNK + row] = yq[CHUNK + row];
+            }
+            fence_proxy_async();   // the f16 stage, visible to the tensor core
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) {
+                mbar_arrive(saddr(&M->xfull[s]));
+                mbar_arrive(saddr(&M->x8empty[s8]));
+            }
+            if (++s8 == P.stages8) { s8 = 0; ph8 ^= 1u; }
+            if (++s == P.stages) { s = 0; ph ^= 1u; }
         }
     } else if (warp == kFwdWarp || warp == kBwdWarp) {
         // ---------------- MMA issue: forwards and backwards from two threads ----------------
@@ -582,7 +659,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                     xv[j] = i0 + j < P.d ? P.x_in[(int64_t)(i0 + j) * P.pstride + src] : 0.0f;
                 Th.write_a(i0, xv);
             }
-            const double ellv = Th.template eval<FAM>();
+            const double ellv = Th.template eval<FAM, Q8>();
             for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
                 float gv[kSlice];
                 Th.load_grad(i0, gv);
@@ -605,7 +682,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
             }
             Th.write_a(i0, z);
         }
-        double ell = Th.template eval<FAM>();
+        double ell = Th.template eval<FAM, Q8>();
         for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
             float gv[kSlice];
             Th.load_grad(i0, gv);
@@ -649,7 +726,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                 double ellp = 0.0;
                 float tail = 0.0f;   // MALA: |reverse noise|^2; HMC: |final momentum|^2
                 for (int l = 0; l < Le; ++l) {
-                    ellp = Th.template eval<FAM>();
+                    ellp = Th.template eval<FAM, Q8>();
                     const bool last = l + 1 == Le;
                     if (P.move == kHmc) {
                         const float f = last ? he : eps;
@@ -733,8 +810,8 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
     }
 }
 
-template <int FAM, int DP>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int FAM, int DP, int Q8>
+__global__ void __launch_bounds__(threads_for(Q8), 1)
 oais_sweep_tcs_kernel(const Params P)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -744,7 +821,7 @@ oais_sweep_tcs_kernel(const Params P)
     }
     Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
     const int warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) init_barriers(M, P.stages, 0);
+    if (threadIdx.x == 0) init_barriers(M, P.stages, 0, Q8 ? P.stages8 : 0);
     if (warp == 0) {
         tmem_alloc(saddr(&M->tmem), P.tmem_cols);
         tmem_relinquish();
@@ -753,7 +830,7 @@ oais_sweep_tcs_kernel(const Params P)
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&M->tmem);
-    run_tile<FAM, DP>(P, blockIdx.x, gridDim.x, smem, tmem);
+    run_tile<FAM, DP, Q8>(P, blockIdx.x, gridDim.x, smem, tmem);
     tc_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, P.tmem_cols);
@@ -801,10 +878,10 @@ oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __res
         const uint32_t tile = items[it].y;
         const uint32_t tiles = (uint32_t)((sP.sp.N + kTile - 1) / kTile);
         switch (sP.dp) {
-        case 16: run_tile<FAM, 16>(sP, tile, tiles, smem, tmem); break;
-        case 32: run_tile<FAM, 32>(sP, tile, tiles, smem, tmem); break;
-        case 64: run_tile<FAM, 64>(sP, tile, tiles, smem, tmem); break;
-        case 128: run_tile<FAM, 128>(sP, tile, tiles, smem, tmem); break;
+        case 16: run_tile<FAM, 16, 0>(sP, tile, tiles, smem, tmem); break;
+        case 32: run_tile<FAM, 32, 0>(sP, tile, tiles, smem, tmem); break;
+        case 64: run_tile<FAM, 64, 0>(sP, tile, tiles, smem, tmem); break;
+        case 128: run_tile<FAM, 128, 0>(sP, tile, tiles, smem, tmem); break;
         default: if (threadIdx.x == 0) atomicOr(sP.sp.status, 8u);
         }
         // every role has finished the tile (its copies and MMAs complete) before the barriers
@@ -833,28 +910,39 @@ int padded_dim(int d)
 uint32_t align1024(uint32_t v) { return (v + 1023u) & ~1023u; }
 } // namespace
 
-TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages)
+TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8)
 {
     TcsPlan L{};
+    L.q8 = q8;
     L.dp = padded_dim(d);
     L.chunk = chunk > 0 ? chunk : tcs::chunk_rows(L.dp);
     L.nch = (n + L.chunk - 1) / L.chunk;
     L.y_off = (uint32_t)L.chunk * L.dp * 2;
-    L.stage_bytes = align1024(L.y_off + (kind == kLinreg ? (uint32_t)L.chunk * 4 : 0u));
+    // f16 stage: lines, y (linear regression), and with FP8 storage the row scales
+    const uint32_t tail = (kind == kLinreg ? (uint32_t)L.chunk * 4 : 0u) * (q8 ? 2u : 1u);
+    L.stage_bytes = align1024(L.y_off + tail);
     const uint32_t a_bytes = (uint32_t)tcs::kTile * L.dp * 2;   // hi term of the positions
     L.off_x = a_bytes;
     const uint32_t limit = 227u * 1024u;
     const uint32_t misc = (uint32_t)((sizeof(tcs::Misc) + 1023) & ~(size_t)1023);
+    if (q8) {
+        // FP8 chunk image (q rows, y, s) ring: three buffers, the rest to the f16 ring
+        L.stage8_bytes = align1024((uint32_t)L.chunk * L.dp + 2u * (uint32_t)L.chunk * 4u);
+        L.stages8 = 3;
+    }
+    const uint32_t ring8 = (uint32_t)L.stages8 * L.stage8_bytes;
     int S = stages > 0 ? stages : 8;
-    while (S > 2 && L.off_x + (uint32_t)S * L.stage_bytes + misc > limit) --S;
+    while (S > 2 && L.off_x + (uint32_t)S * L.stage_bytes + ring8 + misc > limit) --S;
     L.stages = S;
-    L.off_misc = L.off_x + (uint32_t)S * L.stage_bytes;
+    L.off_x8 = L.off_x + (uint32_t)S * L.stage_bytes;
+    L.off_misc = L.off_x8 + ring8;
     L.smem = L.off_misc + (uint32_t)sizeof(tcs::Misc);
     L.tmem_cols = 512;
     // 512 TMEM columns leave room for one CTA per SM: make the shared memory say so too
     if (L.tmem_cols == 512 && L.smem < 120u * 1024u) L.smem = 120u * 1024u;
-    L.img_bytes = (size_t)L.nch * L.stage_bytes;
-    L.ok = L.dp <= 256 && L.chunk == tcs::chunk_rows(L.dp) && L.smem <= limit && L.stages >= 2 && L.stages <= 8;
+    L.img_bytes = (size_t)L.nch * (q8 ? L.stage8_bytes : L.stage_bytes);
+    L.ok = L.dp <= 256 && L.chunk == tcs::chunk_rows(L.dp) && L.smem <= limit && L.stages >= 2 && L.stages <= 8 &&
+           (!q8 || kind == kLinreg);
     return L;
 }
 
@@ -892,6 +980,41 @@ void tcs_prepare(const TcsPlan& L, int kind, const float* X, const float* y, int
     }
 }
 
+// e4m3 (bias 7, three mantissa bits, subnormal quantum 2^-9, largest 448) nearest to a finite
+// |v| <= 448, ties to even
+static uint8_t e4m3_rn(float v)
+{
+    const uint8_t sign = std::signbit(v) ? 0x80u : 0u;
+    const double a = std::fabs((double)v);
+    if (a == 0.0) return sign;
+    int e = 0;
+    std::frexp(a, &e);                         // a in [2^(e-1), 2^e)
+    int E = std::max(e - 1, -6);               // below 2^-6: the subnormal quantum 2^-9
+    double r = std::nearbyint(std::ldexp(a, -(E - 3)));   // a / quantum, ties to even
+    if (r >= 16.0) { ++E; r = 8.0; }
+    if (r < 8.0) return sign | (uint8_t)r;     // subnormal (E == -6)
+    uint32_t ex = (uint32_t)(E + 7), mant = (uint32_t)r - 8u;
+    if (ex > 15u || (ex == 15u && mant > 6u)) { ex = 15u; mant = 6u; }
+    return sign | (uint8_t)(ex << 3) | (uint8_t)mant;
+}
+
+// FP8 chunk images: per row r the scale s_r = max_j |X_rj| / 448 (1 for a zero row, fp32) and
+// q_rj = e4m3(X_rj / s_r); per chunk [q rows (d_pad bytes each) | y | s]
+void tcs_prepare_q8(const TcsPlan& L, const float* X, const float* y, int n, int d, std::vector<unsigned char>& img)
+{
+    img.assign(L.img_bytes, 0);
+    for (int r = 0; r < n; ++r) {
+        const int c = r / L.chunk, rr = r % L.chunk;
+        unsigned char* st = img.data() + (size_t)c * L.stage8_bytes;
+        float mx = 0.0f;
+        for (int i = 0; i < d; ++i) mx = std::max(mx, std::fabs(X[(size_t)r * d + i]));
+        const float sc = mx > 0.0f ? mx / 448.0f : 1.0f;
+        for (int i = 0; i < d; ++i) st[(size_t)rr * L.dp + i] = e4m3_rn(X[(size_t)r * d + i] / sc);
+        std::memcpy(st + (size_t)L.chunk * L.dp + (size_t)rr * 4, &y[r], 4);
+        std::memcpy(st + (size_t)L.chunk * L.dp + (size_t)(L.chunk + rr) * 4, &sc, 4);
+    }
+}
+
 int tcs_tiles(int64_t N) { return (int)((N + tcs::kTile - 1) / tcs::kTile); }
 
 static void fill_params(tcs::Params& P, const TcsPlan& L, int kind, const SweepParams& sp, const void* img,
@@ -920,6 +1043,9 @@ static void fill_params(tcs::Params& P, const TcsPlan& L, int kind, const SweepP
     P.stages = L.stages;
     P.stage_bytes = L.stage_bytes;
     P.y_off = L.y_off;
+    P.off_x8 = L.off_x8;
+    P.stage8_bytes = L.stage8_bytes;
+    P.stages8 = L.stages8;
     P.off_x = L.off_x;
     P.off_misc = L.off_misc;
     P.tmem_cols = (uint32_t)L.tmem_cols;
@@ -941,11 +1067,22 @@ static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp,
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
         if (e != cudaSuccess) return e;
-        kern<<<tiles, tcs::kThreads, L.smem, s>>>(P);
+        kern<<<tiles, tcs::threads_for(L.q8 ? 1 : 0), L.smem, s>>>(P);
         return cudaGetLastError();
     };
     if (L.chunk != tcs::chunk_rows(L.dp)) return cudaErrorInvalidValue;
-#define OAIS_TCS_DP(FAMK, DPV) case DPV: return go(tcs::oais_sweep_tcs_kernel<FAMK, DPV>);
+    if (L.q8) {
+        if (kind != kLinreg) return cudaErrorInvalidValue;
+        switch (L.dp) {
+        case 16: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 16, 1>);
+        case 32: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 32, 1>);
+        case 64: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 64, 1>);
+        case 128: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 128, 1>);
+        case 256: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 256, 1>);
+        }
+        return cudaErrorInvalidValue;
+    }
+#define OAIS_TCS_DP(FAMK, DPV) case DPV: return go(tcs::oais_sweep_tcs_kernel<FAMK, DPV, 0>);
     if (kind == kLinreg) {
         switch (L.dp) {
         OAIS_TCS_DP(kLinreg, 16) OAIS_TCS_DP(kLinreg, 32) OAIS_TCS_DP(kLinreg, 64)

@@ -210,6 +210,14 @@ __host__ __device__ constexpr uint32_t idesc_kind_f16(int M, int N, bool bf16, b
 }
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn_major) { return idesc_kind_f16(M, N, true, b_mn_major); }
 
+// two e4m3 values (low byte first) to an f16 pair (exact: every e4m3 value is an f16 value)
+__device__ __forceinline__ uint32_t cvt_f16x2_e4m3x2(uint16_t v)
+{
+    uint32_t d;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(d) : "h"(v));
+    return d;
+}
+
 // special-function unit, flush-to-zero forms (documented PTX approximations)
 __device__ __forceinline__ float ex2_approx(float x)
 {

@@ -19,7 +19,7 @@ from . import _build
 GAUSS, LOGREG, GMM, LINREG = 0, 1, 2, 3
 RWMH, MALA, HMC = 0, 1, 2
 DT_F64, DT_F32 = 0, 1
-CONTRACT_FP32, CONTRACT_BF16_TC, CONTRACT_BF16_TC_STREAM = 0, 1, 2
+CONTRACT_FP32, CONTRACT_BF16_TC, CONTRACT_BF16_TC_STREAM, CONTRACT_FP8_TC_STREAM = 0, 1, 2, 3
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "non-finite value", 5: "device wait timed out", 6: "unsupported configuration"}

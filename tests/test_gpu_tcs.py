@@ -34,9 +34,19 @@ def oracle_target(pr):
     return o.Target(pr.kind, f16_of_bf16(pr.X), pr.y, pr.ref_scale, pr.p0)
 
 
-def run(pr, move, N, beta, eps, seed, leapfrog=5, rounds=1):
+def fp8_rows(X):
+    # X~_rj = s_r q_rj with s_r = max_j |X_rj| / 448 (fp32) and q = e4m3(X / s_r), rounded to
+    # nearest even by torch's own float8 conversion
+    X32 = np.ascontiguousarray(X, dtype=np.float32)
+    mx = np.abs(X32).max(axis=1)
+    s = np.where(mx > 0, mx / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    q = torch.from_numpy((X32 / s[:, None]).astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    return s.astype(np.float64)[:, None] * q
+
+
+def run(pr, move, N, beta, eps, seed, leapfrog=5, rounds=1, contraction=None):
     r = oais.OAIS(pr, move, N, beta, eps=eps, seed=seed, leapfrog=leapfrog,
-                  contraction=oais.CONTRACT_BF16_TC_STREAM)
+                  contraction=oais.CONTRACT_BF16_TC_STREAM if contraction is None else contraction)
     for _ in range(rounds):
         res = r.round(len(beta) - 1)
     logw, ell, x = r.particles()
@@ -177,3 +187,37 @@ def test_stream_rounds_repeat_bitwise():
     a = run(pr, oais.HMC, 512, beta, eps, 3, leapfrog=3)
     b = run(pr, oais.HMC, 512, beta, eps, 3, leapfrog=3)
     assert np.array_equal(a["logw"], b["logw"]) and np.array_equal(a["log_ghat"], b["log_ghat"])
+
+
+@pytest.mark.parametrize("n,d,N,T,move,L", [(300, 20, 300, 4, oais.HMC, 3), (130, 70, 256, 3, oais.MALA, 1),
+                                            (100, 256, 200, 2, oais.HMC, 5), (64, 8, 129, 3, oais.HMC, 2)])
+def test_stream_fp8_matches_oracle(n, d, N, T, move, L):
+    # X stored as FP8 e4m3 with per-row scales: the sampler targets X~ = s q, which the oracle
+    # receives dequantised
+    pr = W.linreg(n=n, d=d, seed=n + d)
+    beta = W.linear_schedule(T) ** 3
+    eps = oais.default_step_sizes(pr, beta, move)
+    g = run(pr, move, N, beta, eps, 31, leapfrog=L, contraction=oais.CONTRACT_FP8_TC_STREAM)
+    r = o.asmc(o.Target(pr.kind, fp8_rows(pr.X), pr.y, pr.ref_scale, pr.p0), move, N, beta, eps, 31, leapfrog=L)
+    ok = agree(g["logw"], g["ell"], g["x"], r["logw"], r["ell"], r["x"], r["margin"])
+    assert ok.mean() >= 0.9
+
+
+def test_stream_fp8_potential_full_size():
+    # single evaluations on the full-size linear-regression data stored as FP8
+    pr = W.linreg()
+    N = 512
+    xs = potential_states(pr, N, 4)
+    r = oais.OAIS(pr, oais.HMC, N, [0.0, 1.0], eps=0.01, seed=1, contraction=oais.CONTRACT_FP8_TC_STREAM)
+    ell, g = r.potential(torch.from_numpy(xs.T.copy()).cuda())
+    ell, g = ell.cpu().numpy(), g.cpu().numpy().T
+    r.close()
+    Xt = fp8_rows(pr.X)
+    tg = o.Target(pr.kind, Xt, pr.y, pr.ref_scale, pr.p0)
+    A = np.abs(Xt)
+    for i in [0, 1, N // 2, N - 1]:
+        xi = xs[i].astype(np.float64)
+        e_o, g_o = tg.log_lik(xi, grad=True)
+        assert ell[i] == pytest.approx(e_o, rel=1e-5), (i, ell[i], e_o)
+        scale = A.T @ (np.abs(tg.y) + A @ np.abs(xi)) / pr.p0 ** 2
+        assert (np.abs(g[i] - g_o) / scale).max() < 2.0 ** -20
