@@ -45,10 +45,11 @@ constexpr int kTile = 128;
 constexpr int kEpiThreads = 256;
 constexpr int kThreads = kEpiThreads + 96;
 constexpr int kFwdWarp = 8, kLoadWarp = 9, kBwdWarp = 10;
-// FP8 storage of X (e4m3 values q with a per-row scale s, X~ = s q): one more warp expands each
-// chunk from the FP8 ring into the f16 stage the MMAs read, two rows per thread (a 12-warp
-// block keeps the register budget of the other roles)
-constexpr int kCvtWarp0 = 11, kCvtThreads = 32;
+// FP8 storage of X (e4m3 values q with a per-row scale s, X~ = s q): two warps expand each
+// chunk from the FP8 ring into the f16 stage the MMAs read, one row per thread: the producer
+// warp (whose lane 0 also issues the copies) and one more warp (a 12-warp block keeps the
+// register budget of the other roles)
+constexpr int kCvtWarp0 = 11, kCvtThreads = 32, kCvtArrivals = 2;
 constexpr int kThreadsQ8 = kThreads + kCvtThreads;
 __host__ __device__ constexpr int threads_for(int q8) { return q8 ? kThreadsQ8 : kThreads; }
 constexpr int kSlice = 8;   // coordinates per state-update step (one 16-byte f16 chunk)
@@ -424,12 +425,12 @@ __device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stag
     // f16 stages are filled by the bulk copy (one arrival + bytes) or, with FP8 storage, by
     // the two converter warps
     for (int s = 0; s < stages; ++s) {
-        mbar_init(saddr(&M->xfull[s]), stages8 > 0 ? kCvtThreads / 32 : 1);
+        mbar_init(saddr(&M->xfull[s]), stages8 > 0 ? kCvtArrivals : 1);
         mbar_init(saddr(&M->xempty[s]), 1);
     }
     for (int s = 0; s < stages8; ++s) {
         mbar_init(saddr(&M->x8full[s]), 1);
-        mbar_init(saddr(&M->x8empty[s]), kCvtThreads / 32);
+        mbar_init(saddr(&M->x8empty[s]), kCvtArrivals);
     }
     mbar_init(saddr(&M->d1full), 1);
     mbar_init(saddr(&M->d1empty), kEpiThreads / 32);
@@ -446,6 +447,32 @@ __device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stag
 
 // One tile (128 particles) of one problem for a whole sweep, by all 352 threads of the CTA;
 // the barriers are fresh and TMEM (512 columns at `tmem`) is held by the caller.
+// FP8 -> f16 stage: row `row` of a chunk (q bytes to the swizzled f16 lines), its y and s
+template <int DP>
+__device__ __forceinline__ void convert_row(const unsigned char* src, unsigned char* dst, int row, uint32_t y_off)
+{
+    constexpr int CHUNK = chunk_rows(DP);
+    constexpr KLayout LA = klayout(DP);
+    const unsigned char* qrow = src + (uint32_t)row * DP;
+#pragma unroll 4
+    for (int k0 = 0; k0 < DP; k0 += 16) {
+        const uint4 raw = *reinterpret_cast<const uint4*>(qrow + k0);
+        const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+        uint32_t hv[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            hv[2 * i] = cvt_f16x2_e4m3x2((uint16_t)(w[i] & 0xFFFFu));
+            hv[2 * i + 1] = cvt_f16x2_e4m3x2((uint16_t)(w[i] >> 16));
+        }
+        *reinterpret_cast<uint4*>(dst + kmaj_off(row, k0, CHUNK, LA)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(dst + kmaj_off(row, k0 + 8, CHUNK, LA)) = make_uint4(hv[4], hv[5], hv[6], hv[7]);
+    }
+    const float* yq = reinterpret_cast<const float*>(src + (uint32_t)CHUNK * DP);
+    float* yd = reinterpret_cast<float*>(dst + y_off);
+    yd[row] = yq[row];
+    yd[CHUNK + row] = yq[CHUNK + row];
+}
+
 template <int FAM, int DP, int Q8>
 __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_t tiles, unsigned char* smem,
                                          uint32_t tmem)
@@ -460,17 +487,67 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
     const uint32_t D2 = tmem + (uint32_t)kColD2;
     constexpr KLayout LA = klayout(DP);
 
-    if (warp == kLoadWarp) {
+    if (Q8 && warp == kLoadWarp) {
+        // ---------------- producer + converter (rows 0-31) ----------------
+        // lane 0 keeps the FP8 ring full: it issues every copy whose ring slot is free, from
+        // inside the warp's waits, so the warp never blocks on a copy nobody has issued
+        uint32_t issued = 0, c = 0, pph = 0;
+        int ps = 0;
+        const uint32_t bytes8 = P.stage8_bytes;
+        const uint32_t base8 = saddr(smem + P.off_x8);
+        auto try_issue = [&]() {
+            while (issued < total && mbar_try_wait(saddr(&M->x8empty[ps]), pph ^ 1u)) {
+                mbar_arrive_expect_tx(saddr(&M->x8full[ps]), bytes8);
+                bulk_g2s(base8 + (uint32_t)ps * bytes8, P.img + (size_t)c * bytes8, bytes8, saddr(&M->x8full[ps]));
+                ++issued;
+                if (++c == (uint32_t)P.nch) c = 0;
+                if (++ps == P.stages8) { ps = 0; pph ^= 1u; }
+            }
+        };
+        auto wait_issuing = [&](uint32_t bar, uint32_t parity) -> bool {
+            const uint64_t t0 = globaltimer();
+            for (;;) {
+                if (lane == 0) try_issue();
+                if (mbar_try_wait(bar, parity)) return true;
+                if (M->abort || globaltimer() - t0 > kWaitLimitNs) return false;
+            }
+        };
+        int s8 = 0, s = 0;
+        uint32_t ph8 = 0, ph = 0;
+        for (uint32_t g = 0; g < total; ++g) {
+            if (!wait_issuing(saddr(&M->x8full[s8]), ph8) || !wait_issuing(saddr(&M->xempty[s]), ph ^ 1u)) {
+                M->abort = 1;
+                atomicOr(S.status, 2u);
+                break;
+            }
+            convert_row<DP>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
+                            lane, P.y_off);
+            fence_proxy_async();   // the f16 stage, visible to the tensor core
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(saddr(&M->xfull[s]));
+                mbar_arrive(saddr(&M->x8empty[s8]));
+                try_issue();
+            }
+            if (++s8 == P.stages8) { s8 = 0; ph8 ^= 1u; }
+            if (++s == P.stages) { s = 0; ph ^= 1u; }
+        }
+        // copies still in flight land before the CTA ends (bounded)
+        if (lane == 0) {
+            const uint32_t first = issued > (uint32_t)P.stages8 ? issued - P.stages8 : 0u;
+            for (uint32_t g = first; g < issued; ++g)
+                mbar_wait(saddr(&M->x8full[g % P.stages8]), (g / P.stages8) & 1u);
+        }
+    } else if (warp == kLoadWarp) {
         // ---------------- producer: chunk images into the stage ring ----------------
         if (lane == 0) {
-            // with FP8 storage the copies fill the FP8 ring (freed by the converters)
-            const int ring = Q8 ? P.stages8 : P.stages;
-            const uint32_t bytes = Q8 ? P.stage8_bytes : P.stage_bytes;
-            uint64_t* full = Q8 ? M->x8full : M->xfull;
-            uint64_t* empty = Q8 ? M->x8empty : M->xempty;
+            const int ring = P.stages;
+            const uint32_t bytes = P.stage_bytes;
+            uint64_t* full = M->xfull;
+            uint64_t* empty = M->xempty;
             int s = 0;
             uint32_t ph = 0, issued = 0;
-            const uint32_t sbase = saddr(smem + (Q8 ? P.off_x8 : P.off_x));
+            const uint32_t sbase = saddr(smem + P.off_x);
             for (uint32_t g = 0, c = 0; g < total; ++g) {
                 if (M->abort) break;
                 if (!mbar_wait(saddr(&empty[s]), ph ^ 1u, &M->abort)) {
@@ -489,8 +566,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
             for (uint32_t g = first; g < issued; ++g) mbar_wait(saddr(&full[g % ring]), (g / ring) & 1u);
         }
     } else if (Q8 && warp >= kCvtWarp0) {
-        // ---------------- converter: FP8 chunk -> f16 stage (rows lane, lane + 32) ----------------
-        const int lane_c = threadIdx.x - kCvtWarp0 * 32;
+        // ---------------- converter: FP8 chunk -> f16 stage (rows 32-63) ----------------
         int s8 = 0, s = 0;
         uint32_t ph8 = 0, ph = 0;
         for (uint32_t g = 0; g < total; ++g) {
@@ -500,31 +576,8 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                 atomicOr(S.status, 2u);
                 break;
             }
-            const unsigned char* src = smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes;
-            unsigned char* dst = smem + P.off_x + (uint32_t)s * P.stage_bytes;
-            for (int row = lane_c; row < CHUNK; row += 32) {
-                const unsigned char* qrow = src + (uint32_t)row * DP;
-#pragma unroll 4
-                for (int k0 = 0; k0 < DP; k0 += 16) {
-                    const uint4 raw = *reinterpret_cast<const uint4*>(qrow + k0);
-                    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
-                    uint32_t hv[8];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        hv[2 * i] = cvt_f16x2_e4m3x2((uint16_t)(w[i] & 0xFFFFu));
-                        hv[2 * i + 1] = cvt_f16x2_e4m3x2((uint16_t)(w[i] >> 16));
-                    }
-                    *reinterpret_cast<uint4*>(dst + kmaj_off(row, k0, CHUNK, LA)) =
-                        make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                    *reinterpret_cast<uint4*>(dst + kmaj_off(row, k0 + 8, CHUNK, LA)) =
-                        make_uint4(hv[4], hv[5], hv[6], hv[7]);
-                }
-                // y and s follow the rows in both layouts
-                const float* yq = reinterpret_cast<const float*>(src + (uint32_t)CHUNK * DP);
-                float* yd = reinterpret_cast<float*>(dst + P.y_off);
-                yd[row] = yq[row];
-                yd[CHUNK + row] = yq[CHUNK + row];
-            }
+            convert_row<DP>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
+                            32 + lane, P.y_off);
             fence_proxy_async();   // the f16 stage, visible to the tensor core
             __syncwarp();
             if ((threadIdx.x & 31) == 0) {
