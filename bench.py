@@ -58,14 +58,17 @@ def parse():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other form of the contraction")
     ap.add_argument("--workload", default="logreg", choices=["logreg", "linreg", "batched"])
+    ap.add_argument("--particles", type=int, default=None,
+                    help="linreg / batched: particles per problem (profiling a smaller case)")
     ap.add_argument("--x-storage", default="bf16", choices=["bf16", "fp8"],
                     help="linreg: X held as bf16 values (f16 encoding) or FP8 e4m3 with per-row scales")
     ap.add_argument("--compare-sequential", action="store_true",
                     help="batched: also time the problems one after another (single contexts)")
     a = ap.parse_args()
-    if a.rounds:
+    a.rounds_list = [int(v) for v in a.rounds.split(",")] if a.rounds else None
+    if a.rounds_list and a.workload == "logreg":
         global ROUNDS_T
-        ROUNDS_T = [int(v) for v in a.rounds.split(",")]
+        ROUNDS_T = a.rounds_list
     return a
 
 
@@ -389,7 +392,7 @@ def bench_linreg(args):
     from paper_2408_12057_gb300 import oais, workloads as W
     torch.cuda.set_device(0)
     pr = W.linreg()
-    N, rounds, L = 1 << 16, [64, 128, 256, 512], 5
+    N, rounds, L = args.particles or (1 << 16), args.rounds_list or [64, 128, 256, 512], 5
     stream = torch.cuda.current_stream()
     beta0 = np.linspace(0.0, 1.0, rounds[0] + 1)
     eps0 = oais.default_step_sizes(pr, beta0, oais.HMC)
@@ -433,7 +436,7 @@ def bench_batched(args):
     from paper_2408_12057_gb300 import oais, workloads as W
     torch.cuda.set_device(0)
     probs = W.batched_logistic()
-    N, T, R = 1 << 14, 256, 3
+    N, T, R = args.particles or (1 << 14), (args.rounds_list or [256])[0], 3
     stream = torch.cuda.current_stream()
     beta0 = np.linspace(0.0, 1.0, T + 1)
     eps0 = np.stack([oais.default_step_sizes(pr, beta0, oais.MALA) for pr in probs])

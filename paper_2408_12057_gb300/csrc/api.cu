@@ -1171,7 +1171,7 @@ oais_status oais_batch_init(oais_batch** out, int32_t P, const oais_target* targ
     std::vector<uint2> items;
     batch_items(b, items);
     b->n_items = (uint32_t)items.size();
-    b->pbytes = (tcs_params_bytes() + 15) & ~(size_t)15;
+    b->pbytes = tcs_params_bytes();   // the kernel indexes the blocks as an array: no padding
     b->sched_stride = 2 * (size_t)T_max + 1;
     b->out_stride = 4 * (size_t)T_max + 2;
     int dev = 0, sms = 0;

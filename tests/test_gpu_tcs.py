@@ -221,3 +221,29 @@ def test_stream_fp8_potential_full_size():
         assert ell[i] == pytest.approx(e_o, rel=1e-5), (i, ell[i], e_o)
         scale = A.T @ (np.abs(tg.y) + A @ np.abs(xi)) / pr.p0 ** 2
         assert (np.abs(g[i] - g_o) / scale).max() < 2.0 ** -20
+
+
+def test_stream_linreg_logZ_and_gradient_closed_form():
+    # stable regime (n = 400, d = 8, Lambda ~ 17): three OAIS rounds of the streamed HMC kernel
+    # estimate log Z and the Fisher-identity gradient d log Z / d(log tau, log sigma) of the
+    # posterior of X~, both against their closed forms (Woodbury / determinant lemma)
+    from test_oracle_closed_forms import linreg_grad_closed, linreg_logZ_woodbury
+    pr = W.linreg(n=400, d=8, seed=11)
+    Xt, y = f16_of_bf16(pr.X), pr.y.astype(np.float64)
+    lz = linreg_logZ_woodbury(Xt, y, pr.ref_scale, pr.p0)
+    gc = linreg_grad_closed(Xt, y, pr.ref_scale, pr.p0)
+    N, T = 8192, 256
+    beta = W.linear_schedule(T)
+    eps = oais.default_step_sizes(pr, beta, oais.HMC)
+    r = oais.OAIS(pr, oais.HMC, N, beta, eps=eps, seed=3, leapfrog=5, adapt=True,
+                  contraction=oais.CONTRACT_BF16_TC_STREAM)
+    for _ in range(3):
+        res = r.round(T)
+    assert abs(res["logZ"] - lz) < 4 * res["se"] + 0.05, (res, lz)
+    g = r.grad_logZ()
+    np.testing.assert_allclose(g, gc, rtol=0.05, atol=2.5)
+    # the gradient estimator itself: the oracle's weighted sum over the same particles
+    logw, ell, x = r.particles()
+    go = o.fisher_grad(oracle_target(pr), logw.cpu().numpy(), x.cpu().numpy().T.astype(np.float64))
+    np.testing.assert_allclose(g, go, rtol=1e-4, atol=1e-2)
+    r.close()
