@@ -452,6 +452,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
             else tcs_prepare(tp, tg->kind, Xf.data(), yf.data(), tg->n, tg->d, img);
             dt.tcs = true;
             dt.tcs_q8 = q8;
+            dt.tcs_dp = tp.dp;
             dt.tcs_img = b + L.tcs_img;
             dt.tcs_state = reinterpret_cast<float*>(b + L.tcs_state);
             e = cudaMemcpy(dt.tcs_img, img.data(), img.size(), cudaMemcpyHostToDevice);
@@ -1017,6 +1018,7 @@ struct oais_batch {
     cudaStream_t work = nullptr;          // the batch's own stream (captured; the default stream cannot be)
     cudaEvent_t ready = nullptr;
     int stages_class[4] = {0, 0, 0, 0};   // ring depth per d_pad class 16/32/64/128 (0: largest that fits)
+    int h = 2;                            // column split of the batched kernel
     std::vector<TcsPlan> plan;
     uint32_t off_misc = 0, smem = 0;
     size_t pbytes = 0, sched_stride = 0, out_stride = 0;
@@ -1057,11 +1059,19 @@ static void batch_plan(oais_batch* b)
 {
     b->plan.resize(b->P);
     uint32_t top = 0;
+    // one launch, one column split: the problems' own (default) split if they all agree, else 2
+    int h = 0;
     for (int p = 0; p < b->P; ++p) {
         const DevTarget& dt = b->ctx[p]->dt;
-        TcsPlan L = tcs_plan(dt.kind, dt.n, dt.d, 0, 0);
+        const int hp = tcs_plan(dt.kind, dt.n, dt.d, 0, 0, false, 0, dt.tcs_dp).h;
+        h = (p == 0 || h == hp) ? hp : 2;
+    }
+    b->h = h;
+    for (int p = 0; p < b->P; ++p) {
+        const DevTarget& dt = b->ctx[p]->dt;
+        TcsPlan L = tcs_plan(dt.kind, dt.n, dt.d, 0, 0, false, h, dt.tcs_dp);
         const int want = b->stages_class[dp_class(L.dp)];
-        if (want > 0 && want < L.stages) L = tcs_plan(dt.kind, dt.n, dt.d, 0, want);
+        if (want > 0 && want < L.stages) L = tcs_plan(dt.kind, dt.n, dt.d, 0, want, false, h, dt.tcs_dp);
         b->plan[p] = L;
         top = std::max(top, L.off_x + (uint32_t)L.stages * L.stage_bytes);
     }
@@ -1115,7 +1125,7 @@ static oais_status batch_enqueue(oais_batch* b, int T)
     BK(cudaMemsetAsync(b->d_head, 0, sizeof(uint32_t), s));
     // external records: inside a captured graph a plain record only orders the capture
     BK(cudaEventRecordWithFlags(b->ev0, s, cudaEventRecordExternal));
-    BK(launch_sweep_tcs_batch(b->kind, b->d_params, b->d_items, b->n_items, b->d_head, b->off_misc, b->smem,
+    BK(launch_sweep_tcs_batch(b->kind, b->h, b->d_params, b->d_items, b->n_items, b->d_head, b->off_misc, b->smem,
                               b->grid, s));
     BK(cudaEventRecordWithFlags(b->ev1, s, cudaEventRecordExternal));
     for (int p = 0; p < b->P; ++p) {
@@ -1279,10 +1289,10 @@ oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
         const int64_t Nprobe = std::min<int64_t>(x->N, (int64_t)b->grid * 128);
         float best_ms = 0.0f;
         int best_S = 0;
-        const TcsPlan full = tcs_plan(x->dt.kind, x->dt.n, x->dt.d, 0, 0);
+        const TcsPlan full = tcs_plan(x->dt.kind, x->dt.n, x->dt.d, 0, 0, false, b->h, x->dt.tcs_dp);
         for (int S : {2, 3, 4, 6, 8}) {
             if (S > full.stages) break;
-            const TcsPlan L = tcs_plan(x->dt.kind, x->dt.n, x->dt.d, 0, S);
+            const TcsPlan L = tcs_plan(x->dt.kind, x->dt.n, x->dt.d, 0, S, false, b->h, x->dt.tcs_dp);
             SweepParams sp = make_params(x, T_probe, b->d_sched, b->d_sched + T_probe + 1, x->seed, 0xFFFFu, 0, Nprobe,
                                          x->d_logw, x->d_ell, x->d_x, x->d_parts, b->d_status);
             float ms = 0.0f;

@@ -24,6 +24,7 @@ struct DevTarget {
     void* tcs_img = nullptr;
     float* tcs_state = nullptr;
     bool tcs_q8 = false; // the streamed form's X is stored as FP8 e4m3 with per-row scales
+    int tcs_dp = 0;      // padded width of the streamed form's chunk images
 };
 
 // Streamed tensor-core sweep (sweep_tcs.cu): sizes of one configuration.  dp = d padded to
@@ -35,12 +36,14 @@ struct TcsPlan {
     int dp = 0, chunk = 0, nch = 0, stages = 0, tmem_cols = 0;
     uint32_t y_off = 0, stage_bytes = 0, off_x = 0, off_misc = 0, smem = 0;
     bool q8 = false;                     // FP8 e4m3 storage of X with per-row scales
+    int h = 2;                           // column groups per lane quarter (particle warps / 4)
     int stages8 = 0;
     uint32_t off_x8 = 0, stage8_bytes = 0;
     size_t img_bytes = 0;
     bool ok = false;
 };
-TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8 = false);
+// dp > 0 forces the padded width (a context keeps the width its chunk images were made for)
+TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8 = false, int h = 0, int dp = 0);
 void tcs_prepare(const TcsPlan& L, int kind, const float* X, const float* y, int n, int d,
                  std::vector<unsigned char>& img);
 void tcs_prepare_q8(const TcsPlan& L, const float* X, const float* y, int n, int d, std::vector<unsigned char>& img);
@@ -56,7 +59,7 @@ size_t tcs_params_bytes();
 uint32_t tcs_misc_bytes();
 void tcs_batch_params(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state, int move,
                       int leapfrog, double p0, int n, int d, uint32_t off_misc, void* out);
-cudaError_t launch_sweep_tcs_batch(int kind, const void* d_params, const void* d_items, uint32_t n_items,
+cudaError_t launch_sweep_tcs_batch(int kind, int h, const void* d_params, const void* d_items, uint32_t n_items,
                                    uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s);
 // one evaluation of log L and grad log L (grad may be null) at states x [d][N] with the
 // streamed tensor-core contraction

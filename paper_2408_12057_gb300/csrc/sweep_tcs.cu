@@ -28,927 +28,9 @@
 // Particle state between evaluations lives in global memory (L2): accepted position and
 // gradient, proposal position and momentum, [d_pad][N_pad] fp32 each, read and written only
 // by the thread that owns the (particle, coordinate) pair.
-#include <cuda_fp16.h>
-#include <cmath>
-#include <cstring>
-#include <vector>
-
-#include "internal.h"
-#include "tcgen05.cuh"
-#include "../../include/oais.h"
+#include "sweep_tcs.cuh"
 
 namespace oais {
-namespace tcs {
-using namespace oais::tc;
-
-constexpr int kTile = 128;
-constexpr int kEpiThreads = 256;
-constexpr int kThreads = kEpiThreads + 96;
-constexpr int kFwdWarp = 8, kLoadWarp = 9, kBwdWarp = 10;
-// FP8 storage of X (e4m3 values q with a per-row scale s, X~ = s q): two warps expand each
-// chunk from the FP8 ring into the f16 stage the MMAs read, one row per thread: the producer
-// warp (whose lane 0 also issues the copies) and one more warp (a 12-warp block keeps the
-// register budget of the other roles)
-constexpr int kCvtWarp0 = 11, kCvtThreads = 32, kCvtArrivals = 2;
-constexpr int kThreadsQ8 = kThreads + kCvtThreads;
-__host__ __device__ constexpr int threads_for(int q8) { return q8 ? kThreadsQ8 : kThreads; }
-constexpr int kSlice = 8;   // coordinates per state-update step (one 16-byte f16 chunk)
-// The tensor core rounds each accumulation toward zero, so a long running sum in one TMEM
-// accumulator drifts toward zero by about half an ulp per MMA (a relative shrink of ~1e-4
-// after the ~6000 backward MMAs of a 50 000-row evaluation).  The gradient sum is therefore
-// cut into segments of kSegMmas MMAs (relative drift ~1e-5): at the end of a segment the
-// particle threads add D2 into an fp32 sum in memory (round to nearest) and the next
-// segment restarts D2.
-constexpr int kSegMmas = 512;
-
-// ---------------------------------------------------------------------------------------
-// K-major operand layout in shared memory: rows of `kw` 16-bit elements (kw = 64 with the
-// 128-byte swizzle when the K extent is a multiple of 64, else 32 / 16 with the 64 / 32-byte
-// swizzle); K beyond 64 is split into slabs of `rows` lines each.  The swizzle permutes the
-// 16-byte chunks of a line by the line index (bits 4-6 of the address XOR bits 7-9 for
-// 128B, bits 4-5 XOR 7-8 for 64B, bit 4 XOR bit 7 for 32B).  The same bytes read as an
-// MN-major operand (N along the line) give the backward's B.
-// ---------------------------------------------------------------------------------------
-struct KLayout {
-    int kw;      // elements per line
-    int lb;      // bytes per line
-    int mode;    // 0: 128B, 1: 64B, 2: 32B swizzle
-};
-__host__ __device__ constexpr KLayout klayout(int k_extent)
-{
-    return KLayout{k_extent >= 64 ? 64 : k_extent, 2 * (k_extent >= 64 ? 64 : k_extent),
-                   k_extent >= 64 ? 0 : (k_extent == 32 ? 1 : 2)};
-}
-// rows per chunk: 64, or 32 when d_pad = 256 (shared memory)
-#ifndef OAIS_TCS_CHUNK256
-#define OAIS_TCS_CHUNK256 64
-#endif
-__host__ __device__ constexpr int chunk_rows(int dp) { return dp >= 256 ? OAIS_TCS_CHUNK256 : 64; }
-// TMEM columns: D1 (forward accumulator, one chunk), R (per-row factors of one chunk, hi |
-// lo, f16 pairs), A_lo (the lo term of the positions, f16 pairs: the forward's A operand for
-// that term), D2 (gradient accumulator, d_pad columns).  The hi term of the positions is the
-// shared-memory A operand.
-constexpr int kColD1 = 0, kColR = 64, kColAlo = 128, kColD2 = 256;
-// byte offset of the 16-byte chunk holding elements [k0, k0 + 8) of `row`
-__host__ __device__ inline uint32_t kmaj_off(int row, int k0, int rows, const KLayout& L)
-{
-    const int slab = k0 / L.kw;
-    const int line = slab * rows + row;
-    const int c = (k0 % L.kw) >> 3;
-    const int sw = L.mode == 0 ? (line & 7) : (L.mode == 1 ? ((line >> 1) & 3) : ((line >> 2) & 1));
-    return (uint32_t)line * (uint32_t)L.lb + (uint32_t)((c ^ sw) << 4);
-}
-__host__ __device__ constexpr uint64_t layout_code(const KLayout& L)
-{
-    return L.mode == 0 ? kSW128 : (L.mode == 1 ? kSW64 : kSW32);
-}
-
-struct Params {
-    SweepParams sp;
-    const unsigned char* img;   // [nch][stage_bytes] chunk images
-    float* xa;                  // accepted positions    [dp][Np]
-    float* ga;                  // grad log L at xa      [dp][Np]
-    float* xp;                  // proposal / trajectory [dp][Np]
-    float* mom;                 // HMC momentum; MALA: z + (eps/2) grad log pi(x)  [dp][Np]
-    float* gs;                  // drained part of the running gradient sum G      [dp][Np]
-    int64_t Np;
-    int seg;                    // chunks per gradient segment (see kSegMmas)
-    int n, d, dp, nch, stages;
-    uint32_t stage_bytes, y_off;   // f16 stage: lines, then y [64] and (FP8 storage) s [64]
-    uint32_t off_x8, stage8_bytes; // FP8 storage: ring of chunk images (q rows, y, s)
-    int stages8;
-    uint32_t off_x, off_misc;   // shared-memory regions (A starts at 0)
-    uint32_t tmem_cols;
-    int move, leapfrog;
-    // potential mode (one evaluation at given states, no sweep): x_in [d][N], outputs
-    // ell_pot [N] and grad_pot [d][N] (may be null)
-    const float* x_in;
-    double* ell_pot;
-    float* grad_pot;
-    int64_t pstride;            // row stride of x_in and grad_pot
-    double log_norm;            // linear regression: n (log sigma + log(2 pi) / 2)
-    float gscale;               // grad log L = gscale * G (1 / sigma^2 or 1)
-    float half_inv_var;         // linear regression: 1 / (2 sigma^2)
-};
-
-// misc region: barriers, TMEM address, abort flag, exchange buffers, moment scratch
-struct Misc {
-    uint64_t xfull[8], xempty[8];
-    uint64_t x8full[4], x8empty[4];
-    uint64_t d1full, d1empty, rfull, rempty;
-    uint64_t afull, d2full, done, d2seg, d2drained;
-    uint32_t tmem;
-    volatile int abort;
-    double xl[2][kTile];        // per coordinate half: partial log-likelihood
-    float4 xm[2][kTile];        // per coordinate half: partial sums of the MH ratio
-    double s_m[2][4][3];
-    float s_s[2][4][3];
-    unsigned s_acc[2][4];
-    Params prm;                 // batched launch: the current item's problem
-    uint32_t item;              // batched launch: the current item
-};
-
-// f16 two-term split of a pair: hi = f16(v), lo = f16(v - hi)
-__device__ __forceinline__ void split_pair_h(float a, float b, uint32_t& hi, uint32_t& lo)
-{
-    const __half2 h = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
-    hi = *reinterpret_cast<const uint32_t*>(&h);
-    lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
-__device__ __forceinline__ void normals8(const Rng& rng, uint32_t n, uint32_t t, uint32_t k, int d, int i0,
-                                         float (&z)[kSlice])
-{
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-        const int j = i0 / 4 + b;
-        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (4 * j < d) box_muller4(rng.block(n, t, k, (uint32_t)j), v);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) z[4 * b + q] = (4 * j + q < d) ? v[q] : 0.0f;
-    }
-}
-
-template <int DP>
-struct Thread {
-    static constexpr int CHUNK = chunk_rows(DP);
-    static constexpr int HC = CHUNK / 2;   // columns of a chunk per thread
-    static constexpr int DH = DP / 2;      // coordinates per thread
-    unsigned char* smem;
-    Misc* M;
-    const Params* P;
-    int p, h, q, lane;
-    uint32_t lane_off;
-    uint32_t tmem;  // TMEM base (lane 0, column 0)
-    uint32_t d2;
-    uint32_t g;     // chunks consumed
-    uint32_t e;     // evaluations done
-    int xs;         // stage of chunk g
-    uint32_t xph;   // phase of that stage
-    uint32_t sph;   // phase of the segment barrier
-    bool drained;   // the last evaluation drained D2 at least once
-    float* GS;      // this particle's drained gradient sum (stride Np)
-
-    __device__ bool wait(uint64_t* bar, uint32_t parity)
-    {
-        if (M->abort) return false;
-        if (mbar_wait(saddr(bar), parity, &M->abort)) return true;
-        M->abort = 1;
-        atomicOr(P->sp.status, 2u);
-        return false;
-    }
-
-    // one 8-coordinate slice of the tile's positions into the A operand (both terms)
-    __device__ void write_a(int i0, const float (&v)[kSlice])
-    {
-        constexpr KLayout L = klayout(DP);
-        const uint32_t off = kmaj_off(p, i0, kTile, L);
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) split_pair_h(v[2 * j], v[2 * j + 1], hi[j], lo[j]);
-        *reinterpret_cast<uint4*>(smem + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        tmem_st4(tmem + (uint32_t)(kColAlo + i0 / 2) + lane_off, lo);
-    }
-
-    __device__ void load_grad(int i0, float (&gv)[kSlice])
-    {
-        uint32_t v[8];
-        tmem_ld8(d2 + lane_off + (uint32_t)i0, v);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < kSlice; ++j) {
-            float gsum = __uint_as_float(v[j]);
-            if (drained) gsum += GS[(int64_t)(i0 + j) * P->Np];
-            gv[j] = P->gscale * gsum;
-        }
-    }
-
-    // end of a gradient segment: add D2 (this thread's lanes and coordinate half) into GS,
-    // W columns at a time with all W memory reads in flight together
-    __device__ void drain(bool first)
-    {
-        wait(&M->d2seg, sph);
-        sph ^= 1u;
-        __syncwarp();
-        tc_after_sync();
-        constexpr int W = DH < 32 ? DH : 32;
-        for (int i0 = h * DH; i0 < (h + 1) * DH; i0 += W) {
-            uint32_t v[W];
-            if constexpr (W == 32) tmem_ld32(d2 + lane_off + (uint32_t)i0, v);
-            else if constexpr (W == 16) tmem_ld16(d2 + lane_off + (uint32_t)i0, v);
-            else tmem_ld8(d2 + lane_off + (uint32_t)i0, v);
-            float old[W];
-#pragma unroll
-            for (int j = 0; j < W; ++j) old[j] = first ? 0.0f : GS[(int64_t)(i0 + j) * P->Np];
-            tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < W; ++j) GS[(int64_t)(i0 + j) * P->Np] = old[j] + __uint_as_float(v[j]);
-        }
-        tc_before_sync();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(saddr(&M->d2drained));
-    }
-
-    // log L at the positions just written to A (this thread's half of the rows' terms summed
-    // with the other half's), leaving grad log L / gscale in D2.
-    template <int FAM, int Q8>
-    __device__ double eval()
-    {
-        tmem_wait_st();   // A_lo in TMEM
-        fence_proxy_async();   // A_hi in shared memory, visible to the tensor core
-        tc_before_sync();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(saddr(&M->afull));
-        const int nch = P->nch;
-        double acc0 = 0.0, acc1 = 0.0;   // linear: sum r^2; logistic: sum (u - |u|), sum log2 q
-        float mid0 = 0.0f, mid1 = 0.0f;
-        const int seg = P->seg;
-        drained = false;
-        for (int c = 0; c < nch; ++c, ++g) {
-            const uint32_t ph = g & 1u;
-            wait(&M->d1full, ph);
-            __syncwarp();
-            tc_after_sync();
-            uint32_t v[HC];
-            const uint32_t src = tmem + (uint32_t)(kColD1 + h * HC) + lane_off;
-            if constexpr (HC == 16) tmem_ld16(src, v);
-            else tmem_ld32(src, v);
-            tmem_wait_ld();
-            tc_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(saddr(&M->d1empty));
-            uint32_t hi[HC / 2], lo[HC / 2];
-            float part0 = 0.0f, part1 = 0.0f;
-            if constexpr (FAM == kLinreg) {
-                wait(&M->xfull[xs], xph);   // y of this chunk is in the stage
-                const float* ys = reinterpret_cast<const float*>(smem + P->off_x + (uint32_t)xs * P->stage_bytes +
-                                                                 P->y_off) + h * HC;
-                if constexpr (Q8) {
-                    // X~_r = s_r q_r: z = s_r (q_r . x), and the backward's factor is r s_r
-                    const float* ss = ys + CHUNK;
-#pragma unroll
-                    for (int j = 0; j < HC; j += 2) {
-                        const float r0 = fmaf(-ss[j], __uint_as_float(v[j]), ys[j]);
-                        const float r1 = fmaf(-ss[j + 1], __uint_as_float(v[j + 1]), ys[j + 1]);
-                        part0 = fmaf(r0, r0, part0);
-                        part0 = fmaf(r1, r1, part0);
-                        split_pair_h(r0 * ss[j], r1 * ss[j + 1], hi[j / 2], lo[j / 2]);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < HC; j += 2) {
-                        const float r0 = ys[j] - __uint_as_float(v[j]);
-                        const float r1 = ys[j + 1] - __uint_as_float(v[j + 1]);
-                        part0 = fmaf(r0, r0, part0);
-                        part0 = fmaf(r1, r1, part0);
-                        split_pair_h(r0, r1, hi[j / 2], lo[j / 2]);
-                    }
-                }
-            } else {
-                // X'_r = s_r X~_r with s_r = 2 y_r - 1, so u = s z; log sigmoid(u) =
-                // min(u, 0) + log q with q = 1 / (1 + e^-|u|), d/dz = s sigmoid(-u)
-                float prod = 1.0f;
-#pragma unroll
-                for (int j = 0; j < HC; j += 2) {
-                    float r2[2];
-#pragma unroll
-                    for (int w = 0; w < 2; ++w) {
-                        const float u = __uint_as_float(v[j + w]);
-                        const float ee = ex2_approx(fabsf(u) * -1.4426950408889634f);
-                        const float qi = rcp_approx(1.0f + ee);
-                        r2[w] = u >= 0.0f ? ee * qi : qi;
-                        part0 += u - fabsf(u);
-                        prod *= qi;
-                    }
-                    if ((j & 15) == 14) { part1 += lg2_approx(prod); prod = 1.0f; }
-                    split_pair_h(r2[0], r2[1], hi[j / 2], lo[j / 2]);
-                }
-            }
-            if (++xs == P->stages) { xs = 0; xph ^= 1u; }
-            // R (two f16 terms) into TMEM, the A operand of the backward
-            wait(&M->rempty, ph ^ 1u);
-            __syncwarp();
-            tc_after_sync();
-            const uint32_t rcol = tmem + (uint32_t)(kColR + h * (HC / 2)) + lane_off;
-            if constexpr (HC == 32) {
-                tmem_st16(rcol, hi);
-                tmem_st16(rcol + CHUNK / 2, lo);
-            } else {
-                tmem_st8(rcol, hi);
-                tmem_st8(rcol + CHUNK / 2, lo);
-            }
-            tmem_wait_st();
-            tc_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(saddr(&M->rfull));
-            // chunk c - 1 closed a gradient segment: its backward is the last of the segment
-            if (c >= 1 && (c - 1) % seg == seg - 1) {
-                drain(!drained);
-                drained = true;
-            }
-            mid0 += part0;
-            mid1 += part1;
-            if ((c & 15) == 15) { acc0 += mid0; acc1 += mid1; mid0 = 0.0f; mid1 = 0.0f; }
-        }
-        acc0 += mid0;
-        acc1 += mid1;
-        wait(&M->d2full, e & 1u);
-        __syncwarp();
-        tc_after_sync();
-        ++e;
-        double part;
-        if constexpr (FAM == kLinreg) part = -P->half_inv_var * acc0;
-        else part = 0.5 * acc0 + 0.69314718055994531 * acc1;
-        M->xl[h][p] = part;
-        named_sync(1, kEpiThreads);
-        const double tot = M->xl[0][p] + M->xl[1][p];
-        named_sync(1, kEpiThreads);
-        if constexpr (FAM == kLinreg) return tot - P->log_norm;
-        else return tot + (double)(nch * CHUNK - P->n) * 0.69314718055994531;
-    }
-
-    // sum of this particle's four partial sums over the two coordinate halves
-    __device__ float4 combine(float4 mine)
-    {
-        M->xm[h][p] = mine;
-        named_sync(1, kEpiThreads);
-        const float4 a = M->xm[0][p], b = M->xm[1][p];
-        named_sync(1, kEpiThreads);
-        return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-    }
-};
-
-// the tile's four particle warps of half 0 merge their (m, s) moment pieces and acceptance
-// counts in a fixed order (one record per step and tile)
-__device__ __forceinline__ void tile_record(int lane, const double (*wm)[3], const float (*ws)[3],
-                                            const unsigned* wacc, StepPartial* out)
-{
-    StepPartial rec;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const double m = lane < 4 ? wm[lane][i] : -INFINITY;
-        double Mx = m;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) Mx = fmax(Mx, __shfl_xor_sync(0xFFFFFFFFu, Mx, o));
-        double v = (lane < 4 && m != -INFINITY) ? (double)ws[lane][i] * exp(m - Mx) : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        rec.m[i] = Mx;
-        rec.s[i] = v;
-    }
-    unsigned a = lane < 4 ? wacc[lane] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-    if (lane == 0) {
-        rec.accepted = a;
-        rec.pad = 0;
-        *out = rec;
-    }
-}
-
-__device__ __forceinline__ void mbar_inval(uint32_t bar)
-{
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-// (thread 0) fresh barriers for one tile; prev_stages > 0: the previous tile's barriers (with
-// that many stage pairs) are invalidated first
-__device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stages, int stages8 = 0)
-{
-    uint64_t* all[] = {&M->d1full, &M->d1empty, &M->rfull, &M->rempty, &M->afull, &M->d2full,
-                       &M->done, &M->d2seg, &M->d2drained};
-    if (prev_stages > 0) {
-        for (int s = 0; s < prev_stages; ++s) { mbar_inval(saddr(&M->xfull[s])); mbar_inval(saddr(&M->xempty[s])); }
-        for (uint64_t* b : all) mbar_inval(saddr(b));
-    }
-    // f16 stages are filled by the bulk copy (one arrival + bytes) or, with FP8 storage, by
-    // the two converter warps
-    for (int s = 0; s < stages; ++s) {
-        mbar_init(saddr(&M->xfull[s]), stages8 > 0 ? kCvtArrivals : 1);
-        mbar_init(saddr(&M->xempty[s]), 1);
-    }
-    for (int s = 0; s < stages8; ++s) {
-        mbar_init(saddr(&M->x8full[s]), 1);
-        mbar_init(saddr(&M->x8empty[s]), kCvtArrivals);
-    }
-    mbar_init(saddr(&M->d1full), 1);
-    mbar_init(saddr(&M->d1empty), kEpiThreads / 32);
-    mbar_init(saddr(&M->rfull), kEpiThreads / 32);
-    mbar_init(saddr(&M->rempty), 1);
-    mbar_init(saddr(&M->afull), kEpiThreads / 32);
-    mbar_init(saddr(&M->d2full), 1);
-    mbar_init(saddr(&M->done), 2);
-    mbar_init(saddr(&M->d2seg), 1);
-    mbar_init(saddr(&M->d2drained), kEpiThreads / 32);
-    M->abort = 0;
-    fence_mbar_init();
-}
-
-// One tile (128 particles) of one problem for a whole sweep, by all 352 threads of the CTA;
-// the barriers are fresh and TMEM (512 columns at `tmem`) is held by the caller.
-// FP8 -> f16 stage: row `row` of a chunk (q bytes to the swizzled f16 lines), its y and s
-template <int DP>
-__device__ __forceinline__ void convert_row(const unsigned char* src, unsigned char* dst, int row, uint32_t y_off)
-{
-    constexpr int CHUNK = chunk_rows(DP);
-    constexpr KLayout LA = klayout(DP);
-    const unsigned char* qrow = src + (uint32_t)row * DP;
-#pragma unroll 4
-    for (int k0 = 0; k0 < DP; k0 += 16) {
-        const uint4 raw = *reinterpret_cast<const uint4*>(qrow + k0);
-        const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
-        uint32_t hv[8];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            hv[2 * i] = cvt_f16x2_e4m3x2((uint16_t)(w[i] & 0xFFFFu));
-            hv[2 * i + 1] = cvt_f16x2_e4m3x2((uint16_t)(w[i] >> 16));
-        }
-        *reinterpret_cast<uint4*>(dst + kmaj_off(row, k0, CHUNK, LA)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<uint4*>(dst + kmaj_off(row, k0 + 8, CHUNK, LA)) = make_uint4(hv[4], hv[5], hv[6], hv[7]);
-    }
-    const float* yq = reinterpret_cast<const float*>(src + (uint32_t)CHUNK * DP);
-    float* yd = reinterpret_cast<float*>(dst + y_off);
-    yd[row] = yq[row];
-    yd[CHUNK + row] = yq[CHUNK + row];
-}
-
-template <int FAM, int DP, int Q8>
-__device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_t tiles, unsigned char* smem,
-                                         uint32_t tmem)
-{
-    constexpr int CHUNK = chunk_rows(DP);
-    const SweepParams& S = P.sp;
-    Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int Le = P.move == kHmc ? P.leapfrog : 1;
-    const uint32_t evals = P.x_in ? 1u : 1u + (uint32_t)S.T * (uint32_t)S.mv.K * (uint32_t)Le;
-    const uint32_t total = evals * (uint32_t)P.nch;
-    const uint32_t D2 = tmem + (uint32_t)kColD2;
-    constexpr KLayout LA = klayout(DP);
-
-    if (Q8 && warp == kLoadWarp) {
-        // ---------------- producer + converter (rows 0-31) ----------------
-        // lane 0 keeps the FP8 ring full: it issues every copy whose ring slot is free, from
-        // inside the warp's waits, so the warp never blocks on a copy nobody has issued
-        uint32_t issued = 0, c = 0, pph = 0;
-        int ps = 0;
-        const uint32_t bytes8 = P.stage8_bytes;
-        const uint32_t base8 = saddr(smem + P.off_x8);
-        auto try_issue = [&]() {
-            while (issued < total && mbar_try_wait(saddr(&M->x8empty[ps]), pph ^ 1u)) {
-                mbar_arrive_expect_tx(saddr(&M->x8full[ps]), bytes8);
-                bulk_g2s(base8 + (uint32_t)ps * bytes8, P.img + (size_t)c * bytes8, bytes8, saddr(&M->x8full[ps]));
-                ++issued;
-                if (++c == (uint32_t)P.nch) c = 0;
-                if (++ps == P.stages8) { ps = 0; pph ^= 1u; }
-            }
-        };
-        auto wait_issuing = [&](uint32_t bar, uint32_t parity) -> bool {
-            const uint64_t t0 = globaltimer();
-            for (;;) {
-                if (lane == 0) try_issue();
-                if (mbar_try_wait(bar, parity)) return true;
-                if (M->abort || globaltimer() - t0 > kWaitLimitNs) return false;
-            }
-        };
-        int s8 = 0, s = 0;
-        uint32_t ph8 = 0, ph = 0;
-        for (uint32_t g = 0; g < total; ++g) {
-            if (!wait_issuing(saddr(&M->x8full[s8]), ph8) || !wait_issuing(saddr(&M->xempty[s]), ph ^ 1u)) {
-                M->abort = 1;
-                atomicOr(S.status, 2u);
-                break;
-            }
-            convert_row<DP>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
-                            lane, P.y_off);
-            fence_proxy_async();   // the f16 stage, visible to the tensor core
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(saddr(&M->xfull[s]));
-                mbar_arrive(saddr(&M->x8empty[s8]));
-                try_issue();
-            }
-            if (++s8 == P.stages8) { s8 = 0; ph8 ^= 1u; }
-            if (++s == P.stages) { s = 0; ph ^= 1u; }
-        }
-        // copies still in flight land before the CTA ends (bounded)
-        if (lane == 0) {
-            const uint32_t first = issued > (uint32_t)P.stages8 ? issued - P.stages8 : 0u;
-            for (uint32_t g = first; g < issued; ++g)
-                mbar_wait(saddr(&M->x8full[g % P.stages8]), (g / P.stages8) & 1u);
-        }
-    } else if (warp == kLoadWarp) {
-        // ---------------- producer: chunk images into the stage ring ----------------
-        if (lane == 0) {
-            const int ring = P.stages;
-            const uint32_t bytes = P.stage_bytes;
-            uint64_t* full = M->xfull;
-            uint64_t* empty = M->xempty;
-            int s = 0;
-            uint32_t ph = 0, issued = 0;
-            const uint32_t sbase = saddr(smem + P.off_x);
-            for (uint32_t g = 0, c = 0; g < total; ++g) {
-                if (M->abort) break;
-                if (!mbar_wait(saddr(&empty[s]), ph ^ 1u, &M->abort)) {
-                    M->abort = 1;
-                    atomicOr(S.status, 2u);
-                    break;
-                }
-                mbar_arrive_expect_tx(saddr(&full[s]), bytes);
-                bulk_g2s(sbase + (uint32_t)s * bytes, P.img + (size_t)c * bytes, bytes, saddr(&full[s]));
-                ++issued;
-                if (++c == (uint32_t)P.nch) c = 0;
-                if (++s == ring) { s = 0; ph ^= 1u; }
-            }
-            // copies still in flight land before the CTA ends (bounded)
-            const uint32_t first = issued > (uint32_t)ring ? issued - ring : 0u;
-            for (uint32_t g = first; g < issued; ++g) mbar_wait(saddr(&full[g % ring]), (g / ring) & 1u);
-        }
-    } else if (Q8 && warp >= kCvtWarp0) {
-        // ---------------- converter: FP8 chunk -> f16 stage (rows 32-63) ----------------
-        int s8 = 0, s = 0;
-        uint32_t ph8 = 0, ph = 0;
-        for (uint32_t g = 0; g < total; ++g) {
-            if (!mbar_wait(saddr(&M->x8full[s8]), ph8, &M->abort) ||
-                !mbar_wait(saddr(&M->xempty[s]), ph ^ 1u, &M->abort)) {
-                M->abort = 1;
-                atomicOr(S.status, 2u);
-                break;
-            }
-            convert_row<DP>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
-                            32 + lane, P.y_off);
-            fence_proxy_async();   // the f16 stage, visible to the tensor core
-            __syncwarp();
-            if ((threadIdx.x & 31) == 0) {
-                mbar_arrive(saddr(&M->xfull[s]));
-                mbar_arrive(saddr(&M->x8empty[s8]));
-            }
-            if (++s8 == P.stages8) { s8 = 0; ph8 ^= 1u; }
-            if (++s == P.stages) { s = 0; ph ^= 1u; }
-        }
-    } else if (warp == kFwdWarp || warp == kBwdWarp) {
-        // ---------------- MMA issue: forwards and backwards from two threads ----------------
-        // Each stream is issued in chunk order as soon as its inputs are ready; a commit
-        // tracks only its own thread's MMAs, and every buffer the two streams share is
-        // ordered through the particle warps' barriers (a backward of chunk g follows the
-        // particle warps' read of that chunk's forward result).
-        if (lane == 0) {
-            constexpr uint32_t idf = idesc_kind_f16(kTile, CHUNK, false, false);
-            constexpr uint32_t idb = idesc_kind_f16(kTile, DP, false, true);
-            constexpr uint64_t ca = layout_code(LA);
-            const uint32_t xbase = saddr(smem + P.off_x);
-            const int nch = P.nch, seg = P.seg, S_ = P.stages;
-            bool ok = true;
-            int s = 0;
-            uint32_t ph = 0;
-            if (warp == kFwdWarp) {
-                // forward g: its X stage loaded, its D1 buffer read by the particle warps and,
-                // for the first chunk of an evaluation, the new positions in A.  The
-                // descriptors of the A bases take constant offsets (16-byte units) per K step.
-                const uint64_t adesc = sdesc(saddr(smem), 16, 8 * LA.lb, ca);
-                const uint32_t d1 = tmem + (uint32_t)kColD1, alo = tmem + (uint32_t)kColAlo;
-                for (uint32_t g = 0, c = 0, e = 0; g < total; ++g) {
-                    if ((c == 0 && !mbar_wait(saddr(&M->afull), e & 1u, &M->abort)) ||
-                        !mbar_wait(saddr(&M->xfull[s]), ph, &M->abort) ||
-                        !mbar_wait(saddr(&M->d1empty), (g & 1u) ^ 1u, &M->abort)) { ok = false; break; }
-                    tc_after_sync();
-                    const uint64_t xd = sdesc(xbase + (uint32_t)s * P.stage_bytes, 16, 8 * LA.lb, ca);
-                    // the small (lo) term first, from TMEM: the running sum is small while it
-                    // accumulates, so only the hi term's steps round a large sum toward zero
-#pragma unroll
-                    for (int kk = 0; kk < DP / 16; ++kk) {
-                        constexpr int kw = LA.kw;
-                        const int slab = 16 * kk / kw, within = (16 * kk % kw) * 2;
-                        mma_f16_ts(d1, alo + (uint32_t)(kk * 8), xd + (uint64_t)((slab * CHUNK * LA.lb + within) / 16),
-                                   idf, kk == 0 ? 0u : 1u);
-                    }
-#pragma unroll
-                    for (int kk = 0; kk < DP / 16; ++kk) {
-                        constexpr int kw = LA.kw;
-                        const int slab = 16 * kk / kw, within = (16 * kk % kw) * 2;
-                        mma_f16(d1, adesc + (uint64_t)((slab * kTile * LA.lb + within) / 16),
-                                xd + (uint64_t)((slab * CHUNK * LA.lb + within) / 16), idf, 1u);
-                    }
-                    mma_commit(saddr(&M->d1full));
-                    if (++s == S_) { s = 0; ph ^= 1u; }
-                    if (++c == (uint32_t)nch) { c = 0; ++e; }
-                }
-            } else {
-                // backward g: R of chunk g in TMEM and, for the first chunk of a gradient
-                // segment, the previous segment drained
-                uint32_t dph = 0;
-                for (uint32_t g = 0, c = 0; g < total; ++g) {
-                    const bool first = c % (uint32_t)seg == 0;
-                    if (!mbar_wait(saddr(&M->rfull), g & 1u, &M->abort) ||
-                        !mbar_wait(saddr(&M->xfull[s]), ph, &M->abort) ||
-                        (first && c != 0 && !mbar_wait(saddr(&M->d2drained), dph, &M->abort))) { ok = false; break; }
-                    if (first && c != 0) dph ^= 1u;
-                    tc_after_sync();
-                    const uint64_t xd = sdesc(xbase + (uint32_t)s * P.stage_bytes, CHUNK * LA.lb, 8 * LA.lb, ca);
-                    const uint32_t ra = tmem + (uint32_t)kColR;
-#pragma unroll
-                    for (int term = 0; term < 2; ++term) {
-#pragma unroll
-                        for (int kk = 0; kk < CHUNK / 16; ++kk)
-                            mma_f16_ts(D2, ra + (uint32_t)(term * (CHUNK / 2) + kk * 8),
-                                       xd + (uint64_t)(kk * 16 * LA.lb / 16), idb,
-                                       (first && term == 0 && kk == 0) ? 0u : 1u);
-                    }
-                    mma_commit(saddr(&M->rempty));
-                    mma_commit(saddr(&M->xempty[s]));
-                    if (c % (uint32_t)seg == (uint32_t)seg - 1 && c < (uint32_t)nch - 1) mma_commit(saddr(&M->d2seg));
-                    if (c == (uint32_t)nch - 1) mma_commit(saddr(&M->d2full));
-                    if (++s == S_) { s = 0; ph ^= 1u; }
-                    if (++c == (uint32_t)nch) c = 0;
-                }
-            }
-            if (!ok) { M->abort = 1; atomicOr(S.status, 2u); }
-            // every MMA issued by either thread has completed before TMEM is released (bounded)
-            mma_commit(saddr(&M->done));
-            mbar_wait(saddr(&M->done), 0u);
-        }
-    } else {
-        // ---------------- particle warps ----------------
-        Thread<DP> Th;
-        Th.smem = smem;
-        Th.M = M;
-        Th.P = &P;
-        Th.q = warp & 3;
-        Th.h = warp >> 2;
-        Th.lane = lane;
-        Th.p = 32 * Th.q + lane;
-        Th.lane_off = (uint32_t)(Th.q * 32) << 16;
-        Th.tmem = tmem;
-        Th.d2 = D2;
-        Th.g = 0;
-        Th.e = 0;
-        Th.xs = 0;
-        Th.xph = 0;
-        Th.sph = 0;
-        Th.drained = false;
-        const int p = Th.p, h = Th.h;
-        const int64_t n64 = (int64_t)tile * kTile + p;
-        const bool active = n64 < S.N;
-        Th.GS = P.gs + n64;
-        const uint32_t n = (uint32_t)(S.n_offset + (active ? n64 : S.N - 1));
-        constexpr int dh = DP / 2;
-        const int c0 = h * dh;
-        const int64_t Np = P.Np;
-        const float sref = (float)S.ref_scale;
-        const float inv_s2 = 1.0f / (sref * sref);
-        float* XA = P.xa + n64;
-        float* GA = P.ga + n64;
-        float* XP = P.xp + n64;
-        float* MO = P.mom + n64;
-
-        if (P.x_in) {
-            // potential mode: log L and grad log L at the given states
-            const int64_t src = active ? n64 : S.N - 1;
-            for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-                float xv[kSlice];
-#pragma unroll
-                for (int j = 0; j < kSlice; ++j)
-                    xv[j] = i0 + j < P.d ? P.x_in[(int64_t)(i0 + j) * P.pstride + src] : 0.0f;
-                Th.write_a(i0, xv);
-            }
-            const double ellv = Th.template eval<FAM, Q8>();
-            for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-                float gv[kSlice];
-                Th.load_grad(i0, gv);
-                if (active && P.grad_pot) {
-#pragma unroll
-                    for (int j = 0; j < kSlice; ++j)
-                        if (i0 + j < P.d) P.grad_pot[(int64_t)(i0 + j) * P.pstride + n64] = gv[j];
-                }
-            }
-            if (active && h == 0) P.ell_pot[n64] = ellv;
-        } else {
-        // x_0 ~ eta, its log L and gradient
-        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-            float z[kSlice];
-            normals8(S.mv.rng, n, 0u, 0u, P.d, i0, z);
-#pragma unroll
-            for (int j = 0; j < kSlice; ++j) {
-                z[j] *= sref;
-                XA[(int64_t)(i0 + j) * Np] = z[j];
-            }
-            Th.write_a(i0, z);
-        }
-        double ell = Th.template eval<FAM, Q8>();
-        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-            float gv[kSlice];
-            Th.load_grad(i0, gv);
-#pragma unroll
-            for (int j = 0; j < kSlice; ++j) GA[(int64_t)(i0 + j) * Np] = gv[j];
-        }
-
-        double logw = 0.0;
-        double beta_prev = S.beta[0];
-        for (int t = 1; t <= S.T; ++t) {
-            const double beta_t = __ldg(S.beta + t);
-            const double eps_t = __ldg(S.eps + t - 1);
-            const double lg = (beta_t - beta_prev) * ell;
-            beta_prev = beta_t;
-            const int slot = t & 1;
-            if (h == 0) warp_moment_partial(logw, lg, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
-            logw += lg;
-            unsigned acc = 0;
-            const float beta = (float)beta_t, eps = (float)eps_t, he = 0.5f * eps;
-            for (int k = 0; k < S.mv.K; ++k) {
-                // proposal start: MALA x' = x + eps (z + (eps/2) grad log pi(x));
-                // HMC m = z + (eps/2) grad log pi(x), x' = x + eps m
-                float zz = 0.0f, dxx = 0.0f;
-                for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-                    float z[kSlice], xpv[kSlice];
-                    normals8(S.mv.rng, n, (uint32_t)t, (uint32_t)k, P.d, i0, z);
-#pragma unroll
-                    for (int j = 0; j < kSlice; ++j) {
-                        const int64_t o = (int64_t)(i0 + j) * Np;
-                        const float xv = XA[o], gv = GA[o];
-                        const float gpi = -xv * inv_s2 + beta * gv;
-                        const float m = z[j] + he * gpi;
-                        xpv[j] = xv + eps * m;
-                        zz += z[j] * z[j];
-                        dxx += (xpv[j] - xv) * (xpv[j] + xv);
-                        XP[o] = xpv[j];
-                        MO[o] = m;
-                    }
-                    Th.write_a(i0, xpv);
-                }
-                double ellp = 0.0;
-                float tail = 0.0f;   // MALA: |reverse noise|^2; HMC: |final momentum|^2
-                for (int l = 0; l < Le; ++l) {
-                    ellp = Th.template eval<FAM, Q8>();
-                    const bool last = l + 1 == Le;
-                    if (P.move == kHmc) {
-                        const float f = last ? he : eps;
-                        dxx = last ? 0.0f : dxx;
-                        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-                            float gv[kSlice], xpv[kSlice];
-                            Th.load_grad(i0, gv);
-#pragma unroll
-                            for (int j = 0; j < kSlice; ++j) {
-                                const int64_t o = (int64_t)(i0 + j) * Np;
-                                const float xq = XP[o];
-                                float m = MO[o] + f * (-xq * inv_s2 + beta * gv[j]);
-                                if (!last) {
-                                    xpv[j] = xq + eps * m;
-                                    XP[o] = xpv[j];
-                                    MO[o] = m;
-                                } else {
-                                    const float xv = XA[o];
-                                    tail += m * m;
-                                    dxx += (xq - xv) * (xq + xv);
-                                    xpv[j] = xq;
-                                }
-                            }
-                            if (!last) Th.write_a(i0, xpv);
-                        }
-                    } else {
-                        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-                            float gv[kSlice];
-                            Th.load_grad(i0, gv);
-#pragma unroll
-                            for (int j = 0; j < kSlice; ++j) {
-                                const int64_t o = (int64_t)(i0 + j) * Np;
-                                const float qv = MO[o] + he * (-XP[o] * inv_s2 + beta * gv[j]);
-                                tail += qv * qv;
-                            }
-                        }
-                    }
-                }
-                const float4 tot = Th.combine(make_float4(zz, dxx, tail, 0.0f));
-                // HMC: log alpha = [log pi(x') - |m'|^2/2] - [log pi(x) - |z|^2/2];
-                // MALA: log alpha = log pi(x') - log pi(x) - (|q|^2 - |z|^2) / 2
-                const float log_alpha =
-                    -0.5f * tot.y * inv_s2 + beta * (float)(ellp - ell) - 0.5f * (tot.z - tot.x);
-                const float logu = mh_log_uniform(S.mv.rng, n, (uint32_t)t, (uint32_t)k, 0.0f);
-                const bool accept = logu < log_alpha;
-                for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-                    float gv[kSlice];
-                    Th.load_grad(i0, gv);   // warp-collective: outside the branch
-                    if (accept) {
-#pragma unroll
-                        for (int j = 0; j < kSlice; ++j) {
-                            const int64_t o = (int64_t)(i0 + j) * Np;
-                            XA[o] = XP[o];
-                            GA[o] = gv[j];
-                        }
-                    }
-                }
-                if (accept) { ell = ellp; ++acc; }
-            }
-            if (h == 0) {
-                acc = active ? acc : 0u;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-                if (lane == 0) M->s_acc[slot][Th.q] = acc;
-                named_sync(2, 128);
-                if (warp == 0)
-                    tile_record(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot],
-                                S.partials + (size_t)(t - 1) * tiles + tile);
-            }
-        }
-        if (active) {
-            float* xo = reinterpret_cast<float*>(S.x_out);
-            for (int i = c0; i < c0 + dh && i < P.d; ++i) xo[(size_t)i * S.N + n64] = XA[(int64_t)i * Np];
-            if (h == 0) {
-                S.logw[n64] = logw;
-                S.ell_out[n64] = ell;
-                if (!isfinite(logw) || !isfinite(ell)) atomicOr(S.status, 1u);
-            }
-        }
-        }   // sweep
-    }
-}
-
-template <int FAM, int DP, int Q8>
-__global__ void __launch_bounds__(threads_for(Q8), 1)
-oais_sweep_tcs_kernel(const Params P)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    if (saddr(smem) & 1023u) {
-        if (threadIdx.x == 0) atomicOr(P.sp.status, 4u);
-        return;
-    }
-    Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
-    const int warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) init_barriers(M, P.stages, 0, Q8 ? P.stages8 : 0);
-    if (warp == 0) {
-        tmem_alloc(saddr(&M->tmem), P.tmem_cols);
-        tmem_relinquish();
-    }
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&M->tmem);
-    run_tile<FAM, DP, Q8>(P, blockIdx.x, gridDim.x, smem, tmem);
-    tc_before_sync();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, P.tmem_cols);
-}
-
-// Many independent problems in one persistent launch: each CTA takes (problem, tile) items
-// from a queue ordered by decreasing cost (longest first) until it is empty.  All problems
-// share the family; their widths may differ (the item picks the instantiation).  Every
-// problem's Misc region sits at the same offset (the launch's largest).
-template <int FAM>
-__global__ void __launch_bounds__(kThreads, 1)
-oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __restrict__ items, uint32_t n_items,
-                            uint32_t* head, uint32_t off_misc)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    if (saddr(smem) & 1023u) {
-        if (threadIdx.x == 0) atomicOr(probs[0].sp.status, 4u);
-        return;
-    }
-    Misc* M = reinterpret_cast<Misc*>(smem + off_misc);
-    Params& sP = M->prm;
-    const int warp = threadIdx.x >> 5;
-    if (warp == 0) {
-        tmem_alloc(saddr(&M->tmem), 512);
-        tmem_relinquish();
-    }
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&M->tmem);
-    int prev_stages = 0;   // thread 0 only
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const uint32_t it = atomicAdd(head, 1u);
-            M->item = it;
-            if (it < n_items) {
-                sP = probs[items[it].x];
-                init_barriers(M, sP.stages, prev_stages);
-                prev_stages = sP.stages;
-            }
-        }
-        __syncthreads();
-        const uint32_t it = M->item;
-        if (it >= n_items) break;
-        const uint32_t tile = items[it].y;
-        const uint32_t tiles = (uint32_t)((sP.sp.N + kTile - 1) / kTile);
-        switch (sP.dp) {
-        case 16: run_tile<FAM, 16, 0>(sP, tile, tiles, smem, tmem); break;
-        case 32: run_tile<FAM, 32, 0>(sP, tile, tiles, smem, tmem); break;
-        case 64: run_tile<FAM, 64, 0>(sP, tile, tiles, smem, tmem); break;
-        case 128: run_tile<FAM, 128, 0>(sP, tile, tiles, smem, tmem); break;
-        default: if (threadIdx.x == 0) atomicOr(sP.sp.status, 8u);
-        }
-        // every role has finished the tile (its copies and MMAs complete) before the barriers
-        // and the item slot are reused
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
-    }
-    tc_before_sync();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 512);
-}
-
-} // namespace tcs
 
 // ---------------------------------------------------------------------------------------
 // host side
@@ -963,11 +45,16 @@ int padded_dim(int d)
 uint32_t align1024(uint32_t v) { return (v + 1023u) & ~1023u; }
 } // namespace
 
-TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8)
+TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8, int h, int dp)
 {
     TcsPlan L{};
     L.q8 = q8;
-    L.dp = padded_dim(d);
+    L.dp = dp > 0 ? dp : padded_dim(d);
+    // column split: two column groups per lane quarter (8 particle warps).  Four groups (16
+    // warps, a quarter of each chunk's columns per thread) were measured slower on the logistic
+    // workload: the per-chunk synchronisation is paid for half the work and the register cap
+    // drops to 96; the split stays a template parameter of the kernel.
+    L.h = h > 0 ? h : 2;
     L.chunk = chunk > 0 ? chunk : tcs::chunk_rows(L.dp);
     L.nch = (n + L.chunk - 1) / L.chunk;
     L.y_off = (uint32_t)L.chunk * L.dp * 2;
@@ -995,7 +82,7 @@ TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8)
     if (L.tmem_cols == 512 && L.smem < 120u * 1024u) L.smem = 120u * 1024u;
     L.img_bytes = (size_t)L.nch * (q8 ? L.stage8_bytes : L.stage_bytes);
     L.ok = L.dp <= 256 && L.chunk == tcs::chunk_rows(L.dp) && L.smem <= limit && L.stages >= 2 && L.stages <= 8 &&
-           (!q8 || kind == kLinreg);
+           L.h == 2;
     return L;
 }
 
@@ -1120,22 +207,23 @@ static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp,
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
         if (e != cudaSuccess) return e;
-        kern<<<tiles, tcs::threads_for(L.q8 ? 1 : 0), L.smem, s>>>(P);
+        kern<<<tiles, tcs::Roles<2>::threads(L.q8 ? 1 : 0), L.smem, s>>>(P);
         return cudaGetLastError();
     };
     if (L.chunk != tcs::chunk_rows(L.dp)) return cudaErrorInvalidValue;
     if (L.q8) {
-        if (kind != kLinreg) return cudaErrorInvalidValue;
+        if (kind != kLinreg || L.h != 2) return cudaErrorInvalidValue;
         switch (L.dp) {
-        case 16: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 16, 1>);
-        case 32: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 32, 1>);
-        case 64: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 64, 1>);
-        case 128: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 128, 1>);
-        case 256: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 256, 1>);
+        case 16: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 16, 1, 2>);
+        case 32: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 32, 1, 2>);
+        case 64: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 64, 1, 2>);
+        case 128: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 128, 1, 2>);
+        case 256: return go(tcs::oais_sweep_tcs_kernel<kLinreg, 256, 1, 2>);
         }
         return cudaErrorInvalidValue;
     }
-#define OAIS_TCS_DP(FAMK, DPV) case DPV: return go(tcs::oais_sweep_tcs_kernel<FAMK, DPV, 0>);
+    if (L.h != 2) return cudaErrorInvalidValue;
+#define OAIS_TCS_DP(FAMK, DPV) case DPV: return go(tcs::oais_sweep_tcs_kernel<FAMK, DPV, 0, 2>);
     if (kind == kLinreg) {
         switch (L.dp) {
         OAIS_TCS_DP(kLinreg, 16) OAIS_TCS_DP(kLinreg, 32) OAIS_TCS_DP(kLinreg, 64)
@@ -1188,20 +276,6 @@ void tcs_batch_params(const TcsPlan& L, int kind, const SweepParams& sp, const v
     fill_params(P, L, kind, sp, img, state, move, leapfrog, p0, n, d, nullptr, nullptr, nullptr, 0, 0);
     P.off_misc = off_misc;
     std::memcpy(out, &P, sizeof(P));
-}
-
-cudaError_t launch_sweep_tcs_batch(int kind, const void* d_params, const void* d_items, uint32_t n_items,
-                                   uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s)
-{
-    auto go = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, tcs::kThreads, smem, s>>>(static_cast<const tcs::Params*>(d_params),
-                                                 static_cast<const uint2*>(d_items), n_items, d_head, off_misc);
-        return cudaGetLastError();
-    };
-    if (kind == kLinreg) return go(tcs::oais_sweep_tcs_batch_kernel<kLinreg>);
-    return go(tcs::oais_sweep_tcs_batch_kernel<kLogreg>);
 }
 
 } // namespace oais
