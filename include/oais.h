@@ -86,10 +86,11 @@ typedef struct {
                              expanded to f16 on chip (exact), so the contraction keeps the
                              accuracy of the f16 form; LINREG only.
                            The tensor-core forms run the OAIS sweep (oais_round and the shard
-                           calls) and, for the streamed form, oais_potential; resampling
-                           rounds (oasmc_round) and oais_ctx_sweep use the CUDA-core form,
-                           which exists for d <= 32 (they return OAIS_EUNSUPPORTED above
-                           that).  Other combinations
+                           calls); the streamed form also runs resampling rounds (oasmc_round:
+                           one launch per step over its stored particle state) and
+                           oais_potential.  For the resident form those two, and
+                           oais_ctx_sweep for every form, use the CUDA-core form, which exists
+                           for d <= 32 (they return OAIS_EUNSUPPORTED above that).  Other combinations
                            return OAIS_EUNSUPPORTED at init. */
 } oais_target;
 

@@ -674,21 +674,41 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         se = std::sqrt(std::max(0.0, 1.0 / ess - 1.0 / (double)ctx->N));
     } else {
         if (ctx->N_total != ctx->N) return fail(ctx, OAIS_EUNSUPPORTED, "ASMC resamples globally: no shards");
-        if (ctx->dt.D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "resampling rounds need the CUDA-core form (d <= 32)");
+        if (ctx->dt.D == 0 && !ctx->dt.tcs)
+            return fail(ctx, OAIS_EUNSUPPORTED, "resampling rounds need the CUDA-core or the streamed form");
         CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(AsmcState), s));
         StepParams P = make_step_params(ctx, T, tag);
         const bool grad = ctx->mv.kind != OAIS_RWMH;
+        int records = grid;
         CK(cudaEventRecord(ctx->ev0, s));
-        CK(launch_asmc(ctx->dt, ctx->mv.kind, true, P, s));
-        for (int t = 1; t <= T; ++t) {
-            P.t = t;
-            CK(launch_asmc(ctx->dt, ctx->mv.kind, false, P, s));
-            CK(launch_asmc_resample(ctx->d_st, P, grid, ess_frac, ctx->dt.d, grad, ctx->dt.kind == kGauss,
-                                    ctx->d_bsum, ctx->d_boff, ctx->d_cdf, ctx->d_ess_trace, ctx->d_resampled,
-                                    ctx->d_anc, s));
+        if (ctx->dt.tcs) {
+            // the streamed tensor-core form: one launch per step over the stored particle state
+            const TcsPlan tp = tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0, ctx->dt.tcs_q8);
+            SweepParams S = make_params(ctx, T, ctx->d_beta, ctx->d_eps, ctx->seed, tag, 0, ctx->N, ctx->d_logw,
+                                        ctx->d_ell, ctx->d_x, ctx->d_parts, ctx->d_status);
+            records = tcs_tiles(ctx->N);
+            for (int t = 0; t <= T; ++t) {
+                CK(launch_step_tcs(tp, ctx->dt.kind, S, ctx->dt.tcs_img, ctx->dt.tcs_state, ctx->mv.kind,
+                                   ctx->mv.leapfrog, ctx->dt.p0, ctx->dt.n, ctx->dt.d, t, ctx->d_ess_parts, s));
+                if (t == 0) continue;
+                P.t = t;
+                CK(launch_asmc_decide_scan(ctx->d_st, P, records, ess_frac, ctx->d_bsum, ctx->d_boff, ctx->d_cdf,
+                                           ctx->d_ess_trace, ctx->d_resampled, s));
+                CK(launch_gather_tcs(tp, ctx->d_st, ctx->d_cdf, ctx->N, ctx->dt.tcs_state, ctx->d_ell, ctx->d_ell1,
+                                     ctx->d_logw, ctx->d_anc, s));
+            }
+        } else {
+            CK(launch_asmc(ctx->dt, ctx->mv.kind, true, P, s));
+            for (int t = 1; t <= T; ++t) {
+                P.t = t;
+                CK(launch_asmc(ctx->dt, ctx->mv.kind, false, P, s));
+                CK(launch_asmc_resample(ctx->d_st, P, grid, ess_frac, ctx->dt.d, grad, ctx->dt.kind == kGauss,
+                                        ctx->d_bsum, ctx->d_boff, ctx->d_cdf, ctx->d_ess_trace, ctx->d_resampled,
+                                        ctx->d_anc, s));
+            }
         }
         CK(cudaEventRecord(ctx->ev1, s));
-        CK(launch_merge_stats(ctx->d_parts, grid, T, 1.0 / ((double)ctx->N * ctx->mv.moves),
+        CK(launch_merge_stats(ctx->d_parts, records, T, 1.0 / ((double)ctx->N * ctx->mv.moves),
                               ctx->d_log_ghat, ctx->d_accept, s));
         AsmcState st;
         ess_tr.resize(T);
@@ -701,7 +721,7 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         // the particles of the last step live in buffer cur (no resampling is pending at t = T)
-        if ((st.cur ^ st.pend) == 1) {
+        if (!ctx->dt.tcs && (st.cur ^ st.pend) == 1) {
             const size_t xb = elt_bytes(ctx->dt.kind) * (size_t)ctx->dt.d * ctx->N;
             CK(cudaMemcpyAsync(ctx->d_x, ctx->d_x1, xb, cudaMemcpyDeviceToDevice, s));
             CK(cudaMemcpyAsync(ctx->d_ell, ctx->d_ell1, sizeof(double) * ctx->N, cudaMemcpyDeviceToDevice, s));

@@ -174,6 +174,18 @@ asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const dou
     if (ancestors) ancestors[n] = a;
 }
 
+cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int nparts, double ess_frac, double* bsum,
+                                    double* boff, double* cdf, double* ess_trace, int* resampled, cudaStream_t s)
+{
+    asmc_decide_kernel<<<1, 256, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, ess_frac, P.N, P.mv.rng,
+                                         ess_trace, resampled);
+    const int nb = scan_blocks(P.N);
+    asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
+    asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);
+    asmc_cdf_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, boff, cdf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts, double ess_frac, int d,
                                  bool grad, bool fp64, double* bsum, double* boff, double* cdf,
                                  double* ess_trace, int* resampled, int64_t* ancestors, cudaStream_t s)

@@ -61,6 +61,16 @@ void tcs_batch_params(const TcsPlan& L, int kind, const SweepParams& sp, const v
                       int leapfrog, double p0, int n, int d, uint32_t off_misc, void* out);
 cudaError_t launch_sweep_tcs_batch(int kind, int h, const void* d_params, const void* d_items, uint32_t n_items,
                                    uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s);
+// ASMC on the streamed form: step t (t = 0: the draw from eta) of the whole population, with
+// the tiles' (log w, 2 log w) records in ess_parts; then the resampling test, scan and CDF of
+// asmc.cu (decide/scan/cdf, no gather) and launch_gather_tcs for the particle state
+cudaError_t launch_step_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
+                            int move, int leapfrog, double p0, int n, int d, int t, StepPartial* ess_parts,
+                            cudaStream_t s);
+cudaError_t launch_gather_tcs(const TcsPlan& L, const AsmcState* st, const double* cdf, int64_t N, float* state,
+                              double* ell, double* ell_scratch, double* logw, int64_t* ancestors, cudaStream_t s);
+cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int nparts, double ess_frac, double* bsum,
+                                    double* boff, double* cdf, double* ess_trace, int* resampled, cudaStream_t s);
 // one evaluation of log L and grad log L (grad may be null) at states x [d][N] with the
 // streamed tensor-core contraction
 cudaError_t launch_potential_tcs(const TcsPlan& L, int kind, const void* img, const float* x, int64_t N,

@@ -162,6 +162,10 @@ static void fill_params(tcs::Params& P, const TcsPlan& L, int kind, const SweepP
                         double* ell_pot, float* grad_pot, int64_t pstride, int64_t state_particles)
 {
     P.sp = sp;
+    P.t_begin = 1;          // the OAIS sweep: x_0 ~ eta, then steps 1..T
+    P.t_end = sp.T;
+    P.resume = 0;
+    P.ess_parts = nullptr;
     P.x_in = x_in;
     P.ell_pot = ell_pot;
     P.grad_pot = grad_pot;
@@ -198,11 +202,18 @@ static void fill_params(tcs::Params& P, const TcsPlan& L, int kind, const SweepP
 
 static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
                               int move, int leapfrog, double p0, int n, int d, const float* x_in, double* ell_pot,
-                              float* grad_pot, int64_t pstride, cudaStream_t s, int64_t state_particles = 0)
+                              float* grad_pot, int64_t pstride, cudaStream_t s, int64_t state_particles = 0,
+                              int t_begin = 1, int t_end = -1, int resume = 0, StepPartial* ess_parts = nullptr)
 {
     tcs::Params P;
     fill_params(P, L, kind, sp, img, state, move, leapfrog, p0, n, d, x_in, ell_pot, grad_pot, pstride,
                 state_particles);
+    if (t_end >= 0) {
+        P.t_begin = t_begin;
+        P.t_end = t_end;
+        P.resume = resume;
+        P.ess_parts = ess_parts;
+    }
     const int tiles = tcs_tiles(sp.N);
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
@@ -243,6 +254,69 @@ cudaError_t launch_sweep_tcs(const TcsPlan& L, int kind, const SweepParams& sp, 
                              int move, int leapfrog, double p0, int n, int d, cudaStream_t s)
 {
     return launch_tcs(L, kind, sp, img, state, move, leapfrog, p0, n, d, nullptr, nullptr, nullptr, 0, s);
+}
+
+cudaError_t launch_step_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
+                            int move, int leapfrog, double p0, int n, int d, int t, StepPartial* ess_parts,
+                            cudaStream_t s)
+{
+    // t = 0: x_0 ~ eta and its evaluation; t >= 1: step t from the stored state
+    return launch_tcs(L, kind, sp, img, state, move, leapfrog, p0, n, d, nullptr, nullptr, nullptr, 0, s, 0,
+                      t == 0 ? 1 : t, t == 0 ? 0 : t, t == 0 ? 0 : 1, t == 0 ? nullptr : ess_parts);
+}
+
+// systematic resampling of the streamed form's particles (after asmc_decide / scan / cdf):
+// the ancestor rows of position and gradient go to the scratch arrays, then back
+__global__ void __launch_bounds__(256)
+tcs_gather_kernel(const AsmcState* st, const double* __restrict__ cdf, int64_t N, int64_t Np, int dp,
+                  const float* __restrict__ xa, const float* __restrict__ ga, float* xs, float* gs,
+                  const double* __restrict__ ell, double* ell_s, double* logw, int64_t* ancestors)
+{
+    if (!st->pend) return;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double thr = ((double)n + st->U) / (double)N;
+    int64_t lo = 0, hi = N - 1;   // a = min{m : C_m > thr}, clamped to N - 1
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cdf[mid] > thr) hi = mid; else lo = mid + 1;
+    }
+    for (int i = 0; i < dp; ++i) {
+        xs[(int64_t)i * Np + n] = xa[(int64_t)i * Np + lo];
+        gs[(int64_t)i * Np + n] = ga[(int64_t)i * Np + lo];
+    }
+    ell_s[n] = ell[lo];
+    logw[n] = 0.0;
+    if (ancestors) ancestors[n] = lo;
+}
+
+__global__ void __launch_bounds__(256)
+tcs_copyback_kernel(const AsmcState* st, int64_t N, int64_t Np, int dp, float* xa, float* ga,
+                    const float* __restrict__ xs, const float* __restrict__ gs, double* ell,
+                    const double* __restrict__ ell_s)
+{
+    if (!st->pend) return;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    for (int i = 0; i < dp; ++i) {
+        xa[(int64_t)i * Np + n] = xs[(int64_t)i * Np + n];
+        ga[(int64_t)i * Np + n] = gs[(int64_t)i * Np + n];
+    }
+    ell[n] = ell_s[n];
+}
+
+cudaError_t launch_gather_tcs(const TcsPlan& L, const AsmcState* st, const double* cdf, int64_t N, float* state,
+                              double* ell, double* ell_scratch, double* logw, int64_t* ancestors, cudaStream_t s)
+{
+    const int64_t Np = (int64_t)tcs_tiles(N) * tcs::kTile;
+    float* xa = state;
+    float* ga = state + (size_t)L.dp * Np;
+    float* xs = state + (size_t)2 * L.dp * Np;
+    float* gs = state + (size_t)3 * L.dp * Np;
+    const int gb = (int)((N + 255) / 256);
+    tcs_gather_kernel<<<gb, 256, 0, s>>>(st, cdf, N, Np, L.dp, xa, ga, xs, gs, ell, ell_scratch, logw, ancestors);
+    tcs_copyback_kernel<<<gb, 256, 0, s>>>(st, N, Np, L.dp, xa, ga, xs, gs, ell, ell_scratch);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_potential_tcs(const TcsPlan& L, int kind, const void* img, const float* x, int64_t N,

@@ -115,6 +115,11 @@ struct Params {
     double* ell_pot;
     float* grad_pot;
     int64_t pstride;            // row stride of x_in and grad_pot
+    // step range: steps t_begin..t_end of the schedule; resume = 0 starts from x_0 ~ eta (the
+    // OAIS sweep: 1..T), resume = 1 continues from the stored state, log w and log L (one ASMC
+    // step) and writes each tile's (log w, 2 log w) moment record to ess_parts
+    int t_begin, t_end, resume;
+    StepPartial* ess_parts;
     double log_norm;            // linear regression: n (log sigma + log(2 pi) / 2)
     float gscale;               // grad log L = gscale * G (1 / sigma^2 or 1)
     float half_inv_var;         // linear regression: 1 / (2 sigma^2)
@@ -484,7 +489,8 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
     Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Le = P.move == kHmc ? P.leapfrog : 1;
-    const uint32_t evals = P.x_in ? 1u : 1u + (uint32_t)S.T * (uint32_t)S.mv.K * (uint32_t)Le;
+    const uint32_t nsteps = P.t_end >= P.t_begin ? (uint32_t)(P.t_end - P.t_begin + 1) : 0u;
+    const uint32_t evals = P.x_in ? 1u : (P.resume ? 0u : 1u) + nsteps * (uint32_t)S.mv.K * (uint32_t)Le;
     const uint32_t total = evals * (uint32_t)P.nch;
     const uint32_t D2 = tmem + (uint32_t)Cols<DP>::D2;
     constexpr int NB = Cols<DP>::NB;
@@ -733,28 +739,35 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
             }
             if (active && h == 0) P.ell_pot[n64] = ellv;
         } else {
-        // x_0 ~ eta, its log L and gradient
-        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-            float z[kSlice];
-            normals8(S.mv.rng, n, 0u, 0u, P.d, i0, z);
+        double ell, logw;
+        if (!P.resume) {
+            // x_0 ~ eta, its log L and gradient
+            for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+                float z[kSlice];
+                normals8(S.mv.rng, n, 0u, 0u, P.d, i0, z);
 #pragma unroll
-            for (int j = 0; j < kSlice; ++j) {
-                z[j] *= sref;
-                XA[(int64_t)(i0 + j) * Np] = z[j];
+                for (int j = 0; j < kSlice; ++j) {
+                    z[j] *= sref;
+                    XA[(int64_t)(i0 + j) * Np] = z[j];
+                }
+                Th.write_a(i0, z);
             }
-            Th.write_a(i0, z);
-        }
-        double ell = Th.template eval<FAM, Q8>();
-        for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
-            float gv[kSlice];
-            Th.load_grad(i0, gv);
+            ell = Th.template eval<FAM, Q8>();
+            for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
+                float gv[kSlice];
+                Th.load_grad(i0, gv);
 #pragma unroll
-            for (int j = 0; j < kSlice; ++j) GA[(int64_t)(i0 + j) * Np] = gv[j];
+                for (int j = 0; j < kSlice; ++j) GA[(int64_t)(i0 + j) * Np] = gv[j];
+            }
+            logw = 0.0;
+        } else {
+            // an ASMC step continues from the stored state (gathered after a resampling)
+            const int64_t src = active ? n64 : S.N - 1;
+            ell = S.ell_out[src];
+            logw = S.logw[src];
         }
-
-        double logw = 0.0;
-        double beta_prev = S.beta[0];
-        for (int t = 1; t <= S.T; ++t) {
+        double beta_prev = S.beta[P.t_begin - 1];
+        for (int t = P.t_begin; t <= P.t_end; ++t) {
             const double beta_t = __ldg(S.beta + t);
             const double eps_t = __ldg(S.eps + t - 1);
             const double lg = (beta_t - beta_prev) * ell;
@@ -859,9 +872,19 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                                 S.partials + (size_t)(t - 1) * tiles + tile);
             }
         }
+        if (P.ess_parts && h == 0) {
+            // (log w, 2 log w) moments of the tile for the ESS of the resampling test
+            const int slot = (P.t_end + 1) & 1;
+            warp_moment_partial(logw, logw, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
+            if (lane == 0) M->s_acc[slot][Th.q] = 0u;
+            named_sync(2, 128);
+            if (warp == 0) tile_record(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot], P.ess_parts + tile);
+        }
         if (active) {
-            float* xo = reinterpret_cast<float*>(S.x_out);
-            for (int i = c0; i < c0 + dh && i < P.d; ++i) xo[(size_t)i * S.N + n64] = XA[(int64_t)i * Np];
+            if (P.t_end == S.T) {
+                float* xo = reinterpret_cast<float*>(S.x_out);
+                for (int i = c0; i < c0 + dh && i < P.d; ++i) xo[(size_t)i * S.N + n64] = XA[(int64_t)i * Np];
+            }
             if (h == 0) {
                 S.logw[n64] = logw;
                 S.ell_out[n64] = ell;

@@ -247,3 +247,66 @@ def test_stream_linreg_logZ_and_gradient_closed_form():
     go = o.fisher_grad(oracle_target(pr), logw.cpu().numpy(), x.cpu().numpy().T.astype(np.float64))
     np.testing.assert_allclose(g, go, rtol=1e-4, atol=1e-2)
     r.close()
+
+
+def tcs_asmc(pr, move, N, beta, eps, seed, ess_frac, leapfrog=5, contraction=None):
+    r = oais.OAIS(pr, move, N, beta, eps=eps, seed=seed, leapfrog=leapfrog,
+                  contraction=oais.CONTRACT_BF16_TC_STREAM if contraction is None else contraction)
+    res = r.asmc_round(ess_frac, len(beta) - 1)
+    logw, ell, x = r.particles()
+    ess, rs, anc = r.resampling()
+    out = dict(res=res, logw=logw.cpu().numpy().copy(), ell=ell.cpu().numpy().copy(),
+               x=x.cpu().numpy().T.astype(np.float64).copy(), ess=ess, resampled=rs, anc=anc, **r.stats())
+    r.close()
+    return out
+
+
+@pytest.mark.parametrize("kind,n,d,move,L", [("linreg", 300, 20, oais.HMC, 3), ("logreg", 777, 64, oais.MALA, 1)])
+def test_stream_asmc_without_resampling_equals_sweep(kind, n, d, move, L):
+    # with nu = 0 the lock-step ASMC (one launch per step over the stored state) only closes
+    # the last segment: the same particles, weights and statistics as the one-launch sweep
+    pr = problem(kind, n, d, seed=n + d)
+    N, T = 300, 5
+    beta = W.linear_schedule(T) ** 3
+    eps = oais.default_step_sizes(pr, beta, move)
+    a = tcs_asmc(pr, move, N, beta, eps, 17, 0.0, leapfrog=L)
+    b = run(pr, move, N, beta, eps, 17, leapfrog=L)
+    assert a["res"]["n_resample"] == 0
+    np.testing.assert_array_equal(a["logw"], b["logw"])
+    np.testing.assert_array_equal(a["ell"], b["ell"])
+    np.testing.assert_array_equal(a["x"], b["x"])
+    np.testing.assert_array_equal(a["log_ghat"], b["log_ghat"])
+    # ASMC closes the segment with the log-sum-exp of its per-warp (fp32-summed) pieces, the
+    # sweep with the two-pass fp64 reduction: the same weights, agreeing to 1e-6
+    assert a["res"]["logZ"] == pytest.approx(b["res"]["logZ"], rel=1e-6)
+
+
+def test_stream_asmc_matches_oracle():
+    # adaptive resampling (ESS < N / 2) on the streamed HMC kernel against the oracle's Alg. 1
+    pr = W.linreg(n=300, d=20, seed=320)
+    N, T = 400, 12
+    beta = W.linear_schedule(T) ** 2
+    eps = oais.default_step_sizes(pr, beta, oais.HMC)
+    g = tcs_asmc(pr, oais.HMC, N, beta, eps, 29, 0.5, leapfrog=3)
+    r = o.asmc(oracle_target(pr), o.HMC, N, beta, eps, 29, leapfrog=3, ess_frac=0.5)
+    assert r["n_resample"] > 0
+    np.testing.assert_array_equal(g["resampled"], r["resampled"])
+    np.testing.assert_allclose(g["ess"], r["ess"], rtol=1e-5)
+    assert g["res"]["logZ"] == pytest.approx(r["logZ"], rel=1e-5, abs=1e-3)
+    ok = agree(g["logw"], g["ell"], g["x"], r["logw"], r["ell"], r["x"], r["margin"])
+    assert ok.mean() >= 0.9
+
+
+def test_stream_asmc_linreg_logZ_closed_form():
+    # ASMC in a regime where plain AIS degenerates: log Z_hat within 4 delta-method SE (plus
+    # 0.1) of the closed form on X~
+    from test_oracle_closed_forms import linreg_logZ_woodbury
+    pr = W.linreg(n=2000, d=16, seed=12)
+    Xt, y = f16_of_bf16(pr.X), pr.y.astype(np.float64)
+    lz = linreg_logZ_woodbury(Xt, y, pr.ref_scale, pr.p0)
+    N, T = 8192, 128
+    beta = W.linear_schedule(T) ** 4
+    eps = oais.default_step_sizes(pr, beta, oais.HMC)
+    g = tcs_asmc(pr, oais.HMC, N, beta, eps, 41, 0.5, leapfrog=5)
+    assert g["res"]["n_resample"] > 0
+    assert abs(g["res"]["logZ"] - lz) < 4 * g["res"]["se"] + 0.1, (g["res"], lz)
