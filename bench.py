@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--workload", default="logreg", choices=["logreg", "linreg", "batched", "gmm", "gauss"])
     ap.add_argument("--particles", type=int, default=None,
                     help="linreg / batched: particles per problem (profiling a smaller case)")
+    ap.add_argument("--asmc", action="store_true",
+                    help="linreg: ASMC rounds (resampling when ESS < N/2) instead of OAIS rounds, with the "
+                         "closed-form log Z of the data the kernel samples")
     ap.add_argument("--x-storage", default="bf16", choices=["bf16", "fp8"],
                     help="linreg: X held as bf16 values (f16 encoding) or FP8 e4m3 with per-row scales")
     ap.add_argument("--compare-sequential", action="store_true",
@@ -411,10 +414,32 @@ def bench_linreg(args):
 
     def job():
         run.set_schedule(beta0, eps0)
+        if args.asmc:
+            return [run.asmc_round(0.5, rounds[min(k + 1, len(rounds) - 1)]) for k in range(len(rounds))]
         return [run.round(rounds[min(k + 1, len(rounds) - 1)]) for k in range(len(rounds))]
 
     total, last, clk = timed_job(job, args.steps, args.warmup, stream, ClockSampler(0))
     peaks, src = measured_peaks()
+    closed = None
+    if args.asmc:
+        # log Z of the data the kernel samples (X~ = f16(bf16(X)), or s q for FP8 storage),
+        # Woodbury / determinant-lemma form in fp64
+        import torch as th
+        X32 = np.ascontiguousarray(pr.X, dtype=np.float32)
+        if args.x_storage == "fp8":
+            mx = np.abs(X32).max(axis=1)
+            sc = np.where(mx > 0, mx / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+            q = th.from_numpy((X32 / sc[:, None]).astype(np.float32)).to(th.float8_e4m3fn).to(th.float64).numpy()
+            Xt = sc.astype(np.float64)[:, None] * q
+        else:
+            Xt = th.from_numpy(X32).to(th.bfloat16).to(th.float32).numpy().astype(np.float16).astype(np.float64)
+        yv = pr.y.astype(np.float64)
+        XtX, Xty = Xt.T @ Xt, Xt.T @ yv
+        A = np.eye(pr.d) / pr.ref_scale ** 2 + XtX / pr.p0 ** 2
+        _, logdet = np.linalg.slogdet(np.eye(pr.d) + (pr.ref_scale ** 2 / pr.p0 ** 2) * XtX)
+        m = np.linalg.solve(A, Xty / pr.p0 ** 2)
+        closed = float(-0.5 * pr.n * np.log(2 * np.pi) - pr.n * np.log(pr.p0) - 0.5 * logdet
+                       - yv @ yv / (2 * pr.p0 ** 2) + Xty @ m / (2 * pr.p0 ** 2))
     sweep_s = sum(r["sweep_ms"] for r in last) / 1e3
     ps = N * sum(rounds)
     evals = N * sum(1 + T * L for T in rounds)          # log L + gradient evaluations per job
@@ -429,6 +454,8 @@ def bench_linreg(args):
                    "x_storage": args.x_storage,
                    "l2": "flushed between timed steps (256 MiB write)"},
         "logZ_last_round": last[-1]["logZ"], "se_last_round": last[-1]["se"],
+        "asmc": ({"logZ_closed_form": closed, "resampling_events": [r["n_resample"] for r in last],
+                  "logZ_per_round": [r["logZ"] for r in last]} if args.asmc else None),
         "roofline": {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
                      "traffic": None, "peak_source": f"{src} cuBLAS bf16 sustained (f16 runs at the same rate)",
                      "issued_tflops": 2 * alg, "issued_frac": 2 * alg / peak,

@@ -364,6 +364,18 @@ oais_status oais_batch_context(oais_batch* b, int32_t p, oais_ctx** ctx);
 const char* oais_batch_last_error(const oais_batch* b);
 void oais_batch_destroy(oais_batch* b);
 
+/* Budget (Alg. 2; the paper's rule for increasing N and T between rounds): multiply the
+ * particle count and the schedule length by sqrt(2) until the particle count reaches N_cap
+ * (the step that would pass it stops at N_cap), then keep N and double T; T never exceeds
+ * T_cap.  N_next is rounded to the nearest multiple of 128 (at least 128, at most N_cap),
+ * T_next to the nearest integer (at least T + 1 while T < T_cap).  Pure host arithmetic; OAIS_EINVAL for N, T < 1 or caps below them. */
+oais_status oais_budget(int64_t N, int32_t T, int64_t N_cap, int32_t T_cap, int64_t* N_next, int32_t* T_next);
+
+/* Active particle count of the next rounds (1 <= N <= the count the context was created
+ * with; unsharded contexts): a round with more particles needs no new workspace as long as
+ * the context was created with the largest count (Budget). */
+oais_status oais_set_particles(oais_ctx* ctx, int64_t N);
+
 /* Problem index p (0 <= p <= 65535) of a single context: its random numbers use the tag
  * round | p << 16, as problem p of a batch does.  Default 0. */
 oais_status oais_set_problem(oais_ctx* ctx, int32_t p);

@@ -123,6 +123,7 @@ struct oais_ctx {
     oais_move mv{};
     DevTarget dt;
     int64_t N = 0;
+    int64_t N_cap = 0;                   // the particle count the workspace was laid out for
     int T_max = 0;
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
@@ -370,6 +371,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     ctx->tg_in = *tg;
     ctx->mv = *mv;
     ctx->N = N;
+    ctx->N_cap = N;
     ctx->N_total = N;
     ctx->T_max = T_max;
     ctx->seed = seed;
@@ -1362,6 +1364,37 @@ void oais_batch_destroy(oais_batch* b)
     cudaFreeHost(b->h_status);
     for (oais_ctx* c : b->ctx) oais_destroy(c);
     delete b;
+}
+
+oais_status oais_budget(int64_t N, int32_t T, int64_t N_cap, int32_t T_cap, int64_t* N_next, int32_t* T_next)
+{
+    if (N < 1 || T < 1 || N_cap < N || T_cap < T || !N_next || !T_next)
+        return fail(nullptr, OAIS_EINVAL, "bad arguments to oais_budget");
+    const double r2 = std::sqrt(2.0);
+    int64_t n = (int64_t)std::llround((double)N * r2 / 128.0) * 128;
+    n = std::max<int64_t>(128, n);
+    int64_t t;
+    if (N < N_cap) {    // grow both; the last growth step stops at the cap
+        n = std::min(std::max(n, N + 1), N_cap);
+        t = std::llround((double)T * r2);
+    } else {            // memory exhausted: keep N, double T
+        n = N;
+        t = 2 * (int64_t)T;
+    }
+    t = std::max<int64_t>(t, (int64_t)T + 1);
+    *N_next = std::min(n, N_cap);
+    *T_next = (int32_t)std::min<int64_t>(t, T_cap);
+    return OAIS_OK;
+}
+
+oais_status oais_set_particles(oais_ctx* ctx, int64_t N)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (ctx->N_total != ctx->N) return fail(ctx, OAIS_EINVAL, "sharded contexts keep their particle block");
+    if (N < 1 || N > ctx->N_cap) return fail(ctx, OAIS_EINVAL, "N outside [1, the count the context was created with]");
+    ctx->N = N;
+    ctx->N_total = N;
+    return OAIS_OK;
 }
 
 oais_status oais_set_problem(oais_ctx* ctx, int32_t p)

@@ -101,6 +101,8 @@ def lib():
                 "oais_batch_last_error": ([P], ctypes.c_char_p),
                 "oais_batch_destroy": ([P], None),
                 "oais_set_problem": ([P, i32], i32),
+                "oais_budget": ([i64, i32, i64, i32, P, P], i32),
+                "oais_set_particles": ([P, i64], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -207,6 +209,11 @@ class OAIS:
         if getattr(self, "_ctx", None) and self._ctx.value:
             lib().oais_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
+
+    def set_particles(self, N):
+        """Active particle count of the next rounds (at most the count the run was created with)."""
+        _check(lib().oais_set_particles(self._ctx, int(N)), self._ctx)
+        self.N = int(N)
 
     def set_problem(self, p):
         """Problem index p in the random-number tag (round | p << 16), as problem p of a batch."""
@@ -437,6 +444,33 @@ def log_likelihood_function():
             return (grad_out.to(g.dtype)[:, None] * g.t()), None
 
     return LogLikelihood
+
+
+def budget(N, T, N_cap, T_cap):
+    """Alg. 2's Budget: (N, T) times sqrt(2) while N fits N_cap, then T doubles (oais_budget)."""
+    Nn, Tn = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().oais_budget(int(N), int(T), int(N_cap), int(T_cap), ctypes.byref(Nn), ctypes.byref(Tn)))
+    return Nn.value, Tn.value
+
+
+def run_rounds(problem, move_kind, N0, T0, rounds, N_cap, T_cap, asmc=False, ess_frac=0.5, **kw):
+    """Alg. 2 with Budget: `rounds` rounds starting from N0 particles on the linear schedule of
+    length T0; each round's particle count and schedule length come from budget().  One run
+    holds N_cap particles' worth of memory.  Returns [(N, T, result)] per round."""
+    beta0 = np.linspace(0.0, 1.0, int(T0) + 1)
+    r = OAIS(problem, move_kind, int(N_cap), beta0, T_max=int(T_cap), **kw)
+    r.set_particles(N0)
+    N, T, out = int(N0), int(T0), []
+    try:
+        for _ in range(int(rounds)):
+            Nn, Tn = budget(N, T, N_cap, T_cap)
+            res = r.asmc_round(ess_frac, Tn) if asmc else r.round(Tn)
+            out.append((N, T, res))
+            r.set_particles(Nn)
+            N, T = Nn, Tn
+    finally:
+        r.close()
+    return out
 
 
 class OAISBatch:

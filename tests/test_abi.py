@@ -73,3 +73,22 @@ def test_validation_errors_need_no_gpu():
     assert L.oais_workspace_bytes(ctypes.byref(tg), ctypes.byref(mv), 100, 4, ctypes.byref(nbytes)) == 0
     assert nbytes.value > 0
     assert L.oais_status_string(4) == b"non-finite log-weight or log-likelihood"
+
+
+def test_budget_rule():
+    # Alg. 2's Budget: (N, T) x sqrt(2) while N fits the cap, then T doubles with N kept
+    from paper_2408_12057_gb300 import oais
+    N, T, seen = 1024, 64, []
+    for _ in range(8):
+        N2, T2 = oais.budget(N, T, 4096, 4096)
+        seen.append((N2, T2))
+        if N < 4096:
+            assert N2 % 128 == 0 and (N2 == 4096 or abs(N2 / N - 2 ** 0.5) < 0.1)
+            assert abs(T2 / T - 2 ** 0.5) < 0.05
+        else:
+            assert N2 == N and T2 == min(2 * T, 4096)
+        N, T = N2, T2
+    assert seen == [(1408, 91), (2048, 129), (2944, 182), (4096, 257), (4096, 514), (4096, 1028),
+                    (4096, 2056), (4096, 4096)]
+    with pytest.raises(Exception):
+        oais.budget(0, 10, 100, 100)
