@@ -9,7 +9,7 @@
 // so log L(x) = sum f (kept in fp32 registers) and grad log L(x) = G (kept in TMEM)
 // for every particle of the tile in one pass over X.  To keep the products at fp32
 // accuracy the particle states and the residuals are split into two BF16 terms,
-// v = hi + lo with hi a bf16 and lo = bf16(v - hi) (relative error below 2^-15), and each
+// v = hi + lo with hi a bf16 and lo = bf16(v - hi) (relative error below 2^-16), and each
 // contraction is issued once per term.  The data X is rounded to BF16 once (X~); the
 // sampler targets the posterior of X~.
 //
@@ -55,24 +55,24 @@ constexpr int kSmemBytes = kOffStat + kGroups * kStatBytes;
 constexpr int kTmemCols = 512;               // group g: D1[0], D1[1] at 256 g + {0, 64}, D2 at 256 g + 128
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
+constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint32_t kIdescFwd = idesc_bf16(128, kChunk, false);
 constexpr uint32_t kIdescBwd = idesc_bf16(128, kD, true);
 
 __device__ __forceinline__ void group_sync(int g) { named_sync(1 + g, kGroupThreads); }
 
 // Two-term bf16 split of a pair of floats, v = hi + lo: hi = v with the low 16 bits of its
-// fp32 word cleared (a bf16 value), lo = v - hi (exact in fp32, |lo| < 2^-7 |v|); lo is
-// rounded to the nearest bf16 by adding half a bf16 ulp to its fp32 word before taking the
-// top half (error at most 2^-8 |lo|, no sign bias), so hi + bf16(lo) is within 2^-15 |v|.
-// The bf16 bit patterns are the top halves of the fp32 words, packed pairwise with one byte
-// permute each.
+// fp32 word cleared (a bf16 value, |v - hi| < 2^-7 |v|, exact in fp32), lo = v - hi rounded
+// to the nearest bf16 (error at most 2^-9 |v - hi|, no sign bias), so hi + lo is within
+// 2^-16 |v|.  The hi pair is the top halves of the two fp32 words (one byte permute); the
+// two differences take one packed subtraction and the lo pair one conversion.
 __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo)
 {
     const float ha = __uint_as_float(__float_as_uint(a) & 0xFFFF0000u);
     const float hb = __uint_as_float(__float_as_uint(b) & 0xFFFF0000u);
-    const float la = __fsub_rn(a, ha), lb = __fsub_rn(b, hb);
+    const float2 l = sub_f32x2(make_float2(a, b), make_float2(ha, hb));
     hi = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
-    lo = __byte_perm(__float_as_uint(la) + 0x8000u, __float_as_uint(lb) + 0x8000u, 0x7632);
+    lo = bf16x2_rn(l.x, l.y);
 }
 
 struct TcParams {
@@ -94,12 +94,13 @@ struct Group {
     unsigned char* smem;
 };
 
-// write a 128-particle row of 32 values (split hi/lo) into the group's A tiles
+// write a 128-particle row of 32 values, scaled by log2(e) and split hi/lo, into the group's
+// A tiles (the forward contraction then gives the margins in base-2 units)
 __device__ __forceinline__ void write_state_tile(const Group& G, const float (&v)[kD])
 {
     uint32_t hi[16], lo[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) split_pair(v[2 * j], v[2 * j + 1], hi[j], lo[j]);
+    for (int j = 0; j < 16; ++j) split_pair(kLog2e * v[2 * j], kLog2e * v[2 * j + 1], hi[j], lo[j]);
     unsigned char* ah = G.smem + kOffA + (G.g * 2 + 0) * kATile;
     unsigned char* al = G.smem + kOffA + (G.g * 2 + 1) * kATile;
     const int p = G.tid;
@@ -175,18 +176,21 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
     const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
     unsigned char* rh = G.smem + kOffR + (G.g * 2 + 0) * kRTile;
     unsigned char* rl = G.smem + kOffR + (G.g * 2 + 1) * kRTile;
-    // The image holds X'_r = s_r X~_r with s_r = 2 y_r - 1, so the forward contraction gives
-    // u = s z directly.  Per row: log-likelihood term log sigmoid(u) = min(u, 0) + log(q),
-    // q = 1 / (1 + e^-|u|), and d/dz = s sigmoid(-u), so grad = sum_r sigmoid(-u_r) X'_r.
-    // sum min(u, 0) is accumulated as sum (u - |u|) / 2; the logs (base 2) as one log per 16
-    // rows of the product of q (each q in [1/2, 1], no underflow).  Padded rows (X' = 0) give
-    // u = 0: -log 2 each, corrected below, and nothing to the gradient.
-    float twice_min = 0.0f, logs2 = 0.0f;
+    // The image holds X'_r = s_r X~_r with s_r = 2 y_r - 1 and the state tile holds log2(e) x,
+    // so the forward contraction gives u = log2(e) s z (the margin in base-2 units).  Per row:
+    // log sigmoid(s z) = ln 2 (min(u, 0) + log2 q), q = 1 / (1 + 2^-|u|), and d/dz = s sigmoid(-s z),
+    // so grad = sum_r sigmoid(-s_r z_r) X'_r with sigmoid(-s z) = 2^-|u| q for u >= 0, q for u < 0.
+    // The rows of a pair go through the packed fp32 pair instructions; the sum of min(u, 0)
+    // and the product of q are kept per lane of the pair and per chunk (64 rows: each product
+    // of 32 values in [1/2, 1], no underflow), with one log per chunk.  Padded rows (X' = 0)
+    // give u = 0: log2 q = -1 each, corrected below, and nothing to the gradient.
+    float sum_min = 0.0f, logs2 = 0.0f;
     if (G.tid == 0 && !G.dead) {
         tc_after_sync();
         issue_fwd(G, 0, 0);
         if (nch > 1) issue_fwd(G, 1, 1);
     }
+    const float2 one2 = make_float2(1.0f, 1.0f);
     for (int c = 0; c < nch; ++c) {
         const int b = c & 1;
         wait_fwd(G, b);
@@ -197,27 +201,22 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
 #pragma unroll
         for (int s = 0; s < kChunk / 32; ++s) tmem_ld32(G.d1[b] + lane_off + s * 32, vs[s]);
         tmem_wait_ld();
+        float2 prod = one2, mn = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int s = 0; s < kChunk / 32; ++s) {
             const uint32_t (&v)[32] = vs[s];
-            float prod = 1.0f, tm = 0.0f;
             uint32_t hi[16], lo[16];
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
-                float r2[2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const float u = __uint_as_float(v[j + q]);
-                    const float e = ex2_approx(fabsf(u) * -1.4426950408889634f);   // e^-|u|
-                    const float qinv = rcp_approx(1.0f + e);
-                    r2[q] = u >= 0.0f ? e * qinv : qinv;                          // sigmoid(-u)
-                    tm += u - fabsf(u);
-                    prod *= qinv;
-                }
-                if ((j & 15) == 14) { logs2 += lg2_approx(prod); prod = 1.0f; }
-                split_pair(r2[0], r2[1], hi[j / 2], lo[j / 2]);
+                const float ua = __uint_as_float(v[j]), ub = __uint_as_float(v[j + 1]);
+                const float2 e = make_float2(ex2_approx(-fabsf(ua)), ex2_approx(-fabsf(ub)));
+                const float2 dq = add_f32x2(e, one2);
+                const float2 q = make_float2(rcp_approx(dq.x), rcp_approx(dq.y));
+                const float2 eq = mul_f32x2(e, q);
+                mn = add_f32x2(mn, make_float2(fminf(ua, 0.0f), fminf(ub, 0.0f)));
+                prod = mul_f32x2(prod, q);
+                split_pair(ua >= 0.0f ? eq.x : q.x, ub >= 0.0f ? eq.y : q.y, hi[j / 2], lo[j / 2]);
             }
-            twice_min += tm;
             if (s == 0 && c > 0) wait_bwd(G);     // the backward of chunk c-1 has read R
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
@@ -229,6 +228,8 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
                     make_uint4(lo[4 * cc], lo[4 * cc + 1], lo[4 * cc + 2], lo[4 * cc + 3]);
             }
         }
+        sum_min += mn.x + mn.y;
+        logs2 += lg2_approx(prod.x * prod.y);
         fence_proxy_async();                      // my R rows, visible to the tensor core
         tc_before_sync();                         // my reads of D1[b] before its next forward
         __syncwarp();
@@ -253,7 +254,7 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
     for (int i = 0; i < kD; ++i) grad[i] = __uint_as_float(v[i]);
     tc_before_sync();
     const float ln2 = 0.69314718055994531f;
-    return 0.5f * twice_min + ln2 * logs2 + (float)(nch * kChunk - P.n) * ln2;
+    return ln2 * (sum_min + logs2 + (float)(nch * kChunk - P.n));
 }
 
 // the group's 4 warps merge their (m, s) moment pieces and acceptance counts (fixed order)
