@@ -102,7 +102,12 @@ static_assert(sizeof(StepPartial) == 56, "StepPartial layout");
 constexpr int kMaxWarps = 32;
 
 // Warp part: v_i = lw + i * lg for the lane's particle (or -inf if inactive).
-// Writes the warp's (m_i, s_i) for i = 0..2 through lane 0.
+// Writes the warp's (m_i, s_i) for i = 0..2 through lane 0.  By default the offsets from the
+// anchor particle and from the warp maximum are fp64 differences rounded once.  kFast (the
+// tensor-core kernels, whose particle arithmetic is fp32 and whose fp64 pipe is slow): both
+// come from two fp64 differences per particle (lw - lw_a, lg - lg_a) in fp32, which adds
+// about 2^-24 |offset from the anchor| to each exponent.
+template <bool kFast = false>
 __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool active,
                                                     double* wm /*3*/, float* ws /*3*/)
 {
@@ -118,51 +123,81 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
     }
     const int src = __ffs(act) - 1;
     const double a0 = __shfl_sync(full, lw, src), b0 = __shfl_sync(full, lg, src);
+    const float dw = kFast ? (float)(lw - a0) : 0.0f, dg = kFast ? (float)(lg - b0) : 0.0f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const double anchor = a0 + i * b0;
         const double v = lw + i * lg;
-        float f = active ? (float)(v - anchor) : -INFINITY;
+        float f = !active ? -INFINITY : kFast ? dw + (float)i * dg : (float)(v - anchor);
         float mx = f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
         const double M = anchor + (double)mx;
-        float e = active ? __expf((float)(v - M)) : 0.0f;
+        float e = !active ? 0.0f : kFast ? __expf(f - mx) : __expf((float)(v - M));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
         if ((threadIdx.x & 31) == 0) { wm[i] = M; ws[i] = e; }
     }
 }
 
-// CTA part: warp 0 merges the W warps' (m, s) (lane j holds warp j) in a fixed order and
-// writes one record.  Call after a __syncthreads that follows warp_moment_partial.
-template <int W>
-__device__ __forceinline__ void cta_moment_record(const double (*wm)[3], const float (*ws)[3],
+// Merge of W warps' (m, s) pieces (lane j of the calling warp reads warp j's) in a fixed
+// order into one record: M = max_j m_j, S = sum_j s_j exp(m_j - M).  The shifts stay in
+// fp64.  kFast: the rescaling takes d_j = m_j - M (exact in fp64) rounded to fp32 and an fp32
+// exponential, and the sum is fp32 (|d| e^d <= 1/e bounds the effect of the rounding of d on S
+// by 2^-24 / e of S; the pieces s_j are fp32 sums already), a handful of fp64 instructions
+// instead of an fp64 exponential per moment: the tensor-core kernels use it, the fp64 pipe
+// being slow on this part.  Lanes < W take part (every lane of the warp calls it); W is a
+// power of two <= 32.
+// kFast = false keeps the rescaling and the sum in fp64 (the CUDA-core forms).
+template <int W, bool kFast>
+__device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3], const float (*ws)[3],
                                                   const unsigned* wacc, StepPartial* out)
 {
-    const int lane = threadIdx.x & 31;
-    if ((threadIdx.x >> 5) != 0) return;
+    static_assert(W >= 1 && W <= 32 && (W & (W - 1)) == 0, "W: a power of two");
     StepPartial rec;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const double m = lane < W ? wm[lane][i] : -INFINITY;
         double M = m;
+        if (kFast) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
-        double v = (lane < W && m != -INFINITY) ? (double)ws[lane][i] * exp(m - M) : 0.0;
+            for (int o = 1; o < W; o <<= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
+        } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
+        }
+        if (kFast) {
+            const float dj = (float)(m - M);      // -inf for an empty piece; NaN when every piece is
+            float v = (lane < W && !isnan(dj)) ? ws[lane][i] * expf(dj) : 0.0f;
+#pragma unroll
+            for (int o = 1; o < W; o <<= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            rec.s[i] = (double)v;
+        } else {
+            double v = (lane < W && m != -INFINITY) ? (double)ws[lane][i] * exp(m - M) : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            rec.s[i] = v;
+        }
         rec.m[i] = M;
-        rec.s[i] = v;
     }
     unsigned a = (wacc && lane < W) ? wacc[lane] : 0u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    for (int o = 1; o < 32; o <<= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
     if (lane == 0) {
         rec.accepted = a;
         rec.pad = 0;
         *out = rec;
     }
+}
+
+// CTA part: warp 0 merges the W warps' pieces and writes one record.  Call after a
+// __syncthreads that follows warp_moment_partial.
+template <int W>
+__device__ __forceinline__ void cta_moment_record(const double (*wm)[3], const float (*ws)[3],
+                                                  const unsigned* wacc, StepPartial* out)
+{
+    if ((threadIdx.x >> 5) != 0) return;
+    merge_warp_pieces<W, false>(threadIdx.x & 31, wm, ws, wacc, out);
 }
 
 // merge (m, s) pairs: exp(m) s + exp(m') s'

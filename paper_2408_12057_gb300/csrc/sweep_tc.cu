@@ -13,9 +13,11 @@
 // contraction is issued once per term.  The data X is rounded to BF16 once (X~); the
 // sampler targets the posterior of X~.
 //
-// CTA = 2 independent groups of 4 warps; group g owns 128 particles, its own TMEM
-// columns, operand tiles and MMA barrier, and shares the BF16 image of X (resident in
-// shared memory for the whole sweep).  One thread per group issues the MMAs.
+// CTA = 2 independent groups of 4 particle warps plus one MMA warp each; group g owns 128
+// particles, its own TMEM columns, operand tiles and barriers, and shares the BF16 image of
+// X (resident in shared memory for the whole sweep).  The group's MMA warp issues its
+// tcgen05.mma instructions (one lane issues, the warp runs the loop), so the particle warps
+// never wait on the issue of a contraction.
 //
 // Shared memory (dynamic, 1024-byte aligned base):
 //   R tiles  [group][hi|lo]  128 x 64 bf16, K-major, 128B swizzle    4 x 16 KB
@@ -23,7 +25,7 @@
 //   X image  2048 x 32 bf16, rows of 64 B, 64B swizzle              128 KB
 //            (read as the K-major B of the forward and the MN-major B of the backward)
 //   y bits   2048 labels as a bitmask                                256 B
-//   2 mbarriers, the TMEM base address, per-group moment scratch
+//   6 mbarriers per group, the TMEM base address, the abort flag, per-group moment scratch
 #include <cuda_bf16.h>
 #include <cstring>
 #include <vector>
@@ -37,7 +39,10 @@ namespace tc {
 
 constexpr int kGroups = 2;
 constexpr int kGroupThreads = 128;
-constexpr int kThreads = kGroups * kGroupThreads;
+constexpr int kMmaWarp0 = kGroups * kGroupThreads / 32;  // group g's MMA warp: kMmaWarp0 + g
+constexpr int kParticlesPerCta = kGroups * kGroupThreads;
+constexpr int kThreads = kParticlesPerCta + 32 * kGroups;
+constexpr int kBarsPerGroup = 6;             // forward into D1[0], D1[1]; backward; R written; A written; end
 constexpr int kD = 32;                       // padded state dimension
 constexpr int kChunk = 64;                   // data rows per contraction chunk
 constexpr int kMaxRows = 2048;
@@ -47,8 +52,9 @@ constexpr int kOffR = 0;
 constexpr int kOffA = kOffR + kGroups * 2 * kRTile;          // 64 KB
 constexpr int kOffX = kOffA + kGroups * 2 * kATile;          // 96 KB
 constexpr int kOffY = kOffX + kMaxRows * kD * 2;             // 224 KB
-constexpr int kOffBar = kOffY + kMaxRows / 8;                // + 256 B; 3 barriers per group
-constexpr int kOffTmem = kOffBar + 8 * 4 * kGroups;       // 4 barriers per group
+constexpr int kOffBar = kOffY + kMaxRows / 8;                // + 256 B
+constexpr int kOffTmem = kOffBar + 8 * kBarsPerGroup * kGroups;
+constexpr int kOffAbort = kOffTmem + 4;
 constexpr int kOffStat = kOffTmem + 16;
 constexpr int kStatBytes = 2 * 4 * 3 * 8 + 2 * 4 * 3 * 4 + 2 * 4 * 4;   // [slot][warp] m, s, acc
 constexpr int kSmemBytes = kOffStat + kGroups * kStatBytes;
@@ -83,14 +89,41 @@ struct TcParams {
     int d;                   // true dimension (<= 32; padded columns of X are zero)
 };
 
-struct Group {
-    int g, tid, warp;
-    uint32_t barF[2], barB;  // mbarriers (smem addresses): forward into D1[i], backward
+// the shared-memory and TMEM addresses of group g's barriers and accumulators
+struct GroupAddr {
+    uint32_t barF[2], barB;  // mbarriers: forward into D1[i] done, backward done
     uint32_t barR;           // mbarrier: the group's 4 warps have written their R rows
+    uint32_t barA;           // mbarrier: the group's 4 warps have written their A rows
+    uint32_t barEnd;         // mbarrier: every MMA of the group has completed (end of the sweep)
     uint32_t d1[2], d2;      // TMEM addresses
+    uint32_t smem;           // shared-memory base address
+    int g;
+};
+__device__ __forceinline__ GroupAddr group_addr(unsigned char* smem, uint32_t tmem, int g)
+{
+    GroupAddr A;
+    const uint32_t bars = saddr(smem + kOffBar) + 8u * (uint32_t)(kBarsPerGroup * g);
+    A.barF[0] = bars;
+    A.barF[1] = bars + 8;
+    A.barB = bars + 16;
+    A.barR = bars + 24;
+    A.barA = bars + 32;
+    A.barEnd = bars + 40;
+    A.d1[0] = tmem + (uint32_t)(g * 256);
+    A.d1[1] = tmem + (uint32_t)(g * 256 + 64);
+    A.d2 = tmem + (uint32_t)(g * 256 + 128);
+    A.smem = saddr(smem);
+    A.g = g;
+    return A;
+}
+
+struct Group {
+    GroupAddr a;
+    int g, tid, warp;
     uint32_t stash;          // TMEM columns parking the particle state during an evaluation
-    uint32_t phF, phB, phR;  // expected phase of barF[i] (bit i), barB, barR
-    bool dead;               // an MMA barrier wait timed out
+    uint32_t phF, phB;       // expected phase of barF[i] (bit i), barB
+    bool dead;               // a barrier wait timed out or the MMA warp gave up
+    volatile int* abort;     // set by whichever role times out first
     unsigned char* smem;
 };
 
@@ -113,9 +146,9 @@ __device__ __forceinline__ void write_state_tile(const Group& G, const float (&v
 }
 
 // forward contraction of chunk c into D1[buf]: Z = (P_hi + P_lo) X'_c^T
-__device__ __forceinline__ void issue_fwd(const Group& G, int c, int buf)
+__device__ __forceinline__ void issue_fwd(const GroupAddr& G, int c, int buf, uint32_t leader)
 {
-    const uint32_t base = saddr(G.smem);
+    const uint32_t base = G.smem;
     const uint32_t xb = base + kOffX;
 #pragma unroll
     for (int hl = 0; hl < 2; ++hl) {
@@ -124,16 +157,16 @@ __device__ __forceinline__ void issue_fwd(const Group& G, int c, int buf)
         for (int kk = 0; kk < kD / 16; ++kk) {
             const uint64_t a = sdesc(aa + kk * 32, 16, 512, kSW64);
             const uint64_t b = sdesc(xb + c * kChunk * 64 + kk * 32, 16, 512, kSW64);
-            mma_f16(G.d1[buf], a, b, kIdescFwd, (hl == 0 && kk == 0) ? 0u : 1u);
+            mma_f16_by(leader, G.d1[buf], a, b, kIdescFwd, (hl == 0 && kk == 0) ? 0u : 1u);
         }
     }
-    mma_commit(G.barF[buf]);
+    mma_commit_by(leader, G.barF[buf]);
 }
 
 // backward contraction of chunk c into D2: G += (R_hi + R_lo) X'_c (first starts the sum)
-__device__ __forceinline__ void issue_bwd(const Group& G, int c, bool first)
+__device__ __forceinline__ void issue_bwd(const GroupAddr& G, int c, bool first, uint32_t leader)
 {
-    const uint32_t base = saddr(G.smem);
+    const uint32_t base = G.smem;
     const uint32_t xb = base + kOffX;
 #pragma unroll
     for (int hl = 0; hl < 2; ++hl) {
@@ -142,35 +175,80 @@ __device__ __forceinline__ void issue_bwd(const Group& G, int c, bool first)
         for (int kk = 0; kk < kChunk / 16; ++kk) {
             const uint64_t a = sdesc(ra + kk * 32, 16, 1024, kSW128);
             const uint64_t b = sdesc(xb + (c * kChunk + kk * 16) * 64, 8192, 512, kSW64);
-            mma_f16(G.d2, a, b, kIdescBwd, (first && hl == 0 && kk == 0) ? 0u : 1u);
+            mma_f16_by(leader, G.d2, a, b, kIdescBwd, (first && hl == 0 && kk == 0) ? 0u : 1u);
         }
     }
-    mma_commit(G.barB);
+    mma_commit_by(leader, G.barB);
 }
 
 __device__ __forceinline__ void wait_fwd(Group& G, int buf)
 {
-    if (!G.dead && !mbar_wait(G.barF[buf], (G.phF >> buf) & 1u)) G.dead = true;
+    if (!G.dead && !mbar_wait(G.a.barF[buf], (G.phF >> buf) & 1u, G.abort)) {
+        G.dead = true;
+        *G.abort = 1;
+    }
     G.phF ^= 1u << buf;
 }
 __device__ __forceinline__ void wait_bwd(Group& G)
 {
-    if (!G.dead && !mbar_wait(G.barB, G.phB)) G.dead = true;
+    if (!G.dead && !mbar_wait(G.a.barB, G.phB, G.abort)) {
+        G.dead = true;
+        *G.abort = 1;
+    }
     G.phB ^= 1u;
+}
+
+// Group g's MMA warp (lane 0 issues): per evaluation it waits for the A tile and issues the
+// forwards of chunks 0 and 1, then per chunk c waits for the R tile and issues the backward
+// of chunk c and the forward of chunk c + 2 into the D1 buffer just read.  A wait that times
+// out (or another role's) sets the abort flag and ends the loop; before returning the warp
+// waits for every MMA it issued, so tensor memory is never released under a running
+// contraction.
+__device__ void mma_issuer(unsigned char* smem, uint32_t tmem, int g, int nch, int evals, volatile int* abort)
+{
+    const GroupAddr A = group_addr(smem, tmem, g);
+    const uint32_t leader = (threadIdx.x & 31) == 0;
+    uint32_t phA = 0, phR = 0;
+    bool ok = true;
+    for (int e = 0; e < evals && ok; ++e) {
+        ok = mbar_wait(A.barA, phA, abort);
+        phA ^= 1u;
+        if (!ok) break;
+        tc_after_sync();
+        issue_fwd(A, 0, 0, leader);
+        if (nch > 1) issue_fwd(A, 1, 1, leader);
+        for (int c = 0; c < nch; ++c) {
+            ok = mbar_wait(A.barR, phR, abort);
+            phR ^= 1u;
+            if (!ok) break;
+            tc_after_sync();
+            issue_bwd(A, c, c == 0, leader);
+            if (c + 2 < nch) issue_fwd(A, c + 2, c & 1, leader);
+        }
+    }
+    if (!ok) *abort = 1;
+    mma_commit_by(leader, A.barEnd);
+    if (!mbar_wait(A.barEnd, 0)) *abort = 1;
 }
 
 // log L(x) and grad log L(x) for the group's 128 particles; every thread of the group calls it.
 // Pipeline per chunk c: the forward of chunk c+1 runs into the other D1 buffer while the
-// epilogue of chunk c reads D1[c%2].  Each warp, once its rows of the R tile are written,
-// arrives on barR; only the issuing thread waits for all four, then issues the backward of
-// chunk c (it runs while the next chunk's first slice is computed; the R tile is waited for
-// before the next write) and the forward of chunk c+2 into the D1 buffer just read.
-__device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], float (&grad)[kD])
+// epilogue of chunk c reads D1[c%2].  Each warp arrives on barA once its rows of the A tile
+// are written and on barR once its rows of the R tile are written (and its reads of D1 are
+// done); the MMA warp then issues the backward of chunk c (it runs while the next chunk's
+// first slice is computed; the R tile is waited for before the next write) and the forward
+// of chunk c+2 into the D1 buffer just read.
+// tc_eval_begin writes the state tile; tc_eval_run does the chunks and returns log L.
+__device__ __forceinline__ void tc_eval_begin(Group& G, const float (&x)[kD])
 {
     write_state_tile(G, x);
     fence_proxy_async();
     tc_before_sync();
-    group_sync(G.g);
+    __syncwarp();
+    if ((G.tid & 31) == 0) mbar_arrive(G.a.barA);
+}
+__device__ float tc_eval_run(Group& G, const TcParams& P, float (&grad)[kD])
+{
     const int nch = (P.n + kChunk - 1) / kChunk;
     const int p = G.tid;
     const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
@@ -185,26 +263,18 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
     // of 32 values in [1/2, 1], no underflow), with one log per chunk.  Padded rows (X' = 0)
     // give u = 0: log2 q = -1 each, corrected below, and nothing to the gradient.
     float sum_min = 0.0f, logs2 = 0.0f;
-    if (G.tid == 0 && !G.dead) {
-        tc_after_sync();
-        issue_fwd(G, 0, 0);
-        if (nch > 1) issue_fwd(G, 1, 1);
-    }
     const float2 one2 = make_float2(1.0f, 1.0f);
     for (int c = 0; c < nch; ++c) {
         const int b = c & 1;
         wait_fwd(G, b);
         __syncwarp();                             // tcgen05.ld below is warp-aligned
         tc_after_sync();
-        // both 32-column slices of the chunk are requested before one wait
-        uint32_t vs[kChunk / 32][32];
-#pragma unroll
-        for (int s = 0; s < kChunk / 32; ++s) tmem_ld32(G.d1[b] + lane_off + s * 32, vs[s]);
-        tmem_wait_ld();
         float2 prod = one2, mn = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int s = 0; s < kChunk / 32; ++s) {
-            const uint32_t (&v)[32] = vs[s];
+            uint32_t v[32];
+            tmem_ld32(G.a.d1[b] + lane_off + s * 32, v);
+            tmem_wait_ld();
             uint32_t hi[16], lo[16];
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
@@ -233,22 +303,13 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
         fence_proxy_async();                      // my R rows, visible to the tensor core
         tc_before_sync();                         // my reads of D1[b] before its next forward
         __syncwarp();
-        if ((G.tid & 31) == 0) mbar_arrive(G.barR);
-        if (G.tid == 0) {
-            if (!G.dead && !mbar_wait(G.barR, G.phR)) G.dead = true;
-            G.phR ^= 1u;
-            if (!G.dead) {
-                tc_after_sync();
-                issue_bwd(G, c, c == 0);
-                if (c + 2 < nch) issue_fwd(G, c + 2, b);
-            }
-        }
+        if ((G.tid & 31) == 0) mbar_arrive(G.a.barR);
     }
     wait_bwd(G);                                  // the backward of the last chunk
     __syncwarp();
     tc_after_sync();
     uint32_t v[32];
-    tmem_ld32(G.d2 + lane_off, v);
+    tmem_ld32(G.a.d2 + lane_off, v);
     tmem_wait_ld();
 #pragma unroll
     for (int i = 0; i < kD; ++i) grad[i] = __uint_as_float(v[i]);
@@ -256,34 +317,10 @@ __device__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], floa
     const float ln2 = 0.69314718055994531f;
     return ln2 * (sum_min + logs2 + (float)(nch * kChunk - P.n));
 }
-
-// the group's 4 warps merge their (m, s) moment pieces and acceptance counts (fixed order)
-__device__ __forceinline__ void group_record(const Group& G, const double (*wm)[3], const float (*ws)[3],
-                                             const unsigned* wacc, StepPartial* out)
+__device__ __forceinline__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], float (&grad)[kD])
 {
-    if (G.warp != 0) return;
-    const int lane = G.tid & 31;
-    StepPartial rec;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const double m = lane < 4 ? wm[lane][i] : -INFINITY;
-        double M = m;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
-        double v = (lane < 4 && m != -INFINITY) ? (double)ws[lane][i] * exp(m - M) : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        rec.m[i] = M;
-        rec.s[i] = v;
-    }
-    unsigned a = lane < 4 ? wacc[lane] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-    if (lane == 0) {
-        rec.accepted = a;
-        rec.pad = 0;
-        *out = rec;
-    }
+    tc_eval_begin(G, x);
+    return tc_eval_run(G, P, grad);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -304,11 +341,15 @@ oais_sweep_tc_kernel(const TcParams P)
         cp_async_wait<0>();
     }
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
+    volatile int* abort = reinterpret_cast<volatile int*>(smem + kOffAbort);
     if (threadIdx.x == 0) {
         for (int g = 0; g < kGroups; ++g) {
-            for (int i = 0; i < 3; ++i) mbar_init(saddr(&bars[4 * g + i]), 1);
-            mbar_init(saddr(&bars[4 * g + 3]), kGroupThreads / 32);   // one arrival per warp
+            for (int i = 0; i < 3; ++i) mbar_init(saddr(&bars[kBarsPerGroup * g + i]), 1);
+            mbar_init(saddr(&bars[kBarsPerGroup * g + 3]), kGroupThreads / 32);   // one arrival per warp
+            mbar_init(saddr(&bars[kBarsPerGroup * g + 4]), kGroupThreads / 32);
+            mbar_init(saddr(&bars[kBarsPerGroup * g + 5]), 1);
         }
+        *abort = 0;
         fence_mbar_init();
     }
     if (threadIdx.x < 32) {
@@ -321,22 +362,24 @@ oais_sweep_tc_kernel(const TcParams P)
     tc_after_sync();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + kOffTmem);
 
+    if (threadIdx.x / 32 >= kMmaWarp0) {
+        mma_issuer(smem, tmem, threadIdx.x / 32 - kMmaWarp0, (P.n + kChunk - 1) / kChunk, 1 + S.T * S.mv.K, abort);
+        if (threadIdx.x % 32 == 0 && *abort) atomicOr(S.status, 2u);
+        tc_before_sync();
+        __syncthreads();
+        return;
+    }
+
     Group G;
     G.g = threadIdx.x / kGroupThreads;
     G.tid = threadIdx.x % kGroupThreads;
     G.warp = G.tid / 32;
-    G.barF[0] = saddr(&bars[4 * G.g + 0]);
-    G.barF[1] = saddr(&bars[4 * G.g + 1]);
-    G.barB = saddr(&bars[4 * G.g + 2]);
-    G.barR = saddr(&bars[4 * G.g + 3]);
-    G.d1[0] = tmem + (uint32_t)(G.g * 256);
-    G.d1[1] = tmem + (uint32_t)(G.g * 256 + 64);
-    G.d2 = tmem + (uint32_t)(G.g * 256 + 128);
+    G.a = group_addr(smem, tmem, G.g);
     G.stash = tmem + (uint32_t)(G.g * 256 + 160);   // 96 free columns: x, grad, w
     G.phF = 0;
     G.phB = 0;
-    G.phR = 0;
     G.dead = false;
+    G.abort = abort;
     G.smem = smem;
     unsigned char* st = smem + kOffStat + G.g * kStatBytes;
     double (*s_m)[4][3] = reinterpret_cast<double (*)[4][3]>(st);
@@ -365,47 +408,53 @@ oais_sweep_tc_kernel(const TcParams P)
         const double lg = (beta_t - beta_prev) * (double)ell;
         beta_prev = beta_t;
         const int slot = t & 1;
-        warp_moment_partial(logw, lg, active, s_m[slot][G.warp], s_s[slot][G.warp]);
+        warp_moment_partial<true>(logw, lg, active, s_m[slot][G.warp], s_s[slot][G.warp]);
         logw += lg;
         unsigned acc = 0;
         const float beta = (float)beta_t, e = (float)eps_t, h = 0.5f * e;
         for (int k = 0; k < S.mv.K; ++k) {
-            // MALA (Sec. 2.1.1 kernel family): x' = x + (e^2/2) grad log pi(x) + e z
-            float z[kD], xp[kD];
-            normals<kD>(S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, z);
+            // MALA (Sec. 2.1.1 kernel family): x' = x + e w with w = z + (e/2) grad log pi(x)
+            float w[kD];
+            normals<kD>(S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, w);
             float zz = 0.0f, dxx = 0.0f;
-#pragma unroll
-            for (int i = 0; i < kD; ++i) {
-                const float gpi = -x[i] * inv_s2 + beta * gl[i];
-                xp[i] = x[i] + e * (h * gpi + z[i]);
-                zz += z[i] * z[i];
-                z[i] = z[i] + h * gpi;
-                dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
-            }
-            // park x, grad and w in the group's free TMEM columns while the evaluation
-            // runs (registers go to the epilogue), then bring them back
             const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
-            tmem_st32(G.stash + lane_off, x);
-            tmem_st32(G.stash + lane_off + 32, gl);
-            tmem_st32(G.stash + lane_off + 64, z);
-            tmem_wait_st();
+            {
+                float xp[kD];
+#pragma unroll
+                for (int i = 0; i < kD; ++i) {
+                    const float gpi = -x[i] * inv_s2 + beta * gl[i];
+                    zz += w[i] * w[i];
+                    w[i] = __fmaf_rn(h, gpi, w[i]);
+                    xp[i] = __fmaf_rn(e, w[i], x[i]);
+                    dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
+                }
+                // park x, grad and w in the group's free TMEM columns while the evaluation
+                // runs (registers go to the epilogue), then bring them back; x' is rebuilt
+                // from them with the same rounding
+                tmem_st32(G.stash + lane_off, x);
+                tmem_st32(G.stash + lane_off + 32, gl);
+                tmem_st32(G.stash + lane_off + 64, w);
+                tmem_wait_st();
+                tc_eval_begin(G, xp);
+            }
             float glp[kD];
-            const float ellp = tc_eval(G, P, xp, glp);
+            const float ellp = tc_eval_run(G, P, glp);
             __syncwarp();
             tmem_ld32f(G.stash + lane_off, x);
             tmem_ld32f(G.stash + lane_off + 32, gl);
-            tmem_ld32f(G.stash + lane_off + 64, z);
+            tmem_ld32f(G.stash + lane_off + 64, w);
             float rev = 0.0f;
 #pragma unroll
             for (int i = 0; i < kD; ++i) {
-                const float q = z[i] + h * (-xp[i] * inv_s2 + beta * glp[i]);
+                const float xp = __fmaf_rn(e, w[i], x[i]);
+                const float q = w[i] + h * (-xp * inv_s2 + beta * glp[i]);
                 rev += q * q;
             }
             const float log_alpha = -0.5f * dxx * inv_s2 + beta * (ellp - ell) - 0.5f * (rev - zz);
             const float logu = mh_log_uniform(S.mv.rng, n, (uint32_t)t, (uint32_t)k, 0.0f);
             if (logu < log_alpha) {
 #pragma unroll
-                for (int i = 0; i < kD; ++i) { x[i] = xp[i]; gl[i] = glp[i]; }
+                for (int i = 0; i < kD; ++i) { x[i] = __fmaf_rn(e, w[i], x[i]); gl[i] = glp[i]; }
                 ell = ellp;
                 ++acc;
             }
@@ -415,8 +464,10 @@ oais_sweep_tc_kernel(const TcParams P)
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if (lane == 0) s_acc[slot][G.warp] = acc;
         group_sync(G.g);
-        group_record(G, s_m[slot], s_s[slot], s_acc[slot],
-                     S.partials + (size_t)(t - 1) * (gridDim.x * kGroups) + tile);
+        // the group's 4 warps merge their moment pieces and acceptance counts (fixed order)
+        if (G.warp == 0)
+            merge_warp_pieces<4, true>(lane, s_m[slot], s_s[slot], s_acc[slot],
+                                 S.partials + (size_t)(t - 1) * (gridDim.x * kGroups) + tile);
     }
     if (active) {
         S.logw[n64] = logw;
@@ -434,7 +485,7 @@ oais_sweep_tc_kernel(const TcParams P)
 
 } // namespace tc
 
-int tc_grid(int64_t N) { return (int)((N + tc::kThreads - 1) / tc::kThreads); }
+int tc_grid(int64_t N) { return (int)((N + tc::kParticlesPerCta - 1) / tc::kParticlesPerCta); }
 int tc_records(int64_t N) { return tc_grid(N) * tc::kGroups; }
 
 // BF16 image of X in the kernel's shared-memory layout (rows of 64 B, 64B swizzle) and the

@@ -385,34 +385,6 @@ struct Thread {
     }
 };
 
-// the tile's four particle warps of half 0 merge their (m, s) moment pieces and acceptance
-// counts in a fixed order (one record per step and tile)
-__device__ __forceinline__ void tile_record(int lane, const double (*wm)[3], const float (*ws)[3],
-                                            const unsigned* wacc, StepPartial* out)
-{
-    StepPartial rec;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const double m = lane < 4 ? wm[lane][i] : -INFINITY;
-        double Mx = m;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) Mx = fmax(Mx, __shfl_xor_sync(0xFFFFFFFFu, Mx, o));
-        double v = (lane < 4 && m != -INFINITY) ? (double)ws[lane][i] * exp(m - Mx) : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        rec.m[i] = Mx;
-        rec.s[i] = v;
-    }
-    unsigned a = lane < 4 ? wacc[lane] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-    if (lane == 0) {
-        rec.accepted = a;
-        rec.pad = 0;
-        *out = rec;
-    }
-}
-
 __device__ __forceinline__ void mbar_inval(uint32_t bar)
 {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
@@ -773,7 +745,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
             const double lg = (beta_t - beta_prev) * ell;
             beta_prev = beta_t;
             const int slot = t & 1;
-            if (h == 0) warp_moment_partial(logw, lg, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
+            if (h == 0) warp_moment_partial<true>(logw, lg, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
             logw += lg;
             unsigned acc = 0;
             const float beta = (float)beta_t, eps = (float)eps_t, he = 0.5f * eps;
@@ -868,17 +840,17 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                 if (lane == 0) M->s_acc[slot][Th.q] = acc;
                 named_sync(2, 128);
                 if (warp == 0)
-                    tile_record(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot],
-                                S.partials + (size_t)(t - 1) * tiles + tile);
+                    merge_warp_pieces<4, true>(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot],
+                                         S.partials + (size_t)(t - 1) * tiles + tile);
             }
         }
         if (P.ess_parts && h == 0) {
             // (log w, 2 log w) moments of the tile for the ESS of the resampling test
             const int slot = (P.t_end + 1) & 1;
-            warp_moment_partial(logw, logw, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
+            warp_moment_partial<true>(logw, logw, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
             if (lane == 0) M->s_acc[slot][Th.q] = 0u;
             named_sync(2, 128);
-            if (warp == 0) tile_record(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot], P.ess_parts + tile);
+            if (warp == 0) merge_warp_pieces<4, true>(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot], P.ess_parts + tile);
         }
         if (active) {
             if (P.t_end == S.T) {

@@ -87,6 +87,24 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                  ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
 }
+// the same, issued by the lanes with `leader` != 0 only: lets a whole warp run the issue loop
+// (warp-uniform control flow and descriptor arithmetic) while one lane issues
+__device__ __forceinline__ void mma_f16_by(uint32_t leader, uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p, l;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "setp.ne.b32 l, %5, 0;\n\t"
+                 "@l tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(leader) : "memory");
+}
+__device__ __forceinline__ void mma_commit_by(uint32_t leader, uint32_t bar)
+{
+    asm volatile("{\n\t.reg .pred l;\n\t"
+                 "setp.ne.b32 l, %1, 0;\n\t"
+                 "@l tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+                 ::"r"(bar), "r"(leader) : "memory");
+}
 // D (TMEM) (+)= A (TMEM) * B (smem): A is M lanes x K 16-bit elements, two per 32-bit column
 // (the lower K index in the low half)
 __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
