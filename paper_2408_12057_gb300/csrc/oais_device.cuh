@@ -52,6 +52,24 @@ __device__ __forceinline__ void box_muller4(const Philox4& b, float z[4])
     sincospif(2.0f * u01f(b.v[3]), &s1, &c1);
     z[0] = r0 * c0; z[1] = r0 * s0; z[2] = r1 * c1; z[3] = r1 * s1;
 }
+// the same four normals with the special-function-unit forms of log2, sqrt, sin and cos
+// (documented PTX approximations, absolute error of order 1e-6 in z): the tensor-core kernels,
+// whose particle arithmetic is fp32.  The angle 2 pi u is taken as pi (2u - 1) + pi so that
+// the sine and cosine arguments lie in (-pi, pi).
+__device__ __forceinline__ float sfu_lg2(float x) { float y; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_sqrt(float x) { float y; asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_sin(float x) { float y; asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_cos(float x) { float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ void box_muller4_sfu(const Philox4& b, float z[4])
+{
+    const float m2ln2 = -1.3862943611198906f;                  // -2 ln 2
+    const float pi = 3.14159265358979f;
+    const float r0 = sfu_sqrt(m2ln2 * sfu_lg2(u01f(b.v[0])));
+    const float r1 = sfu_sqrt(m2ln2 * sfu_lg2(u01f(b.v[2])));
+    const float a0 = pi * (2.0f * u01f(b.v[1]) - 1.0f), a1 = pi * (2.0f * u01f(b.v[3]) - 1.0f);
+    // cos(a + pi) = -cos a, sin(a + pi) = -sin a
+    z[0] = -r0 * sfu_cos(a0); z[1] = -r0 * sfu_sin(a0); z[2] = -r1 * sfu_cos(a1); z[3] = -r1 * sfu_sin(a1);
+}
 __device__ __forceinline__ void box_muller4(const Philox4& b, double z[4])
 {
     double s0, c0, s1, c1;
@@ -73,6 +91,19 @@ __device__ __forceinline__ void normals(const Rng& rng, uint32_t n, uint32_t t, 
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (4 * j + q < D) z[4 * j + q] = (4 * j + q < d) ? v[q] : R(0);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void normals_sfu(const Rng& rng, uint32_t n, uint32_t t, uint32_t k, int d, float (&z)[D])
+{
+#pragma unroll
+    for (int j = 0; j < (D + 3) / 4; ++j) {
+        float v[4];
+        if (4 * j < d) box_muller4_sfu(rng.block(n, t, k, (uint32_t)j), v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (4 * j + q < D) z[4 * j + q] = (4 * j + q < d) ? v[q] : 0.0f;
     }
 }
 
@@ -148,16 +179,17 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
 // instead of an fp64 exponential per moment: the tensor-core kernels use it, the fp64 pipe
 // being slow on this part.  Lanes < W take part (every lane of the warp calls it); W is a
 // power of two <= 32.
-// kFast = false keeps the rescaling and the sum in fp64 (the CUDA-core forms).
+// kFast = false keeps the rescaling and the sum in fp64 (the CUDA-core forms).  Lane j < W
+// passes piece j's shifts m[3], sums s[3] and count acc; lane 0 writes the record.
 template <int W, bool kFast>
-__device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3], const float (*ws)[3],
-                                                  const unsigned* wacc, StepPartial* out)
+__device__ __forceinline__ void merge_lane_pieces(int lane, const double (&mj)[3], const float (&sj)[3],
+                                                  unsigned accj, StepPartial* out)
 {
     static_assert(W >= 1 && W <= 32 && (W & (W - 1)) == 0, "W: a power of two");
     StepPartial rec;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const double m = lane < W ? wm[lane][i] : -INFINITY;
+        const double m = lane < W ? mj[i] : -INFINITY;
         double M = m;
         if (kFast) {
 #pragma unroll
@@ -168,19 +200,19 @@ __device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3
         }
         if (kFast) {
             const float dj = (float)(m - M);      // -inf for an empty piece; NaN when every piece is
-            float v = (lane < W && !isnan(dj)) ? ws[lane][i] * expf(dj) : 0.0f;
+            float v = (lane < W && !isnan(dj)) ? sj[i] * expf(dj) : 0.0f;
 #pragma unroll
             for (int o = 1; o < W; o <<= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
             rec.s[i] = (double)v;
         } else {
-            double v = (lane < W && m != -INFINITY) ? (double)ws[lane][i] * exp(m - M) : 0.0;
+            double v = (lane < W && m != -INFINITY) ? (double)sj[i] * exp(m - M) : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
             rec.s[i] = v;
         }
         rec.m[i] = M;
     }
-    unsigned a = (wacc && lane < W) ? wacc[lane] : 0u;
+    unsigned a = lane < W ? accj : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
     if (lane == 0) {
@@ -188,6 +220,19 @@ __device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3
         rec.pad = 0;
         *out = rec;
     }
+}
+template <int W, bool kFast>
+__device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3], const float (*ws)[3],
+                                                  const unsigned* wacc, StepPartial* out)
+{
+    double m[3];
+    float sv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        m[i] = lane < W ? wm[lane][i] : -INFINITY;
+        sv[i] = lane < W ? ws[lane][i] : 0.0f;
+    }
+    merge_lane_pieces<W, kFast>(lane, m, sv, (wacc && lane < W) ? wacc[lane] : 0u, out);
 }
 
 // CTA part: warp 0 merges the W warps' pieces and writes one record.  Call after a

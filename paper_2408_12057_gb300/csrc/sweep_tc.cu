@@ -56,7 +56,7 @@ constexpr int kOffBar = kOffY + kMaxRows / 8;                // + 256 B
 constexpr int kOffTmem = kOffBar + 8 * kBarsPerGroup * kGroups;
 constexpr int kOffAbort = kOffTmem + 4;
 constexpr int kOffStat = kOffTmem + 16;
-constexpr int kStatBytes = 2 * 4 * 3 * 8 + 2 * 4 * 3 * 4 + 2 * 4 * 4;   // [slot][warp] m, s, acc
+constexpr int kStatBytes = 2 * 4 * 40;       // [slot][warp] WarpPiece
 constexpr int kSmemBytes = kOffStat + kGroups * kStatBytes;
 constexpr int kTmemCols = 512;               // group g: D1[0], D1[1] at 256 g + {0, 64}, D2 at 256 g + 128
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
@@ -115,6 +115,64 @@ __device__ __forceinline__ GroupAddr group_addr(unsigned char* smem, uint32_t tm
     A.smem = saddr(smem);
     A.g = g;
     return A;
+}
+
+// One warp's share of a step's moment record (Alg. 1 moments, Sec. 5.1.1): the anchor (the
+// first active particle's log w and log g), per moment i the maximum fp32 offset
+// (log w - a0) + i (log g - b0) over the warp and the sum of exp(offset - maximum), and the
+// warp's acceptance count.  The shift m_i = a0 + i b0 + mx_i is formed in fp64 by the merge.
+struct WarpPiece {
+    double a0;               // -inf: no active particle in the warp
+    float b0, mx[3], s[3];
+    unsigned acc;
+};
+static_assert(sizeof(WarpPiece) == 40, "WarpPiece layout");
+
+__device__ __forceinline__ void warp_piece(double lw, float lg, bool active, WarpPiece* out)
+{
+    const unsigned full = 0xFFFFFFFFu;
+    const unsigned act = __ballot_sync(full, active);
+    const bool lead = (threadIdx.x & 31) == 0;
+    if (act == 0) {
+        if (lead) {
+            out->a0 = -INFINITY;
+            out->b0 = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { out->mx[i] = 0.0f; out->s[i] = 0.0f; }
+        }
+        return;
+    }
+    const int src = __ffs(act) - 1;
+    const double a0 = __shfl_sync(full, lw, src);
+    const float b0 = __shfl_sync(full, lg, src);
+    const float dw = (float)(lw - a0), dg = lg - b0;
+    if (lead) { out->a0 = a0; out->b0 = b0; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float f = active ? dw + (float)i * dg : -INFINITY;
+        float mx = f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
+        float e = active ? __expf(f - mx) : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
+        if (lead) { out->mx[i] = mx; out->s[i] = e; }
+    }
+}
+
+// the group's 4 pieces of a step into one record (every lane of the calling warp takes part)
+__device__ __forceinline__ void merge_pieces(int lane, const WarpPiece* pc, StepPartial* out)
+{
+    const WarpPiece& q = pc[lane & 3];         // lanes >= 4 read a valid piece and ignore it
+    double m[3];
+    float sv[3];
+    const bool has = lane < 4 && q.a0 != -INFINITY;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        m[i] = has ? q.a0 + i * (double)q.b0 + (double)q.mx[i] : -INFINITY;
+        sv[i] = has ? q.s[i] : 0.0f;
+    }
+    merge_lane_pieces<4, true>(lane, m, sv, lane < 4 ? q.acc : 0u, out);
 }
 
 struct Group {
@@ -200,13 +258,16 @@ __device__ __forceinline__ void wait_bwd(Group& G)
 
 // Group g's MMA warp (lane 0 issues): per evaluation it waits for the A tile and issues the
 // forwards of chunks 0 and 1, then per chunk c waits for the R tile and issues the backward
-// of chunk c and the forward of chunk c + 2 into the D1 buffer just read.  A wait that times
+// of chunk c and the forward of chunk c + 2 into the D1 buffer just read.  It also merges the
+// moment record of each finished step but the last.  A wait that times
 // out (or another role's) sets the abort flag and ends the loop; before returning the warp
 // waits for every MMA it issued, so tensor memory is never released under a running
 // contraction.
-__device__ void mma_issuer(unsigned char* smem, uint32_t tmem, int g, int nch, int evals, volatile int* abort)
+__device__ void mma_issuer(unsigned char* smem, uint32_t tmem, int g, int nch, int K, int evals,
+                           volatile int* abort, StepPartial* records, int64_t record_stride)
 {
     const GroupAddr A = group_addr(smem, tmem, g);
+    const WarpPiece (*pieces)[4] = reinterpret_cast<const WarpPiece (*)[4]>(smem + kOffStat + g * kStatBytes);
     const uint32_t leader = (threadIdx.x & 31) == 0;
     uint32_t phA = 0, phR = 0;
     bool ok = true;
@@ -217,6 +278,13 @@ __device__ void mma_issuer(unsigned char* smem, uint32_t tmem, int g, int nch, i
         tc_after_sync();
         issue_fwd(A, 0, 0, leader);
         if (nch > 1) issue_fwd(A, 1, 1, leader);
+        // the first evaluation of step t + 1 begins once every piece of step t is written:
+        // merge step t's record here, off the particle warps' path (step t's slot is next
+        // written by the pieces of step t + 2, after this evaluation's contractions)
+        if (K > 0 && e > K && (e - 1) % K == 0) {
+            const int t = (e - 1) / K;
+            merge_pieces(threadIdx.x & 31, pieces[t & 1], records + (int64_t)(t - 1) * record_stride);
+        }
         for (int c = 0; c < nch; ++c) {
             ok = mbar_wait(A.barR, phR, abort);
             phR ^= 1u;
@@ -363,7 +431,9 @@ oais_sweep_tc_kernel(const TcParams P)
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + kOffTmem);
 
     if (threadIdx.x / 32 >= kMmaWarp0) {
-        mma_issuer(smem, tmem, threadIdx.x / 32 - kMmaWarp0, (P.n + kChunk - 1) / kChunk, 1 + S.T * S.mv.K, abort);
+        const int g = threadIdx.x / 32 - kMmaWarp0;
+        mma_issuer(smem, tmem, g, (P.n + kChunk - 1) / kChunk, S.mv.K, 1 + S.T * S.mv.K, abort,
+                   S.partials + (int64_t)blockIdx.x * kGroups + g, (int64_t)gridDim.x * kGroups);
         if (threadIdx.x % 32 == 0 && *abort) atomicOr(S.status, 2u);
         tc_before_sync();
         __syncthreads();
@@ -381,10 +451,7 @@ oais_sweep_tc_kernel(const TcParams P)
     G.dead = false;
     G.abort = abort;
     G.smem = smem;
-    unsigned char* st = smem + kOffStat + G.g * kStatBytes;
-    double (*s_m)[4][3] = reinterpret_cast<double (*)[4][3]>(st);
-    float (*s_s)[4][3] = reinterpret_cast<float (*)[4][3]>(st + 2 * 4 * 3 * 8);
-    unsigned (*s_acc)[4] = reinterpret_cast<unsigned (*)[4]>(st + 2 * 4 * 3 * 8 + 2 * 4 * 3 * 4);
+    WarpPiece (*pieces)[4] = reinterpret_cast<WarpPiece (*)[4]>(smem + kOffStat + G.g * kStatBytes);
 
     const int64_t tile = (int64_t)blockIdx.x * kGroups + G.g;
     const int64_t n64 = tile * kGroupThreads + G.tid;
@@ -396,7 +463,7 @@ oais_sweep_tc_kernel(const TcParams P)
     const int lane = G.tid & 31;
 
     float x[kD], gl[kD];
-    normals<kD>(S.mv.rng, n, 0u, 0u, d, x);
+    normals_sfu<kD>(S.mv.rng, n, 0u, 0u, d, x);
 #pragma unroll
     for (int i = 0; i < kD; ++i) x[i] *= sref;
     float ell = tc_eval(G, P, x, gl);
@@ -405,17 +472,18 @@ oais_sweep_tc_kernel(const TcParams P)
     for (int t = 1; t <= S.T; ++t) {
         const double beta_t = __ldg(S.beta + t);
         const double eps_t = __ldg(S.eps + t - 1);
-        const double lg = (beta_t - beta_prev) * (double)ell;
+        // log g_t = (beta_t - beta_{t-1}) log L(x) in fp32 (log L is an fp32 value); log w in fp64
+        const float lg = (float)(beta_t - beta_prev) * ell;
         beta_prev = beta_t;
         const int slot = t & 1;
-        warp_moment_partial<true>(logw, lg, active, s_m[slot][G.warp], s_s[slot][G.warp]);
-        logw += lg;
+        warp_piece(logw, lg, active, &pieces[slot][G.warp]);
+        logw += (double)lg;
         unsigned acc = 0;
         const float beta = (float)beta_t, e = (float)eps_t, h = 0.5f * e;
         for (int k = 0; k < S.mv.K; ++k) {
             // MALA (Sec. 2.1.1 kernel family): x' = x + e w with w = z + (e/2) grad log pi(x)
             float w[kD];
-            normals<kD>(S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, w);
+            normals_sfu<kD>(S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, w);
             float zz = 0.0f, dxx = 0.0f;
             const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
             {
@@ -462,13 +530,12 @@ oais_sweep_tc_kernel(const TcParams P)
         acc = active ? acc : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-        if (lane == 0) s_acc[slot][G.warp] = acc;
-        group_sync(G.g);
-        // the group's 4 warps merge their moment pieces and acceptance counts (fixed order)
-        if (G.warp == 0)
-            merge_warp_pieces<4, true>(lane, s_m[slot], s_s[slot], s_acc[slot],
-                                 S.partials + (size_t)(t - 1) * (gridDim.x * kGroups) + tile);
+        if (lane == 0) pieces[slot][G.warp].acc = acc;
     }
+    // the last step's record (the MMA warp merges the others)
+    group_sync(G.g);
+    if (S.T > 0 && G.warp == 0)
+        merge_pieces(lane, pieces[S.T & 1], S.partials + (size_t)(S.T - 1) * (gridDim.x * kGroups) + tile);
     if (active) {
         S.logw[n64] = logw;
         S.ell_out[n64] = (double)ell;
