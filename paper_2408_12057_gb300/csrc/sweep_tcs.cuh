@@ -142,12 +142,12 @@ struct Misc {
     uint32_t item;              // batched launch: the current item
 };
 
-// f16 two-term split of a pair: hi = f16(v), lo = f16(v - hi)
+// f16 two-term split of a pair: hi = f16(v), lo = f16(v - hi) (one packed subtraction)
 __device__ __forceinline__ void split_pair_h(float a, float b, uint32_t& hi, uint32_t& lo)
 {
     const __half2 h = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    const float2 d = sub_f32x2(make_float2(a, b), __half22float2(h));
+    const __half2 l = __floats2half2_rn(d.x, d.y);
     hi = *reinterpret_cast<const uint32_t*>(&h);
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
@@ -159,7 +159,7 @@ __device__ __forceinline__ void normals8(const Rng& rng, uint32_t n, uint32_t t,
     for (int b = 0; b < 2; ++b) {
         const int j = i0 / 4 + b;
         float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (4 * j < d) box_muller4(rng.block(n, t, k, (uint32_t)j), v);
+        if (4 * j < d) box_muller4_sfu(rng.block(n, t, k, (uint32_t)j), v);
 #pragma unroll
         for (int q = 0; q < 4; ++q) z[4 * b + q] = (4 * j + q < d) ? v[q] : 0.0f;
     }
@@ -196,14 +196,16 @@ struct Thread {
         return false;
     }
 
-    // one 8-coordinate slice of the tile's positions into the A operand (both terms)
-    __device__ void write_a(int i0, const float (&v)[kSlice])
+    // one 8-coordinate slice of the tile's positions, times `scale`, into the A operand (both
+    // terms); the logistic family passes log2(e), so that the forward gives the margins in
+    // base-2 units
+    __device__ void write_a(int i0, const float (&v)[kSlice], float scale)
     {
         constexpr KLayout L = klayout(DP);
         const uint32_t off = kmaj_off(p, i0, kTile, L);
         uint32_t hi[4], lo[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) split_pair_h(v[2 * j], v[2 * j + 1], hi[j], lo[j]);
+        for (int j = 0; j < 4; ++j) split_pair_h(scale * v[2 * j], scale * v[2 * j + 1], hi[j], lo[j]);
         *reinterpret_cast<uint4*>(smem + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         tmem_st4(tmem + (uint32_t)(Cols<DP>::ALO + i0 / 2) + lane_off, lo);
     }
@@ -305,24 +307,26 @@ struct Thread {
                     }
                 }
             } else {
-                // X'_r = s_r X~_r with s_r = 2 y_r - 1, so u = s z; log sigmoid(u) =
-                // min(u, 0) + log q with q = 1 / (1 + e^-|u|), d/dz = s sigmoid(-u)
-                float prod = 1.0f;
+                // X'_r = s_r X~_r with s_r = 2 y_r - 1 and the A operand log2(e) x, so u is the
+                // margin s z in base-2 units: log sigmoid(s z) = ln 2 (min(u, 0) + log2 q) with
+                // q = 1 / (1 + 2^-|u|), d/dz = s sigmoid(-s z) = s (u >= 0 ? 2^-|u| q : q).  The rows
+                // of a pair go through the packed fp32 pair instructions; the product of q is kept
+                // per lane of the pair (HC / 2 <= 16 values in [1/2, 1] each), one log per chunk.
+                const float2 one2 = make_float2(1.0f, 1.0f);
+                float2 prod = one2, mn = make_float2(0.0f, 0.0f);
 #pragma unroll
                 for (int j = 0; j < HC; j += 2) {
-                    float r2[2];
-#pragma unroll
-                    for (int w = 0; w < 2; ++w) {
-                        const float u = __uint_as_float(v[j + w]);
-                        const float ee = ex2_approx(fabsf(u) * -1.4426950408889634f);
-                        const float qi = rcp_approx(1.0f + ee);
-                        r2[w] = u >= 0.0f ? ee * qi : qi;
-                        part0 += u - fabsf(u);
-                        prod *= qi;
-                    }
-                    if ((j & 15) == 14) { part1 += lg2_approx(prod); prod = 1.0f; }
-                    split_pair_h(r2[0], r2[1], hi[j / 2], lo[j / 2]);
+                    const float ua = __uint_as_float(v[j]), ub = __uint_as_float(v[j + 1]);
+                    const float2 ee = make_float2(ex2_approx(-fabsf(ua)), ex2_approx(-fabsf(ub)));
+                    const float2 dq = add_f32x2(ee, one2);
+                    const float2 q = make_float2(rcp_approx(dq.x), rcp_approx(dq.y));
+                    const float2 eq = mul_f32x2(ee, q);
+                    mn = add_f32x2(mn, make_float2(fminf(ua, 0.0f), fminf(ub, 0.0f)));
+                    prod = mul_f32x2(prod, q);
+                    split_pair_h(ua >= 0.0f ? eq.x : q.x, ub >= 0.0f ? eq.y : q.y, hi[j / 2], lo[j / 2]);
                 }
+                part0 = mn.x + mn.y;
+                part1 = lg2_approx(prod.x * prod.y);
             }
             if (++xs == P->stages) { xs = 0; xph ^= 1u; }
             // R (two f16 terms) into TMEM, the A operand of the backward
@@ -358,7 +362,7 @@ struct Thread {
         ++e;
         double part;
         if constexpr (FAM == kLinreg) part = -P->half_inv_var * acc0;
-        else part = 0.5 * acc0 + 0.69314718055994531 * acc1;
+        else part = 0.69314718055994531 * ((double)acc0 + (double)acc1);
         M->xl[h][p] = part;
         named_sync(1, kEpi);
         double tot = M->xl[0][p];
@@ -457,6 +461,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                                          uint32_t tmem)
 {
     constexpr int CHUNK = chunk_rows(DP);
+    constexpr float kAScale = FAM == kLogreg ? 1.4426950408889634f : 1.0f;   // A operand scale
     const SweepParams& S = P.sp;
     Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -697,7 +702,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
 #pragma unroll
                 for (int j = 0; j < kSlice; ++j)
                     xv[j] = i0 + j < P.d ? P.x_in[(int64_t)(i0 + j) * P.pstride + src] : 0.0f;
-                Th.write_a(i0, xv);
+                Th.write_a(i0, xv, kAScale);
             }
             const double ellv = Th.template eval<FAM, Q8>();
             for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
@@ -722,7 +727,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                     z[j] *= sref;
                     XA[(int64_t)(i0 + j) * Np] = z[j];
                 }
-                Th.write_a(i0, z);
+                Th.write_a(i0, z, kAScale);
             }
             ell = Th.template eval<FAM, Q8>();
             for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
@@ -768,7 +773,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                         XP[o] = xpv[j];
                         MO[o] = m;
                     }
-                    Th.write_a(i0, xpv);
+                    Th.write_a(i0, xpv, kAScale);
                 }
                 double ellp = 0.0;
                 float tail = 0.0f;   // MALA: |reverse noise|^2; HMC: |final momentum|^2
@@ -797,7 +802,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                                     xpv[j] = xq;
                                 }
                             }
-                            if (!last) Th.write_a(i0, xpv);
+                            if (!last) Th.write_a(i0, xpv, kAScale);
                         }
                     } else {
                         for (int i0 = c0; i0 < c0 + dh; i0 += kSlice) {
