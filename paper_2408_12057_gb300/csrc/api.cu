@@ -194,7 +194,7 @@ static size_t elt_bytes(int kind) { return kind == kGauss ? sizeof(double) : siz
 struct Layout {
     size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, lse, lse_scr, status;
     size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, tc_img, tc_y;
-    size_t tcs_img, tcs_state, total;
+    size_t tcs_img, tcs_state, tc_handed, total;
 };
 
 // which sweep form a target runs: 0 CUDA cores, 1 resident tensor-core, 2 streamed tensor-core
@@ -247,6 +247,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     const int form = sweep_form(tg, mv);
     L.tc_img = take(form == 1 ? (size_t)tc_image_bytes() : 0);
     L.tc_y = take(form == 1 ? (size_t)tc_max_rows() / 8 : 0);
+    L.tc_handed = take(form == 1 ? sizeof(int) * (size_t)tc_records(N) : 0);
     TcsPlan tp;
     if (form == 2) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
     L.tcs_img = take(form == 2 ? tp.img_bytes : 0);
@@ -469,6 +470,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
             dt.tc = true;
             dt.tc_img = b + L.tc_img;
             dt.tc_ybits = reinterpret_cast<uint32_t*>(b + L.tc_y);
+            dt.tc_handed = reinterpret_cast<int*>(b + L.tc_handed);
             e = cudaMemcpy(dt.tc_img, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
                 e = cudaMemcpy(dt.tc_ybits, yb.data(), yb.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -639,7 +641,9 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         SweepParams P = make_params(ctx, T, ctx->d_beta, ctx->d_eps, ctx->seed, tag, ctx->n_offset, ctx->N,
                                     ctx->d_logw, ctx->d_ell, ctx->d_x, ctx->d_parts, ctx->d_status);
         CK(cudaEventRecord(ctx->ev0, s));
-        if (ctx->dt.tc) CK(launch_sweep_tc(P, ctx->dt.tc_img, ctx->dt.tc_ybits, ctx->dt.n, ctx->dt.d, s));
+        // the resident form hands a split tile's gradient over in the ASMC gradient buffer
+        if (ctx->dt.tc) CK(launch_sweep_tc(P, ctx->dt.tc_img, ctx->dt.tc_ybits, ctx->dt.n, ctx->dt.d,
+                                           static_cast<float*>(ctx->d_g0), ctx->dt.tc_handed, s));
         else if (ctx->dt.tcs)
             CK(launch_sweep_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0, ctx->dt.tcs_q8), ctx->dt.kind, P, ctx->dt.tcs_img,
                                 ctx->dt.tcs_state, ctx->mv.kind, ctx->mv.leapfrog, ctx->dt.p0, ctx->dt.n,

@@ -20,6 +20,7 @@ struct DevTarget {
     bool tc = false;     // tensor-core form: BF16 image of X and label bits below
     void* tc_img = nullptr;
     uint32_t* tc_ybits = nullptr;
+    int* tc_handed = nullptr;    // [tiles] hand-off flags of the persistent schedule
     bool tcs = false;    // streamed tensor-core form: chunk images of X~ (and y), particle state
     void* tcs_img = nullptr;
     float* tcs_state = nullptr;
@@ -81,7 +82,7 @@ cudaError_t launch_potential_tcs(const TcsPlan& L, int kind, const void* img, co
 int tc_grid(int64_t N);
 int tc_records(int64_t N);
 cudaError_t launch_sweep_tc(const SweepParams& sp, const void* Ximg, const uint32_t* ybits, int n, int d,
-                            cudaStream_t s);
+                            float* grad_state, int* handed, cudaStream_t s);
 
 // smallest compiled width >= d for the family, 0 if none
 int padded_width(int kind, int d);

@@ -27,6 +27,7 @@
 //   y bits   2048 labels as a bitmask                                256 B
 //   6 mbarriers per group, the TMEM base address, the abort flag, per-group moment scratch
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -57,7 +58,8 @@ constexpr int kOffTmem = kOffBar + 8 * kBarsPerGroup * kGroups;
 constexpr int kOffAbort = kOffTmem + 4;
 constexpr int kOffStat = kOffTmem + 16;
 constexpr int kStatBytes = 2 * 4 * 40;       // [slot][warp] WarpPiece
-constexpr int kSmemBytes = kOffStat + kGroups * kStatBytes;
+constexpr int kOffDesc = kOffStat + kGroups * kStatBytes;  // [group] EvalDesc
+constexpr int kSmemBytes = kOffDesc + kGroups * 16;
 constexpr int kTmemCols = 512;               // group g: D1[0], D1[1] at 256 g + {0, 64}, D2 at 256 g + 128
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
@@ -87,6 +89,10 @@ struct TcParams {
     const uint32_t* ybits;   // [kMaxRows / 32]
     int n;                   // data rows
     int d;                   // true dimension (<= 32; padded columns of X are zero)
+    int tiles;               // tiles of 128 particles (moment records per step)
+    int64_t span;            // annealing steps per slot (group) of the persistent grid
+    float* grad_state;       // [d][N]: grad log L of a tile handed between two slots
+    int* handed;             // [tiles]: 1 once a tile's first part has stored its state
 };
 
 // the shared-memory and TMEM addresses of group g's barriers and accumulators
@@ -175,6 +181,16 @@ __device__ __forceinline__ void merge_pieces(int lane, const WarpPiece* pc, Step
     merge_lane_pieces<4, true>(lane, m, sv, lane < 4 ? q.acc : 0u, out);
 }
 
+// What the MMA warp does at the start of an evaluation (written by the group's thread 0
+// before it arrives on barA): stop, or issue the evaluation and, at the first evaluation of
+// step t + 1 of a piece, merge step t's record into rec.
+struct EvalDesc {
+    StepPartial* rec;        // null: no record to merge
+    int slot;                // pieces slot of that step (t & 1)
+    int stop;                // 1: no more evaluations
+};
+static_assert(sizeof(EvalDesc) <= 16, "EvalDesc fits its slot");
+
 struct Group {
     GroupAddr a;
     int g, tid, warp;
@@ -256,35 +272,33 @@ __device__ __forceinline__ void wait_bwd(Group& G)
     G.phB ^= 1u;
 }
 
-// Group g's MMA warp (lane 0 issues): per evaluation it waits for the A tile and issues the
-// forwards of chunks 0 and 1, then per chunk c waits for the R tile and issues the backward
-// of chunk c and the forward of chunk c + 2 into the D1 buffer just read.  It also merges the
-// moment record of each finished step but the last.  A wait that times
-// out (or another role's) sets the abort flag and ends the loop; before returning the warp
-// waits for every MMA it issued, so tensor memory is never released under a running
+// Group g's MMA warp (lane 0 issues): per evaluation it waits for the A tile, reads the
+// evaluation's descriptor and issues the forwards of chunks 0 and 1, then per chunk c waits
+// for the R tile and issues the backward of chunk c and the forward of chunk c + 2 into the D1
+// buffer just read.  Between the forwards and the first backward it merges the moment record
+// the descriptor names (a finished step's; off the particle warps' path: that step's pieces
+// slot is next written two steps later, after this evaluation's contractions).  A wait that
+// times out (or another role's) sets the abort flag and ends the loop; before returning the
+// warp waits for every MMA it issued, so tensor memory is never released under a running
 // contraction.
-__device__ void mma_issuer(unsigned char* smem, uint32_t tmem, int g, int nch, int K, int evals,
-                           volatile int* abort, StepPartial* records, int64_t record_stride)
+__device__ void mma_issuer(unsigned char* smem, uint32_t tmem, int g, int nch, volatile int* abort)
 {
     const GroupAddr A = group_addr(smem, tmem, g);
     const WarpPiece (*pieces)[4] = reinterpret_cast<const WarpPiece (*)[4]>(smem + kOffStat + g * kStatBytes);
+    const volatile EvalDesc* desc = reinterpret_cast<const volatile EvalDesc*>(smem + kOffDesc + 16 * g);
     const uint32_t leader = (threadIdx.x & 31) == 0;
     uint32_t phA = 0, phR = 0;
     bool ok = true;
-    for (int e = 0; e < evals && ok; ++e) {
+    for (;;) {
         ok = mbar_wait(A.barA, phA, abort);
         phA ^= 1u;
-        if (!ok) break;
+        if (!ok || desc->stop) break;
+        StepPartial* rec = desc->rec;
+        const int slot = desc->slot;
         tc_after_sync();
         issue_fwd(A, 0, 0, leader);
         if (nch > 1) issue_fwd(A, 1, 1, leader);
-        // the first evaluation of step t + 1 begins once every piece of step t is written:
-        // merge step t's record here, off the particle warps' path (step t's slot is next
-        // written by the pieces of step t + 2, after this evaluation's contractions)
-        if (K > 0 && e > K && (e - 1) % K == 0) {
-            const int t = (e - 1) / K;
-            merge_pieces(threadIdx.x & 31, pieces[t & 1], records + (int64_t)(t - 1) * record_stride);
-        }
+        if (rec) merge_pieces(threadIdx.x & 31, pieces[slot], rec);
         for (int c = 0; c < nch; ++c) {
             ok = mbar_wait(A.barR, phR, abort);
             phR ^= 1u;
@@ -293,6 +307,7 @@ __device__ void mma_issuer(unsigned char* smem, uint32_t tmem, int g, int nch, i
             issue_bwd(A, c, c == 0, leader);
             if (c + 2 < nch) issue_fwd(A, c + 2, c & 1, leader);
         }
+        if (!ok) break;
     }
     if (!ok) *abort = 1;
     mma_commit_by(leader, A.barEnd);
@@ -350,10 +365,14 @@ __device__ float tc_eval_run(Group& G, const TcParams& P, float (&grad)[kD])
                 const float2 e = make_float2(ex2_approx(-fabsf(ua)), ex2_approx(-fabsf(ub)));
                 const float2 dq = add_f32x2(e, one2);
                 const float2 q = make_float2(rcp_approx(dq.x), rcp_approx(dq.y));
-                const float2 eq = mul_f32x2(e, q);
-                mn = add_f32x2(mn, make_float2(fminf(ua, 0.0f), fminf(ub, 0.0f)));
+                // with h = [u >= 0] and 1 - h (each 0 or 1, so the products below are exact):
+                // sigmoid(-u) = q (h 2^-|u| + (1 - h)), min(u, 0) = u (1 - h)
+                const float2 hge = make_float2(step_ge0(ua), step_ge0(ub));
+                const float2 omh = sub_f32x2(one2, hge);
+                const float2 r = mul_f32x2(q, fma_f32x2(hge, e, omh));
+                mn = fma_f32x2(make_float2(ua, ub), omh, mn);
                 prod = mul_f32x2(prod, q);
-                split_pair(ua >= 0.0f ? eq.x : q.x, ub >= 0.0f ? eq.y : q.y, hi[j / 2], lo[j / 2]);
+                split_pair(r.x, r.y, hi[j / 2], lo[j / 2]);
             }
             if (s == 0 && c > 0) wait_bwd(G);     // the backward of chunk c-1 has read R
 #pragma unroll
@@ -431,9 +450,7 @@ oais_sweep_tc_kernel(const TcParams P)
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + kOffTmem);
 
     if (threadIdx.x / 32 >= kMmaWarp0) {
-        const int g = threadIdx.x / 32 - kMmaWarp0;
-        mma_issuer(smem, tmem, g, (P.n + kChunk - 1) / kChunk, S.mv.K, 1 + S.T * S.mv.K, abort,
-                   S.partials + (int64_t)blockIdx.x * kGroups + g, (int64_t)gridDim.x * kGroups);
+        mma_issuer(smem, tmem, threadIdx.x / 32 - kMmaWarp0, (P.n + kChunk - 1) / kChunk, abort);
         if (threadIdx.x % 32 == 0 && *abort) atomicOr(S.status, 2u);
         tc_before_sync();
         __syncthreads();
@@ -453,97 +470,173 @@ oais_sweep_tc_kernel(const TcParams P)
     G.smem = smem;
     WarpPiece (*pieces)[4] = reinterpret_cast<WarpPiece (*)[4]>(smem + kOffStat + G.g * kStatBytes);
 
-    const int64_t tile = (int64_t)blockIdx.x * kGroups + G.g;
-    const int64_t n64 = tile * kGroupThreads + G.tid;
-    const bool active = n64 < S.N;
-    const uint32_t n = (uint32_t)(S.n_offset + (active ? n64 : S.N - 1));
+    volatile EvalDesc* desc = reinterpret_cast<volatile EvalDesc*>(smem + kOffDesc + 16 * G.g);
     const int d = P.d;
     const float sref = (float)S.ref_scale;
     const float inv_s2 = 1.0f / (sref * sref);
     const int lane = G.tid & 31;
+    const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
+    // thread 0 says what the MMA warp does at the next evaluation, before the group's barA
+    auto announce = [&](StepPartial* rec, int slot) {
+        if (G.tid == 0) {
+            desc->rec = rec;
+            desc->slot = slot;
+            desc->stop = 0;
+        }
+    };
 
-    float x[kD], gl[kD];
-    normals_sfu<kD>(S.mv.rng, n, 0u, 0u, d, x);
+    // Persistent grid, wrap-around schedule (McNaughton's rule for preemptive scheduling of
+    // independent jobs): tile i is the job of T steps at positions [i T, (i + 1) T) of the
+    // concatenated sequence, slot s (group g of CTA b, s = 2 b + g) covers the positions
+    // [s L, (s + 1) L) with L = span >= T.  A tile split between slots s and s + 1 runs its
+    // first steps at the start of slot s + 1 and its last steps at the end of slot s, which
+    // cannot overlap in time because L >= T; the first part stores the tile's state and sets
+    // handed[tile], the last part waits for the flag (bounded) and loads the state.  So the
+    // slot's work is: the head (a split tile's first steps), whole tiles, the tail (a split
+    // tile's last steps).  With at most one tile per slot (L = T) this is one tile per group.
+    const int T = S.T;
+    const int64_t total = (int64_t)P.tiles * T;
+    const int64_t slot_id = (int64_t)blockIdx.x * kGroups + G.g;
+    const int64_t pos0 = slot_id * P.span, pos1 = min(pos0 + P.span, total);
+    float* xo = reinterpret_cast<float*>(S.x_out);
+    for (int64_t pos = pos0; pos < pos1 && T > 0;) {
+        // the piece at position pos: tile, first and last step
+        const int64_t tile = pos / T;
+        const int off = (int)(pos % T);
+        int t0, t1;
+        if (off != 0) {                       // head: the first T - off steps of a split tile
+            t0 = 1;
+            t1 = T - off;
+            pos = (tile + 1) * T;
+        } else if (pos + T <= pos1) {         // a whole tile
+            t0 = 1;
+            t1 = T;
+            pos += T;
+        } else {                              // tail: the last pos1 - pos steps of a split tile
+            t0 = T - (int)(pos1 - pos) + 1;
+            t1 = T;
+            pos = pos1;
+        }
+        const int64_t n64 = tile * kGroupThreads + G.tid;
+        const bool active = n64 < S.N;
+        const uint32_t n = (uint32_t)(S.n_offset + (active ? n64 : S.N - 1));
+        float x[kD], gl[kD], ell;
+        double logw;
+        if (t0 == 1) {
+            normals_sfu<kD>(S.mv.rng, n, 0u, 0u, d, x);
 #pragma unroll
-    for (int i = 0; i < kD; ++i) x[i] *= sref;
-    float ell = tc_eval(G, P, x, gl);
-    double logw = 0.0;
-    double beta_prev = S.beta[0];
-    for (int t = 1; t <= S.T; ++t) {
-        const double beta_t = __ldg(S.beta + t);
-        const double eps_t = __ldg(S.eps + t - 1);
-        // log g_t = (beta_t - beta_{t-1}) log L(x) in fp32 (log L is an fp32 value); log w in fp64
-        const float lg = (float)(beta_t - beta_prev) * ell;
-        beta_prev = beta_t;
-        const int slot = t & 1;
-        warp_piece(logw, lg, active, &pieces[slot][G.warp]);
-        logw += (double)lg;
-        unsigned acc = 0;
-        const float beta = (float)beta_t, e = (float)eps_t, h = 0.5f * e;
-        for (int k = 0; k < S.mv.K; ++k) {
-            // MALA (Sec. 2.1.1 kernel family): x' = x + e w with w = z + (e/2) grad log pi(x)
-            float w[kD];
-            normals_sfu<kD>(S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, w);
-            float zz = 0.0f, dxx = 0.0f;
-            const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
-            {
-                float xp[kD];
-#pragma unroll
-                for (int i = 0; i < kD; ++i) {
-                    const float gpi = -x[i] * inv_s2 + beta * gl[i];
-                    zz += w[i] * w[i];
-                    w[i] = __fmaf_rn(h, gpi, w[i]);
-                    xp[i] = __fmaf_rn(e, w[i], x[i]);
-                    dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
+            for (int i = 0; i < kD; ++i) x[i] *= sref;
+            announce(nullptr, 0);
+            ell = tc_eval(G, P, x, gl);
+            logw = 0.0;
+        } else {
+            // the tile's first part ran at the start of the next slot: wait for its state
+            if (G.tid == 0 && !G.dead) {
+                const uint64_t w0 = globaltimer();
+                while (ld_acquire_gpu(P.handed + tile) == 0) {
+                    if (*G.abort || globaltimer() - w0 > kWaitLimitNs) { G.dead = true; *G.abort = 1; break; }
+                    __nanosleep(256);
                 }
-                // park x, grad and w in the group's free TMEM columns while the evaluation
-                // runs (registers go to the epilogue), then bring them back; x' is rebuilt
-                // from them with the same rounding
-                tmem_st32(G.stash + lane_off, x);
-                tmem_st32(G.stash + lane_off + 32, gl);
-                tmem_st32(G.stash + lane_off + 64, w);
-                tmem_wait_st();
-                tc_eval_begin(G, xp);
             }
-            float glp[kD];
-            const float ellp = tc_eval_run(G, P, glp);
-            __syncwarp();
-            tmem_ld32f(G.stash + lane_off, x);
-            tmem_ld32f(G.stash + lane_off + 32, gl);
-            tmem_ld32f(G.stash + lane_off + 64, w);
-            float rev = 0.0f;
+            group_sync(G.g);
+            (void)ld_acquire_gpu(P.handed + tile);
 #pragma unroll
             for (int i = 0; i < kD; ++i) {
-                const float xp = __fmaf_rn(e, w[i], x[i]);
-                const float q = w[i] + h * (-xp * inv_s2 + beta * glp[i]);
-                rev += q * q;
+                x[i] = (active && i < d) ? xo[(size_t)i * S.N + n64] : 0.0f;
+                gl[i] = (active && i < d) ? P.grad_state[(size_t)i * S.N + n64] : 0.0f;
             }
-            const float log_alpha = -0.5f * dxx * inv_s2 + beta * (ellp - ell) - 0.5f * (rev - zz);
-            const float logu = mh_log_uniform(S.mv.rng, n, (uint32_t)t, (uint32_t)k, 0.0f);
-            if (logu < log_alpha) {
+            ell = active ? (float)S.ell_out[n64] : 0.0f;
+            logw = active ? S.logw[n64] : 0.0;
+        }
+        double beta_prev = S.beta[t0 - 1];
+        for (int t = t0; t <= t1; ++t) {
+            const double beta_t = __ldg(S.beta + t);
+            const double eps_t = __ldg(S.eps + t - 1);
+            // log g_t = (beta_t - beta_{t-1}) log L(x) in fp32 (log L is an fp32 value); log w in fp64
+            const float lg = (float)(beta_t - beta_prev) * ell;
+            beta_prev = beta_t;
+            const int slot = t & 1;
+            warp_piece(logw, lg, active, &pieces[slot][G.warp]);
+            logw += (double)lg;
+            unsigned acc = 0;
+            const float beta = (float)beta_t, e = (float)eps_t, h = 0.5f * e;
+            for (int k = 0; k < S.mv.K; ++k) {
+                // MALA (Sec. 2.1.1 kernel family): x' = x + e w with w = z + (e/2) grad log pi(x)
+                float w[kD];
+                normals_sfu<kD>(S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, w);
+                float zz = 0.0f, dxx = 0.0f;
+                {
+                    float xp[kD];
 #pragma unroll
-                for (int i = 0; i < kD; ++i) { x[i] = __fmaf_rn(e, w[i], x[i]); gl[i] = glp[i]; }
-                ell = ellp;
-                ++acc;
+                    for (int i = 0; i < kD; ++i) {
+                        const float gpi = -x[i] * inv_s2 + beta * gl[i];
+                        zz += w[i] * w[i];
+                        w[i] = __fmaf_rn(h, gpi, w[i]);
+                        xp[i] = __fmaf_rn(e, w[i], x[i]);
+                        dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
+                    }
+                    // park x, grad and w in the group's free TMEM columns while the evaluation
+                    // runs (registers go to the epilogue), then bring them back; x' is rebuilt
+                    // from them with the same rounding
+                    tmem_st32(G.stash + lane_off, x);
+                    tmem_st32(G.stash + lane_off + 32, gl);
+                    tmem_st32(G.stash + lane_off + 64, w);
+                    tmem_wait_st();
+                    // the first evaluation of step t: step t - 1's record is complete
+                    const bool merge = k == 0 && t > t0;
+                    announce(merge ? S.partials + (int64_t)(t - 2) * P.tiles + tile : nullptr, (t - 1) & 1);
+                    tc_eval_begin(G, xp);
+                }
+                float glp[kD];
+                const float ellp = tc_eval_run(G, P, glp);
+                __syncwarp();
+                tmem_ld32f(G.stash + lane_off, x);
+                tmem_ld32f(G.stash + lane_off + 32, gl);
+                tmem_ld32f(G.stash + lane_off + 64, w);
+                float rev = 0.0f;
+#pragma unroll
+                for (int i = 0; i < kD; ++i) {
+                    const float xp = __fmaf_rn(e, w[i], x[i]);
+                    const float q = w[i] + h * (-xp * inv_s2 + beta * glp[i]);
+                    rev += q * q;
+                }
+                const float log_alpha = -0.5f * dxx * inv_s2 + beta * (ellp - ell) - 0.5f * (rev - zz);
+                const float logu = mh_log_uniform(S.mv.rng, n, (uint32_t)t, (uint32_t)k, 0.0f);
+                if (logu < log_alpha) {
+#pragma unroll
+                    for (int i = 0; i < kD; ++i) { x[i] = __fmaf_rn(e, w[i], x[i]); gl[i] = glp[i]; }
+                    ell = ellp;
+                    ++acc;
+                }
+            }
+            acc = active ? acc : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+            if (lane == 0) pieces[slot][G.warp].acc = acc;
+        }
+        // the piece's last step's record (the MMA warp merged the others)
+        group_sync(G.g);
+        if (G.warp == 0) merge_pieces(lane, pieces[t1 & 1], S.partials + (int64_t)(t1 - 1) * P.tiles + tile);
+        if (active) {
+            S.logw[n64] = logw;
+            S.ell_out[n64] = (double)ell;
+#pragma unroll
+            for (int i = 0; i < kD; ++i) if (i < d) xo[(size_t)i * S.N + n64] = x[i];
+            if (t1 < T) {
+#pragma unroll
+                for (int i = 0; i < kD; ++i) if (i < d) P.grad_state[(size_t)i * S.N + n64] = gl[i];
+            } else if (!isfinite(logw) || !isfinite(ell)) {
+                atomicOr(S.status, 1u);
             }
         }
-        acc = active ? acc : 0u;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-        if (lane == 0) pieces[slot][G.warp].acc = acc;
+        if (t1 < T) __threadfence();
+        group_sync(G.g);                      // pieces slots free; the state is stored
+        if (t1 < T && G.tid == 0) st_release_gpu(P.handed + tile, 1);
     }
-    // the last step's record (the MMA warp merges the others)
-    group_sync(G.g);
-    if (S.T > 0 && G.warp == 0)
-        merge_pieces(lane, pieces[S.T & 1], S.partials + (size_t)(S.T - 1) * (gridDim.x * kGroups) + tile);
-    if (active) {
-        S.logw[n64] = logw;
-        S.ell_out[n64] = (double)ell;
-        float* xo = reinterpret_cast<float*>(S.x_out);
-#pragma unroll
-        for (int i = 0; i < kD; ++i) if (i < d) xo[(size_t)i * S.N + n64] = x[i];
-        if (!isfinite(logw) || !isfinite(ell)) atomicOr(S.status, 1u);
-    }
+    // no more evaluations: release the MMA warp
+    if (G.tid == 0) desc->stop = 1;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(G.a.barA);
     if (G.dead && G.tid == 0) atomicOr(S.status, 2u);
     tc_before_sync();
     __syncthreads();
@@ -583,8 +676,10 @@ void tc_prepare_logreg(const float* X, const float* y, int n, int d, std::vector
     }
 }
 
+// Persistent grid: one tile per group when the tiles fit in one wave of groups, else one CTA
+// per SM and the wrap-around schedule over tiles x steps (span = steps per group >= T).
 cudaError_t launch_sweep_tc(const SweepParams& sp, const void* Ximg, const uint32_t* ybits, int n, int d,
-                            cudaStream_t s)
+                            float* grad_state, int* handed, cudaStream_t s)
 {
     tc::TcParams P;
     P.sp = sp;
@@ -592,10 +687,37 @@ cudaError_t launch_sweep_tc(const SweepParams& sp, const void* Ximg, const uint3
     P.ybits = ybits;
     P.n = n;
     P.d = d;
-    cudaError_t e = cudaFuncSetAttribute(tc::oais_sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tc::kSmemBytes);
+    P.tiles = tc_records(sp.N);
+    P.grad_state = grad_state;
+    P.handed = handed;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    tc::oais_sweep_tc_kernel<<<tc_grid(sp.N), tc::kThreads, tc::kSmemBytes, s>>>(P);
+    int grid = (P.tiles + tc::kGroups - 1) / tc::kGroups;
+    P.span = sp.T;
+    if (grid > sms) {
+        grid = sms;
+        const int64_t slots = (int64_t)grid * tc::kGroups, total = (int64_t)P.tiles * sp.T;
+        P.span = std::max<int64_t>(sp.T, (total + slots - 1) / slots);
+        e = cudaMemsetAsync(handed, 0, sizeof(int) * P.tiles, s);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaFuncSetAttribute(tc::oais_sweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    // a group may wait for another CTA's hand-off: every CTA resident at once (cooperative)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tc::kThreads);
+    cfg.dynamicSmemBytes = tc::kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, tc::oais_sweep_tc_kernel, P);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
