@@ -301,10 +301,12 @@ def main():
                     "kernel": "oais_sweep_kernel<RowsTarget<32,logistic>, MALA>"}
     else:
         # tensor-core form: the contractions run on tcgen05 (a small share of their peak); the
-        # per-row epilogue needs one exp and one reciprocal per row and one log per 16 rows on
-        # the special-function unit, whose measured rates bound the row throughput
-        sec_per_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (16.0 * rates["lg2"])
-        sfu_per_row = 2.0 + 1.0 / 16.0
+        # per-row epilogue needs one exp and one reciprocal per row on the special-function
+        # unit, and one log per 64-row chunk of a particle (resident form) or per 32-row half
+        # chunk (streamed form); the unit's measured rates bound the row throughput
+        rows_per_log = 64.0 if args.contraction == "bf16_tc" else 32.0
+        sec_per_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (rows_per_log * rates["lg2"])
+        sfu_per_row = 2.0 + 1.0 / rows_per_log
         rows = pr.n * ps_per_job * args.steps
         achieved = sfu_per_row * rows / sweep_s / 1e12
         peak = sfu_per_row * N_SM / sec_per_row_sm / 1e12
@@ -495,10 +497,10 @@ def bench_batched(args):
              [("ex2", oais.UNIT_EX2), ("rcp", oais.UNIT_RCP), ("lg2", oais.UNIT_LG2)]}
     peaks, src = measured_peaks()
     tpeak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1e12
-    # per problem the binding unit: special-function work (1 ex2 + 1 rcp + 1/16 lg2 per row
-    # and evaluation) or the tensor pipe (two-term split: 8 n d FLOP per evaluation); the
-    # roofline time of the job is the sum of the per-problem maxima
-    sec_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (16.0 * rates["lg2"])
+    # per problem the binding unit: special-function work (1 ex2 + 1 rcp per row and
+    # evaluation, 1 lg2 per 32-row half chunk) or the tensor pipe (two-term split: 8 n d FLOP
+    # per evaluation); the roofline time of the job is the sum of the per-problem maxima
+    sec_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (32.0 * rates["lg2"])
     t_bound = 0.0
     for pr in probs:
         ev = N * (1 + T) * R
