@@ -344,6 +344,7 @@ def main():
                        "move": "MALA", "l2": "flushed between timed steps (256 MiB write)",
                        "log_weights": "f64", "contraction": args.contraction},
             "logZ_last_round": last[-1]["logZ"], "se_last_round": se_last,
+            "elbo_last_round": last[-1]["elbo"], "kl_last_round": last[-1]["kl"],
             "sec_to_logZ_se_0.01": sec_to_se,
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cb, "other_form": compare,
             "gpu_launches": 4 * len(ROUNDS_T) * args.steps,

@@ -123,6 +123,11 @@ typedef struct {
     int32_t round;      /* 0-based index of the round */
     int32_t n_resample; /* asmc_run: intermediate resampling events; 0 for OAIS */
     int32_t pad;
+    double elbo;        /* ELBO estimate sum_t sum_n W_{t-1}^n log g_t^n with the normalised
+                           weights since the last resampling (Sec. on the KL divergence of a
+                           schedule: log Z = ELBO + KL); NaN for a sharded round */
+    double kl;          /* logZ - elbo: the accumulated-KL estimate, >= 0 up to rounding (per
+                           step, log sum_n W g >= sum_n W log g by Jensen) */
 } oais_round_result;
 
 typedef struct oais_ctx oais_ctx;
@@ -212,6 +217,14 @@ oais_status oais_logZ(const oais_ctx* ctx, double* logZ, double* se);
  * accept [T] mean MH acceptance per step.  Any output pointer may be NULL. */
 oais_status oais_get_stats(const oais_ctx* ctx, double* log_ghat, double* D_hat, double* beta,
                            double* accept, int32_t* T);
+
+/* ELBO terms of the last completed round, host [T] (query *T with elbo_terms = NULL):
+ * elbo_terms[t-1] = sum_n W_{t-1}^n log g_t^n, the step-t term of the ELBO estimator of the
+ * paper's section on the KL divergence of a schedule, with W_{t-1} the normalised weights
+ * since the last resampling.  Reading of the printed estimator: its weights are the
+ * normalised W of Alg. 1, so no further 1/N factor applies.  EINVAL before the first round
+ * and after a sharded round (the terms are per shard there). */
+oais_status oais_get_elbo(const oais_ctx* ctx, double* elbo_terms, int32_t* T);
 
 /* The schedule the next round will run (host [*T + 1]; query *T with beta = NULL) and
  * its step sizes (host [*T], may be NULL). */

@@ -360,7 +360,8 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
              /* outputs (any may be NULL except res) */
              orc_result* res, double* log_ghat /* T x 3 */, double* accept /* T */,
              double* ess_trace /* T */, double* logw_out /* N */, double* x_out /* N x d */,
-             double* ell_out /* N */, double* margin_out /* N */, int64_t* resample_steps /* T */)
+             double* ell_out /* N */, double* margin_out /* N */, int64_t* resample_steps /* T */,
+             double* elbo_t /* T */)
 {
     const int d = tg->d;
     int need_grad = (mv->kind != ORC_RWMH);   /* EXACT keeps the gradient too (cheap) */
@@ -395,6 +396,15 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
                 for (long n = 0; n < N; ++n) tmp[n] = logw[n] + i * logg[n];
                 log_ghat[(size_t)(t - 1) * 3 + i] = orc_logsumexp(tmp, N);
             }
+        }
+        /* ELBO term of step t (the estimator of the section on the KL divergence of a schedule):
+           sum_n W_{t-1}^n log g_t^n, W_{t-1}^n = w_{t-1}^n / sum_m w_{t-1}^m the normalised
+           weights (since the last resampling) */
+        if (elbo_t) {
+            const double lse = orc_logsumexp(logw, N);
+            double e = 0.0;
+            for (long n = 0; n < N; ++n) e += exp(logw[n] - lse) * logg[n];
+            elbo_t[t - 1] = e;
         }
         /* reweight: w_{t^-} = w_{t-1} g_t */
         for (long n = 0; n < N; ++n) logw[n] += logg[n];

@@ -19,7 +19,7 @@ int tc_image_bytes();
 int tc_max_rows();
 void tc_prepare_logreg(const float* X, const float* y, int n, int d, std::vector<uint16_t>& img,
                        std::vector<uint32_t>& ybits);
-cudaError_t launch_merge_stats(const StepPartial*, int, int, double, double*, double*, cudaStream_t);
+cudaError_t launch_merge_stats(const StepPartial*, int, int, double, double*, double*, double*, cudaStream_t);
 cudaError_t launch_fisher(const double* logw, const double* ell, const void* x, bool fp64, int64_t N, int d,
                           const double* lse, double ref_scale, int kind, int nrows, double p0, void* scratch,
                           double* out, cudaStream_t s);
@@ -134,6 +134,7 @@ struct oais_ctx {
     void* d_x = nullptr;
     StepPartial* d_parts = nullptr;
     double *d_log_ghat = nullptr, *d_accept = nullptr, *d_lse = nullptr;
+    double* d_elbo = nullptr;            // [T_max] ELBO terms sum_n W_{t-1}^n log g_t^n
     void* d_lse_scratch = nullptr;
     unsigned* d_status = nullptr;
     // ASMC: second particle buffer, gradient buffers, resampling scratch and traces
@@ -153,6 +154,7 @@ struct oais_ctx {
     float pend_ms = 0.0f;
     std::vector<double> pend_lg, pend_acc;
     double pend_lse[2] = {0.0, 0.0};
+    std::vector<double> cur_elbo;        // the running round's ELBO terms (empty: not available)
     std::vector<double> l_ess_trace;
     std::vector<int> l_resampled;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -162,7 +164,7 @@ struct oais_ctx {
     int problem = 0;                     // problem index in the random-number tag
     // last completed round
     bool have_last = false;
-    std::vector<double> l_beta, l_eps, l_log_ghat, l_D, l_accept;
+    std::vector<double> l_beta, l_eps, l_log_ghat, l_D, l_accept, l_elbo;
     double l_logZ = 0, l_se = 0, l_Lambda = 0, l_ess = 0;
     std::string err;
 };
@@ -192,7 +194,7 @@ static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 static size_t elt_bytes(int kind) { return kind == kGauss ? sizeof(double) : sizeof(float); }
 
 struct Layout {
-    size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, lse, lse_scr, status;
+    size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, elbo, lse, lse_scr, status;
     size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, tc_img, tc_y;
     size_t tcs_img, tcs_state, tc_handed, total;
 };
@@ -228,6 +230,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     L.parts = take(sizeof(StepPartial) * (size_t)T_max * records_per_step(N));
     L.lg = take(sizeof(double) * 3 * T_max);
     L.acc = take(sizeof(double) * T_max);
+    L.elbo = take(sizeof(double) * T_max);
     L.lse = take(sizeof(double) * 2);
     L.lse_scr = take(logsumexp_scratch_bytes(N));
     L.status = take(sizeof(unsigned));
@@ -404,6 +407,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     ctx->d_x = b + L.x;
     ctx->d_parts = reinterpret_cast<StepPartial*>(b + L.parts);
     ctx->d_log_ghat = reinterpret_cast<double*>(b + L.lg);
+    ctx->d_elbo = reinterpret_cast<double*>(b + L.elbo);
     ctx->d_accept = reinterpret_cast<double*>(b + L.acc);
     ctx->d_lse = reinterpret_cast<double*>(b + L.lse);
     ctx->d_lse_scratch = b + L.lse_scr;
@@ -539,7 +543,7 @@ oais_status oais_merge_stats(const void* d_partials, int32_t nblocks, int32_t T,
     if (!d_partials || nblocks < 1 || T < 1 || N < 1 || moves < 1 || !d_log_ghat || !d_accept)
         return fail(nullptr, OAIS_EINVAL, "bad arguments to oais_merge_stats");
     CK(launch_merge_stats(static_cast<const StepPartial*>(d_partials), nblocks, T, 1.0 / ((double)N * moves),
-                          d_log_ghat, d_accept, static_cast<cudaStream_t>(stream)));
+                          d_log_ghat, d_accept, nullptr, static_cast<cudaStream_t>(stream)));
     return OAIS_OK;
 }
 
@@ -632,7 +636,7 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
     const uint32_t tag = (uint32_t)(ctx->round & 0xFFFF) | ((uint32_t)ctx->problem << 16);
     const int grid = sweep_grid(ctx->N);
     const double logN = std::log((double)ctx->N);
-    std::vector<double> lg(3 * T), acc(T), ess_tr;
+    std::vector<double> lg(3 * T), acc(T), elbo(T), ess_tr;
     std::vector<int> rs;
     unsigned status = 0;
     double logZ, ess, se;
@@ -652,11 +656,12 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         CK(cudaEventRecord(ctx->ev1, s));
         const int records = ctx->dt.tc ? tc_records(ctx->N) : (ctx->dt.tcs ? tcs_tiles(ctx->N) : grid);
         CK(launch_merge_stats(ctx->d_parts, records, T,
-                              1.0 / ((double)ctx->N * ctx->mv.moves), ctx->d_log_ghat, ctx->d_accept, s));
+                              1.0 / ((double)ctx->N * ctx->mv.moves), ctx->d_log_ghat, ctx->d_accept, ctx->d_elbo, s));
         CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
         double lse[2];
         CK(cudaMemcpyAsync(lg.data(), ctx->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(acc.data(), ctx->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(elbo.data(), ctx->d_elbo, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(lse, ctx->d_lse, sizeof(lse), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -715,12 +720,13 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         }
         CK(cudaEventRecord(ctx->ev1, s));
         CK(launch_merge_stats(ctx->d_parts, records, T, 1.0 / ((double)ctx->N * ctx->mv.moves),
-                              ctx->d_log_ghat, ctx->d_accept, s));
+                              ctx->d_log_ghat, ctx->d_accept, ctx->d_elbo, s));
         AsmcState st;
         ess_tr.resize(T);
         rs.resize(T);
         CK(cudaMemcpyAsync(lg.data(), ctx->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(acc.data(), ctx->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(elbo.data(), ctx->d_elbo, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(&st, ctx->d_st, sizeof(st), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(ess_tr.data(), ctx->d_ess_trace, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(rs.data(), ctx->d_resampled, sizeof(int) * T, cudaMemcpyDeviceToHost, s));
@@ -746,6 +752,7 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
     if (status & 2u) return fail(ctx, OAIS_ETIMEOUT, "a tensor-core completion wait gave up");
     if (status & 4u) return fail(ctx, OAIS_ECUDA, "shared memory base not 1024-byte aligned");
     if (status & 1u) return fail(ctx, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood");
+    ctx->cur_elbo = elbo;
     return commit_round(ctx, T, T_next, lg, acc, logZ, ess, se, ms, asmc, n_res, ess_tr, rs, out);
 }
 
@@ -773,6 +780,15 @@ static oais_status commit_round(oais_ctx* ctx, int T, int32_t T_next, const std:
     ctx->l_n_resample = n_res;
     ctx->l_ess_trace = ess_tr;
     ctx->l_resampled = rs;
+    // ELBO = sum_t sum_n W_{t-1}^n log g_t^n and KL = log Z_hat - ELBO (log Z = ELBO + KL);
+    // not formed for a sharded round (its terms are per shard)
+    double elbo = NAN;
+    if ((int)ctx->cur_elbo.size() == T) {
+        elbo = 0.0;
+        for (int t = 0; t < T; ++t) elbo += ctx->cur_elbo[t];
+    }
+    ctx->l_elbo = ctx->cur_elbo;
+    ctx->cur_elbo.clear();
     if (out) {
         out->logZ = logZ;
         out->se = se;
@@ -783,6 +799,8 @@ static oais_status commit_round(oais_ctx* ctx, int T, int32_t T_next, const std:
         out->round = ctx->round;
         out->n_resample = n_res;
         out->pad = 0;
+        out->elbo = elbo;
+        out->kl = logZ - elbo;
     }
     ctx->beta = beta_next;
     ctx->eps = eps_next;
@@ -946,6 +964,16 @@ oais_status oais_get_stats(const oais_ctx* ctx, double* log_ghat, double* D_hat,
     if (D_hat) std::copy(ctx->l_D.begin(), ctx->l_D.end(), D_hat);
     if (beta) std::copy(ctx->l_beta.begin(), ctx->l_beta.end(), beta);
     if (accept) std::copy(ctx->l_accept.begin(), ctx->l_accept.end(), accept);
+    return OAIS_OK;
+}
+
+oais_status oais_get_elbo(const oais_ctx* ctx, double* elbo_terms, int32_t* T)
+{
+    if (!ctx || !ctx->have_last) return fail(nullptr, OAIS_EINVAL, "no completed round");
+    if ((int)ctx->l_elbo.size() != (int)ctx->l_D.size())
+        return fail(nullptr, OAIS_EINVAL, "the last round was a sharded round: no ELBO terms");
+    if (T) *T = (int32_t)ctx->l_elbo.size();
+    if (elbo_terms) std::copy(ctx->l_elbo.begin(), ctx->l_elbo.end(), elbo_terms);
     return OAIS_OK;
 }
 
@@ -1157,12 +1185,13 @@ static oais_status batch_enqueue(oais_batch* b, int T)
     for (int p = 0; p < b->P; ++p) {
         oais_ctx* c = b->ctx[p];
         BK(launch_merge_stats(c->d_parts, tcs_tiles(c->N), T, 1.0 / ((double)c->N * c->mv.moves), c->d_log_ghat,
-                              c->d_accept, s));
+                              c->d_accept, c->d_elbo, s));
         BK(launch_logsumexp(c->d_logw, c->N, c->d_lse, c->d_lse_scratch, s));
         double* o = b->h_out + (size_t)p * b->out_stride;
         BK(cudaMemcpyAsync(o, c->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
         BK(cudaMemcpyAsync(o + 3 * b->T_max, c->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
         BK(cudaMemcpyAsync(o + 4 * b->T_max, c->d_lse, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        BK(cudaMemcpyAsync(o + 4 * b->T_max + 2, c->d_elbo, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
     }
     BK(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(unsigned) * b->P, cudaMemcpyDeviceToHost, s));
     return OAIS_OK;
@@ -1209,7 +1238,7 @@ oais_status oais_batch_init(oais_batch** out, int32_t P, const oais_target* targ
     b->n_items = (uint32_t)items.size();
     b->pbytes = tcs_params_bytes();   // the kernel indexes the blocks as an array: no padding
     b->sched_stride = 2 * (size_t)T_max + 1;
-    b->out_stride = 4 * (size_t)T_max + 2;
+    b->out_stride = 5 * (size_t)T_max + 2;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1280,6 +1309,7 @@ oais_status oais_batch_round(oais_batch* b, int32_t T_next, oais_round_result* r
             const double logZ = lse0 - std::log((double)c->N);
             const double ess = std::exp(2.0 * lse0 - lse1);
             const double se = std::sqrt(std::max(0.0, 1.0 / ess - 1.0 / (double)c->N));
+            c->cur_elbo.assign(o + 4 * b->T_max + 2, o + 4 * b->T_max + 2 + T);
             st = commit_round(c, T, T_next, lg, acc, logZ, ess, se, ms, false, 0, {}, {},
                               results ? results + p : nullptr);
         }

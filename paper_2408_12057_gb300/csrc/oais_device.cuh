@@ -119,28 +119,32 @@ __device__ __forceinline__ double mh_log_uniform(const Rng& rng, uint32_t n, uin
 // ---------------------------------------------------------------------------
 // Per-step moment statistics (Alg. 1, "compute moments"; Sec. 5.1.1):
 //   g_hat_{t,i} = sum_n w_{t-1}^n (g_t^n)^i,  i = 0, 1, 2,
-// kept as a shifted sum: g_hat = exp(m) * s.  One record per (t, CTA); the
-// records are merged in a fixed order by oais_merge_stats_kernel.
+// kept as a shifted sum: g_hat = exp(m) * s, and with it the weighted sum of log g_t on
+// moment 0's shift, u = sum_n exp(log w - m[0]) log g, so that u / s[0] is the term
+// sum_n W_{t-1}^n log g_t^n of the ELBO estimator (Sec. on the KL divergence of a schedule).
+// One record per (t, CTA or tile); the records are merged in a fixed order by
+// merge_stats_kernel.
 // ---------------------------------------------------------------------------
 struct StepPartial {
     double m[3];    // shift (an upper estimate of max_n log w + i log g)
     double s[3];    // sum_n exp(log w + i log g - m)
+    double u;       // sum_n exp(log w - m[0]) log g
     uint32_t accepted;
     uint32_t pad;
 };
-static_assert(sizeof(StepPartial) == 56, "StepPartial layout");
+static_assert(sizeof(StepPartial) == 64, "StepPartial layout");
 
 constexpr int kMaxWarps = 32;
 
 // Warp part: v_i = lw + i * lg for the lane's particle (or -inf if inactive).
-// Writes the warp's (m_i, s_i) for i = 0..2 through lane 0.  By default the offsets from the
+// Writes the warp's (m_i, s_i) for i = 0..2 and u (ws[3], on m_0) through lane 0.  By default the offsets from the
 // anchor particle and from the warp maximum are fp64 differences rounded once.  kFast (the
 // tensor-core kernels, whose particle arithmetic is fp32 and whose fp64 pipe is slow): both
 // come from two fp64 differences per particle (lw - lw_a, lg - lg_a) in fp32, which adds
 // about 2^-24 |offset from the anchor| to each exponent.
 template <bool kFast = false>
 __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool active,
-                                                    double* wm /*3*/, float* ws /*3*/)
+                                                    double* wm /*3*/, float* ws /*4*/)
 {
     const unsigned full = 0xFFFFFFFFu;
     // anchor = a representative active value: avoids fp64 max over the warp
@@ -149,6 +153,7 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
         if ((threadIdx.x & 31) == 0) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) { wm[i] = -INFINITY; ws[i] = 0.0f; }
+            ws[3] = 0.0f;
         }
         return;
     }
@@ -165,9 +170,18 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
         const double M = anchor + (double)mx;
         float e = !active ? 0.0f : kFast ? __expf(f - mx) : __expf((float)(v - M));
+        float u = i == 0 ? e * (float)lg : 0.0f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
-        if ((threadIdx.x & 31) == 0) { wm[i] = M; ws[i] = e; }
+        if (i == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            wm[i] = M;
+            ws[i] = e;
+            if (i == 0) ws[3] = u;
+        }
     }
 }
 
@@ -182,7 +196,7 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
 // kFast = false keeps the rescaling and the sum in fp64 (the CUDA-core forms).  Lane j < W
 // passes piece j's shifts m[3], sums s[3] and count acc; lane 0 writes the record.
 template <int W, bool kFast>
-__device__ __forceinline__ void merge_lane_pieces(int lane, const double (&mj)[3], const float (&sj)[3],
+__device__ __forceinline__ void merge_lane_pieces(int lane, const double (&mj)[3], const float (&sj)[4],
                                                   unsigned accj, StepPartial* out)
 {
     static_assert(W >= 1 && W <= 32 && (W & (W - 1)) == 0, "W: a power of two");
@@ -200,15 +214,25 @@ __device__ __forceinline__ void merge_lane_pieces(int lane, const double (&mj)[3
         }
         if (kFast) {
             const float dj = (float)(m - M);      // -inf for an empty piece; NaN when every piece is
-            float v = (lane < W && !isnan(dj)) ? sj[i] * expf(dj) : 0.0f;
+            const float fj = (lane < W && !isnan(dj)) ? expf(dj) : 0.0f;
+            float v = sj[i] * fj, uu = i == 0 ? sj[3] * fj : 0.0f;
 #pragma unroll
-            for (int o = 1; o < W; o <<= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            for (int o = 1; o < W; o <<= 1) {
+                v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                uu += __shfl_xor_sync(0xFFFFFFFFu, uu, o);
+            }
             rec.s[i] = (double)v;
+            if (i == 0) rec.u = (double)uu;
         } else {
-            double v = (lane < W && m != -INFINITY) ? (double)sj[i] * exp(m - M) : 0.0;
+            const double fj = (lane < W && m != -INFINITY) ? exp(m - M) : 0.0;
+            double v = (double)sj[i] * fj, uu = i == 0 ? (double)sj[3] * fj : 0.0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                uu += __shfl_xor_sync(0xFFFFFFFFu, uu, o);
+            }
             rec.s[i] = v;
+            if (i == 0) rec.u = uu;
         }
         rec.m[i] = M;
     }
@@ -222,23 +246,22 @@ __device__ __forceinline__ void merge_lane_pieces(int lane, const double (&mj)[3
     }
 }
 template <int W, bool kFast>
-__device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3], const float (*ws)[3],
+__device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3], const float (*ws)[4],
                                                   const unsigned* wacc, StepPartial* out)
 {
     double m[3];
-    float sv[3];
+    float sv[4];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        m[i] = lane < W ? wm[lane][i] : -INFINITY;
-        sv[i] = lane < W ? ws[lane][i] : 0.0f;
-    }
+    for (int i = 0; i < 3; ++i) m[i] = lane < W ? wm[lane][i] : -INFINITY;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sv[i] = lane < W ? ws[lane][i] : 0.0f;
     merge_lane_pieces<W, kFast>(lane, m, sv, (wacc && lane < W) ? wacc[lane] : 0u, out);
 }
 
 // CTA part: warp 0 merges the W warps' pieces and writes one record.  Call after a
 // __syncthreads that follows warp_moment_partial.
 template <int W>
-__device__ __forceinline__ void cta_moment_record(const double (*wm)[3], const float (*ws)[3],
+__device__ __forceinline__ void cta_moment_record(const double (*wm)[3], const float (*ws)[4],
                                                   const unsigned* wacc, StepPartial* out)
 {
     if ((threadIdx.x >> 5) != 0) return;

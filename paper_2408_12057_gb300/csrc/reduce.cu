@@ -11,32 +11,47 @@ namespace oais {
 
 constexpr int kMergeThreads = 256;
 
-// one CTA per step t
+// merge of (m, s, u): exp(m) s + exp(m') s' with u carried on the same shift as s
+__device__ __forceinline__ void lse_merge_u(double& m, double& s, double& u, double m2, double s2, double u2)
+{
+    if (m2 == -INFINITY) return;
+    if (m == -INFINITY) { m = m2; s = s2; u = u2; return; }
+    if (m2 > m) { const double f = exp(m - m2); s = s * f + s2; u = u * f + u2; m = m2; }
+    else        { const double f = exp(m2 - m); s = s + s2 * f; u = u + u2 * f; }
+}
+
+// one CTA per step t: log g_hat_{t,i}, the acceptance rate and (elbo != null) the ELBO term
+// sum_n W_{t-1}^n log g_t^n = u / s_0
 __global__ void __launch_bounds__(kMergeThreads)
 merge_stats_kernel(const StepPartial* __restrict__ parts, int nblocks, double inv_count,
-                   double* __restrict__ log_ghat, double* __restrict__ accept)
+                   double* __restrict__ log_ghat, double* __restrict__ accept, double* __restrict__ elbo)
 {
-    __shared__ double sm[3][kMergeThreads], ss[3][kMergeThreads];
+    __shared__ double sm[3][kMergeThreads], ss[3][kMergeThreads], su[kMergeThreads];
     __shared__ unsigned long long sa[kMergeThreads];
     const int t = blockIdx.x, tid = threadIdx.x;
     const StepPartial* p = parts + (size_t)t * nblocks;
-    double m[3] = {-INFINITY, -INFINITY, -INFINITY}, s[3] = {0.0, 0.0, 0.0};
+    double m[3] = {-INFINITY, -INFINITY, -INFINITY}, s[3] = {0.0, 0.0, 0.0}, u = 0.0;
     unsigned long long a = 0;
     for (int j = tid; j < nblocks; j += kMergeThreads) {
         const StepPartial q = p[j];
+        lse_merge_u(m[0], s[0], u, q.m[0], q.s[0], q.u);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) lse_merge(m[i], s[i], q.m[i], q.s[i]);
+        for (int i = 1; i < 3; ++i) lse_merge(m[i], s[i], q.m[i], q.s[i]);
         a += q.accepted;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) { sm[i][tid] = m[i]; ss[i][tid] = s[i]; }
+    su[tid] = u;
     sa[tid] = a;
     __syncthreads();
     for (int stride = kMergeThreads / 2; stride > 0; stride >>= 1) {
         if (tid < stride) {
+            double mm = sm[0][tid], s0 = ss[0][tid], u0 = su[tid];
+            lse_merge_u(mm, s0, u0, sm[0][tid + stride], ss[0][tid + stride], su[tid + stride]);
+            sm[0][tid] = mm; ss[0][tid] = s0; su[tid] = u0;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                double mm = sm[i][tid], s0 = ss[i][tid];
+            for (int i = 1; i < 3; ++i) {
+                mm = sm[i][tid]; s0 = ss[i][tid];
                 lse_merge(mm, s0, sm[i][tid + stride], ss[i][tid + stride]);
                 sm[i][tid] = mm; ss[i][tid] = s0;
             }
@@ -48,6 +63,7 @@ merge_stats_kernel(const StepPartial* __restrict__ parts, int nblocks, double in
 #pragma unroll
         for (int i = 0; i < 3; ++i) log_ghat[3 * t + i] = sm[i][0] + log(ss[i][0]);
         accept[t] = (double)sa[0] * inv_count;
+        if (elbo) elbo[t] = su[0] / ss[0][0];
     }
 }
 
@@ -128,10 +144,10 @@ int lse_blocks(int64_t n)
 }
 
 cudaError_t launch_merge_stats(const StepPartial* parts, int nblocks, int T, double inv_count,
-                               double* log_ghat, double* accept, cudaStream_t s)
+                               double* log_ghat, double* accept, double* elbo, cudaStream_t s)
 {
     if (T <= 0) return cudaSuccess;
-    merge_stats_kernel<<<T, kMergeThreads, 0, s>>>(parts, nblocks, inv_count, log_ghat, accept);
+    merge_stats_kernel<<<T, kMergeThreads, 0, s>>>(parts, nblocks, inv_count, log_ghat, accept, elbo);
     return cudaGetLastError();
 }
 

@@ -129,7 +129,7 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_m[2][kSweepThreads / 32][3];
-    __shared__ float s_s[2][kSweepThreads / 32][3];
+    __shared__ float s_s[2][kSweepThreads / 32][4];
     __shared__ unsigned s_acc[2][kSweepThreads / 32];
 
     tg.setup(smem);
@@ -225,7 +225,7 @@ asmc_step_kernel(const StepParams P, Tgt tg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_m[kSweepThreads / 32][3];
-    __shared__ float s_s[kSweepThreads / 32][3];
+    __shared__ float s_s[kSweepThreads / 32][4];
     __shared__ unsigned s_acc[kSweepThreads / 32];
     constexpr bool GRAD = (MOVE != kRwmh);
 

@@ -57,7 +57,7 @@ constexpr int kOffBar = kOffY + kMaxRows / 8;                // + 256 B
 constexpr int kOffTmem = kOffBar + 8 * kBarsPerGroup * kGroups;
 constexpr int kOffAbort = kOffTmem + 4;
 constexpr int kOffStat = kOffTmem + 16;
-constexpr int kStatBytes = 2 * 4 * 40;       // [slot][warp] WarpPiece
+constexpr int kStatBytes = 2 * 4 * 48;       // [slot][warp] WarpPiece
 constexpr int kOffDesc = kOffStat + kGroups * kStatBytes;  // [group] EvalDesc
 constexpr int kSmemBytes = kOffDesc + kGroups * 16;
 constexpr int kTmemCols = 512;               // group g: D1[0], D1[1] at 256 g + {0, 64}, D2 at 256 g + 128
@@ -126,13 +126,15 @@ __device__ __forceinline__ GroupAddr group_addr(unsigned char* smem, uint32_t tm
 // One warp's share of a step's moment record (Alg. 1 moments, Sec. 5.1.1): the anchor (the
 // first active particle's log w and log g), per moment i the maximum fp32 offset
 // (log w - a0) + i (log g - b0) over the warp and the sum of exp(offset - maximum), and the
-// warp's acceptance count.  The shift m_i = a0 + i b0 + mx_i is formed in fp64 by the merge.
+// warp's acceptance count, and u = sum exp(offset_0 - mx_0) log g (the ELBO term on moment
+// 0's shift).  The shift m_i = a0 + i b0 + mx_i is formed in fp64 by the merge.
 struct WarpPiece {
     double a0;               // -inf: no active particle in the warp
-    float b0, mx[3], s[3];
+    float b0, mx[3], s[3], u;
     unsigned acc;
+    unsigned pad;
 };
-static_assert(sizeof(WarpPiece) == 40, "WarpPiece layout");
+static_assert(sizeof(WarpPiece) == 48, "WarpPiece layout");
 
 __device__ __forceinline__ void warp_piece(double lw, float lg, bool active, WarpPiece* out)
 {
@@ -145,6 +147,7 @@ __device__ __forceinline__ void warp_piece(double lw, float lg, bool active, War
             out->b0 = 0.0f;
 #pragma unroll
             for (int i = 0; i < 3; ++i) { out->mx[i] = 0.0f; out->s[i] = 0.0f; }
+            out->u = 0.0f;
         }
         return;
     }
@@ -160,9 +163,18 @@ __device__ __forceinline__ void warp_piece(double lw, float lg, bool active, War
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
         float e = active ? __expf(f - mx) : 0.0f;
+        float u = i == 0 ? e * lg : 0.0f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
-        if (lead) { out->mx[i] = mx; out->s[i] = e; }
+        if (i == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
+        }
+        if (lead) {
+            out->mx[i] = mx;
+            out->s[i] = e;
+            if (i == 0) out->u = u;
+        }
     }
 }
 
@@ -171,13 +183,14 @@ __device__ __forceinline__ void merge_pieces(int lane, const WarpPiece* pc, Step
 {
     const WarpPiece& q = pc[lane & 3];         // lanes >= 4 read a valid piece and ignore it
     double m[3];
-    float sv[3];
+    float sv[4];
     const bool has = lane < 4 && q.a0 != -INFINITY;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         m[i] = has ? q.a0 + i * (double)q.b0 + (double)q.mx[i] : -INFINITY;
         sv[i] = has ? q.s[i] : 0.0f;
     }
+    sv[3] = has ? q.u : 0.0f;
     merge_lane_pieces<4, true>(lane, m, sv, lane < 4 ? q.acc : 0u, out);
 }
 

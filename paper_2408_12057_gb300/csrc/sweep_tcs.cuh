@@ -136,7 +136,7 @@ struct Misc {
     double xl[kMaxH][kTile];    // per column group: partial log-likelihood
     float4 xm[kMaxH][kTile];    // per coordinate group: partial sums of the MH ratio
     double s_m[2][4][3];
-    float s_s[2][4][3];
+    float s_s[2][4][4];
     unsigned s_acc[2][4];
     Params prm;                 // batched launch: the current item's problem
     uint32_t item;              // batched launch: the current item

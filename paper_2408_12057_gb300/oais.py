@@ -46,7 +46,8 @@ class _Move(ctypes.Structure):
 class _RoundResult(ctypes.Structure):
     _fields_ = [("logZ", ctypes.c_double), ("se", ctypes.c_double), ("Lambda_hat", ctypes.c_double),
                 ("ess", ctypes.c_double), ("sweep_ms", ctypes.c_double), ("T", ctypes.c_int32),
-                ("round", ctypes.c_int32), ("n_resample", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("round", ctypes.c_int32), ("n_resample", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("elbo", ctypes.c_double), ("kl", ctypes.c_double)]
 
 
 _lib = None
@@ -72,6 +73,7 @@ def lib():
                 "asmc_run": ([P, P, i64, P, i32, P, f64, u64, P, P, P, P, P], i32),
                 "oais_logZ": ([P, P, P], i32),
                 "oais_get_stats": ([P, P, P, P, P, P], i32),
+                "oais_get_elbo": ([P, P, P], i32),
                 "oais_get_schedule": ([P, P, P, P], i32),
                 "oais_set_schedule": ([P, P, P, i32], i32),
                 "oais_particles": ([P, P, P, P], i32),
@@ -257,6 +259,15 @@ class OAIS:
         _check(lib().oais_get_stats(self._ctx, _np_ptr(lg), _np_ptr(D), _np_ptr(b), _np_ptr(a), None),
                self._ctx)
         return {"log_ghat": lg, "D_hat": D, "beta": b, "accept": a}
+
+    def elbo_terms(self):
+        """Per-step ELBO terms sum_n W_{t-1}^n log g_t^n of the last round (their sum is the
+        round result's ``elbo``, and ``kl`` = logZ - elbo)."""
+        T = ctypes.c_int32()
+        _check(lib().oais_get_elbo(self._ctx, None, ctypes.byref(T)), self._ctx)
+        e = np.zeros(T.value)
+        _check(lib().oais_get_elbo(self._ctx, _np_ptr(e), None), self._ctx)
+        return e
 
     def schedule(self):
         T = ctypes.c_int32()

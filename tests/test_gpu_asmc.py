@@ -33,7 +33,7 @@ def gpu_asmc(pr, move, N, beta, eps, seed, ess_frac, **kw):
     ess, rs, anc = r.resampling()
     out = dict(res=res, logw=logw.cpu().numpy().copy(), ell=ell.cpu().numpy().copy(),
                x=x.cpu().numpy().T.astype(np.float64).copy(), ess=ess, resampled=rs, anc=anc,
-               **r.stats())
+               elbo_t=r.elbo_terms(), **r.stats())
     r.close()
     return out
 
@@ -54,6 +54,10 @@ def test_gauss_asmc_matches_oracle(ess_frac, N, T):
     np.testing.assert_allclose(g["ell"], r["ell"], rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(g["x"], r["x"], rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(g["log_ghat"], r["log_ghat"], rtol=1e-9, atol=1e-6)
+    # ELBO terms with the weights since the last resampling (fp32 partial sums on the device)
+    np.testing.assert_allclose(g["elbo_t"], r["elbo_t"], rtol=1e-5, atol=1e-5)
+    assert g["res"]["kl"] == pytest.approx(g["res"]["logZ"] - g["elbo_t"].sum(), rel=1e-9, abs=1e-9)
+    assert r["kl"] >= 0.0
     if ess_frac >= 1.0:
         assert r["n_resample"] == T - 1
 

@@ -85,6 +85,7 @@ def test_batch_equals_single_contexts_over_rounds():
             assert np.array_equal(g["logw"], h["logw"]), (rnd, p)
             assert np.array_equal(g["log_ghat"], h["log_ghat"]), (rnd, p)
             assert rb[p]["logZ"] == rs["logZ"] and rb[p]["Lambda_hat"] == rs["Lambda_hat"]
+            assert rb[p]["elbo"] == rs["elbo"] and np.isfinite(rs["elbo"])
             assert np.array_equal(b.problem(p).schedule()[0], s.schedule()[0])
     for s in singles:
         s.close()

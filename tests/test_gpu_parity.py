@@ -41,9 +41,18 @@ def run_gpu(pr, move, N, beta, eps, seed, **kw):
     res = r.round(len(beta) - 1)
     logw, ell, x = r.particles()
     out = dict(res=res, logw=logw.cpu().numpy().copy(), ell=ell.cpu().numpy().copy(),
-               x=x.cpu().numpy().T.astype(np.float64).copy(), **r.stats())
+               x=x.cpu().numpy().T.astype(np.float64).copy(), elbo_t=r.elbo_terms(), **r.stats())
     r.close()
     return out
+
+
+def check_elbo(g, r, rtol, atol):
+    # the ELBO terms sum_n W_{t-1}^n log g_t^n against the oracle's; their sum and the KL
+    # estimate log Z_hat - ELBO, which Jensen's inequality keeps non-negative
+    np.testing.assert_allclose(g["elbo_t"], r["elbo_t"], rtol=rtol, atol=atol)
+    assert g["res"]["elbo"] == pytest.approx(g["elbo_t"].sum(), rel=1e-12, abs=1e-12)
+    assert g["res"]["kl"] == pytest.approx(g["res"]["logZ"] - g["res"]["elbo"], rel=1e-12, abs=1e-12)
+    assert g["res"]["kl"] >= -atol * len(g["elbo_t"])
 
 
 def tolerances(pr):
@@ -85,6 +94,7 @@ def compare(pr, move, N, beta, eps, seed, min_frac=0.9, **kw):
         _, Dg, Lg = oais.optimise_schedule(g["beta"], g["log_ghat"], 4)
         _, Do, Lo = o.optimise_schedule(np.asarray(beta, dtype=float), r["log_ghat"], 4)
         assert Lg[-1] == pytest.approx(Lo[-1], rel=1e-3 if pr.kind != W.GAUSS else 1e-6)
+        check_elbo(g, r, 1e-5 if pr.kind == W.GAUSS else 1e-4, 1e-5 if pr.kind == W.GAUSS else 1e-3)
     return g, r, ok
 
 

@@ -34,7 +34,7 @@ def run(pr, N, beta, eps, seed, contraction):
     res = r.round(len(beta) - 1)
     logw, ell, x = r.particles()
     out = dict(res=res, logw=logw.cpu().numpy().copy(), ell=ell.cpu().numpy().copy(),
-               x=x.cpu().numpy().T.astype(np.float64).copy(), **r.stats())
+               x=x.cpu().numpy().T.astype(np.float64).copy(), elbo_t=r.elbo_terms(), **r.stats())
     r.close()
     return out
 
@@ -61,6 +61,9 @@ def test_tc_matches_oracle_on_bf16_data(n, d, N, T):
     if ok.all():
         np.testing.assert_allclose(g["log_ghat"], r["log_ghat"], rtol=1e-5, atol=1e-4)
         np.testing.assert_allclose(g["accept"], r["accept"], rtol=0, atol=1e-12)
+        # ELBO terms sum_n W_{t-1}^n log g_t^n (fp32 offsets and sums on this path)
+        np.testing.assert_allclose(g["elbo_t"], r["elbo_t"], rtol=1e-4, atol=1e-3)
+        assert g["res"]["kl"] >= -1e-3 * T
 
 
 def test_tc_importance_sampling_invariant_full_size():

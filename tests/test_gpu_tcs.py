@@ -51,7 +51,7 @@ def run(pr, move, N, beta, eps, seed, leapfrog=5, rounds=1, contraction=None):
         res = r.round(len(beta) - 1)
     logw, ell, x = r.particles()
     out = dict(res=res, logw=logw.cpu().numpy().copy(), ell=ell.cpu().numpy().copy(),
-               x=x.cpu().numpy().T.astype(np.float64).copy(), **r.stats())
+               x=x.cpu().numpy().T.astype(np.float64).copy(), elbo_t=r.elbo_terms(), **r.stats())
     r.close()
     return out
 
@@ -96,6 +96,7 @@ def test_stream_matches_oracle(kind, n, d, N, T, move, L):
     if ok.all():
         np.testing.assert_allclose(g["log_ghat"], r["log_ghat"], rtol=1e-5, atol=1e-4)
         np.testing.assert_allclose(g["accept"], r["accept"], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(g["elbo_t"], r["elbo_t"], rtol=1e-4, atol=1e-3)
 
 
 def test_stream_importance_sampling_invariant():
