@@ -62,7 +62,7 @@ def parse():
                          "shared memory; bf16_tc_stream: the streamed kernel), or on CUDA cores in fp32")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other form of the contraction")
-    ap.add_argument("--workload", default="logreg", choices=["logreg", "linreg", "batched", "gmm", "gauss"])
+    ap.add_argument("--workload", default="logreg", choices=["logreg", "linreg", "batched", "gmm", "gauss", "unid"])
     ap.add_argument("--particles", type=int, default=None,
                     help="linreg / batched: particles per problem (profiling a smaller case)")
     ap.add_argument("--asmc", action="store_true",
@@ -198,6 +198,8 @@ def main():
         return bench_batched(args)
     if args.workload == "gmm":
         return bench_gmm(args)
+    if args.workload == "unid":
+        return bench_unid(args)
     if args.workload == "gauss":
         return bench_gauss(args)
     import torch
@@ -642,6 +644,46 @@ def bench_gauss(args):
         "roofline": {"bound": "latency", "note": "8 CTAs of 128 particles cannot fill 152 SMs; the round is "
                      "bound by the T = 64 dependent steps of each particle and the host's schedule update"},
         "gpu_launches": 3 * 4 * steps, "clocks": clk,
+    }))
+    run.close()
+
+
+def bench_unid(args):
+    """The paper's GPU workload "Unid" (X, Y ~ Uniform(0, 10), K ~ Binomial(10^11, X Y),
+    k = 10^10; fp64): N = 2^14 particles, four OAIS rounds (T = 64 -> 512, the schedule of each
+    round optimised from the previous one), RWMH with the 0.1 / 1 / 10 proposal cycle."""
+    import torch
+    from paper_2408_12057_gb300 import oais, workloads as W
+    torch.cuda.set_device(0)
+    pr = W.unid()
+    N, Ts = 1 << 14, [64, 128, 256, 512]
+    stream = torch.cuda.current_stream()
+    beta0 = np.linspace(0.0, 1.0, Ts[0] + 1) ** 5
+    run = oais.OAIS(pr, oais.RWMH, N, beta0, T_max=max(Ts), eps=0.1, seed=12057, moves=2, cycle=True,
+                    stream=stream)
+
+    def job():
+        run.set_schedule(beta0, np.full(Ts[0], 0.1))
+        return [run.round(Ts[i + 1] if i + 1 < len(Ts) else Ts[-1]) for i in range(len(Ts))]
+
+    steps = max(args.steps, 3)
+    t, last, clk = timed_job(job, steps, args.warmup, stream, ClockSampler(0))
+    m, k, b = float(pr.X[0]), float(pr.X[1]), pr.p0
+    logZ_closed = float(np.log(np.log(b * b * m / k) / (b * b * (m + 1))))
+    ps = N * sum(Ts) * steps
+    print(json.dumps({
+        "metric": METRIC, "value": ps / (t / 1e3), "unit": METRIC, "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": t / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (the model has no data beyond m, k)",
+        "config": {"workload": "unid_m1e11_k1e10_N16384_T64-128-256-512_rwmh_cycle", "N_per_gpu": N,
+                   "T_rounds": Ts, "moves": 2},
+        "sweep_ms_per_round": [r["sweep_ms"] for r in last],
+        "logZ_rounds": [r["logZ"] for r in last], "se_rounds": [r["se"] for r in last],
+        "Lambda_hat_rounds": [r["Lambda_hat"] for r in last], "logZ_closed_form": logZ_closed,
+        "roofline": {"bound": "latency", "note": "128 CTAs of 128 particles on 152 SMs, one fp64 "
+                     "likelihood (two normal CDFs, two log1p) per move; the round is bound by the "
+                     "dependent steps of each particle"},
+        "gpu_launches": 3 * len(Ts) * steps, "clocks": clk,
     }))
     run.close()
 

@@ -37,7 +37,7 @@ typedef enum {
     OAIS_EINVAL = 1,        /* bad argument: sizes, schedule not strictly increasing 0..1, ... */
     OAIS_ENOMEM = 2,        /* device allocation failed or workspace too small */
     OAIS_ECUDA = 3,         /* a CUDA runtime call failed */
-    OAIS_ENONFINITE = 4,    /* a log-weight or log-likelihood became NaN/inf */
+    OAIS_ENONFINITE = 4,    /* a log-weight or log-likelihood became NaN or +inf (-inf is a zero weight) */
     OAIS_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
     OAIS_EUNSUPPORTED = 6   /* combination not built (dimension, family, move) */
 } oais_status;
@@ -47,7 +47,13 @@ typedef enum {
     OAIS_T_GAUSS = 0,   /* L(x) = exp(-|x - mu|^2 / (2 p0^2)); X = mu[d]                   */
     OAIS_T_LOGREG = 1,  /* L(x) = prod_r Bern(y_r | sigmoid(X_r . x)); X[n][d], y[n] in {0,1} */
     OAIS_T_GMM = 2,     /* L(x) = p(x)/eta(x), p = (1/n) sum_k N(X_k, p0 I); X[n][d] means   */
-    OAIS_T_LINREG = 3   /* L(x) = prod_r N(y_r; X_r . x, p0^2); X[n][d], y[n]               */
+    OAIS_T_LINREG = 3,  /* L(x) = prod_r N(y_r; X_r . x, p0^2); X[n][d], y[n]               */
+    OAIS_T_UNID = 4     /* the unidentifiable product model of the paper's model appendix and
+                           GPU experiments: X, Y ~ Uniform(0, p0), K ~ Binomial(m, X Y) observed
+                           at k.  State z in R^2 under eta = N(0, I) (ref_scale must be 1), with
+                           X = p0 Phi(z_1), Y = p0 Phi(z_2); L(z) = Binom(k; m, X Y), 0 where
+                           X Y >= 1 (log L = -inf: such states get weight 0).  X = (m, k) as
+                           float64, d = 2, n = 0; fp64 throughout, CUDA-core form only */
 } oais_target_kind;
 
 typedef enum { OAIS_DT_F64 = 0, OAIS_DT_F32 = 1 } oais_dtype;
@@ -56,13 +62,14 @@ typedef struct {
     int32_t kind;       /* oais_target_kind */
     int32_t d;          /* state dimension, 1 <= d <= 32 (GAUSS: <= 16); the streamed
                            tensor-core form takes LOGREG and LINREG up to d = 256 */
-    int32_t n;          /* rows of X (LOGREG, LINREG), mixture components (GMM, <= 16); 0 for GAUSS */
-    int32_t dtype;      /* oais_dtype of X and y: GAUSS runs in F64 and takes F64 mu;
+    int32_t n;          /* rows of X (LOGREG, LINREG), mixture components (GMM, <= 16); 0 for GAUSS, UNID */
+    int32_t dtype;      /* oais_dtype of X and y: GAUSS and UNID run in F64 and take F64 X;
                            the other families run in F32 and take F32 or F64 input */
     const void* X;      /* row-major, see kind; host or device per on_device */
     const void* y;      /* [n] (LOGREG, LINREG), else NULL */
     double ref_scale;   /* s > 0 */
-    double p0;          /* GAUSS: likelihood sigma; GMM: component variance; LINREG: noise sigma */
+    double p0;          /* GAUSS: likelihood sigma; GMM: component variance; LINREG: noise sigma;
+                           UNID: upper end of the uniform priors */
     int32_t on_device;  /* 0: X, y are host memory, copied at init.  1: device memory, also copied
                            (to the padded device layout); the caller may free them after init */
     int32_t contraction;/* how X x is computed (oais_contraction):

@@ -37,7 +37,7 @@ _LIB = os.path.join(_HERE, "liboais_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-GAUSS, LOGREG, GMM, LINREG = 0, 1, 2, 3
+GAUSS, LOGREG, GMM, LINREG, UNID = 0, 1, 2, 3, 4
 RWMH, MALA, HMC, EXACT = 0, 1, 2, 3
 
 
@@ -86,6 +86,8 @@ def _load():
             lib.orc_log_ref.restype = f64
             lib.orc_log_lik.argtypes = [P, P, P]
             lib.orc_log_lik.restype = f64
+            lib.orc_binom_mode_logpmf.argtypes = [f64, f64]
+            lib.orc_binom_mode_logpmf.restype = f64
             lib.orc_logsumexp.argtypes = [P, i64]
             lib.orc_logsumexp.restype = f64
             lib.orc_systematic_resample.argtypes = [i64, P, f64, P]
@@ -118,6 +120,7 @@ class Target:
     kind LOGREG: L(x) = prod_r Bern(y_r | sigmoid(X_r . x)),    X (n, d), y (n,)
     kind GMM   : L(x) = p(x) / eta(x), p = mean_k N(mu_k, p0 I), X = means (K, d)
     kind LINREG: L(x) = prod_r N(y_r; X_r . x, p0^2),           X (n, d), y (n,)
+    kind UNID  : L(z) = Binom(k; m, p0^2 Phi(z_1) Phi(z_2)),     X = (m, k), d = 2, ref_scale 1
     """
 
     def __init__(self, kind, X, y=None, ref_scale=1.0, p0=1.0):
@@ -125,6 +128,8 @@ class Target:
         self.X = _f64(X)
         if self.kind == GAUSS:
             self.d, self.n = self.X.shape[0], 0
+        elif self.kind == UNID:
+            self.d, self.n = 2, 0
         else:
             self.n, self.d = self.X.shape
         self.y = None if y is None else _f64(y)
@@ -143,6 +148,11 @@ class Target:
 
     def log_ref(self, x):
         return _load().orc_log_ref(ctypes.byref(self._c), _ptr(_f64(x)))
+
+
+def binom_mode_logpmf(m, k):
+    """log Binom(k; m, k/m): log-gamma below a million counts, Stirling's series above."""
+    return _load().orc_binom_mode_logpmf(float(m), float(k))
 
 
 def philox4x32_10(ctr, key):

@@ -108,17 +108,35 @@ double orc_resample_uniform(uint64_t seed, uint32_t t, uint32_t tag)
 /* Targets: path gamma_beta = eta^(1-beta) gamma^beta = eta * L^beta     */
 /* (Sec. 2, geometric path), with eta = N(0, s^2 I) and gamma = eta * L. */
 /* ------------------------------------------------------------------ */
-enum { ORC_GAUSS = 0, ORC_LOGREG = 1, ORC_GMM = 2, ORC_LINREG = 3 };
+enum { ORC_GAUSS = 0, ORC_LOGREG = 1, ORC_GMM = 2, ORC_LINREG = 3, ORC_UNID = 4 };
 
 typedef struct {
     int kind;
     int d;            /* state dimension */
     int n;            /* data rows (LOGREG, LINREG) or mixture components (GMM) */
-    const double* X;  /* LOGREG/LINREG: n x d row-major; GMM: n x d means; GAUSS: mu (d) */
+    const double* X;  /* LOGREG/LINREG: n x d row-major; GMM: n x d means; GAUSS: mu (d);
+                         UNID: (m, k) trials and successes */
     const double* y;  /* LOGREG: labels in {0,1}; LINREG: responses */
     double ref_scale; /* s: eta = N(0, s^2 I) */
-    double p0;        /* GAUSS: sigma of the likelihood; GMM: component variance; LINREG: noise sigma */
+    double p0;        /* GAUSS: sigma of the likelihood; GMM: component variance; LINREG: noise sigma;
+                         UNID: upper end b of the uniform priors */
 } orc_target;
+
+/* log of the binomial probability of k successes in m trials at the success rate k/m:
+ * log C(m, k) + k log(k/m) + (m - k) log(1 - k/m).  Log-gamma for moderate counts; for
+ * counts of a million and more Stirling's series (each log-gamma expanded to its 1/(12x)
+ * term, the rest O(1/min(k, m-k)^3)), which keeps the O(1) result free of the cancellation
+ * of terms of size m log m. */
+double orc_binom_mode_logpmf(double m, double k)
+{
+    const double q = k / m;
+    if (k < 1e6 || m - k < 1e6)
+        return lgamma(m + 1.0) - lgamma(k + 1.0) - lgamma(m - k + 1.0) + k * log(q) + (m - k) * log1p(-q);
+    return -0.5 * log(2.0 * ORC_PI * m * q * (1.0 - q)) + 1.0 / (12.0 * m) - 1.0 / (12.0 * k) -
+           1.0 / (12.0 * (m - k));
+}
+
+static double std_normal_cdf(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
 
 static double dot(const double* a, const double* b, int d)
 {
@@ -200,6 +218,27 @@ double orc_log_lik(const orc_target* tg, const double* x, double* grad)
             if (grad) for (int i = 0; i < d; ++i) grad[i] += res * xr[i] / sig2;
         }
         return -0.5 * n * log(2.0 * ORC_PI * sig2) - 0.5 * acc / sig2;
+    }
+    case ORC_UNID: {
+        /* the unidentifiable product model (the paper's model appendix, its GPU workload
+         * "Unid"): X, Y ~ Uniform(0, b), K ~ Binomial(m, X Y).  State z in R^2 under N(0, I),
+         * X = b Phi(z_1), Y = b Phi(z_2).  log L = log Binom(k; m, p), p = X Y, -inf outside
+         * (0, 1); by the identity log Binom(k; m, p) = log Binom(k; m, q) - m D(q || p), q = k/m,
+         * D(q || p) = q log(q/p) + (1 - q) log((1 - q)/(1 - p)) the Bernoulli KL divergence
+         * (written with log1p of the relative differences). */
+        const double m = tg->X[0], k = tg->X[1], b = tg->p0, q = k / m;
+        const double u1 = std_normal_cdf(x[0]), u2 = std_normal_cdf(x[1]);
+        const double p = b * b * u1 * u2;
+        if (!(p > 0.0 && p < 1.0)) return -INFINITY;
+        const double D = -q * log1p((p - q) / q) - (1.0 - q) * log1p((q - p) / (1.0 - q));
+        if (grad) {
+            const double dldp = k / p - (m - k) / (1.0 - p);
+            const double phi1 = exp(-0.5 * x[0] * x[0]) / sqrt(2.0 * ORC_PI);
+            const double phi2 = exp(-0.5 * x[1] * x[1]) / sqrt(2.0 * ORC_PI);
+            grad[0] = dldp * b * b * phi1 * u2;
+            grad[1] = dldp * b * b * u1 * phi2;
+        }
+        return orc_binom_mode_logpmf(m, k) - m * D;
     }
     }
     return NAN;
@@ -389,11 +428,12 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
     for (int t = 1; t <= T; ++t) {
         double db = beta[t] - beta[t - 1];
         /* g_t^n = gamma_{beta_t}(X_{t-1}^n) / gamma_{beta_{t-1}}(X_{t-1}^n) = L(X_{t-1}^n)^(db) */
-        for (long n = 0; n < N; ++n) logg[n] = db * ell[n];
+        /* L^0 = 1, also where L = 0 (a state outside the support) */
+        for (long n = 0; n < N; ++n) logg[n] = db == 0.0 ? 0.0 : db * ell[n];
         /* moments g_hat_{t,i} = sum_n w_{t-1}^n (g_t^n)^i, as logarithms */
         if (log_ghat) {
             for (int i = 0; i < 3; ++i) {
-                for (long n = 0; n < N; ++n) tmp[n] = logw[n] + i * logg[n];
+                for (long n = 0; n < N; ++n) tmp[n] = i == 0 ? logw[n] : logw[n] + i * logg[n];
                 log_ghat[(size_t)(t - 1) * 3 + i] = orc_logsumexp(tmp, N);
             }
         }
@@ -403,7 +443,10 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
         if (elbo_t) {
             const double lse = orc_logsumexp(logw, N);
             double e = 0.0;
-            for (long n = 0; n < N; ++n) e += exp(logw[n] - lse) * logg[n];
+            for (long n = 0; n < N; ++n) {
+                const double W = exp(logw[n] - lse);
+                if (W > 0.0) e += W * logg[n];   /* a zero weight adds nothing, even with g = 0 */
+            }
             elbo_t[t - 1] = e;
         }
         /* reweight: w_{t^-} = w_{t-1} g_t */

@@ -26,9 +26,13 @@ cudaError_t launch_fisher(const double* logw, const double* ell, const void* x, 
 cudaError_t launch_logsumexp(const double*, int64_t, double*, void*, cudaStream_t);
 size_t logsumexp_scratch_bytes(int64_t n);
 
+// the families whose particles and arithmetic are fp64 (the others run in fp32)
+static bool f64_kind(int kind) { return kind == kGauss || kind == kUnid; }
+
 int padded_width(int kind, int d)
 {
     static const int gauss[] = {1, 2, 4, 8, 16}, rows[] = {2, 4, 8, 16, 32}, gmm[] = {2, 4, 8, 16};
+    if (kind == kUnid) return d == 2 ? 2 : 0;
     const int* w = rows; int nw = 5;
     if (kind == kGauss) { w = gauss; nw = 5; }
     else if (kind == kGmm) { w = gmm; nw = 4; }
@@ -191,7 +195,7 @@ static oais_status fail(oais_ctx* ctx, oais_status s, const std::string& m)
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-static size_t elt_bytes(int kind) { return kind == kGauss ? sizeof(double) : sizeof(float); }
+static size_t elt_bytes(int kind) { return f64_kind(kind) ? sizeof(double) : sizeof(float); }
 
 struct Layout {
     size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, elbo, lse, lse_scr, status;
@@ -218,6 +222,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes ? bytes : 1); return o; };
     size_t xb;
     if (tg->kind == kGauss) xb = sizeof(double) * D;
+    else if (tg->kind == kUnid) xb = sizeof(double) * 4;   // m, k, b, c0
     else if (tg->kind == kGmm) xb = sizeof(float) * (size_t)tg->n * D;
     else xb = sizeof(float) * (size_t)n_pad * D;
     L.X = take(xb);
@@ -263,10 +268,21 @@ static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais
                                 int T_max, int* D)
 {
     if (!tg || !mv) return fail(ctx, OAIS_EINVAL, "null target or move");
-    if (tg->kind < 0 || tg->kind > 3) return fail(ctx, OAIS_EINVAL, "unknown target kind");
+    if (tg->kind < 0 || tg->kind > 4) return fail(ctx, OAIS_EINVAL, "unknown target kind");
     if (tg->d < 1 || !tg->X) return fail(ctx, OAIS_EINVAL, "bad dimension or missing X");
     if (!(tg->ref_scale > 0) || !(tg->p0 > 0)) return fail(ctx, OAIS_EINVAL, "ref_scale and p0 must be > 0");
-    if (tg->kind != kGauss && tg->n < 1) return fail(ctx, OAIS_EINVAL, "n must be >= 1");
+    if (!f64_kind(tg->kind) && tg->n < 1) return fail(ctx, OAIS_EINVAL, "n must be >= 1");
+    if (tg->kind == kUnid) {
+        if (tg->d != 2 || tg->ref_scale != 1.0 || tg->dtype != OAIS_DT_F64)
+            return fail(ctx, OAIS_EINVAL, "UNID: d = 2, ref_scale = 1 and float64 (m, k)");
+        if (tg->contraction != OAIS_CONTRACT_FP32)
+            return fail(ctx, OAIS_EUNSUPPORTED, "UNID runs on the CUDA-core form");
+        if (!tg->on_device) {
+            const double* mk = static_cast<const double*>(tg->X);
+            if (!(mk[0] >= 1.0 && mk[1] > 0.0 && mk[1] < mk[0]))
+                return fail(ctx, OAIS_EINVAL, "UNID: trials m >= 1 and successes 0 < k < m");
+        }
+    }
     if ((tg->kind == kLogreg || tg->kind == kLinreg) && !tg->y) return fail(ctx, OAIS_EINVAL, "missing y");
     if (tg->kind == kGmm && tg->n > GmmTarget<float, 16>::kMaxK)
         return fail(ctx, OAIS_EUNSUPPORTED, "at most 16 mixture components");
@@ -395,7 +411,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     }
     char* b = static_cast<char*>(ctx->ws);
     DevTarget& dt = ctx->dt;
-    dt.kind = tg->kind; dt.d = tg->d; dt.D = D; dt.n = tg->kind == kGauss ? 0 : tg->n;
+    dt.kind = tg->kind; dt.d = tg->d; dt.D = D; dt.n = f64_kind(tg->kind) ? 0 : tg->n;
     dt.n_pad = (dt.n + 3) & ~3;
     dt.ref_scale = tg->ref_scale; dt.p0 = tg->p0;
     dt.X = b + L.X;
@@ -426,7 +442,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     ctx->d_anc = reinterpret_cast<int64_t*>(b + L.anc);
 
     // data in the padded device layout
-    const int rows = tg->kind == kGauss ? 1 : tg->n;
+    const int rows = f64_kind(tg->kind) ? 1 : tg->n;
     std::vector<double> Xh, yh;
     st = fetch(ctx, tg->X, (size_t)rows * tg->d, tg->dtype, tg->on_device, Xh);
     if (st == OAIS_OK && dt.y) st = fetch(ctx, tg->y, (size_t)tg->n, tg->dtype, tg->on_device, yh);
@@ -436,6 +452,21 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
         std::vector<double> mu(D, 0.0);
         for (int i = 0; i < tg->d; ++i) mu[i] = Xh[i];
         e = cudaMemcpy(dt.X, mu.data(), sizeof(double) * D, cudaMemcpyHostToDevice);
+    } else if (tg->kind == kUnid) {
+        // (m, k, b, c0) with c0 = log Binom(k; m, k/m): Stirling's series for large counts
+        // (-1/2 log(2 pi m q (1 - q)) + 1/(12 m) - 1/(12 k) - 1/(12 (m - k))), log-gamma below
+        const double m = Xh[0], k = Xh[1], q = k / m;
+        double c0;
+        if (std::min(k, m - k) >= 1e6)
+            c0 = -0.5 * std::log(6.283185307179586 * m * q * (1.0 - q)) + 1.0 / (12.0 * m) - 1.0 / (12.0 * k) -
+                 1.0 / (12.0 * (m - k));
+        else
+            c0 = std::lgamma(m + 1.0) - std::lgamma(k + 1.0) - std::lgamma(m - k + 1.0) + k * std::log(q) +
+                 (m - k) * std::log1p(-q);
+        const double par[4] = {m, k, tg->p0, c0};
+        if (!(m >= 1.0 && k > 0.0 && k < m)) { fail(ctx, OAIS_EINVAL, "UNID: trials m >= 1 and successes 0 < k < m");
+                                               g_err = ctx->err; oais_destroy(ctx); return OAIS_EINVAL; }
+        e = cudaMemcpy(dt.X, par, sizeof(par), cudaMemcpyHostToDevice);
     } else {
         const int nr = tg->kind == kGmm ? tg->n : dt.n_pad;
         std::vector<float> Xp((size_t)nr * D, 0.0f), yp(dt.n_pad, 0.0f);
@@ -500,6 +531,7 @@ static cudaError_t launch_sweep(const DevTarget& dt, int move, const SweepParams
 {
     switch (dt.kind) {
     case kGauss: return launch_sweep_gauss(dt, move, P, s);
+    case kUnid: return launch_sweep_unid(dt, move, P, s);
     case kLogreg: return launch_sweep_logreg(dt, move, P, s);
     case kGmm: return launch_sweep_gmm(dt, move, P, s);
     case kLinreg: return launch_sweep_linreg(dt, move, P, s);
@@ -603,6 +635,7 @@ static cudaError_t launch_asmc(const DevTarget& dt, int move, bool init, const S
 {
     switch (dt.kind) {
     case kGauss: return launch_asmc_gauss(dt, move, init, P, s);
+    case kUnid: return launch_asmc_unid(dt, move, init, P, s);
     case kLogreg: return launch_asmc_logreg(dt, move, init, P, s);
     case kGmm: return launch_asmc_gmm(dt, move, init, P, s);
     case kLinreg: return launch_asmc_linreg(dt, move, init, P, s);
@@ -713,7 +746,7 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
             for (int t = 1; t <= T; ++t) {
                 P.t = t;
                 CK(launch_asmc(ctx->dt, ctx->mv.kind, false, P, s));
-                CK(launch_asmc_resample(ctx->d_st, P, grid, ess_frac, ctx->dt.d, grad, ctx->dt.kind == kGauss,
+                CK(launch_asmc_resample(ctx->d_st, P, grid, ess_frac, ctx->dt.d, grad, f64_kind(ctx->dt.kind),
                                         ctx->d_bsum, ctx->d_boff, ctx->d_cdf, ctx->d_ess_trace, ctx->d_resampled,
                                         ctx->d_anc, s));
             }
@@ -1014,13 +1047,14 @@ oais_status oais_grad_logZ(oais_ctx* ctx, double* grad)
     cudaStream_t s = ctx->stream;
     // log-sum-exp of the final weights, then the weighted sums of grad_theta log gamma
     CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
-    CK(launch_fisher(ctx->d_logw, ctx->d_ell, ctx->d_x, ctx->dt.kind == kGauss, ctx->N, ctx->dt.d, ctx->d_lse,
+    CK(launch_fisher(ctx->d_logw, ctx->d_ell, ctx->d_x, f64_kind(ctx->dt.kind), ctx->N, ctx->dt.d, ctx->d_lse,
                      ctx->dt.ref_scale, ctx->dt.kind, ctx->dt.n, ctx->dt.p0, ctx->d_lse_scratch,
                      ctx->d_lse, s));
     double g[2];
     CK(cudaMemcpyAsync(g, ctx->d_lse, sizeof(g), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    grad[0] = g[0];
+    // UNID: the reference is fixed (it makes X and Y uniform), no scale to differentiate
+    grad[0] = ctx->dt.kind == kUnid ? NAN : g[0];
     grad[1] = (ctx->dt.kind == kGauss || ctx->dt.kind == kLinreg) ? g[1] : NAN;
     return OAIS_OK;
 }
@@ -1049,6 +1083,7 @@ oais_status oais_potential(oais_ctx* ctx, const void* d_x, int64_t N, double* d_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (ctx->dt.kind) {
     case kGauss: CK(launch_potential_gauss(ctx->dt, P, s)); break;
+    case kUnid: CK(launch_potential_unid(ctx->dt, P, s)); break;
     case kLogreg: CK(launch_potential_logreg(ctx->dt, P, s)); break;
     case kGmm: CK(launch_potential_gmm(ctx->dt, P, s)); break;
     case kLinreg: CK(launch_potential_linreg(ctx->dt, P, s)); break;

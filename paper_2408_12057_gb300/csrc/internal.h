@@ -89,18 +89,21 @@ int padded_width(int kind, int d);
 
 // launch the sweep for one family; grid = oais_sweep_blocks(P.N)
 cudaError_t launch_sweep_gauss(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s);
+cudaError_t launch_sweep_unid(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s);
 cudaError_t launch_sweep_logreg(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s);
 cudaError_t launch_sweep_gmm(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s);
 cudaError_t launch_sweep_linreg(const DevTarget& t, int move, const SweepParams& P, cudaStream_t s);
 
 // ASMC: init (t = 0) or one annealing step, per family
 cudaError_t launch_asmc_gauss(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
+cudaError_t launch_asmc_unid(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
 cudaError_t launch_asmc_logreg(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
 cudaError_t launch_asmc_gmm(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
 cudaError_t launch_asmc_linreg(const DevTarget& t, int move, bool init, const StepParams& P, cudaStream_t s);
 
 // log L and grad log L for a batch of states, per family
 cudaError_t launch_potential_gauss(const DevTarget& t, const PotentialParams& P, cudaStream_t s);
+cudaError_t launch_potential_unid(const DevTarget& t, const PotentialParams& P, cudaStream_t s);
 cudaError_t launch_potential_logreg(const DevTarget& t, const PotentialParams& P, cudaStream_t s);
 cudaError_t launch_potential_gmm(const DevTarget& t, const PotentialParams& P, cudaStream_t s);
 cudaError_t launch_potential_linreg(const DevTarget& t, const PotentialParams& P, cudaStream_t s);

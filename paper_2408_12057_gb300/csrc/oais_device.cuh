@@ -136,6 +136,16 @@ static_assert(sizeof(StepPartial) == 64, "StepPartial layout");
 
 constexpr int kMaxWarps = 32;
 
+// log g_t = (beta_t - beta_{t-1}) log L(X_{t-1}); a state outside the likelihood's support
+// (log L = -inf) gets weight 0 for any positive increment and keeps its weight for a zero one
+__device__ __forceinline__ double log_increment(double dbeta, double ell)
+{
+    return dbeta == 0.0 ? 0.0 : dbeta * ell;
+}
+// a log-weight or log-likelihood is admissible unless NaN or +inf (-inf: zero weight or a
+// state outside the support)
+__device__ __forceinline__ bool admissible(double v) { return !isnan(v) && v != INFINITY; }
+
 // Warp part: v_i = lw + i * lg for the lane's particle (or -inf if inactive).
 // Writes the warp's (m_i, s_i) for i = 0..2 and u (ws[3], on m_0) through lane 0.  By default the offsets from the
 // anchor particle and from the warp maximum are fp64 differences rounded once.  kFast (the
@@ -147,37 +157,73 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
                                                     double* wm /*3*/, float* ws /*4*/)
 {
     const unsigned full = 0xFFFFFFFFu;
-    // anchor = a representative active value: avoids fp64 max over the warp
-    const unsigned act = __ballot_sync(full, active);
-    if (act == 0) {
-        if ((threadIdx.x & 31) == 0) {
+    const bool lead = (threadIdx.x & 31) == 0;
+    if (kFast) {
+        // the tensor-core kernels: log w and log g finite for every active particle
+        const unsigned act = __ballot_sync(full, active);
+        if (act == 0) {
+            if (lead) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) { wm[i] = -INFINITY; ws[i] = 0.0f; }
-            ws[3] = 0.0f;
+                for (int i = 0; i < 3; ++i) { wm[i] = -INFINITY; ws[i] = 0.0f; }
+                ws[3] = 0.0f;
+            }
+            return;
+        }
+        // anchor = a representative active value: avoids fp64 max over the warp
+        const int src = __ffs(act) - 1;
+        const double a0 = __shfl_sync(full, lw, src), b0 = __shfl_sync(full, lg, src);
+        const float dw = (float)(lw - a0), dg = (float)(lg - b0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float f = active ? dw + (float)i * dg : -INFINITY;
+            float mx = f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
+            float e = active ? __expf(f - mx) : 0.0f;
+            float u = i == 0 ? e * (float)lg : 0.0f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
+            if (i == 0) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
+            }
+            if (lead) {
+                wm[i] = a0 + i * b0 + (double)mx;
+                ws[i] = e;
+                if (i == 0) ws[3] = u;
+            }
         }
         return;
     }
-    const int src = __ffs(act) - 1;
-    const double a0 = __shfl_sync(full, lw, src), b0 = __shfl_sync(full, lg, src);
-    const float dw = kFast ? (float)(lw - a0) : 0.0f, dg = kFast ? (float)(lg - b0) : 0.0f;
+    // per moment, the particles with v_i = lw + i lg > -inf take part (log w or log g may be
+    // -inf: zero weight, or a state outside the likelihood's support); the anchor of moment i
+    // is the first such particle, and an offset is the fp64 difference rounded once
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const double anchor = a0 + i * b0;
-        const double v = lw + i * lg;
-        float f = !active ? -INFINITY : kFast ? dw + (float)i * dg : (float)(v - anchor);
+        const double v = i == 0 ? lw : lw + i * lg;
+        const bool on = active && v > -INFINITY;
+        const unsigned act = __ballot_sync(full, on);
+        if (act == 0) {
+            if (lead) { wm[i] = -INFINITY; ws[i] = 0.0f; if (i == 0) ws[3] = 0.0f; }
+            continue;
+        }
+        const double anchor = __shfl_sync(full, v, __ffs(act) - 1);
+        const float f = on ? (float)(v - anchor) : -INFINITY;
         float mx = f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
         const double M = anchor + (double)mx;
-        float e = !active ? 0.0f : kFast ? __expf(f - mx) : __expf((float)(v - M));
-        float u = i == 0 ? e * (float)lg : 0.0f;
+        float e = on ? __expf((float)(v - M)) : 0.0f;
+        // the ELBO sum: a weighted particle outside the support (log g = -inf) makes it -inf;
+        // a weight that underflowed to 0 adds nothing
+        float u = (i == 0 && e > 0.0f) ? e * (float)lg : 0.0f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
         if (i == 0) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
         }
-        if ((threadIdx.x & 31) == 0) {
+        if (lead) {
             wm[i] = M;
             ws[i] = e;
             if (i == 0) ws[3] = u;
@@ -215,7 +261,7 @@ __device__ __forceinline__ void merge_lane_pieces(int lane, const double (&mj)[3
         if (kFast) {
             const float dj = (float)(m - M);      // -inf for an empty piece; NaN when every piece is
             const float fj = (lane < W && !isnan(dj)) ? expf(dj) : 0.0f;
-            float v = sj[i] * fj, uu = i == 0 ? sj[3] * fj : 0.0f;
+            float v = sj[i] * fj, uu = (i == 0 && fj > 0.0f) ? sj[3] * fj : 0.0f;
 #pragma unroll
             for (int o = 1; o < W; o <<= 1) {
                 v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
@@ -225,7 +271,7 @@ __device__ __forceinline__ void merge_lane_pieces(int lane, const double (&mj)[3
             if (i == 0) rec.u = (double)uu;
         } else {
             const double fj = (lane < W && m != -INFINITY) ? exp(m - M) : 0.0;
-            double v = (double)sj[i] * fj, uu = i == 0 ? (double)sj[3] * fj : 0.0;
+            double v = (double)sj[i] * fj, uu = (i == 0 && fj > 0.0) ? (double)sj[3] * fj : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 v += __shfl_xor_sync(0xFFFFFFFFu, v, o);

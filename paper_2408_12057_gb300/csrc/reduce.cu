@@ -11,13 +11,15 @@ namespace oais {
 
 constexpr int kMergeThreads = 256;
 
-// merge of (m, s, u): exp(m) s + exp(m') s' with u carried on the same shift as s
+// merge of (m, s, u): exp(m) s + exp(m') s' with u carried on the same shift as s (a part
+// whose factor underflows to 0 adds nothing to u, even a -inf one)
+__device__ __forceinline__ double scaled(double u, double f) { return f > 0.0 ? u * f : 0.0; }
 __device__ __forceinline__ void lse_merge_u(double& m, double& s, double& u, double m2, double s2, double u2)
 {
     if (m2 == -INFINITY) return;
     if (m == -INFINITY) { m = m2; s = s2; u = u2; return; }
-    if (m2 > m) { const double f = exp(m - m2); s = s * f + s2; u = u * f + u2; m = m2; }
-    else        { const double f = exp(m2 - m); s = s + s2 * f; u = u + u2 * f; }
+    if (m2 > m) { const double f = exp(m - m2); s = s * f + s2; u = scaled(u, f) + u2; m = m2; }
+    else        { const double f = exp(m2 - m); s = s + s2 * f; u = u + scaled(u2, f); }
 }
 
 // one CTA per step t: log g_hat_{t,i}, the acceptance rate and (elbo != null) the ELBO term

@@ -157,7 +157,7 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
     for (int t = 1; t <= P.T; ++t) {
         const double beta_t = __ldg(P.beta + t);
         const double eps_t = __ldg(P.eps + t - 1);
-        const double lg = (beta_t - beta_prev) * (double)ell;
+        const double lg = log_increment(beta_t - beta_prev, (double)ell);
         beta_prev = beta_t;
         const int slot = t & 1;
         warp_moment_partial(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
@@ -174,7 +174,7 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
         cta_moment_record<kSweepThreads / 32>(s_m[slot], s_s[slot], s_acc[slot],
                                               P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
     }
-    if (!isfinite(logw) || !isfinite((double)ell)) bad = 1;
+    if (!admissible(logw) || !admissible((double)ell)) bad = 1;
     if (active) {
         P.logw[n64] = logw;
         P.ell_out[n64] = (double)ell;
@@ -252,7 +252,7 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     double logw = P.logw[idx];
 
     const double beta_t = P.beta[P.t], eps_t = P.eps[P.t - 1];
-    const double lg = (beta_t - P.beta[P.t - 1]) * (double)ell;
+    const double lg = log_increment(beta_t - P.beta[P.t - 1], (double)ell);
     warp_moment_partial(logw, lg, active, s_m[warp], s_s[warp]);
     logw += lg;
     unsigned acc = 0;
@@ -283,7 +283,7 @@ asmc_step_kernel(const StepParams P, Tgt tg)
         }
         P.ell[b][n64] = (double)ell;
         P.logw[n64] = logw;
-        if (!isfinite(logw) || !isfinite((double)ell)) atomicOr(P.status, 1u);
+        if (!admissible(logw) || !admissible((double)ell)) atomicOr(P.status, 1u);
     }
 }
 

@@ -7,7 +7,7 @@
 
 namespace oais {
 
-enum TargetKind { kGauss = 0, kLogreg = 1, kGmm = 2, kLinreg = 3 };
+enum TargetKind { kGauss = 0, kLogreg = 1, kGmm = 2, kLinreg = 3, kUnid = 4 };
 
 // -------------------------------------------------------------------------
 // Conjugate Gaussian likelihood L(x) = exp(-|x - mu|^2 / (2 sigma^2)).
@@ -36,6 +36,47 @@ struct GaussTarget {
             if (GRAD) g[i] = -r * inv_sig2;
         }
         return R(-0.5) * acc * inv_sig2;
+    }
+};
+
+// -------------------------------------------------------------------------
+// Unidentifiable product parameterisation (the paper's GPU workload "Unid", its model
+// appendix): X, Y ~ Uniform(0, b), K | X, Y ~ Binomial(m, X Y).  The state is z in R^2 under
+// the reference N(0, I): X = b Phi(z_1), Y = b Phi(z_2) are then Uniform(0, b), so the path
+// eta L^beta has the model's Z.  log L = log Binom(k; m, p) with p = X Y, -inf where p is
+// not in (0, 1).  It is evaluated as c0 - m D(p^ || p), p^ = k / m, c0 = log Binom(k; m, p^)
+// (precomputed on the host), D the Bernoulli KL divergence in log1p form: with m = 10^11
+// the terms are ~10^10 and their differences O(1), which fp64 keeps.
+// -------------------------------------------------------------------------
+template <typename R, int D>
+struct UnidTarget {
+    static constexpr int kind = kUnid;
+    const double* par;   // [4] in global memory: m, k, b, c0
+    int d;
+    double m, k, b, c0, ph;
+
+    __device__ void setup(unsigned char*) {
+        m = par[0]; k = par[1]; b = par[2]; c0 = par[3];
+        ph = k / m;
+    }
+    static constexpr size_t smem_bytes(int) { return 0; }
+
+    template <bool GRAD>
+    __device__ R eval(const R (&x)[D], R (&g)[D]) const {
+        static_assert(D == 2, "the Unid state is two-dimensional");
+        const double u1 = normcdf((double)x[0]), u2 = normcdf((double)x[1]);
+        const double p = b * b * u1 * u2;
+        if (GRAD) { g[0] = R(0); g[1] = R(0); }
+        if (!(p > 0.0 && p < 1.0)) return R(-INFINITY);
+        const double dkl = -ph * log1p((p - ph) / ph) - (1.0 - ph) * log1p((ph - p) / (1.0 - ph));
+        if (GRAD) {
+            // d log L / dp = (k - m p) / (p (1 - p)); dp/dz_i = b^2 phi(z_i) u_j
+            const double dldp = (k - m * p) / (p * (1.0 - p));
+            const double c = 0.39894228040143268 * b * b;   // b^2 / sqrt(2 pi)
+            g[0] = R(dldp * c * u2 * exp(-0.5 * (double)x[0] * (double)x[0]));
+            g[1] = R(dldp * c * u1 * exp(-0.5 * (double)x[1] * (double)x[1]));
+        }
+        return R(c0 - m * dkl);
     }
 };
 

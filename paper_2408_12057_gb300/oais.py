@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _build
 
-GAUSS, LOGREG, GMM, LINREG = 0, 1, 2, 3
+GAUSS, LOGREG, GMM, LINREG, UNID = 0, 1, 2, 3, 4
 RWMH, MALA, HMC = 0, 1, 2
 DT_F64, DT_F32 = 0, 1
 CONTRACT_FP32, CONTRACT_BF16_TC, CONTRACT_BF16_TC_STREAM, CONTRACT_FP8_TC_STREAM = 0, 1, 2, 3
@@ -156,6 +156,12 @@ def default_step_sizes(problem, beta, move_kind):
         curv = 0.25 * float((np.asarray(problem.X, dtype=np.float64) ** 2).sum()) / d
     elif problem.kind == LINREG:
         curv = float((np.asarray(problem.X, dtype=np.float64) ** 2).sum()) / d / problem.p0 ** 2
+    elif problem.kind == UNID:
+        # the ridge p = const is ~ sqrt(q (1 - q) / m) wide in p; in z that is about the
+        # ridge width over (dp / dz ~ p)
+        m, k = float(problem.X[0]), float(problem.X[1])
+        q = k / m
+        curv = m / (q * (1.0 - q)) * q * q
     else:
         curv = 1.0 / problem.p0
     scale = 1.0 / np.sqrt(1.0 / problem.ref_scale ** 2 + beta * curv)
@@ -178,7 +184,7 @@ class OAIS:
         self.T_max = int(T_max if T_max is not None else T)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         kind = problem.kind
-        dtype = DT_F64 if kind == GAUSS else DT_F32
+        dtype = DT_F64 if kind in (GAUSS, UNID) else DT_F32
         npdt = np.float64 if dtype == DT_F64 else np.float32
         X = np.ascontiguousarray(problem.X, dtype=npdt)
         y = None if problem.y is None else np.ascontiguousarray(problem.y, dtype=npdt)
@@ -350,7 +356,7 @@ class OAIS:
             off = ptr - base
             return self.workspace[off:off + count * esz].view(dtype)
 
-        xdt = torch.float64 if self.problem.kind == GAUSS else torch.float32
+        xdt = torch.float64 if self.problem.kind in (GAUSS, UNID) else torch.float32
         return (view(pl.value, torch.float64, N), view(pe.value, torch.float64, N),
                 view(px.value, xdt, d * N).view(d, N))
 

@@ -25,7 +25,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-GAUSS, LOGREG, GMM, LINREG = 0, 1, 2, 3
+GAUSS, LOGREG, GMM, LINREG, UNID = 0, 1, 2, 3, 4
 
 
 def data_seed(cfg: int) -> int:
@@ -40,10 +40,12 @@ def run_seed(replicate: int = 0) -> int:
 class Problem:
     """One target on the geometric path eta * L^beta, eta = N(0, ref_scale^2 I).
 
-    kind   GAUSS / LOGREG / GMM / LINREG
-    X      GAUSS: mu (d,); LOGREG/LINREG: design (n, d); GMM: means (K, d)
+    kind   GAUSS / LOGREG / GMM / LINREG / UNID
+    X      GAUSS: mu (d,); LOGREG/LINREG: design (n, d); GMM: means (K, d);
+           UNID: (m, k) trials and successes (d = 2)
     y      LOGREG labels {0,1} / LINREG responses (n,), else None
-    p0     GAUSS: likelihood sigma; GMM: component variance; LINREG: noise sigma
+    p0     GAUSS: likelihood sigma; GMM: component variance; LINREG: noise sigma;
+           UNID: upper end b of the uniform priors
     """
     kind: int
     X: np.ndarray
@@ -55,11 +57,13 @@ class Problem:
 
     @property
     def d(self) -> int:
+        if self.kind == UNID:
+            return 2
         return int(self.X.shape[0] if self.kind == GAUSS else self.X.shape[1])
 
     @property
     def n(self) -> int:
-        return 0 if self.kind == GAUSS else int(self.X.shape[0])
+        return 0 if self.kind in (GAUSS, UNID) else int(self.X.shape[0])
 
 
 def gauss_conj(d: int = 8, sigma: float = 0.5, mu_scale: float = 2.0, seed: int | None = None,
@@ -69,6 +73,15 @@ def gauss_conj(d: int = 8, sigma: float = 0.5, mu_scale: float = 2.0, seed: int 
         mu = rng.normal(0.0, mu_scale, size=d)
     return Problem(GAUSS, np.asarray(mu, dtype=np.float64), None, 1.0, sigma,
                    name=f"gauss_conj_d{d}")
+
+
+def unid(m: float = 1e11, k: float = 1e10, b: float = 10.0) -> Problem:
+    """The unidentifiable product parameterisation (the paper's model appendix; its GPU
+    experiments use m = 10^11 trials and k = 10^10 successes): X, Y ~ Uniform(0, b),
+    K | X, Y ~ Binomial(m, X Y).  The state is z in R^2 under N(0, I) with X = b Phi(z_1),
+    Y = b Phi(z_2); no data beyond (m, k)."""
+    return Problem(UNID, np.array([float(m), float(k)]), None, 1.0, float(b),
+                   name=f"unid_m{m:.0e}_k{k:.0e}")
 
 
 def annealed_mvn(d: int = 5, tau: float = 5.0, tau0: float = 1.0) -> Problem:
