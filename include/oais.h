@@ -174,6 +174,20 @@ oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out);
  * OptimiseSchedule(T_next, ...) like oais_round.  Same errors as oais_round. */
 oais_status oasmc_round(oais_ctx* ctx, int32_t T_next, double ess_frac, oais_round_result* out);
 
+/* The online conditional-ESS comparator of the paper's section on the connection to online
+ * CESS optimisation (Zhou, Johansen & Aston 2016, "ZJA"; the method the paper's GPU
+ * experiments compare against): like oasmc_round, but before step t the next annealing
+ * parameter is chosen on the device so that CESS_t / N = (sum_n W_n g_n)^2 / sum_n W_n g_n^2
+ * = cess_frac, g_n = L(X_{t-1}^n)^(beta_t - beta_{t-1}), W the normalised weights since the last
+ * resampling (the paper matches budgets with cess_frac = exp(-Lambda^2 / T^2)).  The line
+ * search refines a bracket of beta_t - beta_{t-1} in four passes of 32 candidates, keeping the
+ * last candidate meeting the target.  The run ends at beta = 1 or after T_max steps (the last
+ * forced to beta = 1); step sizes are the current schedule's, log eps interpolated linearly
+ * in beta.  ess_frac as in oasmc_round.  The schedule that ran becomes the round's
+ * (oais_get_stats), and OptimiseSchedule(T_next, ...) of its moments the next one.  CUDA-core
+ * form only (EUNSUPPORTED otherwise); not on a shard (EUNSUPPORTED). */
+oais_status oais_zja_round(oais_ctx* ctx, double cess_frac, double ess_frac, int32_t T_next, oais_round_result* out);
+
 /* Resampling record of the last oasmc_round: ess [T] (ESS of w_{t^-} at every step),
  * resampled [T] (1 where a segment closed, including t = T), ancestors [N] (int64, the
  * ancestor indices of the last intermediate event; undefined if there was none).

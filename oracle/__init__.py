@@ -21,6 +21,8 @@ Function map (paper passage each one follows):
   pchip                monotone interpolation used by Alg. 3
   fisher_grad          grad_theta log Z = E_pi[grad_theta log gamma] with the
                        weighted estimator of eq. estimator_pi_t
+  zja                  the online conditional-ESS comparator (section on the
+                       connection to online CESS optimisation)
 """
 from __future__ import annotations
 
@@ -94,6 +96,11 @@ def _load():
             lib.orc_asmc.argtypes = [P, P, i64, i32, P, P, u64, u32, i64, f64,
                                      P, P, P, P, P, P, P, P, P, P]
             lib.orc_asmc.restype = i32
+            lib.orc_zja.argtypes = [P, P, i64, i32, P, P, i32, f64, f64, u64, u32,
+                                    P, P, P, P, P, P, P, P, P, P]
+            lib.orc_zja.restype = i32
+            lib.orc_zja_next_beta.argtypes = [i64, P, P, f64, f64, i32, i32]
+            lib.orc_zja_next_beta.restype = f64
             lib.orc_pchip_slopes.argtypes = [i32, P, P, P]
             lib.orc_pchip_eval.argtypes = [i32, P, P, P, f64]
             lib.orc_pchip_eval.restype = f64
@@ -223,6 +230,43 @@ def asmc(target: Target, move_kind, N, beta, eps, seed, tag=0, moves=1, leapfrog
     out["elbo"] = float(out["elbo_t"].sum())
     out["kl"] = out["logZ"] - out["elbo"]
     return out
+
+
+def zja(target: Target, move_kind, N, T_max, beta_ref, eps_ref, cess_frac, seed, tag=0, moves=1,
+        leapfrog=1, cycle=False, ess_frac=0.0):
+    """The online conditional-ESS comparator (section on the connection to online CESS
+    optimisation): the schedule is found step by step so that CESS / N = cess_frac (line search
+    of four passes over 32 candidates), step sizes interpolated from (beta_ref, eps_ref); then
+    the steps of Alg. 1.  Returns a dict with logZ, T, beta (T+1,), eps (T,), log_ghat (T,3),
+    elbo_t (T,), logw, x, ell, margin, n_resample."""
+    lib = _load()
+    beta_ref = _f64(beta_ref)
+    T_ref = beta_ref.size - 1
+    eps_ref = _f64(np.broadcast_to(np.asarray(eps_ref, dtype=np.float64), (T_ref,)))
+    mv = _Move(int(move_kind), int(moves), int(leapfrog), int(bool(cycle)))
+    res = _Result()
+    Tout = ctypes.c_int()
+    out = dict(beta=np.zeros(T_max + 1), eps=np.zeros(T_max), log_ghat=np.zeros((T_max, 3)),
+               logw=np.zeros(N), x=np.zeros((N, target.d)), ell=np.zeros(N), margin=np.zeros(N),
+               elbo_t=np.zeros(T_max))
+    rc = lib.orc_zja(ctypes.byref(target._c), ctypes.byref(mv), int(N), int(T_max), _ptr(beta_ref),
+                     _ptr(eps_ref), int(T_ref), float(cess_frac), float(ess_frac), int(seed), int(tag),
+                     ctypes.byref(res), ctypes.byref(Tout), _ptr(out["beta"]), _ptr(out["eps"]),
+                     _ptr(out["log_ghat"]), _ptr(out["logw"]), _ptr(out["x"]), _ptr(out["ell"]),
+                     _ptr(out["margin"]), _ptr(out["elbo_t"]))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    T = Tout.value
+    out.update(beta=out["beta"][:T + 1], eps=out["eps"][:T], log_ghat=out["log_ghat"][:T],
+               elbo_t=out["elbo_t"][:T], T=T, logZ=res.logZ, n_resample=res.n_resample)
+    return out
+
+
+def zja_next_beta(logw, ell, beta_prev, cess_frac, t=1, T_max=1 << 30):
+    """The line search alone: beta_t from the particles' log-weights and log-likelihoods."""
+    logw, ell = _f64(logw), _f64(ell)
+    return _load().orc_zja_next_beta(logw.size, _ptr(logw), _ptr(ell), float(beta_prev), float(cess_frac),
+                                     int(t), int(T_max))
 
 
 def pchip(xk, yk):

@@ -517,6 +517,176 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
 }
 
 /* ------------------------------------------------------------------ */
+/* The online conditional-ESS schedule of Zhou, Johansen & Aston (2016), */
+/* the comparator of the section on the connection to online CESS        */
+/* optimisation: before step t, beta_t is chosen so that                  */
+/* CESS_t / N = (sum W g)^2 / (sum W g^2) = cess_frac, g = L^(beta_t -    */
+/* beta_{t-1}), W the normalised weights since the last resampling.       */
+/* Line search (a reading): a bracket of delta = beta_t - beta_{t-1},     */
+/* initially [0, 1 - beta_{t-1}], refined in four passes over the 32      */
+/* candidates lo + (hi - lo) j / 32, j = 1..32, keeping the last one that  */
+/* meets the target; the step is the final lower end (the first candidate */
+/* of the last pass if that is 0), or the whole interval when its end     */
+/* meets the target.  Step sizes: log eps interpolated linearly in beta   */
+/* through the points (beta_ref[t], eps_ref[t-1]), constant beyond.        */
+/* Then the ASMC step of orc_asmc; the step with beta_t = 1 (forced at     */
+/* t = T_max) closes the last segment.                                    */
+/* ------------------------------------------------------------------ */
+static double lse_shift(const double* lw, const double* ell, double k, double delta, long N)
+{
+    /* log sum_n exp(lw_n + k delta ell_n), zero weights and (k > 0) zero likelihoods skipped */
+    double mx = -INFINITY;
+    for (long n = 0; n < N; ++n) {
+        if (lw[n] == -INFINITY || (k > 0.0 && ell[n] == -INFINITY)) continue;
+        const double v = k > 0.0 ? lw[n] + k * delta * ell[n] : lw[n];
+        if (v > mx) mx = v;
+    }
+    if (mx == -INFINITY) return -INFINITY;
+    double s = 0.0;
+    for (long n = 0; n < N; ++n) {
+        if (lw[n] == -INFINITY || (k > 0.0 && ell[n] == -INFINITY)) continue;
+        s += exp((k > 0.0 ? lw[n] + k * delta * ell[n] : lw[n]) - mx);
+    }
+    return mx + log(s);
+}
+
+static double zja_step_size(double b, const double* beta_ref, const double* eps_ref, int T_ref)
+{
+    if (T_ref <= 1 || b <= beta_ref[1]) return eps_ref[0];
+    if (b >= beta_ref[T_ref]) return eps_ref[T_ref - 1];
+    int t = 1;
+    while (t + 1 < T_ref && beta_ref[t + 1] <= b) ++t;
+    const double u = (b - beta_ref[t]) / (beta_ref[t + 1] - beta_ref[t]);
+    return exp(log(eps_ref[t - 1]) + u * (log(eps_ref[t]) - log(eps_ref[t - 1])));
+}
+
+/* the next annealing parameter from the particles' log-weights and log-likelihoods */
+double orc_zja_next_beta(long N, const double* logw, const double* ell, double beta_prev, double cess_frac,
+                         int t, int T_max)
+{
+    double lo = 0.0, hi = 1.0 - beta_prev, delta = 0.0;
+    const double l0 = lse_shift(logw, ell, 0.0, 0.0, N), lt = log(cess_frac);
+    for (int pass = 0; pass < 4; ++pass) {
+        const double w = hi - lo;
+        int best = 0;
+        for (int j = 1; j <= 32; ++j) {
+            const double dj = lo + w * j / 32.0;
+            const double ratio = 2.0 * lse_shift(logw, ell, 1.0, dj, N) - l0 - lse_shift(logw, ell, 2.0, dj, N);
+            if (ratio >= lt) best = j;
+        }
+        if (best == 32) { delta = hi; break; }
+        const double nlo = lo + w * best / 32.0, nhi = lo + w * (best + 1) / 32.0;
+        if (pass == 3) { delta = nlo > 0.0 ? nlo : lo + w / 32.0; break; }
+        lo = nlo;
+        hi = nhi;
+    }
+    double bt = beta_prev + delta;
+    if (bt >= 1.0 - 1e-12 || t >= T_max) bt = 1.0;
+    return bt;
+}
+
+int orc_zja(const orc_target* tg, const orc_move* mv, long N, int T_max, const double* beta_ref,
+            const double* eps_ref, int T_ref, double cess_frac, double ess_frac, uint64_t seed, uint32_t tag,
+            /* outputs */
+            orc_result* res, int* T_out, double* beta /* T_max + 1 */, double* eps /* T_max */,
+            double* log_ghat /* T_max x 3 */, double* logw_out /* N */, double* x_out /* N x d */,
+            double* ell_out /* N */, double* margin_out /* N */, double* elbo_t /* T_max */)
+{
+    const int d = tg->d;
+    int need_grad = (mv->kind != ORC_RWMH);
+    double* X = (double*)malloc(sizeof(double) * N * d);
+    double* G = (double*)malloc(sizeof(double) * N * d);
+    double* ell = (double*)malloc(sizeof(double) * N);
+    double* logw = (double*)malloc(sizeof(double) * N);
+    double* logg = (double*)malloc(sizeof(double) * N);
+    double* tmp = (double*)malloc(sizeof(double) * N);
+    double* margin = (double*)malloc(sizeof(double) * N);
+    if (!X || !G || !ell || !logw || !logg || !tmp || !margin) return -1;
+    for (long n = 0; n < N; ++n) {
+        orc_normals(seed, (uint32_t)n, 0u, 0u, tag, d, X + n * d);
+        for (int i = 0; i < d; ++i) X[n * d + i] *= tg->ref_scale;
+        ell[n] = orc_log_lik(tg, X + n * d, need_grad ? G + n * d : NULL);
+        logw[n] = 0.0;
+        margin[n] = INFINITY;
+    }
+    double logZ = 0.0;
+    int n_res = 0, T = 0;
+    beta[0] = 0.0;
+    for (int t = 1; t <= T_max; ++t) {
+        beta[t] = orc_zja_next_beta(N, logw, ell, beta[t - 1], cess_frac, t, T_max);
+        eps[t - 1] = zja_step_size(beta[t], beta_ref, eps_ref, T_ref);
+        const double db = beta[t] - beta[t - 1];
+        for (long n = 0; n < N; ++n) logg[n] = db == 0.0 ? 0.0 : db * ell[n];
+        if (log_ghat) {
+            for (int i = 0; i < 3; ++i) {
+                for (long n = 0; n < N; ++n) tmp[n] = i == 0 ? logw[n] : logw[n] + i * logg[n];
+                log_ghat[(size_t)(t - 1) * 3 + i] = orc_logsumexp(tmp, N);
+            }
+        }
+        if (elbo_t) {
+            const double lse = orc_logsumexp(logw, N);
+            double e = 0.0;
+            for (long n = 0; n < N; ++n) {
+                const double W = exp(logw[n] - lse);
+                if (W > 0.0) e += W * logg[n];
+            }
+            elbo_t[t - 1] = e;
+        }
+        for (long n = 0; n < N; ++n) logw[n] += logg[n];
+        #pragma omp parallel for schedule(static)
+        for (long n = 0; n < N; ++n) {
+            double work[6 * 512];
+            double* wk = (d <= 512) ? work : (double*)malloc(sizeof(double) * 6 * d);
+            particle_ref p = {X + n * d, ell[n], G + n * d};
+            for (int k = 0; k < mv->moves; ++k)
+                mh_move(tg, mv, beta[t], eps[t - 1], seed, (uint32_t)n, (uint32_t)t, (uint32_t)k, tag,
+                        (t - 1) * mv->moves + k, &p, &margin[n], wk);
+            ell[n] = p.ell;
+            if (wk != work) free(wk);
+        }
+        const double lse1 = orc_logsumexp(logw, N);
+        for (long n = 0; n < N; ++n) tmp[n] = 2.0 * logw[n];
+        const double ess = exp(2.0 * lse1 - orc_logsumexp(tmp, N));
+        const int last = beta[t] >= 1.0;
+        T = t;
+        if (last || (ess_frac > 0.0 && ess < ess_frac * (double)N)) {
+            logZ += lse1 - log((double)N);
+            if (!last) {
+                ++n_res;
+                int64_t* anc = (int64_t*)malloc(sizeof(int64_t) * N);
+                orc_systematic_resample(N, logw, orc_resample_uniform(seed, (uint32_t)t, tag), anc);
+                double* X2 = (double*)malloc(sizeof(double) * N * d);
+                double* G2 = (double*)malloc(sizeof(double) * N * d);
+                double* e2 = (double*)malloc(sizeof(double) * N);
+                double* m2 = (double*)malloc(sizeof(double) * N);
+                for (long n = 0; n < N; ++n) {
+                    memcpy(X2 + n * d, X + anc[n] * d, sizeof(double) * d);
+                    memcpy(G2 + n * d, G + anc[n] * d, sizeof(double) * d);
+                    e2[n] = ell[anc[n]];
+                    m2[n] = margin[anc[n]];
+                }
+                memcpy(X, X2, sizeof(double) * N * d);
+                memcpy(G, G2, sizeof(double) * N * d);
+                memcpy(ell, e2, sizeof(double) * N);
+                memcpy(margin, m2, sizeof(double) * N);
+                for (long n = 0; n < N; ++n) logw[n] = 0.0;
+                free(anc); free(X2); free(G2); free(e2); free(m2);
+            }
+        }
+        if (last) break;
+    }
+    res->logZ = logZ;
+    res->n_resample = n_res;
+    *T_out = T;
+    if (logw_out) memcpy(logw_out, logw, sizeof(double) * N);
+    if (x_out) memcpy(x_out, X, sizeof(double) * N * d);
+    if (ell_out) memcpy(ell_out, ell, sizeof(double) * N);
+    if (margin_out) memcpy(margin_out, margin, sizeof(double) * N);
+    free(X); free(G); free(ell); free(logw); free(logg); free(tmp); free(margin);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Monotone piecewise cubic Hermite interpolation (Fritsch & Carlson,    */
 /* SIAM J. Numer. Anal. 1980, with the harmonic-mean interior slopes of  */
 /* Fritsch & Butland 1984 and three-point one-sided end slopes).          */

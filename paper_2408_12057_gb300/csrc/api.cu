@@ -139,6 +139,12 @@ struct oais_ctx {
     StepPartial* d_parts = nullptr;
     double *d_log_ghat = nullptr, *d_accept = nullptr, *d_lse = nullptr;
     double* d_elbo = nullptr;            // [T_max] ELBO terms sum_n W_{t-1}^n log g_t^n
+    // online conditional-ESS rounds
+    float2* d_zfg = nullptr;
+    double2* d_zanchor = nullptr;
+    float2* d_zpart = nullptr;
+    ZjaState* d_zstate = nullptr;
+    double *d_zbeta = nullptr, *d_zeps = nullptr;
     void* d_lse_scratch = nullptr;
     unsigned* d_status = nullptr;
     // ASMC: second particle buffer, gradient buffers, resampling scratch and traces
@@ -200,7 +206,7 @@ static size_t elt_bytes(int kind) { return f64_kind(kind) ? sizeof(double) : siz
 struct Layout {
     size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, elbo, lse, lse_scr, status;
     size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, tc_img, tc_y;
-    size_t tcs_img, tcs_state, tc_handed, total;
+    size_t tcs_img, tcs_state, tc_handed, zja_fg, zja_anchor, zja_part, zja_state, zja_beta, zja_eps, total;
 };
 
 // which sweep form a target runs: 0 CUDA cores, 1 resident tensor-core, 2 streamed tensor-core
@@ -256,6 +262,14 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     L.tc_img = take(form == 1 ? (size_t)tc_image_bytes() : 0);
     L.tc_y = take(form == 1 ? (size_t)tc_max_rows() / 8 : 0);
     L.tc_handed = take(form == 1 ? sizeof(int) * (size_t)tc_records(N) : 0);
+    // online conditional-ESS rounds (CUDA-core form): offsets, anchors, candidate sums, state,
+    // the schedule found online and its step sizes
+    L.zja_fg = take(sizeof(float2) * (size_t)N);
+    L.zja_anchor = take(sizeof(double2) * (size_t)zja_grid(N));
+    L.zja_part = take(zja_part_bytes(N));
+    L.zja_state = take(sizeof(ZjaState));
+    L.zja_beta = take(sizeof(double) * (T_max + 1));
+    L.zja_eps = take(sizeof(double) * T_max);
     TcsPlan tp;
     if (form == 2) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
     L.tcs_img = take(form == 2 ? tp.img_bytes : 0);
@@ -424,6 +438,12 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     ctx->d_parts = reinterpret_cast<StepPartial*>(b + L.parts);
     ctx->d_log_ghat = reinterpret_cast<double*>(b + L.lg);
     ctx->d_elbo = reinterpret_cast<double*>(b + L.elbo);
+    ctx->d_zfg = reinterpret_cast<float2*>(b + L.zja_fg);
+    ctx->d_zanchor = reinterpret_cast<double2*>(b + L.zja_anchor);
+    ctx->d_zpart = reinterpret_cast<float2*>(b + L.zja_part);
+    ctx->d_zstate = reinterpret_cast<ZjaState*>(b + L.zja_state);
+    ctx->d_zbeta = reinterpret_cast<double*>(b + L.zja_beta);
+    ctx->d_zeps = reinterpret_cast<double*>(b + L.zja_eps);
     ctx->d_accept = reinterpret_cast<double*>(b + L.acc);
     ctx->d_lse = reinterpret_cast<double*>(b + L.lse);
     ctx->d_lse_scratch = b + L.lse_scr;
@@ -844,6 +864,90 @@ static oais_status commit_round(oais_ctx* ctx, int T, int32_t T_next, const std:
 oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out)
 {
     return run_round(ctx, T_next, false, 0.0, out);
+}
+
+// The online conditional-ESS comparator (Zhou, Johansen & Aston 2016; the paper's section on
+// the connection to online CESS optimisation): lock-step particles as in oasmc_round, but
+// beta_t is found on the device before step t (zja.cu) so that CESS_t / N = cess_frac; the
+// run ends at beta = 1 (at most T_max steps, the last one forced to beta = 1).  One host
+// round trip per step reads beta_t.
+oais_status oais_zja_round(oais_ctx* ctx, double cess_frac, double ess_frac, int32_t T_next, oais_round_result* out)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (!(cess_frac > 0.0 && cess_frac < 1.0)) return fail(ctx, OAIS_EINVAL, "cess_frac must be in (0, 1)");
+    if (!(ess_frac >= 0.0 && ess_frac <= 1.0 + 1e-12)) return fail(ctx, OAIS_EINVAL, "ess_frac must be in [0, 1]");
+    if (T_next < 1 || T_next > ctx->T_max) return fail(ctx, OAIS_EINVAL, "T_next out of range");
+    if (ctx->N_total != ctx->N) return fail(ctx, OAIS_EUNSUPPORTED, "the online schedule needs every particle: no shards");
+    if (ctx->dt.D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "online-CESS rounds run on the CUDA-core form");
+    cudaStream_t s = ctx->stream;
+    const int T_ref = (int)ctx->beta.size() - 1;
+    const int T_max = ctx->T_max;
+    // the current schedule is the step-size reference (log eps interpolated in beta)
+    CK(cudaMemcpyAsync(ctx->d_beta, ctx->beta.data(), sizeof(double) * (T_ref + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_eps, ctx->eps.data(), sizeof(double) * T_ref, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s));
+    CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(AsmcState), s));
+    const ZjaState z0{0.0, 1.0, 0.0, 0, 0};
+    const double b0 = 0.0;
+    CK(cudaMemcpyAsync(ctx->d_zstate, &z0, sizeof(z0), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_zbeta, &b0, sizeof(double), cudaMemcpyHostToDevice, s));
+    const uint32_t tag = (uint32_t)(ctx->round & 0xFFFF) | ((uint32_t)ctx->problem << 16);
+    StepParams P = make_step_params(ctx, T_max, tag);
+    P.beta = ctx->d_zbeta;
+    P.eps = ctx->d_zeps;
+    const int grid = sweep_grid(ctx->N);
+    const bool grad = ctx->mv.kind != OAIS_RWMH;
+    CK(cudaEventRecord(ctx->ev0, s));
+    CK(launch_asmc(ctx->dt, ctx->mv.kind, true, P, s));
+    int T = 0;
+    for (int t = 1; t <= T_max; ++t) {
+        CK(launch_zja_search(ctx->d_zstate, ctx->d_st, P, ctx->d_zfg, ctx->d_zanchor, ctx->d_zpart, cess_frac, t,
+                             T_max, ctx->d_zbeta, ctx->d_zeps, ctx->d_beta, ctx->d_eps, T_ref, s));
+        P.t = t;
+        CK(launch_asmc(ctx->dt, ctx->mv.kind, false, P, s));
+        CK(launch_asmc_resample(ctx->d_st, P, grid, ess_frac, ctx->dt.d, grad, f64_kind(ctx->dt.kind), ctx->d_bsum,
+                                ctx->d_boff, ctx->d_cdf, ctx->d_ess_trace, ctx->d_resampled, ctx->d_anc, s));
+        double bt = 0.0;
+        CK(cudaMemcpyAsync(&bt, ctx->d_zbeta + t, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        T = t;
+        if (bt >= 1.0) break;
+    }
+    CK(cudaEventRecord(ctx->ev1, s));
+    std::vector<double> lg(3 * T), acc(T), elbo(T), ess_tr(T), zb(T + 1), ze(T);
+    std::vector<int> rs(T);
+    CK(launch_merge_stats(ctx->d_parts, grid, T, 1.0 / ((double)ctx->N * ctx->mv.moves), ctx->d_log_ghat,
+                          ctx->d_accept, ctx->d_elbo, s));
+    AsmcState st;
+    unsigned status = 0;
+    CK(cudaMemcpyAsync(lg.data(), ctx->d_log_ghat, sizeof(double) * 3 * T, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(acc.data(), ctx->d_accept, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(elbo.data(), ctx->d_elbo, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&st, ctx->d_st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ess_tr.data(), ctx->d_ess_trace, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(rs.data(), ctx->d_resampled, sizeof(int) * T, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(zb.data(), ctx->d_zbeta, sizeof(double) * (T + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ze.data(), ctx->d_zeps, sizeof(double) * T, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // the particles of the last step live in buffer cur (no resampling is pending at beta = 1)
+    if ((st.cur ^ st.pend) == 1) {
+        const size_t xb = elt_bytes(ctx->dt.kind) * (size_t)ctx->dt.d * ctx->N;
+        CK(cudaMemcpyAsync(ctx->d_x, ctx->d_x1, xb, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->d_ell, ctx->d_ell1, sizeof(double) * ctx->N, cudaMemcpyDeviceToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (status & 1u) return fail(ctx, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood");
+    double v = 0.0;
+    for (int t = 0; t < T; ++t) if (rs[t]) v += std::max(0.0, 1.0 / ess_tr[t] - 1.0 / (double)ctx->N);
+    // the schedule that ran is the round's (its moments give D_hat and the next schedule)
+    ctx->beta = zb;
+    ctx->eps = ze;
+    ctx->cur_elbo = elbo;
+    return commit_round(ctx, T, T_next, lg, acc, st.logZ, ess_tr[T - 1], std::sqrt(v), ms, true, st.n_resample,
+                        ess_tr, rs, out);
 }
 
 oais_status oasmc_round(oais_ctx* ctx, int32_t T_next, double ess_frac, oais_round_result* out)

@@ -1,6 +1,6 @@
 // asmc.cu -- the resampling half of ASMC (Alg. 1, resample step; Sec. 2.1.3):
 //   decide:   ESS of w_{t^-} = (sum w)^2 / sum w^2 (eq. sample_size_IS); resample when
-//             ESS < nu N, and always close the last segment at t = T; on a resampling
+//             ESS < nu N, and always close the last segment (t = T, or beta_t = 1); on a resampling
 //             time Z_hat *= mean(w) (eq. estimator_Z), kept as log Z_hat += LSE(log w) - log N;
 //   scan:     weights exp(log w_m - LSE~) and their inclusive cumulative sums P_m in fp64
 //             (block sums, block offsets, in-block scan: a fixed order), normalised by
@@ -22,7 +22,8 @@ int scan_blocks(int64_t N) { return (int)((N + kScanTile - 1) / kScanTile); }
 
 __global__ void __launch_bounds__(256)
 asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ ess_parts, int nparts, int t, int T,
-                   double ess_frac, int64_t N, Rng rng, double* ess_trace, int* resampled)
+                   const double* __restrict__ beta, double ess_frac, int64_t N, Rng rng, double* ess_trace,
+                   int* resampled)
 {
     __shared__ double sm[2][256], ss[2][256];
     const int tid = threadIdx.x;
@@ -49,11 +50,13 @@ asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ ess_parts, int
         const double lse2 = sm[1][0] + log(ss[1][0]);
         const double ess = exp(2.0 * lse1 - lse2);
         st->cur ^= st->pend;             // the previous step's gather is now the live buffer
-        const bool fire = (t == T) || (ess_frac > 0.0 && ess < ess_frac * (double)N);
+        // the last step (t = T, or beta_t = 1 for a schedule found online) closes the segment
+        const bool last = (t == T) || beta[t] >= 1.0;
+        const bool fire = last || (ess_frac > 0.0 && ess < ess_frac * (double)N);
         int pend = 0;
         if (fire) {
             st->logZ += lse1 - log((double)N);
-            if (t < T) {
+            if (!last) {
                 pend = 1;
                 st->n_resample += 1;
                 st->lse = lse1;
@@ -177,7 +180,7 @@ asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const dou
 cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int nparts, double ess_frac, double* bsum,
                                     double* boff, double* cdf, double* ess_trace, int* resampled, cudaStream_t s)
 {
-    asmc_decide_kernel<<<1, 256, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, ess_frac, P.N, P.mv.rng,
+    asmc_decide_kernel<<<1, 256, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
                                          ess_trace, resampled);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
@@ -190,7 +193,7 @@ cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts,
                                  bool grad, bool fp64, double* bsum, double* boff, double* cdf,
                                  double* ess_trace, int* resampled, int64_t* ancestors, cudaStream_t s)
 {
-    asmc_decide_kernel<<<1, 256, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, ess_frac, P.N, P.mv.rng,
+    asmc_decide_kernel<<<1, 256, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
                                          ess_trace, resampled);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);

@@ -81,6 +81,19 @@ cudaError_t launch_potential_tcs(const TcsPlan& L, int kind, const void* img, co
 // tensor-core logistic sweep (sweep_tc.cu)
 int tc_grid(int64_t N);
 int tc_records(int64_t N);
+// Online conditional-ESS schedule (zja.cu): line-search state of the current step
+struct ZjaState {
+    double lo, hi;       // bracket of delta = beta_t - beta_{t-1}
+    double beta_prev;    // beta_{t-1}
+    int done;            // 1: beta_t fixed (the pass and narrow kernels return at once)
+    int pad;
+};
+int zja_grid(int64_t N);
+size_t zja_part_bytes(int64_t N);
+cudaError_t launch_zja_search(ZjaState* zs, const AsmcState* st, const StepParams& P, float2* fg, double2* anchor,
+                              float2* part, double cess_frac, int t, int T_max, double* beta, double* eps,
+                              const double* beta_ref, const double* eps_ref, int T_ref, cudaStream_t s);
+
 cudaError_t launch_sweep_tc(const SweepParams& sp, const void* Ximg, const uint32_t* ybits, int n, int d,
                             float* grad_state, int* handed, cudaStream_t s);
 

@@ -69,6 +69,7 @@ def lib():
                 "oais_init": ([P, P, P, i64, P, i32, i32, P, u64, P, sz, P], i32),
                 "oais_round": ([P, i32, P], i32),
                 "oasmc_round": ([P, i32, f64, P], i32),
+                "oais_zja_round": ([P, f64, f64, i32, P], i32),
                 "oais_get_resampling": ([P, P, P, P], i32),
                 "asmc_run": ([P, P, i64, P, i32, P, f64, u64, P, P, P, P, P], i32),
                 "oais_logZ": ([P, P, P], i32),
@@ -243,6 +244,16 @@ class OAIS:
             T_next = self.schedule()[0].size - 1
         r = _RoundResult()
         _check(lib().oasmc_round(self._ctx, int(T_next), float(ess_frac), ctypes.byref(r)), self._ctx)
+        return {f: getattr(r, f) for f, _ in _RoundResult._fields_ if f != "pad"}
+
+    def zja_round(self, cess_frac, T_next=None, ess_frac=0.0):
+        """One run of the online conditional-ESS comparator (the schedule found step by step
+        so that CESS / N = cess_frac); the schedule that ran is then ``stats()["beta"]``."""
+        if T_next is None:
+            T_next = self.schedule()[0].size - 1
+        r = _RoundResult()
+        _check(lib().oais_zja_round(self._ctx, float(cess_frac), float(ess_frac), int(T_next), ctypes.byref(r)),
+               self._ctx)
         return {f: getattr(r, f) for f, _ in _RoundResult._fields_ if f != "pad"}
 
     def resampling(self):
