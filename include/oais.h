@@ -180,7 +180,7 @@ oais_status oasmc_round(oais_ctx* ctx, int32_t T_next, double ess_frac, oais_rou
  * parameter is chosen on the device so that CESS_t / N = (sum_n W_n g_n)^2 / sum_n W_n g_n^2
  * = cess_frac, g_n = L(X_{t-1}^n)^(beta_t - beta_{t-1}), W the normalised weights since the last
  * resampling (the paper matches budgets with cess_frac = exp(-Lambda^2 / T^2)).  The line
- * search refines a bracket of beta_t - beta_{t-1} in four passes of 32 candidates, keeping the
+ * search refines a bracket of beta_t - beta_{t-1} in a geometric scan and five linear passes of 32 candidates, keeping the
  * last candidate meeting the target.  The run ends at beta = 1 or after T_max steps (the last
  * forced to beta = 1); step sizes are the current schedule's, log eps interpolated linearly
  * in beta.  ess_frac as in oasmc_round.  The schedule that ran becomes the round's

@@ -522,12 +522,16 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
 /* optimisation: before step t, beta_t is chosen so that                  */
 /* CESS_t / N = (sum W g)^2 / (sum W g^2) = cess_frac, g = L^(beta_t -    */
 /* beta_{t-1}), W the normalised weights since the last resampling.       */
-/* Line search (a reading): a bracket of delta = beta_t - beta_{t-1},     */
-/* initially [0, 1 - beta_{t-1}], refined in four passes over the 32      */
-/* candidates lo + (hi - lo) j / 32, j = 1..32, keeping the last one that  */
-/* meets the target; the step is the final lower end (the first candidate */
-/* of the last pass if that is 0), or the whole interval when its end     */
-/* meets the target.  Step sizes: log eps interpolated linearly in beta   */
+/* Line search (a reading): the geometric candidates hi 4^-(32-j),       */
+/* j = 1..32, hi = 1 - beta_{t-1}, keeping the last one that meets the    */
+/* target, then five passes over 32 equally spaced candidates of the      */
+/* bracket it ends in; the step is the final lower end, the whole interval */
+/* when its end meets the target, the smallest geometric candidate when   */
+/* none does (steps of at least 1e-14).  The target is relative to the   */
+/* weight share A inside the likelihood's support: CESS/N >= c A (A = 1   */
+/* unless weighted states have L = 0).  Candidates are fp32 values, as on */
+/* the device.                                                            */
+/* Step sizes: log eps interpolated linearly in beta                      */
 /* through the points (beta_ref[t], eps_ref[t-1]), constant beyond.        */
 /* Then the ASMC step of orc_asmc; the step with beta_t = 1 (forced at     */
 /* t = T_max) closes the last segment.                                    */
@@ -561,25 +565,38 @@ static double zja_step_size(double b, const double* beta_ref, const double* eps_
 }
 
 /* the next annealing parameter from the particles' log-weights and log-likelihoods */
+static double zja_candidate(int pass, double lo, double hi, int j)
+{
+    /* the device computes its candidates in fp32; the same values here */
+    return pass == 0 ? (double)((float)hi * exp2f(-2.0f * (float)(32 - j)))
+                     : (double)((float)lo + ((float)hi - (float)lo) * (float)j / 32.0f);
+}
+
 double orc_zja_next_beta(long N, const double* logw, const double* ell, double beta_prev, double cess_frac,
                          int t, int T_max)
 {
     double lo = 0.0, hi = 1.0 - beta_prev, delta = 0.0;
-    const double l0 = lse_shift(logw, ell, 0.0, 0.0, N), lt = log(cess_frac);
-    for (int pass = 0; pass < 4; ++pass) {
-        const double w = hi - lo;
+    /* the target relative to the weight share A inside the support (CESS -> A as the step
+       -> 0+: weighted states with L = 0 are lost at any positive step) */
+    const double l0 = lse_shift(logw, ell, 0.0, 0.0, N);
+    const double la = lse_shift(logw, ell, 1.0, 0.0, N);
+    const double lt = log(cess_frac) + la - l0;
+    for (int pass = 0; pass < 6; ++pass) {
         int best = 0;
         for (int j = 1; j <= 32; ++j) {
-            const double dj = lo + w * j / 32.0;
+            const double dj = zja_candidate(pass, lo, hi, j);
             const double ratio = 2.0 * lse_shift(logw, ell, 1.0, dj, N) - l0 - lse_shift(logw, ell, 2.0, dj, N);
             if (ratio >= lt) best = j;
         }
         if (best == 32) { delta = hi; break; }
-        const double nlo = lo + w * best / 32.0, nhi = lo + w * (best + 1) / 32.0;
-        if (pass == 3) { delta = nlo > 0.0 ? nlo : lo + w / 32.0; break; }
+        if (best == 0 && pass == 0) { delta = zja_candidate(0, lo, hi, 1); break; }
+        const double nlo = best > 0 ? zja_candidate(pass, lo, hi, best) : lo;
+        const double nhi = zja_candidate(pass, lo, hi, best + 1);
+        if (pass == 5) { delta = nlo; break; }
         lo = nlo;
         hi = nhi;
     }
+    if (delta < 1e-14 && hi > 1e-14) delta = 1e-14;   /* every step advances beta */
     double bt = beta_prev + delta;
     if (bt >= 1.0 - 1e-12 || t >= T_max) bt = 1.0;
     return bt;

@@ -4,11 +4,16 @@
 //   CESS_t / N = (sum_n W_n g_n)^2 / (sum_n W_n g_n^2) = c,   g_n = L(X_{t-1}^n)^delta,
 // delta = beta_t - beta_{t-1}, W the normalised weights since the last resampling, c a target
 // fraction (the paper sets it from D ~ Lambda^2 / T^2, i.e. c = exp(-Lambda^2 / T^2)).
-// CESS is 1 at delta = 0 and decreases in delta.  The line search keeps a bracket [lo, hi]
-// (initially [0, 1 - beta_{t-1}]) and refines it in four passes over 32 equally spaced
-// candidates lo + (hi - lo) j / 32, j = 1..32, keeping the last candidate that still meets the
-// target; the step is the bracket's lower end (or, if it is still 0, the first candidate of the
-// last pass), and the whole remaining interval when it meets the target.
+// CESS is 1 at delta = 0 and decreases in delta; where weighted particles lie outside the
+// likelihood's support (log L = -inf), CESS drops at once to their complement's share A of the
+// weight, which no step can avoid, so the target is taken relative to it: CESS / N >= c A.
+// The line search first scans the geometric
+// candidates hi 4^-(32-j), j = 1..32 (hi = 1 - beta_{t-1}: eighteen decades, for targets whose
+// likelihood spread asks for steps of 1e-10 and less), keeping the last one that meets the
+// target, then refines the bracket it ends in over five passes of 32 equally spaced candidates
+// lo + (hi - lo) j / 32; the step is the final lower end.  The whole interval is taken when its
+// end meets the target, and the smallest geometric candidate when none does (every step
+// advances).
 //
 // Per pass: zja_pass_kernel writes, per CTA, the shifted sums of the three weighted powers of
 // g at each candidate; zja_narrow_kernel (one CTA) merges them, evaluates the candidates and
@@ -20,8 +25,8 @@ namespace oais {
 
 constexpr int kZjaThreads = 256;
 constexpr int kZjaCand = 32;                  // candidates per pass
-constexpr int kZjaSums = 1 + 2 * kZjaCand;    // S0; S1 at each candidate; S2 at each candidate
-constexpr int kZjaPasses = 4;
+constexpr int kZjaSums = 2 + 2 * kZjaCand;    // S0; S_alive; S1 at each candidate; S2 at each
+constexpr int kZjaPasses = 6;                 // one geometric scan, five linear refinements
 
 int zja_grid(int64_t N) { return (int)((N + kZjaThreads - 1) / kZjaThreads); }
 size_t zja_part_bytes(int64_t N) { return sizeof(float2) * kZjaSums * (size_t)zja_grid(N); }
@@ -55,24 +60,31 @@ zja_prep_kernel(const AsmcState* st, const StepParams P, float2* __restrict__ fg
     if (threadIdx.x == 0) anchor[blockIdx.x] = make_double2(a_lw, a_ell);
 }
 
-// per CTA and candidate: (max, sum exp(e - max)) of e = f + k delta g, k = 0 (S0), 1, 2
+// per CTA and candidate: (max, sum exp(e - max)) of e = f + k delta g: k = 0 (S0); the weight
+// inside the support (S_alive: e = f where g is finite); k = 1, 2 at each candidate
+// candidate j (1..32) of a pass: geometric in pass 0, equally spaced after
+__device__ __forceinline__ float zja_candidate(int pass, float lo, float hi, int j)
+{
+    return pass == 0 ? hi * exp2f(-2.0f * (float)(kZjaCand - j)) : lo + (hi - lo) * (float)j / (float)kZjaCand;
+}
+
 __global__ void __launch_bounds__(kZjaThreads)
-zja_pass_kernel(const ZjaState* zs, int64_t N, const float2* __restrict__ fg, float2* __restrict__ part)
+zja_pass_kernel(const ZjaState* zs, int pass, int64_t N, const float2* __restrict__ fg, float2* __restrict__ part)
 {
     if (zs->done) return;
     __shared__ float wmax[kZjaThreads / 32][kZjaSums], wsum[kZjaThreads / 32][kZjaSums];
     const int64_t n = (int64_t)blockIdx.x * kZjaThreads + threadIdx.x;
     const float2 v = n < N ? fg[n] : make_float2(-INFINITY, 0.0f);
-    const float lo = (float)zs->lo, width = (float)(zs->hi - zs->lo);
+    const float lo = (float)zs->lo, hi = (float)zs->hi;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c = 0; c < kZjaSums; ++c) {
-        const int j = c == 0 ? 0 : (c - 1) % kZjaCand + 1;      // candidate 1..32 (0: S0)
-        const float k = c == 0 ? 0.0f : (c <= kZjaCand ? 1.0f : 2.0f);
-        const float delta = lo + width * (float)j / (float)kZjaCand;
-        // f + k delta g: a zero weight (f = -inf) or, for k > 0, a state outside the support
+        const int j = c < 2 ? 0 : (c - 2) % kZjaCand + 1;      // candidate 1..32 (0: S0, S_alive)
+        const float k = c < 2 ? 0.0f : (c < 2 + kZjaCand ? 1.0f : 2.0f);
+        const float delta = j == 0 ? 0.0f : zja_candidate(pass, lo, hi, j);
+        // f + k delta g: a zero weight (f = -inf) or, for c >= 1, a state outside the support
         // (g = -inf) gives -inf; never 0 * inf
-        const float e = (v.x == -INFINITY || (k > 0.0f && v.y == -INFINITY)) ? -INFINITY
-                                                                           : v.x + k * delta * v.y;
+        const float e = (v.x == -INFINITY || (c >= 1 && v.y == -INFINITY)) ? -INFINITY
+                                                                           : (k > 0.0f ? v.x + k * delta * v.y : v.x);
         float m = e;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
@@ -117,10 +129,10 @@ zja_narrow_kernel(ZjaState* zs, const double2* __restrict__ anchor, const float2
     __shared__ double logS[kZjaSums];
     const double lo = zs->lo, hi = zs->hi;
     for (int c = threadIdx.x; c < kZjaSums; c += blockDim.x) {
-        const int j = c == 0 ? 0 : (c - 1) % kZjaCand + 1;
-        const double k = c == 0 ? 0.0 : (c <= kZjaCand ? 1.0 : 2.0);
+        const int j = c < 2 ? 0 : (c - 2) % kZjaCand + 1;
+        const double k = c < 2 ? 0.0 : (c < 2 + kZjaCand ? 1.0 : 2.0);
         // the same fp32 candidate the pass kernel used
-        const double delta = (double)((float)lo + (float)(hi - lo) * (float)j / (float)kZjaCand);
+        const double delta = j == 0 ? 0.0 : (double)zja_candidate(pass, (float)lo, (float)hi, j);
         double M = -INFINITY;
         for (int b = 0; b < nblk; ++b) {
             const float2 q = part[(size_t)b * kZjaSums + c];
@@ -140,26 +152,34 @@ zja_narrow_kernel(ZjaState* zs, const double2* __restrict__ anchor, const float2
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    // the last candidate whose CESS / N = S1^2 / (S0 S2) still meets the target
+    // the last candidate whose CESS / N = S1^2 / (S0 S2) still meets c A, A = S_alive / S0
+    const double lt = log_target + logS[1] - logS[0];
     int best = 0;
     for (int j = 1; j <= kZjaCand; ++j) {
-        const double lr = 2.0 * logS[j] - logS[0] - logS[kZjaCand + j];
-        if (lr >= log_target) best = j;
+        const double lr = 2.0 * logS[1 + j] - logS[0] - logS[1 + kZjaCand + j];
+        if (lr >= lt) best = j;
     }
-    const double w = hi - lo;
-    double nlo = lo + w * (double)best / kZjaCand, nhi = best < kZjaCand ? lo + w * (double)(best + 1) / kZjaCand : hi;
+    auto cand = [&](int j) { return (double)zja_candidate(pass, (float)lo, (float)hi, j); };
     bool fix = false;
-    double delta = 0.0;
+    double delta = 0.0, nlo = lo, nhi = hi;
     if (best == kZjaCand) {            // the whole remaining interval meets the target
         fix = true;
         delta = hi;
-    } else if (pass == kZjaPasses - 1) {
+    } else if (best == 0 && pass == 0) {   // not even the smallest step does: take it
         fix = true;
-        delta = nlo > 0.0 ? nlo : lo + w / kZjaCand;
+        delta = cand(1);
+    } else {
+        nlo = best > 0 ? cand(best) : lo;
+        nhi = cand(best + 1);
+        if (pass == kZjaPasses - 1) {
+            fix = true;
+            delta = nlo;
+        }
     }
     zs->lo = nlo;
     zs->hi = nhi;
     if (!fix) return;
+    if (delta < 1e-14 && hi > 1e-14) delta = 1e-14;   // every step advances beta
     double bt = zs->beta_prev + delta;
     if (bt >= 1.0 - 1e-12 || t >= T_max) bt = 1.0;
     beta[t] = bt;
@@ -181,7 +201,7 @@ cudaError_t launch_zja_search(ZjaState* zs, const AsmcState* st, const StepParam
     zja_open_kernel<<<1, 1, 0, s>>>(zs);
     zja_prep_kernel<<<grid, kZjaThreads, 0, s>>>(st, P, fg, anchor);
     for (int pass = 0; pass < kZjaPasses; ++pass) {
-        zja_pass_kernel<<<grid, kZjaThreads, 0, s>>>(zs, P.N, fg, part);
+        zja_pass_kernel<<<grid, kZjaThreads, 0, s>>>(zs, pass, P.N, fg, part);
         zja_narrow_kernel<<<1, 128, 0, s>>>(zs, anchor, part, grid, log(cess_frac), pass, t, T_max, beta, eps,
                                             beta_ref, eps_ref, T_ref);
     }

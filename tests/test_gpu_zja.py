@@ -54,8 +54,8 @@ def test_gauss_zja_matches_oracle(ess_frac):
 
 
 def test_unid_zja_runs_and_holds_the_target():
-    # most reference draws are outside the support: the first step's CESS target cannot be met
-    # (the weighted dead states alone push it below c), the search takes its smallest step, and
+    # most reference draws are outside the support: they are lost at the first positive step
+    # whatever its size, so the target is relative to the weight share inside the support, and
     # from then on the live particles carry the run
     pr = W.unid(m=1000, k=100)
     N, c = 2000, 0.8
