@@ -93,10 +93,11 @@ typedef struct {
                              expanded to f16 on chip (exact), so the contraction keeps the
                              accuracy of the f16 form; LINREG only.
                            The tensor-core forms run the OAIS sweep (oais_round and the shard
-                           calls); the streamed form also runs resampling rounds (oasmc_round:
+                           calls); the streamed kernel also runs resampling rounds (oasmc_round:
                            one launch per step over its stored particle state) and
-                           oais_potential.  For the resident form those two, and
-                           oais_ctx_sweep for every form, use the CUDA-core form, which exists
+                           oais_potential, for streamed and resident contexts alike (a resident
+                           context keeps the streamed form's image and state for them).
+                           oais_ctx_sweep and oais_zja_round use the CUDA-core form, which exists
                            for d <= 32 (they return OAIS_EUNSUPPORTED above that).  Other combinations
                            return OAIS_EUNSUPPORTED at init. */
 } oais_target;

@@ -271,9 +271,11 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     L.zja_beta = take(sizeof(double) * (T_max + 1));
     L.zja_eps = take(sizeof(double) * T_max);
     TcsPlan tp;
-    if (form == 2) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
-    L.tcs_img = take(form == 2 ? tp.img_bytes : 0);
-    L.tcs_state = take(form == 2 ? sizeof(float) * 5 * (size_t)tp.dp * tcs_tiles(N) * 128 : 0);
+    // the streamed form's image and state: its own sweeps, and the resampling rounds and the
+    // potential of a resident-form context (whose kernel is a whole-sweep kernel)
+    if (form >= 1) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
+    L.tcs_img = take(form >= 1 ? tp.img_bytes : 0);
+    L.tcs_state = take(form >= 1 ? sizeof(float) * 5 * (size_t)tp.dp * tcs_tiles(N) * 128 : 0);
     L.total = off;
     return L;
 }
@@ -311,7 +313,7 @@ static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais
         if (!fam || tg->d > 256)
             return fail(ctx, OAIS_EUNSUPPORTED,
                         "the tensor-core contraction is built for LOGREG (MALA) and LINREG (MALA, HMC), d <= 256");
-        if (sweep_form(tg, mv) == 2) {
+        if (sweep_form(tg, mv) >= 1) {
             const TcsPlan tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
             const int Le = mv->kind == OAIS_HMC ? mv->leapfrog : 1;
             const double chunks = (1.0 + (double)T_max * mv->moves * Le) * tp.nch;
@@ -499,7 +501,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
             for (int r = 0; r < tg->n; ++r) yp[r] = (float)yh[r];
             e = cudaMemcpy(dt.y, yp.data(), sizeof(float) * yp.size(), cudaMemcpyHostToDevice);
         }
-        if (e == cudaSuccess && sweep_form(tg, mv) == 2) {
+        if (e == cudaSuccess && sweep_form(tg, mv) >= 1) {
             std::vector<float> Xf((size_t)tg->n * tg->d), yf(tg->n);
             for (size_t i = 0; i < Xf.size(); ++i) Xf[i] = (float)Xh[i];
             for (int r = 0; r < tg->n; ++r) yf[r] = (float)yh[r];

@@ -107,3 +107,28 @@ def test_tc_agrees_with_fp32_form_on_bf16_data():
     b = run(prq, 2048, beta, eps, 5, oais.CONTRACT_FP32)
     ok = (np.abs(a["logw"] - b["logw"]) <= ABS + REL * np.abs(b["logw"]))
     assert ok.mean() >= 0.95
+
+
+def test_tc_context_resampling_rounds_and_potential_use_the_streamed_kernel():
+    # a resident-form context keeps the streamed form's image and state: its resampling rounds
+    # and its potential are those of a streamed-form context, bit for bit
+    pr = W.logistic(n=700, d=20, seed=8)
+    N, T = 512, 12
+    beta = W.linear_schedule(T) ** 2
+    eps = oais.default_step_sizes(pr, beta, oais.MALA)
+    out = []
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    x = torch.randn(pr.d, 64, dtype=torch.float32, device="cuda", generator=gen) * 0.3
+    for c in (oais.CONTRACT_BF16_TC, oais.CONTRACT_BF16_TC_STREAM):
+        r = oais.OAIS(pr, oais.MALA, N, beta, eps=eps, seed=3, contraction=c)
+        res = r.asmc_round(0.5, T)
+        logw, ell, _ = r.particles()
+        pot_ell, pot_g = r.potential(x)
+        out.append((res, logw.cpu().numpy().copy(), ell.cpu().numpy().copy(), pot_ell.cpu().numpy().copy(),
+                    pot_g.cpu().numpy().copy()))
+        r.close()
+    (ra, la, ea, pa, ga), (rb, lb, eb, pb, gb) = out
+    assert ra["n_resample"] == rb["n_resample"] and ra["n_resample"] > 0
+    assert ra["logZ"] == rb["logZ"]
+    assert np.array_equal(la, lb) and np.array_equal(ea, eb)
+    assert np.array_equal(pa, pb) and np.array_equal(ga, gb)
