@@ -13,11 +13,12 @@
 // contraction is issued once per term.  The data X is rounded to BF16 once (X~); the
 // sampler targets the posterior of X~.
 //
-// CTA = 2 independent groups of 4 particle warps plus one MMA warp each; group g owns 128
-// particles, its own TMEM columns, operand tiles and barriers, and shares the BF16 image of
-// X (resident in shared memory for the whole sweep).  The group's MMA warp issues its
-// tcgen05.mma instructions (one lane issues, the warp runs the loop), so the particle warps
-// never wait on the issue of a contraction.
+// CTA = 2 independent groups of 8 particle warps plus one MMA warp each; group g owns 128
+// particles, two threads per particle (each takes half the columns of every chunk and half
+// the coordinates; they exchange partial sums through TMEM), its own TMEM columns, operand
+// tiles and barriers, and shares the BF16 image of X (resident in shared memory for the whole
+// sweep).  The group's MMA warp issues its tcgen05.mma instructions (one lane issues, the warp
+// runs the loop), so the particle warps never wait on the issue of a contraction.
 //
 // Shared memory (dynamic, 1024-byte aligned base):
 //   R tiles  [group][hi|lo]  128 x 64 bf16, K-major, 128B swizzle    4 x 16 KB
@@ -39,13 +40,19 @@ namespace oais {
 namespace tc {
 
 constexpr int kGroups = 2;
-constexpr int kGroupThreads = 128;
-constexpr int kMmaWarp0 = kGroups * kGroupThreads / 32;  // group g's MMA warp: kMmaWarp0 + g
-constexpr int kParticlesPerCta = kGroups * kGroupThreads;
-constexpr int kThreads = kParticlesPerCta + 32 * kGroups;
+constexpr int kTile = 128;                   // particles per group (the tcgen05 M = 128 lanes)
+constexpr int kHalves = 2;                   // threads per particle: each takes half the columns
+                                             // of a chunk and half the coordinates
+constexpr int kGroupThreads = kTile * kHalves;
+constexpr int kGroupWarps = kGroupThreads / 32;
+constexpr int kMmaWarp0 = kGroups * kGroupWarps;         // group g's MMA warp: kMmaWarp0 + g
+constexpr int kParticlesPerCta = kGroups * kTile;
+constexpr int kThreads = kGroups * kGroupThreads + 32 * kGroups;
 constexpr int kBarsPerGroup = 6;             // forward into D1[0], D1[1]; backward; R written; A written; end
 constexpr int kD = 32;                       // padded state dimension
 constexpr int kChunk = 64;                   // data rows per contraction chunk
+constexpr int kHalfD = kD / kHalves;         // coordinates per thread
+constexpr int kHalfCols = kChunk / kHalves;  // columns of a chunk per thread
 constexpr int kMaxRows = 2048;
 constexpr int kRTile = 128 * kChunk * 2;     // 16 KB
 constexpr int kATile = 128 * kD * 2;         // 8 KB
@@ -60,7 +67,8 @@ constexpr int kOffStat = kOffTmem + 16;
 constexpr int kStatBytes = 2 * 4 * 48;       // [slot][warp] WarpPiece
 constexpr int kOffDesc = kOffStat + kGroups * kStatBytes;  // [group] EvalDesc
 constexpr int kSmemBytes = kOffDesc + kGroups * 16;
-constexpr int kTmemCols = 512;               // group g: D1[0], D1[1] at 256 g + {0, 64}, D2 at 256 g + 128
+constexpr int kTmemCols = 512;               // group g: D1[0], D1[1] at 256 g + {0, 64}, D2 at 256 g + 128,
+                                             // parked x and grad at + 160, the halves' exchange at + 224
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 constexpr float kLog2e = 1.4426950408889634f;
@@ -68,6 +76,34 @@ constexpr uint32_t kIdescFwd = idesc_bf16(128, kChunk, false);
 constexpr uint32_t kIdescBwd = idesc_bf16(128, kD, true);
 
 __device__ __forceinline__ void group_sync(int g) { named_sync(1 + g, kGroupThreads); }
+
+// two-column TMEM store and load (the halves of a particle exchange partial sums through them)
+__device__ __forceinline__ void tmem_st2f(uint32_t taddr, float a, float b)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ float2 tmem_ld2f(uint32_t taddr)
+{
+    uint32_t a, b;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
+    tmem_wait_ld();
+    return make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+__device__ __forceinline__ void tmem_st16f(uint32_t taddr, const float (&f)[16])
+{
+    uint32_t v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __float_as_uint(f[i]);
+    tmem_st16(taddr, v);
+}
+__device__ __forceinline__ void tmem_ld16f(uint32_t taddr, float (&f)[16])
+{
+    uint32_t v[16];
+    tmem_ld16(taddr, v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+}
 
 // Two-term bf16 split of a pair of floats, v = hi + lo: hi = v with the low 16 bits of its
 // fp32 word cleared (a bf16 value, |v - hi| < 2^-7 |v|, exact in fp32), lo = v - hi rounded
@@ -98,8 +134,8 @@ struct TcParams {
 // the shared-memory and TMEM addresses of group g's barriers and accumulators
 struct GroupAddr {
     uint32_t barF[2], barB;  // mbarriers: forward into D1[i] done, backward done
-    uint32_t barR;           // mbarrier: the group's 4 warps have written their R rows
-    uint32_t barA;           // mbarrier: the group's 4 warps have written their A rows
+    uint32_t barR;           // mbarrier: the group's warps have written their R rows
+    uint32_t barA;           // mbarrier: the group's warps have written their A rows
     uint32_t barEnd;         // mbarrier: every MMA of the group has completed (end of the sweep)
     uint32_t d1[2], d2;      // TMEM addresses
     uint32_t smem;           // shared-memory base address
@@ -206,29 +242,36 @@ static_assert(sizeof(EvalDesc) <= 16, "EvalDesc fits its slot");
 
 struct Group {
     GroupAddr a;
-    int g, tid, warp;
+    int g;                   // group
+    int h;                   // half: columns [32 h, 32 h + 32) of a chunk, coordinates [16 h, 16 h + 16)
+    int q;                   // lane quarter of the warp (TMEM lanes 32 q .. 32 q + 31)
+    int p;                   // particle of the tile: 32 q + lane
+    int gt;                  // thread index within the group
+    uint32_t lane_off;       // TMEM lane offset of the warp
     uint32_t stash;          // TMEM columns parking the particle state during an evaluation
+    uint32_t xch;            // TMEM columns where the two halves exchange partial sums
     uint32_t phF, phB;       // expected phase of barF[i] (bit i), barB
     bool dead;               // a barrier wait timed out or the MMA warp gave up
     volatile int* abort;     // set by whichever role times out first
     unsigned char* smem;
 };
 
-// write a 128-particle row of 32 values, scaled by log2(e) and split hi/lo, into the group's
-// A tiles (the forward contraction then gives the margins in base-2 units)
-__device__ __forceinline__ void write_state_tile(const Group& G, const float (&v)[kD])
+// write this thread's 16 coordinates of its particle's row, scaled by log2(e) and split hi/lo,
+// into the group's A tiles (the forward contraction then gives the margins in base-2 units)
+__device__ __forceinline__ void write_state_tile(const Group& G, const float (&v)[kHalfD])
 {
-    uint32_t hi[16], lo[16];
+    uint32_t hi[8], lo[8];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) split_pair(kLog2e * v[2 * j], kLog2e * v[2 * j + 1], hi[j], lo[j]);
+    for (int j = 0; j < 8; ++j) split_pair(kLog2e * v[2 * j], kLog2e * v[2 * j + 1], hi[j], lo[j]);
     unsigned char* ah = G.smem + kOffA + (G.g * 2 + 0) * kATile;
     unsigned char* al = G.smem + kOffA + (G.g * 2 + 1) * kATile;
-    const int p = G.tid;
+    const int p = G.p;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int cc = 0; cc < 2; ++cc) {
+        const int c = 2 * G.h + cc;            // 16-byte chunk of the 64-byte row: coordinates 8c .. 8c + 7
         const int off = p * 64 + ((c ^ ((p >> 1) & 3)) << 4);
-        *reinterpret_cast<uint4*>(ah + off) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
-        *reinterpret_cast<uint4*>(al + off) = make_uint4(lo[4 * c], lo[4 * c + 1], lo[4 * c + 2], lo[4 * c + 3]);
+        *reinterpret_cast<uint4*>(ah + off) = make_uint4(hi[4 * cc], hi[4 * cc + 1], hi[4 * cc + 2], hi[4 * cc + 3]);
+        *reinterpret_cast<uint4*>(al + off) = make_uint4(lo[4 * cc], lo[4 * cc + 1], lo[4 * cc + 2], lo[4 * cc + 3]);
     }
 }
 
@@ -327,27 +370,28 @@ __device__ void mma_issuer(unsigned char* smem, uint32_t tmem, int g, int nch, v
     if (!mbar_wait(A.barEnd, 0)) *abort = 1;
 }
 
-// log L(x) and grad log L(x) for the group's 128 particles; every thread of the group calls it.
+// log L(x) and grad log L(x) for the group's 128 particles; every thread of the group calls it,
+// the two threads of a particle each taking half the columns of every chunk.
 // Pipeline per chunk c: the forward of chunk c+1 runs into the other D1 buffer while the
 // epilogue of chunk c reads D1[c%2].  Each warp arrives on barA once its rows of the A tile
 // are written and on barR once its rows of the R tile are written (and its reads of D1 are
 // done); the MMA warp then issues the backward of chunk c (it runs while the next chunk's
-// first slice is computed; the R tile is waited for before the next write) and the forward
-// of chunk c+2 into the D1 buffer just read.
-// tc_eval_begin writes the state tile; tc_eval_run does the chunks and returns log L.
-__device__ __forceinline__ void tc_eval_begin(Group& G, const float (&x)[kD])
+// epilogue is computed; the R tile is waited for before the next write) and the forward of
+// chunk c+2 into the D1 buffer just read.
+// tc_eval_begin writes the state tile; tc_eval_run does the chunks and returns this half's
+// part of log L (the halves' parts add up to log L) and its half of grad log L.
+__device__ __forceinline__ void tc_eval_begin(Group& G, const float (&x)[kHalfD])
 {
     write_state_tile(G, x);
     fence_proxy_async();
     tc_before_sync();
     __syncwarp();
-    if ((G.tid & 31) == 0) mbar_arrive(G.a.barA);
+    if ((threadIdx.x & 31) == 0) mbar_arrive(G.a.barA);
 }
-__device__ float tc_eval_run(Group& G, const TcParams& P, float (&grad)[kD])
+__device__ float tc_eval_run(Group& G, const TcParams& P, float (&grad)[kHalfD])
 {
     const int nch = (P.n + kChunk - 1) / kChunk;
-    const int p = G.tid;
-    const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
+    const int p = G.p;
     unsigned char* rh = G.smem + kOffR + (G.g * 2 + 0) * kRTile;
     unsigned char* rl = G.smem + kOffR + (G.g * 2 + 1) * kRTile;
     // The image holds X'_r = s_r X~_r with s_r = 2 y_r - 1 and the state tile holds log2(e) x,
@@ -355,9 +399,9 @@ __device__ float tc_eval_run(Group& G, const TcParams& P, float (&grad)[kD])
     // log sigmoid(s z) = ln 2 (min(u, 0) + log2 q), q = 1 / (1 + 2^-|u|), and d/dz = s sigmoid(-s z),
     // so grad = sum_r sigmoid(-s_r z_r) X'_r with sigmoid(-s z) = 2^-|u| q for u >= 0, q for u < 0.
     // The rows of a pair go through the packed fp32 pair instructions; the sum of min(u, 0)
-    // and the product of q are kept per lane of the pair and per chunk (64 rows: each product
-    // of 32 values in [1/2, 1], no underflow), with one log per chunk.  Padded rows (X' = 0)
-    // give u = 0: log2 q = -1 each, corrected below, and nothing to the gradient.
+    // and the product of q are kept per lane of the pair and per chunk (32 rows of this half:
+    // each product of 16 values in [1/2, 1], no underflow), with one log per chunk.  Padded
+    // rows (X' = 0) give u = 0: log2 q = -1 each, corrected below, and nothing to the gradient.
     float sum_min = 0.0f, logs2 = 0.0f;
     const float2 one2 = make_float2(1.0f, 1.0f);
     for (int c = 0; c < nch; ++c) {
@@ -366,14 +410,15 @@ __device__ float tc_eval_run(Group& G, const TcParams& P, float (&grad)[kD])
         __syncwarp();                             // tcgen05.ld below is warp-aligned
         tc_after_sync();
         float2 prod = one2, mn = make_float2(0.0f, 0.0f);
+        // this half's 32 columns in two 16-column passes (registers: 96 per thread)
 #pragma unroll
-        for (int s = 0; s < kChunk / 32; ++s) {
-            uint32_t v[32];
-            tmem_ld32(G.a.d1[b] + lane_off + s * 32, v);
+        for (int sub = 0; sub < 2; ++sub) {
+            uint32_t v[16];
+            tmem_ld16(G.a.d1[b] + G.lane_off + G.h * kHalfCols + sub * 16, v);
             tmem_wait_ld();
-            uint32_t hi[16], lo[16];
+            uint32_t hi[8], lo[8];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
+            for (int j = 0; j < 16; j += 2) {
                 const float ua = __uint_as_float(v[j]), ub = __uint_as_float(v[j + 1]);
                 const float2 e = make_float2(ex2_approx(-fabsf(ua)), ex2_approx(-fabsf(ub)));
                 const float2 dq = add_f32x2(e, one2);
@@ -387,10 +432,10 @@ __device__ float tc_eval_run(Group& G, const TcParams& P, float (&grad)[kD])
                 prod = mul_f32x2(prod, q);
                 split_pair(r.x, r.y, hi[j / 2], lo[j / 2]);
             }
-            if (s == 0 && c > 0) wait_bwd(G);     // the backward of chunk c-1 has read R
+            if (sub == 0 && c > 0) wait_bwd(G);   // the backward of chunk c-1 has read R
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int chunk = s * 4 + cc;
+            for (int cc = 0; cc < 2; ++cc) {
+                const int chunk = G.h * 4 + sub * 2 + cc;   // 16-byte chunk of the 128-byte R row
                 const int off = p * 128 + ((chunk ^ (p & 7)) << 4);
                 *reinterpret_cast<uint4*>(rh + off) =
                     make_uint4(hi[4 * cc], hi[4 * cc + 1], hi[4 * cc + 2], hi[4 * cc + 3]);
@@ -403,24 +448,59 @@ __device__ float tc_eval_run(Group& G, const TcParams& P, float (&grad)[kD])
         fence_proxy_async();                      // my R rows, visible to the tensor core
         tc_before_sync();                         // my reads of D1[b] before its next forward
         __syncwarp();
-        if ((G.tid & 31) == 0) mbar_arrive(G.a.barR);
+        if ((threadIdx.x & 31) == 0) mbar_arrive(G.a.barR);
     }
     wait_bwd(G);                                  // the backward of the last chunk
     __syncwarp();
     tc_after_sync();
-    uint32_t v[32];
-    tmem_ld32(G.a.d2 + lane_off, v);
+    uint32_t v[kHalfD];
+    tmem_ld16(G.a.d2 + G.lane_off + G.h * kHalfD, v);
     tmem_wait_ld();
 #pragma unroll
-    for (int i = 0; i < kD; ++i) grad[i] = __uint_as_float(v[i]);
+    for (int i = 0; i < kHalfD; ++i) grad[i] = __uint_as_float(v[i]);
     tc_before_sync();
     const float ln2 = 0.69314718055994531f;
-    return ln2 * (sum_min + logs2 + (float)(nch * kChunk - P.n));
+    return ln2 * (sum_min + logs2 + (G.h == 0 ? (float)(nch * kChunk - P.n) : 0.0f));
 }
-__device__ __forceinline__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kD], float (&grad)[kD])
+
+// The two threads of a particle swap a pair of partial sums through TMEM; both return
+// (half 0's, half 1's) so that both form the same totals in the same order.
+__device__ __forceinline__ void exchange(Group& G, float a, float b, float2& h0, float2& h1)
+{
+    tmem_st2f(G.xch + G.lane_off + 2 * G.h, a, b);
+    tmem_wait_st();
+    tc_before_sync();
+    group_sync(G.g);
+    tc_after_sync();
+    const float2 other = tmem_ld2f(G.xch + G.lane_off + 2 * (1 - G.h));
+    const float2 mine = make_float2(a, b);
+    h0 = G.h == 0 ? mine : other;
+    h1 = G.h == 0 ? other : mine;
+}
+
+// log L of the particle (both halves) and this half's gradient
+__device__ __forceinline__ float tc_eval(Group& G, const TcParams& P, const float (&x)[kHalfD],
+                                         float (&grad)[kHalfD])
 {
     tc_eval_begin(G, x);
-    return tc_eval_run(G, P, grad);
+    const float part = tc_eval_run(G, P, grad);
+    float2 a, b;
+    exchange(G, part, 0.0f, a, b);
+    return a.x + b.x;
+}
+
+// this half's 16 normals of block (n, t, k): blocks 4 h .. 4 h + 3 of the particle's draw
+__device__ __forceinline__ void half_normals(const Group& G, const Rng& rng, uint32_t n, uint32_t t, uint32_t k,
+                                             int d, float (&z)[kHalfD])
+{
+#pragma unroll
+    for (int jj = 0; jj < kHalfD / 4; ++jj) {
+        const int j = G.h * (kHalfD / 4) + jj;
+        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (4 * j < d) box_muller4_sfu(rng.block(n, t, k, (uint32_t)j), v);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) z[4 * jj + qq] = (4 * j + qq < d) ? v[qq] : 0.0f;
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -445,8 +525,8 @@ oais_sweep_tc_kernel(const TcParams P)
     if (threadIdx.x == 0) {
         for (int g = 0; g < kGroups; ++g) {
             for (int i = 0; i < 3; ++i) mbar_init(saddr(&bars[kBarsPerGroup * g + i]), 1);
-            mbar_init(saddr(&bars[kBarsPerGroup * g + 3]), kGroupThreads / 32);   // one arrival per warp
-            mbar_init(saddr(&bars[kBarsPerGroup * g + 4]), kGroupThreads / 32);
+            mbar_init(saddr(&bars[kBarsPerGroup * g + 3]), kGroupWarps);   // one arrival per warp
+            mbar_init(saddr(&bars[kBarsPerGroup * g + 4]), kGroupWarps);
             mbar_init(saddr(&bars[kBarsPerGroup * g + 5]), 1);
         }
         *abort = 0;
@@ -472,10 +552,17 @@ oais_sweep_tc_kernel(const TcParams P)
 
     Group G;
     G.g = threadIdx.x / kGroupThreads;
-    G.tid = threadIdx.x % kGroupThreads;
-    G.warp = G.tid / 32;
+    G.gt = threadIdx.x % kGroupThreads;
+    {
+        const int wg = G.gt / 32;
+        G.h = wg / 4;
+        G.q = wg % 4;                                  // = (CTA warp index) % 4: the warp's TMEM lane quarter
+        G.p = G.q * 32 + (threadIdx.x & 31);
+    }
     G.a = group_addr(smem, tmem, G.g);
-    G.stash = tmem + (uint32_t)(G.g * 256 + 160);   // 96 free columns: x, grad, w
+    G.lane_off = (uint32_t)(G.q * 32) << 16;
+    G.stash = tmem + (uint32_t)(G.g * 256 + 160);  // x at + 16 h, grad at + 32 + 16 h
+    G.xch = tmem + (uint32_t)(G.g * 256 + 224);
     G.phF = 0;
     G.phB = 0;
     G.dead = false;
@@ -485,13 +572,15 @@ oais_sweep_tc_kernel(const TcParams P)
 
     volatile EvalDesc* desc = reinterpret_cast<volatile EvalDesc*>(smem + kOffDesc + 16 * G.g);
     const int d = P.d;
+    const int i0 = G.h * kHalfD;                   // this thread's coordinates: i0 .. i0 + 15
     const float sref = (float)S.ref_scale;
     const float inv_s2 = 1.0f / (sref * sref);
-    const int lane = G.tid & 31;
-    const uint32_t lane_off = (uint32_t)(G.warp * 32) << 16;
+    const int lane = threadIdx.x & 31;
+    const uint32_t sx = G.stash + G.lane_off + (uint32_t)(G.h * kHalfD);
+    const uint32_t sg = sx + (uint32_t)kD;
     // thread 0 says what the MMA warp does at the next evaluation, before the group's barA
     auto announce = [&](StepPartial* rec, int slot) {
-        if (G.tid == 0) {
+        if (G.gt == 0) {
             desc->rec = rec;
             desc->slot = slot;
             desc->stop = 0;
@@ -530,21 +619,21 @@ oais_sweep_tc_kernel(const TcParams P)
             t1 = T;
             pos = pos1;
         }
-        const int64_t n64 = tile * kGroupThreads + G.tid;
+        const int64_t n64 = tile * kTile + G.p;
         const bool active = n64 < S.N;
         const uint32_t n = (uint32_t)(S.n_offset + (active ? n64 : S.N - 1));
-        float x[kD], gl[kD], ell;
+        float x[kHalfD], gl[kHalfD], ell;
         double logw;
         if (t0 == 1) {
-            normals_sfu<kD>(S.mv.rng, n, 0u, 0u, d, x);
+            half_normals(G, S.mv.rng, n, 0u, 0u, d, x);
 #pragma unroll
-            for (int i = 0; i < kD; ++i) x[i] *= sref;
+            for (int i = 0; i < kHalfD; ++i) x[i] *= sref;
             announce(nullptr, 0);
             ell = tc_eval(G, P, x, gl);
             logw = 0.0;
         } else {
             // the tile's first part ran at the start of the next slot: wait for its state
-            if (G.tid == 0 && !G.dead) {
+            if (G.gt == 0 && !G.dead) {
                 const uint64_t w0 = globaltimer();
                 while (ld_acquire_gpu(P.handed + tile) == 0) {
                     if (*G.abort || globaltimer() - w0 > kWaitLimitNs) { G.dead = true; *G.abort = 1; break; }
@@ -554,9 +643,9 @@ oais_sweep_tc_kernel(const TcParams P)
             group_sync(G.g);
             (void)ld_acquire_gpu(P.handed + tile);
 #pragma unroll
-            for (int i = 0; i < kD; ++i) {
-                x[i] = (active && i < d) ? xo[(size_t)i * S.N + n64] : 0.0f;
-                gl[i] = (active && i < d) ? P.grad_state[(size_t)i * S.N + n64] : 0.0f;
+            for (int i = 0; i < kHalfD; ++i) {
+                x[i] = (active && i0 + i < d) ? xo[(size_t)(i0 + i) * S.N + n64] : 0.0f;
+                gl[i] = (active && i0 + i < d) ? P.grad_state[(size_t)(i0 + i) * S.N + n64] : 0.0f;
             }
             ell = active ? (float)S.ell_out[n64] : 0.0f;
             logw = active ? S.logw[n64] : 0.0;
@@ -569,55 +658,61 @@ oais_sweep_tc_kernel(const TcParams P)
             const float lg = (float)(beta_t - beta_prev) * ell;
             beta_prev = beta_t;
             const int slot = t & 1;
-            warp_piece(logw, lg, active, &pieces[slot][G.warp]);
+            if (G.h == 0) warp_piece(logw, lg, active, &pieces[slot][G.q]);
             logw += (double)lg;
             unsigned acc = 0;
-            const float beta = (float)beta_t, e = (float)eps_t, h = 0.5f * e;
+            const float beta = (float)beta_t, e = (float)eps_t, hh = 0.5f * e;
             for (int k = 0; k < S.mv.K; ++k) {
-                // MALA (Sec. 2.1.1 kernel family): x' = x + e w with w = z + (e/2) grad log pi(x)
-                float w[kD];
-                normals_sfu<kD>(S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, w);
+                // MALA (Sec. 2.1.1 kernel family): x' = x + e w with w = z + (e/2) grad log pi(x);
+                // each half proposes its 16 coordinates, the sums over coordinates add up
                 float zz = 0.0f, dxx = 0.0f;
                 {
-                    float xp[kD];
+                    float w[kHalfD], xp[kHalfD];
+                    half_normals(G, S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, w);
 #pragma unroll
-                    for (int i = 0; i < kD; ++i) {
+                    for (int i = 0; i < kHalfD; ++i) {
                         const float gpi = -x[i] * inv_s2 + beta * gl[i];
                         zz += w[i] * w[i];
-                        w[i] = __fmaf_rn(h, gpi, w[i]);
+                        w[i] = __fmaf_rn(hh, gpi, w[i]);
                         xp[i] = __fmaf_rn(e, w[i], x[i]);
                         dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
                     }
-                    // park x, grad and w in the group's free TMEM columns while the evaluation
-                    // runs (registers go to the epilogue), then bring them back; x' is rebuilt
-                    // from them with the same rounding
-                    tmem_st32(G.stash + lane_off, x);
-                    tmem_st32(G.stash + lane_off + 32, gl);
-                    tmem_st32(G.stash + lane_off + 64, w);
+                    // park x and grad in the group's free TMEM columns while the evaluation runs
+                    // (registers go to the epilogue); w is drawn again afterwards and x'
+                    // rebuilt from them with the same rounding
+                    tmem_st16f(sx, x);
+                    tmem_st16f(sg, gl);
                     tmem_wait_st();
                     // the first evaluation of step t: step t - 1's record is complete
                     const bool merge = k == 0 && t > t0;
                     announce(merge ? S.partials + (int64_t)(t - 2) * P.tiles + tile : nullptr, (t - 1) & 1);
                     tc_eval_begin(G, xp);
                 }
-                float glp[kD];
-                const float ellp = tc_eval_run(G, P, glp);
+                float glp[kHalfD];
+                const float part = tc_eval_run(G, P, glp);
                 __syncwarp();
-                tmem_ld32f(G.stash + lane_off, x);
-                tmem_ld32f(G.stash + lane_off + 32, gl);
-                tmem_ld32f(G.stash + lane_off + 64, w);
+                tmem_ld16f(sx, x);
+                tmem_ld16f(sg, gl);
+                float w[kHalfD];
+                half_normals(G, S.mv.rng, n, (uint32_t)t, (uint32_t)k, d, w);
                 float rev = 0.0f;
 #pragma unroll
-                for (int i = 0; i < kD; ++i) {
+                for (int i = 0; i < kHalfD; ++i) {
+                    const float gpi = -x[i] * inv_s2 + beta * gl[i];
+                    w[i] = __fmaf_rn(hh, gpi, w[i]);
                     const float xp = __fmaf_rn(e, w[i], x[i]);
-                    const float q = w[i] + h * (-xp * inv_s2 + beta * glp[i]);
-                    rev += q * q;
+                    const float qv = w[i] + hh * (-xp * inv_s2 + beta * glp[i]);
+                    rev += qv * qv;
                 }
-                const float log_alpha = -0.5f * dxx * inv_s2 + beta * (ellp - ell) - 0.5f * (rev - zz);
+                // the halves' parts: log L(x') and -(1/2)(|x'|^2 - |x|^2)/s^2 - (1/2)(|w'|^2 - |z|^2)
+                float2 a0, a1;
+                exchange(G, part, -0.5f * dxx * inv_s2 - 0.5f * (rev - zz), a0, a1);
+                const float ellp = a0.x + a1.x;
+                const float log_alpha = (a0.y + a1.y) + beta * (ellp - ell);
                 const float logu = mh_log_uniform(S.mv.rng, n, (uint32_t)t, (uint32_t)k, 0.0f);
                 if (logu < log_alpha) {
 #pragma unroll
-                    for (int i = 0; i < kD; ++i) { x[i] = __fmaf_rn(e, w[i], x[i]); gl[i] = glp[i]; }
+                    for (int i = 0; i < kHalfD; ++i) { x[i] = __fmaf_rn(e, w[i], x[i]); gl[i] = glp[i]; }
                     ell = ellp;
                     ++acc;
                 }
@@ -625,32 +720,34 @@ oais_sweep_tc_kernel(const TcParams P)
             acc = active ? acc : 0u;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-            if (lane == 0) pieces[slot][G.warp].acc = acc;
+            if (G.h == 0 && lane == 0) pieces[slot][G.q].acc = acc;
         }
         // the piece's last step's record (the MMA warp merged the others)
         group_sync(G.g);
-        if (G.warp == 0) merge_pieces(lane, pieces[t1 & 1], S.partials + (int64_t)(t1 - 1) * P.tiles + tile);
+        if (G.gt < 32) merge_pieces(lane, pieces[t1 & 1], S.partials + (int64_t)(t1 - 1) * P.tiles + tile);
         if (active) {
-            S.logw[n64] = logw;
-            S.ell_out[n64] = (double)ell;
+            if (G.h == 0) {
+                S.logw[n64] = logw;
+                S.ell_out[n64] = (double)ell;
+            }
 #pragma unroll
-            for (int i = 0; i < kD; ++i) if (i < d) xo[(size_t)i * S.N + n64] = x[i];
+            for (int i = 0; i < kHalfD; ++i) if (i0 + i < d) xo[(size_t)(i0 + i) * S.N + n64] = x[i];
             if (t1 < T) {
 #pragma unroll
-                for (int i = 0; i < kD; ++i) if (i < d) P.grad_state[(size_t)i * S.N + n64] = gl[i];
-            } else if (!isfinite(logw) || !isfinite(ell)) {
+                for (int i = 0; i < kHalfD; ++i) if (i0 + i < d) P.grad_state[(size_t)(i0 + i) * S.N + n64] = gl[i];
+            } else if (G.h == 0 && (!isfinite(logw) || !isfinite(ell))) {
                 atomicOr(S.status, 1u);
             }
         }
         if (t1 < T) __threadfence();
         group_sync(G.g);                      // pieces slots free; the state is stored
-        if (t1 < T && G.tid == 0) st_release_gpu(P.handed + tile, 1);
+        if (t1 < T && G.gt == 0) st_release_gpu(P.handed + tile, 1);
     }
     // no more evaluations: release the MMA warp
-    if (G.tid == 0) desc->stop = 1;
+    if (G.gt == 0) desc->stop = 1;
     __syncwarp();
     if (lane == 0) mbar_arrive(G.a.barA);
-    if (G.dead && G.tid == 0) atomicOr(S.status, 2u);
+    if (G.dead && G.gt == 0) atomicOr(S.status, 2u);
     tc_before_sync();
     __syncthreads();
     if (threadIdx.x < 32) tmem_dealloc(tmem, kTmemCols);
