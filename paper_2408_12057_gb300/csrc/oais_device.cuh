@@ -15,6 +15,41 @@
 
 namespace oais {
 
+// packed fp32 pairs (one instruction for both lanes of a pair, round to nearest even)
+__device__ __forceinline__ float2 add_f32x2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub_f32x2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul_f32x2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 fma_f32x2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 struct Philox4 { uint32_t v[4]; };
 
 __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -149,9 +184,18 @@ __device__ __forceinline__ bool admissible(double v) { return !isnan(v) && v != 
 // Warp part: v_i = lw + i * lg for the lane's particle (or -inf if inactive).
 // Writes the warp's (m_i, s_i) for i = 0..2 and u (ws[3], on m_0) through lane 0.  By default the offsets from the
 // anchor particle and from the warp maximum are fp64 differences rounded once.  kFast (the
-// tensor-core kernels, whose particle arithmetic is fp32 and whose fp64 pipe is slow): both
-// come from two fp64 differences per particle (lw - lw_a, lg - lg_a) in fp32, which adds
-// about 2^-24 |offset from the anchor| to each exponent.
+// forms whose particle arithmetic is fp32; the fp64 pipe of this part is slow): the offsets
+// come from two fp64 differences per particle, lw - lw_a and lg - lg_a, rounded to fp32,
+// which adds about 2^-24 (|lw - lw_a| + i |lg - lg_a|) to exponent i.  The anchor a is the
+// warp's largest v_1 (found from a first pass of the same form anchored at the first lanes
+// with finite values), so that the error is small where the weight is: with an arbitrary
+// anchor, spreads of 10^4 in log w (a large first step of a likelihood over hundreds of
+// rows) moved D_hat by ~1e-3.  Both paths let log w = -inf (a zero weight) and log g = -inf
+// (a state outside the likelihood's support) drop out of the moments they zero.
+__device__ __forceinline__ bool finite_bits(double v)
+{
+    return (__double2hiint(v) & 0x7FF00000) != 0x7FF00000;   // exponent field not all ones
+}
 template <bool kFast = false>
 __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool active,
                                                     double* wm /*3*/, float* ws /*4*/)
@@ -159,9 +203,9 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
     const unsigned full = 0xFFFFFFFFu;
     const bool lead = (threadIdx.x & 31) == 0;
     if (kFast) {
-        // the tensor-core kernels: log w and log g finite for every active particle
-        const unsigned act = __ballot_sync(full, active);
-        if (act == 0) {
+        const bool fw = active && finite_bits(lw), fg = active && finite_bits(lg);
+        const unsigned bw = __ballot_sync(full, fw);
+        if (bw == 0) {
             if (lead) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) { wm[i] = -INFINITY; ws[i] = 0.0f; }
@@ -169,18 +213,28 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
             }
             return;
         }
-        // anchor = a representative active value: avoids fp64 max over the warp
-        const int src = __ffs(act) - 1;
-        const double a0 = __shfl_sync(full, lw, src), b0 = __shfl_sync(full, lg, src);
+        const unsigned bg = __ballot_sync(full, fg);
+        double a0 = __shfl_sync(full, lw, __ffs(bw) - 1);
+        double b0 = bg ? __shfl_sync(full, lg, __ffs(bg) - 1) : 0.0;
+        if (__ballot_sync(full, fw && fg)) {
+            // re-anchor at the lane with the largest v_1 (first-pass estimate)
+            const float f1 = (fw && fg) ? (float)(lw - a0) + (float)(lg - b0) : -INFINITY;
+            float m1 = f1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m1 = fmaxf(m1, __shfl_xor_sync(full, m1, o));
+            const int src = __ffs(__ballot_sync(full, f1 == m1)) - 1;
+            a0 = __shfl_sync(full, lw, src);
+            b0 = __shfl_sync(full, lg, src);
+        }
         const float dw = (float)(lw - a0), dg = (float)(lg - b0);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const float f = active ? dw + (float)i * dg : -INFINITY;
+            const float f = !active ? -INFINITY : (i == 0 ? dw : dw + (float)i * dg);
             float mx = f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
-            float e = active ? __expf(f - mx) : 0.0f;
-            float u = i == 0 ? e * (float)lg : 0.0f;
+            float e = f > -INFINITY ? __expf(f - mx) : 0.0f;
+            float u = (i == 0 && e > 0.0f) ? e * (float)lg : 0.0f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
             if (i == 0) {
@@ -188,7 +242,7 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
                 for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
             }
             if (lead) {
-                wm[i] = a0 + i * b0 + (double)mx;
+                wm[i] = mx > -INFINITY ? a0 + i * b0 + (double)mx : -INFINITY;
                 ws[i] = e;
                 if (i == 0) ws[3] = u;
             }
@@ -236,10 +290,10 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
 // fp64.  kFast: the rescaling takes d_j = m_j - M (exact in fp64) rounded to fp32 and an fp32
 // exponential, and the sum is fp32 (|d| e^d <= 1/e bounds the effect of the rounding of d on S
 // by 2^-24 / e of S; the pieces s_j are fp32 sums already), a handful of fp64 instructions
-// instead of an fp64 exponential per moment: the tensor-core kernels use it, the fp64 pipe
-// being slow on this part.  Lanes < W take part (every lane of the warp calls it); W is a
+// instead of an fp64 exponential per moment: the forms with fp32 particle arithmetic use it,
+// the fp64 pipe being slow on this part.  Lanes < W take part (every lane of the warp calls it); W is a
 // power of two <= 32.
-// kFast = false keeps the rescaling and the sum in fp64 (the CUDA-core forms).  Lane j < W
+// kFast = false keeps the rescaling and the sum in fp64 (the fp64 forms).  Lane j < W
 // passes piece j's shifts m[3], sums s[3] and count acc; lane 0 writes the record.
 template <int W, bool kFast>
 __device__ __forceinline__ void merge_lane_pieces(int lane, const double (&mj)[3], const float (&sj)[4],
@@ -306,12 +360,12 @@ __device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3
 
 // CTA part: warp 0 merges the W warps' pieces and writes one record.  Call after a
 // __syncthreads that follows warp_moment_partial.
-template <int W>
+template <int W, bool kFast = false>
 __device__ __forceinline__ void cta_moment_record(const double (*wm)[3], const float (*ws)[4],
                                                   const unsigned* wacc, StepPartial* out)
 {
     if ((threadIdx.x >> 5) != 0) return;
-    merge_warp_pieces<W, false>(threadIdx.x & 31, wm, ws, wacc, out);
+    merge_warp_pieces<W, kFast>(threadIdx.x & 31, wm, ws, wacc, out);
 }
 
 // merge (m, s) pairs: exp(m) s + exp(m') s'

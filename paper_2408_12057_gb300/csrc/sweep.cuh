@@ -44,6 +44,16 @@ struct SweepParams {
 
 template <typename R> __device__ __forceinline__ R rsq(R a) { return a * a; }
 
+// Forms with fp32 particle arithmetic take the moment partials with fp32 offsets and
+// rescaling (warp_moment_partial / merge_lane_pieces, kFast), and their random-walk moves the
+// special-function-unit Box-Muller (absolute error of order 1e-6 in z, like the tensor-core
+// kernels): the fp64 pipe of this part is slow, and with a cheap target (the mixture: two
+// moves of a few hundred operations a step) the per-step fp64 bookkeeping and the exact
+// Box-Muller took half of the step.  MALA and HMC keep the exact Box-Muller: their gradient
+// evaluations dominate the step, and an HMC trajectory amplifies an error in its momentum.
+// The fp64 forms keep both exact.
+template <typename R> constexpr bool kFp32 = sizeof(R) == 4;
+
 template <class Tgt, int MOVE, int D, typename R>
 __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[D], R& ell,
                                         R (&gl)[D], double beta_t, double eps_t, uint32_t n,
@@ -52,7 +62,8 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
     constexpr bool GRAD = (MOVE != kRwmh);
     const R beta = (R)beta_t;
     R z[D];
-    normals<D>(P.rng, n, t, k, d, z);
+    if constexpr (kFp32<R> && MOVE == kRwmh) normals_sfu<D>(P.rng, n, t, k, d, z);
+    else normals<D>(P.rng, n, t, k, d, z);
     R xp[D], glp[D];
     R log_alpha;
     R ellp;
@@ -63,11 +74,26 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
             const int c = gm % 3;
             sd = c == 0 ? R(0.1) : (c == 1 ? R(1) : R(10));
         }
-        R dxx = 0;
+        R dxx = 0;                                    // |xp|^2 - |x|^2
+        if constexpr (kFp32<R> && D % 2 == 0) {
+            // two coordinates per packed instruction
+            const float2 sd2 = make_float2(sd, sd);
+            float2 a2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            xp[i] = x[i] + sd * z[i];
-            dxx += (xp[i] - x[i]) * (xp[i] + x[i]);   // |xp|^2 - |x|^2
+            for (int i = 0; i < D; i += 2) {
+                const float2 x2 = make_float2(x[i], x[i + 1]);
+                const float2 p2 = fma_f32x2(sd2, make_float2(z[i], z[i + 1]), x2);
+                xp[i] = p2.x;
+                xp[i + 1] = p2.y;
+                a2 = fma_f32x2(sub_f32x2(p2, x2), add_f32x2(p2, x2), a2);
+            }
+            dxx = a2.x + a2.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                xp[i] = x[i] + sd * z[i];
+                dxx += (xp[i] - x[i]) * (xp[i] + x[i]);
+            }
         }
         ellp = tg.template eval<false>(xp, glp);
         log_alpha = -R(0.5) * dxx * inv_s2 + beta * (ellp - ell);
@@ -160,7 +186,7 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
         const double lg = log_increment(beta_t - beta_prev, (double)ell);
         beta_prev = beta_t;
         const int slot = t & 1;
-        warp_moment_partial(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
+        warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
         logw += lg;
         unsigned acc = 0;
         for (int k = 0; k < P.mv.K; ++k)
@@ -171,7 +197,7 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if (lane == 0) s_acc[slot][warp] = acc;
         __syncthreads();
-        cta_moment_record<kSweepThreads / 32>(s_m[slot], s_s[slot], s_acc[slot],
+        cta_moment_record<kSweepThreads / 32, kFp32<R>>(s_m[slot], s_s[slot], s_acc[slot],
                                               P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
     }
     if (!admissible(logw) || !admissible((double)ell)) bad = 1;
@@ -253,7 +279,7 @@ asmc_step_kernel(const StepParams P, Tgt tg)
 
     const double beta_t = P.beta[P.t], eps_t = P.eps[P.t - 1];
     const double lg = log_increment(beta_t - P.beta[P.t - 1], (double)ell);
-    warp_moment_partial(logw, lg, active, s_m[warp], s_s[warp]);
+    warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[warp], s_s[warp]);
     logw += lg;
     unsigned acc = 0;
     for (int k = 0; k < P.mv.K; ++k)
@@ -264,13 +290,13 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if (lane == 0) s_acc[warp] = acc;
     __syncthreads();
-    cta_moment_record<kSweepThreads / 32>(s_m, s_s, s_acc,
+    cta_moment_record<kSweepThreads / 32, kFp32<R>>(s_m, s_s, s_acc,
                                           P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
     __syncthreads();
     // ESS pieces of w_{t^-}: LSE of log w (slot 0) and of 2 log w (slot 1)
-    warp_moment_partial(logw, logw, active, s_m[warp], s_s[warp]);
+    warp_moment_partial<kFp32<R>>(logw, logw, active, s_m[warp], s_s[warp]);
     __syncthreads();
-    cta_moment_record<kSweepThreads / 32>(s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
+    cta_moment_record<kSweepThreads / 32, kFp32<R>>(s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
     if (active) {
         R* xw = reinterpret_cast<R*>(P.x[b]);
         R* gw = reinterpret_cast<R*>(P.gl[b]);

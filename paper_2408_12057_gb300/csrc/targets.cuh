@@ -105,14 +105,28 @@ struct GmmTarget {
 
     template <bool GRAD>
     __device__ R eval(const R (&x)[D], R (&g)[D]) const {
+        // fp32: the squared distances, |x|^2 and the gradient's mixture sums two coordinates
+        // per packed instruction (even and odd coordinates summed apart, then added)
+        constexpr bool kPair = sizeof(R) == 4 && D % 2 == 0;
         R q[kMaxK];
         R mx = R(-INFINITY);
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k) {
             if (k < K) {
                 R acc = 0;
+                if constexpr (kPair) {
+                    const float2* m2 = reinterpret_cast<const float2*>(sm + k * D);
+                    float2 a2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                for (int i = 0; i < D; ++i) { const R r = x[i] - sm[k * D + i]; acc += r * r; }
+                    for (int i = 0; i < D / 2; ++i) {
+                        const float2 r = sub_f32x2(make_float2(x[2 * i], x[2 * i + 1]), m2[i]);
+                        a2 = fma_f32x2(r, r, a2);
+                    }
+                    acc = a2.x + a2.y;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) { const R r = x[i] - sm[k * D + i]; acc += r * r; }
+                }
                 q[k] = R(-0.5) * acc * inv_v;
                 mx = q[k] > mx ? q[k] : mx;
             }
@@ -121,16 +135,38 @@ struct GmmTarget {
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k)
             if (k < K) { q[k] = exp_(q[k] - mx); sum += q[k]; }
+        if constexpr (kPair) {
+            float2 a2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < D; ++i) xx += x[i] * x[i];
+            for (int i = 0; i < D / 2; ++i) {
+                const float2 v = make_float2(x[2 * i], x[2 * i + 1]);
+                a2 = fma_f32x2(v, v, a2);
+            }
+            xx = a2.x + a2.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) xx += x[i] * x[i];
+        }
         if (GRAD) {
             const R inv = R(1) / sum;
+            if constexpr (kPair) {
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                R acc = 0;
+                for (int i = 0; i < D / 2; ++i) {
+                    float2 a2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                for (int k = 0; k < kMaxK; ++k) if (k < K) acc += q[k] * sm[k * D + i];
-                g[i] = (acc * inv - x[i]) * inv_v + x[i] * inv_s2;
+                    for (int k = 0; k < kMaxK; ++k)
+                        if (k < K) a2 = fma_f32x2(make_float2(q[k], q[k]), reinterpret_cast<const float2*>(sm + k * D)[i], a2);
+                    g[2 * i] = (a2.x * inv - x[2 * i]) * inv_v + x[2 * i] * inv_s2;
+                    g[2 * i + 1] = (a2.y * inv - x[2 * i + 1]) * inv_v + x[2 * i + 1] * inv_s2;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    R acc = 0;
+#pragma unroll
+                    for (int k = 0; k < kMaxK; ++k) if (k < K) acc += q[k] * sm[k * D + i];
+                    g[i] = (acc * inv - x[i]) * inv_v + x[i] * inv_s2;
+                }
             }
         }
         return mx + log_(sum) + log_const + R(0.5) * xx * inv_s2;
