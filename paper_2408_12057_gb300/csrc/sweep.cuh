@@ -149,8 +149,15 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
     return acc;
 }
 
+// CTAs per SM that the register allocation of the sweep must allow (0: the compiler's
+// choice): the random-walk step of the mixture is cheap and latency-bound, and 8 CTAs (32
+// warps) per SM at 64 registers ran it 3 % faster than the 94 registers the compiler picks
+// (an explicit 1 gave 122 registers and 20 % slower)
+template <class Tgt, int MOVE> struct SweepMinBlocks { static constexpr int value = 0; };
+template <typename R, int D> struct SweepMinBlocks<GmmTarget<R, D>, kRwmh> { static constexpr int value = 8; };
+
 template <class Tgt, int MOVE, int D, typename R>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads, (SweepMinBlocks<Tgt, MOVE>::value))
 oais_sweep_kernel(const SweepParams P, Tgt tg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -246,7 +253,7 @@ struct StepParams {
 };
 
 template <class Tgt, int MOVE, int D, typename R>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads, (SweepMinBlocks<Tgt, MOVE>::value))
 asmc_step_kernel(const StepParams P, Tgt tg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
