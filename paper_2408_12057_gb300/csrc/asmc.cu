@@ -20,34 +20,66 @@ constexpr int kScanTile = kScanThreads * kScanItems;   // particles per scan blo
 
 int scan_blocks(int64_t N) { return (int)((N + kScanTile - 1) / kScanTile); }
 
-__global__ void __launch_bounds__(256)
+// The ESS test merges the per-CTA pieces (m_j, s_j) of log w and 2 log w into
+// LSE = M + log sum_j s_j exp(m_j - M) in two passes: the largest shift M, then the rescaled
+// sum, whose factors exp(m_j - M) take the fp64 difference (<= 0) rounded once to fp32 and an
+// fp32 exponential (relative effect on the sum below a few 1e-8, the pieces themselves being
+// fp32 sums).  One pass of dependent fp64 merges (an fp64 exponential per piece, each waiting
+// for the last) took 70 us for 2 048 pieces on this part's slow fp64 pipe; the two passes
+// have no chain and no fp64 exponential.
+constexpr int kDecideThreads = 512;
+__device__ __forceinline__ double block_reduce_max(double v, double* sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    v = lane < kDecideThreads / 32 ? sh[lane] : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;                                     // in every thread
+}
+__device__ __forceinline__ double block_reduce_sum(double v, double* sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    v = lane < kDecideThreads / 32 ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kDecideThreads)
 asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ ess_parts, int nparts, int t, int T,
                    const double* __restrict__ beta, double ess_frac, int64_t N, Rng rng, double* ess_trace,
                    int* resampled)
 {
-    __shared__ double sm[2][256], ss[2][256];
+    __shared__ double sh[kDecideThreads / 32];
     const int tid = threadIdx.x;
-    double m[2] = {-INFINITY, -INFINITY}, s[2] = {0.0, 0.0};
-    for (int j = tid; j < nparts; j += 256) {
-        lse_merge(m[0], s[0], ess_parts[j].m[0], ess_parts[j].s[0]);
-        lse_merge(m[1], s[1], ess_parts[j].m[1], ess_parts[j].s[1]);
-    }
-    sm[0][tid] = m[0]; ss[0][tid] = s[0]; sm[1][tid] = m[1]; ss[1][tid] = s[1];
-    __syncthreads();
-    for (int stride = 128; stride > 0; stride >>= 1) {
-        if (tid < stride) {
+    double M[2], S[2];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                double mm = sm[i][tid], s0 = ss[i][tid];
-                lse_merge(mm, s0, sm[i][tid + stride], ss[i][tid + stride]);
-                sm[i][tid] = mm; ss[i][tid] = s0;
+    for (int i = 0; i < 2; ++i) {
+        double mx = -INFINITY;
+        for (int j = tid; j < nparts; j += kDecideThreads) mx = fmax(mx, ess_parts[j].m[i]);
+        M[i] = block_reduce_max(mx, sh);
+        double sum = 0.0;
+        if (M[i] > -INFINITY) {
+            for (int j = tid; j < nparts; j += kDecideThreads) {
+                const double m = ess_parts[j].m[i];
+                if (m > -INFINITY) sum += ess_parts[j].s[i] * (double)expf((float)(m - M[i]));
             }
         }
-        __syncthreads();
+        S[i] = block_reduce_sum(sum, sh);
     }
     if (tid == 0) {
-        const double lse1 = sm[0][0] + log(ss[0][0]);
-        const double lse2 = sm[1][0] + log(ss[1][0]);
+        const double lse1 = M[0] + log(S[0]);
+        const double lse2 = M[1] + log(S[1]);
         const double ess = exp(2.0 * lse1 - lse2);
         st->cur ^= st->pend;             // the previous step's gather is now the live buffer
         // the last step (t = T, or beta_t = 1 for a schedule found online) closes the segment
@@ -180,7 +212,7 @@ asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const dou
 cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int nparts, double ess_frac, double* bsum,
                                     double* boff, double* cdf, double* ess_trace, int* resampled, cudaStream_t s)
 {
-    asmc_decide_kernel<<<1, 256, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
+    asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
                                          ess_trace, resampled);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
@@ -193,7 +225,7 @@ cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts,
                                  bool grad, bool fp64, double* bsum, double* boff, double* cdf,
                                  double* ess_trace, int* resampled, int64_t* ancestors, cudaStream_t s)
 {
-    asmc_decide_kernel<<<1, 256, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
+    asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
                                          ess_trace, resampled);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
