@@ -265,7 +265,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     // online conditional-ESS rounds (CUDA-core form): offsets, anchors, candidate sums, state,
     // the schedule found online and its step sizes
     L.zja_fg = take(sizeof(float2) * (size_t)N);
-    L.zja_anchor = take(sizeof(double2) * (size_t)zja_grid(N));
+    L.zja_anchor = take((sizeof(double2) + sizeof(float2)) * (size_t)zja_grid(N));   // anchors, then their fp32 offsets
     L.zja_part = take(zja_part_bytes(N));
     L.zja_state = take(sizeof(ZjaState));
     L.zja_beta = take(sizeof(double) * (T_max + 1));

@@ -16,9 +16,13 @@
 // advances).
 //
 // Per pass: zja_pass_kernel writes, per CTA, the shifted sums of the three weighted powers of
-// g at each candidate; zja_narrow_kernel (one CTA) merges them, evaluates the candidates and
-// narrows the bracket.  The particles' (log w, log L) enter as fp32 offsets from a per-CTA
-// anchor (zja_prep_kernel, once per step), so the candidate sums need no fp64 exponentials.
+// g at each candidate; zja_narrow_kernel (one CTA, a warp per sum) merges them, evaluates the
+// candidates and narrows the bracket.  The particles' (log w, log L) enter as fp32 offsets
+// from a per-CTA anchor, the CTA's particle of largest log w (zja_prep_kernel, once per step),
+// and the anchors as fp32 offsets from the largest of them (zja_anchor_kernel), so neither the
+// candidate sums nor their merge need fp64 arithmetic; the reference anchor cancels from the
+// ratios the search compares.  (The merge had taken fp64 offsets per CTA and sum in a few
+// threads, 30 us per pass on this part's slow fp64 pipe.)
 #include "internal.h"
 
 namespace oais {
@@ -31,33 +35,72 @@ constexpr int kZjaPasses = 6;                 // one geometric scan, five linear
 int zja_grid(int64_t N) { return (int)((N + kZjaThreads - 1) / kZjaThreads); }
 size_t zja_part_bytes(int64_t N) { return sizeof(float2) * kZjaSums * (size_t)zja_grid(N); }
 
-// offsets of each particle from its CTA's anchor: f = log w - log w_a, g = log L - log L_a
-// (the anchor: the CTA's first particle with finite log w and log L; -inf offsets mark a zero
-// weight, g = -inf a state outside the likelihood's support)
+// offsets of each particle from its CTA's anchor: f = log w - log w_a, g = log L - log L_a.
+// The anchor is the CTA's particle of largest log w among those with finite log w and log L
+// (or, if none has both, of largest finite log w, with log L_a = 0: then every g is -inf);
+// -inf offsets mark a zero weight, g = -inf a state outside the likelihood's support.
+__device__ __forceinline__ unsigned long long zja_order_key(double v)
+{
+    // a 64-bit key ordered like v (for the block maximum by an integer atomic)
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
 __global__ void __launch_bounds__(kZjaThreads)
 zja_prep_kernel(const AsmcState* st, const StepParams P, float2* __restrict__ fg, double2* __restrict__ anchor)
 {
-    __shared__ int first;
-    if (threadIdx.x == 0) first = kZjaThreads;
+    __shared__ unsigned long long best_both, best_w;
+    __shared__ int who_both, who_w;
+    __shared__ double a_lw, a_ell;
+    if (threadIdx.x == 0) { best_both = 0ull; best_w = 0ull; who_both = kZjaThreads; who_w = kZjaThreads; }
     __syncthreads();
     const int64_t n = (int64_t)blockIdx.x * kZjaThreads + threadIdx.x;
     const int b = st->cur ^ st->pend;
     const double lw = n < P.N ? P.logw[n] : -INFINITY;
     const double ell = n < P.N ? P.ell[b][n] : -INFINITY;
-    const bool ok = lw > -INFINITY && ell > -INFINITY;
-    if (ok) atomicMin(&first, (int)threadIdx.x);
+    const bool fw = lw > -INFINITY, both = fw && ell > -INFINITY;
+    const unsigned long long key = zja_order_key(lw);
+    if (both) atomicMax(&best_both, key);
+    if (fw) atomicMax(&best_w, key);
     __syncthreads();
-    __shared__ double a_lw, a_ell;
-    if ((int)threadIdx.x == first) { a_lw = lw; a_ell = ell; }
+    if (both && key == best_both) atomicMin(&who_both, (int)threadIdx.x);
+    if (fw && key == best_w) atomicMin(&who_w, (int)threadIdx.x);
     __syncthreads();
-    if (first == kZjaThreads) {
+    const bool any_both = who_both < kZjaThreads;
+    if ((int)threadIdx.x == (any_both ? who_both : who_w)) { a_lw = lw; a_ell = any_both ? ell : 0.0; }
+    __syncthreads();
+    if (who_w == kZjaThreads) {               // no finite weight in this CTA
         if (n < P.N) fg[n] = make_float2(-INFINITY, 0.0f);
         if (threadIdx.x == 0) anchor[blockIdx.x] = make_double2(-INFINITY, 0.0);
         return;
     }
-    if (n < P.N) fg[n] = make_float2(lw > -INFINITY ? (float)(lw - a_lw) : -INFINITY,
+    if (n < P.N) fg[n] = make_float2(fw ? (float)(lw - a_lw) : -INFINITY,
                                      ell > -INFINITY ? (float)(ell - a_ell) : -INFINITY);
     if (threadIdx.x == 0) anchor[blockIdx.x] = make_double2(a_lw, a_ell);
+}
+
+// the CTA anchors as fp32 offsets from the one of largest log w (-inf: a CTA without weight)
+__global__ void __launch_bounds__(kZjaThreads)
+zja_anchor_kernel(const ZjaState* zs, const double2* __restrict__ anchor, int nblk, float2* __restrict__ adiff)
+{
+    if (zs->done) return;
+    __shared__ unsigned long long best;
+    __shared__ int who;
+    __shared__ double2 ref;
+    if (threadIdx.x == 0) { best = 0ull; who = nblk; }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nblk; b += kZjaThreads)
+        if (anchor[b].x > -INFINITY) atomicMax(&best, zja_order_key(anchor[b].x));
+    __syncthreads();
+    for (int b = threadIdx.x; b < nblk; b += kZjaThreads)
+        if (anchor[b].x > -INFINITY && zja_order_key(anchor[b].x) == best) atomicMin(&who, b);
+    __syncthreads();
+    if (threadIdx.x == 0) ref = who < nblk ? anchor[who] : make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nblk; b += kZjaThreads) {
+        const double2 a = anchor[b];
+        adiff[b] = a.x > -INFINITY ? make_float2((float)(a.x - ref.x), (float)(a.y - ref.y))
+                                   : make_float2(-INFINITY, 0.0f);
+    }
 }
 
 // per CTA and candidate: (max, sum exp(e - max)) of e = f + k delta g: k = 0 (S0); the weight
@@ -120,43 +163,51 @@ __device__ double zja_step_size(double b, const double* beta_ref, const double* 
 // Merge the CTAs' sums, evaluate CESS / N at the candidates and narrow the bracket; after the
 // last pass (or when the whole remaining interval meets the target) fix beta_t, its step size
 // (linear interpolation of the reference schedule's in beta) and the next step's bracket.
-__global__ void __launch_bounds__(128)
-zja_narrow_kernel(ZjaState* zs, const double2* __restrict__ anchor, const float2* __restrict__ part, int nblk,
+constexpr int kZjaNarrowThreads = 1024;
+__global__ void __launch_bounds__(kZjaNarrowThreads)
+zja_narrow_kernel(ZjaState* zs, const float2* __restrict__ adiff, const float2* __restrict__ part, int nblk,
                   double log_target, int pass, int t, int T_max, double* beta, double* eps,
                   const double* __restrict__ beta_ref, const double* __restrict__ eps_ref, int T_ref)
 {
     if (zs->done) return;
-    __shared__ double logS[kZjaSums];
+    __shared__ float logS[kZjaSums];
     const double lo = zs->lo, hi = zs->hi;
-    for (int c = threadIdx.x; c < kZjaSums; c += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warp w merges sums w, w + 32, ...: lane l the CTAs l, l + 32, ...; each CTA's sum enters on
+    // its anchor's offset from the reference anchor, v = a_f + k delta a_g + m_CTA
+    for (int c = warp; c < kZjaSums; c += kZjaNarrowThreads / 32) {
         const int j = c < 2 ? 0 : (c - 2) % kZjaCand + 1;
-        const double k = c < 2 ? 0.0 : (c < 2 + kZjaCand ? 1.0 : 2.0);
+        const float k = c < 2 ? 0.0f : (c < 2 + kZjaCand ? 1.0f : 2.0f);
         // the same fp32 candidate the pass kernel used
-        const double delta = j == 0 ? 0.0 : (double)zja_candidate(pass, (float)lo, (float)hi, j);
-        double M = -INFINITY;
-        for (int b = 0; b < nblk; ++b) {
+        const float delta = j == 0 ? 0.0f : zja_candidate(pass, (float)lo, (float)hi, j);
+        float M = -INFINITY;
+        for (int b = lane; b < nblk; b += 32) {
             const float2 q = part[(size_t)b * kZjaSums + c];
-            const double2 a = anchor[b];
+            const float2 a = adiff[b];
             if (q.x == -INFINITY || a.x == -INFINITY) continue;
-            M = fmax(M, a.x + k * delta * a.y + (double)q.x);
+            M = fmaxf(M, (k > 0.0f ? a.x + k * delta * a.y : a.x) + q.x);
         }
-        double S = 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
+        float S = 0.0f;
         if (M > -INFINITY)
-            for (int b = 0; b < nblk; ++b) {
+            for (int b = lane; b < nblk; b += 32) {
                 const float2 q = part[(size_t)b * kZjaSums + c];
-                const double2 a = anchor[b];
+                const float2 a = adiff[b];
                 if (q.x == -INFINITY || a.x == -INFINITY) continue;
-                S += (double)q.y * (double)__expf((float)(a.x + k * delta * a.y + (double)q.x - M));
+                S += q.y * __expf((k > 0.0f ? a.x + k * delta * a.y : a.x) + q.x - M);
             }
-        logS[c] = M > -INFINITY ? M + log(S) : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xFFFFFFFFu, S, o);
+        if (lane == 0) logS[c] = M > -INFINITY ? M + logf(S) : -INFINITY;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
     // the last candidate whose CESS / N = S1^2 / (S0 S2) still meets c A, A = S_alive / S0
-    const double lt = log_target + logS[1] - logS[0];
+    const double lt = log_target + (double)logS[1] - (double)logS[0];
     int best = 0;
     for (int j = 1; j <= kZjaCand; ++j) {
-        const double lr = 2.0 * logS[1 + j] - logS[0] - logS[1 + kZjaCand + j];
+        const double lr = 2.0 * (double)logS[1 + j] - (double)logS[0] - (double)logS[1 + kZjaCand + j];
         if (lr >= lt) best = j;
     }
     auto cand = [&](int j) { return (double)zja_candidate(pass, (float)lo, (float)hi, j); };
@@ -198,12 +249,14 @@ cudaError_t launch_zja_search(ZjaState* zs, const AsmcState* st, const StepParam
                               const double* beta_ref, const double* eps_ref, int T_ref, cudaStream_t s)
 {
     const int grid = zja_grid(P.N);
+    float2* adiff = reinterpret_cast<float2*>(anchor + grid);   // the buffer's second part
     zja_open_kernel<<<1, 1, 0, s>>>(zs);
     zja_prep_kernel<<<grid, kZjaThreads, 0, s>>>(st, P, fg, anchor);
+    zja_anchor_kernel<<<1, kZjaThreads, 0, s>>>(zs, anchor, grid, adiff);
     for (int pass = 0; pass < kZjaPasses; ++pass) {
         zja_pass_kernel<<<grid, kZjaThreads, 0, s>>>(zs, pass, P.N, fg, part);
-        zja_narrow_kernel<<<1, 128, 0, s>>>(zs, anchor, part, grid, log(cess_frac), pass, t, T_max, beta, eps,
-                                            beta_ref, eps_ref, T_ref);
+        zja_narrow_kernel<<<1, kZjaNarrowThreads, 0, s>>>(zs, adiff, part, grid, log(cess_frac), pass, t, T_max,
+                                                          beta, eps, beta_ref, eps_ref, T_ref);
     }
     return cudaGetLastError();
 }
