@@ -250,7 +250,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     L.g0 = take(xbytes);
     L.g1 = take(xbytes);
     L.ell1 = take(sizeof(double) * N);
-    L.ess_parts = take(sizeof(StepPartial) * (size_t)sweep_grid(N));
+    L.ess_parts = take(sizeof(StepPartial) * (size_t)(sweep_grid(N) + asmc_ess_groups(sweep_grid(N))));
     L.st = take(sizeof(AsmcState));
     L.bsum = take(sizeof(double) * scan_blocks(N));
     L.boff = take(sizeof(double) * (scan_blocks(N) + 1));

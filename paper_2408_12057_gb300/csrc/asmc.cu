@@ -21,13 +21,18 @@ constexpr int kScanTile = kScanThreads * kScanItems;   // particles per scan blo
 int scan_blocks(int64_t N) { return (int)((N + kScanTile - 1) / kScanTile); }
 
 // The ESS test merges the per-CTA pieces (m_j, s_j) of log w and 2 log w into
-// LSE = M + log sum_j s_j exp(m_j - M) in two passes: the largest shift M, then the rescaled
-// sum, whose factors exp(m_j - M) take the fp64 difference (<= 0) rounded once to fp32 and an
-// fp32 exponential (relative effect on the sum below a few 1e-8, the pieces themselves being
-// fp32 sums).  One pass of dependent fp64 merges (an fp64 exponential per piece, each waiting
-// for the last) took 70 us for 2 048 pieces on this part's slow fp64 pipe; the two passes
-// have no chain and no fp64 exponential.
-constexpr int kDecideThreads = 512;
+// LSE = M + log sum_j s_j exp(m_j - M), in two levels: groups of kEssGroup pieces on as many
+// CTAs (asmc_ess_group_kernel), then the groups on one (the decision).  Each merge takes two
+// passes, the largest shift M and then the rescaled sum, whose factors exp(m_j - M) take the
+// fp64 difference (<= 0) rounded once to fp32 and an fp32 exponential (relative effect on a
+// sum below a few 1e-8, the pieces themselves being fp32 sums).  One CTA merging every piece
+// through a chain of fp64 exponentials (each waiting for the last) took 70 us for 2 048 pieces
+// on this part's slow fp64 pipe; one CTA doing the two passes over them, 21 us.
+constexpr int kDecideThreads = 256;
+constexpr int kEssGroup = 64;
+int asmc_ess_groups(int nparts) { return (nparts + kEssGroup - 1) / kEssGroup; }
+
+template <int NT>
 __device__ __forceinline__ double block_reduce_max(double v, double* sh)
 {
 #pragma unroll
@@ -36,11 +41,12 @@ __device__ __forceinline__ double block_reduce_max(double v, double* sh)
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();
-    v = lane < kDecideThreads / 32 ? sh[lane] : -INFINITY;
+    v = lane < NT / 32 ? sh[lane] : -INFINITY;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
     return v;                                     // in every thread
 }
+template <int NT>
 __device__ __forceinline__ double block_reduce_sum(double v, double* sh)
 {
 #pragma unroll
@@ -49,34 +55,58 @@ __device__ __forceinline__ double block_reduce_sum(double v, double* sh)
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();
-    v = lane < kDecideThreads / 32 ? sh[lane] : 0.0;
+    v = lane < NT / 32 ? sh[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     return v;
 }
+// (M_i, S_i), i = 0, 1, of the pieces [0, n) (all threads of the CTA call it; thread t takes
+// pieces t, t + NT, ...)
+template <int NT>
+__device__ __forceinline__ void merge_ess_pieces(const StepPartial* __restrict__ parts, int n, double (&M)[2],
+                                                 double (&S)[2], double* sh)
+{
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        double mx = -INFINITY;
+        for (int j = threadIdx.x; j < n; j += NT) mx = fmax(mx, parts[j].m[i]);
+        M[i] = block_reduce_max<NT>(mx, sh);
+        double sum = 0.0;
+        if (M[i] > -INFINITY) {
+            for (int j = threadIdx.x; j < n; j += NT) {
+                const double m = parts[j].m[i];
+                if (m > -INFINITY) sum += parts[j].s[i] * (double)expf((float)(m - M[i]));
+            }
+        }
+        S[i] = block_reduce_sum<NT>(sum, sh);
+    }
+}
+
+__global__ void __launch_bounds__(kEssGroup)
+asmc_ess_group_kernel(const StepPartial* __restrict__ parts, int nparts, StepPartial* __restrict__ groups)
+{
+    __shared__ double sh[kEssGroup / 32];
+    const int j0 = blockIdx.x * kEssGroup;
+    double M[2], S[2];
+    merge_ess_pieces<kEssGroup>(parts + j0, min(kEssGroup, nparts - j0), M, S, sh);
+    if (threadIdx.x == 0) {
+        StepPartial g{};
+        g.m[0] = M[0]; g.s[0] = S[0];
+        g.m[1] = M[1]; g.s[1] = S[1];
+        g.m[2] = -INFINITY;
+        groups[blockIdx.x] = g;
+    }
+}
 
 __global__ void __launch_bounds__(kDecideThreads)
-asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ ess_parts, int nparts, int t, int T,
+asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ groups, int ngroups, int t, int T,
                    const double* __restrict__ beta, double ess_frac, int64_t N, Rng rng, double* ess_trace,
                    int* resampled)
 {
     __shared__ double sh[kDecideThreads / 32];
     const int tid = threadIdx.x;
     double M[2], S[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        double mx = -INFINITY;
-        for (int j = tid; j < nparts; j += kDecideThreads) mx = fmax(mx, ess_parts[j].m[i]);
-        M[i] = block_reduce_max(mx, sh);
-        double sum = 0.0;
-        if (M[i] > -INFINITY) {
-            for (int j = tid; j < nparts; j += kDecideThreads) {
-                const double m = ess_parts[j].m[i];
-                if (m > -INFINITY) sum += ess_parts[j].s[i] * (double)expf((float)(m - M[i]));
-            }
-        }
-        S[i] = block_reduce_sum(sum, sh);
-    }
+    merge_ess_pieces<kDecideThreads>(groups, ngroups, M, S, sh);
     if (tid == 0) {
         const double lse1 = M[0] + log(S[0]);
         const double lse2 = M[1] + log(S[1]);
@@ -212,8 +242,11 @@ asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const dou
 cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int nparts, double ess_frac, double* bsum,
                                     double* boff, double* cdf, double* ess_trace, int* resampled, cudaStream_t s)
 {
-    asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
-                                         ess_trace, resampled);
+    const int ng = asmc_ess_groups(nparts);
+    StepPartial* groups = P.ess_parts + nparts;   // the buffer holds nparts pieces, then the groups
+    asmc_ess_group_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups);
+    asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, groups, ng, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
+                                                    ess_trace, resampled);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);
@@ -225,8 +258,11 @@ cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts,
                                  bool grad, bool fp64, double* bsum, double* boff, double* cdf,
                                  double* ess_trace, int* resampled, int64_t* ancestors, cudaStream_t s)
 {
-    asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, P.ess_parts, nparts, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
-                                         ess_trace, resampled);
+    const int ng = asmc_ess_groups(nparts);
+    StepPartial* groups = P.ess_parts + nparts;   // the buffer holds nparts pieces, then the groups
+    asmc_ess_group_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups);
+    asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, groups, ng, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
+                                                    ess_trace, resampled);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);

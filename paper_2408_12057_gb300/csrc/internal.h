@@ -70,6 +70,9 @@ cudaError_t launch_step_tcs(const TcsPlan& L, int kind, const SweepParams& sp, c
                             cudaStream_t s);
 cudaError_t launch_gather_tcs(const TcsPlan& L, const AsmcState* st, const double* cdf, int64_t N, float* state,
                               double* ell, double* ell_scratch, double* logw, int64_t* ancestors, cudaStream_t s);
+// the ESS pieces' buffer (StepParams::ess_parts) holds nparts pieces and then
+// asmc_ess_groups(nparts) group records of the two-level merge
+int asmc_ess_groups(int nparts);
 cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int nparts, double ess_frac, double* bsum,
                                     double* boff, double* cdf, double* ess_trace, int* resampled, cudaStream_t s);
 // one evaluation of log L and grad log L (grad may be null) at states x [d][N] with the
