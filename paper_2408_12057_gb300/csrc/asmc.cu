@@ -108,15 +108,19 @@ asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ groups, int ng
     double M[2], S[2];
     merge_ess_pieces<kDecideThreads>(groups, ngroups, M, S, sh);
     if (tid == 0) {
-        const double lse1 = M[0] + log(S[0]);
-        const double lse2 = M[1] + log(S[1]);
-        const double ess = exp(2.0 * lse1 - lse2);
+        // ESS = exp(2 LSE(log w) - LSE(2 log w)) = S_0^2 / S_1 exp(2 M_0 - M_1); the shift of the
+        // doubled weights is exactly twice the other (doubling commutes with rounding), so the
+        // exponential is 1 but for empty sums, and the logarithms (fp64, slow here) are taken
+        // only when the segment closes
+        const double d2 = 2.0 * M[0] - M[1];
+        const double ess = S[0] * S[0] / S[1] * (d2 == 0.0 ? 1.0 : exp(d2));
         st->cur ^= st->pend;             // the previous step's gather is now the live buffer
         // the last step (t = T, or beta_t = 1 for a schedule found online) closes the segment
         const bool last = (t == T) || beta[t] >= 1.0;
         const bool fire = last || (ess_frac > 0.0 && ess < ess_frac * (double)N);
         int pend = 0;
         if (fire) {
+            const double lse1 = M[0] + log(S[0]);
             st->logZ += lse1 - log((double)N);
             if (!last) {
                 pend = 1;
