@@ -261,7 +261,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     const int form = sweep_form(tg, mv);
     L.tc_img = take(form == 1 ? (size_t)tc_image_bytes() : 0);
     L.tc_y = take(form == 1 ? (size_t)tc_max_rows() / 8 : 0);
-    L.tc_handed = take(form == 1 ? sizeof(int) * (size_t)tc_records(N) : 0);
+    L.tc_handed = take(form >= 1 ? sizeof(int) * (size_t)std::max(tc_records(N), tcs_tiles(N)) : 0);
     // online conditional-ESS rounds (CUDA-core form): offsets, anchors, candidate sums, state,
     // the schedule found online and its step sizes
     L.zja_fg = take(sizeof(float2) * (size_t)N);
@@ -515,6 +515,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
             dt.tcs_dp = tp.dp;
             dt.tcs_img = b + L.tcs_img;
             dt.tcs_state = reinterpret_cast<float*>(b + L.tcs_state);
+            dt.tc_handed = reinterpret_cast<int*>(b + L.tc_handed);
             e = cudaMemcpy(dt.tcs_img, img.data(), img.size(), cudaMemcpyHostToDevice);
         }
         if (e == cudaSuccess && sweep_form(tg, mv) == 1) {
@@ -706,7 +707,7 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
         else if (ctx->dt.tcs)
             CK(launch_sweep_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0, ctx->dt.tcs_q8), ctx->dt.kind, P, ctx->dt.tcs_img,
                                 ctx->dt.tcs_state, ctx->mv.kind, ctx->mv.leapfrog, ctx->dt.p0, ctx->dt.n,
-                                ctx->dt.d, s));
+                                ctx->dt.d, s, ctx->dt.tc_handed));
         else CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
         CK(cudaEventRecord(ctx->ev1, s));
         const int records = ctx->dt.tc ? tc_records(ctx->N) : (ctx->dt.tcs ? tcs_tiles(ctx->N) : grid);

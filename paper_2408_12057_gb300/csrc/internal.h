@@ -20,7 +20,7 @@ struct DevTarget {
     bool tc = false;     // tensor-core form: BF16 image of X and label bits below
     void* tc_img = nullptr;
     uint32_t* tc_ybits = nullptr;
-    int* tc_handed = nullptr;    // [tiles] hand-off flags of the persistent schedule
+    int* tc_handed = nullptr;    // [tiles] hand-off flags of the persistent schedules (resident and streamed forms)
     bool tcs = false;    // streamed tensor-core form: chunk images of X~ (and y), particle state
     void* tcs_img = nullptr;
     float* tcs_state = nullptr;
@@ -51,8 +51,11 @@ void tcs_prepare_q8(const TcsPlan& L, const float* X, const float* y, int n, int
 int tcs_tiles(int64_t N);
 // state: 5 arrays [dp][tiles * 128] fp32 (accepted x, its gradient, proposal, momentum,
 // drained gradient sum)
+// handed: [tiles] hand-off flags (nullable): with more tiles than CTAs resident at once the
+// sweep runs as a persistent grid with the wrap-around schedule over tiles x steps
 cudaError_t launch_sweep_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
-                             int move, int leapfrog, double p0, int n, int d, cudaStream_t s);
+                             int move, int leapfrog, double p0, int n, int d, cudaStream_t s,
+                             int* handed = nullptr);
 // batched persistent form: per-problem parameter blocks (opaque, tcs_params_bytes each) whose
 // Misc region sits at the common offset off_misc, a queue of (problem, tile) items, a head
 // counter (zero before the launch), one CTA per SM

@@ -166,6 +166,9 @@ static void fill_params(tcs::Params& P, const TcsPlan& L, int kind, const SweepP
     P.t_end = sp.T;
     P.resume = 0;
     P.ess_parts = nullptr;
+    P.span = 0;
+    P.tiles = tcs_tiles(sp.N);
+    P.handed = nullptr;
     P.x_in = x_in;
     P.ell_pot = ell_pot;
     P.grad_pot = grad_pot;
@@ -203,7 +206,8 @@ static void fill_params(tcs::Params& P, const TcsPlan& L, int kind, const SweepP
 static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
                               int move, int leapfrog, double p0, int n, int d, const float* x_in, double* ell_pot,
                               float* grad_pot, int64_t pstride, cudaStream_t s, int64_t state_particles = 0,
-                              int t_begin = 1, int t_end = -1, int resume = 0, StepPartial* ess_parts = nullptr)
+                              int t_begin = 1, int t_end = -1, int resume = 0, StepPartial* ess_parts = nullptr,
+                              int* handed = nullptr)
 {
     tcs::Params P;
     fill_params(P, L, kind, sp, img, state, move, leapfrog, p0, n, d, x_in, ell_pot, grad_pot, pstride,
@@ -218,7 +222,38 @@ static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp,
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
         if (e != cudaSuccess) return e;
-        kern<<<tiles, tcs::Roles<2>::threads(L.q8 ? 1 : 0), L.smem, s>>>(P);
+        const int threads = tcs::Roles<2>::threads(L.q8 ? 1 : 0);
+        // the OAIS sweep with more tiles than CTAs resident at once: a persistent grid with the
+        // wrap-around schedule (every CTA resident: a cooperative launch, since a CTA may wait
+        // for another's hand-off)
+        int per_sm = 0, dev = 0, sms = 0;
+        if (handed && !x_in && t_end < 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, L.smem);
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+        }
+        const int resident = per_sm * sms;
+        if (resident > 0 && tiles > resident && sp.T > 0) {
+            P.span = std::max<int64_t>(sp.T, ((int64_t)tiles * sp.T + resident - 1) / resident);
+            P.handed = handed;
+            e = cudaMemsetAsync(handed, 0, sizeof(int) * (size_t)tiles, s);
+            if (e != cudaSuccess) return e;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(resident);
+            cfg.blockDim = dim3(threads);
+            cfg.dynamicSmemBytes = L.smem;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, kern, P);
+            if (e != cudaSuccess) return e;
+            return cudaGetLastError();
+        }
+        kern<<<tiles, threads, L.smem, s>>>(P);
         return cudaGetLastError();
     };
     if (L.chunk != tcs::chunk_rows(L.dp)) return cudaErrorInvalidValue;
@@ -251,9 +286,10 @@ static cudaError_t launch_tcs(const TcsPlan& L, int kind, const SweepParams& sp,
 }
 
 cudaError_t launch_sweep_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,
-                             int move, int leapfrog, double p0, int n, int d, cudaStream_t s)
+                             int move, int leapfrog, double p0, int n, int d, cudaStream_t s, int* handed)
 {
-    return launch_tcs(L, kind, sp, img, state, move, leapfrog, p0, n, d, nullptr, nullptr, nullptr, 0, s);
+    return launch_tcs(L, kind, sp, img, state, move, leapfrog, p0, n, d, nullptr, nullptr, nullptr, 0, s, 0, 1, -1,
+                      0, nullptr, handed);
 }
 
 cudaError_t launch_step_tcs(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state,

@@ -120,6 +120,12 @@ struct Params {
     // step) and writes each tile's (log w, 2 log w) moment record to ess_parts
     int t_begin, t_end, resume;
     StepPartial* ess_parts;
+    // persistent wrap-around schedule of the OAIS sweep (span > 0): CTA b runs the positions
+    // [b span, (b + 1) span) of the tiles x steps sequence; handed[tile] flags a split tile's
+    // first part done (0: one tile per CTA, the whole sweep)
+    int64_t span;
+    int tiles;
+    int* handed;
     double log_norm;            // linear regression: n (log sigma + log(2 pi) / 2)
     float gscale;               // grad log L = gscale * G (1 / sigma^2 or 1)
     float half_inv_var;         // linear regression: 1 / (2 sigma^2)
@@ -401,6 +407,7 @@ __device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stag
                        &M->rfull[1], &M->rempty[1], &M->afull, &M->d2full, &M->done, &M->d2seg, &M->d2drained};
     if (prev_stages > 0) {
         for (int s = 0; s < prev_stages; ++s) { mbar_inval(saddr(&M->xfull[s])); mbar_inval(saddr(&M->xempty[s])); }
+        for (int s = 0; s < stages8; ++s) { mbar_inval(saddr(&M->x8full[s])); mbar_inval(saddr(&M->x8empty[s])); }
         for (uint64_t* b : all) mbar_inval(saddr(b));
     }
     // f16 stages are filled by the bulk copy (one arrival + bytes) or, with FP8 storage, by
@@ -892,7 +899,75 @@ oais_sweep_tcs_kernel(const Params P)
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&M->tmem);
-    run_tile<FAM, DP, Q8, H>(P, blockIdx.x, gridDim.x, smem, tmem);
+    if (P.span == 0) {
+        run_tile<FAM, DP, Q8, H>(P, blockIdx.x, gridDim.x, smem, tmem);
+    } else {
+        // Persistent grid, wrap-around schedule (McNaughton's rule for preemptive scheduling
+        // of independent jobs): tile i is the job of T steps at positions [i T, (i + 1) T) of
+        // the concatenated sequence, CTA b covers [b L, (b + 1) L) with L = span >= T.  A tile
+        // split between CTAs b and b + 1 runs its first steps at the start of CTA b + 1 and its
+        // last steps at the end of CTA b, which cannot overlap in time because L >= T; the
+        // first part leaves the state where the resumed part reads it (positions, gradients,
+        // log w, log L) and sets handed[tile], the last part waits for the flag (bounded).
+        // Every piece starts on fresh barriers (TMEM stays allocated).
+        Params& sP = M->prm;
+        const int T = P.sp.T;
+        const int64_t total = (int64_t)P.tiles * T;
+        const int64_t pos1 = min(((int64_t)blockIdx.x + 1) * P.span, total);
+        bool first = true;
+        for (int64_t pos = (int64_t)blockIdx.x * P.span; pos < pos1 && T > 0;) {
+            const int64_t tile = pos / T;
+            const int off = (int)(pos % T);
+            int t0, t1;
+            if (off != 0) {                       // head: the first T - off steps of a split tile
+                t0 = 1;
+                t1 = T - off;
+                pos = (tile + 1) * T;
+            } else if (pos + T <= pos1) {         // a whole tile
+                t0 = 1;
+                t1 = T;
+                pos += T;
+            } else {                              // tail: the last pos1 - pos steps of a split tile
+                t0 = T - (int)(pos1 - pos) + 1;
+                t1 = T;
+                pos = pos1;
+            }
+            if (threadIdx.x == 0) {
+                if (!first) init_barriers(M, P.stages, P.stages, Q8 ? P.stages8 : 0, Roles<H>::kEpiWarps);
+                sP = P;
+                sP.t_begin = t0;
+                sP.t_end = t1;
+                sP.resume = t0 > 1 ? 1 : 0;
+                if (t0 > 1) {
+                    const uint64_t w0 = globaltimer();
+                    while (ld_acquire_gpu(P.handed + tile) == 0) {
+                        if (globaltimer() - w0 > kWaitLimitNs) {
+                            M->abort = 1;
+                            atomicOr(P.sp.status, 2u);
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+            }
+            tc_before_sync();
+            __syncthreads();
+            tc_after_sync();
+            if (M->abort) break;
+            run_tile<FAM, DP, Q8, H>(sP, (uint32_t)tile, (uint32_t)P.tiles, smem, tmem);
+            // every role has finished the piece (its copies and MMAs complete) before the
+            // barriers are reused; the piece's state is written before the flag is raised
+            tc_before_sync();
+            __syncthreads();
+            tc_after_sync();
+            if (M->abort) break;
+            if (t1 < T && threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(P.handed + tile, 1);
+            }
+            first = false;
+        }
+    }
     tc_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, P.tmem_cols);
