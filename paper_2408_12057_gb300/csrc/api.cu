@@ -872,8 +872,11 @@ oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out)
 // The online conditional-ESS comparator (Zhou, Johansen & Aston 2016; the paper's section on
 // the connection to online CESS optimisation): lock-step particles as in oasmc_round, but
 // beta_t is found on the device before step t (zja.cu) so that CESS_t / N = cess_frac; the
-// run ends at beta = 1 (at most T_max steps, the last one forced to beta = 1).  One host
-// round trip per step reads beta_t.
+// run ends at beta = 1 (at most T_max steps, the last one forced to beta = 1).  The host
+// reads beta once every kZjaCheck steps; steps launched after the one that reached beta = 1
+// find the device flag set and do nothing.
+constexpr int kZjaCheck = 8;
+
 oais_status oais_zja_round(oais_ctx* ctx, double cess_frac, double ess_frac, int32_t T_next, oais_round_result* out)
 {
     if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
@@ -898,6 +901,7 @@ oais_status oais_zja_round(oais_ctx* ctx, double cess_frac, double ess_frac, int
     StepParams P = make_step_params(ctx, T_max, tag);
     P.beta = ctx->d_zbeta;
     P.eps = ctx->d_zeps;
+    P.skip = &ctx->d_zstate->skip;
     const int grid = sweep_grid(ctx->N);
     const bool grad = ctx->mv.kind != OAIS_RWMH;
     CK(cudaEventRecord(ctx->ev0, s));
@@ -910,11 +914,21 @@ oais_status oais_zja_round(oais_ctx* ctx, double cess_frac, double ess_frac, int
         CK(launch_asmc(ctx->dt, ctx->mv.kind, false, P, s));
         CK(launch_asmc_resample(ctx->d_st, P, grid, ess_frac, ctx->dt.d, grad, f64_kind(ctx->dt.kind), ctx->d_bsum,
                                 ctx->d_boff, ctx->d_cdf, ctx->d_ess_trace, ctx->d_resampled, ctx->d_anc, s));
-        double bt = 0.0;
-        CK(cudaMemcpyAsync(&bt, ctx->d_zbeta + t, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        T = t;
-        if (bt >= 1.0) break;
+        if (t % kZjaCheck == 0 || t == T_max) {
+            double bp = 0.0;
+            CK(cudaMemcpyAsync(&bp, &ctx->d_zstate->beta_prev, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (bp >= 1.0 || t == T_max) {
+                // the step that reached beta = 1: the first one since this round began
+                std::vector<double> zb_head(t + 1);
+                CK(cudaMemcpyAsync(zb_head.data(), ctx->d_zbeta, sizeof(double) * (t + 1), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                T = t;
+                for (int u = 1; u <= t; ++u)
+                    if (zb_head[u] >= 1.0) { T = u; break; }
+                break;
+            }
+        }
     }
     CK(cudaEventRecord(ctx->ev1, s));
     std::vector<double> lg(3 * T), acc(T), elbo(T), ess_tr(T), zb(T + 1), ze(T);

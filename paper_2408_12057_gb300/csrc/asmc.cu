@@ -83,8 +83,10 @@ __device__ __forceinline__ void merge_ess_pieces(const StepPartial* __restrict__
 }
 
 __global__ void __launch_bounds__(kEssGroup)
-asmc_ess_group_kernel(const StepPartial* __restrict__ parts, int nparts, StepPartial* __restrict__ groups)
+asmc_ess_group_kernel(const StepPartial* __restrict__ parts, int nparts, StepPartial* __restrict__ groups,
+                      const int* skip)
 {
+    if (skip && *skip) return;
     __shared__ double sh[kEssGroup / 32];
     const int j0 = blockIdx.x * kEssGroup;
     double M[2], S[2];
@@ -101,8 +103,9 @@ asmc_ess_group_kernel(const StepPartial* __restrict__ parts, int nparts, StepPar
 __global__ void __launch_bounds__(kDecideThreads)
 asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ groups, int ngroups, int t, int T,
                    const double* __restrict__ beta, double ess_frac, int64_t N, Rng rng, double* ess_trace,
-                   int* resampled)
+                   int* resampled, const int* skip)
 {
+    if (skip && *skip) return;           // the step was skipped: st (pend = 0) stays as it is
     __shared__ double sh[kDecideThreads / 32];
     const int tid = threadIdx.x;
     double M[2], S[2];
@@ -248,9 +251,9 @@ cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int npar
 {
     const int ng = asmc_ess_groups(nparts);
     StepPartial* groups = P.ess_parts + nparts;   // the buffer holds nparts pieces, then the groups
-    asmc_ess_group_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups);
+    asmc_ess_group_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups, P.skip);
     asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, groups, ng, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
-                                                    ess_trace, resampled);
+                                                    ess_trace, resampled, P.skip);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);
@@ -264,9 +267,9 @@ cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts,
 {
     const int ng = asmc_ess_groups(nparts);
     StepPartial* groups = P.ess_parts + nparts;   // the buffer holds nparts pieces, then the groups
-    asmc_ess_group_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups);
+    asmc_ess_group_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups, P.skip);
     asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, groups, ng, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
-                                                    ess_trace, resampled);
+                                                    ess_trace, resampled, P.skip);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);

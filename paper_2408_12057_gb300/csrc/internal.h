@@ -92,7 +92,7 @@ struct ZjaState {
     double lo, hi;       // bracket of delta = beta_t - beta_{t-1}
     double beta_prev;    // beta_{t-1}
     int done;            // 1: beta_t fixed (the pass and narrow kernels return at once)
-    int pad;
+    int skip;            // 1: beta reached 1 at an earlier step (this step does nothing)
 };
 int zja_grid(int64_t N);
 size_t zja_part_bytes(int64_t N);

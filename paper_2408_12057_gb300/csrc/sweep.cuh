@@ -251,12 +251,15 @@ struct StepParams {
     StepPartial* partials;  // [T][gridDim.x]
     StepPartial* ess_parts; // [gridDim.x]: m/s[0] for log w, m/s[1] for 2 log w
     unsigned* status;
+    const int* skip;        // nullable device flag: when set, the step and its decision do nothing
+                            // (a schedule found online that has already reached beta = 1)
 };
 
 template <class Tgt, int MOVE, int D, typename R>
 __global__ void __launch_bounds__(kSweepThreads, (SweepMinBlocks<Tgt, MOVE>::value))
 asmc_step_kernel(const StepParams P, Tgt tg)
 {
+    if (P.skip && *P.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_m[kSweepThreads / 32][3];
     __shared__ float s_s[kSweepThreads / 32][4];

@@ -241,8 +241,14 @@ zja_narrow_kernel(ZjaState* zs, const float2* __restrict__ adiff, const float2* 
     zs->done = 1;
 }
 
-// open the search for step t (the pass and narrow kernels return at once while done == 1)
-__global__ void zja_open_kernel(ZjaState* zs) { zs->done = zs->beta_prev >= 1.0 ? 1 : 0; }
+// open the search for step t (the pass and narrow kernels return at once while done == 1); a
+// step after the one that reached beta = 1 is skipped altogether (the host looks only every
+// few steps)
+__global__ void zja_open_kernel(ZjaState* zs)
+{
+    zs->skip = zs->beta_prev >= 1.0 ? 1 : 0;
+    zs->done = zs->skip;
+}
 
 cudaError_t launch_zja_search(ZjaState* zs, const AsmcState* st, const StepParams& P, float2* fg, double2* anchor,
                               float2* part, double cess_frac, int t, int T_max, double* beta, double* eps,
