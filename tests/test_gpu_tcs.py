@@ -291,8 +291,10 @@ def test_stream_asmc_without_resampling_equals_sweep(kind, n, d, move, L):
     assert a["res"]["logZ"] == pytest.approx(b["res"]["logZ"], rel=1e-6)
 
 
-@pytest.mark.parametrize("kind,n,d,move,L,T", [("logreg", 200, 16, oais.MALA, 1, 7), ("linreg", 150, 32, oais.HMC, 2, 3)])
-def test_stream_persistent_sweep_equals_per_step(kind, n, d, move, L, T):
+@pytest.mark.parametrize("kind,n,d,move,L,T,fp8", [("logreg", 200, 16, oais.MALA, 1, 7, False),
+                                                   ("linreg", 150, 32, oais.HMC, 2, 3, False),
+                                                   ("linreg", 100, 24, oais.MALA, 1, 5, True)])
+def test_stream_persistent_sweep_equals_per_step(kind, n, d, move, L, T, fp8):
     # more tiles than CTAs resident at once (257 tiles of 128, the last one ragged): the sweep
     # runs as a persistent grid with the wrap-around schedule, tiles split between two CTAs
     # hand their state over; the lock-step ASMC without resampling (one launch per step, one
@@ -301,8 +303,9 @@ def test_stream_persistent_sweep_equals_per_step(kind, n, d, move, L, T):
     N = 256 * 128 + 77
     beta = W.linear_schedule(T) ** 3
     eps = oais.default_step_sizes(pr, beta, move)
-    a = tcs_asmc(pr, move, N, beta, eps, 23, 0.0, leapfrog=L)
-    b = run(pr, move, N, beta, eps, 23, leapfrog=L)
+    c = oais.CONTRACT_FP8_TC_STREAM if fp8 else None
+    a = tcs_asmc(pr, move, N, beta, eps, 23, 0.0, leapfrog=L, contraction=c)
+    b = run(pr, move, N, beta, eps, 23, leapfrog=L, contraction=c)
     assert a["res"]["n_resample"] == 0
     np.testing.assert_array_equal(a["logw"], b["logw"])
     np.testing.assert_array_equal(a["ell"], b["ell"])
