@@ -217,8 +217,9 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
         double a0 = __shfl_sync(full, lw, __ffs(bw) - 1);
         double b0 = bg ? __shfl_sync(full, lg, __ffs(bg) - 1) : 0.0;
         if (__ballot_sync(full, fw && fg)) {
-            // re-anchor at the lane with the largest v_1 (first-pass estimate)
-            const float f1 = (fw && fg) ? (float)(lw - a0) + (float)(lg - b0) : -INFINITY;
+            // re-anchor at the lane with the largest v_1 (a first-pass estimate from the fp32
+            // roundings of log w and log g: the anchor need only be near the maximum)
+            const float f1 = (fw && fg) ? (float)lw + (float)lg : -INFINITY;
             float m1 = f1;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m1 = fmaxf(m1, __shfl_xor_sync(full, m1, o));

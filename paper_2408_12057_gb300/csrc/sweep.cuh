@@ -54,13 +54,26 @@ template <typename R> __device__ __forceinline__ R rsq(R a) { return a * a; }
 // The fp64 forms keep both exact.
 template <typename R> constexpr bool kFp32 = sizeof(R) == 4;
 
+// log g_t = (beta_t - beta_{t-1}) log L(X_{t-1}): in fp64 for the fp64 forms; for the fp32 forms
+// (log L an fp32 value) the product in fp32, log w accumulated in fp64 by the caller
+template <typename R>
+__device__ __forceinline__ double step_log_increment(double dbeta, R ell)
+{
+    if constexpr (kFp32<R>) {
+        const float db = (float)dbeta;
+        return db == 0.0f ? 0.0 : (double)(db * ell);
+    } else {
+        return log_increment(dbeta, (double)ell);
+    }
+}
+
+// beta and eps: beta_t and the step size of step t in the particle precision
 template <class Tgt, int MOVE, int D, typename R>
 __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[D], R& ell,
-                                        R (&gl)[D], double beta_t, double eps_t, uint32_t n,
+                                        R (&gl)[D], R beta, R eps, uint32_t n,
                                         uint32_t t, uint32_t k, int d, R inv_s2)
 {
     constexpr bool GRAD = (MOVE != kRwmh);
-    const R beta = (R)beta_t;
     R z[D];
     if constexpr (kFp32<R> && MOVE == kRwmh) normals_sfu<D>(P.rng, n, t, k, d, z);
     else normals<D>(P.rng, n, t, k, d, z);
@@ -68,7 +81,7 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
     R log_alpha;
     R ellp;
     if (MOVE == kRwmh) {
-        R sd = (R)eps_t;
+        R sd = eps;
         if (P.cycle) {
             const int gm = ((int)t - 1) * P.K + (int)k;
             const int c = gm % 3;
@@ -100,7 +113,7 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
     } else if (MOVE == kMala) {
         // x' = x + (e^2/2) grad log pi(x) + e z;  with w = z + (e/2) grad log pi(x) the
         // reverse-proposal term is |w + (e/2) grad log pi(x')|^2 / 2 and the forward one |z|^2 / 2
-        const R e = (R)eps_t, h = R(0.5) * e;
+        const R e = eps, h = R(0.5) * e;
         R zz = 0, dxx = 0;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
@@ -117,7 +130,7 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
         log_alpha = -R(0.5) * dxx * inv_s2 + beta * (ellp - ell) - R(0.5) * (rev - zz);
     } else {
         // HMC, identity mass: leapfrog with momentum p (kept in z)
-        const R e = (R)eps_t;
+        const R e = eps;
         R ke0 = 0;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
@@ -191,14 +204,15 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
     for (int t = 1; t <= P.T; ++t) {
         const double beta_t = __ldg(P.beta + t);
         const double eps_t = __ldg(P.eps + t - 1);
-        const double lg = log_increment(beta_t - beta_prev, (double)ell);
+        const double lg = step_log_increment<R>(beta_t - beta_prev, ell);
         beta_prev = beta_t;
+        const R beta_r = (R)beta_t, eps_r = (R)eps_t;
         const int slot = t & 1;
         warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
         logw += lg;
         unsigned acc = 0;
         for (int k = 0; k < P.mv.K; ++k)
-            acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_t, eps_t, n, (uint32_t)t,
+            acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_r, eps_r, n, (uint32_t)t,
                                             (uint32_t)k, d, inv_s2) ? 1u : 0u;
         acc = active ? acc : 0u;
 #pragma unroll
@@ -289,12 +303,13 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     double logw = P.logw[idx];
 
     const double beta_t = P.beta[P.t], eps_t = P.eps[P.t - 1];
-    const double lg = log_increment(beta_t - P.beta[P.t - 1], (double)ell);
+    const double lg = step_log_increment<R>(beta_t - P.beta[P.t - 1], ell);
+    const R beta_r = (R)beta_t, eps_r = (R)eps_t;
     warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[warp], s_s[warp]);
     logw += lg;
     unsigned acc = 0;
     for (int k = 0; k < P.mv.K; ++k)
-        acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_t, eps_t, n, (uint32_t)P.t,
+        acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_r, eps_r, n, (uint32_t)P.t,
                                         (uint32_t)k, d, inv_s2) ? 1u : 0u;
     acc = active ? acc : 0u;
 #pragma unroll
