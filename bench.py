@@ -564,22 +564,25 @@ def bench_batched(args):
 
 
 def gmm_ops_per_particle_step(d, K, moves):
-    """Lane operations one particle-step of the mixture sweep needs as the algorithm is written
-    (Alg. 1's weight and moments, then `moves` random-walk MH moves), by kind:
-      Philox4x32-10 per call: 10 rounds x (2 low and 2 high 32-bit products, 2 three-way xors)
-        (the key schedule is shared by all particles); ceil(d/4) calls for the normals and one
-        for the MH uniform per move;
+    """Instructions per lane that one particle-step of the mixture sweep needs as the algorithm
+    is written for this instruction set (Alg. 1's weight and moments, then `moves` random-walk
+    MH moves), by kind; a packed fp32 pair instruction (add/sub/fma.rn.f32x2) counts once for its
+    two coordinates, a 32 x 32 -> 64-bit multiply once for its two halves:
+      Philox4x32-10 per call: 10 rounds x (2 wide multiplies, 2 three-input xors) (the key
+        schedule is shared by all particles); ceil(d/4) calls for the normals and one for the
+        MH uniform per move;
       uniforms: shift, int-to-float, scale per word used (d + 1 per move);
-      Box-Muller: per normal one of lg2/sqrt/sin/cos pairs (2 special-function ops) and 2 fp32;
-      proposal x' = x + s z and |x'|^2 - |x|^2: d + 3 d;
-      density: K d (difference, square-accumulate) x 2, then per component scale, max, shift,
-        exp (1 special + 1 fp32), sum; one log; |x|^2: d; the MH test: log u, compare, d selects;
+      Box-Muller: per pair of normals lg2, scale, sqrt, angle, sin, cos and two products;
+      proposal x' = x + s z and |x'|^2 - |x|^2, two coordinates per packed instruction: 2 d;
+      density: K d / 2 packed differences and K d / 2 packed square-accumulates, then per
+        component the pair sum, scale, max, shift, exp (2) and sum; one log; |x|^2 (d / 2);
+      the MH test: log u, compare, d selects;
       per step: the weight increment, the moments (3 x (offset, max, exp, sum)) and acceptance."""
-    philox = moves * (-(-d // 4) + 1) * 10 * 6
+    philox = moves * (-(-d // 4) + 1) * 10 * 4
     unif = moves * (d + 1) * 3
     bm = moves * d * 4
-    prop = moves * 4 * d
-    dens = moves * (2 * K * d + 6 * K + 1 + d + 4)
+    prop = moves * 2 * d
+    dens = moves * (K * d + 7 * K + 1 + d // 2 + 4)
     mh = moves * (2 + d)
     step = 30
     total = philox + unif + bm + prop + dens + mh + step
@@ -628,7 +631,9 @@ def bench_gmm(args):
                  "ms_per_step": t_smc / max(1, args.steps // 2), "logZ_last_round": last_smc[-1]["logZ"],
                  "resampling_events": [r["n_resample"] for r in last_smc]},
         "roofline": {"bound": "alu", "pipe": "instruction issue (integer Philox, fp32, special-function mix)",
-                     "achieved": achieved, "peak": peak, "unit": "T lane-ops/s", "frac": achieved / peak,
+                     "note": "achieved = the instructions the algorithm needs per particle-step (ops_per_particle_step) "
+                             "x particle-steps / sweep time; the kernel executes about 2.3x that many",
+                     "achieved": achieved, "peak": peak, "unit": "T lane-instructions/s", "frac": achieved / peak,
                      "traffic": None, "ops_per_particle_step": ops,
                      "peak_source": "measured FFMA lane-op rate (oais_measure_unit_rate) x 152 SMs = one "
                                     "instruction per lane per cycle",
