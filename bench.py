@@ -306,9 +306,10 @@ def main():
     else:
         # tensor-core form: the contractions run on tcgen05 (a small share of their peak); the
         # per-row epilogue needs one exp and one reciprocal per row on the special-function
-        # unit, and one log per 64-row chunk of a particle (resident form) or per 32-row half
-        # chunk (streamed form); the unit's measured rates bound the row throughput
-        rows_per_log = 64.0 if args.contraction == "bf16_tc" else 32.0
+        # unit, and one log per 32 rows (each of a particle's two threads takes a log of the
+        # product over its 32 rows of a 64-row chunk, in both forms); the unit's measured
+        # rates bound the row throughput
+        rows_per_log = 32.0
         sec_per_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (rows_per_log * rates["lg2"])
         sfu_per_row = 2.0 + 1.0 / rows_per_log
         rows = pr.n * ps_per_job * args.steps
