@@ -196,9 +196,12 @@ __device__ __forceinline__ bool finite_bits(double v)
 {
     return (__double2hiint(v) & 0x7FF00000) != 0x7FF00000;   // exponent field not all ones
 }
-template <bool kFast = false>
+// kDefer (with kFast): the lead lane leaves the anchors (wm[0] = log w_a, wm[1] = log g_a) and
+// the fp32 maxima (ws[4 + i]) instead of forming m_i = log w_a + i log g_a + max_i in fp64, which
+// the CTA merge then does for its W pieces only (merge_deferred_pieces; ws holds 8 floats).
+template <bool kFast = false, bool kDefer = false>
 __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool active,
-                                                    double* wm /*3*/, float* ws /*4*/)
+                                                    double* wm /*3*/, float* ws /*4, or 8 with kDefer*/)
 {
     const unsigned full = 0xFFFFFFFFu;
     const bool lead = (threadIdx.x & 31) == 0;
@@ -208,7 +211,11 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
         if (bw == 0) {
             if (lead) {
 #pragma unroll
-                for (int i = 0; i < 3; ++i) { wm[i] = -INFINITY; ws[i] = 0.0f; }
+                for (int i = 0; i < 3; ++i) {
+                    wm[i] = kDefer ? 0.0 : -INFINITY;
+                    ws[i] = 0.0f;
+                    if (kDefer) ws[4 + i] = -INFINITY;
+                }
                 ws[3] = 0.0f;
             }
             return;
@@ -243,7 +250,12 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
                 for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
             }
             if (lead) {
-                wm[i] = mx > -INFINITY ? a0 + i * b0 + (double)mx : -INFINITY;
+                if (kDefer) {
+                    ws[4 + i] = mx;
+                    if (i == 0) { wm[0] = a0; wm[1] = b0; }
+                } else {
+                    wm[i] = mx > -INFINITY ? a0 + i * b0 + (double)mx : -INFINITY;
+                }
                 ws[i] = e;
                 if (i == 0) ws[3] = u;
             }
@@ -357,6 +369,27 @@ __device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3
 #pragma unroll
     for (int i = 0; i < 4; ++i) sv[i] = lane < W ? ws[lane][i] : 0.0f;
     merge_lane_pieces<W, kFast>(lane, m, sv, (wacc && lane < W) ? wacc[lane] : 0u, out);
+}
+
+// The merge of W pieces written with kDefer: lane j < W forms piece j's shifts
+// m_i = log w_a + i log g_a + max_i in fp64 (-inf for an empty moment), then as merge_warp_pieces
+// with the fp32 rescaling.
+template <int W>
+__device__ __forceinline__ void merge_deferred_pieces(int lane, const double (*wm)[3], const float (*ws)[8],
+                                                      const unsigned* wacc, StepPartial* out)
+{
+    const bool on = lane < W;
+    const double a = on ? wm[lane][0] : 0.0, b = on ? wm[lane][1] : 0.0;
+    double m[3];
+    float sv[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float mx = on ? ws[lane][4 + i] : -INFINITY;
+        m[i] = mx > -INFINITY ? a + i * b + (double)mx : -INFINITY;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sv[i] = on ? ws[lane][i] : 0.0f;
+    merge_lane_pieces<W, true>(lane, m, sv, (wacc && on) ? wacc[lane] : 0u, out);
 }
 
 // CTA part: warp 0 merges the W warps' pieces and writes one record.  Call after a

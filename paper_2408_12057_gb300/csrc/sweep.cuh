@@ -175,8 +175,9 @@ __global__ void __launch_bounds__(kSweepThreads, (SweepMinBlocks<Tgt, MOVE>::val
 oais_sweep_kernel(const SweepParams P, Tgt tg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int kSS = kFp32<R> ? 8 : 4;   // floats per warp piece (fp32 forms: deferred shifts)
     __shared__ double s_m[2][kSweepThreads / 32][3];
-    __shared__ float s_s[2][kSweepThreads / 32][4];
+    __shared__ float s_s[2][kSweepThreads / 32][kSS];
     __shared__ unsigned s_acc[2][kSweepThreads / 32];
 
     tg.setup(smem);
@@ -208,7 +209,7 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
         beta_prev = beta_t;
         const R beta_r = (R)beta_t, eps_r = (R)eps_t;
         const int slot = t & 1;
-        warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
+        warp_moment_partial<kFp32<R>, kFp32<R>>(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
         logw += lg;
         unsigned acc = 0;
         for (int k = 0; k < P.mv.K; ++k)
@@ -219,8 +220,14 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if (lane == 0) s_acc[slot][warp] = acc;
         __syncthreads();
-        cta_moment_record<kSweepThreads / 32, kFp32<R>>(s_m[slot], s_s[slot], s_acc[slot],
-                                              P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
+        if constexpr (kFp32<R>) {
+            if (warp == 0)
+                merge_deferred_pieces<kSweepThreads / 32>(lane, s_m[slot], s_s[slot], s_acc[slot],
+                                                          P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
+        } else {
+            cta_moment_record<kSweepThreads / 32, false>(s_m[slot], s_s[slot], s_acc[slot],
+                                                         P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
+        }
     }
     if (!admissible(logw) || !admissible((double)ell)) bad = 1;
     if (active) {
@@ -275,8 +282,9 @@ asmc_step_kernel(const StepParams P, Tgt tg)
 {
     if (P.skip && *P.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int kSS = kFp32<R> ? 8 : 4;   // floats per warp piece (fp32 forms: deferred shifts)
     __shared__ double s_m[kSweepThreads / 32][3];
-    __shared__ float s_s[kSweepThreads / 32][4];
+    __shared__ float s_s[kSweepThreads / 32][kSS];
     __shared__ unsigned s_acc[kSweepThreads / 32];
     constexpr bool GRAD = (MOVE != kRwmh);
 
@@ -305,7 +313,7 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     const double beta_t = P.beta[P.t], eps_t = P.eps[P.t - 1];
     const double lg = step_log_increment<R>(beta_t - P.beta[P.t - 1], ell);
     const R beta_r = (R)beta_t, eps_r = (R)eps_t;
-    warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[warp], s_s[warp]);
+    warp_moment_partial<kFp32<R>, kFp32<R>>(logw, lg, active, s_m[warp], s_s[warp]);
     logw += lg;
     unsigned acc = 0;
     for (int k = 0; k < P.mv.K; ++k)
@@ -316,13 +324,23 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if (lane == 0) s_acc[warp] = acc;
     __syncthreads();
-    cta_moment_record<kSweepThreads / 32, kFp32<R>>(s_m, s_s, s_acc,
-                                          P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
+    if constexpr (kFp32<R>) {
+        if (warp == 0)
+            merge_deferred_pieces<kSweepThreads / 32>(lane, s_m, s_s, s_acc,
+                                                      P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
+    } else {
+        cta_moment_record<kSweepThreads / 32, false>(s_m, s_s, s_acc,
+                                                     P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
+    }
     __syncthreads();
     // ESS pieces of w_{t^-}: LSE of log w (slot 0) and of 2 log w (slot 1)
-    warp_moment_partial<kFp32<R>>(logw, logw, active, s_m[warp], s_s[warp]);
+    warp_moment_partial<kFp32<R>, kFp32<R>>(logw, logw, active, s_m[warp], s_s[warp]);
     __syncthreads();
-    cta_moment_record<kSweepThreads / 32, kFp32<R>>(s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
+    if constexpr (kFp32<R>) {
+        if (warp == 0) merge_deferred_pieces<kSweepThreads / 32>(lane, s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
+    } else {
+        cta_moment_record<kSweepThreads / 32, false>(s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
+    }
     if (active) {
         R* xw = reinterpret_cast<R*>(P.x[b]);
         R* gw = reinterpret_cast<R*>(P.gl[b]);
