@@ -21,14 +21,14 @@ constexpr int kScanTile = kScanThreads * kScanItems;   // particles per scan blo
 int scan_blocks(int64_t N) { return (int)((N + kScanTile - 1) / kScanTile); }
 
 // The ESS test merges the per-CTA pieces (m_j, s_j) of log w and 2 log w into
-// LSE = M + log sum_j s_j exp(m_j - M), in two levels: groups of kEssGroup pieces on as many
-// CTAs (asmc_ess_group_kernel), then the groups on one (the decision).  Each merge takes two
-// passes, the largest shift M and then the rescaled sum, whose factors exp(m_j - M) take the
-// fp64 difference (<= 0) rounded once to fp32 and an fp32 exponential (relative effect on a
-// sum below a few 1e-8, the pieces themselves being fp32 sums).  One CTA merging every piece
-// through a chain of fp64 exponentials (each waiting for the last) took 70 us for 2 048 pieces
-// on this part's slow fp64 pipe; one CTA doing the two passes over them, 21 us.
-constexpr int kDecideThreads = 256;
+// LSE = M + log sum_j s_j exp(m_j - M), in two levels within one launch: groups of kEssGroup
+// pieces on as many CTAs, then the groups in the CTA that completes the last one (the
+// decision).  Each merge takes two passes, the largest shift M and then the rescaled sum, whose
+// factors exp(m_j - M) take the fp64 difference (<= 0) rounded once to fp32 and an fp32
+// exponential (relative effect on a sum below a few 1e-8, the pieces themselves being fp32
+// sums).  One CTA merging every piece through a chain of fp64 exponentials (each waiting for
+// the last) took 70 us for 2 048 pieces on this part's slow fp64 pipe; one CTA doing the two
+// passes over them, 21 us; the two levels in two launches, 13 us.
 constexpr int kEssGroup = 64;
 int asmc_ess_groups(int nparts) { return (nparts + kEssGroup - 1) / kEssGroup; }
 
@@ -62,32 +62,71 @@ __device__ __forceinline__ double block_reduce_sum(double v, double* sh)
 }
 // (M_i, S_i), i = 0, 1, of the pieces [0, n) (all threads of the CTA call it; thread t takes
 // pieces t, t + NT, ...)
-template <int NT>
+// kL2: read the pieces at L2 (written by other CTAs of the same launch)
+template <int NT, bool kL2 = false>
 __device__ __forceinline__ void merge_ess_pieces(const StepPartial* __restrict__ parts, int n, double (&M)[2],
                                                  double (&S)[2], double* sh)
 {
+    auto ld = [](const double* p) { return kL2 ? __ldcg(p) : *p; };
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         double mx = -INFINITY;
-        for (int j = threadIdx.x; j < n; j += NT) mx = fmax(mx, parts[j].m[i]);
+        for (int j = threadIdx.x; j < n; j += NT) mx = fmax(mx, ld(&parts[j].m[i]));
         M[i] = block_reduce_max<NT>(mx, sh);
         double sum = 0.0;
         if (M[i] > -INFINITY) {
             for (int j = threadIdx.x; j < n; j += NT) {
-                const double m = parts[j].m[i];
-                if (m > -INFINITY) sum += parts[j].s[i] * (double)expf((float)(m - M[i]));
+                const double m = ld(&parts[j].m[i]);
+                if (m > -INFINITY) sum += ld(&parts[j].s[i]) * (double)expf((float)(m - M[i]));
             }
         }
         S[i] = block_reduce_sum<NT>(sum, sh);
     }
 }
 
-__global__ void __launch_bounds__(kEssGroup)
-asmc_ess_group_kernel(const StepPartial* __restrict__ parts, int nparts, StepPartial* __restrict__ groups,
-                      const int* skip)
+// the decision of step t from the merged shifts and sums (one thread)
+__device__ __forceinline__ void asmc_decide(AsmcState* st, const double (&M)[2], const double (&S)[2], int t, int T,
+                                        const double* __restrict__ beta, double ess_frac, int64_t N, Rng rng,
+                                        double* ess_trace, int* resampled)
 {
-    if (skip && *skip) return;
+    // ESS = exp(2 LSE(log w) - LSE(2 log w)) = S_0^2 / S_1 exp(2 M_0 - M_1); the shift of the
+    // doubled weights is exactly twice the other (doubling commutes with rounding), so the
+    // exponential is 1 but for empty sums, and the logarithms (fp64, slow here) are taken
+    // only when the segment closes
+    const double d2 = 2.0 * M[0] - M[1];
+    const double ess = S[0] * S[0] / S[1] * (d2 == 0.0 ? 1.0 : exp(d2));
+    st->cur ^= st->pend;             // the previous step's gather is now the live buffer
+    // the last step (t = T, or beta_t = 1 for a schedule found online) closes the segment
+    const bool last = (t == T) || beta[t] >= 1.0;
+    const bool fire = last || (ess_frac > 0.0 && ess < ess_frac * (double)N);
+    int pend = 0;
+    if (fire) {
+        const double lse1 = M[0] + log(S[0]);
+        st->logZ += lse1 - log((double)N);
+        if (!last) {
+            pend = 1;
+            st->n_resample += 1;
+            st->lse = lse1;
+            const Philox4 r = philox4x32_10(0xFFFFFFFFu, (uint32_t)t, 0u, rng.tag, rng.k0, rng.k1);
+            st->U = u01d(r.v[0]);
+        }
+    }
+    st->pend = pend;
+    if (ess_trace) ess_trace[t - 1] = ess;
+    if (resampled) resampled[t - 1] = fire ? 1 : 0;
+}
+
+// One launch per step: CTA g merges the pieces [64 g, 64 g + 64) into group record g; the CTA
+// that completes the last group (a ticket in the ASMC state, no waiting) merges the groups and
+// takes the decision, then resets the ticket for the next step.
+__global__ void __launch_bounds__(kEssGroup)
+asmc_ess_decide_kernel(const StepPartial* __restrict__ parts, int nparts, StepPartial* __restrict__ groups,
+                       AsmcState* st, int t, int T, const double* __restrict__ beta, double ess_frac, int64_t N,
+                       Rng rng, double* ess_trace, int* resampled, const int* skip)
+{
+    if (skip && *skip) return;           // the step was skipped: st (pend = 0) stays as it is
     __shared__ double sh[kEssGroup / 32];
+    __shared__ int last;
     const int j0 = blockIdx.x * kEssGroup;
     double M[2], S[2];
     merge_ess_pieces<kEssGroup>(parts + j0, min(kEssGroup, nparts - j0), M, S, sh);
@@ -97,45 +136,16 @@ asmc_ess_group_kernel(const StepPartial* __restrict__ parts, int nparts, StepPar
         g.m[1] = M[1]; g.s[1] = S[1];
         g.m[2] = -INFINITY;
         groups[blockIdx.x] = g;
+        __threadfence();                 // the record before the ticket
+        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
     }
-}
-
-__global__ void __launch_bounds__(kDecideThreads)
-asmc_decide_kernel(AsmcState* st, const StepPartial* __restrict__ groups, int ngroups, int t, int T,
-                   const double* __restrict__ beta, double ess_frac, int64_t N, Rng rng, double* ess_trace,
-                   int* resampled, const int* skip)
-{
-    if (skip && *skip) return;           // the step was skipped: st (pend = 0) stays as it is
-    __shared__ double sh[kDecideThreads / 32];
-    const int tid = threadIdx.x;
-    double M[2], S[2];
-    merge_ess_pieces<kDecideThreads>(groups, ngroups, M, S, sh);
-    if (tid == 0) {
-        // ESS = exp(2 LSE(log w) - LSE(2 log w)) = S_0^2 / S_1 exp(2 M_0 - M_1); the shift of the
-        // doubled weights is exactly twice the other (doubling commutes with rounding), so the
-        // exponential is 1 but for empty sums, and the logarithms (fp64, slow here) are taken
-        // only when the segment closes
-        const double d2 = 2.0 * M[0] - M[1];
-        const double ess = S[0] * S[0] / S[1] * (d2 == 0.0 ? 1.0 : exp(d2));
-        st->cur ^= st->pend;             // the previous step's gather is now the live buffer
-        // the last step (t = T, or beta_t = 1 for a schedule found online) closes the segment
-        const bool last = (t == T) || beta[t] >= 1.0;
-        const bool fire = last || (ess_frac > 0.0 && ess < ess_frac * (double)N);
-        int pend = 0;
-        if (fire) {
-            const double lse1 = M[0] + log(S[0]);
-            st->logZ += lse1 - log((double)N);
-            if (!last) {
-                pend = 1;
-                st->n_resample += 1;
-                st->lse = lse1;
-                const Philox4 r = philox4x32_10(0xFFFFFFFFu, (uint32_t)t, 0u, rng.tag, rng.k0, rng.k1);
-                st->U = u01d(r.v[0]);
-            }
-        }
-        st->pend = pend;
-        if (ess_trace) ess_trace[t - 1] = ess;
-        if (resampled) resampled[t - 1] = fire ? 1 : 0;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();                     // every group record before reading them
+    merge_ess_pieces<kEssGroup, true>(groups, gridDim.x, M, S, sh);
+    if (threadIdx.x == 0) {
+        st->ticket = 0u;
+        asmc_decide(st, M, S, t, T, beta, ess_frac, N, rng, ess_trace, resampled);
     }
 }
 
@@ -251,9 +261,8 @@ cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int npar
 {
     const int ng = asmc_ess_groups(nparts);
     StepPartial* groups = P.ess_parts + nparts;   // the buffer holds nparts pieces, then the groups
-    asmc_ess_group_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups, P.skip);
-    asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, groups, ng, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
-                                                    ess_trace, resampled, P.skip);
+    asmc_ess_decide_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups, st, P.t, P.T, P.beta, ess_frac,
+                                                    P.N, P.mv.rng, ess_trace, resampled, P.skip);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);
@@ -267,9 +276,8 @@ cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts,
 {
     const int ng = asmc_ess_groups(nparts);
     StepPartial* groups = P.ess_parts + nparts;   // the buffer holds nparts pieces, then the groups
-    asmc_ess_group_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups, P.skip);
-    asmc_decide_kernel<<<1, kDecideThreads, 0, s>>>(st, groups, ng, P.t, P.T, P.beta, ess_frac, P.N, P.mv.rng,
-                                                    ess_trace, resampled, P.skip);
+    asmc_ess_decide_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups, st, P.t, P.T, P.beta, ess_frac,
+                                                    P.N, P.mv.rng, ess_trace, resampled, P.skip);
     const int nb = scan_blocks(P.N);
     asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);

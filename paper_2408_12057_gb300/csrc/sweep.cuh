@@ -251,7 +251,7 @@ struct AsmcState {
     int cur;            // buffer holding the particles at the start of the last decision
     int pend;           // 1: the last step resampled into buffer cur ^ 1
     int n_resample;     // intermediate resampling events so far
-    int pad;
+    unsigned ticket;    // CTAs of the ESS merge done this step (the last one decides, then resets it)
     double logZ;        // accumulated sum_r (LSE(log w_{tau_r^-}) - log N)
     double lse;         // LSE of the weights of the pending resampling event
     double U;           // its systematic-resampling uniform
