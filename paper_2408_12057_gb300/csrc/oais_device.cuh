@@ -187,8 +187,8 @@ __device__ __forceinline__ bool admissible(double v) { return !isnan(v) && v != 
 // forms whose particle arithmetic is fp32; the fp64 pipe of this part is slow): the offsets
 // come from two fp64 differences per particle, lw - lw_a and lg - lg_a, rounded to fp32,
 // which adds about 2^-24 (|lw - lw_a| + i |lg - lg_a|) to exponent i.  The anchor a is the
-// warp's largest v_1 (found from a first pass of the same form anchored at the first lanes
-// with finite values), so that the error is small where the weight is: with an arbitrary
+// warp's largest v_1 (found from a first pass over the fp32 roundings of log w and log g),
+// so that the error is small where the weight is: with an arbitrary
 // anchor, spreads of 10^4 in log w (a large first step of a likelihood over hundreds of
 // rows) moved D_hat by ~1e-3.  Both paths let log w = -inf (a zero weight) and log g = -inf
 // (a state outside the likelihood's support) drop out of the moments they zero.
@@ -196,12 +196,12 @@ __device__ __forceinline__ bool finite_bits(double v)
 {
     return (__double2hiint(v) & 0x7FF00000) != 0x7FF00000;   // exponent field not all ones
 }
-// kDefer (with kFast): the lead lane leaves the anchors (wm[0] = log w_a, wm[1] = log g_a) and
-// the fp32 maxima (ws[4 + i]) instead of forming m_i = log w_a + i log g_a + max_i in fp64, which
-// the CTA merge then does for its W pieces only (merge_deferred_pieces; ws holds 8 floats).
-template <bool kFast = false, bool kDefer = false>
+// With kFast the lead lane leaves the anchors (wm[0] = log w_a, wm[1] = log g_a) and the fp32
+// maxima (ws[4 + i]) instead of forming m_i = log w_a + i log g_a + max_i in fp64, which the CTA
+// merge then does for its W pieces only (merge_deferred_pieces; ws holds 8 floats).
+template <bool kFast = false>
 __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool active,
-                                                    double* wm /*3*/, float* ws /*4, or 8 with kDefer*/)
+                                                    double* wm /*3*/, float* ws /*4, or 8 with kFast*/)
 {
     const unsigned full = 0xFFFFFFFFu;
     const bool lead = (threadIdx.x & 31) == 0;
@@ -212,9 +212,9 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
             if (lead) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    wm[i] = kDefer ? 0.0 : -INFINITY;
+                    wm[i] = 0.0;
                     ws[i] = 0.0f;
-                    if (kDefer) ws[4 + i] = -INFINITY;
+                    ws[4 + i] = -INFINITY;
                 }
                 ws[3] = 0.0f;
             }
@@ -250,12 +250,8 @@ __device__ __forceinline__ void warp_moment_partial(double lw, double lg, bool a
                 for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
             }
             if (lead) {
-                if (kDefer) {
-                    ws[4 + i] = mx;
-                    if (i == 0) { wm[0] = a0; wm[1] = b0; }
-                } else {
-                    wm[i] = mx > -INFINITY ? a0 + i * b0 + (double)mx : -INFINITY;
-                }
+                ws[4 + i] = mx;
+                if (i == 0) { wm[0] = a0; wm[1] = b0; }
                 ws[i] = e;
                 if (i == 0) ws[3] = u;
             }
@@ -371,7 +367,7 @@ __device__ __forceinline__ void merge_warp_pieces(int lane, const double (*wm)[3
     merge_lane_pieces<W, kFast>(lane, m, sv, (wacc && lane < W) ? wacc[lane] : 0u, out);
 }
 
-// The merge of W pieces written with kDefer: lane j < W forms piece j's shifts
+// The merge of W pieces written with kFast: lane j < W forms piece j's shifts
 // m_i = log w_a + i log g_a + max_i in fp64 (-inf for an empty moment), then as merge_warp_pieces
 // with the fp32 rescaling.
 template <int W>

@@ -209,7 +209,7 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
         beta_prev = beta_t;
         const R beta_r = (R)beta_t, eps_r = (R)eps_t;
         const int slot = t & 1;
-        warp_moment_partial<kFp32<R>, kFp32<R>>(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
+        warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
         logw += lg;
         unsigned acc = 0;
         for (int k = 0; k < P.mv.K; ++k)
@@ -313,7 +313,7 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     const double beta_t = P.beta[P.t], eps_t = P.eps[P.t - 1];
     const double lg = step_log_increment<R>(beta_t - P.beta[P.t - 1], ell);
     const R beta_r = (R)beta_t, eps_r = (R)eps_t;
-    warp_moment_partial<kFp32<R>, kFp32<R>>(logw, lg, active, s_m[warp], s_s[warp]);
+    warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[warp], s_s[warp]);
     logw += lg;
     unsigned acc = 0;
     for (int k = 0; k < P.mv.K; ++k)
@@ -334,7 +334,7 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     }
     __syncthreads();
     // ESS pieces of w_{t^-}: LSE of log w (slot 0) and of 2 log w (slot 1)
-    warp_moment_partial<kFp32<R>, kFp32<R>>(logw, logw, active, s_m[warp], s_s[warp]);
+    warp_moment_partial<kFp32<R>>(logw, logw, active, s_m[warp], s_s[warp]);
     __syncthreads();
     if constexpr (kFp32<R>) {
         if (warp == 0) merge_deferred_pieces<kSweepThreads / 32>(lane, s_m, s_s, nullptr, P.ess_parts + blockIdx.x);

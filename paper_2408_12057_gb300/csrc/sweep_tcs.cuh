@@ -142,7 +142,7 @@ struct Misc {
     double xl[kMaxH][kTile];    // per column group: partial log-likelihood
     float4 xm[kMaxH][kTile];    // per coordinate group: partial sums of the MH ratio
     double s_m[2][4][3];
-    float s_s[2][4][8];                // warp pieces with deferred shifts (warp_moment_partial<true, true>)
+    float s_s[2][4][8];                // warp pieces with deferred shifts (warp_moment_partial<true>)
     unsigned s_acc[2][4];
     Params prm;                 // batched launch: the current item's problem
     uint32_t item;              // batched launch: the current item
@@ -757,7 +757,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
             const double lg = (beta_t - beta_prev) * ell;
             beta_prev = beta_t;
             const int slot = t & 1;
-            if (h == 0) warp_moment_partial<true, true>(logw, lg, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
+            if (h == 0) warp_moment_partial<true>(logw, lg, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
             logw += lg;
             unsigned acc = 0;
             const float beta = (float)beta_t, eps = (float)eps_t, he = 0.5f * eps;
@@ -859,7 +859,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
         if (P.ess_parts && h == 0) {
             // (log w, 2 log w) moments of the tile for the ESS of the resampling test
             const int slot = (P.t_end + 1) & 1;
-            warp_moment_partial<true, true>(logw, logw, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
+            warp_moment_partial<true>(logw, logw, active, M->s_m[slot][Th.q], M->s_s[slot][Th.q]);
             if (lane == 0) M->s_acc[slot][Th.q] = 0u;
             named_sync(2, 128);
             if (warp == 0) merge_deferred_pieces<4>(lane, M->s_m[slot], M->s_s[slot], M->s_acc[slot], P.ess_parts + tile);
