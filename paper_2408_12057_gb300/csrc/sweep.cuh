@@ -162,13 +162,15 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
     return acc;
 }
 
-// CTAs per SM that the register allocation of the sweep must allow (0: the compiler's
-// choice): the random-walk step of the mixture is cheap and latency-bound, and 8 CTAs (32
-// warps) per SM at 64 registers ran it 3 % faster than the 94 registers the compiler picks
-// (an explicit 1 gave 122 registers and 20 % slower); the lock-step ASMC kernel of the same
-// step, 7 % faster (a T = 256 round at N = 2^20: 49.1 against 53.0 ms)
+// CTAs per SM that the register allocation must allow (0: the compiler's choice).  The
+// random-walk step of the mixture is cheap and latency-bound: the sweep ran fastest at 6 CTAs
+// (24.5 ms for T = 256 at N = 2^20, 80 registers; 24.9 ms at 8 CTAs and 64 registers; an
+// explicit 1 gave 122 registers and 30 % slower), the lock-step ASMC kernel of the same step at
+// 8 (a T = 256 round in 44.1 ms; 46.1 at 6, 53.0 with the compiler's 92 registers).
 template <class Tgt, int MOVE> struct SweepMinBlocks { static constexpr int value = 0; };
-template <typename R, int D> struct SweepMinBlocks<GmmTarget<R, D>, kRwmh> { static constexpr int value = 8; };
+template <typename R, int D> struct SweepMinBlocks<GmmTarget<R, D>, kRwmh> { static constexpr int value = 6; };
+template <class Tgt, int MOVE> struct StepMinBlocks { static constexpr int value = 0; };
+template <typename R, int D> struct StepMinBlocks<GmmTarget<R, D>, kRwmh> { static constexpr int value = 8; };
 
 template <class Tgt, int MOVE, int D, typename R>
 __global__ void __launch_bounds__(kSweepThreads, (SweepMinBlocks<Tgt, MOVE>::value))
@@ -277,7 +279,7 @@ struct StepParams {
 };
 
 template <class Tgt, int MOVE, int D, typename R>
-__global__ void __launch_bounds__(kSweepThreads, (SweepMinBlocks<Tgt, MOVE>::value))
+__global__ void __launch_bounds__(kSweepThreads, (StepMinBlocks<Tgt, MOVE>::value))
 asmc_step_kernel(const StepParams P, Tgt tg)
 {
     if (P.skip && *P.skip) return;
