@@ -160,7 +160,9 @@ oais_status oais_init(oais_ctx** ctx, const oais_target* target, const oais_move
  * merge the per-step moments, form log Z_hat, then install
  * OptimiseSchedule(T_next, B_T, g_hat) (Alg. 3) as the schedule of the next round.
  * T_next <= T_max.  Synchronises the context's stream.  On error the previous round's
- * results and the current schedule are left unchanged (anytime property, Sec. 1). */
+ * results and the current schedule are left unchanged (anytime property, Sec. 1) and the round
+ * counter does not advance; the particle buffers of oais_particles then hold the failed
+ * round's values. */
 oais_status oais_round(oais_ctx* ctx, int32_t T_next, oais_round_result* out);
 
 /* One round of optimised ASMC (Alg. 2 with Alg. 1's adaptive resampling): particles
@@ -226,7 +228,11 @@ oais_status oais_round_commit(oais_ctx* ctx, int32_t T_next, const double* log_g
  * redrawn every round, and the counter-based random numbers make a resumed round
  * bit-identical to an uninterrupted one.  oais_state_bytes gives the size of the blob;
  * oais_save_state writes it into host memory; oais_load_state restores it into a context
- * created for the same target, move and N (EINVAL otherwise, the context unchanged). */
+ * created for the same target, move and N (EINVAL otherwise, the context unchanged).  A blob
+ * is checked as the setters check their arguments (schedule as oais_set_schedule, step sizes
+ * finite and > 0, shard block as oais_set_shard); a successful load discards the results of
+ * any round run before it (oais_logZ and the other last-round queries return EINVAL until the
+ * next round completes). */
 oais_status oais_state_bytes(const oais_ctx* ctx, size_t* bytes);
 oais_status oais_save_state(const oais_ctx* ctx, void* buf, size_t bytes);
 oais_status oais_load_state(oais_ctx* ctx, const void* buf, size_t bytes);
@@ -294,6 +300,30 @@ oais_status oais_optimise_schedule(int32_t T, const double* beta, const double* 
                                    int32_t T_next, double* beta_next, double* D_hat,
                                    double* Lambda);
 
+/* Merge of per-shard round statistics for oais_round_commit (Sec. 5.1.2: within a round the
+ * particles are independent, so a sum over all particles is the sum of the shards' sums).
+ * Inputs are the P shards' outputs of oais_round_local, stacked in rank order (host arrays):
+ * log_ghat [P][T][3], accepted [P][T], lse [P][2].  Outputs (host): log_ghat_out [T][3] and
+ * lse_out [2], each the log-sum-exp over shards of the inputs at that position (maximum, then
+ * the sum of exp(a_p - maximum) in rank order: every rank given the same inputs gets the same
+ * bits; -inf entries are zero sums), and accepted_out [T], the sums of the counts.  No device
+ * work.  EINVAL for P < 1, T < 1 or a null pointer. */
+oais_status oais_merge_shard_stats(int32_t P, int32_t T, const double* log_ghat, const double* accepted,
+                                   const double* lse, double* log_ghat_out, double* accepted_out,
+                                   double* lse_out);
+
+/* A starting rule for the per-step sizes of a first round (the paper fixes none; App. on
+ * propagation-kernel adaptation tunes them between rounds): eps[t-1] = c / sqrt(1/s^2 +
+ * beta[t] kappa), t = 1..T, i.e. the scale of pi_beta_t along a typical direction under a
+ * Gaussian approximation whose precision is the reference's plus beta_t times a diagonal
+ * curvature estimate kappa of -log L, times the kernel's dimension scaling c (RWMH 2.38/sqrt(d),
+ * MALA 1.2 d^(-1/6), HMC d^(-1/4)).  kappa: GAUSS 1/p0^2; LOGREG sum_rj X_rj^2 / (4 d); LINREG
+ * sum_rj X_rj^2 / (d p0^2); GMM 1/p0; UNID m q (1 - q)^-1 q^2 with q = k/m.  target as for
+ * oais_init (X read from host or device memory per on_device; contraction ignored); beta: host
+ * [T+1]; eps: host [T].  No device work beyond reading a device-resident X. */
+oais_status oais_default_step_sizes(const oais_target* target, int32_t move_kind, const double* beta, int32_t T,
+                                    double* eps);
+
 /* ---------------------------------------------------------------------------------
  * Kernel-level entry points (device pointers only, no host synchronisation).
  * --------------------------------------------------------------------------------- */
@@ -352,6 +382,11 @@ oais_status oais_measure_unit_rate(int32_t unit, double* lane_ops_per_s_per_sm);
  *   wrong results -- order them on one stream.
  *   The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make it before any stream capture.
+ *   The cached address is only valid for the device's current primary context: do not call
+ *   this entry point on a device after cudaDeviceReset in the same process.
+ *   Errors: OAIS_EINVAL (null pointer, n out of range), OAIS_ECUDA (no device, lookup or
+ *   launch failed; an error left pending by an earlier call is cleared first), with the text
+ *   in oais_last_error(NULL).
  *   Calls no cudaMalloc/cudaFree and no allocating library routine. */
 #define OAIS_LOGSUMEXP_NOALLOC_MAX_N 16777216LL
 oais_status oais_logsumexp_noalloc(const double* d_a, int64_t n, double* d_out, void* stream);
@@ -414,6 +449,32 @@ oais_status oais_set_particles(oais_ctx* ctx, int64_t N);
 /* Problem index p (0 <= p <= 65535) of a single context: its random numbers use the tag
  * round | p << 16, as problem p of a batch does.  Default 0. */
 oais_status oais_set_problem(oais_ctx* ctx, int32_t p);
+
+/* ------------------------------------------------------------------------------------------
+ * Test support: failure paths without a GPU fault.  No counterpart in the paper.
+ *
+ * oais_arm_fault arms one fault, made on the host side, for the next round of the context
+ * (oais_round, oasmc_round or oais_round_local), so that a test can drive a round into each of
+ * its failure paths while the GPU stays healthy; the fault is disarmed when that round ends.
+ *   OAIS_FAULT_NONE: disarm.
+ *   OAIS_FAULT_NAN_DATA: before the round, element 0 of every device copy of the data X that
+ *     the context holds (the CUDA-core layout, the resident bf16 image, the streamed f16 image)
+ *     is overwritten with a quiet NaN by a host-to-device copy, and its value is copied back
+ *     when the round ends.  Every log-likelihood is then NaN and the round returns
+ *     OAIS_ENONFINITE.  EUNSUPPORTED for FP8 storage.
+ *   OAIS_FAULT_WITHHOLD_HANDOFF: a tensor-core sweep that runs as a persistent grid (more tiles
+ *     of 128 particles than the resident groups or CTAs of one wave) raises none of its hand-off
+ *     flags, so every resumed tile's bounded wait for its flag gives up after wait_seconds
+ *     (0: the default limit of 2 s), the CTA stops its work and releases its tensor memory, and
+ *     the round returns OAIS_ETIMEOUT.  A sweep that fits in one wave hands nothing over and is
+ *     not affected.  EUNSUPPORTED for the CUDA-core form.
+ * wait_seconds: in [0, 60], used by OAIS_FAULT_WITHHOLD_HANDOFF only.  A failed round leaves
+ * the last completed round's results and the next round's schedule as they were (the anytime
+ * property, Sec. 1), and does not advance the round counter: the next round draws the random
+ * numbers the failed one drew.  The particle buffers (oais_particles) hold the failed round's
+ * values.  EINVAL for an unknown kind. */
+typedef enum { OAIS_FAULT_NONE = 0, OAIS_FAULT_NAN_DATA = 1, OAIS_FAULT_WITHHOLD_HANDOFF = 2 } oais_fault;
+oais_status oais_arm_fault(oais_ctx* ctx, int32_t kind, double wait_seconds);
 
 #ifdef __cplusplus
 }

@@ -94,7 +94,7 @@ def _load():
             lib.orc_logsumexp.restype = f64
             lib.orc_systematic_resample.argtypes = [i64, P, f64, P]
             lib.orc_asmc.argtypes = [P, P, i64, i32, P, P, u64, u32, i64, f64,
-                                     P, P, P, P, P, P, P, P, P, P]
+                                     P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_asmc.restype = i32
             lib.orc_zja.argtypes = [P, P, i64, i32, P, P, i32, f64, f64, u64, u32,
                                     P, P, P, P, P, P, P, P, P, P]
@@ -204,7 +204,8 @@ def systematic_resample(logw, U):
 def asmc(target: Target, move_kind, N, beta, eps, seed, tag=0, moves=1, leapfrog=1,
          cycle=False, ess_frac=0.0, n_offset=0):
     """Alg. 1.  Returns a dict with logZ, log_ghat (T,3), accept (T,), ess (T,),
-    logw (N,), x (N,d), ell (N,), margin (N,), resampled (T,), n_resample, and the ELBO
+    logw (N,), x (N,d), ell (N,), margin (N,), resampled (T,), n_resample, ancestors (N,) of
+    the last intermediate resampling event (-1 if there was none), and the ELBO
     estimator's terms elbo_t (T,) = sum_n W_{t-1}^n log g_t^n with their sum elbo and
     kl = logZ - elbo (log Z = ELBO + KL, section on the KL divergence of a schedule).
     Particle n draws from counter n_offset + n (AIS particles are independent, so a
@@ -217,12 +218,13 @@ def asmc(target: Target, move_kind, N, beta, eps, seed, tag=0, moves=1, leapfrog
     res = _Result()
     out = dict(log_ghat=np.zeros((T, 3)), accept=np.zeros(T), ess=np.zeros(T),
                logw=np.zeros(N), x=np.zeros((N, target.d)), ell=np.zeros(N),
-               margin=np.zeros(N), resampled=np.zeros(T, dtype=np.int64), elbo_t=np.zeros(T))
+               margin=np.zeros(N), resampled=np.zeros(T, dtype=np.int64), elbo_t=np.zeros(T),
+               ancestors=np.full(N, -1, dtype=np.int64))
     rc = lib.orc_asmc(ctypes.byref(target._c), ctypes.byref(mv), int(N), int(T), _ptr(beta),
                       _ptr(eps), int(seed), int(tag), int(n_offset), float(ess_frac), ctypes.byref(res),
                       _ptr(out["log_ghat"]), _ptr(out["accept"]), _ptr(out["ess"]),
                       _ptr(out["logw"]), _ptr(out["x"]), _ptr(out["ell"]), _ptr(out["margin"]),
-                      _ptr(out["resampled"]), _ptr(out["elbo_t"]))
+                      _ptr(out["resampled"]), _ptr(out["elbo_t"]), _ptr(out["ancestors"]))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     out["logZ"] = res.logZ

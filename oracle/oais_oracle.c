@@ -400,7 +400,7 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
              orc_result* res, double* log_ghat /* T x 3 */, double* accept /* T */,
              double* ess_trace /* T */, double* logw_out /* N */, double* x_out /* N x d */,
              double* ell_out /* N */, double* margin_out /* N */, int64_t* resample_steps /* T */,
-             double* elbo_t /* T */)
+             double* elbo_t /* T */, int64_t* anc_out /* N: ancestors of the last intermediate event */)
 {
     const int d = tg->d;
     int need_grad = (mv->kind != ORC_RWMH);   /* EXACT keeps the gradient too (cheap) */
@@ -500,6 +500,7 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
                 memcpy(ell, e2, sizeof(double) * N);
                 memcpy(margin, m2, sizeof(double) * N);
                 for (long n = 0; n < N; ++n) logw[n] = 0.0;   /* w_t^n = 1 */
+                if (anc_out) memcpy(anc_out, anc, sizeof(int64_t) * N);
                 free(anc); free(X2); free(G2); free(e2); free(m2);
             }
         } else if (resample_steps) {
@@ -529,8 +530,7 @@ int orc_asmc(const orc_target* tg, const orc_move* mv, long N, int T, const doub
 /* when its end meets the target, the smallest geometric candidate when   */
 /* none does (steps of at least 1e-14).  The target is relative to the   */
 /* weight share A inside the likelihood's support: CESS/N >= c A (A = 1   */
-/* unless weighted states have L = 0).  Candidates are fp32 values, as on */
-/* the device.                                                            */
+/* unless weighted states have L = 0).  The candidates are fp64 values.   */
 /* Step sizes: log eps interpolated linearly in beta                      */
 /* through the points (beta_ref[t], eps_ref[t-1]), constant beyond.        */
 /* Then the ASMC step of orc_asmc; the step with beta_t = 1 (forced at     */
@@ -564,13 +564,16 @@ static double zja_step_size(double b, const double* beta_ref, const double* eps_
     return exp(log(eps_ref[t - 1]) + u * (log(eps_ref[t]) - log(eps_ref[t - 1])));
 }
 
-/* the next annealing parameter from the particles' log-weights and log-likelihoods */
+/* Candidate j (1..32) of a pass of the line search (a reading; the paper fixes only the CESS
+ * target): geometric in pass 0, hi 4^-(32 - j); equally spaced in the bracket after,
+ * lo + ((hi - lo) j) / 32.  Plain fp64 arithmetic, rounded to nearest at every operation
+ * (the oracle is built without contraction), so the grid is defined exactly. */
 static double zja_candidate(int pass, double lo, double hi, int j)
 {
-    /* the device computes its candidates in fp32; the same values here */
-    return pass == 0 ? (double)((float)hi * exp2f(-2.0f * (float)(32 - j)))
-                     : (double)((float)lo + ((float)hi - (float)lo) * (float)j / 32.0f);
+    return pass == 0 ? ldexp(hi, -2 * (32 - j)) : lo + ((hi - lo) * (double)j) * (1.0 / 32.0);
 }
+
+/* the next annealing parameter from the particles' log-weights and log-likelihoods */
 
 double orc_zja_next_beta(long N, const double* logw, const double* ell, double beta_prev, double cess_frac,
                          int t, int T_max)

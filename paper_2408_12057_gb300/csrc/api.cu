@@ -172,6 +172,9 @@ struct oais_ctx {
     std::vector<double> beta, eps;
     int round = 0;
     int problem = 0;                     // problem index in the random-number tag
+    // test support (oais_arm_fault): a fault armed for the next round
+    int fault_kind = 0;
+    uint64_t fault_wait_ns = 0;
     // last completed round
     bool have_last = false;
     std::vector<double> l_beta, l_eps, l_log_ghat, l_D, l_accept, l_elbo;
@@ -198,6 +201,16 @@ static oais_status fail(oais_ctx* ctx, oais_status s, const std::string& m)
     set_err(ctx, m);
     return s;
 }
+
+// the calling thread's error text for calls without a context (oais_last_error(NULL)), for
+// the library's other translation units
+namespace oais {
+int fail_call(int s, const char* m)
+{
+    g_err = m;
+    return s;
+}
+} // namespace oais
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -573,6 +586,10 @@ static SweepParams make_params(const oais_ctx* ctx, int T, const double* d_beta,
     P.mv.rng.k0 = (uint32_t)(seed & 0xFFFFFFFFu); P.mv.rng.k1 = (uint32_t)(seed >> 32); P.mv.rng.tag = tag;
     P.logw = logw; P.x_out = x; P.ell_out = ell; P.partials = static_cast<StepPartial*>(parts);
     P.status = status;
+    if (ctx->fault_kind == OAIS_FAULT_WITHHOLD_HANDOFF) {
+        P.withhold = 1;
+        P.handoff_wait_ns = ctx->fault_wait_ns;
+    }
     return P;
 }
 
@@ -675,10 +692,9 @@ static oais_status commit_round(oais_ctx* ctx, int T, int32_t T_next, const std:
                                 bool asmc, int n_res, const std::vector<double>& ess_tr,
                                 const std::vector<int>& rs, oais_round_result* out);
 
-static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double ess_frac, oais_round_result* out,
-                             bool local_only = false)
+static oais_status run_round_impl(oais_ctx* ctx, int32_t T_next, bool asmc, double ess_frac, oais_round_result* out,
+                                  bool local_only)
 {
-    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
     if (T_next < 1 || T_next > ctx->T_max) return fail(ctx, OAIS_EINVAL, "T_next out of range");
     if (asmc && !(ess_frac >= 0.0 && ess_frac <= 1.0 + 1e-12))
         return fail(ctx, OAIS_EINVAL, "ess_frac must be in [0, 1]");
@@ -810,6 +826,52 @@ static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double es
     if (status & 1u) return fail(ctx, OAIS_ENONFINITE, "non-finite log-weight or log-likelihood");
     ctx->cur_elbo = elbo;
     return commit_round(ctx, T, T_next, lg, acc, logZ, ess, se, ms, asmc, n_res, ess_tr, rs, out);
+}
+
+// Test support: the device copies of the data whose first element an armed NaN-data fault
+// overwrites (the CUDA-core layout, the resident tensor-core image, the streamed f16 image),
+// with the width of that element
+struct FaultSite { void* p; size_t bytes; };
+static std::vector<FaultSite> fault_sites(const oais_ctx* ctx)
+{
+    std::vector<FaultSite> v;
+    if (ctx->dt.D > 0 && ctx->dt.X) v.push_back({ctx->dt.X, f64_kind(ctx->dt.kind) ? sizeof(double) : sizeof(float)});
+    if (ctx->dt.tc && ctx->dt.tc_img) v.push_back({ctx->dt.tc_img, 2});
+    if (ctx->dt.tcs && ctx->dt.tcs_img && !ctx->dt.tcs_q8) v.push_back({ctx->dt.tcs_img, 2});
+    return v;
+}
+
+static oais_status run_round(oais_ctx* ctx, int32_t T_next, bool asmc, double ess_frac, oais_round_result* out,
+                             bool local_only = false)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (ctx->fault_kind != OAIS_FAULT_NAN_DATA) {
+        const oais_status st = run_round_impl(ctx, T_next, asmc, ess_frac, out, local_only);
+        ctx->fault_kind = OAIS_FAULT_NONE;        // a fault is armed for one round
+        return st;
+    }
+    // NaN data: element 0 of every device copy of X becomes a quiet NaN for this round and gets
+    // its value back afterwards (whatever the round's outcome)
+    const std::vector<FaultSite> sites = fault_sites(ctx);
+    std::vector<uint64_t> saved(sites.size(), 0);
+    ctx->fault_kind = OAIS_FAULT_NONE;
+    CK(cudaStreamSynchronize(ctx->stream));   // no earlier work of the context still reads X
+    for (size_t i = 0; i < sites.size(); ++i) {
+        const double qd = NAN;
+        const float qf = NAN;
+        const uint16_t qh = sites[i].p == ctx->dt.tc_img ? 0x7FC0u : 0x7E00u;   // bf16 / f16 quiet NaN
+        const void* q = sites[i].bytes == 8 ? (const void*)&qd : sites[i].bytes == 4 ? (const void*)&qf
+                                                                                       : (const void*)&qh;
+        CK(cudaMemcpy(&saved[i], sites[i].p, sites[i].bytes, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(sites[i].p, q, sites[i].bytes, cudaMemcpyHostToDevice));
+    }
+    const oais_status st = run_round_impl(ctx, T_next, asmc, ess_frac, out, local_only);
+    const std::string msg = ctx->err;
+    cudaStreamSynchronize(ctx->stream);
+    for (size_t i = 0; i < sites.size(); ++i)
+        CK(cudaMemcpy(sites[i].p, &saved[i], sites[i].bytes, cudaMemcpyHostToDevice));
+    ctx->err = msg;
+    return st;
 }
 
 // Alg. 3 and the carry-over of step sizes from the round's (global) statistics
@@ -1021,6 +1083,13 @@ oais_status oais_load_state(oais_ctx* ctx, const void* buf, size_t bytes)
         return fail(ctx, OAIS_EINVAL, "bad schedule size in state");
     const double* b = reinterpret_cast<const double*>(static_cast<const char*>(buf) + sizeof(h));
     if (!valid_schedule(b, h.T)) return fail(ctx, OAIS_EINVAL, "bad schedule in state");
+    // the same checks as oais_set_schedule (step sizes) and oais_set_shard (particle block)
+    for (int t = 0; t < h.T; ++t)
+        if (!(b[h.T + 1 + t] > 0.0) || !std::isfinite(b[h.T + 1 + t]))
+            return fail(ctx, OAIS_EINVAL, "bad step sizes in state");
+    if (h.n_offset < 0 || h.N_total < ctx->N || h.n_offset + ctx->N > h.N_total || h.N_total > 0xFFFFFFFFLL)
+        return fail(ctx, OAIS_EINVAL, "bad shard block in state");
+    if (h.round < 0) return fail(ctx, OAIS_EINVAL, "bad round index in state");
     ctx->beta.assign(b, b + h.T + 1);
     ctx->eps.assign(b + h.T + 1, b + 2 * h.T + 1);
     ctx->seed = h.seed;
@@ -1028,6 +1097,8 @@ oais_status oais_load_state(oais_ctx* ctx, const void* buf, size_t bytes)
     ctx->n_offset = h.n_offset;
     ctx->N_total = h.N_total;
     ctx->pend_T = 0;
+    // the results of a round run before the load belong to another state
+    ctx->have_last = false;
     return OAIS_OK;
 }
 
@@ -1556,6 +1627,87 @@ void oais_batch_destroy(oais_batch* b)
     delete b;
 }
 
+// Merge of per-shard round statistics (Sec. 5.1.2: the particles of a round are independent,
+// so a sum over all particles is the sum of the shards' sums).  Each moment log g_hat_{t,i} and
+// each final-weight sum is a logarithm of a sum over particles: the merge is the log-sum-exp
+// over shards, the plain definition (maximum, then the sum of exp(a_p - max) in shard order);
+// acceptance counts add.  Every rank calling it on the same inputs gets the same bits.
+static double lse_over_shards(const double* a, int P, size_t stride)
+{
+    double m = -INFINITY;
+    for (int p = 0; p < P; ++p) {
+        const double v = a[(size_t)p * stride];
+        if (std::isnan(v)) return v;
+        if (v > m) m = v;
+    }
+    if (m == -INFINITY || m == INFINITY) return m;
+    double s = 0.0;
+    for (int p = 0; p < P; ++p) s += std::exp(a[(size_t)p * stride] - m);
+    return m + std::log(s);
+}
+
+oais_status oais_merge_shard_stats(int32_t P, int32_t T, const double* log_ghat, const double* accepted,
+                                   const double* lse, double* log_ghat_out, double* accepted_out, double* lse_out)
+{
+    if (P < 1 || T < 1 || !log_ghat || !accepted || !lse || !log_ghat_out || !accepted_out || !lse_out)
+        return fail(nullptr, OAIS_EINVAL, "bad arguments to oais_merge_shard_stats");
+    for (int j = 0; j < 3 * T; ++j) log_ghat_out[j] = lse_over_shards(log_ghat + j, P, (size_t)3 * T);
+    for (int t = 0; t < T; ++t) {
+        double a = 0.0;
+        for (int p = 0; p < P; ++p) a += accepted[(size_t)p * T + t];
+        accepted_out[t] = a;
+    }
+    for (int i = 0; i < 2; ++i) lse_out[i] = lse_over_shards(lse + i, P, 2);
+    return OAIS_OK;
+}
+
+// The starting rule for per-step sizes (a reading: the paper fixes no step sizes): the scale of
+// pi_beta along a typical direction, approximated by a Gaussian whose precision is the
+// reference's plus beta times a diagonal curvature estimate of -log L, times the usual
+// dimension scaling of each kernel (random walk 2.38 / sqrt(d); MALA 1.2 d^(-1/6); HMC
+// d^(-1/4)).  Curvature per family: Gaussian 1 / p0^2; logistic (1/4) sum X^2 / d (the
+// sigmoid's largest slope); linear regression sum X^2 / (d p0^2); mixture 1 / p0 (a
+// component's precision); Unid m q (1 - q)^-1 q^2 with q = k / m (the binomial ridge's
+// width in the probit coordinates).
+oais_status oais_default_step_sizes(const oais_target* tg, int32_t move_kind, const double* beta, int32_t T,
+                                    double* eps)
+{
+    if (!tg || !beta || !eps || T < 1) return fail(nullptr, OAIS_EINVAL, "bad arguments to oais_default_step_sizes");
+    if (move_kind < OAIS_RWMH || move_kind > OAIS_HMC) return fail(nullptr, OAIS_EINVAL, "bad move kind");
+    if (tg->d < 1 || !tg->X || !(tg->ref_scale > 0) || !(tg->p0 > 0))
+        return fail(nullptr, OAIS_EINVAL, "bad target");
+    if (tg->dtype != OAIS_DT_F64 && tg->dtype != OAIS_DT_F32) return fail(nullptr, OAIS_EINVAL, "bad dtype");
+    const double d = (double)tg->d, p0 = tg->p0;
+    double curv;
+    if (tg->kind == kGauss) {
+        curv = 1.0 / (p0 * p0);
+    } else if (tg->kind == kLogreg || tg->kind == kLinreg) {
+        if (tg->n < 1) return fail(nullptr, OAIS_EINVAL, "n must be >= 1");
+        std::vector<double> Xh;
+        oais_status st = fetch(nullptr, tg->X, (size_t)tg->n * tg->d, tg->dtype, tg->on_device, Xh);
+        if (st != OAIS_OK) return st;
+        double ss = 0.0;
+        for (double v : Xh) ss += v * v;
+        curv = tg->kind == kLogreg ? 0.25 * ss / d : ss / d / (p0 * p0);
+    } else if (tg->kind == kUnid) {
+        std::vector<double> mk;
+        oais_status st = fetch(nullptr, tg->X, 2, OAIS_DT_F64, tg->on_device, mk);
+        if (st != OAIS_OK) return st;
+        const double q = mk[1] / mk[0];
+        if (!(q > 0.0 && q < 1.0)) return fail(nullptr, OAIS_EINVAL, "UNID: successes 0 < k < m");
+        curv = mk[0] / (q * (1.0 - q)) * q * q;
+    } else if (tg->kind == kGmm) {
+        curv = 1.0 / p0;
+    } else {
+        return fail(nullptr, OAIS_EINVAL, "unknown target kind");
+    }
+    const double c = move_kind == OAIS_RWMH ? 2.38 / std::sqrt(d)
+                   : move_kind == OAIS_MALA ? 1.2 * std::pow(d, -1.0 / 6.0) : std::pow(d, -0.25);
+    const double s2 = tg->ref_scale * tg->ref_scale;
+    for (int t = 1; t <= T; ++t) eps[t - 1] = c / std::sqrt(1.0 / s2 + beta[t] * curv);
+    return OAIS_OK;
+}
+
 oais_status oais_budget(int64_t N, int32_t T, int64_t N_cap, int32_t T_cap, int64_t* N_next, int32_t* T_next)
 {
     if (N < 1 || T < 1 || N_cap < N || T_cap < T || !N_next || !T_next)
@@ -1584,6 +1736,29 @@ oais_status oais_set_particles(oais_ctx* ctx, int64_t N)
     if (N < 1 || N > ctx->N_cap) return fail(ctx, OAIS_EINVAL, "N outside [1, the count the context was created with]");
     ctx->N = N;
     ctx->N_total = N;
+    return OAIS_OK;
+}
+
+oais_status oais_arm_fault(oais_ctx* ctx, int32_t kind, double wait_seconds)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (!(wait_seconds >= 0.0 && wait_seconds <= 60.0)) return fail(ctx, OAIS_EINVAL, "wait_seconds in [0, 60]");
+    switch (kind) {
+    case OAIS_FAULT_NONE:
+        break;
+    case OAIS_FAULT_NAN_DATA:
+        if (ctx->dt.tcs_q8) return fail(ctx, OAIS_EUNSUPPORTED, "NaN data: not for FP8 storage");
+        if (fault_sites(ctx).empty()) return fail(ctx, OAIS_EUNSUPPORTED, "NaN data: no device copy of X");
+        break;
+    case OAIS_FAULT_WITHHOLD_HANDOFF:
+        if (!ctx->dt.tc && !ctx->dt.tcs)
+            return fail(ctx, OAIS_EUNSUPPORTED, "withheld hand-off: only the tensor-core forms hand tiles over");
+        break;
+    default:
+        return fail(ctx, OAIS_EINVAL, "unknown fault kind");
+    }
+    ctx->fault_kind = kind;
+    ctx->fault_wait_ns = (uint64_t)(wait_seconds * 1e9);
     return OAIS_OK;
 }
 

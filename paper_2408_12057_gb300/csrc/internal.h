@@ -103,6 +103,10 @@ cudaError_t launch_zja_search(ZjaState* zs, const AsmcState* st, const StepParam
 cudaError_t launch_sweep_tc(const SweepParams& sp, const void* Ximg, const uint32_t* ybits, int n, int d,
                             float* grad_state, int* handed, cudaStream_t s);
 
+// records m as the calling thread's error text for calls without a context
+// (oais_last_error(NULL)) and returns s; the status is an oais_status value
+int fail_call(int s, const char* m);
+
 // smallest compiled width >= d for the family, 0 if none
 int padded_width(int kind, int d);
 

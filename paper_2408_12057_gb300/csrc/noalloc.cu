@@ -22,10 +22,18 @@
 //
 // Set-up: host code cannot use the array's name as a device address.  The first call on
 // each device (with that device current) looks the address up with cudaGetSymbolAddress
-// and caches it; make that first call before any stream capture on the device.
+// and caches it; make that first call before any stream capture on the device.  The cached
+// address belongs to the device's current primary context: after cudaDeviceReset (or any
+// other teardown of that context) the library's module is loaded again and the array may
+// move, so a process that resets a device must not call this entry point on it afterwards.
+//
+// Errors go through the library's per-thread error text (oais_last_error(NULL)).  An error
+// left pending by an earlier, unrelated CUDA call is cleared on entry, so a launch failure
+// reported here is this call's own.
 #include <cmath>
 #include <mutex>
 
+#include "internal.h"
 #include "oais_device.cuh"
 #include "../../include/oais.h"
 
@@ -115,16 +123,23 @@ static_assert(kMaxN == OAIS_LOGSUMEXP_NOALLOC_MAX_N, "limit documented in oais.h
 extern "C" oais_status oais_logsumexp_noalloc(const double* d_a, int64_t n, double* d_out, void* stream)
 {
     using namespace oais::noalloc;
-    if (!d_a || !d_out || n < 1) return OAIS_EINVAL;
-    if (n > kMaxN) return OAIS_EINVAL;   // more inputs than the fixed scratch array covers
+    auto fail = [](oais_status st, const char* m) { return (oais_status)oais::fail_call(st, m); };
+    if (!d_a || !d_out || n < 1) return fail(OAIS_EINVAL, "oais_logsumexp_noalloc: null pointer or n < 1");
+    if (n > kMaxN)   // more inputs than the fixed scratch array covers; nothing is launched
+        return fail(OAIS_EINVAL, "oais_logsumexp_noalloc: n above OAIS_LOGSUMEXP_NOALLOC_MAX_N");
+    // an error left pending by an earlier, unrelated call is not this call's: clear it, so
+    // that the checks after the launches below report only what they did
+    (void)cudaGetLastError();
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return OAIS_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(OAIS_ECUDA, "oais_logsumexp_noalloc: no usable current device");
     Record* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
         if (!g_addr[dev]) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_lse) != cudaSuccess || !p) return OAIS_ECUDA;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_lse);
+            if (e != cudaSuccess || !p) return fail(OAIS_ECUDA, cudaGetErrorString(e));
             g_addr[dev] = static_cast<Record*>(p);
         }
         scratch = g_addr[dev];
@@ -132,6 +147,10 @@ extern "C" oais_status oais_logsumexp_noalloc(const double* d_a, int64_t n, doub
     const int nrec = (int)((n + kNoAllocChunk - 1) / kNoAllocChunk);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     lse_chunk_kernel<<<nrec, kThreads, 0, s>>>(d_a, n, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(OAIS_ECUDA, cudaGetErrorString(e));
     lse_records_kernel<<<1, kThreads, 0, s>>>(scratch, nrec, d_out);
-    return cudaGetLastError() == cudaSuccess ? OAIS_OK : OAIS_ECUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(OAIS_ECUDA, cudaGetErrorString(e));
+    return OAIS_OK;
 }

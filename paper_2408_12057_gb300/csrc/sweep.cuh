@@ -40,6 +40,11 @@ struct SweepParams {
     double* ell_out;      // [N]
     StepPartial* partials;// [T][gridDim.x]
     unsigned* status;     // bit 0: non-finite value seen
+    // test support (oais_arm_fault): with withhold != 0 the persistent tensor-core schedules
+    // raise no hand-off flag, and a resumed tile waits for its flag at most handoff_wait_ns
+    // (0: the default limit of every bounded wait)
+    int withhold;
+    uint64_t handoff_wait_ns;
 };
 
 template <typename R> __device__ __forceinline__ R rsq(R a) { return a * a; }

@@ -637,8 +637,9 @@ oais_sweep_tc_kernel(const TcParams P)
             // the tile's first part ran at the start of the next slot: wait for its state
             if (G.gt == 0 && !G.dead) {
                 const uint64_t w0 = globaltimer();
+                const uint64_t limit = S.handoff_wait_ns ? S.handoff_wait_ns : kWaitLimitNs;
                 while (ld_acquire_gpu(P.handed + tile) == 0) {
-                    if (*G.abort || globaltimer() - w0 > kWaitLimitNs) { G.dead = true; *G.abort = 1; break; }
+                    if (*G.abort || globaltimer() - w0 > limit) { G.dead = true; *G.abort = 1; break; }
                     __nanosleep(256);
                 }
             }
@@ -743,7 +744,7 @@ oais_sweep_tc_kernel(const TcParams P)
         }
         if (t1 < T) __threadfence();
         group_sync(G.g);                      // pieces slots free; the state is stored
-        if (t1 < T && G.gt == 0) st_release_gpu(P.handed + tile, 1);
+        if (t1 < T && G.gt == 0 && !S.withhold) st_release_gpu(P.handed + tile, 1);
     }
     // no more evaluations: release the MMA warp
     if (G.gt == 0) desc->stop = 1;

@@ -940,8 +940,9 @@ oais_sweep_tcs_kernel(const Params P)
                 sP.resume = t0 > 1 ? 1 : 0;
                 if (t0 > 1) {
                     const uint64_t w0 = globaltimer();
+                    const uint64_t limit = P.sp.handoff_wait_ns ? P.sp.handoff_wait_ns : kWaitLimitNs;
                     while (ld_acquire_gpu(P.handed + tile) == 0) {
-                        if (globaltimer() - w0 > kWaitLimitNs) {
+                        if (globaltimer() - w0 > limit) {
                             M->abort = 1;
                             atomicOr(P.sp.status, 2u);
                             break;
@@ -961,7 +962,7 @@ oais_sweep_tcs_kernel(const Params P)
             __syncthreads();
             tc_after_sync();
             if (M->abort) break;
-            if (t1 < T && threadIdx.x == 0) {
+            if (t1 < T && threadIdx.x == 0 && !P.sp.withhold) {
                 __threadfence();
                 st_release_gpu(P.handed + tile, 1);
             }

@@ -105,10 +105,14 @@ zja_anchor_kernel(const ZjaState* zs, const double2* __restrict__ anchor, int nb
 
 // per CTA and candidate: (max, sum exp(e - max)) of e = f + k delta g: k = 0 (S0); the weight
 // inside the support (S_alive: e = f where g is finite); k = 1, 2 at each candidate
-// candidate j (1..32) of a pass: geometric in pass 0, equally spaced after
-__device__ __forceinline__ float zja_candidate(int pass, float lo, float hi, int j)
+// Candidate j (1..32) of a pass, defined in fp64 arithmetic with every operation rounded to
+// nearest (no contraction), so that the grid is one set of values whatever evaluates CESS on
+// it: geometric in pass 0, hi 4^-(32 - j) (an exact power-of-two scaling), equally spaced
+// after, lo + ((hi - lo) j) / 32.
+__device__ __forceinline__ double zja_candidate(int pass, double lo, double hi, int j)
 {
-    return pass == 0 ? hi * exp2f(-2.0f * (float)(kZjaCand - j)) : lo + (hi - lo) * (float)j / (float)kZjaCand;
+    if (pass == 0) return ldexp(hi, -2 * (kZjaCand - j));
+    return __dadd_rn(lo, __dmul_rn(__dmul_rn(__dsub_rn(hi, lo), (double)j), 1.0 / kZjaCand));
 }
 
 __global__ void __launch_bounds__(kZjaThreads)
@@ -116,14 +120,18 @@ zja_pass_kernel(const ZjaState* zs, int pass, int64_t N, const float2* __restric
 {
     if (zs->done) return;
     __shared__ float wmax[kZjaThreads / 32][kZjaSums], wsum[kZjaThreads / 32][kZjaSums];
+    __shared__ float cand[kZjaCand + 1];
     const int64_t n = (int64_t)blockIdx.x * kZjaThreads + threadIdx.x;
     const float2 v = n < N ? fg[n] : make_float2(-INFINITY, 0.0f);
-    const float lo = (float)zs->lo, hi = (float)zs->hi;
+    // the pass's candidates (fp64 grid), rounded once to the fp32 of the per-particle sums
+    if (threadIdx.x <= kZjaCand)
+        cand[threadIdx.x] = threadIdx.x == 0 ? 0.0f : (float)zja_candidate(pass, zs->lo, zs->hi, threadIdx.x);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c = 0; c < kZjaSums; ++c) {
         const int j = c < 2 ? 0 : (c - 2) % kZjaCand + 1;      // candidate 1..32 (0: S0, S_alive)
         const float k = c < 2 ? 0.0f : (c < 2 + kZjaCand ? 1.0f : 2.0f);
-        const float delta = j == 0 ? 0.0f : zja_candidate(pass, lo, hi, j);
+        const float delta = cand[j];
         // f + k delta g: a zero weight (f = -inf) or, for c >= 1, a state outside the support
         // (g = -inf) gives -inf; never 0 * inf
         const float e = (v.x == -INFINITY || (c >= 1 && v.y == -INFINITY)) ? -INFINITY
@@ -178,8 +186,8 @@ zja_narrow_kernel(ZjaState* zs, const float2* __restrict__ adiff, const float2* 
     for (int c = warp; c < kZjaSums; c += kZjaNarrowThreads / 32) {
         const int j = c < 2 ? 0 : (c - 2) % kZjaCand + 1;
         const float k = c < 2 ? 0.0f : (c < 2 + kZjaCand ? 1.0f : 2.0f);
-        // the same fp32 candidate the pass kernel used
-        const float delta = j == 0 ? 0.0f : zja_candidate(pass, (float)lo, (float)hi, j);
+        // the candidate as the pass kernel's sums used it
+        const float delta = j == 0 ? 0.0f : (float)zja_candidate(pass, lo, hi, j);
         float M = -INFINITY;
         for (int b = lane; b < nblk; b += 32) {
             const float2 q = part[(size_t)b * kZjaSums + c];
@@ -210,7 +218,7 @@ zja_narrow_kernel(ZjaState* zs, const float2* __restrict__ adiff, const float2* 
         const double lr = 2.0 * (double)logS[1 + j] - (double)logS[0] - (double)logS[1 + kZjaCand + j];
         if (lr >= lt) best = j;
     }
-    auto cand = [&](int j) { return (double)zja_candidate(pass, (float)lo, (float)hi, j); };
+    auto cand = [&](int j) { return zja_candidate(pass, lo, hi, j); };
     bool fix = false;
     double delta = 0.0, nlo = lo, nhi = hi;
     if (best == kZjaCand) {            // the whole remaining interval meets the target

@@ -8,7 +8,6 @@ cannot be built or loaded, the calls raise.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 import threading
 
@@ -20,6 +19,7 @@ GAUSS, LOGREG, GMM, LINREG, UNID = 0, 1, 2, 3, 4
 RWMH, MALA, HMC = 0, 1, 2
 DT_F64, DT_F32 = 0, 1
 CONTRACT_FP32, CONTRACT_BF16_TC, CONTRACT_BF16_TC_STREAM, CONTRACT_FP8_TC_STREAM = 0, 1, 2, 3
+FAULT_NONE, FAULT_NAN_DATA, FAULT_WITHHOLD_HANDOFF = 0, 1, 2
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "non-finite value", 5: "device wait timed out", 6: "unsupported configuration"}
@@ -106,6 +106,9 @@ def lib():
                 "oais_set_problem": ([P, i32], i32),
                 "oais_budget": ([i64, i32, i64, i32, P, P], i32),
                 "oais_set_particles": ([P, i64], i32),
+                "oais_merge_shard_stats": ([i32, i32, P, P, P, P, P, P], i32),
+                "oais_default_step_sizes": ([P, i32, P, i32, P], i32),
+                "oais_arm_fault": ([P, i32, f64], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -146,28 +149,29 @@ def optimise_schedule(beta, log_ghat, T_next):
     return bn, D, L
 
 
+def _host_target(problem, contraction=CONTRACT_FP32):
+    """(_Target, keep-alive arrays) describing a workloads.Problem with host data."""
+    kind = problem.kind
+    dtype = DT_F64 if kind in (GAUSS, UNID) else DT_F32
+    npdt = np.float64 if dtype == DT_F64 else np.float32
+    X = np.ascontiguousarray(problem.X, dtype=npdt)
+    y = None if problem.y is None else np.ascontiguousarray(problem.y, dtype=npdt)
+    tg = _Target(kind, problem.d, problem.n, dtype, X.ctypes.data, None if y is None else y.ctypes.data,
+                 problem.ref_scale, problem.p0, 0, int(contraction))
+    return tg, (X, y)
+
+
 def default_step_sizes(problem, beta, move_kind):
-    """A starting rule for the per-step sizes: the reference scale shrunk by the tempered
-    curvature of the likelihood (a rough diagonal estimate) and by d^(1/6) (MALA) or d^(1/4) (HMC)."""
-    beta = np.asarray(beta, dtype=np.float64)[1:]
-    d = problem.d
-    if problem.kind == GAUSS:
-        curv = 1.0 / problem.p0 ** 2
-    elif problem.kind == LOGREG:
-        curv = 0.25 * float((np.asarray(problem.X, dtype=np.float64) ** 2).sum()) / d
-    elif problem.kind == LINREG:
-        curv = float((np.asarray(problem.X, dtype=np.float64) ** 2).sum()) / d / problem.p0 ** 2
-    elif problem.kind == UNID:
-        # the ridge p = const is ~ sqrt(q (1 - q) / m) wide in p; in z that is about the
-        # ridge width over (dp / dz ~ p)
-        m, k = float(problem.X[0]), float(problem.X[1])
-        q = k / m
-        curv = m / (q * (1.0 - q)) * q * q
-    else:
-        curv = 1.0 / problem.p0
-    scale = 1.0 / np.sqrt(1.0 / problem.ref_scale ** 2 + beta * curv)
-    c = {RWMH: 2.38 / math.sqrt(d), MALA: 1.2 * d ** (-1.0 / 6.0), HMC: 1.0 * d ** (-0.25)}[move_kind]
-    return c * scale
+    """The library's starting rule for per-step sizes (oais_default_step_sizes): the reference
+    scale shrunk by the tempered curvature of the likelihood and by the kernel's dimension
+    scaling; returns eps [T] for the schedule beta [T+1]."""
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    T = beta.size - 1
+    tg, keep = _host_target(problem)
+    eps = np.zeros(T)
+    _check(lib().oais_default_step_sizes(ctypes.byref(tg), int(move_kind), _np_ptr(beta), T, _np_ptr(eps)))
+    del keep
+    return eps
 
 
 class OAIS:
@@ -223,6 +227,12 @@ class OAIS:
         """Active particle count of the next rounds (at most the count the run was created with)."""
         _check(lib().oais_set_particles(self._ctx, int(N)), self._ctx)
         self.N = int(N)
+
+    def arm_fault(self, kind, wait_seconds=0.0):
+        """Test support: arm a host-side fault for the next round (oais_arm_fault):
+        FAULT_NAN_DATA (the round returns a non-finite error) or FAULT_WITHHOLD_HANDOFF (a
+        persistent tensor-core sweep's bounded hand-off waits give up after wait_seconds)."""
+        _check(lib().oais_arm_fault(self._ctx, int(kind), float(wait_seconds)), self._ctx)
 
     def set_problem(self, p):
         """Problem index p in the random-number tag (round | p << 16), as problem p of a batch."""
@@ -391,12 +401,17 @@ def measure_unit_rate(unit):
 
 
 def merge_shard_stats(parts):
-    """Merge per-shard round statistics: the moments and the final weight sums are sums over
-    particles, so their logarithms combine by log-sum-exp; acceptance counts add."""
-    lg = np.logaddexp.reduce(np.stack([p["log_ghat"] for p in parts]), axis=0)
-    lse = np.logaddexp.reduce(np.stack([p["lse"] for p in parts]), axis=0)
-    acc = np.sum(np.stack([p["accepted"] for p in parts]), axis=0)
-    return {"log_ghat": lg, "accepted": acc, "lse": lse}
+    """Merge per-shard round statistics in rank order (oais_merge_shard_stats): the moments and
+    the final weight sums combine by log-sum-exp over shards, acceptance counts add."""
+    P = len(parts)
+    T = int(np.asarray(parts[0]["log_ghat"]).shape[0])
+    lg = np.ascontiguousarray(np.stack([p["log_ghat"] for p in parts]), dtype=np.float64)
+    acc = np.ascontiguousarray(np.stack([p["accepted"] for p in parts]), dtype=np.float64)
+    lse = np.ascontiguousarray(np.stack([p["lse"] for p in parts]), dtype=np.float64)
+    lg_o, acc_o, lse_o = np.zeros((T, 3)), np.zeros(T), np.zeros(2)
+    _check(lib().oais_merge_shard_stats(P, T, _np_ptr(lg), _np_ptr(acc), _np_ptr(lse), _np_ptr(lg_o),
+                                        _np_ptr(acc_o), _np_ptr(lse_o)))
+    return {"log_ghat": lg_o, "accepted": acc_o, "lse": lse_o}
 
 
 def exchange_stats(local, group=None, device=None):

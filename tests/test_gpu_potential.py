@@ -88,11 +88,12 @@ def test_fisher_gradient_linreg_closed_form():
     beta = W.linear_schedule(200) ** 4
     eps = oais.default_step_sizes(pr, beta, oais.HMC) * 0.6
     gs = []
-    for rep in range(4):
-        run = oais.OAIS(pr, oais.HMC, 1 << 14, beta, eps=eps, seed=40 + rep, leapfrog=5)
+    for rep in range(8):
+        run = oais.OAIS(pr, oais.HMC, 1 << 15, beta, eps=eps, seed=40 + rep, leapfrog=5)
         run.round(200)
         gs.append(run.grad_logZ())
         run.close()
     gs = np.array(gs)
     se = gs.std(axis=0, ddof=1) / np.sqrt(len(gs))
-    assert np.all(np.abs(gs.mean(0) - closed) < 4 * se + 0.02 * np.abs(closed) + 0.05)
+    # within 3 standard errors of the mean over eight seeds
+    assert np.all(np.abs(gs.mean(0) - closed) < 3 * se), (gs.mean(0), closed, se)

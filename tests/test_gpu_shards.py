@@ -56,9 +56,28 @@ def test_checkpoint_resume_is_bit_identical():
     blob = a.save_state()
     z_a = [a.round(64)["logZ"], a.round(64)["logZ"]]
     b = oais.OAIS(pr, oais.MALA, 1000, W.linear_schedule(3), T_max=64, seed=99, adapt=True)
+    b.round(3)
     b.load_state(blob)
+    with pytest.raises(oais.OAISError):
+        b.logZ()                   # the round run before the load belongs to another state
     z_b = [b.round(64)["logZ"], b.round(64)["logZ"]]
     assert z_a == z_b
+    # a blob is checked like the setters' arguments: a zero step size or a shard block past
+    # the counter space is rejected and leaves the context as it was
+    T = 32
+    hdr = len(blob) - 8 * (2 * T + 1)
+    eps_at = hdr + 8 * (T + 1)
+    bad = bytearray(blob)
+    bad[eps_at:eps_at + 8] = np.float64(0.0).tobytes()
+    before = b.schedule()
+    with pytest.raises(oais.OAISError):
+        b.load_state(bytes(bad))
+    after = b.schedule()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    bad = bytearray(blob)
+    bad[16:24] = np.int64(1 << 33).tobytes()           # N_total beyond 2^32
+    with pytest.raises(oais.OAISError):
+        b.load_state(bytes(bad))
     wrong = oais.OAIS(pr, oais.MALA, 999, beta, T_max=64)
     with pytest.raises(oais.OAISError):
         wrong.load_state(blob)
