@@ -158,7 +158,11 @@ oais_status oais_init(oais_ctx** ctx, const oais_target* target, const oais_move
 
 /* One round of OAIS (Alg. 2 body): run the loop-swapped sweep with the current schedule,
  * merge the per-step moments, form log Z_hat, then install
- * OptimiseSchedule(T_next, B_T, g_hat) (Alg. 3) as the schedule of the next round.
+ * OptimiseSchedule(T_next, B_T, g_hat) (Alg. 3) as the schedule of the next round.  Its step
+ * sizes are carried from the round's: each step size is held as its ratio to the shape
+ * 1 / sqrt(1/s^2 + beta kappa) of the starting rule (oais_default_step_sizes), the logarithm of
+ * that ratio interpolated linearly in beta (constant beyond the round's first and last steps),
+ * and with move.adapt each step nudged toward the move's target acceptance.
  * T_next <= T_max.  Synchronises the context's stream.  On error the previous round's
  * results and the current schedule are left unchanged (anytime property, Sec. 1) and the round
  * counter does not advance; the particle buffers of oais_particles then hold the failed

@@ -109,6 +109,24 @@ static void optimise_schedule(int T, const double* beta, const double* lg, int T
     out[Tn] = 1.0;
 }
 
+// Diagonal curvature estimate kappa of -log L (per unit beta) behind the starting step-size rule
+// and the carry-over of step sizes between rounds: the Gaussian 1 / p0^2; logistic
+// sum X^2 / (4 d) (the sigmoid's largest slope); linear regression sum X^2 / (d p0^2); mixture
+// 1 / p0 (a component's precision); Unid m q (1 - q)^-1 q^2, q = k / m (the binomial ridge's
+// width in the probit coordinates).  Xh: the data as doubles (rows of X, or (m, k) for Unid).
+static double curvature(int kind, int d, double p0, const std::vector<double>& Xh)
+{
+    if (kind == kGauss) return 1.0 / (p0 * p0);
+    if (kind == kGmm) return 1.0 / p0;
+    if (kind == kUnid) {
+        const double q = Xh[1] / Xh[0];
+        return Xh[0] / (q * (1.0 - q)) * q * q;
+    }
+    double ss = 0.0;
+    for (double v : Xh) ss += v * v;
+    return kind == kLogreg ? 0.25 * ss / d : ss / d / (p0 * p0);
+}
+
 static bool valid_schedule(const double* beta, int T)
 {
     if (T < 1 || !beta || beta[0] != 0.0 || beta[T] != 1.0) return false;
@@ -172,6 +190,7 @@ struct oais_ctx {
     std::vector<double> beta, eps;
     int round = 0;
     int problem = 0;                     // problem index in the random-number tag
+    double kappa = 0.0;                  // curvature estimate of -log L (step-size carry-over)
     // test support (oais_arm_fault): a fault armed for the next round
     int fault_kind = 0;
     uint64_t fault_wait_ns = 0;
@@ -482,6 +501,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     st = fetch(ctx, tg->X, (size_t)rows * tg->d, tg->dtype, tg->on_device, Xh);
     if (st == OAIS_OK && dt.y) st = fetch(ctx, tg->y, (size_t)tg->n, tg->dtype, tg->on_device, yh);
     if (st != OAIS_OK) { g_err = ctx->err; oais_destroy(ctx); return st; }
+    ctx->kappa = curvature(tg->kind, tg->d, tg->p0, Xh);
     cudaError_t e = cudaSuccess;
     if (tg->kind == kGauss) {
         std::vector<double> mu(D, 0.0);
@@ -629,8 +649,14 @@ oais_status oais_logsumexp(const double* d_a, int64_t n, double* d_out, void* d_
     return OAIS_OK;
 }
 
-// carry step sizes to a new schedule: linear interpolation of log eps in beta, and, when
-// adapting, a multiplicative nudge toward the target acceptance of the move
+// Carry step sizes to a new schedule (reading r9).  A step size is held as its ratio to the
+// shape of the starting rule, h(beta) = 1 / sqrt(1/s^2 + beta kappa) (the scale of pi_beta under
+// a Gaussian approximation of the likelihood's curvature): log(eps / h) is interpolated linearly
+// in beta between the old steps and held constant beyond them, and the new step size is that
+// ratio times h at the new beta.  A new schedule that puts steps at betas far below the old first
+// step (the optimised schedule of a steep start) so gets steps that widen with the flatter
+// tempered targets there, instead of the old first step's size.  When adapting, a
+// multiplicative nudge moves each step toward the move's target acceptance.
 static std::vector<double> next_step_sizes(const oais_ctx* ctx, const std::vector<double>& beta_old,
                                            const std::vector<double>& eps_old,
                                            const std::vector<double>& acc, const std::vector<double>& beta_new)
@@ -638,18 +664,21 @@ static std::vector<double> next_step_sizes(const oais_ctx* ctx, const std::vecto
     const int T = (int)eps_old.size(), Tn = (int)beta_new.size() - 1;
     std::vector<double> out(Tn);
     const double target = ctx->mv.kind == OAIS_RWMH ? 0.3 : (ctx->mv.kind == OAIS_MALA ? 0.574 : 0.7);
+    const double inv_s2 = 1.0 / (ctx->dt.ref_scale * ctx->dt.ref_scale);
+    auto log_h = [&](double b) { return -0.5 * std::log(inv_s2 + b * ctx->kappa); };
     for (int i = 1; i <= Tn; ++i) {
         const double b = beta_new[i];
         // locate b among beta_old[1..T]
         int j = (int)(std::lower_bound(beta_old.begin() + 1, beta_old.end(), b) - beta_old.begin());
         j = std::max(1, std::min(j, T));
-        double le, a;
-        if (j == 1 || T == 1) { le = std::log(eps_old[0]); a = acc[0]; }
+        double lr, a;
+        if (j == 1 || T == 1) { lr = std::log(eps_old[0]) - log_h(beta_old[1]); a = acc[0]; }
         else {
             const double b0 = beta_old[j - 1], b1 = beta_old[j], w = (b - b0) / (b1 - b0);
-            le = (1 - w) * std::log(eps_old[j - 2]) + w * std::log(eps_old[j - 1]);
+            lr = (1 - w) * (std::log(eps_old[j - 2]) - log_h(b0)) + w * (std::log(eps_old[j - 1]) - log_h(b1));
             a = (1 - w) * acc[j - 2] + w * acc[j - 1];
         }
+        double le = lr + log_h(b);
         if (ctx->mv.adapt && !(ctx->mv.kind == OAIS_RWMH && ctx->mv.cycle))
             le += std::max(-0.7, std::min(0.7, 1.5 * (a - target)));
         out[i - 1] = std::exp(le);
@@ -1677,30 +1706,20 @@ oais_status oais_default_step_sizes(const oais_target* tg, int32_t move_kind, co
     if (tg->d < 1 || !tg->X || !(tg->ref_scale > 0) || !(tg->p0 > 0))
         return fail(nullptr, OAIS_EINVAL, "bad target");
     if (tg->dtype != OAIS_DT_F64 && tg->dtype != OAIS_DT_F32) return fail(nullptr, OAIS_EINVAL, "bad dtype");
-    const double d = (double)tg->d, p0 = tg->p0;
-    double curv;
-    if (tg->kind == kGauss) {
-        curv = 1.0 / (p0 * p0);
-    } else if (tg->kind == kLogreg || tg->kind == kLinreg) {
+    const double d = (double)tg->d;
+    if (tg->kind < kGauss || tg->kind > kUnid) return fail(nullptr, OAIS_EINVAL, "unknown target kind");
+    std::vector<double> Xh;
+    if (tg->kind == kLogreg || tg->kind == kLinreg) {
         if (tg->n < 1) return fail(nullptr, OAIS_EINVAL, "n must be >= 1");
-        std::vector<double> Xh;
         oais_status st = fetch(nullptr, tg->X, (size_t)tg->n * tg->d, tg->dtype, tg->on_device, Xh);
         if (st != OAIS_OK) return st;
-        double ss = 0.0;
-        for (double v : Xh) ss += v * v;
-        curv = tg->kind == kLogreg ? 0.25 * ss / d : ss / d / (p0 * p0);
     } else if (tg->kind == kUnid) {
-        std::vector<double> mk;
-        oais_status st = fetch(nullptr, tg->X, 2, OAIS_DT_F64, tg->on_device, mk);
+        oais_status st = fetch(nullptr, tg->X, 2, OAIS_DT_F64, tg->on_device, Xh);
         if (st != OAIS_OK) return st;
-        const double q = mk[1] / mk[0];
+        const double q = Xh[1] / Xh[0];
         if (!(q > 0.0 && q < 1.0)) return fail(nullptr, OAIS_EINVAL, "UNID: successes 0 < k < m");
-        curv = mk[0] / (q * (1.0 - q)) * q * q;
-    } else if (tg->kind == kGmm) {
-        curv = 1.0 / p0;
-    } else {
-        return fail(nullptr, OAIS_EINVAL, "unknown target kind");
     }
+    const double curv = curvature(tg->kind, tg->d, tg->p0, Xh);
     const double c = move_kind == OAIS_RWMH ? 2.38 / std::sqrt(d)
                    : move_kind == OAIS_MALA ? 1.2 * std::pow(d, -1.0 / 6.0) : std::pow(d, -0.25);
     const double s2 = tg->ref_scale * tg->ref_scale;
