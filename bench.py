@@ -88,6 +88,27 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+UNIT_EX2, UNIT_RCP, UNIT_LG2, UNIT_FFMA, UNIT_LOP3 = 0, 1, 2, 3, 4
+_unitrate = None
+
+
+def measure_unit_rate(unit):
+    """Measured lane-operations per second per SM of one instruction kind on this GPU
+    (bench_unitrate.cu, a measurement helper built beside the library)."""
+    global _unitrate
+    import ctypes
+    if _unitrate is None:
+        from paper_2408_12057_gb300 import _build
+        _unitrate = ctypes.CDLL(_build.build_unitrate())
+        _unitrate.unitrate_measure.argtypes = [ctypes.c_int, ctypes.c_void_p]
+        _unitrate.unitrate_measure.restype = ctypes.c_int
+    r = ctypes.c_double()
+    st = _unitrate.unitrate_measure(int(unit), ctypes.byref(r))
+    if st != 0:
+        raise RuntimeError(f"unit-rate probe failed ({st})")
+    return r.value
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -344,9 +365,9 @@ def main():
     sweep_s = sum(sweep_ms) / 1e3
     # rates (lane-operations per second per SM) of the units that bound the two forms,
     # measured on this GPU right after the timed region
-    rates = {name: oais.measure_unit_rate(u) for name, u in
-             [("ex2", oais.UNIT_EX2), ("rcp", oais.UNIT_RCP), ("lg2", oais.UNIT_LG2),
-              ("ffma", oais.UNIT_FFMA)]}
+    rates = {name: measure_unit_rate(u) for name, u in
+             [("ex2", UNIT_EX2), ("rcp", UNIT_RCP), ("lg2", UNIT_LG2),
+              ("ffma", UNIT_FFMA)]}
     if args.contraction == "fp32":
         # FP32 form: the FMA pipe bounds it (4 n d FLOP per particle-step)
         fp32_peak = 2.0 * rates["ffma"] * N_SM / 1e12                          # TFLOP/s
@@ -354,7 +375,7 @@ def main():
         roofline = {"bound": "alu", "pipe": "fp32 fma", "achieved": achieved, "peak": fp32_peak,
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                     "peak_source": f"measured FFMA rate {rates['ffma'] / 1e9:.1f} G lane-ops/s/SM x 2 x "
-                                   f"152 SMs (oais_measure_unit_rate)",
+                                   f"152 SMs (bench_unitrate.cu)",
                     "kernel": "oais_sweep_kernel<RowsTarget<32,logistic>, MALA>"}
     else:
         # tensor-core form: the contractions run on tcgen05 (a small share of their peak); the
@@ -372,7 +393,7 @@ def main():
                     "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
                     "peak_source": f"measured ex2/rcp/lg2 rates {rates['ex2'] / 1e9:.1f}/"
                                    f"{rates['rcp'] / 1e9:.1f}/{rates['lg2'] / 1e9:.1f} G lane-ops/s/SM x "
-                                   f"152 SMs (oais_measure_unit_rate)",
+                                   f"152 SMs (bench_unitrate.cu)",
                     "kernel": ("oais_sweep_tc_kernel (tcgen05 bf16, X resident, MALA)" if args.contraction == "bf16_tc"
                                else "oais_sweep_tcs_kernel<LOGREG, 32> (tcgen05 f16, X streamed, MALA)"),
                     "tensor_tflops_issued": 2 * algorithmic_flops_per_particle_step(pr) * 2048 / pr.n
@@ -621,8 +642,8 @@ def line_batched(args, steps, warmup, compare_sequential):
     rows = sum(pr.n for pr in probs)
     ps = len(probs) * N * T * R
     sweep_s = sum(r[0]["sweep_ms"] for r in last) / 1e3   # the sweeps of one job (the last one)
-    rates = {name: oais.measure_unit_rate(u) for name, u in
-             [("ex2", oais.UNIT_EX2), ("rcp", oais.UNIT_RCP), ("lg2", oais.UNIT_LG2)]}
+    rates = {name: measure_unit_rate(u) for name, u in
+             [("ex2", UNIT_EX2), ("rcp", UNIT_RCP), ("lg2", UNIT_LG2)]}
     peaks, src = measured_peaks()
     tpeak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1e12
     # per problem the binding unit: special-function work (1 ex2 + 1 rcp per row and
@@ -644,7 +665,7 @@ def line_batched(args, steps, warmup, compare_sequential):
                    "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": {"bound": "sfu or tensor per problem", "achieved_s": sweep_s,
                      "bound_s": t_bound, "frac": t_bound / sweep_s, "traffic": None,
-                     "peak_source": f"measured unit rates (oais_measure_unit_rate) and {src} bf16 sustained",
+                     "peak_source": f"measured unit rates (bench_unitrate.cu) and {src} bf16 sustained",
                      "kernel": "oais_sweep_tcs_batch_kernel<LOGREG>"},
         "gpu_launches": (1 + 2 * len(probs)) * R * steps, "clocks": clk,
     }
@@ -750,7 +771,7 @@ def line_gmm(args, steps, warmup):
     t_smc, last_smc, clk_smc = timed_job(lambda: job(True), k_smc, 1, stream, ClockSampler(0))
     se_smc = last_smc[-1]["se"]
     ps = N * sum(rounds)
-    rates = {name: oais.measure_unit_rate(u) for name, u in [("ffma", oais.UNIT_FFMA), ("ex2", oais.UNIT_EX2)]}
+    rates = {name: measure_unit_rate(u) for name, u in [("ffma", UNIT_FFMA), ("ex2", UNIT_EX2)]}
     ops = gmm_ops_per_particle_step(pr.d, pr.X.shape[0], moves=2)
     sweep_s = sum(r["sweep_ms"] for r in last_ais) / 1e3
     achieved = ops["total"] * ps / sweep_s / 1e12
@@ -776,7 +797,7 @@ def line_gmm(args, steps, warmup):
                              "x particle-steps / sweep time; the kernel executes about 2.3x that many",
                      "achieved": achieved, "peak": peak, "unit": "T lane-instructions/s", "frac": achieved / peak,
                      "traffic": None, "ops_per_particle_step": ops,
-                     "peak_source": "measured FFMA lane-op rate (oais_measure_unit_rate) x 152 SMs = one "
+                     "peak_source": "measured FFMA lane-op rate (bench_unitrate.cu) x 152 SMs = one "
                                     "instruction per lane per cycle",
                      "kernel": "oais_sweep_kernel<GmmTarget<float,16>, RWMH>"},
         "gpu_launches": 3 * len(rounds) * steps, "clocks": clk,

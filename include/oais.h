@@ -361,15 +361,6 @@ size_t oais_logsumexp_scratch_bytes(int64_t n);
 oais_status oais_logsumexp(const double* d_a, int64_t n, double* d_out, void* d_scratch,
                            void* stream);
 
-/* Measurement utility (no counterpart in the paper): the sustained rate of one instruction
- * kind on the current GPU, in lane-operations per second per SM, from a probe kernel with one
- * CTA of 32 warps per SM and 8 independent chains per thread, timed with the global
- * nanosecond timer.  The benchmark uses it as the measured peak of the unit that bounds each
- * sweep form.  Allocates and frees a small scratch buffer; synchronises the device. */
-typedef enum { OAIS_UNIT_EX2 = 0, OAIS_UNIT_RCP = 1, OAIS_UNIT_LG2 = 2, OAIS_UNIT_FFMA = 3,
-               OAIS_UNIT_LOP3 = 4 } oais_unit;
-oais_status oais_measure_unit_rate(int32_t unit, double* lane_ops_per_s_per_sm);
-
 /* ---------------------------------------------------------------------------------
  * Allocation-free log-sum-exp.  No counterpart in the paper: this is a service for
  * callers that cannot call cudaMalloc or take scratch memory from elsewhere -- code

@@ -1,4 +1,6 @@
-"""Build liboais.so in-tree with nvcc for sm_103a (one -gencode, translation units in parallel)."""
+"""Build liboais.so in-tree with nvcc for sm_103a (one -gencode, translation units in parallel),
+and the benchmark's measurement helper libbench_unitrate.so (bench_unitrate.cu beside bench.py;
+not part of the library)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -73,5 +75,30 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+ROOT = os.path.dirname(HERE)
+UNITRATE_SRC = os.path.join(ROOT, "bench_unitrate.cu")
+UNITRATE_LIB = os.path.join(ROOT, "libbench_unitrate.so")
+
+
+def build_unitrate(force: bool = False) -> str:
+    """Compile the benchmark's unit-rate probe into its own library (bench.py loads it)."""
+    stamp = UNITRATE_LIB + ".sha"
+    h = hashlib.sha256(open(UNITRATE_SRC, "rb").read() + " ".join(ARCH).encode() + os.uname().machine.encode())
+    dig = h.hexdigest()
+    if not force and os.path.exists(UNITRATE_LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
+        return UNITRATE_LIB
+    tmp = UNITRATE_LIB + ".tmp"
+    cmd = [_nvcc()] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                              "-o", tmp, UNITRATE_SRC, "-cudart", "static"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on bench_unitrate.cu:\n{r.stderr}")
+    os.replace(tmp, UNITRATE_LIB)
+    with open(stamp, "w") as f:
+        f.write(dig)
+    return UNITRATE_LIB
+
+
 if __name__ == "__main__":
     print(build(verbose=True))
+    print(build_unitrate())

@@ -80,7 +80,6 @@ def lib():
                 "oais_particles": ([P, P, P, P], i32),
                 "oais_grad_logZ": ([P, P], i32),
                 "oais_set_shard": ([P, i64, i64], i32),
-                "oais_measure_unit_rate": ([i32, P], i32),
                 "oais_state_bytes": ([P, P], i32),
                 "oais_save_state": ([P, P, sz], i32),
                 "oais_load_state": ([P, P, sz], i32),
@@ -388,16 +387,6 @@ class OAIS:
         _check(lib().oais_ctx_sweep(self._ctx, T, _dptr(beta_dev), _dptr(eps_dev), int(seed), int(tag),
                                     int(n_offset), int(N), _dptr(logw), _dptr(ell), _dptr(x),
                                     _dptr(partials), _dptr(status), _stream_ptr(stream)), self._ctx)
-
-
-UNIT_EX2, UNIT_RCP, UNIT_LG2, UNIT_FFMA, UNIT_LOP3 = 0, 1, 2, 3, 4
-
-
-def measure_unit_rate(unit):
-    """Measured lane-operations per second per SM of one instruction kind on this GPU."""
-    r = ctypes.c_double()
-    _check(lib().oais_measure_unit_rate(int(unit), ctypes.byref(r)))
-    return r.value
 
 
 def merge_shard_stats(parts):
