@@ -60,8 +60,8 @@ typedef enum { OAIS_DT_F64 = 0, OAIS_DT_F32 = 1 } oais_dtype;
 
 typedef struct {
     int32_t kind;       /* oais_target_kind */
-    int32_t d;          /* state dimension, 1 <= d <= 32 (GAUSS: <= 16); the streamed
-                           tensor-core form takes LOGREG and LINREG up to d = 256 */
+    int32_t d;          /* state dimension, 1 <= d <= 32 (GAUSS: <= 16); LOGREG and LINREG up to
+                           d = 256 (the tiled fp32 form and the streamed tensor-core form) */
     int32_t n;          /* rows of X (LOGREG, LINREG), mixture components (GMM, <= 16); 0 for GAUSS, UNID */
     int32_t dtype;      /* oais_dtype of X and y: GAUSS and UNID run in F64 and take F64 X;
                            the other families run in F32 and take F32 or F64 input */
@@ -73,7 +73,13 @@ typedef struct {
     int32_t on_device;  /* 0: X, y are host memory, copied at init.  1: device memory, also copied
                            (to the padded device layout); the caller may free them after init */
     int32_t contraction;/* how X x is computed (oais_contraction):
-                           OAIS_CONTRACT_FP32: CUDA cores, fp32 data.
+                           OAIS_CONTRACT_FP32: CUDA cores, fp32 data.  Up to d = 32 one thread
+                             per particle keeps the particle in registers for the whole sweep;
+                             LOGREG and LINREG with 32 < d <= 256 run the tiled fp32 form: a CTA
+                             per tile of 64 particles evaluates log L and its gradient as two
+                             fp32 contractions over X streamed through shared memory, with the
+                             particle vectors in device memory (OAIS rounds, the shard calls and
+                             oais_potential; not oasmc_round, oais_zja_round or oais_ctx_sweep).
                            OAIS_CONTRACT_BF16_TC: tcgen05 tensor cores with X rounded once to
                              bf16 (the sampler targets that X~).  LOGREG with d <= 32,
                              n <= 2048 and MALA runs with X~ resident in shared memory (states
@@ -97,9 +103,10 @@ typedef struct {
                            one launch per step over its stored particle state) and
                            oais_potential, for streamed and resident contexts alike (a resident
                            context keeps the streamed form's image and state for them).
-                           oais_ctx_sweep and oais_zja_round use the CUDA-core form, which exists
-                           for d <= 32 (they return OAIS_EUNSUPPORTED above that).  Other combinations
-                           return OAIS_EUNSUPPORTED at init. */
+                           oais_ctx_sweep and oais_zja_round use the one-thread-per-particle
+                           CUDA-core form, which exists for d <= 32 (they return
+                           OAIS_EUNSUPPORTED above that).  Other combinations return
+                           OAIS_EUNSUPPORTED at init. */
 } oais_target;
 
 typedef enum {

@@ -238,7 +238,7 @@ static size_t elt_bytes(int kind) { return f64_kind(kind) ? sizeof(double) : siz
 struct Layout {
     size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, elbo, lse, lse_scr, status;
     size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, tc_img, tc_y;
-    size_t tcs_img, tcs_state, tc_handed, zja_fg, zja_anchor, zja_part, zja_state, zja_beta, zja_eps, total;
+    size_t tcs_img, tcs_state, tc_handed, zja_fg, zja_anchor, zja_part, zja_state, zja_beta, zja_eps, wide_state, total;
 };
 
 // which sweep form a target runs: 0 CUDA cores, 1 resident tensor-core, 2 streamed tensor-core
@@ -250,7 +250,10 @@ static int sweep_form(const oais_target* tg, const oais_move* mv)
     return 2;
 }
 
-static int records_per_step(int64_t N) { return std::max(std::max(sweep_grid(N), tc_records(N)), tcs_tiles(N)); }
+static int records_per_step(int64_t N)
+{
+    return std::max(std::max(sweep_grid(N), tc_records(N)), std::max(tcs_tiles(N), wide_tiles(N)));
+}
 
 static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t N, int T_max)
 {
@@ -308,6 +311,8 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     if (form >= 1) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
     L.tcs_img = take(form >= 1 ? tp.img_bytes : 0);
     L.tcs_state = take(form >= 1 ? sizeof(float) * 5 * (size_t)tp.dp * tcs_tiles(N) * 128 : 0);
+    // the tiled fp32 form (32 < d <= 256): positions, gradients, momenta of every tile
+    L.wide_state = take(D > 32 ? wide_state_bytes(D, N) : 0);
     L.total = off;
     return L;
 }
@@ -360,6 +365,9 @@ static oais_status check_target(oais_ctx* ctx, const oais_target* tg, const oais
     if (N < 1 || N > 0x7FFFFFFFLL) return fail(ctx, OAIS_EINVAL, "N out of range");
     if (T_max < 1 || T_max > (1 << 24)) return fail(ctx, OAIS_EINVAL, "T_max out of range");
     *D = padded_width(tg->kind, tg->d);
+    // the row families above d = 32 in fp32: the tiled CUDA-core form, width 64, 128 or 256
+    if (*D == 0 && (tg->kind == kLogreg || tg->kind == kLinreg) && tg->contraction == OAIS_CONTRACT_FP32)
+        *D = wide_width(tg->d);
     // the streamed tensor-core form needs no CUDA-core width (D = 0: no CUDA-core copy of X)
     if (*D == 0 && sweep_form(tg, mv) != 2) return fail(ctx, OAIS_EUNSUPPORTED, "dimension not built for this family");
     return OAIS_OK;
@@ -464,6 +472,8 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     dt.ref_scale = tg->ref_scale; dt.p0 = tg->p0;
     dt.X = b + L.X;
     dt.y = (tg->kind == kLogreg || tg->kind == kLinreg) ? b + L.y : nullptr;
+    dt.wide = D > 32;
+    dt.wide_state = dt.wide ? reinterpret_cast<float*>(b + L.wide_state) : nullptr;
     ctx->d_beta = reinterpret_cast<double*>(b + L.beta);
     ctx->d_eps = reinterpret_cast<double*>(b + L.eps);
     ctx->d_logw = reinterpret_cast<double*>(b + L.logw);
@@ -621,7 +631,8 @@ oais_status oais_ctx_sweep(oais_ctx* ctx, int32_t T, const double* d_beta, const
     if (T < 1 || N < 1 || !d_beta || !d_eps || !d_logw || !d_ell || !d_x || !d_partials || !d_status)
         return fail(ctx, OAIS_EINVAL, "bad arguments to oais_ctx_sweep");
     if (n_offset < 0 || n_offset + N > 0xFFFFFFFFLL) return fail(ctx, OAIS_EINVAL, "particle index out of range");
-    if (ctx->dt.D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "no CUDA-core form for this dimension");
+    if (ctx->dt.D == 0 || ctx->dt.wide)
+        return fail(ctx, OAIS_EUNSUPPORTED, "no one-thread-per-particle CUDA-core form for this dimension");
     SweepParams P = make_params(ctx, T, d_beta, d_eps, seed, tag, n_offset, N, d_logw, d_ell, d_x, d_partials,
                                 d_status);
     CK(launch_sweep(ctx->dt, ctx->mv.kind, P, static_cast<cudaStream_t>(stream)));
@@ -753,9 +764,11 @@ static oais_status run_round_impl(oais_ctx* ctx, int32_t T_next, bool asmc, doub
             CK(launch_sweep_tcs(tcs_plan(ctx->dt.kind, ctx->dt.n, ctx->dt.d, 0, 0, ctx->dt.tcs_q8), ctx->dt.kind, P, ctx->dt.tcs_img,
                                 ctx->dt.tcs_state, ctx->mv.kind, ctx->mv.leapfrog, ctx->dt.p0, ctx->dt.n,
                                 ctx->dt.d, s, ctx->dt.tc_handed));
+        else if (ctx->dt.wide) CK(launch_sweep_wide(ctx->dt, ctx->mv.kind, P, s));
         else CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
         CK(cudaEventRecord(ctx->ev1, s));
-        const int records = ctx->dt.tc ? tc_records(ctx->N) : (ctx->dt.tcs ? tcs_tiles(ctx->N) : grid);
+        const int records = ctx->dt.tc ? tc_records(ctx->N)
+                          : (ctx->dt.tcs ? tcs_tiles(ctx->N) : (ctx->dt.wide ? wide_tiles(ctx->N) : grid));
         CK(launch_merge_stats(ctx->d_parts, records, T,
                               1.0 / ((double)ctx->N * ctx->mv.moves), ctx->d_log_ghat, ctx->d_accept, ctx->d_elbo, s));
         CK(launch_logsumexp(ctx->d_logw, ctx->N, ctx->d_lse, ctx->d_lse_scratch, s));
@@ -786,8 +799,9 @@ static oais_status run_round_impl(oais_ctx* ctx, int32_t T_next, bool asmc, doub
         se = std::sqrt(std::max(0.0, 1.0 / ess - 1.0 / (double)ctx->N));
     } else {
         if (ctx->N_total != ctx->N) return fail(ctx, OAIS_EUNSUPPORTED, "ASMC resamples globally: no shards");
-        if (ctx->dt.D == 0 && !ctx->dt.tcs)
-            return fail(ctx, OAIS_EUNSUPPORTED, "resampling rounds need the CUDA-core or the streamed form");
+        if ((ctx->dt.D == 0 || ctx->dt.wide) && !ctx->dt.tcs)
+            return fail(ctx, OAIS_EUNSUPPORTED,
+                        "resampling rounds need the one-thread-per-particle CUDA-core form (d <= 32) or the streamed form");
         CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(AsmcState), s));
         StepParams P = make_step_params(ctx, T, tag);
         const bool grad = ctx->mv.kind != OAIS_RWMH;
@@ -975,7 +989,8 @@ oais_status oais_zja_round(oais_ctx* ctx, double cess_frac, double ess_frac, int
     if (!(ess_frac >= 0.0 && ess_frac <= 1.0 + 1e-12)) return fail(ctx, OAIS_EINVAL, "ess_frac must be in [0, 1]");
     if (T_next < 1 || T_next > ctx->T_max) return fail(ctx, OAIS_EINVAL, "T_next out of range");
     if (ctx->N_total != ctx->N) return fail(ctx, OAIS_EUNSUPPORTED, "the online schedule needs every particle: no shards");
-    if (ctx->dt.D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "online-CESS rounds run on the CUDA-core form");
+    if (ctx->dt.D == 0 || ctx->dt.wide)
+        return fail(ctx, OAIS_EUNSUPPORTED, "online-CESS rounds run on the one-thread-per-particle CUDA-core form");
     cudaStream_t s = ctx->stream;
     const int T_ref = (int)ctx->beta.size() - 1;
     const int T_max = ctx->T_max;
@@ -1297,6 +1312,11 @@ oais_status oais_potential(oais_ctx* ctx, const void* d_x, int64_t N, double* d_
         CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
         if (status & 2u) return fail(ctx, OAIS_ETIMEOUT, "a tensor-core completion wait gave up");
         if (status & 4u) return fail(ctx, OAIS_ECUDA, "shared memory base not 1024-byte aligned");
+        return OAIS_OK;
+    }
+    if (ctx->dt.wide) {
+        CK(launch_potential_wide(ctx->dt, static_cast<const float*>(d_x), N, d_ell, static_cast<float*>(d_grad),
+                                 static_cast<cudaStream_t>(stream)));
         return OAIS_OK;
     }
     if (ctx->dt.D == 0) return fail(ctx, OAIS_EUNSUPPORTED, "no CUDA-core form for this dimension");

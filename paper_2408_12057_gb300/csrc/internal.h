@@ -26,7 +26,18 @@ struct DevTarget {
     float* tcs_state = nullptr;
     bool tcs_q8 = false; // the streamed form's X is stored as FP8 e4m3 with per-row scales
     int tcs_dp = 0;      // padded width of the streamed form's chunk images
+    bool wide = false;   // plain FP32 form for 32 < d <= 256 (D = 64, 128 or 256): X [n_pad][D]
+    float* wide_state = nullptr;   // positions, gradients, momenta [3][D][tiles * 64]
 };
+
+// Plain FP32 CUDA-core form for the row families at 32 < d <= 256 (sweep_wide.cu): tiles of 64
+// particles, one CTA each; the state width D = wide_width(d)
+int wide_width(int d);
+int wide_tiles(int64_t N);
+size_t wide_state_bytes(int D, int64_t N);
+cudaError_t launch_sweep_wide(const DevTarget& t, int move, const SweepParams& sp, cudaStream_t s);
+cudaError_t launch_potential_wide(const DevTarget& t, const float* x, int64_t N, double* ell, float* grad,
+                                  cudaStream_t s);
 
 // Streamed tensor-core sweep (sweep_tcs.cu): sizes of one configuration.  dp = d padded to
 // 16, 32 or a multiple of 64 (at most 256); X~ is cut into nch chunks of `chunk` rows, each
