@@ -588,6 +588,26 @@ def line_linreg(args, steps, warmup, x_storage, short_warmup=False):
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
     job_s = total / 1e3 / steps
     se = last[-1]["se"]
+    # the plain FP32 form (the tiled CUDA-core contraction, X in fp32) on the same data: one
+    # round at T = 4 from the linear schedule (a full job would take several minutes)
+    other = None
+    if not getattr(args, "no_compare", False) and not args.asmc and x_storage == "bf16":
+        T_fp = 4
+        b_fp = np.linspace(0.0, 1.0, T_fp + 1)
+        e_fp = oais.default_step_sizes(pr, b_fp, oais.HMC)
+        r_fp = oais.OAIS(pr, oais.HMC, N, b_fp, eps=e_fp, seed=12057, leapfrog=L, stream=stream,
+                         contraction=oais.CONTRACT_FP32)
+        r_fp.round(T_fp)
+        t_fp, last_fp, _ = timed_job(lambda: [r_fp.round(T_fp)], 1, 0, stream)
+        v_fp = N * T_fp / (t_fp / 1e3)
+        evals_fp = N * (1 + T_fp * L)
+        tf_fp = 4.0 * pr.n * pr.d * evals_fp / (last_fp[0]["sweep_ms"] / 1e3) / 1e12
+        other = {"form": "plain FP32 (CUDA cores, tiled)", "value": v_fp, "unit": METRIC,
+                 "ms_per_step": t_fp, "T": T_fp, "rounds": 1, "tflops_fp32_algorithmic": tf_fp,
+                 "tensor_over_fp32": (ps * steps / (total / 1e3)) / v_fp,
+                 "note": "particle-steps/s of one T = 4 round; the seconds to a fixed SE are not "
+                         "meaningful in this regime for either form"}
+        r_fp.close()
     line = {
         "metric": METRIC, "value": ps * steps / (total / 1e3), "unit": METRIC, "n_gpus": 1,
         "steps": steps, "warmup": warmup, "ms_per_step": total / steps, "higher_is_better": True,
@@ -607,6 +627,7 @@ def line_linreg(args, steps, warmup, x_storage, short_warmup=False):
         "sec_to_logZ_se_0.01": job_s * (se / SE_TARGET) ** 2,
         "regime": "unstable at these T (Lambda ~ 150, ESS ~ 1): the delta-method SE and the seconds to "
                   "a fixed SE are not meaningful; the line measures throughput",
+        "other_form": other,
         "gpu_launches": 3 * len(rounds) * steps, "clocks": clk,
     }
     run.close()
@@ -676,6 +697,31 @@ def line_batched(args, steps, warmup, compare_sequential):
     line["sec_to_logZ_se_0.01"] = float(np.median(job_s * (se_p / SE_TARGET) ** 2))
     line["sec_to_logZ_se_0.01_note"] = (f"median over the 64 problems; {int((se_p < 0.5).sum())} problems have "
                                         "SE < 0.5 (the largest n and d sit in the unstable regime)")
+    # the plain FP32 form of every problem (one thread per particle for d <= 32, the tiled form
+    # above), the problems one after another: three rounds at T = 256 with --compare-sequential,
+    # else one round at T = 32 per problem (the comparison is per particle-step)
+    T_fp, R_fp = (T, R) if compare_sequential else (32, 1)
+    beta_fp = np.linspace(0.0, 1.0, T_fp + 1)
+    fps = [oais.OAIS(pr, oais.MALA, N, beta_fp, T_max=T_fp,
+                     eps=oais.default_step_sizes(pr, beta_fp, oais.MALA), seed=12057, stream=stream,
+                     contraction=oais.CONTRACT_FP32) for pr in probs]
+
+    def fp32_job():
+        for p, s in enumerate(fps):
+            s.set_schedule(beta_fp, oais.default_step_sizes(probs[p], beta_fp, oais.MALA))
+            for _ in range(R_fp):
+                s.round(T_fp)
+
+    t_fp, _, _ = timed_job(fp32_job, 1, 0 if not compare_sequential else 1, stream)
+    v_fp = len(probs) * N * T_fp * R_fp / (t_fp / 1e3)
+    line["other_form"] = {
+        "form": "64 sequential plain FP32 runs (CUDA cores)", "value": v_fp, "unit": METRIC,
+        "ms_per_step": t_fp, "T": T_fp, "rounds": R_fp, "problems": len(probs),
+        "batched_over_fp32": line["value"] / v_fp,
+        "note": "particle-steps/s of the plain FP32 form over all 64 problems; the job here is "
+                + ("the full one" if compare_sequential else "one round at T = 32 per problem")}
+    for s in fps:
+        s.close()
     if compare_sequential:
         singles = []
         for p, pr in enumerate(probs):
@@ -693,22 +739,8 @@ def line_batched(args, steps, warmup, compare_sequential):
 
         t_seq, _, _ = timed_job(seq_job, 1, 1, stream)
         line["sequential_tc"] = {"value": ps / (t_seq / 1e3), "unit": METRIC, "ms_per_step": t_seq}
-        small = [p for p, pr in enumerate(probs) if pr.d <= 32]
-        fps = [oais.OAIS(probs[p], oais.MALA, N, beta0, eps=eps0[p], seed=12057, stream=stream,
-                         contraction=oais.CONTRACT_FP32) for p in small]
-
-        def fp32_job():
-            for p, s in zip(small, fps):
-                s.set_schedule(beta0, eps0[p])
-                for _ in range(R):
-                    s.round(T)
-
-        t_fp, _, _ = timed_job(fp32_job, 1, 1, stream)
-        line["sequential_fp32_d_le_32"] = {
-            "value": len(small) * N * T * R / (t_fp / 1e3), "unit": METRIC, "ms_per_step": t_fp,
-            "problems": len(small), "note": "the CUDA-core FP32 form exists for d <= 32 only"}
         line["batched_vs_sequential_tc"] = t_seq / (total / steps)
-        for s in singles + fps:
+        for s in singles:
             s.close()
     b.close()
     return line
