@@ -68,8 +68,11 @@ def parse():
     ap.add_argument("--asmc", action="store_true",
                     help="linreg: ASMC rounds (resampling when ESS < N/2) instead of OAIS rounds, with the "
                          "closed-form log Z of the data the kernel samples")
-    ap.add_argument("--x-storage", default="bf16", choices=["bf16", "fp8"],
-                    help="linreg: X held as bf16 values (f16 encoding) or FP8 e4m3 with per-row scales")
+    ap.add_argument("--x-storage", default="bf16", choices=["bf16", "fp8", "fp32"],
+                    help="linreg: X held as bf16 values (f16 encoding) or FP8 e4m3 with per-row scales on the "
+                         "streamed tensor-core kernel, or fp32 on the plain FP32 CUDA-core form (profiling)")
+    ap.add_argument("--no-shift", action="store_true",
+                    help="default run: skip the quantisation-shift measurement (profiling)")
     ap.add_argument("--compare-sequential", action="store_true",
                     help="batched: also time the problems one after another (single contexts)")
     ap.add_argument("--no-nested", action="store_true",
@@ -412,7 +415,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, sample = cpu_baseline(pr, args.cpu_seconds, rounded_X(pr.X, args.contraction))
         acc = abs_err_vs_fp64(pr, code[args.contraction], sample)
-    if rank == 0 and world == 1 and args.contraction != "fp32":
+    if rank == 0 and world == 1 and args.contraction != "fp32" and not args.no_shift:
         shift = quantisation_shift(pr, run)
 
     nested = None
@@ -546,7 +549,8 @@ def line_linreg(args, steps, warmup, x_storage, short_warmup=False):
     stream = torch.cuda.current_stream()
     beta0 = np.linspace(0.0, 1.0, rounds[0] + 1)
     eps0 = oais.default_step_sizes(pr, beta0, oais.HMC)
-    contraction = oais.CONTRACT_FP8_TC_STREAM if x_storage == "fp8" else oais.CONTRACT_BF16_TC_STREAM
+    contraction = {"fp8": oais.CONTRACT_FP8_TC_STREAM, "fp32": oais.CONTRACT_FP32}.get(x_storage,
+                                                                                       oais.CONTRACT_BF16_TC_STREAM)
     run = oais.OAIS(pr, oais.HMC, N, beta0, T_max=max(rounds), eps=eps0, seed=12057, leapfrog=L, adapt=True,
                     stream=stream, contraction=contraction)
 
@@ -586,6 +590,9 @@ def line_linreg(args, steps, warmup, x_storage, short_warmup=False):
     evals = N * sum(1 + T * L for T in rounds)          # log L + gradient evaluations per job
     alg = 4.0 * pr.n * pr.d * evals / sweep_s / 1e12   # z = X x and X^T r per evaluation
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0)))
+    fp32_form = x_storage == "fp32"
+    if fp32_form:   # the plain FP32 form: the FMA pipe, 2 x the measured FFMA rate x 152 SMs
+        peak = 2.0 * measure_unit_rate(UNIT_FFMA) * N_SM / 1e12
     job_s = total / 1e3 / steps
     se = last[-1]["se"]
     # the plain FP32 form (the tiled CUDA-core contraction, X in fp32) on the same data: one
@@ -619,11 +626,15 @@ def line_linreg(args, steps, warmup, x_storage, short_warmup=False):
         "logZ_last_round": last[-1]["logZ"], "se_last_round": last[-1]["se"],
         "asmc": ({"logZ_closed_form": closed, "resampling_events": [r["n_resample"] for r in last],
                   "logZ_per_round": [r["logZ"] for r in last]} if args.asmc else None),
-        "roofline": {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
-                     "traffic": None, "peak_source": f"{src} cuBLAS bf16 sustained (f16 runs at the same rate)",
-                     "issued_tflops": 2 * alg, "issued_frac": 2 * alg / peak,
-                     "note": "achieved counts 4 n d FLOP per evaluation; the two-term operand split issues 2x",
-                     "kernel": f"oais_sweep_tcs_kernel<LINREG, 256, {1 if x_storage == 'fp8' else 0}>"},
+        "roofline": {"bound": "alu" if fp32_form else "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s",
+                     "frac": alg / peak, "traffic": None,
+                     "peak_source": ("measured FFMA rate (bench_unitrate.cu) x 2 x 152 SMs" if fp32_form
+                                     else f"{src} cuBLAS bf16 sustained (f16 runs at the same rate)"),
+                     "issued_tflops": alg if fp32_form else 2 * alg, "issued_frac": (1 if fp32_form else 2) * alg / peak,
+                     "note": "achieved counts 4 n d FLOP per evaluation" + ("" if fp32_form else
+                             "; the two-term operand split issues 2x"),
+                     "kernel": ("wide_sweep_kernel<256, linear, HMC> (plain FP32, CUDA cores)" if x_storage == "fp32"
+                                else f"oais_sweep_tcs_kernel<LINREG, 256, {1 if x_storage == 'fp8' else 0}>")},
         "sec_to_logZ_se_0.01": job_s * (se / SE_TARGET) ** 2,
         "regime": "unstable at these T (Lambda ~ 150, ESS ~ 1): the delta-method SE and the seconds to "
                   "a fixed SE are not meaningful; the line measures throughput",
