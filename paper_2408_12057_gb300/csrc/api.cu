@@ -153,6 +153,8 @@ struct oais_ctx {
     void* ws = nullptr;
     bool own_ws = false;
     double *d_beta = nullptr, *d_eps = nullptr, *d_logw = nullptr, *d_ell = nullptr;
+    float* d_fsched = nullptr;           // fp32 roundings of the schedule (GmmTarget::fsched)
+    std::vector<float> h_fsched;
     void* d_x = nullptr;
     StepPartial* d_parts = nullptr;
     double *d_log_ghat = nullptr, *d_accept = nullptr, *d_lse = nullptr;
@@ -238,7 +240,8 @@ static size_t elt_bytes(int kind) { return f64_kind(kind) ? sizeof(double) : siz
 struct Layout {
     size_t X, y, beta, eps, logw, ell, x, parts, lg, acc, elbo, lse, lse_scr, status;
     size_t x1, g0, g1, ell1, ess_parts, st, bsum, boff, cdf, ess_trace, resampled, anc, tc_img, tc_y;
-    size_t tcs_img, tcs_state, tc_handed, zja_fg, zja_anchor, zja_part, zja_state, zja_beta, zja_eps, wide_state, total;
+    size_t tcs_img, tcs_state, tc_handed, zja_fg, zja_anchor, zja_part, zja_state, zja_beta, zja_eps, wide_state, fsched,
+        total;
 };
 
 // which sweep form a target runs: 0 CUDA cores, 1 resident tensor-core, 2 streamed tensor-core
@@ -313,6 +316,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     L.tcs_state = take(form >= 1 ? sizeof(float) * 5 * (size_t)tp.dp * tcs_tiles(N) * 128 : 0);
     // the tiled fp32 form (32 < d <= 256): positions, gradients, momenta of every tile
     L.wide_state = take(D > 32 ? wide_state_bytes(D, N) : 0);
+    L.fsched = take(sizeof(float) * (3 * (size_t)T_max + 1));
     L.total = off;
     return L;
 }
@@ -475,6 +479,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
     dt.wide = D > 32;
     dt.wide_state = dt.wide ? reinterpret_cast<float*>(b + L.wide_state) : nullptr;
     ctx->d_beta = reinterpret_cast<double*>(b + L.beta);
+    ctx->d_fsched = reinterpret_cast<float*>(b + L.fsched);
     ctx->d_eps = reinterpret_cast<double*>(b + L.eps);
     ctx->d_logw = reinterpret_cast<double*>(b + L.logw);
     ctx->d_ell = reinterpret_cast<double*>(b + L.ell);
@@ -748,6 +753,15 @@ static oais_status run_round_impl(oais_ctx* ctx, int32_t T_next, bool asmc, doub
     const uint32_t tag = (uint32_t)(ctx->round & 0xFFFF) | ((uint32_t)ctx->problem << 16);
     const int grid = sweep_grid(ctx->N);
     const double logN = std::log((double)ctx->N);
+    // the fp32 roundings of the schedule for the fp32 forms of the CUDA-core sweep
+    ctx->h_fsched.assign(3 * (size_t)T + 1, 0.0f);
+    for (int t = 0; t <= T; ++t) ctx->h_fsched[t] = (float)ctx->beta[t];
+    for (int t = 1; t <= T; ++t) {
+        ctx->h_fsched[T + t] = (float)(ctx->beta[t] - ctx->beta[t - 1]);
+        ctx->h_fsched[2 * T + t] = (float)ctx->eps[t - 1];
+    }
+    CK(cudaMemcpyAsync(ctx->d_fsched, ctx->h_fsched.data(), sizeof(float) * ctx->h_fsched.size(),
+                       cudaMemcpyHostToDevice, s));
     std::vector<double> lg(3 * T), acc(T), elbo(T), ess_tr;
     std::vector<int> rs;
     unsigned status = 0;
@@ -765,7 +779,11 @@ static oais_status run_round_impl(oais_ctx* ctx, int32_t T_next, bool asmc, doub
                                 ctx->dt.tcs_state, ctx->mv.kind, ctx->mv.leapfrog, ctx->dt.p0, ctx->dt.n,
                                 ctx->dt.d, s, ctx->dt.tc_handed));
         else if (ctx->dt.wide) CK(launch_sweep_wide(ctx->dt, ctx->mv.kind, P, s));
-        else CK(launch_sweep(ctx->dt, ctx->mv.kind, P, s));
+        else {
+            DevTarget dt = ctx->dt;
+            dt.fsched = ctx->d_fsched;
+            CK(launch_sweep(dt, ctx->mv.kind, P, s));
+        }
         CK(cudaEventRecord(ctx->ev1, s));
         const int records = ctx->dt.tc ? tc_records(ctx->N)
                           : (ctx->dt.tcs ? tcs_tiles(ctx->N) : (ctx->dt.wide ? wide_tiles(ctx->N) : grid));

@@ -26,6 +26,7 @@ struct DevTarget {
     float* tcs_state = nullptr;
     bool tcs_q8 = false; // the streamed form's X is stored as FP8 e4m3 with per-row scales
     int tcs_dp = 0;      // padded width of the streamed form's chunk images
+    const float* fsched = nullptr;   // fp32 roundings of the running schedule (GmmTarget::fsched)
     bool wide = false;   // plain FP32 form for 32 < d <= 256 (D = 64, 128 or 256): X [n_pad][D]
     float* wide_state = nullptr;   // positions, gradients, momenta [3][D][tiles * 64]
 };

@@ -146,6 +146,12 @@ __device__ __forceinline__ float mh_log_uniform(const Rng& rng, uint32_t n, uint
 {
     return logf(u01f(rng.block(n, t, k, 0xFFFFu).v[0]));
 }
+// the same with the special-function logarithm (relative error of order 1e-7; a decision can
+// differ from the exact form's only at a near tie): the random-walk moves of the fp32 forms
+__device__ __forceinline__ float mh_log_uniform_sfu(const Rng& rng, uint32_t n, uint32_t t, uint32_t k)
+{
+    return __logf(u01f(rng.block(n, t, k, 0xFFFFu).v[0]));
+}
 __device__ __forceinline__ double mh_log_uniform(const Rng& rng, uint32_t n, uint32_t t, uint32_t k, double)
 {
     return log(u01d(rng.block(n, t, k, 0xFFFFu).v[0]));
@@ -386,6 +392,132 @@ __device__ __forceinline__ void merge_deferred_pieces(int lane, const double (*w
 #pragma unroll
     for (int i = 0; i < 4; ++i) sv[i] = on ? ws[lane][i] : 0.0f;
     merge_lane_pieces<W, true>(lane, m, sv, (wacc && on) ? wacc[lane] : 0u, out);
+}
+
+// ---------------------------------------------------------------------------------------
+// fp32-only bookkeeping of the one-thread-per-particle fp32 forms.  GB300's fp64 pipe runs at a
+// small fraction of its fp32 rate, so the per-step fp64 additions and conversions of the moment
+// bookkeeping occupied it for a third of the mixture sweep.  Instead:
+//   log w is held as an unevaluated sum hi + lo of two fp32 values, each step's log g (an fp32
+//   value) added by Knuth's TwoSum (hi the rounded sum, lo += the exact rounding error), so that
+//   hi + lo carries about 48 bits; a zero weight (-inf) or a non-finite value stays in hi;
+//   the warp piece takes its anchor (a_hi, a_lo, log g_a) and offsets
+//   (hi - a_hi) + (lo - a_lo) + i (log g - log g_a) in fp32 (hi - a_hi is exact where it matters,
+//   within a factor of two of the anchor, by Sterbenz's lemma), and the merge forms the fp64
+//   shift a_hi + a_lo + i log g_a + max_i for its W pieces only.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v)
+{
+    const float s = hi + v;
+    if (!isfinite(s)) { hi = s; lo = 0.0f; return; }
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
+// The warp's piece for log w = lwh + lwl and the fp32 log g: as warp_moment_partial<true>, with
+// the anchors in wf[0..2] = (a_hi, a_lo, log g_a) and the fp32 maxima in ws[4..6].
+__device__ __forceinline__ void warp_moment_partial_df(float lwh, float lwl, float lg, bool active, float* wf /*3*/,
+                                                       float* ws /*8*/)
+{
+    const unsigned full = 0xFFFFFFFFu;
+    const bool lead = (threadIdx.x & 31) == 0;
+    const bool fw = active && isfinite(lwh), fg = active && isfinite(lg);
+    const unsigned bw = __ballot_sync(full, fw);
+    if (bw == 0) {
+        if (lead) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                wf[i] = 0.0f;
+                ws[i] = 0.0f;
+                ws[4 + i] = -INFINITY;
+            }
+            ws[3] = 0.0f;
+        }
+        return;
+    }
+    const unsigned bg = __ballot_sync(full, fg);
+    float ah = __shfl_sync(full, lwh, __ffs(bw) - 1), al = __shfl_sync(full, lwl, __ffs(bw) - 1);
+    float b0 = bg ? __shfl_sync(full, lg, __ffs(bg) - 1) : 0.0f;
+    if (__ballot_sync(full, fw && fg)) {
+        // anchor at the lane with the largest log w + log g (the error of the offsets is
+        // smallest where the weight is)
+        const float f1 = (fw && fg) ? lwh + lg : -INFINITY;
+        float m1 = f1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m1 = fmaxf(m1, __shfl_xor_sync(full, m1, o));
+        const int src = __ffs(__ballot_sync(full, f1 == m1)) - 1;
+        ah = __shfl_sync(full, lwh, src);
+        al = __shfl_sync(full, lwl, src);
+        b0 = __shfl_sync(full, lg, src);
+    }
+    const float dw = (lwh - ah) + (lwl - al), dg = lg - b0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float f = !active ? -INFINITY : (i == 0 ? dw : dw + (float)i * dg);
+        float mx = f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
+        float e = f > -INFINITY ? __expf(f - mx) : 0.0f;
+        float u = (i == 0 && e > 0.0f) ? e * lg : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
+        if (i == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
+        }
+        if (lead) {
+            ws[4 + i] = mx;
+            ws[i] = e;
+            if (i == 0) ws[3] = u;
+        }
+    }
+    if (lead) { wf[0] = ah; wf[1] = al; wf[2] = b0; }
+}
+
+// Merge of G steps' records at once: lanes W s .. W s + W - 1 of the calling warp merge step s's
+// W warp pieces (wf [G][W][3], ws [G][W][8], wacc [G][W]) in a fixed order, as
+// merge_deferred_pieces does for one step, and lane W s writes out[s stride] (steps s >= count
+// are skipped).  W * G == 32.
+template <int W, int G>
+__device__ __forceinline__ void merge_steps_df(int lane, const float (*wf)[W][3], const float (*ws)[W][8],
+                                               const unsigned (*wacc)[W], int count, StepPartial* out,
+                                               size_t stride)
+{
+    static_assert(W * G == 32 && (W & (W - 1)) == 0, "lane groups");
+    const int s = lane / W, j = lane % W;
+    const bool on = s < count;
+    const float ah = on ? wf[s][j][0] : 0.0f, al = on ? wf[s][j][1] : 0.0f, bg = on ? wf[s][j][2] : 0.0f;
+    const double a = (double)ah + (double)al, b = (double)bg;
+    StepPartial rec;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float mxj = on ? ws[s][j][4 + i] : -INFINITY;
+        const double m = mxj > -INFINITY ? a + i * b + (double)mxj : -INFINITY;
+        double M = m;
+#pragma unroll
+        for (int o = 1; o < W; o <<= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
+        const float dj = (float)(m - M);
+        const float fj = (on && !isnan(dj)) ? expf(dj) : 0.0f;
+        float v = (on ? ws[s][j][i] : 0.0f) * fj;
+        float uu = (i == 0 && fj > 0.0f) ? (on ? ws[s][j][3] : 0.0f) * fj : 0.0f;
+#pragma unroll
+        for (int o = 1; o < W; o <<= 1) {
+            v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            uu += __shfl_xor_sync(0xFFFFFFFFu, uu, o);
+        }
+        rec.s[i] = (double)v;
+        if (i == 0) rec.u = (double)uu;
+        rec.m[i] = M;
+    }
+    unsigned acc = on ? wacc[s][j] : 0u;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (on && j == 0) {
+        rec.accepted = acc;
+        rec.pad = 0;
+        out[(size_t)s * stride] = rec;
+    }
 }
 
 // CTA part: warp 0 merges the W warps' pieces and writes one record.  Call after a

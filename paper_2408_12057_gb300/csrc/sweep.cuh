@@ -157,7 +157,9 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
         for (int i = 0; i < D; ++i) { ke1 += z[i] * z[i]; dxx += (xp[i] - x[i]) * (xp[i] + x[i]); }
         log_alpha = -R(0.5) * dxx * inv_s2 + beta * (ellp - ell) - R(0.5) * (ke1 - ke0);
     }
-    const R logu = mh_log_uniform(P.rng, n, t, k, R(0));
+    R logu;
+    if constexpr (kFp32<R> && MOVE == kRwmh) logu = mh_log_uniform_sfu(P.rng, n, t, k);
+    else logu = mh_log_uniform(P.rng, n, t, k, R(0));
     const bool acc = logu < log_alpha;
     if (acc) {
 #pragma unroll
@@ -208,32 +210,86 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
     unsigned bad = 0;
     (void)lane;
 
-    double beta_prev = P.beta[0];
-    for (int t = 1; t <= P.T; ++t) {
-        const double beta_t = __ldg(P.beta + t);
-        const double eps_t = __ldg(P.eps + t - 1);
-        const double lg = step_log_increment<R>(beta_t - beta_prev, ell);
-        beta_prev = beta_t;
-        const R beta_r = (R)beta_t, eps_r = (R)eps_t;
-        const int slot = t & 1;
-        warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
-        logw += lg;
-        unsigned acc = 0;
-        for (int k = 0; k < P.mv.K; ++k)
-            acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_r, eps_r, n, (uint32_t)t,
-                                            (uint32_t)k, d, inv_s2) ? 1u : 0u;
-        acc = active ? acc : 0u;
+    if constexpr (kFp32<R> && Tgt::kind == kGmm) {
+        // fp32 bookkeeping (see warp_moment_partial_df): log w = lwh + lwl, the step's schedule
+        // values from the fp32 roundings the host prepared (the same values the conversions of
+        // the fp64 schedule give), and one CTA merge every kMergeSteps steps: the warps' pieces of
+        // those steps wait in shared memory (double-buffered, so the warps run on while warp 0
+        // merges), and warp 0 merges the batch with a lane group per step.  For the mixture, whose
+        // evaluations are a few hundred instructions without barriers, the per-step fp64
+        // bookkeeping and the per-step barrier were a large share of the step (1.06e10 ->
+        // 1.19e10 particle-steps/s); the row families' evaluations synchronise the CTA every data
+        // chunk anyway and keep the per-step form below (they ran 7 % slower with this one).
+        constexpr int W = kSweepThreads / 32;
+        constexpr int kMergeSteps = 32 / W;
+        __shared__ float s_wf[2][kMergeSteps][W][3];
+        __shared__ float s_ws[2][kMergeSteps][W][8];
+        __shared__ unsigned s_wacc[2][kMergeSteps][W];
+        float lwh = 0.0f, lwl = 0.0f;
+        double beta_prev = P.beta[0];
+        for (int t = 1; t <= P.T; ++t) {
+            float db, beta_r, eps_r;
+            if (tg.fsched) {
+                beta_r = tg.fsched[t];
+                db = tg.fsched[P.T + t];
+                eps_r = tg.fsched[2 * P.T + t];
+            } else {
+                const double beta_t = __ldg(P.beta + t);
+                db = (float)(beta_t - beta_prev);
+                beta_prev = beta_t;
+                beta_r = (float)beta_t;
+                eps_r = (float)__ldg(P.eps + t - 1);
+            }
+            const float lg = db == 0.0f ? 0.0f : db * (float)ell;
+            const int buf = ((t - 1) / kMergeSteps) & 1, st = (t - 1) % kMergeSteps;
+            warp_moment_partial_df(lwh, lwl, lg, active, s_wf[buf][st][warp], s_ws[buf][st][warp]);
+            df_add(lwh, lwl, lg);
+            unsigned acc = 0;
+            for (int k = 0; k < P.mv.K; ++k)
+                acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, (R)beta_r, (R)eps_r, n, (uint32_t)t,
+                                                (uint32_t)k, d, inv_s2) ? 1u : 0u;
+            acc = active ? acc : 0u;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-        if (lane == 0) s_acc[slot][warp] = acc;
-        __syncthreads();
-        if constexpr (kFp32<R>) {
-            if (warp == 0)
-                merge_deferred_pieces<kSweepThreads / 32>(lane, s_m[slot], s_s[slot], s_acc[slot],
-                                                          P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
-        } else {
-            cta_moment_record<kSweepThreads / 32, false>(s_m[slot], s_s[slot], s_acc[slot],
-                                                         P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+            if (lane == 0) s_wacc[buf][st][warp] = acc;
+            if (st == kMergeSteps - 1 || t == P.T) {
+                __syncthreads();
+                if (warp == 0) {
+                    const int t0 = t - st;            // the batch's first step
+                    merge_steps_df<W, kMergeSteps>(lane, s_wf[buf], s_ws[buf], s_wacc[buf], st + 1,
+                                                   P.partials + (size_t)(t0 - 1) * gridDim.x + blockIdx.x, gridDim.x);
+                }
+            }
+        }
+        logw = (double)lwh + (double)lwl;
+    } else {
+        double beta_prev = P.beta[0];
+        for (int t = 1; t <= P.T; ++t) {
+            const double beta_t = __ldg(P.beta + t);
+            const double eps_t = __ldg(P.eps + t - 1);
+            const double lg = step_log_increment<R>(beta_t - beta_prev, ell);
+            beta_prev = beta_t;
+            const R beta_r = (R)beta_t, eps_r = (R)eps_t;
+            const int slot = t & 1;
+            warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[slot][warp], s_s[slot][warp]);
+            logw += lg;
+            unsigned acc = 0;
+            for (int k = 0; k < P.mv.K; ++k)
+                acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_r, eps_r, n, (uint32_t)t,
+                                                (uint32_t)k, d, inv_s2) ? 1u : 0u;
+            acc = active ? acc : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+            if (lane == 0) s_acc[slot][warp] = acc;
+            __syncthreads();
+            if constexpr (kFp32<R>) {
+                if (warp == 0)
+                    merge_deferred_pieces<kSweepThreads / 32>(lane, s_m[slot], s_s[slot], s_acc[slot],
+                                                              P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
+            } else {
+                cta_moment_record<kSweepThreads / 32, false>(s_m[slot], s_s[slot], s_acc[slot],
+                                                             P.partials + (size_t)(t - 1) * gridDim.x + blockIdx.x);
+            }
         }
     }
     if (!admissible(logw) || !admissible((double)ell)) bad = 1;

@@ -17,6 +17,7 @@ static GmmTarget<float, D> make_gmm(const DevTarget& t, size_t* smem)
     tg.log_const = (float)(-0.5 * t.d * std::log(two_pi * t.p0) - std::log((double)t.n)
                            + 0.5 * t.d * std::log(two_pi * t.ref_scale * t.ref_scale));
     tg.sm = nullptr;
+    tg.fsched = t.fsched;
     *smem = GmmTarget<float, D>::smem_bytes(t.n);
     return tg;
 }

@@ -94,6 +94,10 @@ struct GmmTarget {
     R inv_s2;         // 1 / s^2
     R log_const;      // -(d/2) log(2 pi v) - log K + (d/2) log(2 pi s^2)
     const R* sm;      // shared copy
+    // fp32 roundings of the running schedule (nullable), 3 T + 1 floats: beta_t at [t]
+    // (t = 0..T), beta_t - beta_{t-1} (rounded from its fp64 difference) at [T + t] and eps_t at
+    // [2 T + t] (t = 1..T); the sweep reads them instead of converting the fp64 schedule per step
+    const float* fsched;
 
     static constexpr size_t smem_bytes(int K) { return sizeof(R) * (size_t)K * D; }
     __device__ void setup(unsigned char* smem) {
