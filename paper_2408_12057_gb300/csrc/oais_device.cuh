@@ -57,8 +57,10 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        // each 32 x 32 -> 64-bit product is one wide multiply (both halves at once)
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
         c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
         k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
@@ -74,7 +76,13 @@ struct Rng {
     }
 };
 
-__device__ __forceinline__ float u01f(uint32_t r) { return ((float)(r >> 9) + 0.5f) * (1.0f / 8388608.0f); }
+// u = ((r >> 9) + 1/2) 2^-23: the 23 bits as the mantissa of a float in [1, 2), minus
+// 1 - 2^-24 (an exact subtraction by Sterbenz's lemma), the same value as the conversion of
+// the integer, without an integer-to-float conversion
+__device__ __forceinline__ float u01f(uint32_t r)
+{
+    return __uint_as_float((r >> 9) | 0x3F800000u) - 0.99999994039535522461f;
+}
 __device__ __forceinline__ double u01d(uint32_t r) { return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 // four standard normals from one Philox block
