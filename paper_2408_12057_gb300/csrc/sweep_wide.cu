@@ -4,13 +4,14 @@
 //
 // A CTA owns a tile of 64 particles for the whole sweep and runs Alg. 1 on it in lock-step:
 // every evaluation of log L and grad log L at the tile's 64 states is two fp32 contractions
-// on the CUDA cores over the data X, streamed through shared memory in chunks of 32 rows
-// (cp.async, double-buffered):
+// on the CUDA cores over the data X, streamed through shared memory in chunks of 64 rows
+// (cp.async, double-buffered; 64 rows):
 //   forward   Z[r][p] = sum_k X[r][k] Y[k][p]      (Y: the tile's states, in shared memory)
 //   epilogue  f = per-row log-likelihood term, R[r][p] = df/dz
 //   backward  G[k][p] += sum_r X[r][k] R[r][p]     (G: the gradients, in registers)
-// Each thread computes a 2 x 4 block of Z and an (DP/32) x 8 block of G, so both contractions
-// run at several fused multiply-adds per shared-memory load.  Particle vectors (positions,
+// Each thread computes a 4 x 4 block of Z and an (DP/32) x 8 block of G, so both contractions
+// run at 8-16 fused multiply-adds per 16-byte shared-memory load, and loads the next step's
+// operands while the current step's multiply-adds run.  Particle vectors (positions,
 // gradients, momenta) live in device memory between evaluations, each thread touching only
 // its own elements; the per-particle sums of the Metropolis-Hastings ratios are warp
 // reductions; one moment record per (step, tile) as in the other forms.
@@ -32,13 +33,17 @@ constexpr int kP = 64;               // particles per tile (one CTA)
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPW = kP / kWarps;     // particles per warp in the coordinate layout (8)
-constexpr int kRows = 32;            // data rows per chunk
 constexpr int kTS = kP + 4;          // row stride (floats) of the particle-minor tiles Y and R
 static_assert(kPW == 8, "coordinate layout: 8 particles per warp");
 
 template <int DP>
 struct Lay {
     static constexpr int KB = DP / 32;                       // coordinates per lane
+    // data rows per chunk (each thread's forward block is kRPT rows x 4 particles): 64 rows,
+    // 4 x 4 blocks, measured faster than 32 rows and 2 x 4 blocks at every width, although the
+    // larger buffers leave room for fewer tiles per SM at d <= 128
+    static constexpr int kRows = 64;
+    static constexpr int kRPT = kRows / 16;
     static constexpr int kXS = DP + 4;                       // X chunk row stride (floats)
     static constexpr int kOffX = 0;                          // [2][kRows][kXS]
     static constexpr int kOffYv = kOffX + 2 * kRows * kXS;   // [2][kRows] responses / labels
@@ -77,17 +82,17 @@ struct Eval {
 
     __device__ static void load_chunk(const Args& A, float* sm, int c, int buf)
     {
-        const int r0 = c * kRows;
-        const int rows = min(kRows, A.n - r0);
+        const int r0 = c * L::kRows;
+        const int rows = min(L::kRows, A.n - r0);
         const float* src = A.X + (size_t)r0 * DP;
-        float* dst = sm + L::kOffX + buf * kRows * L::kXS;
+        float* dst = sm + L::kOffX + buf * L::kRows * L::kXS;
         constexpr int kPieces = DP / 4;                 // 16-byte pieces per row
         for (int i = threadIdx.x; i < rows * kPieces; i += kThreads) {
             const int r = i / kPieces, q = i % kPieces;
             cp_async16(dst + r * L::kXS + 4 * q, src + (size_t)r * DP + 4 * q);
         }
         const float* sy = A.yv + r0;
-        float* dy = sm + L::kOffYv + buf * kRows;
+        float* dy = sm + L::kOffYv + buf * L::kRows;
         for (int i = threadIdx.x; i < (rows + 3) / 4; i += kThreads) cp_async16(dy + 4 * i, sy + 4 * i);
         cp_async_commit();
     }
@@ -122,44 +127,62 @@ struct Eval {
 #pragma unroll
             for (int b = 0; b < kPW; ++b) G[a][b] = 0.0f;
         float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        const int nch = (A.n + kRows - 1) / kRows;
+        const int nch = (A.n + L::kRows - 1) / L::kRows;
         load_chunk(A, sm, 0, 0);
         for (int c = 0; c < nch; ++c) {
             if (c + 1 < nch) { load_chunk(A, sm, c + 1, (c + 1) & 1); cp_async_wait<1>(); }
             else             { cp_async_wait<0>(); }
             __syncthreads();
-            const float* Xc = sm + L::kOffX + (c & 1) * kRows * L::kXS;
-            const float* yc = sm + L::kOffYv + (c & 1) * kRows;
-            const int rows = min(kRows, A.n - c * kRows);
-            // forward: a 2 x 4 block of Z
-            float z0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, z1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            const float* xa = Xc + (2 * rb) * L::kXS;
-            const float* xb = xa + L::kXS;
-#pragma unroll 4
-            for (int k = 0; k < DP; k += 4) {
-                const float4 va = *reinterpret_cast<const float4*>(xa + k);
-                const float4 vb = *reinterpret_cast<const float4*>(xb + k);
-                const float fa[4] = {va.x, va.y, va.z, va.w}, fb[4] = {vb.x, vb.y, vb.z, vb.w};
+            const float* Xc = sm + L::kOffX + (c & 1) * L::kRows * L::kXS;
+            const float* yc = sm + L::kOffYv + (c & 1) * L::kRows;
+            const int rows = min(L::kRows, A.n - c * L::kRows);
+            // forward: a kRPT x 4 block of Z (rows kRPT rb ..; particles 4 pb ..); the next k step's
+            // operands are loaded while this one's multiply-adds run
+            constexpr int RPT = L::kRPT;
+            float z[RPT][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 yk = *reinterpret_cast<const float4*>(Y + (k + q) * kTS + 4 * pb);
-                    z0[0] = fmaf(fa[q], yk.x, z0[0]); z0[1] = fmaf(fa[q], yk.y, z0[1]);
-                    z0[2] = fmaf(fa[q], yk.z, z0[2]); z0[3] = fmaf(fa[q], yk.w, z0[3]);
-                    z1[0] = fmaf(fb[q], yk.x, z1[0]); z1[1] = fmaf(fb[q], yk.y, z1[1]);
-                    z1[2] = fmaf(fb[q], yk.z, z1[2]); z1[3] = fmaf(fb[q], yk.w, z1[3]);
+            for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) z[i][j] = 0.0f;
+            const float* xrow = Xc + (RPT * rb) * L::kXS;
+            float4 xv[RPT], yv[4];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) xv[i] = *reinterpret_cast<const float4*>(xrow + i * L::kXS);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) yv[q] = *reinterpret_cast<const float4*>(Y + q * kTS + 4 * pb);
+#pragma unroll 2
+            for (int k = 0; k < DP; k += 4) {
+                float4 xn[RPT], yn[4];
+                const int kn = k + 4 < DP ? k + 4 : k;
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) xn[i] = *reinterpret_cast<const float4*>(xrow + i * L::kXS + kn);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) yn[q] = *reinterpret_cast<const float4*>(Y + (kn + q) * kTS + 4 * pb);
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) {
+                    const float fx[4] = {xv[i].x, xv[i].y, xv[i].z, xv[i].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        z[i][0] = fmaf(fx[q], yv[q].x, z[i][0]); z[i][1] = fmaf(fx[q], yv[q].y, z[i][1]);
+                        z[i][2] = fmaf(fx[q], yv[q].z, z[i][2]); z[i][3] = fmaf(fx[q], yv[q].w, z[i][3]);
+                    }
                 }
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) xv[i] = xn[i];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) yv[q] = yn[q];
             }
             // epilogue: rows past the data (stale buffer contents) are masked by selects
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = 2 * rb + i;
+            for (int i = 0; i < RPT; ++i) {
+                const int r = RPT * rb + i;
                 const bool valid = r < rows;
                 const float yr = valid ? yc[r] : 0.0f;
                 float rv[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     float f;
-                    const float dz = row_term(A, i == 0 ? z0[j] : z1[j], yr, f);
+                    const float dz = row_term(A, z[i][j], yr, f);
                     part[j] += valid ? f : 0.0f;
                     rv[j] = valid ? dz : 0.0f;
                 }
@@ -167,10 +190,10 @@ struct Eval {
             }
             if (GRAD) {
                 __syncthreads();
-                // backward: G[coord(a)][8 warp + b] += sum_r X[r][coord(a)] R[r][8 warp + b]
-                for (int r = 0; r < rows; ++r) {
+                // backward: G[coord(a)][8 warp + b] += sum_r X[r][coord(a)] R[r][8 warp + b], the next
+                // row's operands loaded while this row's multiply-adds run
+                auto load_row = [&](int r, float (&xv)[KB], float (&rr)[kPW]) {
                     const float* xr = Xc + r * L::kXS;
-                    float xv[KB];
                     if (KB >= 4) {
 #pragma unroll
                         for (int g4 = 0; g4 < KB / 4; ++g4) {
@@ -183,11 +206,24 @@ struct Eval {
                     }
                     const float4 r0 = *reinterpret_cast<const float4*>(R + r * kTS + kPW * warp);
                     const float4 r1 = *reinterpret_cast<const float4*>(R + r * kTS + kPW * warp + 4);
-                    const float rr[kPW] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                    rr[0] = r0.x; rr[1] = r0.y; rr[2] = r0.z; rr[3] = r0.w;
+                    rr[4] = r1.x; rr[5] = r1.y; rr[6] = r1.z; rr[7] = r1.w;
+                };
+                if (rows > 0) {
+                    float xv[KB], rr[kPW];
+                    load_row(0, xv, rr);
+                    for (int r = 0; r < rows; ++r) {
+                        float xn[KB], rn[kPW];
+                        load_row(r + 1 < rows ? r + 1 : r, xn, rn);
 #pragma unroll
-                    for (int a = 0; a < KB; ++a)
+                        for (int a = 0; a < KB; ++a)
 #pragma unroll
-                        for (int b = 0; b < kPW; ++b) G[a][b] = fmaf(xv[a], rr[b], G[a][b]);
+                            for (int b = 0; b < kPW; ++b) G[a][b] = fmaf(xv[a], rr[b], G[a][b]);
+#pragma unroll
+                        for (int a = 0; a < KB; ++a) xv[a] = xn[a];
+#pragma unroll
+                        for (int b = 0; b < kPW; ++b) rr[b] = rn[b];
+                    }
                 }
             }
             __syncthreads();   // the chunk's buffers and R are free for the next chunk
@@ -303,9 +339,9 @@ __device__ __forceinline__ void load_tile(const float* Y, int warp, int lane, fl
     }
 }
 
-// CTAs per SM the register allocation must allow: the narrower widths hold fewer gradient
-// accumulators and fit two or three tiles per SM
-template <int DP> struct WideMinBlocks { static constexpr int value = DP <= 64 ? 3 : (DP <= 128 ? 2 : 1); };
+// CTAs per SM the register allocation must allow: the narrowest width holds fewer gradient
+// accumulators and fits three tiles per SM
+template <int DP> struct WideMinBlocks { static constexpr int value = DP <= 64 ? 3 : 1; };
 
 template <int DP, bool LOGISTIC, int MOVE>
 __global__ void __launch_bounds__(kThreads, WideMinBlocks<DP>::value)
