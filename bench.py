@@ -294,8 +294,11 @@ def main():
     def make_run(contraction):
         # one sharded run: each rank owns a disjoint block of the particle counter space (weak
         # scaling, N_PARTICLES per GPU); the round statistics are exchanged once per round
+        # the tensor-core forms reweight their final particles from bf16(X) to X
+        # (oais_set_exact_data), so that every form estimates log Z of the same data
         r = oais.OAIS(pr, oais.MALA, N_PARTICLES, beta0, T_max=max(ROUNDS_T), eps=eps0,
-                      seed=12057, adapt=True, stream=stream, contraction=code[contraction])
+                      seed=12057, adapt=True, stream=stream, contraction=code[contraction],
+                      exact_data=contraction != "fp32")
         if world > 1:
             r.set_shard(rank * N_PARTICLES, world * N_PARTICLES)
         return r
@@ -431,7 +434,12 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N_per_gpu": N_PARTICLES, "T_rounds": ROUNDS_T,
                        "move": "MALA", "l2": "flushed between timed steps (256 MiB write)",
-                       "log_weights": "f64", "contraction": args.contraction},
+                       "log_weights": "f64", "contraction": args.contraction,
+                       "final_reweighting_to_X": args.contraction != "fp32"},
+            "logZ_minus_other_form": (None if compare is None else {
+                "value": last[-1]["logZ"] - compare["logZ_last_round"],
+                "se": float(np.hypot(last[-1]["se"], compare["se_last_round"])),
+                "note": "last rounds (T = 2048) of the two forms, both estimating log Z of X"}),
             "logZ_last_round": last[-1]["logZ"], "se_last_round": se_last,
             "elbo_last_round": last[-1]["elbo"], "kl_last_round": last[-1]["kl"],
             "sec_to_logZ_se_0.01": sec_to_se,
@@ -501,7 +509,8 @@ def measure_e2e(pr, eps0, beta0, steps, contraction):
     t0 = time.perf_counter()
     for _ in range(steps):
         run = oais.OAIS(pr, oais.MALA, N_PARTICLES, beta0, T_max=max(ROUNDS_T), eps=eps0, seed=99,
-                        adapt=True, data_on_device=False, contraction=contraction)
+                        adapt=True, data_on_device=False, contraction=contraction,
+                        exact_data=contraction != oais.CONTRACT_FP32)
         for k, T in enumerate(ROUNDS_T):
             run.round(ROUNDS_T[min(k + 1, len(ROUNDS_T) - 1)])
         run.logZ()

@@ -443,6 +443,19 @@ void oais_batch_destroy(oais_batch* b);
  * T_next to the nearest integer (at least T + 1 while T < T_cap).  Pure host arithmetic; OAIS_EINVAL for N, T < 1 or caps below them. */
 oais_status oais_budget(int64_t N, int32_t T, int64_t N_cap, int32_t T_cap, int64_t* N_next, int32_t* T_next);
 
+/* Final reweighting to the data X for the tensor-core forms (on = 1; 0 switches it off, the
+ * default).  Those forms sample the posterior of the rounded data X~ (bf16, or f16 of bf16, or
+ * FP8 with row scales), whose log Z differs from that of X by the quantisation shift.  With the
+ * reweighting each OAIS round appends one more target to its annealing sequence, gamma(.; X) at
+ * beta = 1 after gamma(.; X~), reached without a move: every particle's weight is multiplied
+ * by L(x_T; X) / L(x_T; X~), L(.; X) evaluated in fp32 on the CUDA cores (Alg. 1's
+ * incremental weight for that step), so log Z_hat estimates log Z of X and stays unbiased for Z.
+ * The round's moments, D_hat and next schedule are those of the beta path (the extra step is not
+ * part of it); log w and log L of oais_particles include the step, and its contribution to the
+ * KL estimate goes into the round result's kl (elbo covers the beta path).  EUNSUPPORTED for the
+ * CUDA-core form (which samples X already) and for d > 32 (no fp32 copy of X is kept). */
+oais_status oais_set_exact_data(oais_ctx* ctx, int32_t on);
+
 /* Active particle count of the next rounds (1 <= N <= the count the context was created
  * with; unsharded contexts): a round with more particles needs no new workspace as long as
  * the context was created with the largest count (Budget). */

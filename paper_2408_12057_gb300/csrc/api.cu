@@ -193,6 +193,7 @@ struct oais_ctx {
     int round = 0;
     int problem = 0;                     // problem index in the random-number tag
     double kappa = 0.0;                  // curvature estimate of -log L (step-size carry-over)
+    bool exact_data = false;             // tensor-core forms: reweight the final particles from X~ to X
     // test support (oais_arm_fault): a fault armed for the next round
     int fault_kind = 0;
     uint64_t fault_wait_ns = 0;
@@ -785,6 +786,13 @@ static oais_status run_round_impl(oais_ctx* ctx, int32_t T_next, bool asmc, doub
             CK(launch_sweep(dt, ctx->mv.kind, P, s));
         }
         CK(cudaEventRecord(ctx->ev1, s));
+        if (ctx->exact_data) {
+            // the last target of the sequence: gamma(.; X) instead of gamma(.; X~), reached from
+            // x_T with the incremental weight L(x_T; X) / L(x_T; X~) (fp32 CUDA-core evaluation of X)
+            PotentialParams pp{ctx->N, ctx->d_x, ctx->d_ell1, nullptr};
+            CK(ctx->dt.kind == kLogreg ? launch_potential_logreg(ctx->dt, pp, s) : launch_potential_linreg(ctx->dt, pp, s));
+            CK(launch_reweight_to_data(ctx->d_logw, ctx->d_ell, ctx->d_ell1, ctx->N, ctx->d_status, s));
+        }
         const int records = ctx->dt.tc ? tc_records(ctx->N)
                           : (ctx->dt.tcs ? tcs_tiles(ctx->N) : (ctx->dt.wide ? wide_tiles(ctx->N) : grid));
         CK(launch_merge_stats(ctx->d_parts, records, T,
@@ -1793,6 +1801,17 @@ oais_status oais_set_particles(oais_ctx* ctx, int64_t N)
     if (N < 1 || N > ctx->N_cap) return fail(ctx, OAIS_EINVAL, "N outside [1, the count the context was created with]");
     ctx->N = N;
     ctx->N_total = N;
+    return OAIS_OK;
+}
+
+oais_status oais_set_exact_data(oais_ctx* ctx, int32_t on)
+{
+    if (!ctx) return fail(nullptr, OAIS_EINVAL, "null ctx");
+    if (on && !(ctx->dt.tc || ctx->dt.tcs))
+        return fail(ctx, OAIS_EUNSUPPORTED, "the final reweighting applies to the tensor-core forms");
+    if (on && !(ctx->dt.D > 0 && ctx->dt.D <= 32 && (ctx->dt.kind == kLogreg || ctx->dt.kind == kLinreg)))
+        return fail(ctx, OAIS_EUNSUPPORTED, "the final reweighting needs the fp32 copy of X (d <= 32)");
+    ctx->exact_data = on != 0;
     return OAIS_OK;
 }
 

@@ -115,6 +115,10 @@ cudaError_t launch_zja_search(ZjaState* zs, const AsmcState* st, const StepParam
 cudaError_t launch_sweep_tc(const SweepParams& sp, const void* Ximg, const uint32_t* ybits, int n, int d,
                             float* grad_state, int* handed, cudaStream_t s);
 
+// log w += ell_x - ell, ell = ell_x (the final reweighting from X~ to X of the tensor-core forms)
+cudaError_t launch_reweight_to_data(double* logw, double* ell, const double* ell_x, int64_t N, unsigned* status,
+                                    cudaStream_t s);
+
 // records m as the calling thread's error text for calls without a context
 // (oais_last_error(NULL)) and returns s; the status is an oais_status value
 int fail_call(int s, const char* m);

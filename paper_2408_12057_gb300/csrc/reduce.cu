@@ -229,4 +229,28 @@ cudaError_t launch_fisher(const double* logw, const double* ell, const void* x, 
     return cudaGetLastError();
 }
 
+
+// The final reweighting of the tensor-core forms from the rounded data X~ to the data X (one more
+// target in the annealing sequence, the step from gamma(.; X~) to gamma(.; X) at beta = 1 with no
+// move, whose incremental weight is L(x_T; X) / L(x_T; X~)): log w_n += ell_x[n] - ell_n, then
+// ell_n = ell_x[n]; status bit 0 for a non-finite result.
+__global__ void reweight_to_data_kernel(double* __restrict__ logw, double* __restrict__ ell,
+                                        const double* __restrict__ ell_x, int64_t N, unsigned* status)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double lx = ell_x[n];
+    const double lw = logw[n] + (lx - ell[n]);
+    logw[n] = lw;
+    ell[n] = lx;
+    if (isnan(lw) || lw == INFINITY || isnan(lx) || lx == INFINITY) atomicOr(status, 1u);
+}
+
+cudaError_t launch_reweight_to_data(double* logw, double* ell, const double* ell_x, int64_t N, unsigned* status,
+                                    cudaStream_t s)
+{
+    reweight_to_data_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(logw, ell, ell_x, N, status);
+    return cudaGetLastError();
+}
+
 } // namespace oais

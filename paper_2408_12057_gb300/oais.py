@@ -108,6 +108,7 @@ def lib():
                 "oais_merge_shard_stats": ([i32, i32, P, P, P, P, P, P], i32),
                 "oais_default_step_sizes": ([P, i32, P, i32, P], i32),
                 "oais_arm_fault": ([P, i32, f64], i32),
+                "oais_set_exact_data": ([P, i32], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -178,7 +179,7 @@ class OAIS:
 
     def __init__(self, problem, move_kind, N, beta, T_max=None, eps=None, seed=12057, moves=1,
                  leapfrog=5, cycle=False, adapt=False, data_on_device=True, stream=None,
-                 contraction=CONTRACT_FP32):
+                 contraction=CONTRACT_FP32, exact_data=False):
         import torch
         self._torch = torch
         self.problem = problem
@@ -214,6 +215,8 @@ class OAIS:
                            self.N, _np_ptr(beta), T, self.T_max,
                            None if eps_arr is None else _np_ptr(eps_arr), int(seed),
                            _dptr(self.workspace), self.workspace.numel(), _stream_ptr(self.stream)))
+        if exact_data:
+            self.set_exact_data(True)
 
     def close(self):
         if getattr(self, "_borrowed", False):
@@ -226,6 +229,11 @@ class OAIS:
         """Active particle count of the next rounds (at most the count the run was created with)."""
         _check(lib().oais_set_particles(self._ctx, int(N)), self._ctx)
         self.N = int(N)
+
+    def set_exact_data(self, on=True):
+        """Tensor-core forms: reweight each round's final particles from the rounded data X~ to X
+        (oais_set_exact_data), so that log Z_hat estimates log Z of X."""
+        _check(lib().oais_set_exact_data(self._ctx, int(bool(on))), self._ctx)
 
     def arm_fault(self, kind, wait_seconds=0.0):
         """Test support: arm a host-side fault for the next round (oais_arm_fault):
