@@ -145,19 +145,14 @@ struct Eval {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) z[i][j] = 0.0f;
             const float* xrow = Xc + (RPT * rb) * L::kXS;
-            float4 xv[RPT], yv[4];
+            float4 xa[RPT], ya[4];
+            auto load_k = [&](int k, float4 (&xv)[RPT], float4 (&yv)[4]) {
 #pragma unroll
-            for (int i = 0; i < RPT; ++i) xv[i] = *reinterpret_cast<const float4*>(xrow + i * L::kXS);
+                for (int i = 0; i < RPT; ++i) xv[i] = *reinterpret_cast<const float4*>(xrow + i * L::kXS + k);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) yv[q] = *reinterpret_cast<const float4*>(Y + q * kTS + 4 * pb);
-#pragma unroll 2
-            for (int k = 0; k < DP; k += 4) {
-                float4 xn[RPT], yn[4];
-                const int kn = k + 4 < DP ? k + 4 : k;
-#pragma unroll
-                for (int i = 0; i < RPT; ++i) xn[i] = *reinterpret_cast<const float4*>(xrow + i * L::kXS + kn);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) yn[q] = *reinterpret_cast<const float4*>(Y + (kn + q) * kTS + 4 * pb);
+                for (int q = 0; q < 4; ++q) yv[q] = *reinterpret_cast<const float4*>(Y + (k + q) * kTS + 4 * pb);
+            };
+            auto fma_k = [&](const float4 (&xv)[RPT], const float4 (&yv)[4]) {
 #pragma unroll
                 for (int i = 0; i < RPT; ++i) {
                     const float fx[4] = {xv[i].x, xv[i].y, xv[i].z, xv[i].w};
@@ -167,10 +162,31 @@ struct Eval {
                         z[i][2] = fmaf(fx[q], yv[q].z, z[i][2]); z[i][3] = fmaf(fx[q], yv[q].w, z[i][3]);
                     }
                 }
+            };
+            load_k(0, xa, ya);
+            if constexpr (DP >= 256) {
+                // one tile per SM and the full register budget: two register sets of operands,
+                // used alternately (no copies between them)
+                float4 xb[RPT], yb[4];
+#pragma unroll 1
+                for (int k = 0; k < DP; k += 8) {
+                    load_k(k + 4, xb, yb);                 // DP is a multiple of 8
+                    fma_k(xa, ya);
+                    if (k + 8 < DP) load_k(k + 8, xa, ya);
+                    fma_k(xb, yb);
+                }
+            } else {
+                // two or three tiles per SM: one set, the next step's operands loaded ahead
+#pragma unroll 2
+                for (int k = 0; k < DP; k += 4) {
+                    float4 xn[RPT], yn[4];
+                    load_k(k + 4 < DP ? k + 4 : k, xn, yn);
+                    fma_k(xa, ya);
 #pragma unroll
-                for (int i = 0; i < RPT; ++i) xv[i] = xn[i];
+                    for (int i = 0; i < RPT; ++i) xa[i] = xn[i];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) yv[q] = yn[q];
+                    for (int q = 0; q < 4; ++q) ya[q] = yn[q];
+                }
             }
             // epilogue: rows past the data (stale buffer contents) are masked by selects
 #pragma unroll
@@ -209,16 +225,34 @@ struct Eval {
                     rr[0] = r0.x; rr[1] = r0.y; rr[2] = r0.z; rr[3] = r0.w;
                     rr[4] = r1.x; rr[5] = r1.y; rr[6] = r1.z; rr[7] = r1.w;
                 };
-                if (rows > 0) {
+                auto fma_row = [&](const float (&xv)[KB], const float (&rr)[kPW]) {
+#pragma unroll
+                    for (int a = 0; a < KB; ++a)
+#pragma unroll
+                        for (int b = 0; b < kPW; ++b) G[a][b] = fmaf(xv[a], rr[b], G[a][b]);
+                };
+                if (DP >= 256 && rows > 0) {
+                    // one tile per SM and the full register budget: two register sets of operands,
+                    // used alternately (no copies between them)
+                    float xa[KB], ra[kPW], xb[KB], rb2[kPW];
+                    load_row(0, xa, ra);
+                    int r = 0;
+#pragma unroll 1
+                    for (; r + 1 < rows; r += 2) {
+                        load_row(r + 1, xb, rb2);
+                        fma_row(xa, ra);
+                        if (r + 2 < rows) load_row(r + 2, xa, ra);
+                        fma_row(xb, rb2);
+                    }
+                    if (r < rows) fma_row(xa, ra);   // an odd last row
+                } else if (rows > 0) {
+                    // two or three tiles per SM: one set, the next row's operands loaded ahead
                     float xv[KB], rr[kPW];
                     load_row(0, xv, rr);
                     for (int r = 0; r < rows; ++r) {
                         float xn[KB], rn[kPW];
                         load_row(r + 1 < rows ? r + 1 : r, xn, rn);
-#pragma unroll
-                        for (int a = 0; a < KB; ++a)
-#pragma unroll
-                            for (int b = 0; b < kPW; ++b) G[a][b] = fmaf(xv[a], rr[b], G[a][b]);
+                        fma_row(xv, rr);
 #pragma unroll
                         for (int a = 0; a < KB; ++a) xv[a] = xn[a];
 #pragma unroll
@@ -339,9 +373,9 @@ __device__ __forceinline__ void load_tile(const float* Y, int warp, int lane, fl
     }
 }
 
-// CTAs per SM the register allocation must allow: the narrowest width holds fewer gradient
-// accumulators and fits three tiles per SM
-template <int DP> struct WideMinBlocks { static constexpr int value = DP <= 64 ? 3 : 1; };
+// CTAs per SM the register allocation must allow: two tiles per SM at d <= 64 (128 registers,
+// measured faster than three at 85 registers, which spill), one above
+template <int DP> struct WideMinBlocks { static constexpr int value = DP <= 64 ? 2 : 1; };
 
 template <int DP, bool LOGISTIC, int MOVE>
 __global__ void __launch_bounds__(kThreads, WideMinBlocks<DP>::value)
