@@ -782,14 +782,15 @@ def gmm_ops_per_particle_step(d, K, moves):
       Box-Muller: per pair of normals lg2, scale, sqrt, angle, sin, cos and two products;
       proposal x' = x + s z and |x'|^2 - |x|^2, two coordinates per packed instruction: 2 d;
       density: K d / 2 packed differences and K d / 2 packed square-accumulates, then per
-        component the pair sum, scale, max, shift, exp (2) and sum; one log; |x|^2 (d / 2);
+        component the pair sum, scale (to base-2 units), max, shift, ex2 and sum; one log;
+        |x|^2 (d / 2);
       the MH test: log u, compare, d selects;
       per step: the weight increment, the moments (3 x (offset, max, exp, sum)) and acceptance."""
     philox = moves * (-(-d // 4) + 1) * 10 * 4
     unif = moves * (d + 1) * 3
     bm = moves * d * 4
     prop = moves * 2 * d
-    dens = moves * (K * d + 7 * K + 1 + d // 2 + 4)
+    dens = moves * (K * d + 6 * K + 1 + d // 2 + 4)
     mh = moves * (2 + d)
     step = 30
     total = philox + unif + bm + prop + dens + mh + step

@@ -182,12 +182,18 @@ cudaError_t launch_one(const Tgt& tg, size_t smem, const PotentialParams& P, cud
 }
 
 // one family's dispatch over (move, width) for both kernel kinds
+// targets that carry the launch's random-number generator take it from the move configuration
+template <class TG, class P> inline void bind_rng(TG&, const P&) {}
+template <typename R, int D> inline void bind_rng(GmmTarget<R, D>& tg, const SweepParams& p) { tg.rks.set(p.mv.rng); }
+template <typename R, int D> inline void bind_rng(GmmTarget<R, D>& tg, const StepParams& p) { tg.rks.set(p.mv.rng); }
+
 #define OAIS_FAMILY_DISPATCH(FAM, MAKE, R, ...)                                                  \
     template <int D, class P, class... A>                                                        \
     static cudaError_t go(const DevTarget& t, int move, const P& prm, cudaStream_t s, A... a)   \
     {                                                                                            \
         size_t smem = 0;                                                                         \
         auto tg = MAKE<D>(t, &smem);                                                             \
+        bind_rng(tg, prm);                                                                       \
         using TG = decltype(tg);                                                                 \
         switch (move) {                                                                          \
         case kRwmh: return launch_one<TG, kRwmh, D, R>(tg, smem, prm, a..., s);                  \

@@ -76,6 +76,34 @@ struct Rng {
     }
 };
 
+// The same generator with its ten round keys precomputed on the host (k + r * W for the Weyl
+// constants W above): held in a kernel parameter, each round's key is a constant-bank operand
+// of the round's XOR instead of two additions per round and call.
+struct RngKS {
+    uint32_t k0[10], k1[10], tag;
+    __host__ __device__ void set(const Rng& r) {
+        for (int i = 0; i < 10; ++i) {
+            k0[i] = r.k0 + (uint32_t)i * 0x9E3779B9u;
+            k1[i] = r.k1 + (uint32_t)i * 0xBB67AE85u;
+        }
+        tag = r.tag;
+    }
+    __device__ __forceinline__ Philox4 block(uint32_t n, uint32_t t, uint32_t k, uint32_t j) const {
+        uint32_t c0 = n, c1 = t, c2 = (k << 16) | (j & 0xFFFFu), c3 = tag;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+            const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0[r], n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1[r];
+            c1 = (uint32_t)p1;
+            c3 = (uint32_t)p0;
+            c0 = n0;
+            c2 = n2;
+        }
+        Philox4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+        return o;
+    }
+};
+
 // u = ((r >> 9) + 1/2) 2^-23: the 23 bits as the mantissa of a float in [1, 2), minus
 // 1 - 2^-24 (an exact subtraction by Sterbenz's lemma), the same value as the conversion of
 // the integer, without an integer-to-float conversion
@@ -137,8 +165,8 @@ __device__ __forceinline__ void normals(const Rng& rng, uint32_t n, uint32_t t, 
     }
 }
 
-template <int D>
-__device__ __forceinline__ void normals_sfu(const Rng& rng, uint32_t n, uint32_t t, uint32_t k, int d, float (&z)[D])
+template <int D, class G>
+__device__ __forceinline__ void normals_sfu(const G& rng, uint32_t n, uint32_t t, uint32_t k, int d, float (&z)[D])
 {
 #pragma unroll
     for (int j = 0; j < (D + 3) / 4; ++j) {
@@ -156,7 +184,8 @@ __device__ __forceinline__ float mh_log_uniform(const Rng& rng, uint32_t n, uint
 }
 // the same with the special-function logarithm (relative error of order 1e-7; a decision can
 // differ from the exact form's only at a near tie): the random-walk moves of the fp32 forms
-__device__ __forceinline__ float mh_log_uniform_sfu(const Rng& rng, uint32_t n, uint32_t t, uint32_t k)
+template <class G>
+__device__ __forceinline__ float mh_log_uniform_sfu(const G& rng, uint32_t n, uint32_t t, uint32_t k)
 {
     return __logf(u01f(rng.block(n, t, k, 0xFFFFu).v[0]));
 }

@@ -80,8 +80,16 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
 {
     constexpr bool GRAD = (MOVE != kRwmh);
     R z[D];
-    if constexpr (kFp32<R> && MOVE == kRwmh) normals_sfu<D>(P.rng, n, t, k, d, z);
-    else normals<D>(P.rng, n, t, k, d, z);
+    if constexpr (kFp32<R> && MOVE == kRwmh && Tgt::kind == kGmm) {
+        // the mixture target carries the generator's precomputed round keys; at d = D the
+        // padding tests fold away
+        if (d == D) normals_sfu<D>(tg.rks, n, t, k, D, z);
+        else normals_sfu<D>(tg.rks, n, t, k, d, z);
+    } else if constexpr (kFp32<R> && MOVE == kRwmh) {
+        normals_sfu<D>(P.rng, n, t, k, d, z);
+    } else {
+        normals<D>(P.rng, n, t, k, d, z);
+    }
     R xp[D], glp[D];
     R log_alpha;
     R ellp;
@@ -158,7 +166,8 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
         log_alpha = -R(0.5) * dxx * inv_s2 + beta * (ellp - ell) - R(0.5) * (ke1 - ke0);
     }
     R logu;
-    if constexpr (kFp32<R> && MOVE == kRwmh) logu = mh_log_uniform_sfu(P.rng, n, t, k);
+    if constexpr (kFp32<R> && MOVE == kRwmh && Tgt::kind == kGmm) logu = mh_log_uniform_sfu(tg.rks, n, t, k);
+    else if constexpr (kFp32<R> && MOVE == kRwmh) logu = mh_log_uniform_sfu(P.rng, n, t, k);
     else logu = mh_log_uniform(P.rng, n, t, k, R(0));
     const bool acc = logu < log_alpha;
     if (acc) {

@@ -18,6 +18,8 @@ static GmmTarget<float, D> make_gmm(const DevTarget& t, size_t* smem)
                            + 0.5 * t.d * std::log(two_pi * t.ref_scale * t.ref_scale));
     tg.sm = nullptr;
     tg.fsched = t.fsched;
+    tg.c2 = (float)(-0.5 / t.p0 * 1.4426950408889634);
+    tg.rks = RngKS{};
     *smem = GmmTarget<float, D>::smem_bytes(t.n);
     return tg;
 }

@@ -98,6 +98,11 @@ struct GmmTarget {
     // (t = 0..T), beta_t - beta_{t-1} (rounded from its fp64 difference) at [T + t] and eps_t at
     // [2 T + t] (t = 1..T); the sweep reads them instead of converting the fp64 schedule per step
     const float* fsched;
+    // fp32 forms: -log2(e) / (2 v), the exponent factor of a component in base-2 units
+    float c2;
+    // the launch's random-number generator with its round keys precomputed (set per launch
+    // from the move configuration; the random-walk moves of the fp32 forms draw from it)
+    RngKS rks;
 
     static constexpr size_t smem_bytes(int K) { return sizeof(R) * (size_t)K * D; }
     __device__ void setup(unsigned char* smem) {
@@ -119,26 +124,35 @@ struct GmmTarget {
             if (k < K) {
                 R acc = 0;
                 if constexpr (kPair) {
+                    // two accumulator pairs (even and odd coordinate pairs): half the
+                    // dependent chain of multiply-adds
                     const float2* m2 = reinterpret_cast<const float2*>(sm + k * D);
-                    float2 a2 = make_float2(0.0f, 0.0f);
+                    float2 a2 = make_float2(0.0f, 0.0f), b2 = make_float2(0.0f, 0.0f);
 #pragma unroll
                     for (int i = 0; i < D / 2; ++i) {
                         const float2 r = sub_f32x2(make_float2(x[2 * i], x[2 * i + 1]), m2[i]);
-                        a2 = fma_f32x2(r, r, a2);
+                        if (i & 1) b2 = fma_f32x2(r, r, b2);
+                        else a2 = fma_f32x2(r, r, a2);
                     }
+                    if constexpr (D >= 4) a2 = add_f32x2(a2, b2);
                     acc = a2.x + a2.y;
+                    q[k] = acc * c2;                  // base-2 units
                 } else {
 #pragma unroll
                     for (int i = 0; i < D; ++i) { const R r = x[i] - sm[k * D + i]; acc += r * r; }
+                    q[k] = R(-0.5) * acc * inv_v;
                 }
-                q[k] = R(-0.5) * acc * inv_v;
                 mx = q[k] > mx ? q[k] : mx;
             }
         }
         R sum = 0, xx = 0;
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k)
-            if (k < K) { q[k] = exp_(q[k] - mx); sum += q[k]; }
+            if (k < K) {
+                if constexpr (kPair) q[k] = ex2_(q[k] - mx);
+                else q[k] = exp_(q[k] - mx);
+                sum += q[k];
+            }
         if constexpr (kPair) {
             float2 a2 = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -173,8 +187,11 @@ struct GmmTarget {
                 }
             }
         }
-        return mx + log_(sum) + log_const + R(0.5) * xx * inv_s2;
+        if constexpr (kPair) return 0.69314718055994531f * (mx + lg2_(sum)) + log_const + R(0.5) * xx * inv_s2;
+        else return mx + log_(sum) + log_const + R(0.5) * xx * inv_s2;
     }
+    __device__ static float ex2_(float v) { float y; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v)); return y; }
+    __device__ static float lg2_(float v) { float y; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v)); return y; }
     __device__ static float exp_(float v) { return __expf(v); }
     __device__ static double exp_(double v) { return exp(v); }
     __device__ static float log_(float v) { return __logf(v); }

@@ -18,10 +18,11 @@ def test_mixture_instruction_count():
     assert ops["uniforms"] == moves * 17 * 3
     assert ops["box_muller"] == moves * 16 * 4
     assert ops["proposal"] == moves * 32
-    # the density: K d / 2 packed differences + K d / 2 packed square-accumulates, 7 per
-    # component, one log, |x|^2 in d / 2 packed steps and 4 more
-    assert ops["density"] == moves * (K * d + 7 * K + 1 + d // 2 + 4)
-    assert ops["total"] == sum(v for k, v in ops.items() if k != "total") == 1154
+    # the density: K d / 2 packed differences + K d / 2 packed square-accumulates, 6 per
+    # component (the exponent scaled to base 2, so one ex2), one log, |x|^2 in d / 2 packed
+    # steps and 4 more
+    assert ops["density"] == moves * (K * d + 6 * K + 1 + d // 2 + 4)
+    assert ops["total"] == sum(v for k, v in ops.items() if k != "total") == 1138
 
 
 def test_logistic_flop_count():
