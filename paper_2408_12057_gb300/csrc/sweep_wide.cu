@@ -5,13 +5,14 @@
 // A CTA owns a tile of 64 particles for the whole sweep and runs Alg. 1 on it in lock-step:
 // every evaluation of log L and grad log L at the tile's 64 states is two fp32 contractions
 // on the CUDA cores over the data X, streamed through shared memory in chunks of 64 rows
-// (cp.async, double-buffered; 64 rows):
+// (cp.async, double-buffered):
 //   forward   Z[r][p] = sum_k X[r][k] Y[k][p]      (Y: the tile's states, in shared memory)
 //   epilogue  f = per-row log-likelihood term, R[r][p] = df/dz
 //   backward  G[k][p] += sum_r X[r][k] R[r][p]     (G: the gradients, in registers)
 // Each thread computes a 4 x 4 block of Z and an (DP/32) x 8 block of G, so both contractions
 // run at 8-16 fused multiply-adds per 16-byte shared-memory load, and loads the next step's
-// operands while the current step's multiply-adds run.  Particle vectors (positions,
+// operands while the current step's multiply-adds run (at d = 256 into a second register set,
+// the two sets alternating, so no copies between prefetched and current operands).  Particle vectors (positions,
 // gradients, momenta) live in device memory between evaluations, each thread touching only
 // its own elements; the per-particle sums of the Metropolis-Hastings ratios are warp
 // reductions; one moment record per (step, tile) as in the other forms.
