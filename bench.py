@@ -670,6 +670,7 @@ def line_batched(args, steps, warmup, compare_sequential):
     eps0 = np.stack([oais.default_step_sizes(pr, beta0, oais.MALA) for pr in probs])
     b = oais.OAISBatch(probs, oais.MALA, N, beta0, eps=eps0, seed=12057, stream=stream)
     tuned = b.autotune(T_probe=4)
+    shapes = [list(b.tile_shape(c)) for c in range(4)]   # (chunk rows, ring depth) per width class
 
     def set_all():
         for p in range(len(probs)):
@@ -702,7 +703,7 @@ def line_batched(args, steps, warmup, compare_sequential):
         "steps": steps, "warmup": warmup, "ms_per_step": total / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16 (bf16-valued X)", "data": "synthetic",
         "config": {"workload": "batched64_logreg_n500-50000_d8-128_N16384_T256x3_mala", "problems": len(probs),
-                   "rows_total": rows, "N_per_problem": N, "T": T, "rounds": R, "ring_depths_tuned": tuned,
+                   "rows_total": rows, "N_per_problem": N, "T": T, "rounds": R, "ring_depths_tuned": tuned, "tile_shapes_tuned": shapes,
                    "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": {"bound": "sfu or tensor per problem", "achieved_s": sweep_s,
                      "bound_s": t_bound, "frac": t_bound / sweep_s, "traffic": None,

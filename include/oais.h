@@ -417,11 +417,23 @@ oais_status oais_logsumexp_noalloc(const double* d_a, int64_t n, double* d_out, 
  *             oais_workspace_bytes with contraction OAIS_CONTRACT_BF16_TC_STREAM), or NULL:
  *             the batch allocates them
  *   results   [P] per-problem round results (may be NULL)
- * oais_batch_autotune times the ring depth of the streamed kernel (X chunk buffers in shared
- * memory) for each width class present (d_pad 16, 32, 64, 128) on that class's largest
- * problem over T_probe steps and keeps the fastest; chosen [4] receives the depths (0 =
- * class absent).  oais_batch_context lends problem p's context (owned by the batch) for the
- * per-problem queries (oais_logZ, oais_get_stats, oais_particles, ...).
+ * oais_batch_autotune chooses the tile shape of the batched kernel for each width class
+ * present (d_pad 16, 32, 64, 128; classes 0..3): it times the class's largest problem over
+ * T_probe steps through the batched kernel for every candidate pair of rows per X chunk (the
+ * K extent of the backward contraction and the N extent of the forward one: 64, and 32 for
+ * logistic problems with d_pad <= 64) and ring depth (X chunk buffers in shared memory: 2,
+ * 3, 4, 6, 8 as far as shared memory holds them), and keeps the fastest pair; chosen [4]
+ * receives the depths (0 = class absent).  The probe sweeps overwrite the problems' particle
+ * buffers (the next round redraws them).  The ring depth changes no result; the chunk size
+ * changes the order of the fp32 partial sums of log L (rows are split differently between a
+ * particle's two threads), so a run is reproducible for a given shape, and the shape the
+ * autotuner chose can be read and pinned:
+ * oais_batch_tile_shape writes the chunk rows and ring depth the class's problems run with
+ * (0, 0 for an absent class); oais_batch_set_tile_shape sets them (chunk_rows 0 = 64, stages
+ * 0 = the deepest ring that fits), OAIS_EUNSUPPORTED when a problem of the class cannot take
+ * the chunk size (linear regression, d_pad 128: their chunk images depend on it).
+ * oais_batch_context lends problem p's context (owned by the batch) for the per-problem
+ * queries (oais_logZ, oais_get_stats, oais_particles, ...).
  * Errors: OAIS_EINVAL / OAIS_EUNSUPPORTED for bad lists (mixed families, d > 128), the
  * single-context errors otherwise; oais_batch_last_error gives the detail.  No counterpart in
  * the paper: a way of running its method on many posteriors at once.
@@ -432,6 +444,8 @@ oais_status oais_batch_init(oais_batch** out, int32_t P, const oais_target* targ
                             uint64_t seed, void* const* workspaces, const size_t* ws_bytes, void* stream);
 oais_status oais_batch_round(oais_batch* b, int32_t T_next, oais_round_result* results);
 oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen);
+oais_status oais_batch_tile_shape(const oais_batch* b, int32_t width_class, int32_t* chunk_rows, int32_t* stages);
+oais_status oais_batch_set_tile_shape(oais_batch* b, int32_t width_class, int32_t chunk_rows, int32_t stages);
 oais_status oais_batch_context(oais_batch* b, int32_t p, oais_ctx** ctx);
 const char* oais_batch_last_error(const oais_batch* b);
 void oais_batch_destroy(oais_batch* b);

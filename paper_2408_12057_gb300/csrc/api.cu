@@ -1374,6 +1374,7 @@ struct oais_batch {
     cudaStream_t work = nullptr;          // the batch's own stream (captured; the default stream cannot be)
     cudaEvent_t ready = nullptr;
     int stages_class[4] = {0, 0, 0, 0};   // ring depth per d_pad class 16/32/64/128 (0: largest that fits)
+    int chunk_class[4] = {0, 0, 0, 0};    // rows per X chunk per class (0: the default, 64)
     int h = 2;                            // column split of the batched kernel
     std::vector<TcsPlan> plan;
     uint32_t off_misc = 0, smem = 0;
@@ -1425,9 +1426,10 @@ static void batch_plan(oais_batch* b)
     b->h = h;
     for (int p = 0; p < b->P; ++p) {
         const DevTarget& dt = b->ctx[p]->dt;
-        TcsPlan L = tcs_plan(dt.kind, dt.n, dt.d, 0, 0, false, h, dt.tcs_dp);
+        const int ch = b->chunk_class[dp_class(dt.tcs_dp)];
+        TcsPlan L = tcs_plan(dt.kind, dt.n, dt.d, ch, 0, false, h, dt.tcs_dp);
         const int want = b->stages_class[dp_class(L.dp)];
-        if (want > 0 && want < L.stages) L = tcs_plan(dt.kind, dt.n, dt.d, 0, want, false, h, dt.tcs_dp);
+        if (want > 0 && want < L.stages) L = tcs_plan(dt.kind, dt.n, dt.d, ch, want, false, h, dt.tcs_dp);
         b->plan[p] = L;
         top = std::max(top, L.off_x + (uint32_t)L.stages * L.stage_bytes);
     }
@@ -1481,8 +1483,10 @@ static oais_status batch_enqueue(oais_batch* b, int T)
     BK(cudaMemsetAsync(b->d_head, 0, sizeof(uint32_t), s));
     // external records: inside a captured graph a plain record only orders the capture
     BK(cudaEventRecordWithFlags(b->ev0, s, cudaEventRecordExternal));
+    bool chunk32 = false;
+    for (const TcsPlan& L : b->plan) chunk32 = chunk32 || L.chunk == 32;
     BK(launch_sweep_tcs_batch(b->kind, b->h, b->d_params, b->d_items, b->n_items, b->d_head, b->off_misc, b->smem,
-                              b->grid, s));
+                              b->grid, s, chunk32));
     BK(cudaEventRecordWithFlags(b->ev1, s, cudaEventRecordExternal));
     for (int p = 0; p < b->P; ++p) {
         oais_ctx* c = b->ctx[p];
@@ -1623,9 +1627,12 @@ oais_status oais_batch_round(oais_batch* b, int32_t T_next, oais_round_result* r
     return worst;
 }
 
-// Ring depth per width class, chosen by timing: for each class present, the largest problem
+// Tile shape per width class, chosen by timing: for each class present, the largest problem
 // of the class sweeps T_probe steps (its own data, a linear schedule, the first tiles of its
-// particles filling every SM once) at each candidate depth; the fastest depth is kept.
+// particles filling every SM once) through the batched kernel itself, for every candidate
+// (rows per X chunk, ring depth): chunks of 64 rows and, where the class's chunk images allow
+// it, of 32; ring depths 2, 3, 4, 6, 8 as far as shared memory holds them.  The fastest pair
+// is kept.  The probe runs on the problem's own particle buffers (the next round redraws them).
 oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
 {
     if (!b) return batch_fail(nullptr, OAIS_EINVAL, "null batch");
@@ -1633,6 +1640,14 @@ oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
     cudaStream_t s = b->work;
     BK(cudaEventRecord(b->ready, b->stream));
     BK(cudaStreamWaitEvent(s, b->ready, 0));
+    struct Scratch {
+        void* items = nullptr;
+        void* params = nullptr;
+        ~Scratch() { cudaFree(items); cudaFree(params); }
+    } tmp;
+    BK(cudaMalloc(&tmp.items, sizeof(uint2) * (size_t)b->grid));
+    BK(cudaMalloc(&tmp.params, b->pbytes));
+    std::vector<unsigned char> hp(b->pbytes);
     std::vector<double> sched(2 * (size_t)T_probe + 1);
     for (int t = 0; t <= T_probe; ++t) sched[t] = (double)t / T_probe;
     for (int c = 0; c < 4; ++c) {
@@ -1642,31 +1657,85 @@ oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
         if (chosen) chosen[c] = 0;
         if (best_p < 0) continue;
         oais_ctx* x = b->ctx[best_p];
+        const DevTarget& dt = x->dt;
         for (int t = 0; t < T_probe; ++t) sched[T_probe + 1 + t] = x->eps.empty() ? 0.01 : x->eps[0];
         BK(cudaMemcpyAsync(b->d_sched, sched.data(), sizeof(double) * sched.size(), cudaMemcpyHostToDevice, s));
         const int64_t Nprobe = std::min<int64_t>(x->N, (int64_t)b->grid * 128);
+        const int ptiles = tcs_tiles(Nprobe);
+        std::vector<uint2> items(ptiles);
+        for (int t = 0; t < ptiles; ++t) items[t] = make_uint2(0u, (uint32_t)t);   // the one parameter block
+        BK(cudaMemcpyAsync(tmp.items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice, s));
+        // every problem of the class must take the chunk size
+        std::vector<int> chunks = {64};
+        bool all32 = true;
+        for (int p = 0; p < b->P; ++p)
+            if (dp_class(b->plan[p].dp) == c) all32 = all32 && tcs_chunk_ok(b->ctx[p]->dt.kind, b->plan[p].dp, 32, false);
+        if (all32) chunks.push_back(32);
         float best_ms = 0.0f;
-        int best_S = 0;
-        const TcsPlan full = tcs_plan(x->dt.kind, x->dt.n, x->dt.d, 0, 0, false, b->h, x->dt.tcs_dp);
-        for (int S : {2, 3, 4, 6, 8}) {
-            if (S > full.stages) break;
-            const TcsPlan L = tcs_plan(x->dt.kind, x->dt.n, x->dt.d, 0, S, false, b->h, x->dt.tcs_dp);
-            SweepParams sp = make_params(x, T_probe, b->d_sched, b->d_sched + T_probe + 1, x->seed, 0xFFFFu, 0, Nprobe,
-                                         x->d_logw, x->d_ell, x->d_x, x->d_parts, b->d_status);
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
-                BK(cudaEventRecord(b->ev0, s));
-                BK(launch_sweep_tcs(L, x->dt.kind, sp, x->dt.tcs_img, x->dt.tcs_state, x->mv.kind, x->mv.leapfrog,
-                                    x->dt.p0, x->dt.n, x->dt.d, s));
-                BK(cudaEventRecord(b->ev1, s));
-                BK(cudaEventSynchronize(b->ev1));
-                BK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+        int best_S = 0, best_ch = 0;
+        for (int ch : chunks) {
+            const TcsPlan full = tcs_plan(dt.kind, dt.n, dt.d, ch, 0, false, b->h, dt.tcs_dp);
+            for (int S : {2, 3, 4, 6, 8}) {
+                if (S > full.stages) break;
+                const TcsPlan L = tcs_plan(dt.kind, dt.n, dt.d, ch, S, false, b->h, dt.tcs_dp);
+                if (!L.ok) continue;
+                const uint32_t off_misc = (L.off_x + (uint32_t)S * L.stage_bytes + 1023u) & ~1023u;
+                const uint32_t smem = off_misc + tcs_misc_bytes();
+                SweepParams sp = make_params(x, T_probe, b->d_sched, b->d_sched + T_probe + 1, x->seed, 0xFFFFu, 0,
+                                             Nprobe, x->d_logw, x->d_ell, x->d_x, x->d_parts, b->d_status);
+                tcs_batch_params(L, dt.kind, sp, dt.tcs_img, dt.tcs_state, x->mv.kind, x->mv.leapfrog, dt.p0, dt.n,
+                                 dt.d, off_misc, hp.data());
+                BK(cudaMemcpyAsync(tmp.params, hp.data(), b->pbytes, cudaMemcpyHostToDevice, s));
+                float ms = 0.0f;
+                for (int rep = 0; rep < 2; ++rep) {   // the first run warms up
+                    BK(cudaMemsetAsync(b->d_head, 0, sizeof(uint32_t), s));
+                    BK(cudaEventRecord(b->ev0, s));
+                    BK(launch_sweep_tcs_batch(b->kind, b->h, tmp.params, tmp.items, (uint32_t)ptiles, b->d_head,
+                                              off_misc, smem, std::min(b->grid, ptiles), s, ch == 32));
+                    BK(cudaEventRecord(b->ev1, s));
+                    BK(cudaEventSynchronize(b->ev1));
+                    BK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+                }
+                if (best_S == 0 || ms < best_ms) { best_ms = ms; best_S = S; best_ch = ch; }
             }
-            if (best_S == 0 || ms < best_ms) { best_ms = ms; best_S = S; }
         }
         b->stages_class[c] = best_S;
+        b->chunk_class[c] = best_ch == 64 ? 0 : best_ch;
         if (chosen) chosen[c] = best_S;
     }
+    batch_plan(b);
+    return OAIS_OK;
+}
+
+oais_status oais_batch_tile_shape(const oais_batch* b, int32_t width_class, int32_t* chunk_rows, int32_t* stages)
+{
+    if (!b || width_class < 0 || width_class > 3 || !chunk_rows || !stages)
+        return batch_fail(nullptr, OAIS_EINVAL, "bad batch, width class or output");
+    *chunk_rows = 0;
+    *stages = 0;
+    for (int p = 0; p < b->P; ++p)
+        if (dp_class(b->plan[p].dp) == width_class) {
+            *chunk_rows = b->plan[p].chunk;
+            *stages = b->plan[p].stages;
+            break;
+        }
+    return OAIS_OK;
+}
+
+oais_status oais_batch_set_tile_shape(oais_batch* b, int32_t width_class, int32_t chunk_rows, int32_t stages)
+{
+    if (!b) return batch_fail(nullptr, OAIS_EINVAL, "null batch");
+    if (width_class < 0 || width_class > 3) return batch_fail(b, OAIS_EINVAL, "width class out of range");
+    if (stages != 0 && (stages < 2 || stages > 8)) return batch_fail(b, OAIS_EINVAL, "ring depth out of range");
+    if (chunk_rows != 0 && chunk_rows != 32 && chunk_rows != 64) return batch_fail(b, OAIS_EINVAL, "chunk rows not 32 or 64");
+    for (int p = 0; p < b->P; ++p) {
+        if (dp_class(b->plan[p].dp) != width_class) continue;
+        const int ch = chunk_rows == 0 ? 64 : chunk_rows;
+        if (!tcs_chunk_ok(b->ctx[p]->dt.kind, b->plan[p].dp, ch, false))
+            return batch_fail(b, OAIS_EUNSUPPORTED, "problem " + std::to_string(p) + " cannot take that chunk size");
+    }
+    b->chunk_class[width_class] = chunk_rows == 64 ? 0 : chunk_rows;
+    b->stages_class[width_class] = stages;
     batch_plan(b);
     return OAIS_OK;
 }

@@ -57,6 +57,9 @@ struct TcsPlan {
 };
 // dp > 0 forces the padded width (a context keeps the width its chunk images were made for)
 TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8 = false, int h = 0, int dp = 0);
+// chunk rows a plan may take (the single-problem kernels: the default only; the batched kernel
+// also 32 for logistic problems with d_pad <= 64)
+bool tcs_chunk_ok(int kind, int dp, int chunk, bool q8);
 void tcs_prepare(const TcsPlan& L, int kind, const float* X, const float* y, int n, int d,
                  std::vector<unsigned char>& img);
 void tcs_prepare_q8(const TcsPlan& L, const float* X, const float* y, int n, int d, std::vector<unsigned char>& img);
@@ -76,7 +79,8 @@ uint32_t tcs_misc_bytes();
 void tcs_batch_params(const TcsPlan& L, int kind, const SweepParams& sp, const void* img, float* state, int move,
                       int leapfrog, double p0, int n, int d, uint32_t off_misc, void* out);
 cudaError_t launch_sweep_tcs_batch(int kind, int h, const void* d_params, const void* d_items, uint32_t n_items,
-                                   uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s);
+                                   uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s,
+                                   bool chunk32 = false);
 // ASMC on the streamed form: step t (t = 0: the draw from eta) of the whole population, with
 // the tiles' (log w, 2 log w) records in ess_parts; then the resampling test, scan and CDF of
 // asmc.cu (decide/scan/cdf, no gather) and launch_gather_tcs for the particle state

@@ -81,9 +81,17 @@ TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8, int h, 
     // 512 TMEM columns leave room for one CTA per SM: make the shared memory say so too
     if (L.tmem_cols == 512 && L.smem < 120u * 1024u) L.smem = 120u * 1024u;
     L.img_bytes = (size_t)L.nch * (q8 ? L.stage8_bytes : L.stage_bytes);
-    L.ok = L.dp <= 256 && L.chunk == tcs::chunk_rows(L.dp) && L.smem <= limit && L.stages >= 2 && L.stages <= 8 &&
-           L.h == 2;
+    L.ok = L.dp <= 256 && tcs_chunk_ok(kind, L.dp, L.chunk, q8) && L.smem <= limit && L.stages >= 2 &&
+           L.stages <= 8 && L.h == 2;
     return L;
+}
+
+bool tcs_chunk_ok(int kind, int dp, int chunk, bool q8)
+{
+    // 64 rows (32 at d_pad = 256 if so compiled); the batched launch also takes 32-row chunks
+    // for logistic problems with d_pad <= 64: their chunk images are the rows of X~ in order
+    // (one K slab, no y lines), so the same image serves both chunk sizes
+    return chunk == tcs::chunk_rows(dp) || (!q8 && kind == kLogreg && dp <= 64 && chunk == 32);
 }
 
 // X~ = f16(bf16(X)) in the stage layout (logistic: rows multiplied by the label sign), and y
@@ -174,6 +182,7 @@ static void fill_params(tcs::Params& P, const TcsPlan& L, int kind, const SweepP
     P.grad_pot = grad_pot;
     P.pstride = pstride;
     P.seg = tcs::kSegMmas / (L.chunk / 8);
+    P.chunk = L.chunk;
     P.img = static_cast<const unsigned char*>(img);
     const int tiles = tcs_tiles(sp.N);
     P.Np = state_particles > 0 ? state_particles : (int64_t)tiles * tcs::kTile;

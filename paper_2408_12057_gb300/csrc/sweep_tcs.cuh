@@ -70,10 +70,10 @@ __host__ __device__ constexpr int chunk_rows(int dp) { return dp >= 256 ? OAIS_T
 // operand for that term), D2 (gradient accumulator, d_pad columns).  The hi term of the
 // positions is the shared-memory A operand.  Two buffers (the forward of the next chunk runs
 // while the particle warps work on this one) wherever the 512 columns allow: d_pad <= 128.
-template <int DP>
+template <int DP, int CHR = chunk_rows(DP)>
 struct Cols {
     static constexpr int NB = DP <= 128 ? 2 : 1;
-    static constexpr int CH = chunk_rows(DP);
+    static constexpr int CH = CHR;
     static constexpr int D1 = 0, R = NB * CH, ALO = 2 * NB * CH;
     static constexpr int D2 = (ALO + DP / 2 + 31) / 32 * 32;
     static_assert(D2 + DP <= 512, "TMEM columns");
@@ -103,6 +103,7 @@ struct Params {
     int64_t Np;
     int seg;                    // chunks per gradient segment (see kSegMmas)
     int n, d, dp, nch, stages;
+    int chunk;                  // rows per chunk (the batched launch dispatches on it)
     uint32_t stage_bytes, y_off;   // f16 stage: lines, then y [64] and (FP8 storage) s [64]
     uint32_t off_x8, stage8_bytes; // FP8 storage: ring of chunk images (q rows, y, s)
     int stages8;
@@ -171,9 +172,10 @@ __device__ __forceinline__ void normals8(const Rng& rng, uint32_t n, uint32_t t,
     }
 }
 
-template <int DP, int H>
+template <int DP, int H, int CHR = chunk_rows(DP)>
 struct Thread {
-    static constexpr int CHUNK = chunk_rows(DP);
+    static constexpr int CHUNK = CHR;
+    using C = Cols<DP, CHR>;
     static constexpr int HC = CHUNK / H;   // columns of a chunk per thread
     static constexpr int DH = DP / H;      // coordinates per thread
     static constexpr int kEpi = Roles<H>::kEpiThreads;
@@ -213,7 +215,7 @@ struct Thread {
 #pragma unroll
         for (int j = 0; j < 4; ++j) split_pair_h(scale * v[2 * j], scale * v[2 * j + 1], hi[j], lo[j]);
         *reinterpret_cast<uint4*>(smem + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        tmem_st4(tmem + (uint32_t)(Cols<DP>::ALO + i0 / 2) + lane_off, lo);
+        tmem_st4(tmem + (uint32_t)(C::ALO + i0 / 2) + lane_off, lo);
     }
 
     __device__ void load_grad(int i0, float (&gv)[kSlice])
@@ -271,14 +273,14 @@ struct Thread {
         const int seg = P->seg;
         drained = false;
         for (int c = 0; c < nch; ++c, ++g) {
-            constexpr int NB = Cols<DP>::NB;
+            constexpr int NB = C::NB;
             const int b = NB == 2 ? (int)(g & 1u) : 0;
             const uint32_t ph = NB == 2 ? (g >> 1) & 1u : g & 1u;   // use count of buffer b
             wait(&M->d1full[b], ph);
             __syncwarp();
             tc_after_sync();
             uint32_t v[HC];
-            const uint32_t src = tmem + (uint32_t)(Cols<DP>::D1 + b * CHUNK + h * HC) + lane_off;
+            const uint32_t src = tmem + (uint32_t)(C::D1 + b * CHUNK + h * HC) + lane_off;
             if constexpr (HC == 16) tmem_ld16(src, v);
             else tmem_ld32(src, v);
             tmem_wait_ld();
@@ -339,7 +341,7 @@ struct Thread {
             wait(&M->rempty[b], ph ^ 1u);
             __syncwarp();
             tc_after_sync();
-            const uint32_t rcol = tmem + (uint32_t)(Cols<DP>::R + b * CHUNK + h * (HC / 2)) + lane_off;
+            const uint32_t rcol = tmem + (uint32_t)(C::R + b * CHUNK + h * (HC / 2)) + lane_off;
             if constexpr (HC == 32) {
                 tmem_st16(rcol, hi);
                 tmem_st16(rcol + CHUNK / 2, lo);
@@ -438,10 +440,10 @@ __device__ __forceinline__ void init_barriers(Misc* M, int stages, int prev_stag
 // One tile (128 particles) of one problem for a whole sweep, by all 352 threads of the CTA;
 // the barriers are fresh and TMEM (512 columns at `tmem`) is held by the caller.
 // FP8 -> f16 stage: row `row` of a chunk (q bytes to the swizzled f16 lines), its y and s
-template <int DP>
+template <int DP, int CHR = chunk_rows(DP)>
 __device__ __forceinline__ void convert_row(const unsigned char* src, unsigned char* dst, int row, uint32_t y_off)
 {
-    constexpr int CHUNK = chunk_rows(DP);
+    constexpr int CHUNK = CHR;
     constexpr KLayout LA = klayout(DP);
     const unsigned char* qrow = src + (uint32_t)row * DP;
 #pragma unroll 4
@@ -463,11 +465,12 @@ __device__ __forceinline__ void convert_row(const unsigned char* src, unsigned c
     yd[CHUNK + row] = yq[CHUNK + row];
 }
 
-template <int FAM, int DP, int Q8, int H>
+template <int FAM, int DP, int Q8, int H, int CHR = chunk_rows(DP)>
 __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_t tiles, unsigned char* smem,
                                          uint32_t tmem)
 {
-    constexpr int CHUNK = chunk_rows(DP);
+    constexpr int CHUNK = CHR;
+    using C = Cols<DP, CHR>;
     constexpr float kAScale = FAM == kLogreg ? 1.4426950408889634f : 1.0f;   // A operand scale
     const SweepParams& S = P.sp;
     Misc* M = reinterpret_cast<Misc*>(smem + P.off_misc);
@@ -476,8 +479,8 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
     const uint32_t nsteps = P.t_end >= P.t_begin ? (uint32_t)(P.t_end - P.t_begin + 1) : 0u;
     const uint32_t evals = P.x_in ? 1u : (P.resume ? 0u : 1u) + nsteps * (uint32_t)S.mv.K * (uint32_t)Le;
     const uint32_t total = evals * (uint32_t)P.nch;
-    const uint32_t D2 = tmem + (uint32_t)Cols<DP>::D2;
-    constexpr int NB = Cols<DP>::NB;
+    const uint32_t D2 = tmem + (uint32_t)C::D2;
+    constexpr int NB = C::NB;
     constexpr KLayout LA = klayout(DP);
     constexpr int kFwdWarp = Roles<H>::kFwdWarp, kLoadWarp = Roles<H>::kLoadWarp, kBwdWarp = Roles<H>::kBwdWarp;
     constexpr int kCvtWarp0 = Roles<H>::kCvtWarp0;
@@ -515,7 +518,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                 atomicOr(S.status, 2u);
                 break;
             }
-            convert_row<DP>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
+            convert_row<DP, CHR>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
                             lane, P.y_off);
             fence_proxy_async();   // the f16 stage, visible to the tensor core
             __syncwarp();
@@ -571,7 +574,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                 atomicOr(S.status, 2u);
                 break;
             }
-            convert_row<DP>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
+            convert_row<DP, CHR>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
                             32 + lane, P.y_off);
             fence_proxy_async();   // the f16 stage, visible to the tensor core
             __syncwarp();
@@ -602,14 +605,14 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                 // for the first chunk of an evaluation, the new positions in A.  The
                 // descriptors of the A bases take constant offsets (16-byte units) per K step.
                 const uint64_t adesc = sdesc(saddr(smem), 16, 8 * LA.lb, ca);
-                const uint32_t alo = tmem + (uint32_t)Cols<DP>::ALO;
+                const uint32_t alo = tmem + (uint32_t)C::ALO;
                 for (uint32_t g = 0, c = 0, e = 0; g < total; ++g) {
                     if ((c == 0 && !mbar_wait(saddr(&M->afull), e & 1u, &M->abort)) ||
                         !mbar_wait(saddr(&M->xfull[s]), ph, &M->abort) ||
                         !mbar_wait(saddr(&M->d1empty[NB == 2 ? g & 1u : 0u]), (NB == 2 ? (g >> 1) & 1u : g & 1u) ^ 1u,
                                    &M->abort)) { ok = false; break; }
                     const int b = NB == 2 ? (int)(g & 1u) : 0;
-                    const uint32_t d1 = tmem + (uint32_t)(Cols<DP>::D1 + b * CHUNK);
+                    const uint32_t d1 = tmem + (uint32_t)(C::D1 + b * CHUNK);
                     tc_after_sync();
                     const uint64_t xd = sdesc(xbase + (uint32_t)s * P.stage_bytes, 16, 8 * LA.lb, ca);
                     // the small (lo) term first, from TMEM: the running sum is small while it
@@ -645,7 +648,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                     if (first && c != 0) dph ^= 1u;
                     tc_after_sync();
                     const uint64_t xd = sdesc(xbase + (uint32_t)s * P.stage_bytes, CHUNK * LA.lb, 8 * LA.lb, ca);
-                    const uint32_t ra = tmem + (uint32_t)(Cols<DP>::R + b * CHUNK);
+                    const uint32_t ra = tmem + (uint32_t)(C::R + b * CHUNK);
 #pragma unroll
                     for (int term = 0; term < 2; ++term) {
 #pragma unroll
@@ -669,7 +672,7 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
         }
     } else {
         // ---------------- particle warps ----------------
-        Thread<DP, H> Th;
+        Thread<DP, H, CHR> Th;
         Th.smem = smem;
         Th.M = M;
         Th.P = &P;

@@ -10,7 +10,9 @@ namespace tcs {
 // from a queue ordered by decreasing cost (longest first) until it is empty.  All problems
 // share the family; their widths may differ (the item picks the instantiation).  Every
 // problem's Misc region sits at the same offset (the launch's largest).
-template <int FAM, int H>
+// ALT: some problems run 32-row chunks (a separate instantiation, so that the default one
+// keeps its register allocation)
+template <int FAM, int H, bool ALT>
 __global__ void __launch_bounds__(Roles<H>::threads(0), 1)
 oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __restrict__ items, uint32_t n_items,
                             uint32_t* head, uint32_t off_misc)
@@ -47,10 +49,28 @@ oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __res
         if (it >= n_items) break;
         const uint32_t tile = items[it].y;
         const uint32_t tiles = (uint32_t)((sP.sp.N + kTile - 1) / kTile);
+        // the item's width and chunk rows pick the instantiation: 64-row chunks, or (logistic,
+        // d_pad <= 64, whose chunk images do not depend on the chunk size) 32-row chunks
+        const bool ch32 = sP.chunk == 32;
         switch (sP.dp) {
-        case 16: if constexpr (16 / H >= 8) run_tile<FAM, 16, 0, H>(sP, tile, tiles, smem, tmem); break;
-        case 32: if constexpr (32 / H >= 8) run_tile<FAM, 32, 0, H>(sP, tile, tiles, smem, tmem); break;
-        case 64: if constexpr (64 / H >= 8) run_tile<FAM, 64, 0, H>(sP, tile, tiles, smem, tmem); break;
+        case 16:
+            if constexpr (16 / H >= 8) {
+                if constexpr (ALT && FAM == kLogreg) { if (ch32) { run_tile<FAM, 16, 0, H, 32>(sP, tile, tiles, smem, tmem); break; } }
+                run_tile<FAM, 16, 0, H>(sP, tile, tiles, smem, tmem);
+            }
+            break;
+        case 32:
+            if constexpr (32 / H >= 8) {
+                if constexpr (ALT && FAM == kLogreg) { if (ch32) { run_tile<FAM, 32, 0, H, 32>(sP, tile, tiles, smem, tmem); break; } }
+                run_tile<FAM, 32, 0, H>(sP, tile, tiles, smem, tmem);
+            }
+            break;
+        case 64:
+            if constexpr (64 / H >= 8) {
+                if constexpr (ALT && FAM == kLogreg) { if (ch32) { run_tile<FAM, 64, 0, H, 32>(sP, tile, tiles, smem, tmem); break; } }
+                run_tile<FAM, 64, 0, H>(sP, tile, tiles, smem, tmem);
+            }
+            break;
         case 128: if constexpr (H == 2) run_tile<FAM, 128, 0, H>(sP, tile, tiles, smem, tmem); break;
         default: if (threadIdx.x == 0) atomicOr(sP.sp.status, 8u);
         }
@@ -68,7 +88,8 @@ oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __res
 } // namespace tcs
 
 cudaError_t launch_sweep_tcs_batch(int kind, int h, const void* d_params, const void* d_items, uint32_t n_items,
-                                   uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s)
+                                   uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s,
+                                   bool chunk32)
 {
     auto go = [&](auto kern, int threads) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -78,8 +99,12 @@ cudaError_t launch_sweep_tcs_batch(int kind, int h, const void* d_params, const 
         return cudaGetLastError();
     };
     if (h != 2) return cudaErrorInvalidValue;
-    if (kind == kLinreg) return go(tcs::oais_sweep_tcs_batch_kernel<kLinreg, 2>, tcs::Roles<2>::threads(0));
-    return go(tcs::oais_sweep_tcs_batch_kernel<kLogreg, 2>, tcs::Roles<2>::threads(0));
+    if (kind == kLinreg) {
+        if (chunk32) return cudaErrorInvalidValue;
+        return go(tcs::oais_sweep_tcs_batch_kernel<kLinreg, 2, false>, tcs::Roles<2>::threads(0));
+    }
+    if (chunk32) return go(tcs::oais_sweep_tcs_batch_kernel<kLogreg, 2, true>, tcs::Roles<2>::threads(0));
+    return go(tcs::oais_sweep_tcs_batch_kernel<kLogreg, 2, false>, tcs::Roles<2>::threads(0));
 }
 
 } // namespace oais

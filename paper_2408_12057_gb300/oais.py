@@ -99,6 +99,8 @@ def lib():
                 "oais_batch_init": ([P, i32, P, P, i64, P, i32, i32, P, u64, P, P, P], i32),
                 "oais_batch_round": ([P, i32, P], i32),
                 "oais_batch_autotune": ([P, i32, P], i32),
+                "oais_batch_tile_shape": ([P, i32, P, P], i32),
+                "oais_batch_set_tile_shape": ([P, i32, i32, i32], i32),
                 "oais_batch_context": ([P, i32, P], i32),
                 "oais_batch_last_error": ([P], ctypes.c_char_p),
                 "oais_batch_destroy": ([P], None),
@@ -581,10 +583,21 @@ class OAISBatch:
         return [{f: getattr(r, f) for f, _ in _RoundResult._fields_ if f != "pad"} for r in res]
 
     def autotune(self, T_probe=4):
-        """Time the X-ring depth per width class (d_pad 16/32/64/128); returns the chosen depths."""
+        """Time the tile shapes (rows per X chunk, ring depth) per width class (d_pad 16/32/64/128)
+        and keep the fastest; returns the chosen depths (tile_shape gives the whole shape)."""
         chosen = (ctypes.c_int32 * 4)()
         self._check(lib().oais_batch_autotune(self._b, int(T_probe), chosen))
         return list(chosen)
+
+    def tile_shape(self, width_class):
+        """(rows per X chunk, ring depth) of a width class (0: d_pad 16 ... 3: d_pad 128); (0, 0) if absent."""
+        ch, st = ctypes.c_int32(), ctypes.c_int32()
+        self._check(lib().oais_batch_tile_shape(self._b, int(width_class), ctypes.byref(ch), ctypes.byref(st)))
+        return ch.value, st.value
+
+    def set_tile_shape(self, width_class, chunk_rows=0, stages=0):
+        """Pin a width class's tile shape (0: the default chunk of 64 rows, the deepest ring)."""
+        self._check(lib().oais_batch_set_tile_shape(self._b, int(width_class), int(chunk_rows), int(stages)))
 
     def problem(self, p):
         return self._views[p]

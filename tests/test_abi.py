@@ -92,3 +92,10 @@ def test_budget_rule():
                     (4096, 2056), (4096, 4096)]
     with pytest.raises(Exception):
         oais.budget(0, 10, 100, 100)
+
+
+def test_batch_tile_shape_calls_validate_without_a_gpu():
+    L = oais.lib()
+    ch, st = ctypes.c_int32(7), ctypes.c_int32(7)
+    assert L.oais_batch_tile_shape(None, 0, ctypes.byref(ch), ctypes.byref(st)) == 1   # OAIS_EINVAL
+    assert L.oais_batch_set_tile_shape(None, 0, 32, 0) == 1

@@ -4,7 +4,8 @@ Every problem of a batch is the same computation as a single streamed context wi
 problem index (random-number tag round | p << 16), so: each problem agrees with the FP64
 oracle on X~ = f16(bf16(X)) particle by particle (the tolerances of the streamed form), and
 with the single-context run bit for bit, in the first round and in later rounds replayed
-from the captured graph; the ring-depth autotuner changes no result.
+from the captured graph; the ring depth changes no result, and a tile shape the autotuner
+chose gives the same bits when pinned.
 """
 import numpy as np
 import pytest
@@ -92,7 +93,47 @@ def test_batch_equals_single_contexts_over_rounds():
     b.close()
 
 
-def test_batch_autotune_keeps_results():
+def width_class(d):
+    return 0 if d <= 16 else 1 if d <= 32 else 2 if d <= 64 else 3
+
+
+def test_batch_chunk32_matches_oracle_per_problem():
+    # 32-row chunks for the classes d_pad 16, 32, 64 and the default 64 rows for d_pad 128 in
+    # the same launch: every problem still agrees with the oracle particle by particle
+    probs = mixed_problems()
+    N, T = 300, 3
+    beta = W.linear_schedule(T) ** 3
+    eps = np.stack([oais.default_step_sizes(pr, beta, oais.MALA) for pr in probs])
+    b = oais.OAISBatch(probs, oais.MALA, N, beta, eps=eps, seed=31)
+    for c in (0, 1, 2):
+        b.set_tile_shape(c, chunk_rows=32)
+        assert b.tile_shape(c)[0] == 32 and b.tile_shape(c)[1] >= 2
+    assert b.tile_shape(3)[0] == 64
+    with pytest.raises(oais.OAISError):
+        b.set_tile_shape(3, chunk_rows=32)   # d_pad 128: two K slabs, the image depends on the chunk
+    res = b.round(T)
+    for p, pr in enumerate(probs):
+        g = view(b.problem(p))
+        r = o.asmc(oracle_target(pr), o.MALA, N, beta, eps[p], 31, tag=p << 16)
+        ok = agree(g, r)
+        assert ok.mean() >= 0.9
+        assert res[p]["logZ"] == pytest.approx(float(np.logaddexp.reduce(g["logw"]) - np.log(N)), rel=1e-12)
+    b.close()
+
+
+def test_batch_linreg_refuses_chunk32():
+    probs = [W.linreg(n=300, d=16, seed=3), W.linreg(n=200, d=32, seed=4)]
+    beta = W.linear_schedule(2)
+    b = oais.OAISBatch(probs, oais.HMC, 128, beta, seed=3, leapfrog=2)
+    with pytest.raises(oais.OAISError):
+        b.set_tile_shape(0, chunk_rows=32)   # the chunk images carry y per chunk
+    assert b.tile_shape(0)[0] == 64
+    b.close()
+
+
+def test_batch_autotune_shape_is_reproducible():
+    # the autotuner's tile shapes, pinned on a fresh batch, give the same bits; classes that
+    # kept 64-row chunks give the bits of an untuned batch (the ring depth changes no result)
     probs = mixed_problems()
     N, T = 512, 3
     beta = W.linear_schedule(T) ** 3
@@ -102,12 +143,24 @@ def test_batch_autotune_keeps_results():
     b = oais.OAISBatch(probs, oais.MALA, N, beta, seed=5)
     chosen = b.autotune(T_probe=2)
     assert all(c == 0 or 2 <= c <= 8 for c in chosen) and any(c > 0 for c in chosen)
+    shapes = [b.tile_shape(c) for c in range(4)]
+    for c, (ch, st) in enumerate(shapes):
+        present = any(width_class(pr.d) == c for pr in probs)
+        assert (ch in (32, 64) and st == chosen[c]) if present else (ch, st) == (0, 0)
     rb = b.round(T)
-    for p in range(len(probs)):
-        assert np.array_equal(la[p], view(b.problem(p))["logw"])
-        assert ra[p]["logZ"] == rb[p]["logZ"]
+    lb = [view(b.problem(p))["logw"] for p in range(len(probs))]
+    c2 = oais.OAISBatch(probs, oais.MALA, N, beta, seed=5)
+    for c, (ch, st) in enumerate(shapes):
+        if ch:
+            c2.set_tile_shape(c, ch, st)
+    rc = c2.round(T)
+    for p, pr in enumerate(probs):
+        assert np.array_equal(lb[p], view(c2.problem(p))["logw"]) and rb[p]["logZ"] == rc[p]["logZ"]
+        if shapes[width_class(pr.d)][0] == 64:
+            assert np.array_equal(la[p], lb[p]) and ra[p]["logZ"] == rb[p]["logZ"]
     a.close()
     b.close()
+    c2.close()
 
 
 def test_batch_linreg_hmc():
