@@ -179,12 +179,13 @@ __device__ __forceinline__ bool mh_move(const Tgt& tg, const MoveCfg& P, R (&x)[
 }
 
 // CTAs per SM that the register allocation must allow (0: the compiler's choice).  The
-// random-walk step of the mixture is cheap and latency-bound: the sweep ran fastest at 6 CTAs
-// (24.5 ms for T = 256 at N = 2^20, 80 registers; 24.9 ms at 8 CTAs and 64 registers; an
-// explicit 1 gave 122 registers and 30 % slower), the lock-step ASMC kernel of the same step at
-// 8 (a T = 256 round in 44.1 ms; 46.1 at 6, 53.0 with the compiler's 92 registers).
+// random-walk step of the mixture is cheap and latency-bound: the sweep runs fastest at 5 CTAs
+// (96 registers: 1.445e10 particle-steps/s on the mixture workload, 1.398e10 at 6 CTAs and 80
+// registers, 1.401e10 at 8 and 64; an explicit 1 gave 122 registers and 30 % less), the
+// lock-step ASMC kernel of the same step at 8 (a T = 256 round in 44.1 ms; 46.1 at 6, 53.0
+// with the compiler's 92 registers).
 template <class Tgt, int MOVE> struct SweepMinBlocks { static constexpr int value = 0; };
-template <typename R, int D> struct SweepMinBlocks<GmmTarget<R, D>, kRwmh> { static constexpr int value = 6; };
+template <typename R, int D> struct SweepMinBlocks<GmmTarget<R, D>, kRwmh> { static constexpr int value = 5; };
 template <class Tgt, int MOVE> struct StepMinBlocks { static constexpr int value = 0; };
 template <typename R, int D> struct StepMinBlocks<GmmTarget<R, D>, kRwmh> { static constexpr int value = 8; };
 

@@ -104,10 +104,16 @@ struct GmmTarget {
     // from the move configuration; the random-walk moves of the fp32 forms draw from it)
     RngKS rks;
 
-    static constexpr size_t smem_bytes(int K) { return sizeof(R) * (size_t)K * D; }
+    // fp32 forms take the components two at a time (one test of K per pair, and the two
+    // components' instructions can interleave); an odd K gets a dummy component whose mean lies
+    // so far away (1e18 in every coordinate) that its weight is exactly 0: its exponent is
+    // about -1e37, whose ex2 is +0, so sums, maxima and the gradient are unchanged bit for bit
+    static constexpr int kGroup = (sizeof(R) == 4 && D % 2 == 0) ? 2 : 1;
+    static constexpr size_t smem_bytes(int K) { return sizeof(R) * (size_t)((K + kGroup - 1) / kGroup * kGroup) * D; }
     __device__ void setup(unsigned char* smem) {
         R* s = reinterpret_cast<R*>(smem);
-        for (int i = threadIdx.x; i < K * D; i += blockDim.x) s[i] = means[i];
+        const int Kg = (K + kGroup - 1) / kGroup * kGroup;
+        for (int i = threadIdx.x; i < Kg * D; i += blockDim.x) s[i] = i < K * D ? means[i] : R(1e18);
         sm = s;
         __syncthreads();
     }
@@ -117,11 +123,15 @@ struct GmmTarget {
         // fp32: the squared distances, |x|^2 and the gradient's mixture sums two coordinates
         // per packed instruction (even and odd coordinates summed apart, then added)
         constexpr bool kPair = sizeof(R) == 4 && D % 2 == 0;
+        constexpr int G = kGroup;
+        const int Kg = (K + G - 1) / G * G;
         R q[kMaxK];
         R mx = R(-INFINITY);
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k) {
-            if (k < K) {
+        for (int k0 = 0; k0 < kMaxK; k0 += G) {
+            if (k0 < Kg) {
+#pragma unroll
+            for (int k = k0; k < k0 + G; ++k) {
                 R acc = 0;
                 if constexpr (kPair) {
                     // two accumulator pairs (even and odd coordinate pairs): half the
@@ -144,14 +154,18 @@ struct GmmTarget {
                 }
                 mx = q[k] > mx ? q[k] : mx;
             }
+            }
         }
         R sum = 0, xx = 0;
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k)
-            if (k < K) {
-                if constexpr (kPair) q[k] = ex2_(q[k] - mx);
-                else q[k] = exp_(q[k] - mx);
-                sum += q[k];
+        for (int k0 = 0; k0 < kMaxK; k0 += G)
+            if (k0 < Kg) {
+#pragma unroll
+                for (int k = k0; k < k0 + G; ++k) {
+                    if constexpr (kPair) q[k] = ex2_(q[k] - mx);
+                    else q[k] = exp_(q[k] - mx);
+                    sum += q[k];
+                }
             }
         if constexpr (kPair) {
             float2 a2 = make_float2(0.0f, 0.0f);
@@ -173,7 +187,7 @@ struct GmmTarget {
                     float2 a2 = make_float2(0.0f, 0.0f);
 #pragma unroll
                     for (int k = 0; k < kMaxK; ++k)
-                        if (k < K) a2 = fma_f32x2(make_float2(q[k], q[k]), reinterpret_cast<const float2*>(sm + k * D)[i], a2);
+                        if (k < Kg) a2 = fma_f32x2(make_float2(q[k], q[k]), reinterpret_cast<const float2*>(sm + k * D)[i], a2);
                     g[2 * i] = (a2.x * inv - x[2 * i]) * inv_v + x[2 * i] * inv_s2;
                     g[2 * i + 1] = (a2.y * inv - x[2 * i + 1]) * inv_v + x[2 * i + 1] * inv_s2;
                 }
