@@ -10,6 +10,8 @@
 //             particles copied to the other buffer, w = 1.
 // Every kernel after `decide` reads the device flag `pend` and returns at once when the
 // step does not resample, so a whole schedule is launched without host round-trips.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace oais {
@@ -173,18 +175,24 @@ __device__ __forceinline__ double block_scan_inclusive(double (&v)[kScanItems], 
     return sh[kScanThreads - 1];
 }
 
+// The block-sum, CDF and gather kernels run on every step and return at once unless the step
+// resamples: their grids are capped at a few CTAs per SM (tiles and particles taken
+// grid-stride), so that a step without resampling does not schedule thousands of empty CTAs.
 __global__ void __launch_bounds__(kScanThreads)
-asmc_blocksum_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N, double* bsum)
+asmc_blocksum_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N, int nb, double* bsum)
 {
     if (!st->pend) return;
     __shared__ double sh[kScanThreads];
     const double lse = st->lse;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    double v[kScanItems];
+    for (int tile = blockIdx.x; tile < nb; tile += gridDim.x) {
+        const int64_t base = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+        double v[kScanItems];
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) v[i] = base + i < N ? exp(logw[base + i] - lse) : 0.0;
-    const double tot = block_scan_inclusive(v, sh);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+        for (int i = 0; i < kScanItems; ++i) v[i] = base + i < N ? exp(logw[base + i] - lse) : 0.0;
+        const double tot = block_scan_inclusive(v, sh);
+        if (threadIdx.x == 0) bsum[tile] = tot;
+        __syncthreads();                 // sh is reused by the next tile's scan
+    }
 }
 
 // exclusive scan of the block sums by one CTA, in chunks of kScanTile; boff[nb] = total
@@ -210,30 +218,29 @@ asmc_offsets_kernel(const AsmcState* st, const double* __restrict__ bsum, int nb
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-asmc_cdf_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N,
+asmc_cdf_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N, int nb,
                 const double* __restrict__ boff, double* cdf)
 {
     if (!st->pend) return;
     __shared__ double sh[kScanThreads];
-    const double lse = st->lse;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    double v[kScanItems];
+    const double lse = st->lse, total = boff[nb];
+    for (int tile = blockIdx.x; tile < nb; tile += gridDim.x) {
+        const int64_t base = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+        double v[kScanItems];
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) v[i] = base + i < N ? exp(logw[base + i] - lse) : 0.0;
-    block_scan_inclusive(v, sh);
-    const double off = boff[blockIdx.x], total = boff[gridDim.x];
+        for (int i = 0; i < kScanItems; ++i) v[i] = base + i < N ? exp(logw[base + i] - lse) : 0.0;
+        block_scan_inclusive(v, sh);
+        const double off = boff[tile];
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) if (base + i < N) cdf[base + i] = (off + v[i]) / total;
+        for (int i = 0; i < kScanItems; ++i) if (base + i < N) cdf[base + i] = (off + v[i]) / total;
+        __syncthreads();                 // sh is reused by the next tile's scan
+    }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256)
-asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const double* __restrict__ cdf,
-                   int64_t* ancestors)
+__device__ __forceinline__ void gather_one(const AsmcState* st, const StepParams& P, int d, int grad,
+                                           const double* __restrict__ cdf, int64_t* ancestors, int64_t n)
 {
-    if (!st->pend) return;
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= P.N) return;
     const double thr = ((double)n + st->U) / (double)P.N;
     // a = min{m : C_m > thr}, clamped to N - 1
     int64_t lo = 0, hi = P.N - 1;
@@ -256,6 +263,28 @@ asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const dou
     if (ancestors) ancestors[n] = a;
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256)
+asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const double* __restrict__ cdf,
+                   int64_t* ancestors)
+{
+    if (!st->pend) return;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < P.N; n += (int64_t)gridDim.x * blockDim.x)
+        gather_one<R>(st, P, d, grad, cdf, ancestors, n);
+}
+
+int capped_grid(int64_t want, int per_sm)
+{
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0)
+            sms = 152;
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
+}
+
 cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int nparts, double ess_frac, double* bsum,
                                     double* boff, double* cdf, double* ess_trace, int* resampled, cudaStream_t s)
 {
@@ -263,10 +292,10 @@ cudaError_t launch_asmc_decide_scan(AsmcState* st, const StepParams& P, int npar
     StepPartial* groups = P.ess_parts + nparts;   // the buffer holds nparts pieces, then the groups
     asmc_ess_decide_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups, st, P.t, P.T, P.beta, ess_frac,
                                                     P.N, P.mv.rng, ess_trace, resampled, P.skip);
-    const int nb = scan_blocks(P.N);
-    asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
+    const int nb = scan_blocks(P.N), gs = capped_grid(nb, 2);
+    asmc_blocksum_kernel<<<gs, kScanThreads, 0, s>>>(st, P.logw, P.N, nb, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);
-    asmc_cdf_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, boff, cdf);
+    asmc_cdf_kernel<<<gs, kScanThreads, 0, s>>>(st, P.logw, P.N, nb, boff, cdf);
     return cudaGetLastError();
 }
 
@@ -278,11 +307,11 @@ cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts,
     StepPartial* groups = P.ess_parts + nparts;   // the buffer holds nparts pieces, then the groups
     asmc_ess_decide_kernel<<<ng, kEssGroup, 0, s>>>(P.ess_parts, nparts, groups, st, P.t, P.T, P.beta, ess_frac,
                                                     P.N, P.mv.rng, ess_trace, resampled, P.skip);
-    const int nb = scan_blocks(P.N);
-    asmc_blocksum_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, bsum);
+    const int nb = scan_blocks(P.N), gs = capped_grid(nb, 2);
+    asmc_blocksum_kernel<<<gs, kScanThreads, 0, s>>>(st, P.logw, P.N, nb, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);
-    asmc_cdf_kernel<<<nb, kScanThreads, 0, s>>>(st, P.logw, P.N, boff, cdf);
-    const int gb = (int)((P.N + 255) / 256);
+    asmc_cdf_kernel<<<gs, kScanThreads, 0, s>>>(st, P.logw, P.N, nb, boff, cdf);
+    const int gb = capped_grid((P.N + 255) / 256, 4);
     if (fp64) asmc_gather_kernel<double><<<gb, 256, 0, s>>>(st, P, d, grad ? 1 : 0, cdf, ancestors);
     else      asmc_gather_kernel<float><<<gb, 256, 0, s>>>(st, P, d, grad ? 1 : 0, cdf, ancestors);
     return cudaGetLastError();

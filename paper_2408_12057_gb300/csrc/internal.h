@@ -57,6 +57,9 @@ struct TcsPlan {
 };
 // dp > 0 forces the padded width (a context keeps the width its chunk images were made for)
 TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8 = false, int h = 0, int dp = 0);
+// grid of a per-step kernel that usually returns at once (the resampling kernels): at most
+// per_sm CTAs per SM, the work taken grid-stride
+int capped_grid(int64_t want, int per_sm);
 // chunk rows a plan may take (the single-problem kernels: the default only; the batched kernel
 // also 32 for logistic problems with d_pad <= 64)
 bool tcs_chunk_ok(int kind, int dp, int chunk, bool q8);

@@ -318,21 +318,21 @@ tcs_gather_kernel(const AsmcState* st, const double* __restrict__ cdf, int64_t N
                   const double* __restrict__ ell, double* ell_s, double* logw, int64_t* ancestors)
 {
     if (!st->pend) return;
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const double thr = ((double)n + st->U) / (double)N;
-    int64_t lo = 0, hi = N - 1;   // a = min{m : C_m > thr}, clamped to N - 1
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (cdf[mid] > thr) hi = mid; else lo = mid + 1;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const double thr = ((double)n + st->U) / (double)N;
+        int64_t lo = 0, hi = N - 1;   // a = min{m : C_m > thr}, clamped to N - 1
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cdf[mid] > thr) hi = mid; else lo = mid + 1;
+        }
+        for (int i = 0; i < dp; ++i) {
+            xs[(int64_t)i * Np + n] = xa[(int64_t)i * Np + lo];
+            gs[(int64_t)i * Np + n] = ga[(int64_t)i * Np + lo];
+        }
+        ell_s[n] = ell[lo];
+        logw[n] = 0.0;
+        if (ancestors) ancestors[n] = lo;
     }
-    for (int i = 0; i < dp; ++i) {
-        xs[(int64_t)i * Np + n] = xa[(int64_t)i * Np + lo];
-        gs[(int64_t)i * Np + n] = ga[(int64_t)i * Np + lo];
-    }
-    ell_s[n] = ell[lo];
-    logw[n] = 0.0;
-    if (ancestors) ancestors[n] = lo;
 }
 
 __global__ void __launch_bounds__(256)
@@ -341,13 +341,13 @@ tcs_copyback_kernel(const AsmcState* st, int64_t N, int64_t Np, int dp, float* x
                     const double* __restrict__ ell_s)
 {
     if (!st->pend) return;
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    for (int i = 0; i < dp; ++i) {
-        xa[(int64_t)i * Np + n] = xs[(int64_t)i * Np + n];
-        ga[(int64_t)i * Np + n] = gs[(int64_t)i * Np + n];
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        for (int i = 0; i < dp; ++i) {
+            xa[(int64_t)i * Np + n] = xs[(int64_t)i * Np + n];
+            ga[(int64_t)i * Np + n] = gs[(int64_t)i * Np + n];
+        }
+        ell[n] = ell_s[n];
     }
-    ell[n] = ell_s[n];
 }
 
 cudaError_t launch_gather_tcs(const TcsPlan& L, const AsmcState* st, const double* cdf, int64_t N, float* state,
@@ -358,7 +358,7 @@ cudaError_t launch_gather_tcs(const TcsPlan& L, const AsmcState* st, const doubl
     float* ga = state + (size_t)L.dp * Np;
     float* xs = state + (size_t)2 * L.dp * Np;
     float* gs = state + (size_t)3 * L.dp * Np;
-    const int gb = (int)((N + 255) / 256);
+    const int gb = capped_grid((N + 255) / 256, 4);   // usually returns at once
     tcs_gather_kernel<<<gb, 256, 0, s>>>(st, cdf, N, Np, L.dp, xa, ga, xs, gs, ell, ell_scratch, logw, ancestors);
     tcs_copyback_kernel<<<gb, 256, 0, s>>>(st, N, Np, L.dp, xa, ga, xs, gs, ell, ell_scratch);
     return cudaGetLastError();
