@@ -438,10 +438,10 @@ __device__ __forceinline__ void merge_deferred_pieces(int lane, const double (*w
 //   log w is held as an unevaluated sum hi + lo of two fp32 values, each step's log g (an fp32
 //   value) added by Knuth's TwoSum (hi the rounded sum, lo += the exact rounding error), so that
 //   hi + lo carries about 48 bits; a zero weight (-inf) or a non-finite value stays in hi;
-//   the warp piece takes its anchor (a_hi, a_lo, log g_a) and offsets
+//   a step's record takes an anchor particle (a_hi, a_lo, log g_a) and the offsets
 //   (hi - a_hi) + (lo - a_lo) + i (log g - log g_a) in fp32 (hi - a_hi is exact where it matters,
-//   within a factor of two of the anchor, by Sterbenz's lemma), and the merge forms the fp64
-//   shift a_hi + a_lo + i log g_a + max_i for its W pieces only.
+//   within a factor of two of the anchor, by Sterbenz's lemma), and forms the fp64 shift
+//   a_hi + a_lo + i log g_a + max_i once per record.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void df_add(float& hi, float& lo, float v)
 {
@@ -452,110 +452,88 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v)
     hi = s;
 }
 
-// The warp's piece for log w = lwh + lwl and the fp32 log g: as warp_moment_partial<true>, with
-// the anchors in wf[0..2] = (a_hi, a_lo, log g_a) and the fp32 maxima in ws[4..6].
-__device__ __forceinline__ void warp_moment_partial_df(float lwh, float lwl, float lg, bool active, float* wf /*3*/,
-                                                       float* ws /*8*/)
+// One step's record from the CTA's per-particle values, computed by one half-warp: v holds, for
+// every particle of the CTA, (log w_{t-1} as the pair hi, lo; log g_t; the step's accepted moves,
+// or -1 for an inactive lane), and lane l of the half takes particles l, l + 16, l + 32, ...
+// (NP = particles / 16).  The anchor is the particle of largest log w + log g among those with
+// both finite (else one with a finite log w); the offsets (hi - a_hi) + (lo - a_lo) +
+// i (log g - log g_a) are fp32, and the record's shift is the fp64 a_hi + a_lo + i log g_a +
+// max of the offsets.
+// Both halves of the warp must call it together (the shuffles span the warp); `on` says whether
+// this half's step exists.
+template <int NP>
+__device__ __forceinline__ void half_step_record_df(int lane, const float4* v, bool on, StepPartial* out)
 {
     const unsigned full = 0xFFFFFFFFu;
-    const bool lead = (threadIdx.x & 31) == 0;
-    const bool fw = active && isfinite(lwh), fg = active && isfinite(lg);
-    const unsigned bw = __ballot_sync(full, fw);
-    if (bw == 0) {
-        if (lead) {
+    const int half = lane >> 4, l = lane & 15;
+    float bk = -INFINITY, bh = 0.0f, bl = 0.0f, bg = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const float4 r = v[l + 16 * j];
+        const bool act = r.w >= 0.0f, fw = act && isfinite(r.x), fg = act && isfinite(r.z);
+        const float key = fw ? (fg ? r.x + r.z : -3.0e38f) : -INFINITY;
+        if (key > bk) { bk = key; bh = r.x; bl = r.y; bg = fg ? r.z : 0.0f; }
+    }
+    float mk = bk;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) mk = fmaxf(mk, __shfl_xor_sync(full, mk, o));
+    const unsigned hb = (__ballot_sync(full, bk == mk && mk > -INFINITY) >> (16 * half)) & 0xFFFFu;
+    const int src = hb ? 16 * half + __ffs(hb) - 1 : lane;
+    const float ah = __shfl_sync(full, bh, src), al = __shfl_sync(full, bl, src), b0 = __shfl_sync(full, bg, src);
+    float mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const float4 r = v[l + 16 * j];
+        if (r.w >= 0.0f) {
+            const float dw = (r.x - ah) + (r.y - al), dg = r.z - b0;
+            mx[0] = fmaxf(mx[0], dw);
+            mx[1] = fmaxf(mx[1], dw + dg);
+            mx[2] = fmaxf(mx[2], dw + 2.0f * dg);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) mx[i] = fmaxf(mx[i], __shfl_xor_sync(full, mx[i], o));
+    float e[3] = {0.0f, 0.0f, 0.0f}, u = 0.0f;
+    unsigned acc = 0u;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const float4 r = v[l + 16 * j];
+        if (r.w >= 0.0f) {
+            const float dw = (r.x - ah) + (r.y - al), dg = r.z - b0;
+            const float f[3] = {dw, dw + dg, dw + 2.0f * dg};
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                wf[i] = 0.0f;
-                ws[i] = 0.0f;
-                ws[4 + i] = -INFINITY;
+                const float ei = f[i] > -INFINITY ? __expf(f[i] - mx[i]) : 0.0f;
+                e[i] += ei;
+                if (i == 0 && ei > 0.0f) u += ei * r.z;
             }
-            ws[3] = 0.0f;
-        }
-        return;
-    }
-    const unsigned bg = __ballot_sync(full, fg);
-    float ah = __shfl_sync(full, lwh, __ffs(bw) - 1), al = __shfl_sync(full, lwl, __ffs(bw) - 1);
-    float b0 = bg ? __shfl_sync(full, lg, __ffs(bg) - 1) : 0.0f;
-    if (__ballot_sync(full, fw && fg)) {
-        // anchor at the lane with the largest log w + log g (the error of the offsets is
-        // smallest where the weight is)
-        const float f1 = (fw && fg) ? lwh + lg : -INFINITY;
-        float m1 = f1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m1 = fmaxf(m1, __shfl_xor_sync(full, m1, o));
-        const int src = __ffs(__ballot_sync(full, f1 == m1)) - 1;
-        ah = __shfl_sync(full, lwh, src);
-        al = __shfl_sync(full, lwl, src);
-        b0 = __shfl_sync(full, lg, src);
-    }
-    const float dw = (lwh - ah) + (lwl - al), dg = lg - b0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const float f = !active ? -INFINITY : (i == 0 ? dw : dw + (float)i * dg);
-        float mx = f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
-        float e = f > -INFINITY ? __expf(f - mx) : 0.0f;
-        float u = (i == 0 && e > 0.0f) ? e * lg : 0.0f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(full, e, o);
-        if (i == 0) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(full, u, o);
-        }
-        if (lead) {
-            ws[4 + i] = mx;
-            ws[i] = e;
-            if (i == 0) ws[3] = u;
+            acc += (unsigned)r.w;
         }
     }
-    if (lead) { wf[0] = ah; wf[1] = al; wf[2] = b0; }
-}
-
-// Merge of G steps' records at once: lanes W s .. W s + W - 1 of the calling warp merge step s's
-// W warp pieces (wf [G][W][3], ws [G][W][8], wacc [G][W]) in a fixed order, as
-// merge_deferred_pieces does for one step, and lane W s writes out[s stride] (steps s >= count
-// are skipped).  W * G == 32.
-template <int W, int G>
-__device__ __forceinline__ void merge_steps_df(int lane, const float (*wf)[W][3], const float (*ws)[W][8],
-                                               const unsigned (*wacc)[W], int count, StepPartial* out,
-                                               size_t stride)
-{
-    static_assert(W * G == 32 && (W & (W - 1)) == 0, "lane groups");
-    const int s = lane / W, j = lane % W;
-    const bool on = s < count;
-    const float ah = on ? wf[s][j][0] : 0.0f, al = on ? wf[s][j][1] : 0.0f, bg = on ? wf[s][j][2] : 0.0f;
-    const double a = (double)ah + (double)al, b = (double)bg;
-    StepPartial rec;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const float mxj = on ? ws[s][j][4 + i] : -INFINITY;
-        const double m = mxj > -INFINITY ? a + i * b + (double)mxj : -INFINITY;
-        double M = m;
+    for (int o = 8; o > 0; o >>= 1) {
 #pragma unroll
-        for (int o = 1; o < W; o <<= 1) M = fmax(M, __shfl_xor_sync(0xFFFFFFFFu, M, o));
-        const float dj = (float)(m - M);
-        const float fj = (on && !isnan(dj)) ? expf(dj) : 0.0f;
-        float v = (on ? ws[s][j][i] : 0.0f) * fj;
-        float uu = (i == 0 && fj > 0.0f) ? (on ? ws[s][j][3] : 0.0f) * fj : 0.0f;
-#pragma unroll
-        for (int o = 1; o < W; o <<= 1) {
-            v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-            uu += __shfl_xor_sync(0xFFFFFFFFu, uu, o);
-        }
-        rec.s[i] = (double)v;
-        if (i == 0) rec.u = (double)uu;
-        rec.m[i] = M;
+        for (int i = 0; i < 3; ++i) e[i] += __shfl_xor_sync(full, e[i], o);
+        u += __shfl_xor_sync(full, u, o);
+        acc += __shfl_xor_sync(full, acc, o);
     }
-    unsigned acc = on ? wacc[s][j] : 0u;
+    if (on && l == 0) {
+        StepPartial rec;
+        const double a = (double)ah + (double)al;
 #pragma unroll
-    for (int o = 1; o < W; o <<= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-    if (on && j == 0) {
+        for (int i = 0; i < 3; ++i) {
+            rec.m[i] = mx[i] > -INFINITY ? a + i * (double)b0 + (double)mx[i] : -INFINITY;
+            rec.s[i] = (double)e[i];
+        }
+        rec.u = (double)u;
         rec.accepted = acc;
         rec.pad = 0;
-        out[(size_t)s * stride] = rec;
+        *out = rec;
     }
 }
+
 
 // CTA part: warp 0 merges the W warps' pieces and writes one record.  Call after a
 // __syncthreads that follows warp_moment_partial.

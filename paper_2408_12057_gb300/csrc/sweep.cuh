@@ -221,20 +221,20 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
     (void)lane;
 
     if constexpr (kFp32<R> && Tgt::kind == kGmm) {
-        // fp32 bookkeeping (see warp_moment_partial_df): log w = lwh + lwl, the step's schedule
-        // values from the fp32 roundings the host prepared (the same values the conversions of
-        // the fp64 schedule give), and one CTA merge every kMergeSteps steps: the warps' pieces of
-        // those steps wait in shared memory (double-buffered, so the warps run on while warp 0
-        // merges), and warp 0 merges the batch with a lane group per step.  For the mixture, whose
-        // evaluations are a few hundred instructions without barriers, the per-step fp64
-        // bookkeeping and the per-step barrier were a large share of the step (1.06e10 ->
-        // 1.19e10 particle-steps/s); the row families' evaluations synchronise the CTA every data
-        // chunk anyway and keep the per-step form below (they ran 7 % slower with this one).
-        constexpr int W = kSweepThreads / 32;
-        constexpr int kMergeSteps = 32 / W;
-        __shared__ float s_wf[2][kMergeSteps][W][3];
-        __shared__ float s_ws[2][kMergeSteps][W][8];
-        __shared__ unsigned s_wacc[2][kMergeSteps][W];
+        // fp32 bookkeeping (see df_add): log w = lwh + lwl, the step's schedule values from the
+        // fp32 roundings the host prepared (the same values the conversions of the fp64 schedule
+        // give), and the moment records of kMergeSteps steps at once: every thread leaves its
+        // (log w_{t-1}, log g_t, accepted moves) of each step in shared memory (double-buffered,
+        // so the warps run on into the next steps), and after the batch's barrier each half-warp
+        // forms one step's record from the CTA's 128 values (half_step_record_df).  For the
+        // mixture, whose evaluations are a few hundred instructions without barriers, the
+        // per-step fp64 bookkeeping and barrier were a large share of the step (1.06e10 ->
+        // 1.19e10 particle-steps/s), and the per-step warp reductions of the moments some 90
+        // instructions per particle-step; the row families' evaluations synchronise the CTA
+        // every data chunk anyway and keep the per-step form below.
+        constexpr int kMergeSteps = 2 * (kSweepThreads / 32);   // one step per half-warp
+        static_assert(kSweepThreads == 128, "16 lanes x 8 particles per step record");
+        __shared__ float4 s_v[2][kMergeSteps][kSweepThreads];
         float lwh = 0.0f, lwl = 0.0f;
         double beta_prev = P.beta[0];
         for (int t = 1; t <= P.T; ++t) {
@@ -252,23 +252,20 @@ oais_sweep_kernel(const SweepParams P, Tgt tg)
             }
             const float lg = db == 0.0f ? 0.0f : db * (float)ell;
             const int buf = ((t - 1) / kMergeSteps) & 1, st = (t - 1) % kMergeSteps;
-            warp_moment_partial_df(lwh, lwl, lg, active, s_wf[buf][st][warp], s_ws[buf][st][warp]);
+            const float pwh = lwh, pwl = lwl;   // log w_{t-1}
             df_add(lwh, lwl, lg);
             unsigned acc = 0;
             for (int k = 0; k < P.mv.K; ++k)
                 acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, (R)beta_r, (R)eps_r, n, (uint32_t)t,
                                                 (uint32_t)k, d, inv_s2) ? 1u : 0u;
-            acc = active ? acc : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-            if (lane == 0) s_wacc[buf][st][warp] = acc;
+            s_v[buf][st][threadIdx.x] = make_float4(pwh, pwl, lg, active ? (float)acc : -1.0f);
             if (st == kMergeSteps - 1 || t == P.T) {
                 __syncthreads();
-                if (warp == 0) {
-                    const int t0 = t - st;            // the batch's first step
-                    merge_steps_df<W, kMergeSteps>(lane, s_wf[buf], s_ws[buf], s_wacc[buf], st + 1,
-                                                   P.partials + (size_t)(t0 - 1) * gridDim.x + blockIdx.x, gridDim.x);
-                }
+                const int t0 = t - st, s = 2 * warp + (lane >> 4);   // the batch's first step; this half's
+                const bool on = s <= st;
+                half_step_record_df<kSweepThreads / 16>(lane, s_v[buf][on ? s : 0], on,
+                                                        P.partials + (size_t)(t0 - 1 + (on ? s : 0)) * gridDim.x +
+                                                            blockIdx.x);
             }
         }
         logw = (double)lwh + (double)lwl;
