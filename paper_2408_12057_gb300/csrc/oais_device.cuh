@@ -431,6 +431,97 @@ __device__ __forceinline__ void merge_deferred_pieces(int lane, const double (*w
     merge_lane_pieces<W, true>(lane, m, sv, (wacc && on) ? wacc[lane] : 0u, out);
 }
 
+// One record from a CTA's values in shared memory, computed by one half-warp, for the fp32
+// forms' lock-step ASMC kernel whose log w is fp64: lane l of the half takes particles l,
+// l + 16, ... (NP per lane) with v_i = lw + i lg, lw = lwp[p] + (ess ? lgp[p] : 0) and lg =
+// (ess ? lw : lgp[p]), acc[p] the accepted moves (-1: inactive).  ess = false gives the moment
+// record of (w_{t-1}, g_t); ess = true the (log w, 2 log w) pieces of w_t for the ESS test.  The
+// semantics are warp_moment_partial<true>'s and merge_deferred_pieces' for the whole CTA at
+// once: the anchor at the largest fp32 rounding of v_1 (else a particle with a finite log w), the
+// offsets fp64 differences rounded once to fp32, the fp64 shift formed once per record.  Both
+// halves of the warp call it together (the shuffles span the warp).
+template <int NP>
+__device__ __forceinline__ void half_record_fp64w(int lane, const double* lwp, const float* lgp, const float* accp,
+                                                  bool ess, bool on, StepPartial* out)
+{
+    const unsigned full = 0xFFFFFFFFu;
+    const int half = lane >> 4, l = lane & 15;
+    double lw[NP], lg[NP];
+    bool act[NP];
+    float bk = -INFINITY;
+    int bj = 0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const int p = l + 16 * j;
+        act[j] = accp[p] >= 0.0f;
+        const double g = (double)lgp[p];
+        lw[j] = ess ? lwp[p] + g : lwp[p];
+        lg[j] = ess ? lw[j] : g;
+        const bool fw = act[j] && finite_bits(lw[j]), fg = act[j] && finite_bits(lg[j]);
+        const float key = fw ? (fg ? (float)lw[j] + (float)lg[j] : -3.0e38f) : -INFINITY;
+        if (key > bk) { bk = key; bj = j; }
+    }
+    double ca = 0.0, cb = 0.0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+        if (j == bj) { ca = lw[j]; cb = finite_bits(lg[j]) && act[j] ? lg[j] : 0.0; }
+    float mk = bk;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) mk = fmaxf(mk, __shfl_xor_sync(full, mk, o));
+    const unsigned hb = (__ballot_sync(full, bk == mk && mk > -INFINITY) >> (16 * half)) & 0xFFFFu;
+    const int src = hb ? 16 * half + __ffs(hb) - 1 : lane;
+    const double a0 = __shfl_sync(full, ca, src), b0 = __shfl_sync(full, cb, src);
+    float dw[NP], dg[NP];
+    float mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        dw[j] = (float)(lw[j] - a0);
+        dg[j] = (float)(lg[j] - b0);
+        if (act[j]) {
+            mx[0] = fmaxf(mx[0], dw[j]);
+            mx[1] = fmaxf(mx[1], dw[j] + dg[j]);
+            mx[2] = fmaxf(mx[2], dw[j] + 2.0f * dg[j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) mx[i] = fmaxf(mx[i], __shfl_xor_sync(full, mx[i], o));
+    float e[3] = {0.0f, 0.0f, 0.0f}, u = 0.0f;
+    unsigned acc = 0u;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (!act[j]) continue;
+        const float f[3] = {dw[j], dw[j] + dg[j], dw[j] + 2.0f * dg[j]};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float ei = f[i] > -INFINITY ? __expf(f[i] - mx[i]) : 0.0f;
+            e[i] += ei;
+            if (i == 0 && ei > 0.0f) u += ei * (float)lg[j];
+        }
+        acc += (unsigned)accp[l + 16 * j];
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) e[i] += __shfl_xor_sync(full, e[i], o);
+        u += __shfl_xor_sync(full, u, o);
+        acc += __shfl_xor_sync(full, acc, o);
+    }
+    if (on && l == 0) {
+        StepPartial rec;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            rec.m[i] = mx[i] > -INFINITY ? a0 + i * b0 + (double)mx[i] : -INFINITY;
+            rec.s[i] = (double)e[i];
+        }
+        rec.u = (double)u;
+        rec.accepted = ess ? 0u : acc;
+        rec.pad = 0;
+        *out = rec;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // fp32-only bookkeeping of the one-thread-per-particle fp32 forms.  GB300's fp64 pipe runs at a
 // small fraction of its fp32 rate, so the per-step fp64 additions and conversions of the moment

@@ -383,6 +383,29 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     const double beta_t = P.beta[P.t], eps_t = P.eps[P.t - 1];
     const double lg = step_log_increment<R>(beta_t - P.beta[P.t - 1], ell);
     const R beta_r = (R)beta_t, eps_r = (R)eps_t;
+    if constexpr (kFp32<R>) {
+        // the fp32 forms: the two records of the step (the moments of (w_{t-1}, g_t), the ESS
+        // pieces of w_t) from the CTA's values in shared memory, one per half of warp 0, after
+        // one barrier (instead of warp shuffle trees and a CTA merge for each)
+        __shared__ double s_lw[kSweepThreads];
+        __shared__ float s_lg[kSweepThreads], s_ac[kSweepThreads];
+        const double lw_prev = logw;
+        logw += lg;
+        unsigned acc = 0;
+        for (int k = 0; k < P.mv.K; ++k)
+            acc += mh_move<Tgt, MOVE, D, R>(tg, P.mv, x, ell, gl, beta_r, eps_r, n, (uint32_t)P.t,
+                                            (uint32_t)k, d, inv_s2) ? 1u : 0u;
+        s_lw[threadIdx.x] = lw_prev;
+        s_lg[threadIdx.x] = (float)lg;
+        s_ac[threadIdx.x] = active ? (float)acc : -1.0f;
+        __syncthreads();
+        if (warp == 0) {
+            const bool ess = lane >= 16;
+            half_record_fp64w<kSweepThreads / 16>(lane, s_lw, s_lg, s_ac, ess, true,
+                                                  ess ? P.ess_parts + blockIdx.x
+                                                      : P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
+        }
+    } else {
     warp_moment_partial<kFp32<R>>(logw, lg, active, s_m[warp], s_s[warp]);
     logw += lg;
     unsigned acc = 0;
@@ -394,22 +417,13 @@ asmc_step_kernel(const StepParams P, Tgt tg)
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if (lane == 0) s_acc[warp] = acc;
     __syncthreads();
-    if constexpr (kFp32<R>) {
-        if (warp == 0)
-            merge_deferred_pieces<kSweepThreads / 32>(lane, s_m, s_s, s_acc,
-                                                      P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
-    } else {
-        cta_moment_record<kSweepThreads / 32, false>(s_m, s_s, s_acc,
-                                                     P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
-    }
+    cta_moment_record<kSweepThreads / 32, false>(s_m, s_s, s_acc,
+                                                 P.partials + (size_t)(P.t - 1) * gridDim.x + blockIdx.x);
     __syncthreads();
     // ESS pieces of w_{t^-}: LSE of log w (slot 0) and of 2 log w (slot 1)
     warp_moment_partial<kFp32<R>>(logw, logw, active, s_m[warp], s_s[warp]);
     __syncthreads();
-    if constexpr (kFp32<R>) {
-        if (warp == 0) merge_deferred_pieces<kSweepThreads / 32>(lane, s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
-    } else {
-        cta_moment_record<kSweepThreads / 32, false>(s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
+    cta_moment_record<kSweepThreads / 32, false>(s_m, s_s, nullptr, P.ess_parts + blockIdx.x);
     }
     if (active) {
         R* xw = reinterpret_cast<R*>(P.x[b]);
