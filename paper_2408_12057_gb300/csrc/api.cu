@@ -313,7 +313,7 @@ static Layout layout(const oais_target* tg, const oais_move* mv, int D, int64_t 
     // the streamed form's image and state: its own sweeps, and the resampling rounds and the
     // potential of a resident-form context (whose kernel is a whole-sweep kernel)
     if (form >= 1) tp = tcs_plan(tg->kind, tg->n, tg->d, 0, 0, tg->contraction == OAIS_CONTRACT_FP8_TC_STREAM);
-    L.tcs_img = take(form >= 1 ? tp.img_bytes : 0);
+    L.tcs_img = take(form >= 1 ? tcs_image_bytes(tp, tg->kind, tg->n) : 0);
     L.tcs_state = take(form >= 1 ? sizeof(float) * 5 * (size_t)tp.dp * tcs_tiles(N) * 128 : 0);
     // the tiled fp32 form (32 < d <= 256): positions, gradients, momenta of every tile
     L.wide_state = take(D > 32 ? wide_state_bytes(D, N) : 0);
@@ -559,6 +559,7 @@ oais_status oais_init(oais_ctx** out, const oais_target* tg, const oais_move* mv
             std::vector<unsigned char> img;
             if (q8) tcs_prepare_q8(tp, Xf.data(), yf.data(), tg->n, tg->d, img);
             else tcs_prepare(tp, tg->kind, Xf.data(), yf.data(), tg->n, tg->d, img);
+            img.resize(tcs_image_bytes(tp, tg->kind, tg->n), 0);   // zero rows past the last chunk
             dt.tcs = true;
             dt.tcs_q8 = q8;
             dt.tcs_dp = tp.dp;
@@ -1483,10 +1484,10 @@ static oais_status batch_enqueue(oais_batch* b, int T)
     BK(cudaMemsetAsync(b->d_head, 0, sizeof(uint32_t), s));
     // external records: inside a captured graph a plain record only orders the capture
     BK(cudaEventRecordWithFlags(b->ev0, s, cudaEventRecordExternal));
-    bool chunk32 = false;
-    for (const TcsPlan& L : b->plan) chunk32 = chunk32 || L.chunk == 32;
+    bool alt = false;   // some class runs chunks of other than 64 rows
+    for (const TcsPlan& L : b->plan) alt = alt || L.chunk != 64;
     BK(launch_sweep_tcs_batch(b->kind, b->h, b->d_params, b->d_items, b->n_items, b->d_head, b->off_misc, b->smem,
-                              b->grid, s, chunk32));
+                              b->grid, s, alt));
     BK(cudaEventRecordWithFlags(b->ev1, s, cudaEventRecordExternal));
     for (int p = 0; p < b->P; ++p) {
         oais_ctx* c = b->ctx[p];
@@ -1631,7 +1632,7 @@ oais_status oais_batch_round(oais_batch* b, int32_t T_next, oais_round_result* r
 // of the class sweeps T_probe steps (its own data, a linear schedule, the first tiles of its
 // particles filling every SM once) through the batched kernel itself, for every candidate
 // (rows per X chunk, ring depth): chunks of 64 rows and, where the class's chunk images allow
-// it, of 32; ring depths 2, 3, 4, 6, 8 as far as shared memory holds them.  The fastest pair
+// it, of 32 and 128; ring depths 2, 3, 4, 6, 8 as far as shared memory holds them.  The fastest pair
 // is kept.  The probe runs on the problem's own particle buffers (the next round redraws them).
 oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
 {
@@ -1667,10 +1668,12 @@ oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
         BK(cudaMemcpyAsync(tmp.items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice, s));
         // every problem of the class must take the chunk size
         std::vector<int> chunks = {64};
-        bool all32 = true;
-        for (int p = 0; p < b->P; ++p)
-            if (dp_class(b->plan[p].dp) == c) all32 = all32 && tcs_chunk_ok(b->ctx[p]->dt.kind, b->plan[p].dp, 32, false);
-        if (all32) chunks.push_back(32);
+        for (int ch : {32, 128}) {
+            bool all = true;
+            for (int p = 0; p < b->P; ++p)
+                if (dp_class(b->plan[p].dp) == c) all = all && tcs_chunk_ok(b->ctx[p]->dt.kind, b->plan[p].dp, ch, false);
+            if (all) chunks.push_back(ch);
+        }
         float best_ms = 0.0f;
         int best_S = 0, best_ch = 0;
         for (int ch : chunks) {
@@ -1691,7 +1694,7 @@ oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
                     BK(cudaMemsetAsync(b->d_head, 0, sizeof(uint32_t), s));
                     BK(cudaEventRecord(b->ev0, s));
                     BK(launch_sweep_tcs_batch(b->kind, b->h, tmp.params, tmp.items, (uint32_t)ptiles, b->d_head,
-                                              off_misc, smem, std::min(b->grid, ptiles), s, ch == 32));
+                                              off_misc, smem, std::min(b->grid, ptiles), s, ch != 64));
                     BK(cudaEventRecord(b->ev1, s));
                     BK(cudaEventSynchronize(b->ev1));
                     BK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
@@ -1727,7 +1730,8 @@ oais_status oais_batch_set_tile_shape(oais_batch* b, int32_t width_class, int32_
     if (!b) return batch_fail(nullptr, OAIS_EINVAL, "null batch");
     if (width_class < 0 || width_class > 3) return batch_fail(b, OAIS_EINVAL, "width class out of range");
     if (stages != 0 && (stages < 2 || stages > 8)) return batch_fail(b, OAIS_EINVAL, "ring depth out of range");
-    if (chunk_rows != 0 && chunk_rows != 32 && chunk_rows != 64) return batch_fail(b, OAIS_EINVAL, "chunk rows not 32 or 64");
+    if (chunk_rows != 0 && chunk_rows != 32 && chunk_rows != 64 && chunk_rows != 128)
+        return batch_fail(b, OAIS_EINVAL, "chunk rows not 32, 64 or 128");
     for (int p = 0; p < b->P; ++p) {
         if (dp_class(b->plan[p].dp) != width_class) continue;
         const int ch = chunk_rows == 0 ? 64 : chunk_rows;

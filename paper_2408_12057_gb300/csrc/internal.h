@@ -61,8 +61,11 @@ TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8 = false,
 // per_sm CTAs per SM, the work taken grid-stride
 int capped_grid(int64_t want, int per_sm);
 // chunk rows a plan may take (the single-problem kernels: the default only; the batched kernel
-// also 32 for logistic problems with d_pad <= 64)
+// also 32 and 128 for logistic problems with d_pad <= 64)
 bool tcs_chunk_ok(int kind, int dp, int chunk, bool q8);
+// bytes of a context's chunk images: the plan's, padded with zero rows to a multiple of 128
+// rows where the problem may run 128-row chunks
+size_t tcs_image_bytes(const TcsPlan& L, int kind, int n);
 void tcs_prepare(const TcsPlan& L, int kind, const float* X, const float* y, int n, int d,
                  std::vector<unsigned char>& img);
 void tcs_prepare_q8(const TcsPlan& L, const float* X, const float* y, int n, int d, std::vector<unsigned char>& img);
@@ -83,7 +86,7 @@ void tcs_batch_params(const TcsPlan& L, int kind, const SweepParams& sp, const v
                       int leapfrog, double p0, int n, int d, uint32_t off_misc, void* out);
 cudaError_t launch_sweep_tcs_batch(int kind, int h, const void* d_params, const void* d_items, uint32_t n_items,
                                    uint32_t* d_head, uint32_t off_misc, uint32_t smem, int grid, cudaStream_t s,
-                                   bool chunk32 = false);
+                                   bool alt_chunks = false);
 // ASMC on the streamed form: step t (t = 0: the draw from eta) of the whole population, with
 // the tiles' (log w, 2 log w) records in ess_parts; then the resampling test, scan and CDF of
 // asmc.cu (decide/scan/cdf, no gather) and launch_gather_tcs for the particle state

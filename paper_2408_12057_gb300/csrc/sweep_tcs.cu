@@ -28,6 +28,8 @@
 // Particle state between evaluations lives in global memory (L2): accepted position and
 // gradient, proposal position and momentum, [d_pad][N_pad] fp32 each, read and written only
 // by the thread that owns the (particle, coordinate) pair.
+#include <algorithm>
+
 #include "sweep_tcs.cuh"
 
 namespace oais {
@@ -86,12 +88,21 @@ TcsPlan tcs_plan(int kind, int n, int d, int chunk, int stages, bool q8, int h, 
     return L;
 }
 
+size_t tcs_image_bytes(const TcsPlan& L, int kind, int n)
+{
+    // room for the chunk images at every chunk size the batched launch may give the problem:
+    // 128-row chunks read up to 64 zero rows past a 64-row plan's last chunk
+    if (!tcs_chunk_ok(kind, L.dp, 128, L.q8)) return L.img_bytes;
+    const size_t rows128 = (size_t)(n + 127) / 128 * 128;
+    return std::max(L.img_bytes, rows128 * (size_t)L.dp * 2);
+}
+
 bool tcs_chunk_ok(int kind, int dp, int chunk, bool q8)
 {
-    // 64 rows (32 at d_pad = 256 if so compiled); the batched launch also takes 32-row chunks
-    // for logistic problems with d_pad <= 64: their chunk images are the rows of X~ in order
-    // (one K slab, no y lines), so the same image serves both chunk sizes
-    return chunk == tcs::chunk_rows(dp) || (!q8 && kind == kLogreg && dp <= 64 && chunk == 32);
+    // 64 rows (32 at d_pad = 256 if so compiled); the batched launch also takes 32- and 128-row
+    // chunks for logistic problems with d_pad <= 64: their chunk images are the rows of X~ in
+    // order (one K slab, no y lines), so the same image serves every chunk size
+    return chunk == tcs::chunk_rows(dp) || (!q8 && kind == kLogreg && dp <= 64 && (chunk == 32 || chunk == 128));
 }
 
 // X~ = f16(bf16(X)) in the stage layout (logistic: rows multiplied by the label sign), and y

@@ -72,7 +72,7 @@ __host__ __device__ constexpr int chunk_rows(int dp) { return dp >= 256 ? OAIS_T
 // while the particle warps work on this one) wherever the 512 columns allow: d_pad <= 128.
 template <int DP, int CHR = chunk_rows(DP)>
 struct Cols {
-    static constexpr int NB = DP <= 128 ? 2 : 1;
+    static constexpr int NB = (DP <= 128 && CHR <= 64) ? 2 : 1;
     static constexpr int CH = CHR;
     static constexpr int D1 = 0, R = NB * CH, ALO = 2 * NB * CH;
     static constexpr int D2 = (ALO + DP / 2 + 31) / 32 * 32;
@@ -281,8 +281,15 @@ struct Thread {
             tc_after_sync();
             uint32_t v[HC];
             const uint32_t src = tmem + (uint32_t)(C::D1 + b * CHUNK + h * HC) + lane_off;
-            if constexpr (HC == 16) tmem_ld16(src, v);
-            else tmem_ld32(src, v);
+            if constexpr (HC == 16) {
+                tmem_ld16(src, v);
+            } else if constexpr (HC == 32) {
+                tmem_ld32(src, v);
+            } else {
+                static_assert(HC == 64, "columns per thread");
+                tmem_ld32(src, *reinterpret_cast<uint32_t(*)[32]>(v));
+                tmem_ld32(src + 32, *reinterpret_cast<uint32_t(*)[32]>(v + 32));
+            }
             tmem_wait_ld();
             tc_before_sync();
             __syncwarp();
@@ -319,7 +326,7 @@ struct Thread {
                 // margin s z in base-2 units: log sigmoid(s z) = ln 2 (min(u, 0) + log2 q) with
                 // q = 1 / (1 + 2^-|u|), d/dz = s sigmoid(-s z) = s (u >= 0 ? 2^-|u| q : q).  The rows
                 // of a pair go through the packed fp32 pair instructions; the product of q is kept
-                // per lane of the pair (HC / 2 <= 16 values in [1/2, 1] each), one log per chunk.
+                // per lane of the pair (HC / 2 <= 32 values in [1/2, 1] each), one log per chunk.
                 const float2 one2 = make_float2(1.0f, 1.0f);
                 float2 prod = one2, mn = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -342,7 +349,12 @@ struct Thread {
             __syncwarp();
             tc_after_sync();
             const uint32_t rcol = tmem + (uint32_t)(C::R + b * CHUNK + h * (HC / 2)) + lane_off;
-            if constexpr (HC == 32) {
+            if constexpr (HC == 64) {
+                tmem_st16(rcol, *reinterpret_cast<const uint32_t(*)[16]>(hi));
+                tmem_st16(rcol + 16, *reinterpret_cast<const uint32_t(*)[16]>(hi + 16));
+                tmem_st16(rcol + CHUNK / 2, *reinterpret_cast<const uint32_t(*)[16]>(lo));
+                tmem_st16(rcol + CHUNK / 2 + 16, *reinterpret_cast<const uint32_t(*)[16]>(lo + 16));
+            } else if constexpr (HC == 32) {
                 tmem_st16(rcol, hi);
                 tmem_st16(rcol + CHUNK / 2, lo);
             } else {

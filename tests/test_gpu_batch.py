@@ -97,20 +97,21 @@ def width_class(d):
     return 0 if d <= 16 else 1 if d <= 32 else 2 if d <= 64 else 3
 
 
-def test_batch_chunk32_matches_oracle_per_problem():
-    # 32-row chunks for the classes d_pad 16, 32, 64 and the default 64 rows for d_pad 128 in
-    # the same launch: every problem still agrees with the oracle particle by particle
+@pytest.mark.parametrize("chunk", [32, 128])
+def test_batch_other_chunks_match_oracle_per_problem(chunk):
+    # 32- or 128-row chunks for the classes d_pad 16, 32, 64 and the default 64 rows for d_pad
+    # 128 in the same launch: every problem still agrees with the oracle particle by particle
     probs = mixed_problems()
     N, T = 300, 3
     beta = W.linear_schedule(T) ** 3
     eps = np.stack([oais.default_step_sizes(pr, beta, oais.MALA) for pr in probs])
     b = oais.OAISBatch(probs, oais.MALA, N, beta, eps=eps, seed=31)
     for c in (0, 1, 2):
-        b.set_tile_shape(c, chunk_rows=32)
-        assert b.tile_shape(c)[0] == 32 and b.tile_shape(c)[1] >= 2
+        b.set_tile_shape(c, chunk_rows=chunk)
+        assert b.tile_shape(c)[0] == chunk and b.tile_shape(c)[1] >= 2
     assert b.tile_shape(3)[0] == 64
     with pytest.raises(oais.OAISError):
-        b.set_tile_shape(3, chunk_rows=32)   # d_pad 128: two K slabs, the image depends on the chunk
+        b.set_tile_shape(3, chunk_rows=chunk)   # d_pad 128: two K slabs, the image depends on the chunk
     res = b.round(T)
     for p, pr in enumerate(probs):
         g = view(b.problem(p))
@@ -146,7 +147,7 @@ def test_batch_autotune_shape_is_reproducible():
     shapes = [b.tile_shape(c) for c in range(4)]
     for c, (ch, st) in enumerate(shapes):
         present = any(width_class(pr.d) == c for pr in probs)
-        assert (ch in (32, 64) and st == chosen[c]) if present else (ch, st) == (0, 0)
+        assert (ch in (32, 64, 128) and st == chosen[c]) if present else (ch, st) == (0, 0)
     rb = b.round(T)
     lb = [view(b.problem(p))["logw"] for p in range(len(probs))]
     c2 = oais.OAISBatch(probs, oais.MALA, N, beta, seed=5)
