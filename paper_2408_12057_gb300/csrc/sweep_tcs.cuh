@@ -72,7 +72,8 @@ __host__ __device__ constexpr int chunk_rows(int dp) { return dp >= 256 ? OAIS_T
 // while the particle warps work on this one) wherever the 512 columns allow: d_pad <= 128.
 template <int DP, int CHR = chunk_rows(DP)>
 struct Cols {
-    static constexpr int NB = (DP <= 128 && CHR <= 64) ? 2 : 1;
+    // two buffers of D1 and R wherever the 512 columns hold them with A_lo and D2
+    static constexpr int NB = ((4 * CHR + DP / 2 + 31) / 32 * 32 + DP <= 512) ? 2 : 1;
     static constexpr int CH = CHR;
     static constexpr int D1 = 0, R = NB * CH, ALO = 2 * NB * CH;
     static constexpr int D2 = (ALO + DP / 2 + 31) / 32 * 32;
@@ -530,8 +531,9 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                 atomicOr(S.status, 2u);
                 break;
             }
-            convert_row<DP, CHR>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
-                            lane, P.y_off);
+            if (lane < CHUNK)
+                convert_row<DP, CHR>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes,
+                                     smem + P.off_x + (uint32_t)s * P.stage_bytes, lane, P.y_off);
             fence_proxy_async();   // the f16 stage, visible to the tensor core
             __syncwarp();
             if (lane == 0) {
@@ -586,8 +588,9 @@ __device__ __forceinline__ void run_tile(const Params& P, uint32_t tile, uint32_
                 atomicOr(S.status, 2u);
                 break;
             }
-            convert_row<DP, CHR>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes, smem + P.off_x + (uint32_t)s * P.stage_bytes,
-                            32 + lane, P.y_off);
+            if (32 + lane < CHUNK)   // chunks of 32 rows: the producer warp converts them all
+                convert_row<DP, CHR>(smem + P.off_x8 + (uint32_t)s8 * P.stage8_bytes,
+                                     smem + P.off_x + (uint32_t)s * P.stage_bytes, 32 + lane, P.y_off);
             fence_proxy_async();   // the f16 stage, visible to the tensor core
             __syncwarp();
             if ((threadIdx.x & 31) == 0) {
