@@ -104,17 +104,17 @@ struct GmmTarget {
     // from the move configuration; the random-walk moves of the fp32 forms draw from it)
     RngKS rks;
 
-    // fp32 forms take the components four at a time (one test of K per group, and the group's
-    // instructions can interleave: 1.484e10 particle-steps/s on the mixture workload against
-    // 1.445e10 in pairs and 1.32e10 one by one); K is padded to a multiple of four with dummy
-    // components whose means lie so far away (1e18 in every coordinate) that their weights are
-    // exactly 0: the exponent is about -1e37, whose ex2 is +0, so sums, maxima and the gradient
-    // are unchanged bit for bit
-    static constexpr int kGroup = (sizeof(R) == 4 && D % 2 == 0) ? 4 : 1;
-    static constexpr size_t smem_bytes(int K) { return sizeof(R) * (size_t)((K + kGroup - 1) / kGroup * kGroup) * D; }
+    // fp32 forms take the components in groups of eight (K > 4) or four (one test of K per
+    // group, and the group's instructions can interleave: on the mixture workload, K = 8,
+    // 1.32e10 particle-steps/s one by one, 1.445e10 in pairs, 1.484e10 in fours, 1.503e10 in
+    // eights); K is padded to a multiple of the group with dummy components whose means lie so
+    // far away (1e18 in every coordinate) that their weights are exactly 0: the exponent is
+    // about -1e37, whose ex2 is +0, so sums, maxima and the gradient are unchanged bit for bit
+    static constexpr int kGroupMax = (sizeof(R) == 4 && D % 2 == 0) ? 8 : 1;
+    static constexpr size_t smem_bytes(int K) { return sizeof(R) * (size_t)((K + kGroupMax - 1) / kGroupMax * kGroupMax) * D; }
     __device__ void setup(unsigned char* smem) {
         R* s = reinterpret_cast<R*>(smem);
-        const int Kg = (K + kGroup - 1) / kGroup * kGroup;
+        const int Kg = (K + kGroupMax - 1) / kGroupMax * kGroupMax;
         for (int i = threadIdx.x; i < Kg * D; i += blockDim.x) s[i] = i < K * D ? means[i] : R(1e18);
         sm = s;
         __syncthreads();
@@ -122,10 +122,19 @@ struct GmmTarget {
 
     template <bool GRAD>
     __device__ R eval(const R (&x)[D], R (&g)[D]) const {
+        if constexpr (kGroupMax == 8) {
+            if (K > 4) return eval_g<GRAD, 8>(x, g);
+            return eval_g<GRAD, 4>(x, g);
+        } else {
+            return eval_g<GRAD, 1>(x, g);
+        }
+    }
+
+    template <bool GRAD, int G>
+    __device__ R eval_g(const R (&x)[D], R (&g)[D]) const {
         // fp32: the squared distances, |x|^2 and the gradient's mixture sums two coordinates
         // per packed instruction (even and odd coordinates summed apart, then added)
         constexpr bool kPair = sizeof(R) == 4 && D % 2 == 0;
-        constexpr int G = kGroup;
         const int Kg = (K + G - 1) / G * G;
         R q[kMaxK];
         R mx = R(-INFINITY);

@@ -141,6 +141,16 @@ def test_gmm_rwmh_cycle_workload3_shape():
     compare(pr, oais.RWMH, 1000, beta, 1.0, seed=12057, moves=2, cycle=True)
 
 
+@pytest.mark.parametrize("d,K", [(5, 3), (16, 5), (2, 1), (8, 12)])
+def test_gmm_component_groups_and_widths(d, K):
+    # the fp32 mixture density takes its components in groups (eight for K > 4, else four),
+    # padding K with dummy components of weight exactly 0: odd and small K, K above eight, and
+    # the narrower compiled widths D = 2, 8 against the oracle
+    pr = W.gmm(d=d, K=K, seed=40 + d + K)
+    beta = W.linear_schedule(16) ** 3
+    compare(pr, oais.RWMH, 600, beta, 1.0, seed=7 + K, moves=2, cycle=True)
+
+
 def test_linreg_hmc_small():
     pr = W.linreg(n=500, d=16, seed=8)
     beta = W.linear_schedule(8) ** 3
