@@ -69,7 +69,8 @@ __host__ __device__ constexpr int chunk_rows(int dp) { return dp >= 256 ? OAIS_T
 // (hi | lo, f16 pairs), A_lo (the lo term of the positions, f16 pairs: the forward's A
 // operand for that term), D2 (gradient accumulator, d_pad columns).  The hi term of the
 // positions is the shared-memory A operand.  Two buffers (the forward of the next chunk runs
-// while the particle warps work on this one) wherever the 512 columns allow: d_pad <= 128.
+// while the particle warps work on this one) wherever the 512 columns allow: 64-row chunks up
+// to d_pad = 128, 32-row chunks at 256; 128-row chunks take one.
 template <int DP, int CHR = chunk_rows(DP)>
 struct Cols {
     // two buffers of D1 and R wherever the 512 columns hold them with A_lo and D2
