@@ -420,9 +420,9 @@ oais_status oais_logsumexp_noalloc(const double* d_a, int64_t n, double* d_out, 
  * oais_batch_autotune chooses the tile shape of the batched kernel for each width class
  * present (d_pad 16, 32, 64, 128; classes 0..3): it times the class's largest problem over
  * T_probe steps through the batched kernel for every candidate pair of rows per X chunk (the
- * K extent of the backward contraction and the N extent of the forward one: 64, and 32 and
- * 128 for logistic problems with d_pad <= 64; 128-row chunks have one forward accumulator
- * instead of two) and ring depth (X chunk buffers in shared memory: 2,
+ * K extent of the backward contraction and the N extent of the forward one: 64, and 128 for
+ * logistic problems with d_pad <= 64, which have one forward accumulator instead of two) and
+ * ring depth (X chunk buffers in shared memory: 2,
  * 3, 4, 6, 8 as far as shared memory holds them), and keeps the fastest pair; chosen [4]
  * receives the depths (0 = class absent).  The probe sweeps overwrite the problems' particle
  * buffers (the next round redraws them).  The ring depth changes no result; the chunk size
@@ -430,8 +430,8 @@ oais_status oais_logsumexp_noalloc(const double* d_a, int64_t n, double* d_out, 
  * particle's two threads), so a run is reproducible for a given shape, and the shape the
  * autotuner chose can be read and pinned:
  * oais_batch_tile_shape writes the chunk rows and ring depth the class's problems run with
- * (0, 0 for an absent class); oais_batch_set_tile_shape sets them (chunk_rows 0 = 64, 32, 64
- * or 128; stages
+ * (0, 0 for an absent class); oais_batch_set_tile_shape sets them (chunk_rows 0 = 64, 64 or
+ * 128, else OAIS_EINVAL; stages
  * 0 = the deepest ring that fits), OAIS_EUNSUPPORTED when a problem of the class cannot take
  * the chunk size (linear regression, d_pad 128: their chunk images depend on it).
  * oais_batch_context lends problem p's context (owned by the batch) for the per-problem

@@ -1632,7 +1632,7 @@ oais_status oais_batch_round(oais_batch* b, int32_t T_next, oais_round_result* r
 // of the class sweeps T_probe steps (its own data, a linear schedule, the first tiles of its
 // particles filling every SM once) through the batched kernel itself, for every candidate
 // (rows per X chunk, ring depth): chunks of 64 rows and, where the class's chunk images allow
-// it, of 32 and 128; ring depths 2, 3, 4, 6, 8 as far as shared memory holds them.  The fastest pair
+// it, of 128; ring depths 2, 3, 4, 6, 8 as far as shared memory holds them.  The fastest pair
 // is kept.  The probe runs on the problem's own particle buffers (the next round redraws them).
 oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
 {
@@ -1668,7 +1668,7 @@ oais_status oais_batch_autotune(oais_batch* b, int32_t T_probe, int32_t* chosen)
         BK(cudaMemcpyAsync(tmp.items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice, s));
         // every problem of the class must take the chunk size
         std::vector<int> chunks = {64};
-        for (int ch : {32, 128}) {
+        for (int ch : {128}) {
             bool all = true;
             for (int p = 0; p < b->P; ++p)
                 if (dp_class(b->plan[p].dp) == c) all = all && tcs_chunk_ok(b->ctx[p]->dt.kind, b->plan[p].dp, ch, false);
@@ -1730,8 +1730,8 @@ oais_status oais_batch_set_tile_shape(oais_batch* b, int32_t width_class, int32_
     if (!b) return batch_fail(nullptr, OAIS_EINVAL, "null batch");
     if (width_class < 0 || width_class > 3) return batch_fail(b, OAIS_EINVAL, "width class out of range");
     if (stages != 0 && (stages < 2 || stages > 8)) return batch_fail(b, OAIS_EINVAL, "ring depth out of range");
-    if (chunk_rows != 0 && chunk_rows != 32 && chunk_rows != 64 && chunk_rows != 128)
-        return batch_fail(b, OAIS_EINVAL, "chunk rows not 32, 64 or 128");
+    if (chunk_rows != 0 && chunk_rows != 64 && chunk_rows != 128)
+        return batch_fail(b, OAIS_EINVAL, "chunk rows not 64 or 128");
     for (int p = 0; p < b->P; ++p) {
         if (dp_class(b->plan[p].dp) != width_class) continue;
         const int ch = chunk_rows == 0 ? 64 : chunk_rows;

@@ -99,10 +99,11 @@ size_t tcs_image_bytes(const TcsPlan& L, int kind, int n)
 
 bool tcs_chunk_ok(int kind, int dp, int chunk, bool q8)
 {
-    // 64 rows (32 at d_pad = 256 if so compiled); the batched launch also takes 32- and 128-row
-    // chunks for logistic problems with d_pad <= 64: their chunk images are the rows of X~ in
-    // order (one K slab, no y lines), so the same image serves every chunk size
-    return chunk == tcs::chunk_rows(dp) || (!q8 && kind == kLogreg && dp <= 64 && (chunk == 32 || chunk == 128));
+    // 64 rows (32 at d_pad = 256 if so compiled); the batched launch also takes 128-row chunks
+    // for logistic problems with d_pad <= 64: their chunk images are the rows of X~ in order
+    // (one K slab, no y lines), so the same image serves both chunk sizes.  (32-row chunks for
+    // the same problems were built and measured slower than 64 in every width class.)
+    return chunk == tcs::chunk_rows(dp) || (!q8 && kind == kLogreg && dp <= 64 && chunk == 128);
 }
 
 // X~ = f16(bf16(X)) in the stage layout (logistic: rows multiplied by the label sign), and y

@@ -10,8 +10,8 @@ namespace tcs {
 // from a queue ordered by decreasing cost (longest first) until it is empty.  All problems
 // share the family; their widths may differ (the item picks the instantiation).  Every
 // problem's Misc region sits at the same offset (the launch's largest).
-// ALT: some problems run 32- or 128-row chunks (a separate instantiation, so that the default
-// one keeps its register allocation)
+// ALT: some problems run 128-row chunks (a separate instantiation, so that the default one
+// keeps its register allocation)
 template <int FAM, int H, bool ALT>
 __global__ void __launch_bounds__(Roles<H>::threads(0), 1)
 oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __restrict__ items, uint32_t n_items,
@@ -50,13 +50,12 @@ oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __res
         const uint32_t tile = items[it].y;
         const uint32_t tiles = (uint32_t)((sP.sp.N + kTile - 1) / kTile);
         // the item's width and chunk rows pick the instantiation: 64-row chunks, or (logistic,
-        // d_pad <= 64, whose chunk images do not depend on the chunk size) 32- or 128-row chunks
+        // d_pad <= 64, whose chunk images do not depend on the chunk size) 128-row chunks
         const int chr = sP.chunk;
         switch (sP.dp) {
         case 16:
             if constexpr (16 / H >= 8) {
                 if constexpr (ALT && FAM == kLogreg) {
-                    if (chr == 32) { run_tile<FAM, 16, 0, H, 32>(sP, tile, tiles, smem, tmem); break; }
                     if (chr == 128) { run_tile<FAM, 16, 0, H, 128>(sP, tile, tiles, smem, tmem); break; }
                 }
                 run_tile<FAM, 16, 0, H>(sP, tile, tiles, smem, tmem);
@@ -65,7 +64,6 @@ oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __res
         case 32:
             if constexpr (32 / H >= 8) {
                 if constexpr (ALT && FAM == kLogreg) {
-                    if (chr == 32) { run_tile<FAM, 32, 0, H, 32>(sP, tile, tiles, smem, tmem); break; }
                     if (chr == 128) { run_tile<FAM, 32, 0, H, 128>(sP, tile, tiles, smem, tmem); break; }
                 }
                 run_tile<FAM, 32, 0, H>(sP, tile, tiles, smem, tmem);
@@ -74,7 +72,6 @@ oais_sweep_tcs_batch_kernel(const Params* __restrict__ probs, const uint2* __res
         case 64:
             if constexpr (64 / H >= 8) {
                 if constexpr (ALT && FAM == kLogreg) {
-                    if (chr == 32) { run_tile<FAM, 64, 0, H, 32>(sP, tile, tiles, smem, tmem); break; }
                     if (chr == 128) { run_tile<FAM, 64, 0, H, 128>(sP, tile, tiles, smem, tmem); break; }
                 }
                 run_tile<FAM, 64, 0, H>(sP, tile, tiles, smem, tmem);
