@@ -232,6 +232,14 @@ def abs_err_vs_fp64(pr, contraction_code, sample):
             "note": "GPU form against the FP64 checker on the data the form samples, one T=256 round"}
 
 
+def headline_config(args):
+    """The default line's workload description (the reference arm reports the same one)."""
+    return {"workload": WORKLOAD, "N_per_gpu": N_PARTICLES, "T_rounds": ROUNDS_T,
+            "move": "MALA", "l2": "flushed between timed steps (256 MiB write)",
+            "log_weights": "f64", "contraction": args.contraction,
+            "final_reweighting_to_X": args.contraction != "fp32"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -252,7 +260,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ps_per_job / v,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+        "data": "synthetic", "config": headline_config(args),
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -432,10 +440,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"bf16_tc": "bf16", "bf16_tc_stream": "f16 (bf16-valued X)", "fp32": "f32"}[args.contraction],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N_per_gpu": N_PARTICLES, "T_rounds": ROUNDS_T,
-                       "move": "MALA", "l2": "flushed between timed steps (256 MiB write)",
-                       "log_weights": "f64", "contraction": args.contraction,
-                       "final_reweighting_to_X": args.contraction != "fp32"},
+            "config": headline_config(args),
             "logZ_minus_other_form": (None if compare is None else {
                 "value": last[-1]["logZ"] - compare["logZ_last_round"],
                 "se": float(np.hypot(last[-1]["se"], compare["se_last_round"])),
