@@ -237,18 +237,21 @@ asmc_cdf_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N,
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void gather_one(const AsmcState* st, const StepParams& P, int d, int grad,
-                                           const double* __restrict__ cdf, int64_t* ancestors, int64_t n)
+// a = min{m in [lo, hi] : C_m > thr}, or hi when there is none (C read through `c`)
+template <class C>
+__device__ __forceinline__ int64_t first_above(C c, int64_t lo, int64_t hi, double thr)
 {
-    const double thr = ((double)n + st->U) / (double)P.N;
-    // a = min{m : C_m > thr}, clamped to N - 1
-    int64_t lo = 0, hi = P.N - 1;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (cdf[mid] > thr) hi = mid; else lo = mid + 1;
+        if (c(mid) > thr) hi = mid; else lo = mid + 1;
     }
-    const int64_t a = lo;
+    return lo;
+}
+
+template <typename R>
+__device__ __forceinline__ void gather_one(const AsmcState* st, const StepParams& P, int d, int grad,
+                                           int64_t* ancestors, int64_t n, int64_t a)
+{
     const int src = st->cur, dst = src ^ 1;
     const R* xs = reinterpret_cast<const R*>(P.x[src]);
     R* xd = reinterpret_cast<R*>(P.x[dst]);
@@ -263,14 +266,43 @@ __device__ __forceinline__ void gather_one(const AsmcState* st, const StepParams
     if (ancestors) ancestors[n] = a;
 }
 
+// Systematic resampling's ancestors a^n = min{m : C_m > (n + U)/N} (clamped to N - 1) are
+// non-decreasing in n, so a CTA's 256 consecutive particles descend from the window
+// [a^{first}, a^{last}] of the CDF: two searches over the whole CDF bound it, the window is
+// staged in shared memory (when it has at most kGatherWin entries) and each particle searches
+// there with the same comparisons, instead of a search of ~log2 N dependent loads per particle.
+constexpr int kGatherWin = 2048;
 template <typename R>
 __global__ void __launch_bounds__(256)
 asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const double* __restrict__ cdf,
                    int64_t* ancestors)
 {
     if (!st->pend) return;
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < P.N; n += (int64_t)gridDim.x * blockDim.x)
-        gather_one<R>(st, P, d, grad, cdf, ancestors, n);
+    __shared__ int64_t s_range[2];
+    __shared__ double s_c[kGatherWin];
+    const double U = st->U, Nd = (double)P.N;
+    auto gc = [&](int64_t m) { return cdf[m]; };
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < P.N; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = base + threadIdx.x;
+        const int64_t last = min(base + (int64_t)blockDim.x, P.N) - 1;
+        if (threadIdx.x < 2) {
+            const int64_t nn = threadIdx.x == 0 ? base : last;
+            s_range[threadIdx.x] = first_above(gc, 0, P.N - 1, ((double)nn + U) / Nd);
+        }
+        __syncthreads();
+        const int64_t lo = s_range[0], hi = s_range[1], w = hi - lo + 1;
+        int64_t a = 0;
+        if (w <= kGatherWin) {
+            for (int64_t j = threadIdx.x; j < w; j += blockDim.x) s_c[j] = cdf[lo + j];
+            __syncthreads();
+            if (n < P.N)
+                a = lo + first_above([&](int64_t m) { return s_c[m]; }, 0, w - 1, ((double)n + U) / Nd);
+        } else if (n < P.N) {
+            a = first_above(gc, lo, hi, ((double)n + U) / Nd);
+        }
+        if (n < P.N) gather_one<R>(st, P, d, grad, ancestors, n, a);
+        __syncthreads();                 // s_range and s_c are rewritten by the next block
+    }
 }
 
 int capped_grid(int64_t want, int per_sm)
@@ -311,7 +343,7 @@ cudaError_t launch_asmc_resample(AsmcState* st, const StepParams& P, int nparts,
     asmc_blocksum_kernel<<<gs, kScanThreads, 0, s>>>(st, P.logw, P.N, nb, bsum);
     asmc_offsets_kernel<<<1, kScanThreads, 0, s>>>(st, bsum, nb, boff);
     asmc_cdf_kernel<<<gs, kScanThreads, 0, s>>>(st, P.logw, P.N, nb, boff, cdf);
-    const int gb = capped_grid((P.N + 255) / 256, 4);
+    const int gb = capped_grid((P.N + 255) / 256, 8);
     if (fp64) asmc_gather_kernel<double><<<gb, 256, 0, s>>>(st, P, d, grad ? 1 : 0, cdf, ancestors);
     else      asmc_gather_kernel<float><<<gb, 256, 0, s>>>(st, P, d, grad ? 1 : 0, cdf, ancestors);
     return cudaGetLastError();
