@@ -237,71 +237,45 @@ asmc_cdf_kernel(const AsmcState* st, const double* __restrict__ logw, int64_t N,
     }
 }
 
-// a = min{m in [lo, hi] : C_m > thr}, or hi when there is none (C read through `c`)
-template <class C>
-__device__ __forceinline__ int64_t first_above(C c, int64_t lo, int64_t hi, double thr)
-{
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (c(mid) > thr) hi = mid; else lo = mid + 1;
-    }
-    return lo;
-}
-
+// Systematic resampling: particle n takes ancestor a^n = min{m : C_m > (n + U)/N}, clamped to
+// N - 1 (binary search over the CDF), and copies that ancestor's state.  The copy loads eight
+// coordinates before storing them (the source and destination buffers are distinct, which the
+// compiler cannot see), so that a particle's loads are in flight together.
 template <typename R>
-__device__ __forceinline__ void gather_one(const AsmcState* st, const StepParams& P, int d, int grad,
-                                           int64_t* ancestors, int64_t n, int64_t a)
+__device__ __forceinline__ void copy_rows(const R* __restrict__ src, R* __restrict__ dst, int d, int64_t N,
+                                          int64_t from, int64_t to)
 {
-    const int src = st->cur, dst = src ^ 1;
-    const R* xs = reinterpret_cast<const R*>(P.x[src]);
-    R* xd = reinterpret_cast<R*>(P.x[dst]);
-    for (int i = 0; i < d; ++i) xd[(size_t)i * P.N + n] = xs[(size_t)i * P.N + a];
-    if (grad) {
-        const R* gs = reinterpret_cast<const R*>(P.gl[src]);
-        R* gd = reinterpret_cast<R*>(P.gl[dst]);
-        for (int i = 0; i < d; ++i) gd[(size_t)i * P.N + n] = gs[(size_t)i * P.N + a];
+    for (int i0 = 0; i0 < d; i0 += 8) {
+        R v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = i0 + j < d ? src[(size_t)(i0 + j) * N + from] : R(0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (i0 + j < d) dst[(size_t)(i0 + j) * N + to] = v[j];
     }
-    P.ell[dst][n] = P.ell[src][a];
-    P.logw[n] = 0.0;
-    if (ancestors) ancestors[n] = a;
 }
 
-// Systematic resampling's ancestors a^n = min{m : C_m > (n + U)/N} (clamped to N - 1) are
-// non-decreasing in n, so a CTA's 256 consecutive particles descend from the window
-// [a^{first}, a^{last}] of the CDF: two searches over the whole CDF bound it, the window is
-// staged in shared memory (when it has at most kGatherWin entries) and each particle searches
-// there with the same comparisons, instead of a search of ~log2 N dependent loads per particle.
-constexpr int kGatherWin = 2048;
 template <typename R>
 __global__ void __launch_bounds__(256)
 asmc_gather_kernel(const AsmcState* st, StepParams P, int d, int grad, const double* __restrict__ cdf,
                    int64_t* ancestors)
 {
     if (!st->pend) return;
-    __shared__ int64_t s_range[2];
-    __shared__ double s_c[kGatherWin];
     const double U = st->U, Nd = (double)P.N;
-    auto gc = [&](int64_t m) { return cdf[m]; };
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < P.N; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = base + threadIdx.x;
-        const int64_t last = min(base + (int64_t)blockDim.x, P.N) - 1;
-        if (threadIdx.x < 2) {
-            const int64_t nn = threadIdx.x == 0 ? base : last;
-            s_range[threadIdx.x] = first_above(gc, 0, P.N - 1, ((double)nn + U) / Nd);
+    const int src = st->cur, dst = src ^ 1;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < P.N; n += (int64_t)gridDim.x * blockDim.x) {
+        const double thr = ((double)n + U) / Nd;
+        int64_t lo = 0, hi = P.N - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cdf[mid] > thr) hi = mid; else lo = mid + 1;
         }
-        __syncthreads();
-        const int64_t lo = s_range[0], hi = s_range[1], w = hi - lo + 1;
-        int64_t a = 0;
-        if (w <= kGatherWin) {
-            for (int64_t j = threadIdx.x; j < w; j += blockDim.x) s_c[j] = cdf[lo + j];
-            __syncthreads();
-            if (n < P.N)
-                a = lo + first_above([&](int64_t m) { return s_c[m]; }, 0, w - 1, ((double)n + U) / Nd);
-        } else if (n < P.N) {
-            a = first_above(gc, lo, hi, ((double)n + U) / Nd);
-        }
-        if (n < P.N) gather_one<R>(st, P, d, grad, ancestors, n, a);
-        __syncthreads();                 // s_range and s_c are rewritten by the next block
+        const int64_t a = lo;
+        copy_rows<R>(reinterpret_cast<const R*>(P.x[src]), reinterpret_cast<R*>(P.x[dst]), d, P.N, a, n);
+        if (grad) copy_rows<R>(reinterpret_cast<const R*>(P.gl[src]), reinterpret_cast<R*>(P.gl[dst]), d, P.N, a, n);
+        P.ell[dst][n] = P.ell[src][a];
+        P.logw[n] = 0.0;
+        if (ancestors) ancestors[n] = a;
     }
 }
 
