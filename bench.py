@@ -694,7 +694,8 @@ def line_batched(args, steps, warmup, compare_sequential):
     peaks, src = measured_peaks()
     tpeak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1e12
     # per problem the binding unit: special-function work (1 ex2 + 1 rcp per row and
-    # evaluation, 1 lg2 per 32-row half chunk) or the tensor pipe (two-term split: 8 n d FLOP
+    # evaluation, 1 lg2 per 32-row half of a 64-row chunk: the 64-row shape's count, one lg2 more
+    # per 64 rows than 128-row chunks take) or the tensor pipe (two-term split: 8 n d FLOP
     # per evaluation); the roofline time of the job is the sum of the per-problem maxima
     sec_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (32.0 * rates["lg2"])
     t_bound = 0.0

@@ -79,7 +79,7 @@ CASES = [
     ("linreg", 300, 20, 300, 4, oais.HMC, 3),     # d_pad 32 (64B swizzle), ragged rows and tiles
     ("linreg", 130, 70, 256, 3, oais.MALA, 1),    # d_pad 128: two 128B slabs
     ("logreg", 1000, 8, 200, 4, oais.MALA, 1),    # d_pad 16 (32B swizzle)
-    ("linreg", 100, 256, 200, 2, oais.HMC, 5),    # d_pad 256: 32-row chunks, four slabs
+    ("linreg", 100, 256, 200, 2, oais.HMC, 5),    # d_pad 256: 64-row chunks, four slabs
     ("logreg", 777, 64, 129, 3, oais.MALA, 1),    # d_pad 64, one lone particle in the last tile
     ("linreg", 64, 16, 128, 5, oais.HMC, 2),      # a single full chunk and a single tile
 ]
