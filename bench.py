@@ -694,15 +694,17 @@ def line_batched(args, steps, warmup, compare_sequential):
     peaks, src = measured_peaks()
     tpeak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1e12
     # per problem the binding unit: special-function work (1 ex2 + 1 rcp per row and
-    # evaluation, 1 lg2 per 32-row half of a 64-row chunk: the 64-row shape's count, one lg2 more
-    # per 64 rows than 128-row chunks take) or the tensor pipe (two-term split: 8 n d FLOP
-    # per evaluation); the roofline time of the job is the sum of the per-problem maxima
-    sec_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (32.0 * rates["lg2"])
+    # evaluation, and 1 lg2 per half chunk, the rows one of a particle's two threads takes, at
+    # the chunk rows the problem's width class runs) or the tensor pipe (two-term split: 8 n d
+    # FLOP per evaluation); the roofline time of the job is the sum of the per-problem maxima
     t_bound = 0.0
     for pr in probs:
+        dp = 16 if pr.d <= 16 else 32 if pr.d <= 32 else 64 if pr.d <= 64 else 128
+        half_chunk = (shapes[{16: 0, 32: 1, 64: 2, 128: 3}[dp]][0] or 64) / 2.0
+        sec_row_sm = 1.0 / rates["ex2"] + 1.0 / rates["rcp"] + 1.0 / (half_chunk * rates["lg2"])
         ev = N * (1 + T) * R
         t_sfu = pr.n * ev * sec_row_sm / N_SM
-        t_tc = 8.0 * pr.n * (16 if pr.d <= 16 else 32 if pr.d <= 32 else 64 if pr.d <= 64 else 128) * ev / tpeak
+        t_tc = 8.0 * pr.n * dp * ev / tpeak
         t_bound += max(t_sfu, t_tc)
     line = {
         "metric": METRIC, "value": ps * steps / (total / 1e3), "unit": METRIC, "n_gpus": 1,
